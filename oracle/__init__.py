@@ -1,0 +1,210 @@
+"""Plain FP64 CPU oracle of the finite-volume shallow-water step (ctypes binding).
+
+TEST INFRASTRUCTURE.  Only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference leg may import this package.  It shares no
+code with the CUDA library in ``paper_2002_04889_gb300`` and never calls it.
+
+The arithmetic lives in ``volna_oracle.c`` (built by ``oracle.build``); this
+module only marshals numpy arrays.  Every function cites the section of
+Giles et al., "Performance analysis of Volna-OP2", that it follows.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import library_path, build as _build
+
+_lib = None
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_I64 = C.POINTER(C.c_int64)
+
+
+class Params(C.Structure):
+    """Scheme parameters: g (9.81), CFL, H_threshold (Sec. 2.4), fixed / max dt,
+    end time, and order (1 first order, 2 MUSCL reconstruction of Sec. 2.4)."""
+    _fields_ = [("g", C.c_double), ("cfl", C.c_double), ("h_threshold", C.c_double),
+                ("dt_fixed", C.c_double), ("dt_max", C.c_double), ("t_end", C.c_double),
+                ("order", C.c_int32), ("pad", C.c_int32)]
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        _build()
+    lib = C.CDLL(path)
+    lib.vo_mesh_build.argtypes = [C.c_int64, _D, C.c_int64, _I32, _D, C.POINTER(C.c_void_p)]
+    lib.vo_mesh_build.restype = C.c_int
+    lib.vo_mesh_free.argtypes = [C.c_void_p]
+    lib.vo_default_params.argtypes = [C.POINTER(Params)]
+    lib.vo_hll_normal.argtypes = [C.c_double] * 7 + [_D, _D]
+    lib.vo_hll_speeds.argtypes = [C.c_double] * 5 + [_D]
+    lib.vo_face_flux.argtypes = ([C.c_double] * 10 + [C.c_double, C.c_double, C.c_int]
+                                 + [_D, _D, _D, _D])
+    lib.vo_reconstruct_cell.argtypes = [C.c_void_p, C.POINTER(Params), _D, _D, _D, C.c_int64,
+                                        _D, _D, _D]
+    lib.vo_residual.argtypes = [C.c_void_p, C.POINTER(Params), _D, _D, _D, _D, _D, _D, _D]
+    lib.vo_time_step.argtypes = [C.c_void_p, C.POINTER(Params), _D, C.c_double]
+    lib.vo_time_step.restype = C.c_double
+    lib.vo_step.argtypes = [C.c_void_p, C.POINTER(Params), _D, _D, _D, _D, _D, _I64]
+    lib.vo_run.argtypes = [C.c_void_p, C.POINTER(Params), _D, _D, _D, _D, C.c_int64, _D, _I64,
+                           C.c_int32, _I32, _D]
+    lib.vo_run.restype = C.c_int64
+    lib.vo_locate.argtypes = [C.c_void_p, _D, C.c_int32, _D, _I32]
+    lib.vo_mesh_get.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+    lib.vo_mesh_get.restype = C.c_int
+    lib.vo_mesh_n_flipped.argtypes = [C.c_void_p]
+    lib.vo_mesh_n_flipped.restype = C.c_int64
+    lib.vo_set_threads.argtypes = [C.c_int]
+    lib.vo_max_threads.restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads for the cell and edge loops (results do not depend on it)."""
+    _load().vo_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(_load().vo_max_threads())
+
+
+def params(g=9.81, cfl=0.9, h_threshold=1e-5, dt_fixed=0.0, dt_max=0.0, t_end=0.0,
+           order=2) -> Params:
+    return Params(g, cfl, h_threshold, dt_fixed, dt_max, t_end, order, 0)
+
+
+def hll_normal(g, HL, unL, utL, HR, unR, utR):
+    """HLL flux in the normal frame with the Sec. 2.2 wave speeds; returns (F[3], a)."""
+    F = np.zeros(3)
+    a = C.c_double()
+    _load().vo_hll_normal(g, HL, unL, utL, HR, unR, utR, _dp(F), C.byref(a))
+    return F, a.value
+
+
+def hll_speeds(g, HL, unL, HR, unR):
+    """(s_L, s_R) of Sec. 2.2 (dry-bed speeds when one side is dry)."""
+    s = np.zeros(2)
+    _load().vo_hll_speeds(g, HL, unL, HR, unR, _dp(s))
+    return float(s[0]), float(s[1])
+
+
+def face_flux(g, hthr, left, zL, right, zR, n, wall=False):
+    """Flux through a face seen from the left cell (hydrostatic reconstruction +
+    HLL, Sec. 2.2; wall ghost of Sec. 2.5).  left/right = (H_f, Hu_f, Hv_f).
+    Returns (Phi[3], P_L, P_R, a)."""
+    Phi = np.zeros(3)
+    PL, PR, a = C.c_double(), C.c_double(), C.c_double()
+    r = right if right is not None else (0.0, 0.0, 0.0)
+    _load().vo_face_flux(g, hthr, left[0], left[1], left[2], zL, r[0], r[1], r[2], zR,
+                         n[0], n[1], 1 if wall else 0, _dp(Phi), C.byref(PL), C.byref(PR),
+                         C.byref(a))
+    return Phi, PL.value, PR.value, a.value
+
+
+class OracleMesh:
+    """Mesh with geometry, adjacency and bed of Sec. 2 (see volna_oracle.c)."""
+
+    _FIELDS = {"vtx": (0, np.int32, 3), "nbr": (1, np.int32, 3), "nbr_face": (2, np.int32, 3),
+               "z": (3, np.float64, 1), "area": (4, np.float64, 1), "cx": (5, np.float64, 1),
+               "cy": (6, np.float64, 1), "nx": (7, np.float64, 3), "ny": (8, np.float64, 3),
+               "len": (9, np.float64, 3), "fx": (10, np.float64, 3), "fy": (11, np.float64, 3),
+               "wx": (12, np.float64, 3), "wy": (13, np.float64, 3), "dx": (14, np.float64, 3),
+               "dy": (15, np.float64, 3)}
+
+    def __init__(self, xy, tri, depth):
+        lib = _load()
+        self.xy = _f64(xy).reshape(-1, 2)
+        self.tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
+        self.depth = _f64(depth)
+        h = C.c_void_p()
+        rc = lib.vo_mesh_build(self.xy.shape[0], _dp(self.xy), self.tri.shape[0],
+                               self.tri.ctypes.data_as(_I32), _dp(self.depth), C.byref(h))
+        if rc != 0:
+            raise ValueError(f"oracle mesh rejected (code {rc})")
+        self._h = h
+        self.nc = self.tri.shape[0]
+
+    @classmethod
+    def from_mesh(cls, mesh):
+        return cls(mesh.xy, mesh.tri, mesh.depth)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.vo_mesh_free(self._h)
+            self._h = None
+
+    def get(self, name):
+        what, dt, k = self._FIELDS[name]
+        out = np.empty(self.nc * k, dtype=dt)
+        _load().vo_mesh_get(self._h, what, out.ctypes.data_as(C.c_void_p))
+        return out.reshape(self.nc, 3) if k == 3 else out
+
+    @property
+    def n_flipped(self):
+        return int(_load().vo_mesh_n_flipped(self._h))
+
+    def reconstruct_cell(self, prm, H, Hu, Hv, K):
+        """Face values (H_f, Hu_f, Hv_f) of cell K (Sec. 2.4)."""
+        H, Hu, Hv = _f64(H), _f64(Hu), _f64(Hv)
+        o = [np.zeros(3) for _ in range(3)]
+        _load().vo_reconstruct_cell(self._h, C.byref(prm), _dp(H), _dp(Hu), _dp(Hv), int(K),
+                                    _dp(o[0]), _dp(o[1]), _dp(o[2]))
+        return o
+
+    def residual(self, prm, H, Hu, Hv):
+        """L(w) and per-cell max l_f a_f (Sec. 2.2)."""
+        H, Hu, Hv = _f64(H), _f64(Hu), _f64(Hv)
+        R = [np.zeros(self.nc) for _ in range(3)]
+        am = np.zeros(self.nc)
+        _load().vo_residual(self._h, C.byref(prm), _dp(H), _dp(Hu), _dp(Hv),
+                            _dp(R[0]), _dp(R[1]), _dp(R[2]), _dp(am))
+        return R, am
+
+    def time_step(self, prm, amax, t):
+        return float(_load().vo_time_step(self._h, C.byref(prm), _dp(_f64(amax)), float(t)))
+
+    def locate(self, pts):
+        pts = _f64(pts).reshape(-1, 2)
+        out = np.zeros(pts.shape[0], dtype=np.int32)
+        _load().vo_locate(self._h, _dp(self.xy), pts.shape[0], _dp(pts), out.ctypes.data_as(_I32))
+        return out
+
+    def run(self, prm, state, n_steps, gauge_cells=None):
+        """n SSP-RK(2,2) steps (Sec. 2.3) from state (H, Hu, Hv, t), on copies.
+        Returns dict(H, Hu, Hv, t, dts, neg_count, gauges[n_steps, G])."""
+        H, Hu, Hv = _f64(state[0]).copy(), _f64(state[1]).copy(), _f64(state[2]).copy()
+        t = C.c_double(float(state[3]) if len(state) > 3 else 0.0)
+        dts = np.zeros(max(int(n_steps), 1))
+        neg = C.c_int64(0)
+        if gauge_cells is not None and len(gauge_cells):
+            gc = np.ascontiguousarray(gauge_cells, dtype=np.int32)
+            ge = np.zeros((max(int(n_steps), 1), gc.shape[0]))
+            _load().vo_run(self._h, C.byref(prm), _dp(H), _dp(Hu), _dp(Hv), C.byref(t),
+                           int(n_steps), _dp(dts), C.byref(neg), gc.shape[0],
+                           gc.ctypes.data_as(_I32), _dp(ge))
+        else:
+            ge = None
+            _load().vo_run(self._h, C.byref(prm), _dp(H), _dp(Hu), _dp(Hv), C.byref(t),
+                           int(n_steps), _dp(dts), C.byref(neg), 0, None, None)
+        return dict(H=H, Hu=Hu, Hv=Hv, t=t.value, dts=dts[:n_steps], neg_count=neg.value,
+                    gauges=None if ge is None else ge[:n_steps])
+
+    def mass(self, H):
+        """Discrete mass sum_K |K| H_K."""
+        return float(np.sum(self.get("area") * _f64(H)))

@@ -1,0 +1,36 @@
+"""Compile the oracle's C source into a shared library beside it.
+
+TEST INFRASTRUCTURE (see oracle/__init__.py).  gcc with -O2 -ffp-contract=off,
+so no multiply-add is contracted and every expression rounds as written, and
+with OpenMP for the cell and edge loops.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "volna_oracle.c")
+
+
+def library_path() -> str:
+    return os.path.join(HERE, "_build", "libvolna_oracle.so")
+
+
+def build(verbose: bool = False) -> str:
+    out = library_path()
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(SRC):
+        return out
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+           "-std=c11", "-Wall", "-o", out + ".tmp", SRC, "-lm"]
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    subprocess.run(cmd, check=True)
+    os.replace(out + ".tmp", out)
+    return out
+
+
+if __name__ == "__main__":
+    print(build(verbose=True))

@@ -1,0 +1,679 @@
+/*
+ * volna_oracle.c -- plain, slow FP64 CPU oracle of one explicit time step of the
+ * cell-centred finite-volume scheme for the 2D nonlinear shallow water equations
+ * of Giles et al., "Performance analysis of Volna-OP2" (Sec. 2).
+ *
+ * TEST INFRASTRUCTURE.  Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load or call this file.  It shares no code, header,
+ * table or helper with the CUDA library and never calls it.
+ *
+ * Build with -O2 -ffp-contract=off: no multiply-add contraction, so every
+ * expression rounds exactly as written.  Loops over cells and edges may run
+ * under OpenMP; each thread writes only its own cells, so results do not depend
+ * on the thread count.
+ *
+ * The method, step by step (each function cites what it follows):
+ *   geometry            cell area, centroid, outward unit normals, face midpoints
+ *   bed                 z_K = -(mean of the three vertex depths)        (Sec. 2.1)
+ *   reconstruction      least-squares gradient + Barth-Jespersen limiter,
+ *                       skipped in the wet/dry zone                      (Sec. 2.4, Eq. recon)
+ *   interface           hydrostatic reconstruction of the two face depths (reading of
+ *                       the wet/dry treatment named in Sec. 2.1)
+ *   numerical flux      HLL with the wave speeds of Sec. 2.2, dry-bed speeds
+ *   wall                ghost state with mirrored normal velocity        (Sec. 2.5)
+ *   residual            edge fluxes gathered per cell in a fixed local order (Sec. 2.2)
+ *   time step           CFL condition (reading of Sec. 2.3), SSP-RK(2,2) (Sec. 2.3)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define VO_OK 0
+#define VO_EINVAL (-1)
+#define VO_ENOMEM (-2)
+
+typedef struct vo_params {
+    double g;            /* gravity, m s^-2 (the paper does not state it: 9.81) */
+    double cfl;          /* Courant number of the time-step rule            */
+    double h_threshold;  /* dry threshold H_threshold (Sec. 2.4)             */
+    double dt_fixed;     /* > 0: use this time step instead of the CFL rule   */
+    double dt_max;       /* > 0: upper clamp on the time step                 */
+    double t_end;        /* > 0: the last step ends exactly at t_end          */
+    int32_t order;       /* 1: first order (no reconstruction); 2: MUSCL      */
+    int32_t pad;
+} vo_params;
+
+typedef struct vo_mesh {
+    int64_t nv, nc;
+    int64_t n_flipped;   /* clockwise input triangles that were reoriented */
+    int32_t *vtx;        /* [nc][3] vertex ids in local order              */
+    int32_t *nbr;        /* [nc][3] neighbour across face f, -1 = wall      */
+    int32_t *nbr_face;   /* [nc][3] the same face seen from the neighbour   */
+    double *z, *area, *cx, *cy;                 /* [nc]                     */
+    double *nx, *ny, *len, *fx, *fy;            /* [nc][3] per face         */
+    double *dx, *dy, *wx, *wy;                  /* [nc][3] LSQ stencil      */
+    /* work arrays of the residual */
+    double *Hf, *Huf, *Hvf;                     /* [nc][3] face values      */
+    double *slot;                               /* [nc][3][6] edge results  */
+    double *R0, *R1, *W1, *amax;                /* [3][nc], [3][nc], [3][nc], [nc] */
+} vo_mesh;
+
+void vo_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
+int vo_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void vo_default_params(vo_params *p)
+{
+    p->g = 9.81;
+    p->cfl = 0.9;
+    p->h_threshold = 1e-5;
+    p->dt_fixed = 0.0;
+    p->dt_max = 0.0;
+    p->t_end = 0.0;
+    p->order = 2;
+    p->pad = 0;
+}
+
+void vo_mesh_free(vo_mesh *m)
+{
+    if (!m) return;
+    free(m->vtx); free(m->nbr); free(m->nbr_face);
+    free(m->z); free(m->area); free(m->cx); free(m->cy);
+    free(m->nx); free(m->ny); free(m->len); free(m->fx); free(m->fy);
+    free(m->dx); free(m->dy); free(m->wx); free(m->wy);
+    free(m->Hf); free(m->Huf); free(m->Hvf); free(m->slot);
+    free(m->R0); free(m->R1); free(m->W1); free(m->amax);
+    free(m);
+}
+
+/*
+ * Build the mesh: orientation, local face order, face adjacency and geometry.
+ *
+ * Local order: each triangle is made counter-clockwise (a clockwise input is
+ * reoriented and counted), then rotated so that its first vertex has the
+ * smallest input vertex id.  Face f joins local vertices f and f+1 (mod 3).
+ * This fixes every summation order independently of how cells are numbered.
+ *
+ * Returns VO_EINVAL for an out-of-range or repeated vertex id, a zero-area
+ * triangle, or an edge shared by more than two triangles (or twice in the same
+ * direction).
+ */
+int vo_mesh_build(int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
+                  const double *depth_v, vo_mesh **out)
+{
+    *out = NULL;
+    if (nv < 3 || nc < 1 || !xy || !tri || !depth_v) return VO_EINVAL;
+    vo_mesh *m = (vo_mesh *)calloc(1, sizeof(vo_mesh));
+    if (!m) return VO_ENOMEM;
+    m->nv = nv;
+    m->nc = nc;
+    size_t n3 = (size_t)nc * 3;
+#define VO_ALLOC(p, n, T) do { (p) = (T *)malloc(sizeof(T) * (size_t)(n)); if (!(p)) { vo_mesh_free(m); return VO_ENOMEM; } } while (0)
+    VO_ALLOC(m->vtx, n3, int32_t);
+    VO_ALLOC(m->nbr, n3, int32_t);
+    VO_ALLOC(m->nbr_face, n3, int32_t);
+    VO_ALLOC(m->z, nc, double);
+    VO_ALLOC(m->area, nc, double);
+    VO_ALLOC(m->cx, nc, double);
+    VO_ALLOC(m->cy, nc, double);
+    VO_ALLOC(m->nx, n3, double);
+    VO_ALLOC(m->ny, n3, double);
+    VO_ALLOC(m->len, n3, double);
+    VO_ALLOC(m->fx, n3, double);
+    VO_ALLOC(m->fy, n3, double);
+    VO_ALLOC(m->dx, n3, double);
+    VO_ALLOC(m->dy, n3, double);
+    VO_ALLOC(m->wx, n3, double);
+    VO_ALLOC(m->wy, n3, double);
+    VO_ALLOC(m->Hf, n3, double);
+    VO_ALLOC(m->Huf, n3, double);
+    VO_ALLOC(m->Hvf, n3, double);
+    VO_ALLOC(m->slot, n3 * 6, double);
+    VO_ALLOC(m->R0, n3, double);
+    VO_ALLOC(m->R1, n3, double);
+    VO_ALLOC(m->W1, n3, double);
+    VO_ALLOC(m->amax, nc, double);
+
+    /* orientation and local order */
+    for (int64_t c = 0; c < nc; c++) {
+        int32_t a = tri[3 * c], b = tri[3 * c + 1], d = tri[3 * c + 2];
+        if (a < 0 || b < 0 || d < 0 || a >= nv || b >= nv || d >= nv || a == b || b == d || a == d) {
+            vo_mesh_free(m);
+            return VO_EINVAL;
+        }
+        double s = (xy[2 * b] - xy[2 * a]) * (xy[2 * d + 1] - xy[2 * a + 1])
+                 - (xy[2 * b + 1] - xy[2 * a + 1]) * (xy[2 * d] - xy[2 * a]);
+        if (s == 0.0) { vo_mesh_free(m); return VO_EINVAL; }
+        int32_t v[3] = {a, b, d};
+        if (s < 0.0) { v[1] = d; v[2] = b; m->n_flipped++; }
+        int k0 = 0;
+        if (v[1] < v[k0]) k0 = 1;
+        if (v[2] < v[k0]) k0 = 2;
+        for (int k = 0; k < 3; k++) m->vtx[3 * c + k] = v[(k0 + k) % 3];
+    }
+
+    /* face adjacency through the cells around each vertex */
+    int64_t *start = (int64_t *)calloc((size_t)nv + 1, sizeof(int64_t));
+    int32_t *list = (int32_t *)malloc(sizeof(int32_t) * n3);
+    if (!start || !list) { free(start); free(list); vo_mesh_free(m); return VO_ENOMEM; }
+    for (size_t i = 0; i < n3; i++) start[m->vtx[i] + 1]++;
+    for (int64_t v = 0; v < nv; v++) start[v + 1] += start[v];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)nv);
+    if (!fill) { free(start); free(list); vo_mesh_free(m); return VO_ENOMEM; }
+    memcpy(fill, start, sizeof(int64_t) * (size_t)nv);
+    for (int64_t c = 0; c < nc; c++)
+        for (int k = 0; k < 3; k++) list[fill[m->vtx[3 * c + k]]++] = (int32_t)c;
+    free(fill);
+    int bad = 0;
+    for (int64_t c = 0; c < nc && !bad; c++) {
+        for (int f = 0; f < 3; f++) {
+            int32_t p = m->vtx[3 * c + f], q = m->vtx[3 * c + (f + 1) % 3];
+            int found = 0;
+            m->nbr[3 * c + f] = -1;
+            m->nbr_face[3 * c + f] = -1;
+            for (int64_t i = start[p]; i < start[p + 1]; i++) {
+                int32_t d = list[i];
+                if (d == c) continue;
+                for (int g = 0; g < 3; g++) {
+                    int32_t a = m->vtx[3 * (int64_t)d + g], b = m->vtx[3 * (int64_t)d + (g + 1) % 3];
+                    if (a == q && b == p) {          /* the same edge, opposite direction */
+                        found++;
+                        m->nbr[3 * c + f] = d;
+                        m->nbr_face[3 * c + f] = g;
+                    } else if (a == p && b == q) {   /* same direction: not a manifold */
+                        bad = 1;
+                    }
+                }
+            }
+            if (found > 1) bad = 1;
+        }
+    }
+    free(start);
+    free(list);
+    if (bad) { vo_mesh_free(m); return VO_EINVAL; }
+
+    /* per-cell geometry and bed */
+    for (int64_t c = 0; c < nc; c++) {
+        const int32_t *v = m->vtx + 3 * c;
+        double ax = xy[2 * v[0]], ay = xy[2 * v[0] + 1];
+        double bx = xy[2 * v[1]], by = xy[2 * v[1] + 1];
+        double qx = xy[2 * v[2]], qy = xy[2 * v[2] + 1];
+        m->area[c] = 0.5 * ((bx - ax) * (qy - ay) - (by - ay) * (qx - ax));
+        if (!(m->area[c] > 0.0)) { vo_mesh_free(m); return VO_EINVAL; }
+        m->cx[c] = ((ax + bx) + qx) / 3.0;
+        m->cy[c] = ((ay + by) + qy) / 3.0;
+        m->z[c] = -((depth_v[v[0]] + depth_v[v[1]]) + depth_v[v[2]]) / 3.0;
+        for (int f = 0; f < 3; f++) {
+            int32_t p = v[f], q = v[(f + 1) % 3];
+            double ex = xy[2 * q] - xy[2 * p];
+            double ey = xy[2 * q + 1] - xy[2 * p + 1];
+            double l = sqrt(ex * ex + ey * ey);
+            m->len[3 * c + f] = l;
+            m->nx[3 * c + f] = ey / l;        /* outward: right of p -> q for a CCW cell */
+            m->ny[3 * c + f] = -ex / l;
+            m->fx[3 * c + f] = 0.5 * (xy[2 * p] + xy[2 * q]) - m->cx[c];
+            m->fy[3 * c + f] = 0.5 * (xy[2 * p + 1] + xy[2 * q + 1]) - m->cy[c];
+        }
+    }
+    /* least-squares stencil: neighbour centroids, or the centroid mirrored across a wall */
+    for (int64_t c = 0; c < nc; c++) {
+        double Mxx = 0.0, Mxy = 0.0, Myy = 0.0;
+        for (int f = 0; f < 3; f++) {
+            int64_t i = 3 * c + f;
+            int32_t j = m->nbr[i];
+            if (j >= 0) {
+                m->dx[i] = m->cx[j] - m->cx[c];
+                m->dy[i] = m->cy[j] - m->cy[c];
+            } else {
+                double dn = m->fx[i] * m->nx[i] + m->fy[i] * m->ny[i];
+                m->dx[i] = 2.0 * dn * m->nx[i];
+                m->dy[i] = 2.0 * dn * m->ny[i];
+            }
+            Mxx = Mxx + m->dx[i] * m->dx[i];
+            Mxy = Mxy + m->dx[i] * m->dy[i];
+            Myy = Myy + m->dy[i] * m->dy[i];
+        }
+        double det = Mxx * Myy - Mxy * Mxy;
+        for (int f = 0; f < 3; f++) {
+            int64_t i = 3 * c + f;
+            m->wx[i] = (Myy * m->dx[i] - Mxy * m->dy[i]) / det;
+            m->wy[i] = (Mxx * m->dy[i] - Mxy * m->dx[i]) / det;
+        }
+    }
+    *out = m;
+    return VO_OK;
+}
+
+/* --------------------------------------------------------------------------
+ * Numerical flux (Sec. 2.2)
+ * -------------------------------------------------------------------------- */
+
+/*
+ * HLL flux in the face's normal frame.  Each side is (H, u_n, u_t): depth,
+ * velocity along the unit normal from L to R, and along t = (-n_y, n_x).
+ * Conserved variables in this frame are w = (H, H u_n, H u_t) and the physical
+ * flux is F(w) = (H u_n, H u_n^2 + g H^2 / 2, H u_n u_t).
+ *
+ * Wave speeds follow Sec. 2.2 (after Zhou 2002):
+ *   s_L = min(u_nL - c_L, u*_n - c*),  s_R = max(u*_n + c*, u_nR + c_R),
+ *   u*_n = (u_nL + u_nR)/2 + c_L - c_R,  c* = (c_L + c_R)/2 - (u_nR - u_nL)/4,
+ *   c = sqrt(g H).
+ * When one side is dry the textbook dry-bed speeds apply (reading of the
+ * shoreline Riemann problem named in Sec. 2.1): L dry: s_L = u_nR - 2 c_R,
+ * s_R = u_nR + c_R; R dry: s_L = u_nL - c_L, s_R = u_nL + 2 c_L.  Both dry:
+ * zero flux.  F = F_L if s_L >= 0, F* if s_L < 0 <= s_R, F_R if s_R < 0, with
+ *   F* = (s_R F_L - s_L F_R + s_L s_R (w_R - w_L)) / (s_R - s_L).
+ * *amax receives max(|s_L|, |s_R|).
+ */
+/* The two HLL wave speeds (s_L, s_R) of the normal-frame states; see below. */
+void vo_hll_speeds(double g, double HL, double unL, double HR, double unR, double s[2])
+{
+    double cL = sqrt(g * HL);
+    double cR = sqrt(g * HR);
+    if (HL == 0.0) {
+        s[0] = unR - 2.0 * cR;
+        s[1] = unR + cR;
+    } else if (HR == 0.0) {
+        s[0] = unL - cL;
+        s[1] = unL + 2.0 * cL;
+    } else {
+        double us = 0.5 * (unL + unR) + (cL - cR);
+        double cs = 0.5 * (cL + cR) - 0.25 * (unR - unL);
+        s[0] = fmin(unL - cL, us - cs);
+        s[1] = fmax(us + cs, unR + cR);
+    }
+}
+
+void vo_hll_normal(double g, double HL, double unL, double utL,
+                   double HR, double unR, double utR, double F[3], double *amax)
+{
+    if (HL == 0.0 && HR == 0.0) {
+        F[0] = 0.0; F[1] = 0.0; F[2] = 0.0;
+        *amax = 0.0;
+        return;
+    }
+    double s[2];
+    vo_hll_speeds(g, HL, unL, HR, unR, s);
+    double sL = s[0], sR = s[1];
+    double qL = HL * unL, qR = HR * unR;
+    double FL[3] = {qL, qL * unL + 0.5 * g * HL * HL, qL * utL};
+    double FR[3] = {qR, qR * unR + 0.5 * g * HR * HR, qR * utR};
+    double wL[3] = {HL, qL, HL * utL};
+    double wR[3] = {HR, qR, HR * utR};
+    if (sL >= 0.0) {
+        for (int k = 0; k < 3; k++) F[k] = FL[k];
+    } else if (sR >= 0.0) {
+        double den = sR - sL;
+        for (int k = 0; k < 3; k++)
+            F[k] = ((sR * FL[k] - sL * FR[k]) + (sL * sR) * (wR[k] - wL[k])) / den;
+    } else {
+        for (int k = 0; k < 3; k++) F[k] = FR[k];
+    }
+    *amax = fmax(fabs(sL), fabs(sR));
+}
+
+/*
+ * Flux through one face, seen from the left cell (outward unit normal n).
+ * Inputs are the two reconstructed face states (depth H_f, momenta) and the two
+ * cell beds.  Interface depths follow the hydrostatic reconstruction:
+ *   z* = max(z_L, z_R),  H*_s = max(0, H_{s,f} + z_s - z*);
+ * the face velocity is m_f / H_f where H_f > H_threshold, else 0, and the HLL
+ * states carry H* times that velocity.  A wall face (wall != 0) uses the ghost
+ * state of Sec. 2.5: same depth and bed, normal velocity reversed, tangential
+ * velocity kept.  Outputs: Phi (mass, x- and y-momentum flux along n), the two
+ * pressure corrections P_s = g (H_{s,f}^2 - H*_s^2) / 2 and the wave speed.
+ */
+void vo_face_flux(double g, double hthr,
+                  double HfL, double HufL, double HvfL, double zL,
+                  double HfR, double HufR, double HvfR, double zR,
+                  double nx, double ny, int wall,
+                  double Phi[3], double *PL, double *PR, double *amax)
+{
+    double uL = 0.0, vL = 0.0;
+    if (HfL > hthr) { uL = HufL / HfL; vL = HvfL / HfL; }
+    double unL = uL * nx + vL * ny;
+    double utL = -uL * ny + vL * nx;
+    double HsL, HsR, unR, utR;
+    if (wall) {
+        HsL = fmax(0.0, (HfL + zL) - zL);
+        HsR = HsL;
+        unR = -unL;
+        utR = utL;
+        HfR = HfL;
+    } else {
+        double uR = 0.0, vR = 0.0;
+        if (HfR > hthr) { uR = HufR / HfR; vR = HvfR / HfR; }
+        unR = uR * nx + vR * ny;
+        utR = -uR * ny + vR * nx;
+        double zs = fmax(zL, zR);
+        HsL = fmax(0.0, (HfL + zL) - zs);
+        HsR = fmax(0.0, (HfR + zR) - zs);
+    }
+    double F[3];
+    vo_hll_normal(g, HsL, unL, utL, HsR, unR, utR, F, amax);
+    Phi[0] = F[0];
+    Phi[1] = F[1] * nx - F[2] * ny;
+    Phi[2] = F[1] * ny + F[2] * nx;
+    *PL = 0.5 * g * (HfL * HfL - HsL * HsL);
+    *PR = 0.5 * g * (HfR * HfR - HsR * HsR);
+}
+
+/* --------------------------------------------------------------------------
+ * Reconstruction (Sec. 2.4)
+ * -------------------------------------------------------------------------- */
+
+/*
+ * Face values of cell K.  The reconstructed variables are eta = H + z, Hu, Hv.
+ * Each face neighbour contributes its cell value; a wall contributes the ghost
+ * of Sec. 2.5 (same eta, momentum mirrored: m - 2 (m.n) n).
+ *
+ * The cell reconstructs (Eq. recon: w(x_f) = w_K + alpha_K grad(w)_K . (x_f - x_K))
+ * only when it and every face neighbour are wetter than H_threshold and every
+ * reconstructed face depth H_f = eta_f - z_K stays above H_threshold; otherwise
+ * its face values are its cell values (the threshold rule of Sec. 2.4).
+ *   gradient: least squares over the three stencil offsets d_f,
+ *             grad q = sum_f w_f (q_f - q_K) with w_f = M^-1 d_f, M = sum d d^T;
+ *   limiter:  Barth-Jespersen per variable, alpha = min over faces of
+ *             min(1, (q_max - q_K)/D_f) if D_f > 0, min(1, (q_min - q_K)/D_f) if
+ *             D_f < 0, 1 if D_f = 0, with D_f = grad q . (x_f - x_K) and q_max,
+ *             q_min over the cell and its stencil values.
+ */
+void vo_reconstruct_cell(const vo_mesh *m, const vo_params *p, const double *H,
+                         const double *Hu, const double *Hv, int64_t K,
+                         double Hf[3], double Huf[3], double Hvf[3])
+{
+    double hthr = p->h_threshold;
+    double zK = m->z[K];
+    double qK[3] = {H[K] + zK, Hu[K], Hv[K]};
+    double qn[3][3];
+    int recon = (p->order == 2) && (H[K] > hthr);
+    for (int f = 0; f < 3; f++) {
+        int64_t i = 3 * K + f;
+        int32_t j = m->nbr[i];
+        if (j >= 0) {
+            qn[f][0] = H[j] + m->z[j];
+            qn[f][1] = Hu[j];
+            qn[f][2] = Hv[j];
+            if (!(H[j] > hthr)) recon = 0;
+        } else {
+            double mn = Hu[K] * m->nx[i] + Hv[K] * m->ny[i];
+            qn[f][0] = qK[0];
+            qn[f][1] = Hu[K] - 2.0 * mn * m->nx[i];
+            qn[f][2] = Hv[K] - 2.0 * mn * m->ny[i];
+        }
+    }
+    if (recon) {
+        double face[3][3];
+        for (int v = 0; v < 3; v++) {
+            const double *wx = m->wx + 3 * K, *wy = m->wy + 3 * K;
+            double gx = (wx[0] * (qn[0][v] - qK[v]) + wx[1] * (qn[1][v] - qK[v])) + wx[2] * (qn[2][v] - qK[v]);
+            double gy = (wy[0] * (qn[0][v] - qK[v]) + wy[1] * (qn[1][v] - qK[v])) + wy[2] * (qn[2][v] - qK[v]);
+            double qmax = qK[v], qmin = qK[v];
+            for (int f = 0; f < 3; f++) {
+                qmax = fmax(qmax, qn[f][v]);
+                qmin = fmin(qmin, qn[f][v]);
+            }
+            double alpha = 1.0;
+            for (int f = 0; f < 3; f++) {
+                double D = gx * m->fx[3 * K + f] + gy * m->fy[3 * K + f];
+                double phi = 1.0;
+                if (D > 0.0) phi = fmin(1.0, (qmax - qK[v]) / D);
+                else if (D < 0.0) phi = fmin(1.0, (qmin - qK[v]) / D);
+                alpha = fmin(alpha, phi);
+            }
+            for (int f = 0; f < 3; f++) {
+                double D = gx * m->fx[3 * K + f] + gy * m->fy[3 * K + f];
+                face[f][v] = qK[v] + alpha * D;
+            }
+        }
+        for (int f = 0; f < 3; f++) {
+            Hf[f] = face[f][0] - zK;
+            if (!(Hf[f] > hthr)) recon = 0;
+        }
+        if (recon) {
+            for (int f = 0; f < 3; f++) {
+                Huf[f] = face[f][1];
+                Hvf[f] = face[f][2];
+            }
+            return;
+        }
+    }
+    for (int f = 0; f < 3; f++) {
+        Hf[f] = H[K];
+        Huf[f] = Hu[K];
+        Hvf[f] = Hv[K];
+    }
+}
+
+/* --------------------------------------------------------------------------
+ * Residual L(w) (Sec. 2.2) and time step (Sec. 2.3)
+ * -------------------------------------------------------------------------- */
+
+/* A face is computed once, by the cell that owns it: the lower-numbered of the
+   two cells, or the only cell at a wall. */
+static int owns(const vo_mesh *m, int64_t K, int f)
+{
+    int32_t j = m->nbr[3 * K + f];
+    return j < 0 || K < j;
+}
+
+/*
+ * R = L(w): for every cell K,
+ *   R_K = -(1/|K|) sum_f l_f [ Phi_f + (0, P_{K,f} n_f) ],
+ * summed over the local faces f = 0, 1, 2 in that order, with Phi_f the flux out
+ * of K (the owner's edge flux, negated for the other cell) and P_{K,f} the
+ * pressure correction on K's side.  amax[K] = max_f l_f a_f (NULL: skipped).
+ */
+void vo_residual(vo_mesh *m, const vo_params *p, const double *H, const double *Hu,
+                 const double *Hv, double *RH, double *RHu, double *RHv, double *amax)
+{
+    int64_t nc = m->nc;
+    double g = p->g, hthr = p->h_threshold;
+#pragma omp parallel for schedule(static)
+    for (int64_t K = 0; K < nc; K++)
+        vo_reconstruct_cell(m, p, H, Hu, Hv, K, m->Hf + 3 * K, m->Huf + 3 * K, m->Hvf + 3 * K);
+
+#pragma omp parallel for schedule(static)
+    for (int64_t K = 0; K < nc; K++) {
+        for (int f = 0; f < 3; f++) {
+            if (!owns(m, K, f)) continue;
+            int64_t i = 3 * K + f;
+            int32_t j = m->nbr[i];
+            double *s = m->slot + 6 * i;
+            if (j >= 0) {
+                int64_t k = 3 * (int64_t)j + m->nbr_face[i];
+                vo_face_flux(g, hthr, m->Hf[i], m->Huf[i], m->Hvf[i], m->z[K],
+                             m->Hf[k], m->Huf[k], m->Hvf[k], m->z[j],
+                             m->nx[i], m->ny[i], 0, s, s + 3, s + 4, s + 5);
+            } else {
+                vo_face_flux(g, hthr, m->Hf[i], m->Huf[i], m->Hvf[i], m->z[K],
+                             0.0, 0.0, 0.0, 0.0, m->nx[i], m->ny[i], 1, s, s + 3, s + 4, s + 5);
+            }
+        }
+    }
+
+#pragma omp parallel for schedule(static)
+    for (int64_t K = 0; K < nc; K++) {
+        double aH = 0.0, aHu = 0.0, aHv = 0.0, am = 0.0;
+        for (int f = 0; f < 3; f++) {
+            int64_t i = 3 * K + f;
+            double P0, P1, P2, P, a;
+            if (owns(m, K, f)) {
+                const double *s = m->slot + 6 * i;
+                P0 = s[0]; P1 = s[1]; P2 = s[2]; P = s[3]; a = s[5];
+            } else {
+                const double *s = m->slot + 6 * (3 * (int64_t)m->nbr[i] + m->nbr_face[i]);
+                P0 = -s[0]; P1 = -s[1]; P2 = -s[2]; P = s[4]; a = s[5];
+            }
+            double l = m->len[i];
+            aH = aH + l * P0;
+            aHu = aHu + l * (P1 + P * m->nx[i]);
+            aHv = aHv + l * (P2 + P * m->ny[i]);
+            am = fmax(am, l * a);
+        }
+        RH[K] = -aH / m->area[K];
+        RHu[K] = -aHu / m->area[K];
+        RHv[K] = -aHv / m->area[K];
+        if (amax) amax[K] = am;
+    }
+}
+
+/*
+ * Time step of the stage-1 state (reading of the CFL condition of Sec. 2.3):
+ *   dt = CFL * min_K |K| / (3 max_f l_f a_f)
+ * over cells with a nonzero wave speed, then clamped to dt_max (if > 0) and to
+ * the time left before t_end (if > 0).  dt_fixed > 0 replaces the CFL rule.
+ * With no moving wave anywhere the step is dt_max (0 when unset).
+ */
+double vo_time_step(const vo_mesh *m, const vo_params *p, const double *amax, double t)
+{
+    double dt;
+    if (p->dt_fixed > 0.0) {
+        dt = p->dt_fixed;
+    } else {
+        double mn = INFINITY;
+        for (int64_t K = 0; K < m->nc; K++)
+            if (amax[K] > 0.0) mn = fmin(mn, m->area[K] / (3.0 * amax[K]));
+        dt = isinf(mn) ? (p->dt_max > 0.0 ? p->dt_max : 0.0) : p->cfl * mn;
+    }
+    if (p->dt_max > 0.0) dt = fmin(dt, p->dt_max);
+    if (p->t_end > 0.0 && t + dt > p->t_end) dt = p->t_end - t;
+    if (dt < 0.0) dt = 0.0;
+    return dt;
+}
+
+/* After each stage: a negative depth is counted and the cell emptied; at or
+   below H_threshold the momentum is zeroed. */
+static int64_t dry_fix(int64_t nc, double hthr, double *H, double *Hu, double *Hv)
+{
+    int64_t neg = 0;
+#pragma omp parallel for schedule(static) reduction(+ : neg)
+    for (int64_t K = 0; K < nc; K++) {
+        if (H[K] < 0.0) {
+            neg++;
+            H[K] = 0.0; Hu[K] = 0.0; Hv[K] = 0.0;
+        } else if (H[K] <= hthr) {
+            Hu[K] = 0.0; Hv[K] = 0.0;
+        }
+    }
+    return neg;
+}
+
+/*
+ * One SSP-RK(2,2) step (Sec. 2.3), in place on (H, Hu, Hv):
+ *   w1 = w + dt L(w);  w <- 1/2 w + 1/2 (w1 + dt L(w1)),
+ * the same dt in both stages, each stage followed by the dry fix.
+ * *t advances by dt; *dt_out and *neg_count (added to) report the step.
+ */
+void vo_step(vo_mesh *m, const vo_params *p, double *H, double *Hu, double *Hv,
+             double *t, double *dt_out, int64_t *neg_count)
+{
+    int64_t nc = m->nc;
+    double *R0 = m->R0, *R1 = m->R1, *W1 = m->W1;
+    double *H1 = W1, *Hu1 = W1 + nc, *Hv1 = W1 + 2 * nc;
+    vo_residual(m, p, H, Hu, Hv, R0, R0 + nc, R0 + 2 * nc, m->amax);
+    double dt = vo_time_step(m, p, m->amax, *t);
+#pragma omp parallel for schedule(static)
+    for (int64_t K = 0; K < nc; K++) {
+        H1[K] = H[K] + dt * R0[K];
+        Hu1[K] = Hu[K] + dt * R0[nc + K];
+        Hv1[K] = Hv[K] + dt * R0[2 * nc + K];
+    }
+    int64_t neg = dry_fix(nc, p->h_threshold, H1, Hu1, Hv1);
+    vo_residual(m, p, H1, Hu1, Hv1, R1, R1 + nc, R1 + 2 * nc, NULL);
+#pragma omp parallel for schedule(static)
+    for (int64_t K = 0; K < nc; K++) {
+        H[K] = 0.5 * H[K] + 0.5 * (H1[K] + dt * R1[K]);
+        Hu[K] = 0.5 * Hu[K] + 0.5 * (Hu1[K] + dt * R1[nc + K]);
+        Hv[K] = 0.5 * Hv[K] + 0.5 * (Hv1[K] + dt * R1[2 * nc + K]);
+    }
+    neg += dry_fix(nc, p->h_threshold, H, Hu, Hv);
+    *t += dt;
+    if (dt_out) *dt_out = dt;
+    if (neg_count) *neg_count += neg;
+}
+
+/* n steps; dts (may be NULL) receives each step's dt.  Gauges (may be NULL):
+   eta at the n_gauges cells gauge_cells[] after every step into
+   gauge_eta[step][g].  Returns the number of steps taken. */
+int64_t vo_run(vo_mesh *m, const vo_params *p, double *H, double *Hu, double *Hv,
+               double *t, int64_t n_steps, double *dts, int64_t *neg_count,
+               int32_t n_gauges, const int32_t *gauge_cells, double *gauge_eta)
+{
+    for (int64_t s = 0; s < n_steps; s++) {
+        double dt;
+        vo_step(m, p, H, Hu, Hv, t, &dt, neg_count);
+        if (dts) dts[s] = dt;
+        for (int32_t g = 0; g < n_gauges && gauge_eta; g++) {
+            int32_t c = gauge_cells[g];
+            gauge_eta[s * (int64_t)n_gauges + g] = H[c] + m->z[c];
+        }
+    }
+    return n_steps;
+}
+
+/* The cell containing each point (boundary included; among several, the lowest
+   cell id).  -1 when no cell contains it. */
+void vo_locate(const vo_mesh *m, const double *xy, int32_t n, const double *pts, int32_t *cells)
+{
+    for (int32_t k = 0; k < n; k++) {
+        double px = pts[2 * k], py = pts[2 * k + 1];
+        cells[k] = -1;
+        for (int64_t c = 0; c < m->nc; c++) {
+            int inside = 1;
+            for (int f = 0; f < 3 && inside; f++) {
+                int32_t a = m->vtx[3 * c + f], b = m->vtx[3 * c + (f + 1) % 3];
+                double o = (xy[2 * b] - xy[2 * a]) * (py - xy[2 * a + 1])
+                         - (xy[2 * b + 1] - xy[2 * a + 1]) * (px - xy[2 * a]);
+                if (o < 0.0) inside = 0;
+            }
+            if (inside) { cells[k] = (int32_t)c; break; }
+        }
+    }
+}
+
+/* Accessors: copy a per-cell or per-face array out (what: see the switch). */
+int vo_mesh_get(const vo_mesh *m, int what, void *out)
+{
+    size_t n1 = (size_t)m->nc, n3 = 3 * (size_t)m->nc;
+    switch (what) {
+    case 0: memcpy(out, m->vtx, n3 * sizeof(int32_t)); return 0;
+    case 1: memcpy(out, m->nbr, n3 * sizeof(int32_t)); return 0;
+    case 2: memcpy(out, m->nbr_face, n3 * sizeof(int32_t)); return 0;
+    case 3: memcpy(out, m->z, n1 * sizeof(double)); return 0;
+    case 4: memcpy(out, m->area, n1 * sizeof(double)); return 0;
+    case 5: memcpy(out, m->cx, n1 * sizeof(double)); return 0;
+    case 6: memcpy(out, m->cy, n1 * sizeof(double)); return 0;
+    case 7: memcpy(out, m->nx, n3 * sizeof(double)); return 0;
+    case 8: memcpy(out, m->ny, n3 * sizeof(double)); return 0;
+    case 9: memcpy(out, m->len, n3 * sizeof(double)); return 0;
+    case 10: memcpy(out, m->fx, n3 * sizeof(double)); return 0;
+    case 11: memcpy(out, m->fy, n3 * sizeof(double)); return 0;
+    case 12: memcpy(out, m->wx, n3 * sizeof(double)); return 0;
+    case 13: memcpy(out, m->wy, n3 * sizeof(double)); return 0;
+    case 14: memcpy(out, m->dx, n3 * sizeof(double)); return 0;
+    case 15: memcpy(out, m->dy, n3 * sizeof(double)); return 0;
+    default: return VO_EINVAL;
+    }
+}
+
+int64_t vo_mesh_n_flipped(const vo_mesh *m) { return m->n_flipped; }
+int64_t vo_mesh_nc(const vo_mesh *m) { return m->nc; }
