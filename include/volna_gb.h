@@ -1,0 +1,202 @@
+/*
+ * volna_gb.h -- C ABI of the GB300 (sm_103a) finite-volume shallow-water step.
+ *
+ * The library advances the 2D nonlinear shallow water equations
+ *     dH/dt + div(H u) = 0,
+ *     d(H u)/dt + div(H u (x) u + g H^2 / 2 I) = -g H grad(h)
+ * (Giles et al., "Performance analysis of Volna-OP2", Sec. 2.1) on an
+ * unstructured triangular mesh with the cell-centred finite-volume scheme of
+ * Sec. 2: MUSCL reconstruction with least-squares gradients and the
+ * Barth-Jespersen limiter (Sec. 2.4, Eq. recon), skipped below the dry
+ * threshold; the HLL flux with the wave speeds of Sec. 2.2 and a hydrostatic
+ * wet/dry interface; the wall ghost cell of Sec. 2.5; SSP-RK(2,2) in time
+ * with a CFL time step (Sec. 2.3).
+ *
+ * Conventions
+ *  - Every call returns an int status: VG_OK (0) or a negative VG_E* code.
+ *    vg_last_error() gives a message for the last failing call on a context.
+ *  - Host buffers belong to the caller; the library copies them in or out
+ *    before returning.  Device buffers made by the library belong to the
+ *    context and are freed by vg_destroy().  *_dev calls take caller-owned
+ *    device memory and never free it.
+ *  - Cell arrays passed in or out are in the caller's ORIGINAL cell order;
+ *    the library renumbers cells internally for locality.
+ *  - A context is used by one host thread at a time; contexts are independent
+ *    (no global state).
+ *  - Work is queued on the context's CUDA stream.  vg_step() and the get
+ *    calls synchronise that stream before returning.
+ */
+#ifndef VOLNA_GB_H
+#define VOLNA_GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VG_OK 0
+#define VG_EINVAL (-1)      /* bad argument, bad mesh, gauge outside the mesh   */
+#define VG_ENOMEM (-2)      /* host or device allocation failed                 */
+#define VG_ECUDA (-3)       /* a CUDA runtime call failed (message has details) */
+#define VG_ENONFINITE (-4)  /* a NaN/Inf appeared in the state or the time step */
+#define VG_ENEGDEPTH (-5)   /* negative depth met with params.strict_positivity */
+#define VG_ETIMEOUT (-6)    /* a bounded device-side wait gave up                */
+#define VG_ESTATE (-7)      /* call out of order (no mesh, no state, ...)        */
+
+#define VG_RENUMBER_NONE 0
+#define VG_RENUMBER_MORTON 1
+#define VG_RENUMBER_RCM 2
+
+typedef struct vg_ctx vg_ctx;
+
+/* Scheme and run parameters.  Defaults from vg_default_params(). */
+typedef struct vg_params {
+    double g;              /* gravity (the paper does not state it): 9.81          */
+    double cfl;            /* Courant number of the time-step rule: 0.9            */
+    double h_threshold;    /* dry threshold H_threshold of Sec. 2.4 (m): 1e-5      */
+    double dt_fixed;       /* > 0: fixed time step instead of the CFL rule: 0      */
+    double dt_max;         /* > 0: upper clamp of the time step: 0 (none)          */
+    double t_end;          /* > 0: the step reaching t_end is shortened to end on
+                              it and later steps do not move: 0 (none)             */
+    int32_t order;         /* 1 first order, 2 MUSCL (Sec. 2.4): 2                 */
+    int32_t gauge_every;   /* record gauges every this many steps: 1               */
+    int32_t strict_positivity; /* 1: vg_step fails with VG_ENEGDEPTH when a stage
+                              produced a negative depth (otherwise it is emptied
+                              and counted): 0                                      */
+    int32_t block_cells;   /* cells per thread block of the step kernels
+                              (64..1024, multiple of 32; 0 = library default)      */
+} vg_params;
+
+/* Run diagnostics (vg_get_diagnostics). */
+typedef struct vg_diag {
+    double t;              /* simulated time                                      */
+    double last_dt;        /* time step of the last step                          */
+    double mass;           /* sum_K |K| H_K                                       */
+    double min_H;          /* smallest depth                                      */
+    int64_t steps;         /* steps taken with dt > 0                              */
+    int64_t neg_count;     /* negative depths met (and emptied) so far             */
+    int64_t dry_count;     /* cells with H <= H_threshold                          */
+    int64_t launches;      /* kernels launched by the library so far               */
+    int64_t n_records;     /* gauge records available to vg_get_gauges             */
+} vg_diag;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int vg_version(void);
+
+/* Human-readable name of a status code; static storage. */
+const char *vg_strerror(int code);
+
+/* Fill *p with the defaults listed in vg_params. */
+int vg_default_params(vg_params *p);
+
+/*
+ * Create a context on CUDA device `device` computing in FP32 (precision 32) or
+ * FP64 (precision 64).  cuda_stream is a cudaStream_t to queue work on (for
+ * example a torch stream), or NULL for a stream owned by the context.
+ */
+int vg_create(vg_ctx **out, int precision, int device, void *cuda_stream);
+
+/* Free the context and all device memory it owns.  NULL is allowed. */
+void vg_destroy(vg_ctx *ctx);
+
+/* Message for the last failing call on ctx; valid until the next call on ctx. */
+const char *vg_last_error(vg_ctx *ctx);
+
+/*
+ * Upload an unstructured triangular mesh (Sec. 2.2: cell-centred finite volumes
+ * on triangles) with per-vertex bathymetry depth h (positive down, z = -h,
+ * Sec. 2.1).
+ *   xy[nv][2]   vertex coordinates (m), row major
+ *   tri[nc][3]  vertex ids per triangle; clockwise triangles are reoriented
+ *   depth_v[nv] depth at each vertex; each cell's bed is the mean of its three
+ *   renumber    VG_RENUMBER_NONE / _MORTON (Z-order of centroids) / _RCM
+ *               (reverse Cuthill-McKee on the face graph)
+ * Every edge must belong to one or two triangles; one-triangle edges are walls
+ * (Sec. 2.5).  Returns VG_EINVAL for an out-of-range or repeated vertex id, a
+ * zero-area triangle or a non-manifold edge.  Replaces any previous mesh and
+ * clears the state and gauges.
+ */
+int vg_mesh_upload(vg_ctx *ctx, int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
+                   const double *depth_v, int renumber);
+
+/* new_of_old[nc]: the internal index of each original cell. */
+int vg_get_permutation(vg_ctx *ctx, int32_t *new_of_old);
+
+/* Number of clockwise triangles that vg_mesh_upload reoriented. */
+int vg_get_flipped(vg_ctx *ctx, int64_t *n_flipped);
+
+int vg_set_params(vg_ctx *ctx, const vg_params *p);
+int vg_get_params(vg_ctx *ctx, vg_params *p);
+
+/*
+ * Set the conserved state w = (H, Hu, Hv) (Sec. 2.2) at time t from host FP64
+ * arrays of nc values in the original cell order (converted to the context's
+ * precision).  Depths must be finite and >= 0 (VG_EINVAL otherwise).  Clears
+ * the gauge record and, if gauges are set, records eta = H + z at t.
+ */
+int vg_set_state(vg_ctx *ctx, const double *H, const double *Hu, const double *Hv, double t);
+
+/* Same from device arrays of the context's precision (float or double), in the
+   original cell order, read on the context stream. */
+int vg_set_state_dev(vg_ctx *ctx, const void *H, const void *Hu, const void *Hv, double t);
+
+/* Copy the state out to host FP64 arrays in the original order; *t may be NULL. */
+int vg_get_state(vg_ctx *ctx, double *H, double *Hu, double *Hv, double *t);
+
+/* Copy the state out to device arrays of the context's precision. */
+int vg_get_state_dev(vg_ctx *ctx, void *H, void *Hu, void *Hv);
+
+/*
+ * Virtual gauges (Sec. 3: free-surface elevation recorded at fixed points):
+ * xy[n][2] points, each resolved to the cell containing it (on an edge or a
+ * vertex: the lowest original cell id).  A point outside the mesh returns
+ * VG_EINVAL.  The gauge value is eta = H + z of that cell.  Clears the record
+ * and records the current state if one is set.  n = 0 removes the gauges.
+ */
+int vg_set_gauges(vg_ctx *ctx, int32_t n, const double *xy);
+
+/* Cells (original ids) that vg_set_gauges resolved, cells[n]. */
+int vg_get_gauge_cells(vg_ctx *ctx, int32_t *cells);
+
+/*
+ * Advance n_steps SSP-RK(2,2) steps (Sec. 2.3) on the device; the time step of
+ * each comes from the CFL rule on the stage-1 wave speeds,
+ *   dt = cfl * min_K |K| / (3 max_f l_f a_f),
+ * unless params.dt_fixed > 0, clamped by dt_max and t_end.  The whole loop
+ * stays on the device (CUDA-graph replays); the call synchronises once at the
+ * end and returns VG_ENONFINITE / VG_ENEGDEPTH if a step went wrong.
+ */
+int vg_step(vg_ctx *ctx, int64_t n_steps);
+
+/* Step until the simulated time reaches t (the last step is shortened). */
+int vg_advance_to(vg_ctx *ctx, double t);
+
+/*
+ * Gauge records so far: t[k] and eta[k][n_gauges] for k < min(*n_rec, cap).
+ * *n_rec receives the number of records held.  Either array may be NULL.
+ */
+int vg_get_gauges(vg_ctx *ctx, double *t, double *eta, int64_t cap, int64_t *n_rec);
+
+/* Diagnostics of the current state; synchronises the context stream. */
+int vg_get_diagnostics(vg_ctx *ctx, vg_diag *d);
+
+/*
+ * Per-kernel timing.  With enable != 0, later vg_step calls launch kernel by
+ * kernel (no graph) with CUDA events around each launch on the context
+ * stream, and accumulate device time per kernel.  vg_get_profile returns, for
+ * up to n kernels, their names (static strings), launch counts and total
+ * milliseconds; *n_out receives the number of kernels timed.
+ */
+int vg_profile(vg_ctx *ctx, int enable);
+int vg_get_profile(vg_ctx *ctx, int32_t n, const char **names, int64_t *launches, double *ms,
+                   int32_t *n_out);
+
+/* Bytes of device memory the context holds. */
+int vg_device_bytes(vg_ctx *ctx, int64_t *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VOLNA_GB_H */

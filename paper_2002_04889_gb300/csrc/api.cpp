@@ -1,0 +1,801 @@
+// C ABI of the volna_gb library (declared in include/volna_gb.h): contexts,
+// device memory, state transfer with the cell permutation, gauges, and the
+// step loop (two persistent stage kernels and an epilogue per step, replayed
+// from a CUDA graph two steps at a time).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/volna_gb.h"
+#include "vg_internal.h"
+
+using namespace vg;
+
+namespace {
+
+constexpr int kRingCap = 2048;       // gauge records held on the device between drains
+constexpr int kDiagBlocks = 1024;
+constexpr int kKernels = 3;
+const char *kKernelNames[kKernels] = {"stage1", "stage2", "post_step"};
+
+}  // namespace
+
+struct vg_ctx {
+    int precision = 64;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    vg_params prm{};
+    bool has_mesh = false, has_state = false;
+    HostMesh hm;
+
+    // device memory
+    void *geo = nullptr, *z = nullptr, *w[2] = {nullptr, nullptr}, *R0 = nullptr;
+    int32_t *nbr = nullptr, *halo_ptr = nullptr, *halo_ids = nullptr, *old_of_new = nullptr;
+    uint16_t *nbrl = nullptr;
+    DevScalars *sc = nullptr;
+    int32_t *gauge_cells = nullptr;
+    double *ring_t = nullptr, *ring_eta = nullptr;
+    double *diag_part = nullptr, *diag_out = nullptr;
+    void *staging = nullptr;          // [3][nc] doubles for host transfers
+    int64_t dev_bytes = 0;
+    int cur = 0;
+
+    int32_t n_gauges = 0;
+    std::vector<int32_t> gauge_orig;
+    std::vector<double> rec_t, rec_eta;
+
+    LaunchCfg cfg1{}, cfg2{};
+    cudaGraphExec_t graph2 = nullptr;
+    bool graph_dirty = true;
+    int64_t launches = 0;
+
+    bool profile = false;
+    double prof_ms[kKernels] = {0, 0, 0};
+    int64_t prof_n[kKernels] = {0, 0, 0};
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_kernel;
+    size_t ev_used = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) { if (cudaGetDevice(&prev) != cudaSuccess) prev = -1; cudaSetDevice(dev); }
+    ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+int fail(vg_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(vg_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, VG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define VG_CUDA(ctx, call)                                   \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+int dmalloc(vg_ctx *c, void **p, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(c, VG_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+    }
+    c->dev_bytes += (int64_t)bytes;
+    return VG_OK;
+}
+
+template <typename T>
+void dfree(T *&p)
+{
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+void free_mesh(vg_ctx *c)
+{
+    if (c->graph2) { cudaGraphExecDestroy(c->graph2); c->graph2 = nullptr; }
+    dfree(c->geo); dfree(c->z); dfree(c->w[0]); dfree(c->w[1]); dfree(c->R0);
+    dfree(c->nbr); dfree(c->halo_ptr); dfree(c->halo_ids); dfree(c->old_of_new); dfree(c->nbrl);
+    dfree(c->gauge_cells); dfree(c->ring_t); dfree(c->ring_eta); dfree(c->staging);
+    c->dev_bytes = 0;
+    c->has_mesh = c->has_state = false;
+    c->n_gauges = 0;
+    c->gauge_orig.clear();
+    c->rec_t.clear();
+    c->rec_eta.clear();
+    c->graph_dirty = true;
+}
+
+size_t real_size(const vg_ctx *c) { return c->precision == 64 ? 8 : 4; }
+
+DevPtrs dev_ptrs(const vg_ctx *c)
+{
+    DevPtrs d{};
+    d.nc = c->hm.nc;
+    d.block = c->hm.block;
+    d.nblocks = c->hm.nblocks;
+    d.max_halo = c->hm.max_halo;
+    d.n_gauges = c->n_gauges;
+    d.ring_cap = kRingCap;
+    d.geo = c->geo;
+    d.z = c->z;
+    d.nbr = c->nbr;
+    d.nbrl = c->nbrl;
+    d.halo_ptr = c->halo_ptr;
+    d.halo_ids = c->halo_ids;
+    d.R0 = c->R0;
+    d.sc = c->sc;
+    d.gauge_cells = c->gauge_cells;
+    d.ring_t = c->ring_t;
+    d.ring_eta = c->ring_eta;
+    return d;
+}
+
+StepParams step_params(const vg_ctx *c)
+{
+    StepParams p{};
+    p.g = c->prm.g;
+    p.cfl = c->prm.cfl;
+    p.hthr = c->prm.h_threshold;
+    p.dt_fixed = c->prm.dt_fixed;
+    p.dt_max = c->prm.dt_max;
+    p.t_end = c->prm.t_end;
+    p.order = c->prm.order;
+    p.gauge_every = c->prm.gauge_every;
+    return p;
+}
+
+// Converts host doubles to the context precision into `dst` (device), via staging.
+int upload_real(vg_ctx *c, void *dst, const double *src, size_t n)
+{
+    if (c->precision == 64) {
+        VG_CUDA(c, cudaMemcpy(dst, src, n * 8, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> tmp(n);
+        for (size_t i = 0; i < n; i++) tmp[i] = (float)src[i];
+        VG_CUDA(c, cudaMemcpy(dst, tmp.data(), n * 4, cudaMemcpyHostToDevice));
+    }
+    return VG_OK;
+}
+
+int upload_mesh_arrays(vg_ctx *c)
+{
+    const HostMesh &m = c->hm;
+    size_t rs = real_size(c);
+    int rc;
+    if ((rc = dmalloc(c, &c->geo, rs * GEO_ROWS * m.nc))) return rc;
+    if ((rc = dmalloc(c, &c->z, rs * m.nc))) return rc;
+    if ((rc = dmalloc(c, &c->w[0], rs * 3 * m.nc))) return rc;
+    if ((rc = dmalloc(c, &c->w[1], rs * 3 * m.nc))) return rc;
+    if ((rc = dmalloc(c, &c->R0, rs * 3 * m.nc))) return rc;
+    if ((rc = dmalloc(c, (void **)&c->nbr, 4 * 3 * m.nc))) return rc;
+    if ((rc = dmalloc(c, (void **)&c->nbrl, 2 * 3 * m.nc))) return rc;
+    if ((rc = dmalloc(c, (void **)&c->halo_ptr, 4 * (m.nblocks + 1)))) return rc;
+    if ((rc = dmalloc(c, (void **)&c->halo_ids, 4 * std::max<size_t>(1, m.halo_ids.size())))) return rc;
+    if ((rc = dmalloc(c, (void **)&c->old_of_new, 4 * m.nc))) return rc;
+    if ((rc = dmalloc(c, (void **)&c->ring_t, 8 * kRingCap))) return rc;
+    if ((rc = upload_real(c, c->geo, m.geo.data(), m.geo.size()))) return rc;
+    if ((rc = upload_real(c, c->z, m.z.data(), m.z.size()))) return rc;
+    VG_CUDA(c, cudaMemcpy(c->nbr, m.nbr.data(), 4 * 3 * m.nc, cudaMemcpyHostToDevice));
+    VG_CUDA(c, cudaMemcpy(c->nbrl, m.nbrl.data(), 2 * 3 * m.nc, cudaMemcpyHostToDevice));
+    VG_CUDA(c, cudaMemcpy(c->halo_ptr, m.halo_ptr.data(), 4 * (m.nblocks + 1), cudaMemcpyHostToDevice));
+    if (!m.halo_ids.empty())
+        VG_CUDA(c, cudaMemcpy(c->halo_ids, m.halo_ids.data(), 4 * m.halo_ids.size(), cudaMemcpyHostToDevice));
+    VG_CUDA(c, cudaMemcpy(c->old_of_new, m.old_of_new.data(), 4 * m.nc, cudaMemcpyHostToDevice));
+    return VG_OK;
+}
+
+int configure_launch(vg_ctx *c)
+{
+    DevPtrs d = dev_ptrs(c);
+    int e = c->precision == 64 ? stage_config_f64(d, 1, c->cfg1) : stage_config_f32(d, 1, c->cfg1);
+    if (e) return cuda_fail(c, (cudaError_t)e, "stage 1 launch configuration");
+    e = c->precision == 64 ? stage_config_f64(d, 2, c->cfg2) : stage_config_f32(d, 2, c->cfg2);
+    if (e) return cuda_fail(c, (cudaError_t)e, "stage 2 launch configuration");
+    return VG_OK;
+}
+
+void reset_scalars_host(vg_ctx *c, DevScalars &s, double t)
+{
+    std::memset(&s, 0, sizeof(s));
+    s.t = t;
+    if (c->precision == 64) {
+        double inf = INFINITY;
+        std::memcpy(&s.dtmin_bits, &inf, 8);
+    } else {
+        float inf = INFINITY;
+        uint32_t b;
+        std::memcpy(&b, &inf, 4);
+        s.dtmin_bits = b;
+    }
+}
+
+int ev_begin(vg_ctx *c, int kernel)
+{
+    if (!c->profile) return VG_OK;
+    if (c->ev_used + 2 > c->ev.size()) {
+        for (int k = 0; k < 64; k++) {
+            cudaEvent_t e;
+            VG_CUDA(c, cudaEventCreate(&e));
+            c->ev.push_back(e);
+        }
+        c->ev_kernel.resize(c->ev.size() / 2 + 1);
+    }
+    c->ev_kernel[c->ev_used / 2] = kernel;
+    VG_CUDA(c, cudaEventRecord(c->ev[c->ev_used], c->stream));
+    return VG_OK;
+}
+
+int ev_end(vg_ctx *c)
+{
+    if (!c->profile) return VG_OK;
+    VG_CUDA(c, cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
+    c->ev_used += 2;
+    return VG_OK;
+}
+
+int ev_collect(vg_ctx *c)
+{
+    if (!c->profile) return VG_OK;
+    for (size_t i = 0; i < c->ev_used; i += 2) {
+        float ms = 0;
+        VG_CUDA(c, cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
+        int k = c->ev_kernel[i / 2];
+        c->prof_ms[k] += ms;
+        c->prof_n[k] += 1;
+    }
+    c->ev_used = 0;
+    return VG_OK;
+}
+
+// Queue one step reading w[src] and writing w[1 - src].
+int enqueue_step(vg_ctx *c, int src)
+{
+    DevPtrs d = dev_ptrs(c);
+    StepParams p = step_params(c);
+    void *s = (void *)c->stream;
+    const void *win = c->w[src];
+    void *wout = c->w[1 - src];
+    int e, rc;
+    if ((rc = ev_begin(c, 0))) return rc;
+    e = c->precision == 64 ? launch_stage1_f64(d, p, win, c->cfg1, s) : launch_stage1_f32(d, p, win, c->cfg1, s);
+    if (e) return cuda_fail(c, (cudaError_t)e, "stage 1 launch");
+    if ((rc = ev_end(c))) return rc;
+    if ((rc = ev_begin(c, 1))) return rc;
+    e = c->precision == 64 ? launch_stage2_f64(d, p, win, wout, c->cfg2, s) : launch_stage2_f32(d, p, win, wout, c->cfg2, s);
+    if (e) return cuda_fail(c, (cudaError_t)e, "stage 2 launch");
+    if ((rc = ev_end(c))) return rc;
+    if ((rc = ev_begin(c, 2))) return rc;
+    e = launch_post_step(d, p, wout, c->precision, s);
+    if (e) return cuda_fail(c, (cudaError_t)e, "post-step launch");
+    if ((rc = ev_end(c))) return rc;
+    return VG_OK;
+}
+
+int build_graph(vg_ctx *c)
+{
+    if (c->graph2) { cudaGraphExecDestroy(c->graph2); c->graph2 = nullptr; }
+    bool prof = c->profile;
+    c->profile = false;
+    cudaGraph_t g = nullptr;
+    VG_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_step(c, 0);
+    if (!rc) rc = enqueue_step(c, 1);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    c->profile = prof;
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->graph2, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+    c->graph_dirty = false;
+    return VG_OK;
+}
+
+int read_scalars(vg_ctx *c, DevScalars &s)
+{
+    VG_CUDA(c, cudaMemcpyAsync(&s, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    VG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return VG_OK;
+}
+
+// Move the device gauge records to the host and empty the device ring.
+int drain_gauges(vg_ctx *c, DevScalars &s)
+{
+    if (c->n_gauges > 0 && s.n_rec > 0) {
+        size_t n = (size_t)s.n_rec, G = (size_t)c->n_gauges;
+        size_t t0 = c->rec_t.size();
+        c->rec_t.resize(t0 + n);
+        c->rec_eta.resize((t0 + n) * G);
+        VG_CUDA(c, cudaMemcpyAsync(c->rec_t.data() + t0, c->ring_t, n * 8, cudaMemcpyDeviceToHost, c->stream));
+        VG_CUDA(c, cudaMemcpyAsync(c->rec_eta.data() + t0 * G, c->ring_eta, n * G * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+    static const long long zero = 0;
+    VG_CUDA(c, cudaMemcpyAsync(&c->sc->n_rec, &zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream));
+    VG_CUDA(c, cudaStreamSynchronize(c->stream));
+    s.n_rec = 0;
+    return VG_OK;
+}
+
+int check_flags(vg_ctx *c, const DevScalars &s, int64_t neg_before)
+{
+    if (s.flags & FLAG_NONFINITE_STATE) return fail(c, VG_ENONFINITE, "a non-finite value appeared in the state");
+    if (s.flags & FLAG_NONFINITE_DT) return fail(c, VG_ENONFINITE, "the time step is not finite");
+    if (s.flags & FLAG_RING_FULL) return fail(c, VG_ESTATE, "gauge ring overflow");
+    if (c->prm.strict_positivity && s.neg_count > neg_before)
+        return fail(c, VG_ENEGDEPTH, "a stage produced a negative depth (" + std::to_string(s.neg_count - neg_before) + " cells)");
+    return VG_OK;
+}
+
+int validate_params(const vg_params *p, std::string &why)
+{
+    if (!(p->g > 0) || !std::isfinite(p->g)) { why = "g must be > 0"; return VG_EINVAL; }
+    if (!(p->cfl > 0) || !std::isfinite(p->cfl)) { why = "cfl must be > 0"; return VG_EINVAL; }
+    if (!(p->h_threshold >= 0) || !std::isfinite(p->h_threshold)) { why = "h_threshold must be >= 0"; return VG_EINVAL; }
+    if (!(p->dt_fixed >= 0) || !(p->dt_max >= 0) || !(p->t_end >= 0)) { why = "dt_fixed, dt_max, t_end must be >= 0"; return VG_EINVAL; }
+    if (p->order != 1 && p->order != 2) { why = "order must be 1 or 2"; return VG_EINVAL; }
+    if (p->gauge_every < 1) { why = "gauge_every must be >= 1"; return VG_EINVAL; }
+    if (p->block_cells != 0 && (p->block_cells < 32 || p->block_cells > 256 || p->block_cells % 32)) {
+        why = "block_cells must be 0 or a multiple of 32 in [32, 256]";
+        return VG_EINVAL;
+    }
+    return VG_OK;
+}
+
+int record_now(vg_ctx *c)
+{
+    if (c->n_gauges <= 0 || !c->has_state) return VG_OK;
+    int e = launch_record_gauges(dev_ptrs(c), c->w[c->cur], c->precision, (void *)c->stream);
+    if (e) return cuda_fail(c, (cudaError_t)e, "gauge record launch");
+    c->launches++;
+    return VG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vg_version(void) { return 10000; }
+
+const char *vg_strerror(int code)
+{
+    switch (code) {
+    case VG_OK: return "ok";
+    case VG_EINVAL: return "invalid argument";
+    case VG_ENOMEM: return "out of memory";
+    case VG_ECUDA: return "CUDA error";
+    case VG_ENONFINITE: return "non-finite state or time step";
+    case VG_ENEGDEPTH: return "negative depth";
+    case VG_ETIMEOUT: return "device wait timed out";
+    case VG_ESTATE: return "call out of order";
+    default: return "unknown status";
+    }
+}
+
+int vg_default_params(vg_params *p)
+{
+    if (!p) return VG_EINVAL;
+    p->g = 9.81;
+    p->cfl = 0.9;
+    p->h_threshold = 1e-5;
+    p->dt_fixed = 0.0;
+    p->dt_max = 0.0;
+    p->t_end = 0.0;
+    p->order = 2;
+    p->gauge_every = 1;
+    p->strict_positivity = 0;
+    p->block_cells = 0;
+    return VG_OK;
+}
+
+int vg_create(vg_ctx **out, int precision, int device, void *cuda_stream)
+{
+    if (!out) return VG_EINVAL;
+    *out = nullptr;
+    if (precision != 32 && precision != 64) return VG_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return VG_ECUDA;
+    }
+    vg_ctx *c = new (std::nothrow) vg_ctx();
+    if (!c) return VG_ENOMEM;
+    c->precision = precision;
+    c->device = device;
+    vg_default_params(&c->prm);
+    DeviceGuard guard(device);
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return VG_ECUDA; }
+        c->own_stream = true;
+    }
+    if (cudaMalloc((void **)&c->sc, sizeof(DevScalars)) != cudaSuccess ||
+        cudaMalloc((void **)&c->diag_part, 8 * 3 * kDiagBlocks) != cudaSuccess ||
+        cudaMalloc((void **)&c->diag_out, 8 * 4) != cudaSuccess) {
+        vg_destroy(c);
+        return VG_ENOMEM;
+    }
+    DevScalars s;
+    reset_scalars_host(c, s, 0.0);
+    if (cudaMemcpy(c->sc, &s, sizeof(s), cudaMemcpyHostToDevice) != cudaSuccess) { vg_destroy(c); return VG_ECUDA; }
+    *out = c;
+    return VG_OK;
+}
+
+void vg_destroy(vg_ctx *c)
+{
+    if (!c) return;
+    DeviceGuard guard(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_mesh(c);
+    dfree(c->sc);
+    dfree(c->diag_part);
+    dfree(c->diag_out);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char *vg_last_error(vg_ctx *c) { return c ? c->err.c_str() : "NULL context"; }
+
+int vg_mesh_upload(vg_ctx *c, int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
+                   const double *depth_v, int renumber)
+{
+    if (!c) return VG_EINVAL;
+    DeviceGuard guard(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_mesh(c);
+    int block = c->prm.block_cells ? c->prm.block_cells : 256;
+    int rc = prepare_mesh(nv, xy, nc, tri, depth_v, renumber, block, c->hm, c->err);
+    if (rc) return rc;
+    if ((rc = upload_mesh_arrays(c))) { free_mesh(c); return rc; }
+    if ((rc = configure_launch(c))) { free_mesh(c); return rc; }
+    c->has_mesh = true;
+    c->has_state = false;
+    c->cur = 0;
+    return VG_OK;
+}
+
+int vg_get_permutation(vg_ctx *c, int32_t *new_of_old)
+{
+    if (!c || !new_of_old) return VG_EINVAL;
+    if (!c->has_mesh) return fail(c, VG_ESTATE, "no mesh");
+    std::memcpy(new_of_old, c->hm.new_of_old.data(), 4 * c->hm.nc);
+    return VG_OK;
+}
+
+int vg_get_flipped(vg_ctx *c, int64_t *n)
+{
+    if (!c || !n) return VG_EINVAL;
+    if (!c->has_mesh) return fail(c, VG_ESTATE, "no mesh");
+    *n = c->hm.n_flipped;
+    return VG_OK;
+}
+
+int vg_set_params(vg_ctx *c, const vg_params *p)
+{
+    if (!c || !p) return VG_EINVAL;
+    std::string why;
+    if (validate_params(p, why)) return fail(c, VG_EINVAL, why);
+    DeviceGuard guard(c->device);
+    int old_block = c->prm.block_cells ? c->prm.block_cells : 256;
+    int new_block = p->block_cells ? p->block_cells : 256;
+    c->prm = *p;
+    c->graph_dirty = true;
+    if (c->has_mesh && new_block != old_block) {
+        cudaStreamSynchronize(c->stream);
+        int rc = partition_blocks(c->hm, new_block, c->err);
+        if (rc) return rc;
+        dfree(c->halo_ptr); dfree(c->halo_ids); dfree(c->nbrl);
+        if ((rc = dmalloc(c, (void **)&c->nbrl, 2 * 3 * c->hm.nc))) return rc;
+        if ((rc = dmalloc(c, (void **)&c->halo_ptr, 4 * (c->hm.nblocks + 1)))) return rc;
+        if ((rc = dmalloc(c, (void **)&c->halo_ids, 4 * std::max<size_t>(1, c->hm.halo_ids.size())))) return rc;
+        VG_CUDA(c, cudaMemcpy(c->nbrl, c->hm.nbrl.data(), 2 * 3 * c->hm.nc, cudaMemcpyHostToDevice));
+        VG_CUDA(c, cudaMemcpy(c->halo_ptr, c->hm.halo_ptr.data(), 4 * (c->hm.nblocks + 1), cudaMemcpyHostToDevice));
+        if (!c->hm.halo_ids.empty())
+            VG_CUDA(c, cudaMemcpy(c->halo_ids, c->hm.halo_ids.data(), 4 * c->hm.halo_ids.size(), cudaMemcpyHostToDevice));
+        if ((rc = configure_launch(c))) return rc;
+    }
+    return VG_OK;
+}
+
+int vg_get_params(vg_ctx *c, vg_params *p)
+{
+    if (!c || !p) return VG_EINVAL;
+    *p = c->prm;
+    return VG_OK;
+}
+
+static int set_state_impl(vg_ctx *c, const void *H, const void *Hu, const void *Hv, int is_double, double t)
+{
+    DevScalars s;
+    reset_scalars_host(c, s, t);
+    VG_CUDA(c, cudaMemcpyAsync(c->sc, &s, sizeof(s), cudaMemcpyHostToDevice, c->stream));
+    c->cur = 0;
+    int e = launch_import_state(dev_ptrs(c), c->old_of_new, H, Hu, Hv, is_double, c->w[0], c->precision,
+                                (void *)c->stream);
+    if (e) return cuda_fail(c, (cudaError_t)e, "state import launch");
+    c->launches++;
+    DevScalars r;
+    int rc = read_scalars(c, r);
+    if (rc) return rc;
+    if (r.flags & FLAG_BAD_INPUT) {
+        c->has_state = false;
+        return fail(c, VG_EINVAL, "state has a negative or non-finite depth, or non-finite momentum");
+    }
+    c->has_state = true;
+    c->rec_t.clear();
+    c->rec_eta.clear();
+    if ((rc = record_now(c))) return rc;
+    return VG_OK;
+}
+
+int vg_set_state(vg_ctx *c, const double *H, const double *Hu, const double *Hv, double t)
+{
+    if (!c || !H || !Hu || !Hv) return VG_EINVAL;
+    if (!c->has_mesh) return fail(c, VG_ESTATE, "no mesh");
+    if (!std::isfinite(t)) return fail(c, VG_EINVAL, "t must be finite");
+    DeviceGuard guard(c->device);
+    int64_t nc = c->hm.nc;
+    int rc;
+    if (!c->staging && (rc = dmalloc(c, &c->staging, 8 * 3 * nc))) return rc;
+    double *st = static_cast<double *>(c->staging);
+    VG_CUDA(c, cudaMemcpyAsync(st, H, 8 * nc, cudaMemcpyHostToDevice, c->stream));
+    VG_CUDA(c, cudaMemcpyAsync(st + nc, Hu, 8 * nc, cudaMemcpyHostToDevice, c->stream));
+    VG_CUDA(c, cudaMemcpyAsync(st + 2 * nc, Hv, 8 * nc, cudaMemcpyHostToDevice, c->stream));
+    return set_state_impl(c, st, st + nc, st + 2 * nc, 1, t);
+}
+
+int vg_set_state_dev(vg_ctx *c, const void *H, const void *Hu, const void *Hv, double t)
+{
+    if (!c || !H || !Hu || !Hv) return VG_EINVAL;
+    if (!c->has_mesh) return fail(c, VG_ESTATE, "no mesh");
+    if (!std::isfinite(t)) return fail(c, VG_EINVAL, "t must be finite");
+    DeviceGuard guard(c->device);
+    return set_state_impl(c, H, Hu, Hv, c->precision == 64, t);
+}
+
+int vg_get_state(vg_ctx *c, double *H, double *Hu, double *Hv, double *t)
+{
+    if (!c || !H || !Hu || !Hv) return VG_EINVAL;
+    if (!c->has_state) return fail(c, VG_ESTATE, "no state");
+    DeviceGuard guard(c->device);
+    int64_t nc = c->hm.nc;
+    int rc;
+    if (!c->staging && (rc = dmalloc(c, &c->staging, 8 * 3 * nc))) return rc;
+    double *st = static_cast<double *>(c->staging);
+    int e = launch_export_state(dev_ptrs(c), c->old_of_new, c->w[c->cur], c->precision, st, st + nc, st + 2 * nc, 1,
+                                (void *)c->stream);
+    if (e) return cuda_fail(c, (cudaError_t)e, "state export launch");
+    c->launches++;
+    VG_CUDA(c, cudaMemcpyAsync(H, st, 8 * nc, cudaMemcpyDeviceToHost, c->stream));
+    VG_CUDA(c, cudaMemcpyAsync(Hu, st + nc, 8 * nc, cudaMemcpyDeviceToHost, c->stream));
+    VG_CUDA(c, cudaMemcpyAsync(Hv, st + 2 * nc, 8 * nc, cudaMemcpyDeviceToHost, c->stream));
+    DevScalars s;
+    if ((rc = read_scalars(c, s))) return rc;
+    if (t) *t = s.t;
+    return VG_OK;
+}
+
+int vg_get_state_dev(vg_ctx *c, void *H, void *Hu, void *Hv)
+{
+    if (!c || !H || !Hu || !Hv) return VG_EINVAL;
+    if (!c->has_state) return fail(c, VG_ESTATE, "no state");
+    DeviceGuard guard(c->device);
+    int e = launch_export_state(dev_ptrs(c), c->old_of_new, c->w[c->cur], c->precision, H, Hu, Hv,
+                                c->precision == 64, (void *)c->stream);
+    if (e) return cuda_fail(c, (cudaError_t)e, "state export launch");
+    c->launches++;
+    VG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return VG_OK;
+}
+
+int vg_set_gauges(vg_ctx *c, int32_t n, const double *xy)
+{
+    if (!c || n < 0 || (n > 0 && !xy)) return VG_EINVAL;
+    if (!c->has_mesh) return fail(c, VG_ESTATE, "no mesh");
+    DeviceGuard guard(c->device);
+    std::vector<int32_t> cells(n);
+    locate_points(c->hm, n, xy, cells.data());
+    for (int32_t k = 0; k < n; k++)
+        if (cells[k] < 0) return fail(c, VG_EINVAL, "gauge " + std::to_string(k) + " lies outside the mesh");
+    cudaStreamSynchronize(c->stream);
+    dfree(c->gauge_cells);
+    dfree(c->ring_eta);
+    c->n_gauges = 0;
+    c->gauge_orig = cells;
+    c->rec_t.clear();
+    c->rec_eta.clear();
+    c->graph_dirty = true;
+    if (n == 0) return VG_OK;
+    std::vector<int32_t> internal(n);
+    for (int32_t k = 0; k < n; k++) internal[k] = c->hm.new_of_old[cells[k]];
+    int rc;
+    if ((rc = dmalloc(c, (void **)&c->gauge_cells, 4 * n))) return rc;
+    if ((rc = dmalloc(c, (void **)&c->ring_eta, 8 * (size_t)n * kRingCap))) return rc;
+    VG_CUDA(c, cudaMemcpy(c->gauge_cells, internal.data(), 4 * n, cudaMemcpyHostToDevice));
+    c->n_gauges = n;
+    static const long long zero = 0;
+    VG_CUDA(c, cudaMemcpyAsync(&c->sc->n_rec, &zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream));
+    return record_now(c);
+}
+
+int vg_get_gauge_cells(vg_ctx *c, int32_t *cells)
+{
+    if (!c || (!cells && !c->gauge_orig.empty())) return VG_EINVAL;
+    std::copy(c->gauge_orig.begin(), c->gauge_orig.end(), cells);
+    return VG_OK;
+}
+
+int vg_step(vg_ctx *c, int64_t n_steps)
+{
+    if (!c || n_steps < 0) return VG_EINVAL;
+    if (!c->has_mesh || !c->has_state) return fail(c, VG_ESTATE, "mesh and state must be set before stepping");
+    DeviceGuard guard(c->device);
+    DevScalars s;
+    int rc = read_scalars(c, s);
+    if (rc) return rc;
+    if ((rc = drain_gauges(c, s))) return rc;
+    int64_t neg_before = s.neg_count;
+    int64_t chunk_max = c->n_gauges > 0 ? (int64_t)(kRingCap - 1) * c->prm.gauge_every : n_steps;
+    if (chunk_max < 1) chunk_max = 1;
+    while (n_steps > 0) {
+        int64_t chunk = std::min(n_steps, chunk_max);
+        n_steps -= chunk;
+        int64_t left = chunk;
+        if (c->profile) {
+            while (left > 0) {
+                if ((rc = enqueue_step(c, c->cur))) return rc;
+                c->cur = 1 - c->cur;
+                c->launches += kKernels;
+                left--;
+            }
+        } else {
+            if (c->graph_dirty && (rc = build_graph(c))) return rc;
+            if (c->cur == 1 && left > 0) {
+                if ((rc = enqueue_step(c, 1))) return rc;
+                c->cur = 0;
+                c->launches += kKernels;
+                left--;
+            }
+            while (left >= 2) {
+                VG_CUDA(c, cudaGraphLaunch(c->graph2, c->stream));
+                c->launches += 2 * kKernels;
+                left -= 2;
+            }
+            if (left == 1) {
+                if ((rc = enqueue_step(c, 0))) return rc;
+                c->cur = 1;
+                c->launches += kKernels;
+            }
+        }
+        if ((rc = read_scalars(c, s))) return rc;
+        if ((rc = ev_collect(c))) return rc;
+        if ((rc = drain_gauges(c, s))) return rc;
+        if ((rc = check_flags(c, s, neg_before))) return rc;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "vg_step");
+    return VG_OK;
+}
+
+int vg_advance_to(vg_ctx *c, double t_target)
+{
+    if (!c || !std::isfinite(t_target)) return VG_EINVAL;
+    if (!c->has_mesh || !c->has_state) return fail(c, VG_ESTATE, "mesh and state must be set before stepping");
+    vg_params saved = c->prm;
+    vg_params p = saved;
+    if (!(p.t_end > 0) || p.t_end > t_target) p.t_end = t_target;
+    c->prm = p;
+    c->graph_dirty = true;
+    int rc = VG_OK;
+    for (int iter = 0; iter < 1000000; iter++) {
+        DevScalars s;
+        if ((rc = read_scalars(c, s))) break;
+        if (s.t >= p.t_end) break;
+        double t_before = s.t;
+        if ((rc = vg_step(c, 64))) break;
+        if ((rc = read_scalars(c, s))) break;
+        if (s.t <= t_before) { rc = fail(c, VG_ESTATE, "time does not advance (zero time step)"); break; }
+    }
+    c->prm = saved;
+    c->graph_dirty = true;
+    return rc;
+}
+
+int vg_get_gauges(vg_ctx *c, double *t, double *eta, int64_t cap, int64_t *n_rec)
+{
+    if (!c || cap < 0) return VG_EINVAL;
+    DeviceGuard guard(c->device);
+    if (c->has_mesh) {
+        DevScalars s;
+        int rc = read_scalars(c, s);
+        if (rc) return rc;
+        if ((rc = drain_gauges(c, s))) return rc;
+    }
+    int64_t n = (int64_t)c->rec_t.size();
+    if (n_rec) *n_rec = n;
+    int64_t k = std::min(n, cap);
+    if (t) std::memcpy(t, c->rec_t.data(), 8 * k);
+    if (eta) std::memcpy(eta, c->rec_eta.data(), 8 * k * c->n_gauges);
+    return VG_OK;
+}
+
+int vg_get_diagnostics(vg_ctx *c, vg_diag *d)
+{
+    if (!c || !d) return VG_EINVAL;
+    std::memset(d, 0, sizeof(*d));
+    d->launches = c->launches;
+    d->n_records = (int64_t)c->rec_t.size();
+    if (!c->has_mesh || !c->has_state) return VG_OK;
+    DeviceGuard guard(c->device);
+    int e = launch_diagnostics(dev_ptrs(c), c->w[c->cur], c->precision, c->prm.h_threshold, c->diag_part,
+                               c->diag_out, (void *)c->stream);
+    if (e) return cuda_fail(c, (cudaError_t)e, "diagnostics launch");
+    c->launches += 2;
+    double out[3];
+    VG_CUDA(c, cudaMemcpyAsync(out, c->diag_out, 8 * 3, cudaMemcpyDeviceToHost, c->stream));
+    DevScalars s;
+    int rc = read_scalars(c, s);
+    if (rc) return rc;
+    if ((rc = drain_gauges(c, s))) return rc;
+    d->t = s.t;
+    d->last_dt = s.dt;
+    d->mass = out[0];
+    d->min_H = out[1];
+    d->dry_count = (int64_t)out[2];
+    d->steps = s.steps;
+    d->neg_count = s.neg_count;
+    d->launches = c->launches;
+    d->n_records = (int64_t)c->rec_t.size();
+    return VG_OK;
+}
+
+int vg_profile(vg_ctx *c, int enable)
+{
+    if (!c) return VG_EINVAL;
+    c->profile = enable != 0;
+    for (int k = 0; k < kKernels; k++) { c->prof_ms[k] = 0; c->prof_n[k] = 0; }
+    c->ev_used = 0;
+    return VG_OK;
+}
+
+int vg_get_profile(vg_ctx *c, int32_t n, const char **names, int64_t *launches, double *ms, int32_t *n_out)
+{
+    if (!c || n < 0) return VG_EINVAL;
+    for (int k = 0; k < kKernels && k < n; k++) {
+        if (names) names[k] = kKernelNames[k];
+        if (launches) launches[k] = c->prof_n[k];
+        if (ms) ms[k] = c->prof_ms[k];
+    }
+    if (n_out) *n_out = kKernels;
+    return VG_OK;
+}
+
+int vg_device_bytes(vg_ctx *c, int64_t *bytes)
+{
+    if (!c || !bytes) return VG_EINVAL;
+    *bytes = c->dev_bytes;
+    return VG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,529 @@
+// Step kernels of the finite-volume shallow-water solver (Giles et al., Sec. 2),
+// templated on the arithmetic type.  Included by step_f32.cu and step_f64.cu;
+// the FP64 file is compiled with --fmad=false so that every expression rounds
+// as written.
+//
+// One SSP-RK(2,2) step (Sec. 2.3) is two persistent kernels plus a one-CTA
+// epilogue:
+//   stage 1:  R0 = L(w^n) for every cell (written to scratch) and the running
+//             minimum of the CFL bound |K| / (3 max_f l_f a_f)
+//   stage 2:  w1 = w^n + dt R0 (dry-fixed), recomputed where needed;
+//             w^{n+1} = w^n / 2 + (w1 + dt L(w1)) / 2, dry-fixed
+//   epilogue: t += dt, gauges, reset of the CFL minimum (util_kernels.cu)
+//
+// Each CTA owns a block of B consecutive (renumbered) cells and stages the
+// block plus its one-ring halo in shared memory:
+//   A  load the state of block + halo cells            (smem  sH, sHu, sHv, sz)
+//   B  reconstruct face values of block + halo cells    (smem  fH, fHu, fHv)
+//      (halo cells read their own neighbours from global memory)
+//   C  one thread per owned face computes the interface flux once
+//      (a face is owned by the lower local index, a block cell facing the
+//      halo, or a wall)                                  (smem  owned-face slots)
+//   D  one thread per block cell gathers its three faces in local order,
+//      forms the residual and updates the cell.
+// No float atomics: the gather order is fixed, and the CFL minimum uses an
+// integer atomicMin on the bits of a non-negative value (exact, order-free).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "vg_internal.h"
+
+namespace vg {
+
+template <typename real>
+struct KArgs {
+    int64_t nc;
+    int block, nblocks, max_halo, order;
+    const real *geo;        // [GEO_ROWS][nc]
+    const real *z;          // [nc]
+    const int32_t *nbr;     // [3][nc]
+    const uint16_t *nbrl;   // [3][nc]
+    const int32_t *halo_ptr;
+    const int32_t *halo_ids;
+    const real *w;          // w^n [3][nc]
+    real *R0;               // [3][nc]
+    real *wout;             // w^{n+1} [3][nc] (stage 2)
+    DevScalars *sc;
+    real g, half_g, hthr;
+    double cfl, dt_fixed, dt_max, t_end;
+};
+
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float vabs(float a) { return fabsf(a); }
+__device__ __forceinline__ double vabs(double a) { return fabs(a); }
+__device__ __forceinline__ float vsqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double vsqrt(double a) { return sqrt(a); }
+
+template <typename real> __device__ __forceinline__ real real_inf();
+template <> __device__ __forceinline__ float real_inf<float>() { return CUDART_INF_F; }
+template <> __device__ __forceinline__ double real_inf<double>() { return CUDART_INF; }
+
+// Order-preserving integer image of a non-negative real for atomicMin.
+__device__ __forceinline__ unsigned long long min_bits(float v) { return (unsigned long long)__float_as_uint(v); }
+__device__ __forceinline__ unsigned long long min_bits(double v) { return (unsigned long long)__double_as_longlong(v); }
+template <typename real> __device__ __forceinline__ double decode_min(unsigned long long b);
+template <> __device__ __forceinline__ double decode_min<float>(unsigned long long b) { return (double)__uint_as_float((unsigned int)b); }
+template <> __device__ __forceinline__ double decode_min<double>(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// Time step of the current step from the stage-1 CFL minimum (Sec. 2.3 CFL
+// condition, read as dt = cfl * min_K |K| / (3 max_f l_f a_f)), then the
+// dt_max and t_end clamps.
+template <typename real>
+__device__ __forceinline__ double step_dt(const DevScalars *sc, double cfl, double dt_fixed,
+                                          double dt_max, double t_end)
+{
+    double dt;
+    if (dt_fixed > 0.0) {
+        dt = dt_fixed;
+    } else {
+        double mn = decode_min<real>(sc->dtmin_bits);
+        dt = isinf(mn) ? (dt_max > 0.0 ? dt_max : 0.0) : cfl * mn;
+    }
+    if (dt_max > 0.0) dt = fmin(dt, dt_max);
+    double t = sc->t;
+    if (t_end > 0.0 && t + dt > t_end) dt = t_end - t;
+    if (dt < 0.0) dt = 0.0;
+    return dt;
+}
+
+// HLL flux in the face normal frame (Sec. 2.2) with the dry-bed speeds when one
+// side is dry; each side is (H*, u_n, u_t).
+template <typename real>
+__device__ __forceinline__ void hll_normal(real g, real half_g, real HL, real unL, real utL,
+                                           real HR, real unR, real utR, real F[3], real &amax)
+{
+    if (HL == real(0) && HR == real(0)) {
+        F[0] = real(0); F[1] = real(0); F[2] = real(0);
+        amax = real(0);
+        return;
+    }
+    real cL = vsqrt(g * HL);
+    real cR = vsqrt(g * HR);
+    real sL, sR;
+    if (HL == real(0)) {
+        sL = unR - real(2) * cR;
+        sR = unR + cR;
+    } else if (HR == real(0)) {
+        sL = unL - cL;
+        sR = unL + real(2) * cL;
+    } else {
+        real us = real(0.5) * (unL + unR) + (cL - cR);
+        real cs = real(0.5) * (cL + cR) - real(0.25) * (unR - unL);
+        sL = vmin(unL - cL, us - cs);
+        sR = vmax(us + cs, unR + cR);
+    }
+    real qL = HL * unL, qR = HR * unR;
+    real FL0 = qL, FL1 = qL * unL + half_g * HL * HL, FL2 = qL * utL;
+    real FR0 = qR, FR1 = qR * unR + half_g * HR * HR, FR2 = qR * utR;
+    if (sL >= real(0)) {
+        F[0] = FL0; F[1] = FL1; F[2] = FL2;
+    } else if (sR >= real(0)) {
+        real den = sR - sL;
+        real sLR = sL * sR;
+        F[0] = ((sR * FL0 - sL * FR0) + sLR * (HR - HL)) / den;
+        F[1] = ((sR * FL1 - sL * FR1) + sLR * (qR - qL)) / den;
+        F[2] = ((sR * FL2 - sL * FR2) + sLR * (HR * utR - HL * utL)) / den;
+    } else {
+        F[0] = FR0; F[1] = FR1; F[2] = FR2;
+    }
+    amax = vmax(vabs(sL), vabs(sR));
+}
+
+// Flux through a face seen from its left cell: face velocities, hydrostatic
+// interface depths z* = max(z_L, z_R), H*_s = max(0, H_{s,f} + z_s - z*), HLL,
+// rotation back to (x, y), pressure corrections g (H_{s,f}^2 - H*_s^2) / 2.
+// A wall uses the ghost of Sec. 2.5 (u_n reversed, u_t kept, same depth).
+template <typename real>
+__device__ __forceinline__ void face_flux(real g, real half_g, real hthr,
+                                          real HfL, real HufL, real HvfL, real zL,
+                                          real HfR, real HufR, real HvfR, real zR,
+                                          real nx, real ny, bool wall,
+                                          real Phi[3], real &PL, real &PR, real &amax)
+{
+    real uL = real(0), vL = real(0);
+    if (HfL > hthr) { uL = HufL / HfL; vL = HvfL / HfL; }
+    real unL = uL * nx + vL * ny;
+    real utL = -uL * ny + vL * nx;
+    real HsL, HsR, unR, utR;
+    if (wall) {
+        HsL = vmax(real(0), (HfL + zL) - zL);
+        HsR = HsL;
+        unR = -unL;
+        utR = utL;
+        HfR = HfL;
+    } else {
+        real uR = real(0), vR = real(0);
+        if (HfR > hthr) { uR = HufR / HfR; vR = HvfR / HfR; }
+        unR = uR * nx + vR * ny;
+        utR = -uR * ny + vR * nx;
+        real zs = vmax(zL, zR);
+        HsL = vmax(real(0), (HfL + zL) - zs);
+        HsR = vmax(real(0), (HfR + zR) - zs);
+    }
+    real F[3];
+    hll_normal<real>(g, half_g, HsL, unL, utL, HsR, unR, utR, F, amax);
+    Phi[0] = F[0];
+    Phi[1] = F[1] * nx - F[2] * ny;
+    Phi[2] = F[1] * ny + F[2] * nx;
+    PL = half_g * (HfL * HfL - HsL * HsL);
+    PR = half_g * (HfR * HfR - HsR * HsR);
+}
+
+// State of cell gid as seen by the stage: stage 1 reads w^n; stage 2 forms
+// w1 = w^n + dt R0 and applies the dry fix (negative depth emptied; at or below
+// the threshold, momentum zeroed).  Returns true if a negative depth was met.
+template <typename real, int STAGE>
+__device__ __forceinline__ bool stage_state(const KArgs<real> &a, int64_t gid, real dt, real &H,
+                                            real &Hu, real &Hv)
+{
+    const int64_t nc = a.nc;
+    H = a.w[gid];
+    Hu = a.w[nc + gid];
+    Hv = a.w[2 * nc + gid];
+    if (STAGE == 1) return false;
+    H = H + dt * a.R0[gid];
+    Hu = Hu + dt * a.R0[nc + gid];
+    Hv = Hv + dt * a.R0[2 * nc + gid];
+    if (H < real(0)) {
+        H = real(0); Hu = real(0); Hv = real(0);
+        return true;
+    }
+    if (H <= a.hthr) { Hu = real(0); Hv = real(0); }
+    return false;
+}
+
+template <typename real>
+__host__ __device__ inline size_t stage_smem_bytes(int block, int max_halo)
+{
+    size_t L = (size_t)block + max_halo;
+    return sizeof(real) * (13 * L + 18 * (size_t)block) + sizeof(uint16_t) * 3 * (size_t)block + 16;
+}
+
+template <typename real, int STAGE>
+__global__ void __launch_bounds__(256) stage_kernel(const KArgs<real> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int qcount;
+    __shared__ real red_min[32];
+    __shared__ long long red_neg[32];
+
+    const int B = a.block;
+    const int L = B + a.max_halo;
+    const int64_t nc = a.nc;
+    real *sH = reinterpret_cast<real *>(smem_raw);
+    real *sHu = sH + L;
+    real *sHv = sHu + L;
+    real *sz = sHv + L;
+    real *fH = sz + L;            // [3][L]
+    real *fHu = fH + 3 * L;
+    real *fHv = fHu + 3 * L;
+    real *oP0 = fHv + 3 * L;      // [3][B]
+    real *oP1 = oP0 + 3 * B;
+    real *oP2 = oP1 + 3 * B;
+    real *oPL = oP2 + 3 * B;
+    real *oPR = oPL + 3 * B;
+    real *oA = oPR + 3 * B;
+    uint16_t *queue = reinterpret_cast<uint16_t *>(oA + 3 * B);
+
+    const int tid = threadIdx.x;
+    const real g = a.g, half_g = a.half_g, hthr = a.hthr;
+    const real *geo = a.geo;
+
+    real dt = real(0);
+    if (STAGE == 2) dt = (real)step_dt<real>(a.sc, a.cfl, a.dt_fixed, a.dt_max, a.t_end);
+
+    real my_min = real_inf<real>();
+    long long my_neg = 0;
+    bool bad = false;
+
+    for (int b = blockIdx.x; b < a.nblocks; b += gridDim.x) {
+        const int64_t c0 = (int64_t)b * B;
+        const int ncell = (int)min((int64_t)B, nc - c0);
+        const int h0 = a.halo_ptr[b];
+        const int nh = a.halo_ptr[b + 1] - h0;
+
+        // A: block + halo states into shared memory
+        for (int l = tid; l < B + nh; l += blockDim.x) {
+            if (l < B && l >= ncell) continue;
+            int64_t gid = l < B ? c0 + l : (int64_t)a.halo_ids[h0 + (l - B)];
+            real H, Hu, Hv;
+            bool neg = stage_state<real, STAGE>(a, gid, dt, H, Hu, Hv);
+            if (neg && l < B) my_neg++;
+            sH[l] = H; sHu[l] = Hu; sHv[l] = Hv;
+            sz[l] = a.z[gid];
+        }
+        if (tid == 0) qcount = 0;
+        __syncthreads();
+
+        // B: face values (Sec. 2.4, Eq. recon with the Barth-Jespersen limiter)
+        for (int l = tid; l < B + nh; l += blockDim.x) {
+            if (l < B && l >= ncell) continue;
+            int64_t gid = l < B ? c0 + l : (int64_t)a.halo_ids[h0 + (l - B)];
+            const real HK = sH[l], HuK = sHu[l], HvK = sHv[l], zK = sz[l];
+            real qK[3] = {HK + zK, HuK, HvK};
+            real qn[3][3];
+            bool recon = (a.order == 2) && (HK > hthr);
+            for (int f = 0; f < 3; f++) {
+                bool wall;
+                real Hj = real(0), Huj = real(0), Hvj = real(0), zj = real(0);
+                if (l < B) {
+                    uint16_t code = a.nbrl[f * nc + gid];
+                    wall = code == NBR_WALL;
+                    if (!wall) {
+                        int nl = code >> 2;
+                        Hj = sH[nl]; Huj = sHu[nl]; Hvj = sHv[nl]; zj = sz[nl];
+                    }
+                } else {
+                    int32_t j = a.nbr[f * nc + gid];
+                    wall = j < 0;
+                    if (!wall) {
+                        if (stage_state<real, STAGE>(a, j, dt, Hj, Huj, Hvj)) { /* counted by its owner */ }
+                        zj = a.z[j];
+                    }
+                }
+                if (!wall) {
+                    qn[f][0] = Hj + zj;
+                    qn[f][1] = Huj;
+                    qn[f][2] = Hvj;
+                    if (!(Hj > hthr)) recon = false;
+                } else {
+                    real nxf = geo[(GEO_NX + f) * nc + gid], nyf = geo[(GEO_NY + f) * nc + gid];
+                    real mn = HuK * nxf + HvK * nyf;
+                    qn[f][0] = qK[0];
+                    qn[f][1] = HuK - real(2) * mn * nxf;
+                    qn[f][2] = HvK - real(2) * mn * nyf;
+                }
+            }
+            real Hf[3], Huf[3], Hvf[3];
+            if (recon) {
+                real fx[3], fy[3], wx[3], wy[3];
+                for (int f = 0; f < 3; f++) {
+                    fx[f] = geo[(GEO_FX + f) * nc + gid];
+                    fy[f] = geo[(GEO_FY + f) * nc + gid];
+                    wx[f] = geo[(GEO_WX + f) * nc + gid];
+                    wy[f] = geo[(GEO_WY + f) * nc + gid];
+                }
+                real face[3][3];
+#pragma unroll
+                for (int v = 0; v < 3; v++) {
+                    real d0 = qn[0][v] - qK[v], d1 = qn[1][v] - qK[v], d2 = qn[2][v] - qK[v];
+                    real gx = (wx[0] * d0 + wx[1] * d1) + wx[2] * d2;
+                    real gy = (wy[0] * d0 + wy[1] * d1) + wy[2] * d2;
+                    real qmax = qK[v], qmin = qK[v];
+#pragma unroll
+                    for (int f = 0; f < 3; f++) {
+                        qmax = vmax(qmax, qn[f][v]);
+                        qmin = vmin(qmin, qn[f][v]);
+                    }
+                    real alpha = real(1);
+                    real D[3];
+#pragma unroll
+                    for (int f = 0; f < 3; f++) {
+                        D[f] = gx * fx[f] + gy * fy[f];
+                        real phi = real(1);
+                        if (D[f] > real(0)) phi = vmin(real(1), (qmax - qK[v]) / D[f]);
+                        else if (D[f] < real(0)) phi = vmin(real(1), (qmin - qK[v]) / D[f]);
+                        alpha = vmin(alpha, phi);
+                    }
+#pragma unroll
+                    for (int f = 0; f < 3; f++) face[f][v] = qK[v] + alpha * D[f];
+                }
+#pragma unroll
+                for (int f = 0; f < 3; f++) {
+                    Hf[f] = face[f][0] - zK;
+                    if (!(Hf[f] > hthr)) recon = false;
+                    Huf[f] = face[f][1];
+                    Hvf[f] = face[f][2];
+                }
+            }
+            if (!recon) {
+#pragma unroll
+                for (int f = 0; f < 3; f++) { Hf[f] = HK; Huf[f] = HuK; Hvf[f] = HvK; }
+            }
+#pragma unroll
+            for (int f = 0; f < 3; f++) {
+                fH[f * L + l] = Hf[f];
+                fHu[f * L + l] = Huf[f];
+                fHv[f * L + l] = Hvf[f];
+            }
+        }
+        __syncthreads();
+
+        // C: owned faces, one flux each (Sec. 2.2)
+        if (tid < ncell) {
+            int64_t gid = c0 + tid;
+            int items[3], n = 0;
+#pragma unroll
+            for (int f = 0; f < 3; f++) {
+                uint16_t code = a.nbrl[f * nc + gid];
+                bool owned = code == NBR_WALL || (code >> 2) >= B || (int)(code >> 2) > tid;
+                if (owned) items[n++] = (tid << 2) | f;
+            }
+            if (n) {
+                int pos = atomicAdd(&qcount, n);
+                for (int k = 0; k < n; k++) queue[pos + k] = (uint16_t)items[k];
+            }
+        }
+        __syncthreads();
+        const int nq = qcount;
+        for (int q = tid; q < nq; q += blockDim.x) {
+            int item = queue[q];
+            int l = item >> 2, f = item & 3;
+            int64_t gid = c0 + l;
+            uint16_t code = a.nbrl[f * nc + gid];
+            bool wall = code == NBR_WALL;
+            real HfR = real(0), HufR = real(0), HvfR = real(0), zR = real(0);
+            if (!wall) {
+                int nl = code >> 2, nf = code & 3;
+                HfR = fH[nf * L + nl]; HufR = fHu[nf * L + nl]; HvfR = fHv[nf * L + nl];
+                zR = sz[nl];
+            }
+            real Phi[3], PL, PR, am;
+            face_flux<real>(g, half_g, hthr, fH[f * L + l], fHu[f * L + l], fHv[f * L + l], sz[l],
+                            HfR, HufR, HvfR, zR, geo[(GEO_NX + f) * nc + gid],
+                            geo[(GEO_NY + f) * nc + gid], wall, Phi, PL, PR, am);
+            int s = f * B + l;
+            oP0[s] = Phi[0]; oP1[s] = Phi[1]; oP2[s] = Phi[2];
+            oPL[s] = PL; oPR[s] = PR; oA[s] = am;
+        }
+        __syncthreads();
+
+        // D: residual R_K = -(1/|K|) sum_f l_f [Phi_f + (0, P_{K,f} n_f)], faces in local order
+        if (tid < ncell) {
+            const int l = tid;
+            const int64_t gid = c0 + l;
+            real aH = real(0), aHu = real(0), aHv = real(0), am = real(0);
+#pragma unroll
+            for (int f = 0; f < 3; f++) {
+                uint16_t code = a.nbrl[f * nc + gid];
+                bool owned = code == NBR_WALL || (code >> 2) >= B || (int)(code >> 2) > l;
+                real P0, P1, P2, P, sa;
+                if (owned) {
+                    int s = f * B + l;
+                    P0 = oP0[s]; P1 = oP1[s]; P2 = oP2[s]; P = oPL[s]; sa = oA[s];
+                } else {
+                    int s = (code & 3) * B + (code >> 2);
+                    P0 = -oP0[s]; P1 = -oP1[s]; P2 = -oP2[s]; P = oPR[s]; sa = oA[s];
+                }
+                real len = geo[(GEO_LEN + f) * nc + gid];
+                real nx = geo[(GEO_NX + f) * nc + gid], ny = geo[(GEO_NY + f) * nc + gid];
+                aH = aH + len * P0;
+                aHu = aHu + len * (P1 + P * nx);
+                aHv = aHv + len * (P2 + P * ny);
+                if (STAGE == 1) am = vmax(am, len * sa);
+            }
+            real area = geo[GEO_AREA * nc + gid];
+            real RH = -aH / area, RHu = -aHu / area, RHv = -aHv / area;
+            if (STAGE == 1) {
+                a.R0[gid] = RH;
+                a.R0[nc + gid] = RHu;
+                a.R0[2 * nc + gid] = RHv;
+                if (am > real(0)) my_min = vmin(my_min, area / (real(3) * am));
+            } else {
+                real H0 = a.w[gid], Hu0 = a.w[nc + gid], Hv0 = a.w[2 * nc + gid];
+                real H = real(0.5) * H0 + real(0.5) * (sH[l] + dt * RH);
+                real Hu = real(0.5) * Hu0 + real(0.5) * (sHu[l] + dt * RHu);
+                real Hv = real(0.5) * Hv0 + real(0.5) * (sHv[l] + dt * RHv);
+                if (H < real(0)) {
+                    my_neg++;
+                    H = real(0); Hu = real(0); Hv = real(0);
+                } else if (H <= hthr) {
+                    Hu = real(0); Hv = real(0);
+                }
+                if (!isfinite(H) || !isfinite(Hu) || !isfinite(Hv)) bad = true;
+                a.wout[gid] = H;
+                a.wout[nc + gid] = Hu;
+                a.wout[2 * nc + gid] = Hv;
+            }
+        }
+        __syncthreads();
+    }
+
+    // CTA-level reductions, then one atomic per CTA
+    const int lane = tid & 31, warp = tid >> 5, nwarps = (blockDim.x + 31) >> 5;
+    if (STAGE == 1) {
+        for (int o = 16; o > 0; o >>= 1) my_min = vmin(my_min, __shfl_xor_sync(0xffffffffu, my_min, o));
+        if (lane == 0) red_min[warp] = my_min;
+    }
+    for (int o = 16; o > 0; o >>= 1) my_neg += __shfl_xor_sync(0xffffffffu, my_neg, o);
+    if (lane == 0) red_neg[warp] = my_neg;
+    bad = __syncthreads_or(bad);
+    if (tid == 0) {
+        long long neg = 0;
+        real mn = real_inf<real>();
+        for (int w = 0; w < nwarps; w++) {
+            neg += red_neg[w];
+            if (STAGE == 1) mn = vmin(mn, red_min[w]);
+        }
+        if (STAGE == 1 && mn < real_inf<real>()) atomicMin(&a.sc->dtmin_bits, min_bits(mn));
+        if (neg) atomicAdd((unsigned long long *)&a.sc->neg_count, (unsigned long long)neg);
+        if (bad) atomicOr(&a.sc->flags, FLAG_NONFINITE_STATE);
+    }
+}
+
+template <typename real>
+KArgs<real> make_args(const DevPtrs &d, const StepParams &p, const void *w_in, void *w_out)
+{
+    KArgs<real> a;
+    a.nc = d.nc;
+    a.block = d.block;
+    a.nblocks = d.nblocks;
+    a.max_halo = d.max_halo;
+    a.order = p.order;
+    a.geo = static_cast<const real *>(d.geo);
+    a.z = static_cast<const real *>(d.z);
+    a.nbr = d.nbr;
+    a.nbrl = d.nbrl;
+    a.halo_ptr = d.halo_ptr;
+    a.halo_ids = d.halo_ids;
+    a.w = static_cast<const real *>(w_in);
+    a.R0 = static_cast<real *>(d.R0);
+    a.wout = static_cast<real *>(w_out);
+    a.sc = d.sc;
+    a.g = (real)p.g;
+    a.half_g = (real)(0.5 * p.g);
+    a.hthr = (real)p.hthr;
+    a.cfl = p.cfl;
+    a.dt_fixed = p.dt_fixed;
+    a.dt_max = p.dt_max;
+    a.t_end = p.t_end;
+    return a;
+}
+
+template <typename real>
+int stage_config(const DevPtrs &d, int stage, LaunchCfg &cfg)
+{
+    cfg.smem = stage_smem_bytes<real>(d.block, d.max_halo);
+    auto kern = stage == 1 ? stage_kernel<real, 1> : stage_kernel<real, 2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+    if (e != cudaSuccess) return (int)e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, d.block, cfg.smem);
+    if (e != cudaSuccess) return (int)e;
+    if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long grid = (long long)sms * per_sm;
+    if (grid > d.nblocks) grid = d.nblocks;
+    cfg.grid = (int)(grid < 1 ? 1 : grid);
+    return 0;
+}
+
+template <typename real>
+int launch_stage(const DevPtrs &d, const StepParams &p, int stage, const void *w_in, void *w_out,
+                 const LaunchCfg &c, void *stream)
+{
+    KArgs<real> a = make_args<real>(d, p, w_in, w_out);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (stage == 1) stage_kernel<real, 1><<<c.grid, d.block, c.smem, s>>>(a);
+    else stage_kernel<real, 2><<<c.grid, d.block, c.smem, s>>>(a);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace vg

@@ -1,0 +1,215 @@
+// Small kernels around the step: the per-step epilogue (time, gauges, reset of
+// the CFL minimum), state import/export with the cell permutation, and the
+// diagnostics reduction.
+#include "step_kernels.cuh"
+
+namespace vg {
+
+namespace {
+
+template <typename real>
+__device__ __forceinline__ unsigned long long inf_bits();
+template <> __device__ __forceinline__ unsigned long long inf_bits<float>() { return (unsigned long long)__float_as_uint(CUDART_INF_F); }
+template <> __device__ __forceinline__ unsigned long long inf_bits<double>() { return (unsigned long long)__double_as_longlong(CUDART_INF); }
+
+// Epilogue of one step: t += dt (Sec. 2.3), gauge record (Sec. 3 virtual gauges:
+// eta = H + z of each gauge cell), reset of the CFL minimum for the next step.
+template <typename real>
+__global__ void post_step_kernel(DevPtrs d, StepParams p, const real *w)
+{
+    __shared__ long long rec;
+    DevScalars *sc = d.sc;
+    if (threadIdx.x == 0) {
+        double dt = step_dt<real>(sc, p.cfl, p.dt_fixed, p.dt_max, p.t_end);
+        sc->dt = dt;
+        rec = -1;
+        if (!isfinite(dt)) sc->flags |= FLAG_NONFINITE_DT;
+        if (dt > 0.0) {
+            sc->t = sc->t + dt;
+            sc->steps += 1;
+            if (d.n_gauges > 0 && sc->steps % p.gauge_every == 0) {
+                if (sc->n_rec < d.ring_cap) {
+                    rec = sc->n_rec;
+                    sc->n_rec = rec + 1;
+                    d.ring_t[rec] = sc->t;
+                } else {
+                    sc->flags |= FLAG_RING_FULL;
+                }
+            }
+        }
+        sc->dtmin_bits = inf_bits<real>();
+    }
+    __syncthreads();
+    if (rec >= 0) {
+        const real *z = static_cast<const real *>(d.z);
+        for (int g = threadIdx.x; g < d.n_gauges; g += blockDim.x) {
+            int32_t c = d.gauge_cells[g];
+            d.ring_eta[rec * d.n_gauges + g] = (double)(w[c] + z[c]);
+        }
+    }
+}
+
+template <typename real>
+__global__ void record_gauges_kernel(DevPtrs d, const real *w)
+{
+    DevScalars *sc = d.sc;
+    long long rec = sc->n_rec;
+    if (rec >= d.ring_cap) {
+        if (threadIdx.x == 0) sc->flags |= FLAG_RING_FULL;
+        return;
+    }
+    const real *z = static_cast<const real *>(d.z);
+    for (int g = threadIdx.x; g < d.n_gauges; g += blockDim.x) {
+        int32_t c = d.gauge_cells[g];
+        d.ring_eta[rec * d.n_gauges + g] = (double)(w[c] + z[c]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        d.ring_t[rec] = sc->t;
+        sc->n_rec = rec + 1;
+    }
+}
+
+template <typename real, typename src_t>
+__global__ void import_state_kernel(int64_t nc, const int32_t *old_of_new, const src_t *H,
+                                    const src_t *Hu, const src_t *Hv, real *w, DevScalars *sc)
+{
+    bool bad = false;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nc; k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t o = old_of_new[k];
+        src_t h = H[o], hu = Hu[o], hv = Hv[o];
+        if (!(h >= src_t(0)) || !isfinite(h) || !isfinite(hu) || !isfinite(hv)) bad = true;
+        w[k] = (real)h;
+        w[nc + k] = (real)hu;
+        w[2 * nc + k] = (real)hv;
+    }
+    if (bad) atomicOr(&sc->flags, FLAG_BAD_INPUT);
+}
+
+template <typename real, typename dst_t>
+__global__ void export_state_kernel(int64_t nc, const int32_t *old_of_new, const real *w, dst_t *H,
+                                    dst_t *Hu, dst_t *Hv)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nc; k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t o = old_of_new[k];
+        H[o] = (dst_t)w[k];
+        Hu[o] = (dst_t)w[nc + k];
+        Hv[o] = (dst_t)w[2 * nc + k];
+    }
+}
+
+constexpr int DIAG_BLOCKS = 1024;
+
+// Fixed grid, fixed reduction tree: the sums do not depend on timing.
+template <typename real>
+__global__ void diag_partial_kernel(int64_t nc, const real *w, const real *geo, double hthr, double *part)
+{
+    __shared__ double s_mass[256], s_min[256], s_dry[256];
+    double mass = 0.0, mn = CUDART_INF, dry = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nc; k += (int64_t)gridDim.x * blockDim.x) {
+        double h = (double)w[k];
+        mass += (double)geo[GEO_AREA * nc + k] * h;
+        mn = fmin(mn, h);
+        dry += h <= hthr ? 1.0 : 0.0;
+    }
+    s_mass[threadIdx.x] = mass; s_min[threadIdx.x] = mn; s_dry[threadIdx.x] = dry;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            s_mass[threadIdx.x] += s_mass[threadIdx.x + o];
+            s_min[threadIdx.x] = fmin(s_min[threadIdx.x], s_min[threadIdx.x + o]);
+            s_dry[threadIdx.x] += s_dry[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = s_mass[0];
+        part[3 * blockIdx.x + 1] = s_min[0];
+        part[3 * blockIdx.x + 2] = s_dry[0];
+    }
+}
+
+__global__ void diag_final_kernel(const double *part, int n, double *out)
+{
+    if (threadIdx.x == 0) {
+        double mass = 0.0, mn = CUDART_INF, dry = 0.0;
+        for (int i = 0; i < n; i++) {
+            mass += part[3 * i];
+            mn = fmin(mn, part[3 * i + 1]);
+            dry += part[3 * i + 2];
+        }
+        out[0] = mass; out[1] = mn; out[2] = dry;
+    }
+}
+
+int grid_for(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 4096); }
+
+}  // namespace
+
+int launch_post_step(const DevPtrs &d, const StepParams &p, const void *w, int precision, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == 64) post_step_kernel<double><<<1, 128, 0, s>>>(d, p, static_cast<const double *>(w));
+    else post_step_kernel<float><<<1, 128, 0, s>>>(d, p, static_cast<const float *>(w));
+    return (int)cudaGetLastError();
+}
+
+int launch_record_gauges(const DevPtrs &d, const void *w, int precision, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == 64) record_gauges_kernel<double><<<1, 128, 0, s>>>(d, static_cast<const double *>(w));
+    else record_gauges_kernel<float><<<1, 128, 0, s>>>(d, static_cast<const float *>(w));
+    return (int)cudaGetLastError();
+}
+
+int launch_import_state(const DevPtrs &d, const int32_t *old_of_new, const void *H, const void *Hu,
+                        const void *Hv, int src_is_double, void *w, int precision, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int grid = grid_for(d.nc);
+    if (precision == 64) {
+        if (src_is_double)
+            import_state_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)H, (const double *)Hu, (const double *)Hv, (double *)w, d.sc);
+        else
+            import_state_kernel<double, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)H, (const float *)Hu, (const float *)Hv, (double *)w, d.sc);
+    } else {
+        if (src_is_double)
+            import_state_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)H, (const double *)Hu, (const double *)Hv, (float *)w, d.sc);
+        else
+            import_state_kernel<float, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)H, (const float *)Hu, (const float *)Hv, (float *)w, d.sc);
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_export_state(const DevPtrs &d, const int32_t *old_of_new, const void *w, int precision,
+                        void *H, void *Hu, void *Hv, int dst_is_double, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int grid = grid_for(d.nc);
+    if (precision == 64) {
+        if (dst_is_double)
+            export_state_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)w, (double *)H, (double *)Hu, (double *)Hv);
+        else
+            export_state_kernel<double, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)w, (float *)H, (float *)Hu, (float *)Hv);
+    } else {
+        if (dst_is_double)
+            export_state_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)w, (double *)H, (double *)Hu, (double *)Hv);
+        else
+            export_state_kernel<float, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)w, (float *)H, (float *)Hu, (float *)Hv);
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_diagnostics(const DevPtrs &d, const void *w, int precision, double hthr, double *part,
+                       double *out, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == 64)
+        diag_partial_kernel<double><<<DIAG_BLOCKS, 256, 0, s>>>(d.nc, (const double *)w, (const double *)d.geo, hthr, part);
+    else
+        diag_partial_kernel<float><<<DIAG_BLOCKS, 256, 0, s>>>(d.nc, (const float *)w, (const float *)d.geo, hthr, part);
+    diag_final_kernel<<<1, 32, 0, s>>>(part, DIAG_BLOCKS, out);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace vg

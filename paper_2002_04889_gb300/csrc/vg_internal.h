@@ -1,0 +1,122 @@
+// Internal declarations of the volna_gb library: host mesh preparation, the
+// device data layout, and the launch wrappers of the step kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace vg {
+
+// Per-cell geometry rows stored on the device, [GEO_ROWS][nc], in the order
+// below.  Face f of a cell joins its local vertices f and f+1; the local order
+// is counter-clockwise from the vertex with the smallest input id.
+enum GeoRow : int {
+    GEO_NX = 0,    // 3 rows: outward unit normal x of faces 0..2
+    GEO_NY = 3,    // 3 rows: outward unit normal y
+    GEO_LEN = 6,   // 3 rows: face length
+    GEO_FX = 9,    // 3 rows: face midpoint minus centroid, x
+    GEO_FY = 12,   // 3 rows: face midpoint minus centroid, y
+    GEO_WX = 15,   // 3 rows: least-squares weight, x
+    GEO_WY = 18,   // 3 rows: least-squares weight, y
+    GEO_AREA = 21, // 1 row: cell area
+    GEO_ROWS = 22
+};
+
+constexpr uint16_t NBR_WALL = 0xFFFF;
+
+// Host-side prepared mesh, cells in the library's (renumbered) order.
+struct HostMesh {
+    int64_t nc = 0, nv = 0;
+    int64_t n_flipped = 0;
+    int32_t block = 256;                 // cells per block
+    int32_t nblocks = 0;
+    int32_t max_halo = 0;
+    std::vector<int32_t> new_of_old, old_of_new;
+    std::vector<int32_t> vtx;            // [nc][3] local-order vertices (original cell order)
+    std::vector<double> geo;             // [GEO_ROWS][nc]  (internal order)
+    std::vector<double> z;               // [nc]            (internal order)
+    std::vector<int32_t> nbr;            // [3][nc] internal neighbour ids, -1 wall
+    std::vector<uint16_t> nbrl;          // [3][nc] (local << 2 | face) or NBR_WALL
+    std::vector<int32_t> halo_ptr;       // [nblocks + 1]
+    std::vector<int32_t> halo_ids;       // internal ids of each block's halo cells
+    std::vector<double> xy;              // [nv][2] copy for point location
+};
+
+// Builds everything in HostMesh.  Returns 0 or a VG_E* code with a message.
+int prepare_mesh(int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
+                 const double *depth_v, int renumber, int block, HostMesh &m, std::string &err);
+
+// Re-partitions an already prepared mesh into blocks of `block` cells.
+int partition_blocks(HostMesh &m, int block, std::string &err);
+
+// Cells containing each point (original ids; ties to the lowest id), -1 if none.
+void locate_points(const HostMesh &m, int32_t n, const double *pts, int32_t *cells);
+
+// Device scalars shared by the step kernels of one context.
+struct DevScalars {
+    double t;             // simulated time
+    double dt;            // time step of the current step
+    unsigned long long dtmin_bits;  // running min of the stage-1 CFL bound (bits of a
+                                    // non-negative real: integer order = value order)
+    long long steps;      // steps with dt > 0
+    long long n_rec;      // gauge records in the device ring
+    long long neg_count;  // negative depths met
+    unsigned int flags;   // FLAG_* bits
+    int pad;
+};
+
+enum : unsigned int {
+    FLAG_NONFINITE_STATE = 1u,
+    FLAG_NONFINITE_DT = 2u,
+    FLAG_RING_FULL = 4u,
+    FLAG_BAD_INPUT = 8u,
+};
+
+struct StepParams {
+    double g, cfl, hthr, dt_fixed, dt_max, t_end;
+    int order, gauge_every;
+};
+
+// Device pointers of one context (element type = the context's real).
+struct DevPtrs {
+    int64_t nc;
+    int32_t block, nblocks, max_halo, n_gauges, ring_cap;
+    const void *geo;        // [GEO_ROWS][nc]
+    const void *z;          // [nc]
+    const int32_t *nbr;     // [3][nc]
+    const uint16_t *nbrl;   // [3][nc]
+    const int32_t *halo_ptr;
+    const int32_t *halo_ids;
+    void *R0;               // [3][nc] stage-1 residual (scratch)
+    DevScalars *sc;
+    const int32_t *gauge_cells;   // internal ids
+    double *ring_t;               // [ring_cap]
+    double *ring_eta;             // [ring_cap][n_gauges]
+};
+
+// Launch wrappers (defined in step_f32.cu / step_f64.cu).  w_in, w_out are
+// [3][nc] state buffers.  Return cudaError_t as int.
+struct LaunchCfg {
+    int grid;        // persistent CTAs
+    size_t smem;     // dynamic shared memory per CTA
+};
+int stage_config_f32(const DevPtrs &d, int stage, LaunchCfg &cfg);
+int stage_config_f64(const DevPtrs &d, int stage, LaunchCfg &cfg);
+int launch_stage1_f32(const DevPtrs &d, const StepParams &p, const void *w_in, const LaunchCfg &c, void *stream);
+int launch_stage2_f32(const DevPtrs &d, const StepParams &p, const void *w_in, void *w_out, const LaunchCfg &c, void *stream);
+int launch_stage1_f64(const DevPtrs &d, const StepParams &p, const void *w_in, const LaunchCfg &c, void *stream);
+int launch_stage2_f64(const DevPtrs &d, const StepParams &p, const void *w_in, void *w_out, const LaunchCfg &c, void *stream);
+
+// Utility kernels (util_kernels.cu).
+int launch_post_step(const DevPtrs &d, const StepParams &p, const void *w, int precision, void *stream);
+int launch_record_gauges(const DevPtrs &d, const void *w, int precision, void *stream);
+int launch_import_state(const DevPtrs &d, const int32_t *old_of_new, const void *H, const void *Hu,
+                        const void *Hv, int src_is_double, void *w, int precision, void *stream);
+int launch_export_state(const DevPtrs &d, const int32_t *old_of_new, const void *w, int precision,
+                        void *H, void *Hu, void *Hv, int dst_is_double, void *stream);
+int launch_diagnostics(const DevPtrs &d, const void *w, int precision, double hthr, double *part,
+                       double *out, void *stream);
+
+}  // namespace vg

@@ -1,0 +1,376 @@
+"""Python binding of the volna_gb C ABI (include/volna_gb.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+``_build/libvolna_gb.so``.  There is no fallback: if the library cannot be
+loaded, importing the solver raises.
+
+The functions ``vg_*`` mirror the C entry points one to one (same names,
+same arguments, status codes turned into ``VolnaError``).  ``Solver`` wraps a
+context for convenience and accepts numpy arrays (host) or CUDA torch tensors
+(device, read on the context's stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+VG_OK = 0
+VG_EINVAL = -1
+VG_ENOMEM = -2
+VG_ECUDA = -3
+VG_ENONFINITE = -4
+VG_ENEGDEPTH = -5
+VG_ETIMEOUT = -6
+VG_ESTATE = -7
+
+RENUMBER = {"none": 0, "morton": 1, "rcm": 2}
+
+
+class VolnaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+class vg_params(C.Structure):
+    _fields_ = [("g", C.c_double), ("cfl", C.c_double), ("h_threshold", C.c_double),
+                ("dt_fixed", C.c_double), ("dt_max", C.c_double), ("t_end", C.c_double),
+                ("order", C.c_int32), ("gauge_every", C.c_int32),
+                ("strict_positivity", C.c_int32), ("block_cells", C.c_int32)]
+
+
+class vg_diag(C.Structure):
+    _fields_ = [("t", C.c_double), ("last_dt", C.c_double), ("mass", C.c_double),
+                ("min_H", C.c_double), ("steps", C.c_int64), ("neg_count", C.c_int64),
+                ("dry_count", C.c_int64), ("launches", C.c_int64), ("n_records", C.c_int64)]
+
+
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_I64 = C.POINTER(C.c_int64)
+_V = C.c_void_p
+_lib = None
+
+_SIGNATURES = {
+    "vg_version": ([], C.c_int),
+    "vg_strerror": ([C.c_int], C.c_char_p),
+    "vg_default_params": ([C.POINTER(vg_params)], C.c_int),
+    "vg_create": ([C.POINTER(_V), C.c_int, C.c_int, _V], C.c_int),
+    "vg_destroy": ([_V], None),
+    "vg_last_error": ([_V], C.c_char_p),
+    "vg_mesh_upload": ([_V, C.c_int64, _D, C.c_int64, _I32, _D, C.c_int], C.c_int),
+    "vg_get_permutation": ([_V, _I32], C.c_int),
+    "vg_get_flipped": ([_V, _I64], C.c_int),
+    "vg_set_params": ([_V, C.POINTER(vg_params)], C.c_int),
+    "vg_get_params": ([_V, C.POINTER(vg_params)], C.c_int),
+    "vg_set_state": ([_V, _D, _D, _D, C.c_double], C.c_int),
+    "vg_set_state_dev": ([_V, _V, _V, _V, C.c_double], C.c_int),
+    "vg_get_state": ([_V, _D, _D, _D, _D], C.c_int),
+    "vg_get_state_dev": ([_V, _V, _V, _V], C.c_int),
+    "vg_set_gauges": ([_V, C.c_int32, _D], C.c_int),
+    "vg_get_gauge_cells": ([_V, _I32], C.c_int),
+    "vg_step": ([_V, C.c_int64], C.c_int),
+    "vg_advance_to": ([_V, C.c_double], C.c_int),
+    "vg_get_gauges": ([_V, _D, _D, C.c_int64, _I64], C.c_int),
+    "vg_get_diagnostics": ([_V, C.POINTER(vg_diag)], C.c_int),
+    "vg_profile": ([_V, C.c_int], C.c_int),
+    "vg_get_profile": ([_V, C.c_int32, C.POINTER(C.c_char_p), _I64, _D, _I32], C.c_int),
+    "vg_device_bytes": ([_V, _I64], C.c_int),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libvolna_gb.so (building it first if it is missing); raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"volna_gb CUDA library not built: {path}")
+        _build.build()
+    lib = C.CDLL(path)
+    for name, (args, res) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(ctx, rc: int) -> None:
+    if rc != VG_OK:
+        lib = load()
+        msg = lib.vg_last_error(ctx).decode() if ctx else lib.vg_strerror(rc).decode()
+        raise VolnaError(rc, msg or lib.vg_strerror(rc).decode())
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+# ---------------------------------------------------------------- one-to-one entry points
+
+
+def vg_version() -> int:
+    return load().vg_version()
+
+
+def vg_strerror(code: int) -> str:
+    return load().vg_strerror(code).decode()
+
+
+def vg_default_params() -> vg_params:
+    p = vg_params()
+    _check(None, load().vg_default_params(C.byref(p)))
+    return p
+
+
+def vg_create(precision: int = 64, device: int = 0, stream: int | None = None):
+    h = _V()
+    rc = load().vg_create(C.byref(h), int(precision), int(device), _V(stream) if stream else None)
+    if rc != VG_OK:
+        raise VolnaError(rc, f"vg_create failed: {vg_strerror(rc)}")
+    return h
+
+
+def vg_destroy(ctx) -> None:
+    load().vg_destroy(ctx)
+
+
+def vg_last_error(ctx) -> str:
+    return load().vg_last_error(ctx).decode()
+
+
+def vg_mesh_upload(ctx, xy, tri, depth_v, renumber=1) -> None:
+    xy = _f64(xy).reshape(-1, 2)
+    tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
+    depth_v = _f64(depth_v)
+    if isinstance(renumber, str):
+        renumber = RENUMBER[renumber]
+    _check(ctx, load().vg_mesh_upload(ctx, xy.shape[0], _dp(xy), tri.shape[0],
+                                      tri.ctypes.data_as(_I32), _dp(depth_v), int(renumber)))
+
+
+def vg_get_permutation(ctx, nc: int) -> np.ndarray:
+    out = np.empty(nc, dtype=np.int32)
+    _check(ctx, load().vg_get_permutation(ctx, out.ctypes.data_as(_I32)))
+    return out
+
+
+def vg_get_flipped(ctx) -> int:
+    n = C.c_int64()
+    _check(ctx, load().vg_get_flipped(ctx, C.byref(n)))
+    return n.value
+
+
+def vg_set_params(ctx, p: vg_params) -> None:
+    _check(ctx, load().vg_set_params(ctx, C.byref(p)))
+
+
+def vg_get_params(ctx) -> vg_params:
+    p = vg_params()
+    _check(ctx, load().vg_get_params(ctx, C.byref(p)))
+    return p
+
+
+def vg_set_state(ctx, H, Hu, Hv, t=0.0) -> None:
+    H, Hu, Hv = _f64(H), _f64(Hu), _f64(Hv)
+    _check(ctx, load().vg_set_state(ctx, _dp(H), _dp(Hu), _dp(Hv), float(t)))
+
+
+def vg_set_state_dev(ctx, H_ptr: int, Hu_ptr: int, Hv_ptr: int, t=0.0) -> None:
+    _check(ctx, load().vg_set_state_dev(ctx, _V(H_ptr), _V(Hu_ptr), _V(Hv_ptr), float(t)))
+
+
+def vg_get_state(ctx, nc: int, out=None):
+    if out is None:
+        out = (np.empty(nc), np.empty(nc), np.empty(nc))
+    t = C.c_double()
+    _check(ctx, load().vg_get_state(ctx, _dp(out[0]), _dp(out[1]), _dp(out[2]), C.byref(t)))
+    return out[0], out[1], out[2], t.value
+
+
+def vg_get_state_dev(ctx, H_ptr: int, Hu_ptr: int, Hv_ptr: int) -> None:
+    _check(ctx, load().vg_get_state_dev(ctx, _V(H_ptr), _V(Hu_ptr), _V(Hv_ptr)))
+
+
+def vg_set_gauges(ctx, xy) -> None:
+    xy = _f64(xy).reshape(-1, 2)
+    _check(ctx, load().vg_set_gauges(ctx, xy.shape[0], _dp(xy) if xy.shape[0] else None))
+
+
+def vg_get_gauge_cells(ctx, n: int) -> np.ndarray:
+    out = np.empty(max(n, 1), dtype=np.int32)
+    _check(ctx, load().vg_get_gauge_cells(ctx, out.ctypes.data_as(_I32)))
+    return out[:n]
+
+
+def vg_step(ctx, n_steps: int) -> None:
+    _check(ctx, load().vg_step(ctx, int(n_steps)))
+
+
+def vg_advance_to(ctx, t: float) -> None:
+    _check(ctx, load().vg_advance_to(ctx, float(t)))
+
+
+def vg_get_gauges(ctx, n_gauges: int):
+    n = C.c_int64()
+    _check(ctx, load().vg_get_gauges(ctx, None, None, 0, C.byref(n)))
+    t = np.empty(max(n.value, 1))
+    eta = np.empty((max(n.value, 1), max(n_gauges, 1)))
+    _check(ctx, load().vg_get_gauges(ctx, _dp(t), _dp(eta), n.value, C.byref(n)))
+    return t[:n.value], eta[:n.value, :n_gauges]
+
+
+def vg_get_diagnostics(ctx) -> dict:
+    d = vg_diag()
+    _check(ctx, load().vg_get_diagnostics(ctx, C.byref(d)))
+    return {k: getattr(d, k) for k, _ in vg_diag._fields_}
+
+
+def vg_profile(ctx, enable: bool) -> None:
+    _check(ctx, load().vg_profile(ctx, 1 if enable else 0))
+
+
+def vg_get_profile(ctx) -> dict:
+    n = 16
+    names = (C.c_char_p * n)()
+    launches = np.zeros(n, dtype=np.int64)
+    ms = np.zeros(n)
+    n_out = C.c_int32()
+    _check(ctx, load().vg_get_profile(ctx, n, names, launches.ctypes.data_as(_I64), _dp(ms),
+                                      C.byref(n_out)))
+    return {names[k].decode(): (int(launches[k]), float(ms[k])) for k in range(n_out.value)}
+
+
+def vg_device_bytes(ctx) -> int:
+    b = C.c_int64()
+    _check(ctx, load().vg_device_bytes(ctx, C.byref(b)))
+    return b.value
+
+
+# ---------------------------------------------------------------- convenience wrapper
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)          # torch.cuda.Stream
+
+
+class Solver:
+    """One context: a mesh, parameters, a state and gauges on one GPU."""
+
+    def __init__(self, precision: int = 64, device: int = 0, stream=None):
+        self.precision = precision
+        self.ctx = vg_create(precision, device, _stream_handle(stream))
+        self.nc = 0
+        self.n_gauges = 0
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            vg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # mesh / parameters
+    def upload_mesh(self, mesh=None, xy=None, tri=None, depth=None, renumber="morton") -> None:
+        if mesh is not None:
+            xy, tri, depth = mesh.xy, mesh.tri, mesh.depth
+        vg_mesh_upload(self.ctx, xy, tri, depth, renumber)
+        self.nc = int(np.asarray(tri).reshape(-1, 3).shape[0])
+        self.n_gauges = 0
+
+    def set_params(self, **kw) -> vg_params:
+        p = vg_get_params(self.ctx)
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise KeyError(k)
+            setattr(p, k, v)
+        vg_set_params(self.ctx, p)
+        return p
+
+    @property
+    def params(self) -> dict:
+        p = vg_get_params(self.ctx)
+        return {k: getattr(p, k) for k, _ in vg_params._fields_}
+
+    def permutation(self) -> np.ndarray:
+        return vg_get_permutation(self.ctx, self.nc)
+
+    # state
+    def set_state(self, H, Hu, Hv, t: float = 0.0) -> None:
+        if hasattr(H, "is_cuda") and H.is_cuda:
+            import torch
+            dt = torch.float64 if self.precision == 64 else torch.float32
+            H, Hu, Hv = (x.to(dt).contiguous() for x in (H, Hu, Hv))
+            vg_set_state_dev(self.ctx, H.data_ptr(), Hu.data_ptr(), Hv.data_ptr(), t)
+            self._keep = (H, Hu, Hv)
+        else:
+            vg_set_state(self.ctx, H, Hu, Hv, t)
+
+    def get_state(self):
+        """(H, Hu, Hv, t) as float64 numpy arrays in the original cell order."""
+        return vg_get_state(self.ctx, self.nc)
+
+    def get_state_dev(self, out=None):
+        import torch
+        dt = torch.float64 if self.precision == 64 else torch.float32
+        if out is None:
+            out = tuple(torch.empty(self.nc, dtype=dt, device="cuda") for _ in range(3))
+        vg_get_state_dev(self.ctx, out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr())
+        return out
+
+    # gauges and stepping
+    def set_gauges(self, xy) -> np.ndarray:
+        xy = _f64(xy).reshape(-1, 2)
+        vg_set_gauges(self.ctx, xy)
+        self.n_gauges = xy.shape[0]
+        return vg_get_gauge_cells(self.ctx, self.n_gauges)
+
+    def step(self, n: int = 1) -> None:
+        vg_step(self.ctx, n)
+
+    def advance_to(self, t: float) -> None:
+        vg_advance_to(self.ctx, t)
+
+    def gauges(self):
+        return vg_get_gauges(self.ctx, self.n_gauges)
+
+    def diagnostics(self) -> dict:
+        return vg_get_diagnostics(self.ctx)
+
+    def profile(self, enable: bool = True) -> None:
+        vg_profile(self.ctx, enable)
+
+    def get_profile(self) -> dict:
+        return vg_get_profile(self.ctx)
+
+    def device_bytes(self) -> int:
+        return vg_device_bytes(self.ctx)

@@ -1,0 +1,258 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP64 within 1e-10 relative L2 per field, FP32 within 1e-4 relative
+L2 of the FP64 oracle per field (both after 100 steps on the Thacker basin).
+The FP64 kernels are built without multiply-add contraction and evaluate every
+formula in the same order as the oracle, so FP64 agreement is expected to be
+exact; the test still uses the stated tolerance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2002_04889_gb300 import inputs as I
+from paper_2002_04889_gb300 import volna
+from gpu_helpers import FIELDS, VertexAdjacency, gpu_run, oracle_run, patch_mesh, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def thacker():
+    m = I.thacker_mesh(n=100)                  # 20,000 triangles, dx = 0.04 (Sec. 3 basin)
+    return m, I.thacker_initial_state(m)
+
+
+@pytest.fixture(scope="module")
+def thacker_ref(thacker):
+    m, s = thacker
+    return oracle_run(m, s, 100, gauges=I.THACKER_GAUGES, h_threshold=1e-5, cfl=0.9)
+
+
+@pytest.mark.parametrize("renumber", ["none", "morton", "rcm"])
+def test_fp64_parity_thacker_100_steps(thacker, thacker_ref, renumber):
+    m, s = thacker
+    g = gpu_run(m, s, 100, precision=64, renumber=renumber, gauges=I.THACKER_GAUGES,
+                h_threshold=1e-5, cfl=0.9)
+    for f in FIELDS:
+        err = rel_l2(g[f], thacker_ref[f])
+        assert err <= TOL64, (f, err, np.abs(g[f] - thacker_ref[f]).max())
+    assert g["t"] == pytest.approx(thacker_ref["t"], rel=1e-14)
+    assert g["diag"]["neg_count"] == thacker_ref["neg_count"] == 0
+    # gauges: record at t0 plus one per step, eta of the containing cell
+    assert g["gauge_eta"].shape == (101, 3)
+    np.testing.assert_allclose(g["gauge_eta"][1:], thacker_ref["gauges"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(np.diff(g["gauge_t"]), thacker_ref["dts"], rtol=1e-13)
+
+
+def test_fp32_parity_thacker_100_steps(thacker, thacker_ref):
+    m, s = thacker
+    g = gpu_run(m, s, 100, precision=32, renumber="morton", h_threshold=1e-5, cfl=0.9)
+    errs = {f: rel_l2(g[f], thacker_ref[f]) for f in FIELDS}
+    print("FP32 relative L2 after 100 steps:", errs)
+    for f in FIELDS:
+        assert errs[f] <= TOL32, (f, errs[f])
+    assert g["t"] == pytest.approx(thacker_ref["t"], rel=1e-4)
+
+
+@pytest.mark.parametrize("n,block", [(7, 32), (23, 64), (37, 128), (50, 256), (61, 96)])
+def test_ragged_tiles_fp64(n, block):
+    """Meshes spanning several blocks with a ragged last block, several block sizes."""
+    m = I.thacker_mesh(n=n, shuffle_cells=True)
+    s = I.thacker_initial_state(m)
+    assert m.nc % block != 0
+    g = gpu_run(m, s, 20, precision=64, renumber="morton", h_threshold=1e-5, block_cells=block)
+    r = oracle_run(m, s, 20, h_threshold=1e-5)
+    for f in FIELDS:
+        assert rel_l2(g[f], r[f]) <= TOL64, f
+
+
+def test_coast_basin_fp64_fp32():
+    """Synthetic ocean-to-coast basin (N-wave uplift, inundation, H_threshold 1e-3 m)."""
+    m = I.coast_mesh(n_theta=40, n_xi=120)
+    s = I.coast_initial_state(m)
+    gauges = I.coast_gauges()
+    r = oracle_run(m, s, 60, gauges=gauges, h_threshold=1e-3, cfl=0.9)
+    g64 = gpu_run(m, s, 60, precision=64, gauges=gauges, h_threshold=1e-3, cfl=0.9)
+    g32 = gpu_run(m, s, 60, precision=32, gauges=gauges, h_threshold=1e-3, cfl=0.9)
+    for f in FIELDS:
+        assert rel_l2(g64[f], r[f]) <= TOL64, f
+        assert rel_l2(g32[f], r[f]) <= TOL32, (f, rel_l2(g32[f], r[f]))
+    np.testing.assert_allclose(g64["gauge_eta"][1:], r["gauges"], atol=1e-9)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_fixed_dt_t_end_and_order(thacker, order):
+    m, s = thacker
+    kw = dict(h_threshold=1e-5, dt_fixed=0.45 * 0.04 * 0.1, t_end=0.05, order=order)
+    g = gpu_run(m, s, 40, precision=64, **kw)
+    r = oracle_run(m, s, 40, **kw)
+    for f in FIELDS:
+        assert rel_l2(g[f], r[f]) <= TOL64, f
+    assert g["t"] == pytest.approx(0.05, abs=1e-15) and r["t"] == pytest.approx(0.05, abs=1e-15)
+    assert g["diag"]["steps"] < 40          # steps after t_end do not move
+
+
+def test_lake_at_rest_gpu():
+    """Still water over emerging dry land stays still on the GPU (FP64 and FP32)."""
+    m = I.thacker_mesh(n=60)
+    s = I.lake_at_rest_state(m, 0.0)
+    for prec, tol in ((64, 1e-12), (32, 1e-5)):
+        g = gpu_run(m, s, 300, precision=prec, h_threshold=1e-5, dt_max=0.01)
+        assert np.abs(g["Hu"]).max() <= tol and np.abs(g["Hv"]).max() <= tol
+        wet = s.H > 0
+        z = -m.vertex_mean(m.depth)
+        assert np.abs((g["H"] + z)[wet] - (s.H + z)[wet]).max() <= tol * 10
+
+
+def test_mass_conserved_gpu(thacker):
+    m, s = thacker
+    area = O.OracleMesh.from_mesh(m).get("area")
+    M0 = float(np.sum(area * s.H))
+    g = gpu_run(m, s, 500, precision=64, h_threshold=1e-5)
+    assert abs(float(np.sum(area * g["H"])) - M0) / M0 < 1e-13
+    assert g["diag"]["mass"] == pytest.approx(M0, rel=1e-13)
+    assert g["diag"]["neg_count"] == 0
+
+
+def test_single_and_two_triangles():
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.0]])
+    for tri in (np.array([[0, 1, 2]]), np.array([[0, 1, 3], [0, 3, 2]])):
+        m = I.Mesh(xy, tri.astype(np.int32), np.array([1.0, 1.2, 0.8, 1.1]))
+        st = I.State(np.full(len(tri), 1.0) + 0.1 * np.arange(len(tri)), np.full(len(tri), 0.3),
+                     np.full(len(tri), -0.2))
+        g = gpu_run(m, st, 10, precision=64, h_threshold=1e-5)
+        r = oracle_run(m, st, 10, h_threshold=1e-5)
+        for f in FIELDS:
+            assert rel_l2(g[f], r[f]) <= TOL64, f
+
+
+def test_all_dry_does_not_move():
+    m = I.thacker_mesh(n=10)
+    z = np.zeros(m.nc)
+    st = I.State(z.copy(), z.copy(), z.copy())
+    g = gpu_run(m, st, 5, precision=64)
+    assert g["t"] == 0.0 and g["diag"]["steps"] == 0
+    assert np.all(g["H"] == 0.0)
+    g = gpu_run(m, st, 5, precision=64, dt_max=0.01)
+    assert g["t"] == pytest.approx(0.05) and g["diag"]["steps"] == 5
+
+
+def test_invalid_inputs_rejected():
+    m = I.thacker_mesh(n=8)
+    s = I.thacker_initial_state(m)
+    with volna.Solver(64) as sv:
+        with pytest.raises(volna.VolnaError) as e:
+            sv.step(1)
+        assert e.value.code == volna.VG_ESTATE
+        bad = m.tri.copy()
+        bad[3, 1] = bad[3, 0]
+        with pytest.raises(volna.VolnaError) as e:
+            volna.vg_mesh_upload(sv.ctx, m.xy, bad, m.depth)
+        assert e.value.code == volna.VG_EINVAL
+        with pytest.raises(volna.VolnaError):
+            volna.vg_mesh_upload(sv.ctx, m.xy, np.zeros((0, 3), np.int32), m.depth)
+        sv.upload_mesh(m)
+        H = s.H.copy()
+        H[5] = -1.0
+        with pytest.raises(volna.VolnaError) as e:
+            sv.set_state(H, s.Hu, s.Hv)
+        assert e.value.code == volna.VG_EINVAL
+        H[5] = np.nan
+        with pytest.raises(volna.VolnaError):
+            sv.set_state(H, s.Hu, s.Hv)
+        with pytest.raises(volna.VolnaError) as e:
+            sv.set_gauges([[10.0, 10.0]])
+        assert e.value.code == volna.VG_EINVAL
+        with pytest.raises(volna.VolnaError):
+            sv.set_params(order=3)
+        with pytest.raises(volna.VolnaError):
+            sv.set_params(block_cells=100)
+        sv.set_state(s.H, s.Hu, s.Hv)
+        sv.step(2)
+
+
+def test_device_state_roundtrip_torch():
+    torch = pytest.importorskip("torch")
+    m = I.thacker_mesh(n=30)
+    s = I.thacker_initial_state(m)
+    stream = torch.cuda.Stream()
+    with volna.Solver(64, stream=stream) as sv:
+        sv.upload_mesh(m)
+        Hd = torch.tensor(s.H, device="cuda")
+        sv.set_state(Hd, torch.tensor(s.Hu, device="cuda"), torch.tensor(s.Hv, device="cuda"))
+        sv.step(3)
+        out = sv.get_state_dev()
+        H, Hu, Hv, _ = sv.get_state()
+    np.testing.assert_array_equal(out[0].cpu().numpy(), H)
+    np.testing.assert_array_equal(out[1].cpu().numpy(), Hu)
+    r = oracle_run(m, s, 3, h_threshold=1e-5)
+    assert rel_l2(H, r["H"]) <= TOL64
+
+
+def test_advance_to_and_graph_replay_consistency(thacker):
+    """Graph-replayed steps equal kernel-by-kernel (profiling) steps bit for bit."""
+    m, s = thacker
+    with volna.Solver(64) as a, volna.Solver(64) as b:
+        for sv in (a, b):
+            sv.upload_mesh(m)
+            sv.set_state(s.H, s.Hu, s.Hv)
+        b.profile(True)
+        a.step(33)
+        b.step(33)
+        for x, y in zip(a.get_state()[:3], b.get_state()[:3]):
+            np.testing.assert_array_equal(x, y)
+        prof = b.get_profile()
+        assert prof["stage1"][0] == 33 and prof["stage2"][0] == 33
+        a.advance_to(0.2)
+        assert a.diagnostics()["t"] == pytest.approx(0.2, abs=1e-15)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", [32, 64])
+def test_full_size_40m_sampled(precision):
+    """The 40M-triangle workload in the benchmark's launch configuration (Morton
+    renumbering, 256-cell blocks): one step on the GPU; 48 sampled cells checked
+    against the oracle run on their 4-ring patches with the GPU's time step, the
+    time step checked against the sampled CFL bounds, and mass conservation."""
+    m = I.thacker_large_mesh()
+    s = I.thacker_initial_state(m)
+    rng = np.random.default_rng(11)
+    p = m.cell_points()
+    r2 = (p[:, 0] ** 2 + p[:, 1] ** 2) / m.meta["alpha"] ** 2
+    wet_pool = np.nonzero(s.H > 0)[0]
+    shore_pool = np.nonzero((r2 > 0.75) & (r2 < 0.85))[0]
+    samples = np.concatenate([rng.choice(wet_pool, 32, replace=False),
+                              rng.choice(shore_pool, 16, replace=False)])
+    with volna.Solver(precision) as sv:
+        sv.upload_mesh(m, renumber="morton")
+        sv.set_params(h_threshold=1e-5, cfl=0.9)
+        sv.set_state(s.H, s.Hu, s.Hv)
+        d0 = sv.diagnostics()
+        sv.step(1)
+        d1 = sv.diagnostics()
+        H, Hu, Hv, t = sv.get_state()
+    dt = d1["last_dt"]
+    assert dt > 0 and t == pytest.approx(dt)
+    assert abs(d1["mass"] - d0["mass"]) / d0["mass"] < (1e-13 if precision == 64 else 1e-5)
+    tol = 1e-12 if precision == 64 else 1e-4
+    adj = VertexAdjacency(m.tri, m.nv)
+    for k in samples:
+        cells = adj.rings([k], 4)
+        pm = patch_mesh(m, cells)
+        centre = int(np.searchsorted(cells, k))
+        om = O.OracleMesh.from_mesh(pm)
+        st = (s.H[cells], s.Hu[cells], s.Hv[cells], 0.0)
+        _, am = om.residual(O.params(h_threshold=1e-5), *st[:3])
+        area = om.get("area")
+        if am[centre] > 0:      # the GPU's dt is the global minimum of these bounds
+            assert dt <= 0.9 * area[centre] / (3.0 * am[centre]) * (1 + (1e-12 if precision == 64 else 1e-5))
+        r = om.run(O.params(h_threshold=1e-5, dt_fixed=dt), st, 1)
+        scale = max(float(np.abs(s.H[cells]).max()), 1e-3)
+        for f, gv in (("H", H), ("Hu", Hu), ("Hv", Hv)):
+            assert abs(gv[k] - r[f][centre]) <= tol * scale, (k, f, gv[k], r[f][centre])
