@@ -23,6 +23,17 @@
 //      forms the residual and updates the cell.
 // No float atomics: the gather order is fixed, and the CFL minimum uses an
 // integer atomicMin on the bits of a non-negative value (exact, order-free).
+//
+// Two arithmetic forms of the same scheme:
+//  * FP64 ("literal"): the state is (H, Hu, Hv) and every formula is evaluated
+//    as written, in the same order as any plain implementation of the scheme.
+//  * FP32 ("deviation"): the state is (eta, Hu, Hv) with eta = H + z, and the
+//    momentum flux through each face is carried relative to each cell's own
+//    hydrostatic pressure g H_K^2 / 2.  Because sum_f l_f n_f = 0 on a closed
+//    triangle this reference drops out of the residual exactly, so the scheme is
+//    unchanged; but the large terms g H^2 / 2 (1e8 in a 4000 m ocean) never
+//    appear, only products of small differences (eta_f - eta_K, z* - z_K), so
+//    still water stays still in FP32 and eta keeps full FP32 resolution.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -174,27 +185,117 @@ __device__ __forceinline__ void face_flux(real g, real half_g, real hthr,
     PR = half_g * (HfR * HfR - HsR * HsR);
 }
 
-// State of cell gid as seen by the stage: stage 1 reads w^n; stage 2 forms
-// w1 = w^n + dt R0 and applies the dry fix (negative depth emptied; at or below
-// the threshold, momentum zeroed).  Returns true if a negative depth was met.
+// Deviation form for FP32, literal form for FP64.
+template <typename real> struct EtaForm { static constexpr bool value = false; };
+template <> struct EtaForm<float> { static constexpr bool value = true; };
+
+// Stored state of cell gid as seen by the stage (H or eta first, then Hu, Hv):
+// stage 1 reads w^n; stage 2 forms w1 = w^n + dt R0 and applies the dry fix
+// (negative depth emptied; at or below the threshold, momentum zeroed).
+// Returns true if a negative depth was met.
 template <typename real, int STAGE>
-__device__ __forceinline__ bool stage_state(const KArgs<real> &a, int64_t gid, real dt, real &H,
+__device__ __forceinline__ bool stage_state(const KArgs<real> &a, int64_t gid, real dt, real zc, real &W,
                                             real &Hu, real &Hv)
 {
+    constexpr bool ETA = EtaForm<real>::value;
     const int64_t nc = a.nc;
-    H = a.w[gid];
+    W = a.w[gid];
     Hu = a.w[nc + gid];
     Hv = a.w[2 * nc + gid];
     if (STAGE == 1) return false;
-    H = H + dt * a.R0[gid];
+    W = W + dt * a.R0[gid];
     Hu = Hu + dt * a.R0[nc + gid];
     Hv = Hv + dt * a.R0[2 * nc + gid];
+    real H = ETA ? W - zc : W;
     if (H < real(0)) {
-        H = real(0); Hu = real(0); Hv = real(0);
+        W = ETA ? zc : real(0);
+        Hu = real(0); Hv = real(0);
         return true;
     }
     if (H <= a.hthr) { Hu = real(0); Hv = real(0); }
     return false;
+}
+
+// Deviation-form flux (FP32).  Inputs per side: face eta_f and momenta, bed z
+// and the cell's own eta.  Same interface depths and HLL as face_flux, with
+//   d* = H*_L - H*_R          (eta_fL - eta_fR when both sides are wet)
+//   F1 - C_e for C_e = g H*_L H*_R / 2:  L: q_L u_nL + g H*_L d* / 2,
+//                                        R: q_R u_nR - g H*_R d* / 2
+// (HLL is affine in F with weights summing to one, so F* shifts by -C_e), and
+// side terms Q_s = C_e + P_s - g H_s^2 / 2 that replace the pressure correction:
+//   Q_L = g/2 [(eta_fL - eta_L)(H_fL + H_L) - H*_L d*],
+//   Q_R = g/2 [(eta_fR - eta_R)(H_fR + H_R) + H*_R d*].
+__device__ __forceinline__ void face_flux_dev(float g, float half_g, float hthr,
+                                              float efL, float HufL, float HvfL, float zL, float eL,
+                                              float efR, float HufR, float HvfR, float zR, float eR,
+                                              float nx, float ny, bool wall,
+                                              float Phi[3], float &QL, float &QR, float &amax)
+{
+    float HfL = efL - zL;
+    float uL = 0.f, vL = 0.f;
+    if (HfL > hthr) { uL = HufL / HfL; vL = HvfL / HfL; }
+    float unL = uL * nx + vL * ny;
+    float utL = -uL * ny + vL * nx;
+    float HsL, HsR, unR, utR, ds, HfR;
+    if (wall) {
+        HsL = fmaxf(0.f, HfL);
+        HsR = HsL;
+        unR = -unL;
+        utR = utL;
+        ds = 0.f;
+        HfR = HfL; efR = efL; eR = eL; zR = zL;
+    } else {
+        HfR = efR - zR;
+        float uR = 0.f, vR = 0.f;
+        if (HfR > hthr) { uR = HufR / HfR; vR = HvfR / HfR; }
+        unR = uR * nx + vR * ny;
+        utR = -uR * ny + vR * nx;
+        float zs = fmaxf(zL, zR);
+        HsL = fmaxf(0.f, efL - zs);
+        HsR = fmaxf(0.f, efR - zs);
+        ds = (HsL > 0.f && HsR > 0.f) ? efL - efR : HsL - HsR;
+    }
+    float F[3];
+    if (HsL == 0.f && HsR == 0.f) {
+        F[0] = 0.f; F[1] = 0.f; F[2] = 0.f;
+        amax = 0.f;
+    } else {
+        float cL = sqrtf(g * HsL), cR = sqrtf(g * HsR);
+        float sL, sR;
+        if (HsL == 0.f) {
+            sL = unR - 2.f * cR;
+            sR = unR + cR;
+        } else if (HsR == 0.f) {
+            sL = unL - cL;
+            sR = unL + 2.f * cL;
+        } else {
+            float us = 0.5f * (unL + unR) + (cL - cR);
+            float cs = 0.5f * (cL + cR) - 0.25f * (unR - unL);
+            sL = fminf(unL - cL, us - cs);
+            sR = fmaxf(us + cs, unR + cR);
+        }
+        float qL = HsL * unL, qR = HsR * unR;
+        float FL0 = qL, FL1 = qL * unL + half_g * HsL * ds, FL2 = qL * utL;
+        float FR0 = qR, FR1 = qR * unR - half_g * HsR * ds, FR2 = qR * utR;
+        if (sL >= 0.f) {
+            F[0] = FL0; F[1] = FL1; F[2] = FL2;
+        } else if (sR >= 0.f) {
+            float rden = 1.f / (sR - sL);
+            float sLR = sL * sR;
+            F[0] = ((sR * FL0 - sL * FR0) - sLR * ds) * rden;
+            F[1] = ((sR * FL1 - sL * FR1) + sLR * (qR - qL)) * rden;
+            F[2] = ((sR * FL2 - sL * FR2) + sLR * (HsR * utR - HsL * utL)) * rden;
+        } else {
+            F[0] = FR0; F[1] = FR1; F[2] = FR2;
+        }
+        amax = fmaxf(fabsf(sL), fabsf(sR));
+    }
+    Phi[0] = F[0];
+    Phi[1] = F[1] * nx - F[2] * ny;
+    Phi[2] = F[1] * ny + F[2] * nx;
+    float HL = eL - zL, HR = eR - zR;
+    QL = half_g * ((efL - eL) * (HfL + HL) - HsL * ds);
+    QR = half_g * ((efR - eR) * (HfR + HR) + HsR * ds);
 }
 
 template <typename real>
@@ -230,6 +331,7 @@ __global__ void __launch_bounds__(256) stage_kernel(const KArgs<real> a)
     real *oA = oPR + 3 * B;
     uint16_t *queue = reinterpret_cast<uint16_t *>(oA + 3 * B);
 
+    constexpr bool ETA = EtaForm<real>::value;
     const int tid = threadIdx.x;
     const real g = a.g, half_g = a.half_g, hthr = a.hthr;
     const real *geo = a.geo;
@@ -251,11 +353,12 @@ __global__ void __launch_bounds__(256) stage_kernel(const KArgs<real> a)
         for (int l = tid; l < B + nh; l += blockDim.x) {
             if (l < B && l >= ncell) continue;
             int64_t gid = l < B ? c0 + l : (int64_t)a.halo_ids[h0 + (l - B)];
-            real H, Hu, Hv;
-            bool neg = stage_state<real, STAGE>(a, gid, dt, H, Hu, Hv);
+            real W, Hu, Hv;
+            real zc = a.z[gid];
+            bool neg = stage_state<real, STAGE>(a, gid, dt, zc, W, Hu, Hv);
             if (neg && l < B) my_neg++;
-            sH[l] = H; sHu[l] = Hu; sHv[l] = Hv;
-            sz[l] = a.z[gid];
+            sH[l] = W; sHu[l] = Hu; sHv[l] = Hv;
+            sz[l] = zc;
         }
         if (tid == 0) qcount = 0;
         __syncthreads();
@@ -264,30 +367,32 @@ __global__ void __launch_bounds__(256) stage_kernel(const KArgs<real> a)
         for (int l = tid; l < B + nh; l += blockDim.x) {
             if (l < B && l >= ncell) continue;
             int64_t gid = l < B ? c0 + l : (int64_t)a.halo_ids[h0 + (l - B)];
-            const real HK = sH[l], HuK = sHu[l], HvK = sHv[l], zK = sz[l];
-            real qK[3] = {HK + zK, HuK, HvK};
+            const real HuK = sHu[l], HvK = sHv[l], zK = sz[l];
+            const real HK = ETA ? sH[l] - zK : sH[l];
+            real qK[3] = {ETA ? sH[l] : HK + zK, HuK, HvK};
             real qn[3][3];
             bool recon = (a.order == 2) && (HK > hthr);
             for (int f = 0; f < 3; f++) {
                 bool wall;
-                real Hj = real(0), Huj = real(0), Hvj = real(0), zj = real(0);
+                real Wj = real(0), Huj = real(0), Hvj = real(0), zj = real(0);
                 if (l < B) {
                     uint16_t code = a.nbrl[f * nc + gid];
                     wall = code == NBR_WALL;
                     if (!wall) {
                         int nl = code >> 2;
-                        Hj = sH[nl]; Huj = sHu[nl]; Hvj = sHv[nl]; zj = sz[nl];
+                        Wj = sH[nl]; Huj = sHu[nl]; Hvj = sHv[nl]; zj = sz[nl];
                     }
                 } else {
                     int32_t j = a.nbr[f * nc + gid];
                     wall = j < 0;
                     if (!wall) {
-                        if (stage_state<real, STAGE>(a, j, dt, Hj, Huj, Hvj)) { /* counted by its owner */ }
                         zj = a.z[j];
+                        stage_state<real, STAGE>(a, j, dt, zj, Wj, Huj, Hvj);  // negatives counted by the owner
                     }
                 }
                 if (!wall) {
-                    qn[f][0] = Hj + zj;
+                    const real Hj = ETA ? Wj - zj : Wj;
+                    qn[f][0] = ETA ? Wj : Hj + zj;
                     qn[f][1] = Huj;
                     qn[f][2] = Hvj;
                     if (!(Hj > hthr)) recon = false;
@@ -337,13 +442,14 @@ __global__ void __launch_bounds__(256) stage_kernel(const KArgs<real> a)
                 for (int f = 0; f < 3; f++) {
                     Hf[f] = face[f][0] - zK;
                     if (!(Hf[f] > hthr)) recon = false;
+                    if (ETA) Hf[f] = face[f][0];      // FP32 keeps eta_f
                     Huf[f] = face[f][1];
                     Hvf[f] = face[f][2];
                 }
             }
             if (!recon) {
 #pragma unroll
-                for (int f = 0; f < 3; f++) { Hf[f] = HK; Huf[f] = HuK; Hvf[f] = HvK; }
+                for (int f = 0; f < 3; f++) { Hf[f] = ETA ? sH[l] : HK; Huf[f] = HuK; Hvf[f] = HvK; }
             }
 #pragma unroll
             for (int f = 0; f < 3; f++) {
@@ -384,9 +490,16 @@ __global__ void __launch_bounds__(256) stage_kernel(const KArgs<real> a)
                 zR = sz[nl];
             }
             real Phi[3], PL, PR, am;
-            face_flux<real>(g, half_g, hthr, fH[f * L + l], fHu[f * L + l], fHv[f * L + l], sz[l],
-                            HfR, HufR, HvfR, zR, geo[(GEO_NX + f) * nc + gid],
-                            geo[(GEO_NY + f) * nc + gid], wall, Phi, PL, PR, am);
+            if constexpr (ETA) {
+                float eR = wall ? 0.f : sH[code >> 2];
+                face_flux_dev(g, half_g, hthr, fH[f * L + l], fHu[f * L + l], fHv[f * L + l], sz[l], sH[l],
+                              HfR, HufR, HvfR, zR, eR, geo[(GEO_NX + f) * nc + gid],
+                              geo[(GEO_NY + f) * nc + gid], wall, Phi, PL, PR, am);
+            } else {
+                face_flux<real>(g, half_g, hthr, fH[f * L + l], fHu[f * L + l], fHv[f * L + l], sz[l],
+                                HfR, HufR, HvfR, zR, geo[(GEO_NX + f) * nc + gid],
+                                geo[(GEO_NY + f) * nc + gid], wall, Phi, PL, PR, am);
+            }
             int s = f * B + l;
             oP0[s] = Phi[0]; oP1[s] = Phi[1]; oP2[s] = Phi[2];
             oPL[s] = PL; oPR[s] = PR; oA[s] = am;
@@ -426,17 +539,19 @@ __global__ void __launch_bounds__(256) stage_kernel(const KArgs<real> a)
                 if (am > real(0)) my_min = vmin(my_min, area / (real(3) * am));
             } else {
                 real H0 = a.w[gid], Hu0 = a.w[nc + gid], Hv0 = a.w[2 * nc + gid];
-                real H = real(0.5) * H0 + real(0.5) * (sH[l] + dt * RH);
+                real W = real(0.5) * H0 + real(0.5) * (sH[l] + dt * RH);
                 real Hu = real(0.5) * Hu0 + real(0.5) * (sHu[l] + dt * RHu);
                 real Hv = real(0.5) * Hv0 + real(0.5) * (sHv[l] + dt * RHv);
+                real H = ETA ? W - sz[l] : W;
                 if (H < real(0)) {
                     my_neg++;
-                    H = real(0); Hu = real(0); Hv = real(0);
+                    W = ETA ? sz[l] : real(0);
+                    Hu = real(0); Hv = real(0);
                 } else if (H <= hthr) {
                     Hu = real(0); Hv = real(0);
                 }
-                if (!isfinite(H) || !isfinite(Hu) || !isfinite(Hv)) bad = true;
-                a.wout[gid] = H;
+                if (!isfinite(W) || !isfinite(Hu) || !isfinite(Hv)) bad = true;
+                a.wout[gid] = W;
                 a.wout[nc + gid] = Hu;
                 a.wout[2 * nc + gid] = Hv;
             }

@@ -44,7 +44,7 @@ __global__ void post_step_kernel(DevPtrs d, StepParams p, const real *w)
         const real *z = static_cast<const real *>(d.z);
         for (int g = threadIdx.x; g < d.n_gauges; g += blockDim.x) {
             int32_t c = d.gauge_cells[g];
-            d.ring_eta[rec * d.n_gauges + g] = (double)(w[c] + z[c]);
+            d.ring_eta[rec * d.n_gauges + g] = EtaForm<real>::value ? (double)w[c] : (double)(w[c] + z[c]);
         }
     }
 }
@@ -61,7 +61,7 @@ __global__ void record_gauges_kernel(DevPtrs d, const real *w)
     const real *z = static_cast<const real *>(d.z);
     for (int g = threadIdx.x; g < d.n_gauges; g += blockDim.x) {
         int32_t c = d.gauge_cells[g];
-        d.ring_eta[rec * d.n_gauges + g] = (double)(w[c] + z[c]);
+        d.ring_eta[rec * d.n_gauges + g] = EtaForm<real>::value ? (double)w[c] : (double)(w[c] + z[c]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -70,16 +70,18 @@ __global__ void record_gauges_kernel(DevPtrs d, const real *w)
     }
 }
 
+// State in (original order, H) -> internal order, stored form (H, or eta = H + z
+// formed in FP64 before rounding to FP32).
 template <typename real, typename src_t>
 __global__ void import_state_kernel(int64_t nc, const int32_t *old_of_new, const src_t *H,
-                                    const src_t *Hu, const src_t *Hv, real *w, DevScalars *sc)
+                                    const src_t *Hu, const src_t *Hv, const real *z, real *w, DevScalars *sc)
 {
     bool bad = false;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nc; k += (int64_t)gridDim.x * blockDim.x) {
         int64_t o = old_of_new[k];
         src_t h = H[o], hu = Hu[o], hv = Hv[o];
         if (!(h >= src_t(0)) || !isfinite(h) || !isfinite(hu) || !isfinite(hv)) bad = true;
-        w[k] = (real)h;
+        w[k] = EtaForm<real>::value ? (real)((double)h + (double)z[k]) : (real)h;
         w[nc + k] = (real)hu;
         w[2 * nc + k] = (real)hv;
     }
@@ -87,12 +89,13 @@ __global__ void import_state_kernel(int64_t nc, const int32_t *old_of_new, const
 }
 
 template <typename real, typename dst_t>
-__global__ void export_state_kernel(int64_t nc, const int32_t *old_of_new, const real *w, dst_t *H,
-                                    dst_t *Hu, dst_t *Hv)
+__global__ void export_state_kernel(int64_t nc, const int32_t *old_of_new, const real *w, const real *z,
+                                    dst_t *H, dst_t *Hu, dst_t *Hv)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nc; k += (int64_t)gridDim.x * blockDim.x) {
         int64_t o = old_of_new[k];
-        H[o] = (dst_t)w[k];
+        double h = EtaForm<real>::value ? (double)w[k] - (double)z[k] : (double)w[k];
+        H[o] = (dst_t)h;
         Hu[o] = (dst_t)w[nc + k];
         Hv[o] = (dst_t)w[2 * nc + k];
     }
@@ -102,12 +105,13 @@ constexpr int DIAG_BLOCKS = 1024;
 
 // Fixed grid, fixed reduction tree: the sums do not depend on timing.
 template <typename real>
-__global__ void diag_partial_kernel(int64_t nc, const real *w, const real *geo, double hthr, double *part)
+__global__ void diag_partial_kernel(int64_t nc, const real *w, const real *z, const real *geo, double hthr,
+                                    double *part)
 {
     __shared__ double s_mass[256], s_min[256], s_dry[256];
     double mass = 0.0, mn = CUDART_INF, dry = 0.0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nc; k += (int64_t)gridDim.x * blockDim.x) {
-        double h = (double)w[k];
+        double h = EtaForm<real>::value ? (double)w[k] - (double)z[k] : (double)w[k];
         mass += (double)geo[GEO_AREA * nc + k] * h;
         mn = fmin(mn, h);
         dry += h <= hthr ? 1.0 : 0.0;
@@ -168,15 +172,17 @@ int launch_import_state(const DevPtrs &d, const int32_t *old_of_new, const void 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int grid = grid_for(d.nc);
     if (precision == 64) {
+        const double *z = (const double *)d.z;
         if (src_is_double)
-            import_state_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)H, (const double *)Hu, (const double *)Hv, (double *)w, d.sc);
+            import_state_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)H, (const double *)Hu, (const double *)Hv, z, (double *)w, d.sc);
         else
-            import_state_kernel<double, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)H, (const float *)Hu, (const float *)Hv, (double *)w, d.sc);
+            import_state_kernel<double, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)H, (const float *)Hu, (const float *)Hv, z, (double *)w, d.sc);
     } else {
+        const float *z = (const float *)d.z;
         if (src_is_double)
-            import_state_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)H, (const double *)Hu, (const double *)Hv, (float *)w, d.sc);
+            import_state_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)H, (const double *)Hu, (const double *)Hv, z, (float *)w, d.sc);
         else
-            import_state_kernel<float, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)H, (const float *)Hu, (const float *)Hv, (float *)w, d.sc);
+            import_state_kernel<float, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)H, (const float *)Hu, (const float *)Hv, z, (float *)w, d.sc);
     }
     return (int)cudaGetLastError();
 }
@@ -187,15 +193,17 @@ int launch_export_state(const DevPtrs &d, const int32_t *old_of_new, const void 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int grid = grid_for(d.nc);
     if (precision == 64) {
+        const double *z = (const double *)d.z;
         if (dst_is_double)
-            export_state_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)w, (double *)H, (double *)Hu, (double *)Hv);
+            export_state_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)w, z, (double *)H, (double *)Hu, (double *)Hv);
         else
-            export_state_kernel<double, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)w, (float *)H, (float *)Hu, (float *)Hv);
+            export_state_kernel<double, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)w, z, (float *)H, (float *)Hu, (float *)Hv);
     } else {
+        const float *z = (const float *)d.z;
         if (dst_is_double)
-            export_state_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)w, (double *)H, (double *)Hu, (double *)Hv);
+            export_state_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)w, z, (double *)H, (double *)Hu, (double *)Hv);
         else
-            export_state_kernel<float, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)w, (float *)H, (float *)Hu, (float *)Hv);
+            export_state_kernel<float, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)w, z, (float *)H, (float *)Hu, (float *)Hv);
     }
     return (int)cudaGetLastError();
 }
@@ -205,9 +213,9 @@ int launch_diagnostics(const DevPtrs &d, const void *w, int precision, double ht
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (precision == 64)
-        diag_partial_kernel<double><<<DIAG_BLOCKS, 256, 0, s>>>(d.nc, (const double *)w, (const double *)d.geo, hthr, part);
+        diag_partial_kernel<double><<<DIAG_BLOCKS, 256, 0, s>>>(d.nc, (const double *)w, (const double *)d.z, (const double *)d.geo, hthr, part);
     else
-        diag_partial_kernel<float><<<DIAG_BLOCKS, 256, 0, s>>>(d.nc, (const float *)w, (const float *)d.geo, hthr, part);
+        diag_partial_kernel<float><<<DIAG_BLOCKS, 256, 0, s>>>(d.nc, (const float *)w, (const float *)d.z, (const float *)d.geo, hthr, part);
     diag_final_kernel<<<1, 32, 0, s>>>(part, DIAG_BLOCKS, out);
     return (int)cudaGetLastError();
 }
