@@ -54,6 +54,7 @@ ALGO_BYTES = {32: {"stage1": 64, "stage2": 76}, 64: {"stage1": 104, "stage2": 12
 WORKLOADS = {
     "thacker_paraboloid_40m": dict(n=4472),
     "thacker_paraboloid_10m": dict(n=2236),
+    "thacker_paraboloid_4m": dict(n=1414),
     "thacker_paraboloid_1m": dict(n=707),
 }
 

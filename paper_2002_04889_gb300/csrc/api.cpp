@@ -37,6 +37,7 @@ struct vg_ctx {
 
     // device memory
     void *geo = nullptr, *z = nullptr, *w[2] = {nullptr, nullptr}, *R0 = nullptr;
+    double *z64 = nullptr;
     int32_t *nbr = nullptr, *halo_ptr = nullptr, *halo_ids = nullptr, *old_of_new = nullptr;
     uint16_t *nbrl = nullptr;
     DevScalars *sc = nullptr;
@@ -112,7 +113,8 @@ void dfree(T *&p)
 void free_mesh(vg_ctx *c)
 {
     if (c->graph2) { cudaGraphExecDestroy(c->graph2); c->graph2 = nullptr; }
-    dfree(c->geo); dfree(c->z); dfree(c->w[0]); dfree(c->w[1]); dfree(c->R0);
+    if (c->z64 == c->z) c->z64 = nullptr;
+    dfree(c->geo); dfree(c->z); dfree(c->z64); dfree(c->w[0]); dfree(c->w[1]); dfree(c->R0);
     dfree(c->nbr); dfree(c->halo_ptr); dfree(c->halo_ids); dfree(c->old_of_new); dfree(c->nbrl);
     dfree(c->gauge_cells); dfree(c->ring_t); dfree(c->ring_eta); dfree(c->staging);
     c->dev_bytes = 0;
@@ -137,6 +139,7 @@ DevPtrs dev_ptrs(const vg_ctx *c)
     d.ring_cap = kRingCap;
     d.geo = c->geo;
     d.z = c->z;
+    d.z64 = c->z64;
     d.nbr = c->nbr;
     d.nbrl = c->nbrl;
     d.halo_ptr = c->halo_ptr;
@@ -194,6 +197,12 @@ int upload_mesh_arrays(vg_ctx *c)
     if ((rc = dmalloc(c, (void **)&c->ring_t, 8 * kRingCap))) return rc;
     if ((rc = upload_real(c, c->geo, m.geo.data(), m.geo.size()))) return rc;
     if ((rc = upload_real(c, c->z, m.z.data(), m.z.size()))) return rc;
+    if (c->precision == 64) {
+        c->z64 = static_cast<double *>(c->z);
+    } else {
+        if ((rc = dmalloc(c, (void **)&c->z64, 8 * m.nc))) return rc;
+        VG_CUDA(c, cudaMemcpy(c->z64, m.z.data(), 8 * m.nc, cudaMemcpyHostToDevice));
+    }
     VG_CUDA(c, cudaMemcpy(c->nbr, m.nbr.data(), 4 * 3 * m.nc, cudaMemcpyHostToDevice));
     VG_CUDA(c, cudaMemcpy(c->nbrl, m.nbrl.data(), 2 * 3 * m.nc, cudaMemcpyHostToDevice));
     VG_CUDA(c, cudaMemcpy(c->halo_ptr, m.halo_ptr.data(), 4 * (m.nblocks + 1), cudaMemcpyHostToDevice));

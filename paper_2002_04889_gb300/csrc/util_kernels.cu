@@ -71,10 +71,11 @@ __global__ void record_gauges_kernel(DevPtrs d, const real *w)
 }
 
 // State in (original order, H) -> internal order, stored form (H, or eta = H + z
-// formed in FP64 before rounding to FP32).
+// formed with the FP64 bed before rounding to FP32, so still water at a common
+// level gets exactly the same eta everywhere).
 template <typename real, typename src_t>
 __global__ void import_state_kernel(int64_t nc, const int32_t *old_of_new, const src_t *H,
-                                    const src_t *Hu, const src_t *Hv, const real *z, real *w, DevScalars *sc)
+                                    const src_t *Hu, const src_t *Hv, const double *z, real *w, DevScalars *sc)
 {
     bool bad = false;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nc; k += (int64_t)gridDim.x * blockDim.x) {
@@ -89,7 +90,7 @@ __global__ void import_state_kernel(int64_t nc, const int32_t *old_of_new, const
 }
 
 template <typename real, typename dst_t>
-__global__ void export_state_kernel(int64_t nc, const int32_t *old_of_new, const real *w, const real *z,
+__global__ void export_state_kernel(int64_t nc, const int32_t *old_of_new, const real *w, const double *z,
                                     dst_t *H, dst_t *Hu, dst_t *Hv)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nc; k += (int64_t)gridDim.x * blockDim.x) {
@@ -105,7 +106,7 @@ constexpr int DIAG_BLOCKS = 1024;
 
 // Fixed grid, fixed reduction tree: the sums do not depend on timing.
 template <typename real>
-__global__ void diag_partial_kernel(int64_t nc, const real *w, const real *z, const real *geo, double hthr,
+__global__ void diag_partial_kernel(int64_t nc, const real *w, const double *z, const real *geo, double hthr,
                                     double *part)
 {
     __shared__ double s_mass[256], s_min[256], s_dry[256];
@@ -172,13 +173,13 @@ int launch_import_state(const DevPtrs &d, const int32_t *old_of_new, const void 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int grid = grid_for(d.nc);
     if (precision == 64) {
-        const double *z = (const double *)d.z;
+        const double *z = d.z64;
         if (src_is_double)
             import_state_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)H, (const double *)Hu, (const double *)Hv, z, (double *)w, d.sc);
         else
             import_state_kernel<double, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)H, (const float *)Hu, (const float *)Hv, z, (double *)w, d.sc);
     } else {
-        const float *z = (const float *)d.z;
+        const double *z = d.z64;
         if (src_is_double)
             import_state_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)H, (const double *)Hu, (const double *)Hv, z, (float *)w, d.sc);
         else
@@ -193,13 +194,13 @@ int launch_export_state(const DevPtrs &d, const int32_t *old_of_new, const void 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int grid = grid_for(d.nc);
     if (precision == 64) {
-        const double *z = (const double *)d.z;
+        const double *z = d.z64;
         if (dst_is_double)
             export_state_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)w, z, (double *)H, (double *)Hu, (double *)Hv);
         else
             export_state_kernel<double, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)w, z, (float *)H, (float *)Hu, (float *)Hv);
     } else {
-        const float *z = (const float *)d.z;
+        const double *z = d.z64;
         if (dst_is_double)
             export_state_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)w, z, (double *)H, (double *)Hu, (double *)Hv);
         else
@@ -213,9 +214,9 @@ int launch_diagnostics(const DevPtrs &d, const void *w, int precision, double ht
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (precision == 64)
-        diag_partial_kernel<double><<<DIAG_BLOCKS, 256, 0, s>>>(d.nc, (const double *)w, (const double *)d.z, (const double *)d.geo, hthr, part);
+        diag_partial_kernel<double><<<DIAG_BLOCKS, 256, 0, s>>>(d.nc, (const double *)w, d.z64, (const double *)d.geo, hthr, part);
     else
-        diag_partial_kernel<float><<<DIAG_BLOCKS, 256, 0, s>>>(d.nc, (const float *)w, (const float *)d.z, (const float *)d.geo, hthr, part);
+        diag_partial_kernel<float><<<DIAG_BLOCKS, 256, 0, s>>>(d.nc, (const float *)w, d.z64, (const float *)d.geo, hthr, part);
     diag_final_kernel<<<1, 32, 0, s>>>(part, DIAG_BLOCKS, out);
     return (int)cudaGetLastError();
 }

@@ -85,6 +85,7 @@ struct DevPtrs {
     int32_t block, nblocks, max_halo, n_gauges, ring_cap;
     const void *geo;        // [GEO_ROWS][nc]
     const void *z;          // [nc]
+    const double *z64;      // [nc] FP64 bed (state import/export and diagnostics)
     const int32_t *nbr;     // [3][nc]
     const uint16_t *nbrl;   // [3][nc]
     const int32_t *halo_ptr;
