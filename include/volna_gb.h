@@ -65,7 +65,9 @@ typedef struct vg_params {
                               produced a negative depth (otherwise it is emptied
                               and counted): 0                                      */
     int32_t block_cells;   /* cells per thread block of the step kernels
-                              (64..1024, multiple of 32; 0 = library default)      */
+                              (32..256, multiple of 32; 0 = library default 256;
+                              halved automatically while the block and its
+                              two-ring halo exceed shared memory)                 */
 } vg_params;
 
 /* Run diagnostics (vg_get_diagnostics). */
@@ -194,6 +196,55 @@ int vg_get_profile(vg_ctx *ctx, int32_t n, const char **names, int64_t *launches
 
 /* Bytes of device memory the context holds. */
 int vg_device_bytes(vg_ctx *ctx, int64_t *bytes);
+
+
+/* ------------------------------------------------------------------------
+ * Batched ensembles (uncertainty quantification): many scenarios -- initial
+ * states of the same scheme -- on several meshes of uneven size, advanced
+ * together.  Each scenario has its own time and its own CFL time step; one
+ * batched step is one persistent launch per stage over every (mesh, block)
+ * work item for all scenarios, replayed from a CUDA graph.  Results equal
+ * those of one context per scenario bit for bit (same kernels, same order).
+ * ------------------------------------------------------------------------ */
+typedef struct vg_batch vg_batch;
+
+/* precision 32 or 64, CUDA device, cudaStream_t or NULL (as vg_create). */
+int vg_batch_create(vg_batch **out, int precision, int device, void *cuda_stream);
+void vg_batch_destroy(vg_batch *b);
+const char *vg_batch_last_error(vg_batch *b);
+
+/* Parameters shared by all scenarios (vg_params; gauges are not recorded). */
+int vg_batch_set_params(vg_batch *b, const vg_params *p);
+
+/* Add a mesh (arguments as vg_mesh_upload) carrying n_scenarios scenarios;
+   *mesh_id receives its index.  At most 512 scenarios per batch.  All meshes
+   must end up with the same block size. */
+int vg_batch_add_mesh(vg_batch *b, int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
+                      const double *depth_v, int renumber, int32_t n_scenarios, int32_t *mesh_id);
+
+/* State of one scenario from host FP64 arrays in the mesh's original cell order
+   (as vg_set_state), at time t. */
+int vg_batch_set_state(vg_batch *b, int32_t mesh_id, int32_t scenario, const double *H, const double *Hu,
+                       const double *Hv, double t);
+
+/* State, time and step count of one scenario (t, steps may be NULL). */
+int vg_batch_get_state(vg_batch *b, int32_t mesh_id, int32_t scenario, double *H, double *Hu, double *Hv,
+                       double *t, int64_t *steps);
+
+/* n_steps batched steps of every scenario (each with its own dt). */
+int vg_batch_step(vg_batch *b, int64_t n_steps);
+
+/* Step until every scenario reaches t_end (each stops exactly there), or
+   max_steps; *steps_taken receives the batched steps run. */
+int vg_batch_run(vg_batch *b, double t_end, int64_t max_steps, int64_t *steps_taken);
+
+/* Autotuner: times n_steps batched steps for each candidate block size (64,
+   128, 256 cells per thread block) from the current state, restores the state,
+   and keeps the fastest; *best_block and *best_ms_per_step report it. */
+int vg_batch_autotune(vg_batch *b, int32_t n_steps, int32_t *best_block, double *best_ms_per_step);
+
+/* Meshes, scenarios, total cells over all scenarios, kernels launched. */
+int vg_batch_info(vg_batch *b, int32_t *n_meshes, int32_t *n_scenarios, int64_t *cells, int64_t *launches);
 
 #ifdef __cplusplus
 }

@@ -63,6 +63,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
                  "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", INC, "-o", obj, os.path.join(SRC, f)]
         if f.endswith("_f64.cu"):
             flags.insert(2, "--fmad=false")
+        if f.endswith("_f32.cu"):
+            flags[2:2] = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
         jobs.append(flags)
         objs.append(obj)
     for f in cpp:

@@ -38,8 +38,8 @@ struct vg_ctx {
     // device memory
     void *geo = nullptr, *z = nullptr, *w[2] = {nullptr, nullptr}, *R0 = nullptr;
     double *z64 = nullptr;
-    int32_t *nbr = nullptr, *halo_ptr = nullptr, *halo_ids = nullptr, *old_of_new = nullptr;
-    uint16_t *nbrl = nullptr;
+    int32_t *nbr = nullptr, *halo_ptr = nullptr, *halo_n1 = nullptr, *halo_ids = nullptr, *old_of_new = nullptr;
+    uint16_t *nbrl = nullptr, *ring1_nbr = nullptr;
     DevScalars *sc = nullptr;
     int32_t *gauge_cells = nullptr;
     double *ring_t = nullptr, *ring_eta = nullptr;
@@ -115,7 +115,8 @@ void free_mesh(vg_ctx *c)
     if (c->graph2) { cudaGraphExecDestroy(c->graph2); c->graph2 = nullptr; }
     if (c->z64 == c->z) c->z64 = nullptr;
     dfree(c->geo); dfree(c->z); dfree(c->z64); dfree(c->w[0]); dfree(c->w[1]); dfree(c->R0);
-    dfree(c->nbr); dfree(c->halo_ptr); dfree(c->halo_ids); dfree(c->old_of_new); dfree(c->nbrl);
+    dfree(c->nbr); dfree(c->halo_ptr); dfree(c->halo_n1); dfree(c->halo_ids); dfree(c->ring1_nbr);
+    dfree(c->old_of_new); dfree(c->nbrl);
     dfree(c->gauge_cells); dfree(c->ring_t); dfree(c->ring_eta); dfree(c->staging);
     c->dev_bytes = 0;
     c->has_mesh = c->has_state = false;
@@ -143,7 +144,9 @@ DevPtrs dev_ptrs(const vg_ctx *c)
     d.nbr = c->nbr;
     d.nbrl = c->nbrl;
     d.halo_ptr = c->halo_ptr;
+    d.halo_n1 = c->halo_n1;
     d.halo_ids = c->halo_ids;
+    d.ring1_nbr = c->ring1_nbr;
     d.R0 = c->R0;
     d.sc = c->sc;
     d.gauge_cells = c->gauge_cells;
@@ -179,6 +182,28 @@ int upload_real(vg_ctx *c, void *dst, const double *src, size_t n)
     return VG_OK;
 }
 
+// Block partition arrays (re-uploaded when block_cells changes).
+int upload_partition(vg_ctx *c)
+{
+    const HostMesh &m = c->hm;
+    dfree(c->halo_ptr); dfree(c->halo_n1); dfree(c->halo_ids); dfree(c->ring1_nbr); dfree(c->nbrl);
+    int rc;
+    size_t nh = std::max<size_t>(1, m.halo_ids.size());
+    if ((rc = dmalloc(c, (void **)&c->nbrl, 2 * 3 * m.nc))) return rc;
+    if ((rc = dmalloc(c, (void **)&c->halo_ptr, 4 * (m.nblocks + 1)))) return rc;
+    if ((rc = dmalloc(c, (void **)&c->halo_n1, 4 * m.nblocks))) return rc;
+    if ((rc = dmalloc(c, (void **)&c->halo_ids, 4 * nh))) return rc;
+    if ((rc = dmalloc(c, (void **)&c->ring1_nbr, 2 * 3 * nh))) return rc;
+    VG_CUDA(c, cudaMemcpy(c->nbrl, m.nbrl.data(), 2 * 3 * m.nc, cudaMemcpyHostToDevice));
+    VG_CUDA(c, cudaMemcpy(c->halo_ptr, m.halo_ptr.data(), 4 * (m.nblocks + 1), cudaMemcpyHostToDevice));
+    VG_CUDA(c, cudaMemcpy(c->halo_n1, m.halo_n1.data(), 4 * m.nblocks, cudaMemcpyHostToDevice));
+    if (!m.halo_ids.empty()) {
+        VG_CUDA(c, cudaMemcpy(c->halo_ids, m.halo_ids.data(), 4 * m.halo_ids.size(), cudaMemcpyHostToDevice));
+        VG_CUDA(c, cudaMemcpy(c->ring1_nbr, m.ring1_nbr.data(), 2 * m.ring1_nbr.size(), cudaMemcpyHostToDevice));
+    }
+    return VG_OK;
+}
+
 int upload_mesh_arrays(vg_ctx *c)
 {
     const HostMesh &m = c->hm;
@@ -190,9 +215,6 @@ int upload_mesh_arrays(vg_ctx *c)
     if ((rc = dmalloc(c, &c->w[1], rs * 3 * m.nc))) return rc;
     if ((rc = dmalloc(c, &c->R0, rs * 3 * m.nc))) return rc;
     if ((rc = dmalloc(c, (void **)&c->nbr, 4 * 3 * m.nc))) return rc;
-    if ((rc = dmalloc(c, (void **)&c->nbrl, 2 * 3 * m.nc))) return rc;
-    if ((rc = dmalloc(c, (void **)&c->halo_ptr, 4 * (m.nblocks + 1)))) return rc;
-    if ((rc = dmalloc(c, (void **)&c->halo_ids, 4 * std::max<size_t>(1, m.halo_ids.size())))) return rc;
     if ((rc = dmalloc(c, (void **)&c->old_of_new, 4 * m.nc))) return rc;
     if ((rc = dmalloc(c, (void **)&c->ring_t, 8 * kRingCap))) return rc;
     if ((rc = upload_real(c, c->geo, m.geo.data(), m.geo.size()))) return rc;
@@ -204,11 +226,28 @@ int upload_mesh_arrays(vg_ctx *c)
         VG_CUDA(c, cudaMemcpy(c->z64, m.z.data(), 8 * m.nc, cudaMemcpyHostToDevice));
     }
     VG_CUDA(c, cudaMemcpy(c->nbr, m.nbr.data(), 4 * 3 * m.nc, cudaMemcpyHostToDevice));
-    VG_CUDA(c, cudaMemcpy(c->nbrl, m.nbrl.data(), 2 * 3 * m.nc, cudaMemcpyHostToDevice));
-    VG_CUDA(c, cudaMemcpy(c->halo_ptr, m.halo_ptr.data(), 4 * (m.nblocks + 1), cudaMemcpyHostToDevice));
-    if (!m.halo_ids.empty())
-        VG_CUDA(c, cudaMemcpy(c->halo_ids, m.halo_ids.data(), 4 * m.halo_ids.size(), cudaMemcpyHostToDevice));
     VG_CUDA(c, cudaMemcpy(c->old_of_new, m.old_of_new.data(), 4 * m.nc, cudaMemcpyHostToDevice));
+    return upload_partition(c);
+}
+
+size_t stage_smem(const vg_ctx *c, int block, int max_halo)
+{
+    return c->precision == 64 ? stage_smem_f64(block, max_halo) : stage_smem_f32(block, max_halo);
+}
+
+// Halve the block size until the stage kernels' shared memory (block + two-ring
+// halo) fits the device; scattered meshes without renumbering have halos of
+// about nine times the block.
+int fit_blocks(vg_ctx *c)
+{
+    int limit = 0;
+    VG_CUDA(c, cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    while (stage_smem(c, c->hm.block, c->hm.max_halo) > (size_t)limit) {
+        if (c->hm.block <= 32)
+            return fail(c, VG_EINVAL, "mesh blocks need more shared memory than the device has; renumber the mesh");
+        int rc = partition_blocks(c->hm, c->hm.block / 2, c->err);
+        if (rc) return rc;
+    }
     return VG_OK;
 }
 
@@ -380,6 +419,25 @@ int record_now(vg_ctx *c)
 
 }  // namespace
 
+namespace vg {
+
+// Accessors used by the batched ensemble (batch.cpp).
+DevPtrs ctx_dev_ptrs(vg_ctx *c) { return dev_ptrs(c); }
+StepParams ctx_step_params(vg_ctx *c) { return step_params(c); }
+const HostMesh &ctx_host_mesh(vg_ctx *c) { return c->hm; }
+const int32_t *ctx_old_of_new(vg_ctx *c) { return c->old_of_new; }
+int ctx_staging(vg_ctx *c, double **staging)
+{
+    if (!c->staging) {
+        int rc = dmalloc(c, &c->staging, 8 * 3 * c->hm.nc);
+        if (rc) return rc;
+    }
+    *staging = static_cast<double *>(c->staging);
+    return VG_OK;
+}
+
+}  // namespace vg
+
 extern "C" {
 
 int vg_version(void) { return 10000; }
@@ -476,6 +534,7 @@ int vg_mesh_upload(vg_ctx *c, int64_t nv, const double *xy, int64_t nc, const in
     int block = c->prm.block_cells ? c->prm.block_cells : 256;
     int rc = prepare_mesh(nv, xy, nc, tri, depth_v, renumber, block, c->hm, c->err);
     if (rc) return rc;
+    if ((rc = fit_blocks(c))) return rc;
     if ((rc = upload_mesh_arrays(c))) { free_mesh(c); return rc; }
     if ((rc = configure_launch(c))) { free_mesh(c); return rc; }
     c->has_mesh = true;
@@ -514,14 +573,8 @@ int vg_set_params(vg_ctx *c, const vg_params *p)
         cudaStreamSynchronize(c->stream);
         int rc = partition_blocks(c->hm, new_block, c->err);
         if (rc) return rc;
-        dfree(c->halo_ptr); dfree(c->halo_ids); dfree(c->nbrl);
-        if ((rc = dmalloc(c, (void **)&c->nbrl, 2 * 3 * c->hm.nc))) return rc;
-        if ((rc = dmalloc(c, (void **)&c->halo_ptr, 4 * (c->hm.nblocks + 1)))) return rc;
-        if ((rc = dmalloc(c, (void **)&c->halo_ids, 4 * std::max<size_t>(1, c->hm.halo_ids.size())))) return rc;
-        VG_CUDA(c, cudaMemcpy(c->nbrl, c->hm.nbrl.data(), 2 * 3 * c->hm.nc, cudaMemcpyHostToDevice));
-        VG_CUDA(c, cudaMemcpy(c->halo_ptr, c->hm.halo_ptr.data(), 4 * (c->hm.nblocks + 1), cudaMemcpyHostToDevice));
-        if (!c->hm.halo_ids.empty())
-            VG_CUDA(c, cudaMemcpy(c->halo_ids, c->hm.halo_ids.data(), 4 * c->hm.halo_ids.size(), cudaMemcpyHostToDevice));
+        if ((rc = fit_blocks(c))) return rc;
+        if ((rc = upload_partition(c))) return rc;
         if ((rc = configure_launch(c))) return rc;
     }
     return VG_OK;

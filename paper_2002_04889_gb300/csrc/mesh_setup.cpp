@@ -313,6 +313,11 @@ int prepare_mesh(int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
     return partition_blocks(m, block, err);
 }
 
+// Blocks of `block` consecutive cells.  Each block's halo has two rings:
+// ring 1 = face neighbours of block cells outside the block (their face values
+// are reconstructed by the block), ring 2 = face neighbours of ring-1 cells
+// outside block and ring 1 (their states feed ring-1 gradients).  Local indices:
+// block cells [0, block), ring 1 [block, block + n1), ring 2 after that.
 int partition_blocks(HostMesh &m, int block, std::string &err)
 {
     if (block < 32 || block > 1024 || block % 32) { err = "block_cells must be a multiple of 32 in [32, 1024]"; return VG_EINVAL; }
@@ -323,11 +328,11 @@ int partition_blocks(HostMesh &m, int block, std::string &err)
     int32_t nb = (int32_t)((nc + block - 1) / block);
     m.block = block;
     m.nblocks = nb;
-    std::vector<std::vector<int32_t>> halos(nb);
+    std::vector<std::vector<int32_t>> r1(nb), r2(nb);
 #pragma omp parallel for schedule(dynamic, 64)
     for (int32_t b = 0; b < nb; b++) {
         int64_t c0 = (int64_t)b * block, c1 = std::min<int64_t>(c0 + block, nc);
-        std::vector<int32_t> &h = halos[b];
+        std::vector<int32_t> &h = r1[b];
         for (int f = 0; f < 3; f++)
             for (int64_t c = c0; c < c1; c++) {
                 int32_t j = m.nbr[f * nc + c];
@@ -335,30 +340,53 @@ int partition_blocks(HostMesh &m, int block, std::string &err)
             }
         std::sort(h.begin(), h.end());
         h.erase(std::unique(h.begin(), h.end()), h.end());
+        std::vector<int32_t> &h2 = r2[b];
+        for (int32_t r : h)
+            for (int f = 0; f < 3; f++) {
+                int32_t j = m.nbr[f * nc + r];
+                if (j >= 0 && (j < c0 || j >= c1) && !std::binary_search(h.begin(), h.end(), j)) h2.push_back(j);
+            }
+        std::sort(h2.begin(), h2.end());
+        h2.erase(std::unique(h2.begin(), h2.end()), h2.end());
     }
     m.halo_ptr.assign(nb + 1, 0);
+    m.halo_n1.assign(nb, 0);
     int32_t mh = 0;
     for (int32_t b = 0; b < nb; b++) {
-        m.halo_ptr[b + 1] = m.halo_ptr[b] + (int32_t)halos[b].size();
-        mh = std::max<int32_t>(mh, (int32_t)halos[b].size());
+        int32_t n = (int32_t)(r1[b].size() + r2[b].size());
+        m.halo_ptr[b + 1] = m.halo_ptr[b] + n;
+        m.halo_n1[b] = (int32_t)r1[b].size();
+        mh = std::max(mh, n);
     }
-    if (block + mh >= (1 << 14)) { err = "a block's halo is too large"; return VG_EINVAL; }
+    if (block + mh >= (1 << 14) - 1) { err = "a block's halo is too large"; return VG_EINVAL; }
     m.max_halo = mh;
     m.halo_ids.resize(m.halo_ptr[nb]);
+    m.ring1_nbr.assign(3 * (size_t)m.halo_ptr[nb], NBR_WALL);
     std::vector<uint16_t> nbrl(3 * nc, NBR_WALL);
 #pragma omp parallel for schedule(dynamic, 64)
     for (int32_t b = 0; b < nb; b++) {
         int64_t c0 = (int64_t)b * block, c1 = std::min<int64_t>(c0 + block, nc);
-        const std::vector<int32_t> &h = halos[b];
+        const std::vector<int32_t> &h = r1[b], &h2 = r2[b];
+        int32_t n1 = (int32_t)h.size();
         std::copy(h.begin(), h.end(), m.halo_ids.begin() + m.halo_ptr[b]);
+        std::copy(h2.begin(), h2.end(), m.halo_ids.begin() + m.halo_ptr[b] + n1);
+        auto local_of = [&](int32_t j) -> int32_t {
+            if (j >= c0 && j < c1) return (int32_t)(j - c0);
+            auto it = std::lower_bound(h.begin(), h.end(), j);
+            if (it != h.end() && *it == j) return block + (int32_t)(it - h.begin());
+            it = std::lower_bound(h2.begin(), h2.end(), j);
+            return block + n1 + (int32_t)(it - h2.begin());
+        };
         for (int f = 0; f < 3; f++)
             for (int64_t c = c0; c < c1; c++) {
                 int32_t j = m.nbr[f * nc + c];
                 if (j < 0) continue;
-                int32_t local;
-                if (j >= c0 && j < c1) local = (int32_t)(j - c0);
-                else local = block + (int32_t)(std::lower_bound(h.begin(), h.end(), j) - h.begin());
-                nbrl[f * nc + c] = (uint16_t)((local << 2) | nface[f * nc + c]);
+                nbrl[f * nc + c] = (uint16_t)((local_of(j) << 2) | nface[f * nc + c]);
+            }
+        for (int32_t k = 0; k < n1; k++)
+            for (int f = 0; f < 3; f++) {
+                int32_t j = m.nbr[f * nc + h[k]];
+                if (j >= 0) m.ring1_nbr[3 * ((size_t)m.halo_ptr[b] + k) + f] = (uint16_t)local_of(j);
             }
     }
     m.nbrl.swap(nbrl);

@@ -12,10 +12,11 @@
 //   epilogue: t += dt, gauges, reset of the CFL minimum (util_kernels.cu)
 //
 // Each CTA owns a block of B consecutive (renumbered) cells and stages the
-// block plus its one-ring halo in shared memory:
-//   A  load the state of block + halo cells            (smem  sH, sHu, sHv, sz)
-//   B  reconstruct face values of block + halo cells    (smem  fH, fHu, fHv)
-//      (halo cells read their own neighbours from global memory)
+// block plus a two-ring halo in shared memory (ring 1: face neighbours of the
+// block; ring 2: face neighbours of ring 1), with local indices precomputed on
+// the host so that no phase chases an index through global memory:
+//   A  load the state of block + ring-1 + ring-2 cells  (smem  sH, sHu, sHv, sz)
+//   B  reconstruct face values of block + ring-1 cells  (smem  fH, fHu, fHv)
 //   C  one thread per owned face computes the interface flux once
 //      (a face is owned by the lower local index, a block cell facing the
 //      halo, or a wall)                                  (smem  owned-face slots)
@@ -51,8 +52,10 @@ struct KArgs {
     const real *z;          // [nc]
     const int32_t *nbr;     // [3][nc]
     const uint16_t *nbrl;   // [3][nc]
-    const int32_t *halo_ptr;
-    const int32_t *halo_ids;
+    const int32_t *halo_ptr;  // [nblocks + 1]
+    const int32_t *halo_n1;   // [nblocks] ring-1 count
+    const int32_t *halo_ids;  // per block: ring 1 then ring 2
+    const uint16_t *ring1_nbr;// [3 * ring cells] local neighbours of ring-1 cells
     const real *w;          // w^n [3][nc]
     real *R0;               // [3][nc]
     real *wout;             // w^{n+1} [3][nc] (stage 2)
@@ -302,16 +305,18 @@ template <typename real>
 __host__ __device__ inline size_t stage_smem_bytes(int block, int max_halo)
 {
     size_t L = (size_t)block + max_halo;
-    return sizeof(real) * (13 * L + 18 * (size_t)block) + sizeof(uint16_t) * 3 * (size_t)block + 16;
+    return sizeof(real) * (13 * L + 18 * (size_t)block) + sizeof(int32_t) * L +
+           sizeof(uint16_t) * 3 * (size_t)block + 16;
 }
 
+// One block of cells for one scenario: phases A-D (see the top of this file).
+// my_min collects the thread's stage-1 CFL bound, my_neg its negative-depth
+// events, bad a non-finite result.  Every thread of the CTA must call it.
 template <typename real, int STAGE>
-__global__ void __launch_bounds__(256) stage_kernel(const KArgs<real> a)
+__device__ __forceinline__ void process_block(const KArgs<real> &a, const int b, const real dt,
+                                              unsigned char *smem_raw, int &qcount, real &my_min,
+                                              long long &my_neg, bool &bad)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int qcount;
-    __shared__ real red_min[32];
-    __shared__ long long red_neg[32];
 
     const int B = a.block;
     const int L = B + a.max_halo;
@@ -329,12 +334,236 @@ __global__ void __launch_bounds__(256) stage_kernel(const KArgs<real> a)
     real *oPL = oP2 + 3 * B;
     real *oPR = oPL + 3 * B;
     real *oA = oPR + 3 * B;
-    uint16_t *queue = reinterpret_cast<uint16_t *>(oA + 3 * B);
+    int32_t *sGid = reinterpret_cast<int32_t *>(oA + 3 * B);   // [L] global id of each local cell
+    uint16_t *queue = reinterpret_cast<uint16_t *>(sGid + L);
 
     constexpr bool ETA = EtaForm<real>::value;
     const int tid = threadIdx.x;
     const real g = a.g, half_g = a.half_g, hthr = a.hthr;
     const real *geo = a.geo;
+
+    const int64_t c0 = (int64_t)b * B;
+    const int ncell = (int)min((int64_t)B, nc - c0);
+    const int h0 = a.halo_ptr[b];
+    const int nh = a.halo_ptr[b + 1] - h0;
+    const int n1 = a.halo_n1[b];
+
+    // A: block + ring-1 + ring-2 states into shared memory
+    for (int l = tid; l < B + nh; l += blockDim.x) {
+        if (l < B && l >= ncell) continue;
+        int64_t gid = l < B ? c0 + l : (int64_t)a.halo_ids[h0 + (l - B)];
+        real W, Hu, Hv;
+        real zc = a.z[gid];
+        bool neg = stage_state<real, STAGE>(a, gid, dt, zc, W, Hu, Hv);
+        if (neg && l < B) my_neg++;
+        sH[l] = W; sHu[l] = Hu; sHv[l] = Hv;
+        sz[l] = zc;
+        sGid[l] = (int32_t)gid;
+    }
+    if (tid == 0) qcount = 0;
+    __syncthreads();
+
+    // B: face values of block + ring-1 cells (Sec. 2.4, Eq. recon with the
+    // Barth-Jespersen limiter); every neighbour is in shared memory
+    for (int l = tid; l < B + n1; l += blockDim.x) {
+        if (l < B && l >= ncell) continue;
+        int64_t gid = sGid[l];
+        const real HuK = sHu[l], HvK = sHv[l], zK = sz[l];
+        const real HK = ETA ? sH[l] - zK : sH[l];
+        real qK[3] = {ETA ? sH[l] : HK + zK, HuK, HvK};
+        real qn[3][3];
+        bool recon = (a.order == 2) && (HK > hthr);
+        for (int f = 0; f < 3; f++) {
+            bool wall;
+            real Wj = real(0), Huj = real(0), Hvj = real(0), zj = real(0);
+            int nl;
+            if (l < B) {
+                uint16_t code = a.nbrl[f * nc + gid];
+                wall = code == NBR_WALL;
+                nl = code >> 2;
+            } else {
+                uint16_t code = a.ring1_nbr[3 * (h0 + (l - B)) + f];
+                wall = code == NBR_WALL;
+                nl = code;
+            }
+            if (!wall) { Wj = sH[nl]; Huj = sHu[nl]; Hvj = sHv[nl]; zj = sz[nl]; }
+            if (!wall) {
+                const real Hj = ETA ? Wj - zj : Wj;
+                qn[f][0] = ETA ? Wj : Hj + zj;
+                qn[f][1] = Huj;
+                qn[f][2] = Hvj;
+                if (!(Hj > hthr)) recon = false;
+            } else {
+                real nxf = geo[(GEO_NX + f) * nc + gid], nyf = geo[(GEO_NY + f) * nc + gid];
+                real mn = HuK * nxf + HvK * nyf;
+                qn[f][0] = qK[0];
+                qn[f][1] = HuK - real(2) * mn * nxf;
+                qn[f][2] = HvK - real(2) * mn * nyf;
+            }
+        }
+        real Hf[3], Huf[3], Hvf[3];
+        if (recon) {
+            real fx[3], fy[3], wx[3], wy[3];
+            for (int f = 0; f < 3; f++) {
+                fx[f] = geo[(GEO_FX + f) * nc + gid];
+                fy[f] = geo[(GEO_FY + f) * nc + gid];
+                wx[f] = geo[(GEO_WX + f) * nc + gid];
+                wy[f] = geo[(GEO_WY + f) * nc + gid];
+            }
+            real face[3][3];
+#pragma unroll
+            for (int v = 0; v < 3; v++) {
+                real d0 = qn[0][v] - qK[v], d1 = qn[1][v] - qK[v], d2 = qn[2][v] - qK[v];
+                real gx = (wx[0] * d0 + wx[1] * d1) + wx[2] * d2;
+                real gy = (wy[0] * d0 + wy[1] * d1) + wy[2] * d2;
+                real qmax = qK[v], qmin = qK[v];
+#pragma unroll
+                for (int f = 0; f < 3; f++) {
+                    qmax = vmax(qmax, qn[f][v]);
+                    qmin = vmin(qmin, qn[f][v]);
+                }
+                real alpha = real(1);
+                real D[3];
+#pragma unroll
+                for (int f = 0; f < 3; f++) {
+                    D[f] = gx * fx[f] + gy * fy[f];
+                    real phi = real(1);
+                    if (D[f] > real(0)) phi = vmin(real(1), (qmax - qK[v]) / D[f]);
+                    else if (D[f] < real(0)) phi = vmin(real(1), (qmin - qK[v]) / D[f]);
+                    alpha = vmin(alpha, phi);
+                }
+#pragma unroll
+                for (int f = 0; f < 3; f++) face[f][v] = qK[v] + alpha * D[f];
+            }
+#pragma unroll
+            for (int f = 0; f < 3; f++) {
+                Hf[f] = face[f][0] - zK;
+                if (!(Hf[f] > hthr)) recon = false;
+                if (ETA) Hf[f] = face[f][0];      // FP32 keeps eta_f
+                Huf[f] = face[f][1];
+                Hvf[f] = face[f][2];
+            }
+        }
+        if (!recon) {
+#pragma unroll
+            for (int f = 0; f < 3; f++) { Hf[f] = ETA ? sH[l] : HK; Huf[f] = HuK; Hvf[f] = HvK; }
+        }
+#pragma unroll
+        for (int f = 0; f < 3; f++) {
+            fH[f * L + l] = Hf[f];
+            fHu[f * L + l] = Huf[f];
+            fHv[f * L + l] = Hvf[f];
+        }
+    }
+    __syncthreads();
+
+    // C: owned faces, one flux each (Sec. 2.2)
+    if (tid < ncell) {
+        int64_t gid = c0 + tid;
+        int items[3], n = 0;
+#pragma unroll
+        for (int f = 0; f < 3; f++) {
+            uint16_t code = a.nbrl[f * nc + gid];
+            bool owned = code == NBR_WALL || (code >> 2) >= B || (int)(code >> 2) > tid;
+            if (owned) items[n++] = (tid << 2) | f;
+        }
+        if (n) {
+            int pos = atomicAdd(&qcount, n);
+            for (int k = 0; k < n; k++) queue[pos + k] = (uint16_t)items[k];
+        }
+    }
+    __syncthreads();
+    const int nq = qcount;
+    for (int q = tid; q < nq; q += blockDim.x) {
+        int item = queue[q];
+        int l = item >> 2, f = item & 3;
+        int64_t gid = c0 + l;
+        uint16_t code = a.nbrl[f * nc + gid];
+        bool wall = code == NBR_WALL;
+        real HfR = real(0), HufR = real(0), HvfR = real(0), zR = real(0);
+        if (!wall) {
+            int nl = code >> 2, nf = code & 3;
+            HfR = fH[nf * L + nl]; HufR = fHu[nf * L + nl]; HvfR = fHv[nf * L + nl];
+            zR = sz[nl];
+        }
+        real Phi[3], PL, PR, am;
+        if constexpr (ETA) {
+            float eR = wall ? 0.f : sH[code >> 2];
+            face_flux_dev(g, half_g, hthr, fH[f * L + l], fHu[f * L + l], fHv[f * L + l], sz[l], sH[l],
+                          HfR, HufR, HvfR, zR, eR, geo[(GEO_NX + f) * nc + gid],
+                          geo[(GEO_NY + f) * nc + gid], wall, Phi, PL, PR, am);
+        } else {
+            face_flux<real>(g, half_g, hthr, fH[f * L + l], fHu[f * L + l], fHv[f * L + l], sz[l],
+                            HfR, HufR, HvfR, zR, geo[(GEO_NX + f) * nc + gid],
+                            geo[(GEO_NY + f) * nc + gid], wall, Phi, PL, PR, am);
+        }
+        int s = f * B + l;
+        oP0[s] = Phi[0]; oP1[s] = Phi[1]; oP2[s] = Phi[2];
+        oPL[s] = PL; oPR[s] = PR; oA[s] = am;
+    }
+    __syncthreads();
+
+    // D: residual R_K = -(1/|K|) sum_f l_f [Phi_f + (0, P_{K,f} n_f)], faces in local order
+    if (tid < ncell) {
+        const int l = tid;
+        const int64_t gid = c0 + l;
+        real aH = real(0), aHu = real(0), aHv = real(0), am = real(0);
+#pragma unroll
+        for (int f = 0; f < 3; f++) {
+            uint16_t code = a.nbrl[f * nc + gid];
+            bool owned = code == NBR_WALL || (code >> 2) >= B || (int)(code >> 2) > l;
+            real P0, P1, P2, P, sa;
+            if (owned) {
+                int s = f * B + l;
+                P0 = oP0[s]; P1 = oP1[s]; P2 = oP2[s]; P = oPL[s]; sa = oA[s];
+            } else {
+                int s = (code & 3) * B + (code >> 2);
+                P0 = -oP0[s]; P1 = -oP1[s]; P2 = -oP2[s]; P = oPR[s]; sa = oA[s];
+            }
+            real len = geo[(GEO_LEN + f) * nc + gid];
+            real nx = geo[(GEO_NX + f) * nc + gid], ny = geo[(GEO_NY + f) * nc + gid];
+            aH = aH + len * P0;
+            aHu = aHu + len * (P1 + P * nx);
+            aHv = aHv + len * (P2 + P * ny);
+            if (STAGE == 1) am = vmax(am, len * sa);
+        }
+        real area = geo[GEO_AREA * nc + gid];
+        real RH = -aH / area, RHu = -aHu / area, RHv = -aHv / area;
+        if (STAGE == 1) {
+            a.R0[gid] = RH;
+            a.R0[nc + gid] = RHu;
+            a.R0[2 * nc + gid] = RHv;
+            if (am > real(0)) my_min = vmin(my_min, area / (real(3) * am));
+        } else {
+            real H0 = a.w[gid], Hu0 = a.w[nc + gid], Hv0 = a.w[2 * nc + gid];
+            real W = real(0.5) * H0 + real(0.5) * (sH[l] + dt * RH);
+            real Hu = real(0.5) * Hu0 + real(0.5) * (sHu[l] + dt * RHu);
+            real Hv = real(0.5) * Hv0 + real(0.5) * (sHv[l] + dt * RHv);
+            real H = ETA ? W - sz[l] : W;
+            if (H < real(0)) {
+                my_neg++;
+                W = ETA ? sz[l] : real(0);
+                Hu = real(0); Hv = real(0);
+            } else if (H <= hthr) {
+                Hu = real(0); Hv = real(0);
+            }
+            if (!isfinite(W) || !isfinite(Hu) || !isfinite(Hv)) bad = true;
+            a.wout[gid] = W;
+            a.wout[nc + gid] = Hu;
+            a.wout[2 * nc + gid] = Hv;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename real, int STAGE>
+__global__ void __launch_bounds__(256) stage_kernel(const KArgs<real> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int qcount;
+    __shared__ real red_min[32];
+    __shared__ long long red_neg[32];
+    const int tid = threadIdx.x;
 
     real dt = real(0);
     if (STAGE == 2) dt = (real)step_dt<real>(a.sc, a.cfl, a.dt_fixed, a.dt_max, a.t_end);
@@ -343,221 +572,8 @@ __global__ void __launch_bounds__(256) stage_kernel(const KArgs<real> a)
     long long my_neg = 0;
     bool bad = false;
 
-    for (int b = blockIdx.x; b < a.nblocks; b += gridDim.x) {
-        const int64_t c0 = (int64_t)b * B;
-        const int ncell = (int)min((int64_t)B, nc - c0);
-        const int h0 = a.halo_ptr[b];
-        const int nh = a.halo_ptr[b + 1] - h0;
-
-        // A: block + halo states into shared memory
-        for (int l = tid; l < B + nh; l += blockDim.x) {
-            if (l < B && l >= ncell) continue;
-            int64_t gid = l < B ? c0 + l : (int64_t)a.halo_ids[h0 + (l - B)];
-            real W, Hu, Hv;
-            real zc = a.z[gid];
-            bool neg = stage_state<real, STAGE>(a, gid, dt, zc, W, Hu, Hv);
-            if (neg && l < B) my_neg++;
-            sH[l] = W; sHu[l] = Hu; sHv[l] = Hv;
-            sz[l] = zc;
-        }
-        if (tid == 0) qcount = 0;
-        __syncthreads();
-
-        // B: face values (Sec. 2.4, Eq. recon with the Barth-Jespersen limiter)
-        for (int l = tid; l < B + nh; l += blockDim.x) {
-            if (l < B && l >= ncell) continue;
-            int64_t gid = l < B ? c0 + l : (int64_t)a.halo_ids[h0 + (l - B)];
-            const real HuK = sHu[l], HvK = sHv[l], zK = sz[l];
-            const real HK = ETA ? sH[l] - zK : sH[l];
-            real qK[3] = {ETA ? sH[l] : HK + zK, HuK, HvK};
-            real qn[3][3];
-            bool recon = (a.order == 2) && (HK > hthr);
-            for (int f = 0; f < 3; f++) {
-                bool wall;
-                real Wj = real(0), Huj = real(0), Hvj = real(0), zj = real(0);
-                if (l < B) {
-                    uint16_t code = a.nbrl[f * nc + gid];
-                    wall = code == NBR_WALL;
-                    if (!wall) {
-                        int nl = code >> 2;
-                        Wj = sH[nl]; Huj = sHu[nl]; Hvj = sHv[nl]; zj = sz[nl];
-                    }
-                } else {
-                    int32_t j = a.nbr[f * nc + gid];
-                    wall = j < 0;
-                    if (!wall) {
-                        zj = a.z[j];
-                        stage_state<real, STAGE>(a, j, dt, zj, Wj, Huj, Hvj);  // negatives counted by the owner
-                    }
-                }
-                if (!wall) {
-                    const real Hj = ETA ? Wj - zj : Wj;
-                    qn[f][0] = ETA ? Wj : Hj + zj;
-                    qn[f][1] = Huj;
-                    qn[f][2] = Hvj;
-                    if (!(Hj > hthr)) recon = false;
-                } else {
-                    real nxf = geo[(GEO_NX + f) * nc + gid], nyf = geo[(GEO_NY + f) * nc + gid];
-                    real mn = HuK * nxf + HvK * nyf;
-                    qn[f][0] = qK[0];
-                    qn[f][1] = HuK - real(2) * mn * nxf;
-                    qn[f][2] = HvK - real(2) * mn * nyf;
-                }
-            }
-            real Hf[3], Huf[3], Hvf[3];
-            if (recon) {
-                real fx[3], fy[3], wx[3], wy[3];
-                for (int f = 0; f < 3; f++) {
-                    fx[f] = geo[(GEO_FX + f) * nc + gid];
-                    fy[f] = geo[(GEO_FY + f) * nc + gid];
-                    wx[f] = geo[(GEO_WX + f) * nc + gid];
-                    wy[f] = geo[(GEO_WY + f) * nc + gid];
-                }
-                real face[3][3];
-#pragma unroll
-                for (int v = 0; v < 3; v++) {
-                    real d0 = qn[0][v] - qK[v], d1 = qn[1][v] - qK[v], d2 = qn[2][v] - qK[v];
-                    real gx = (wx[0] * d0 + wx[1] * d1) + wx[2] * d2;
-                    real gy = (wy[0] * d0 + wy[1] * d1) + wy[2] * d2;
-                    real qmax = qK[v], qmin = qK[v];
-#pragma unroll
-                    for (int f = 0; f < 3; f++) {
-                        qmax = vmax(qmax, qn[f][v]);
-                        qmin = vmin(qmin, qn[f][v]);
-                    }
-                    real alpha = real(1);
-                    real D[3];
-#pragma unroll
-                    for (int f = 0; f < 3; f++) {
-                        D[f] = gx * fx[f] + gy * fy[f];
-                        real phi = real(1);
-                        if (D[f] > real(0)) phi = vmin(real(1), (qmax - qK[v]) / D[f]);
-                        else if (D[f] < real(0)) phi = vmin(real(1), (qmin - qK[v]) / D[f]);
-                        alpha = vmin(alpha, phi);
-                    }
-#pragma unroll
-                    for (int f = 0; f < 3; f++) face[f][v] = qK[v] + alpha * D[f];
-                }
-#pragma unroll
-                for (int f = 0; f < 3; f++) {
-                    Hf[f] = face[f][0] - zK;
-                    if (!(Hf[f] > hthr)) recon = false;
-                    if (ETA) Hf[f] = face[f][0];      // FP32 keeps eta_f
-                    Huf[f] = face[f][1];
-                    Hvf[f] = face[f][2];
-                }
-            }
-            if (!recon) {
-#pragma unroll
-                for (int f = 0; f < 3; f++) { Hf[f] = ETA ? sH[l] : HK; Huf[f] = HuK; Hvf[f] = HvK; }
-            }
-#pragma unroll
-            for (int f = 0; f < 3; f++) {
-                fH[f * L + l] = Hf[f];
-                fHu[f * L + l] = Huf[f];
-                fHv[f * L + l] = Hvf[f];
-            }
-        }
-        __syncthreads();
-
-        // C: owned faces, one flux each (Sec. 2.2)
-        if (tid < ncell) {
-            int64_t gid = c0 + tid;
-            int items[3], n = 0;
-#pragma unroll
-            for (int f = 0; f < 3; f++) {
-                uint16_t code = a.nbrl[f * nc + gid];
-                bool owned = code == NBR_WALL || (code >> 2) >= B || (int)(code >> 2) > tid;
-                if (owned) items[n++] = (tid << 2) | f;
-            }
-            if (n) {
-                int pos = atomicAdd(&qcount, n);
-                for (int k = 0; k < n; k++) queue[pos + k] = (uint16_t)items[k];
-            }
-        }
-        __syncthreads();
-        const int nq = qcount;
-        for (int q = tid; q < nq; q += blockDim.x) {
-            int item = queue[q];
-            int l = item >> 2, f = item & 3;
-            int64_t gid = c0 + l;
-            uint16_t code = a.nbrl[f * nc + gid];
-            bool wall = code == NBR_WALL;
-            real HfR = real(0), HufR = real(0), HvfR = real(0), zR = real(0);
-            if (!wall) {
-                int nl = code >> 2, nf = code & 3;
-                HfR = fH[nf * L + nl]; HufR = fHu[nf * L + nl]; HvfR = fHv[nf * L + nl];
-                zR = sz[nl];
-            }
-            real Phi[3], PL, PR, am;
-            if constexpr (ETA) {
-                float eR = wall ? 0.f : sH[code >> 2];
-                face_flux_dev(g, half_g, hthr, fH[f * L + l], fHu[f * L + l], fHv[f * L + l], sz[l], sH[l],
-                              HfR, HufR, HvfR, zR, eR, geo[(GEO_NX + f) * nc + gid],
-                              geo[(GEO_NY + f) * nc + gid], wall, Phi, PL, PR, am);
-            } else {
-                face_flux<real>(g, half_g, hthr, fH[f * L + l], fHu[f * L + l], fHv[f * L + l], sz[l],
-                                HfR, HufR, HvfR, zR, geo[(GEO_NX + f) * nc + gid],
-                                geo[(GEO_NY + f) * nc + gid], wall, Phi, PL, PR, am);
-            }
-            int s = f * B + l;
-            oP0[s] = Phi[0]; oP1[s] = Phi[1]; oP2[s] = Phi[2];
-            oPL[s] = PL; oPR[s] = PR; oA[s] = am;
-        }
-        __syncthreads();
-
-        // D: residual R_K = -(1/|K|) sum_f l_f [Phi_f + (0, P_{K,f} n_f)], faces in local order
-        if (tid < ncell) {
-            const int l = tid;
-            const int64_t gid = c0 + l;
-            real aH = real(0), aHu = real(0), aHv = real(0), am = real(0);
-#pragma unroll
-            for (int f = 0; f < 3; f++) {
-                uint16_t code = a.nbrl[f * nc + gid];
-                bool owned = code == NBR_WALL || (code >> 2) >= B || (int)(code >> 2) > l;
-                real P0, P1, P2, P, sa;
-                if (owned) {
-                    int s = f * B + l;
-                    P0 = oP0[s]; P1 = oP1[s]; P2 = oP2[s]; P = oPL[s]; sa = oA[s];
-                } else {
-                    int s = (code & 3) * B + (code >> 2);
-                    P0 = -oP0[s]; P1 = -oP1[s]; P2 = -oP2[s]; P = oPR[s]; sa = oA[s];
-                }
-                real len = geo[(GEO_LEN + f) * nc + gid];
-                real nx = geo[(GEO_NX + f) * nc + gid], ny = geo[(GEO_NY + f) * nc + gid];
-                aH = aH + len * P0;
-                aHu = aHu + len * (P1 + P * nx);
-                aHv = aHv + len * (P2 + P * ny);
-                if (STAGE == 1) am = vmax(am, len * sa);
-            }
-            real area = geo[GEO_AREA * nc + gid];
-            real RH = -aH / area, RHu = -aHu / area, RHv = -aHv / area;
-            if (STAGE == 1) {
-                a.R0[gid] = RH;
-                a.R0[nc + gid] = RHu;
-                a.R0[2 * nc + gid] = RHv;
-                if (am > real(0)) my_min = vmin(my_min, area / (real(3) * am));
-            } else {
-                real H0 = a.w[gid], Hu0 = a.w[nc + gid], Hv0 = a.w[2 * nc + gid];
-                real W = real(0.5) * H0 + real(0.5) * (sH[l] + dt * RH);
-                real Hu = real(0.5) * Hu0 + real(0.5) * (sHu[l] + dt * RHu);
-                real Hv = real(0.5) * Hv0 + real(0.5) * (sHv[l] + dt * RHv);
-                real H = ETA ? W - sz[l] : W;
-                if (H < real(0)) {
-                    my_neg++;
-                    W = ETA ? sz[l] : real(0);
-                    Hu = real(0); Hv = real(0);
-                } else if (H <= hthr) {
-                    Hu = real(0); Hv = real(0);
-                }
-                if (!isfinite(W) || !isfinite(Hu) || !isfinite(Hv)) bad = true;
-                a.wout[gid] = W;
-                a.wout[nc + gid] = Hu;
-                a.wout[2 * nc + gid] = Hv;
-            }
-        }
-        __syncthreads();
-    }
+    for (int b = blockIdx.x; b < a.nblocks; b += gridDim.x)
+        process_block<real, STAGE>(a, b, dt, smem_raw, qcount, my_min, my_neg, bad);
 
     // CTA-level reductions, then one atomic per CTA
     const int lane = tid & 31, warp = tid >> 5, nwarps = (blockDim.x + 31) >> 5;
@@ -581,6 +597,106 @@ __global__ void __launch_bounds__(256) stage_kernel(const KArgs<real> a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Batched ensembles: many scenarios on several meshes in one persistent launch
+// per stage.  A work item is one block of one mesh; the CTA runs that block for
+// every scenario of the mesh in turn, so the block's mesh data stays in L1/L2
+// across scenarios.  Scenario e (meshes' scenarios numbered consecutively) has
+// its own state slice, its own device scalars sc[e] and its own time step.
+// ---------------------------------------------------------------------------
+
+constexpr int kBatchMaxEntries = 512;
+
+template <typename real>
+struct BatchMesh {
+    KArgs<real> a;         // mesh arrays; w, R0, wout, sc point at the mesh's first scenario
+    int64_t stride;        // 3 * nc: distance between scenario slices
+    int n_scen;            // scenarios of this mesh
+    int first_item;        // first work item (block) of this mesh in the launch
+    int first_entry;       // index of its first scenario among all scenarios
+    int pad;
+};
+
+// Order-preserving integer image of a non-negative value, as 32 bits (FP32) or
+// 64 bits (FP64), kept in shared memory per scenario.
+template <typename real>
+__device__ __forceinline__ unsigned long long warp_min_bits(real v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = vmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return min_bits(v);
+}
+
+template <typename real, int STAGE>
+__global__ void __launch_bounds__(256) batch_stage_kernel(const BatchMesh<real> *meshes, int n_mesh,
+                                                          int n_items, int n_entries, DevScalars *sc_all)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int qcount;
+    __shared__ unsigned long long s_min[kBatchMaxEntries];
+    __shared__ real s_dt[kBatchMaxEntries];
+    __shared__ long long red_neg[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = (blockDim.x + 31) >> 5;
+    const KArgs<real> &p0 = meshes[0].a;
+    for (int e = tid; e < n_entries; e += blockDim.x) {
+        s_min[e] = min_bits(real_inf<real>());
+        s_dt[e] = STAGE == 2 ? (real)step_dt<real>(sc_all + e, p0.cfl, p0.dt_fixed, p0.dt_max, p0.t_end) : real(0);
+    }
+    __syncthreads();
+    long long my_neg = 0;
+    bool bad = false;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        int m = 0;
+        while (m + 1 < n_mesh && item >= meshes[m + 1].first_item) m++;
+        const BatchMesh<real> &bm = meshes[m];
+        const int b = item - bm.first_item;
+        for (int s = 0; s < bm.n_scen; s++) {
+            KArgs<real> a = bm.a;
+            a.w += s * bm.stride;
+            a.R0 += s * bm.stride;
+            if (STAGE == 2) a.wout += s * bm.stride;
+            a.sc += s;
+            const int e = bm.first_entry + s;
+            real mn = real_inf<real>();
+            process_block<real, STAGE>(a, b, s_dt[e], smem_raw, qcount, mn, my_neg, bad);
+            if (STAGE == 1) {
+                unsigned long long bits = warp_min_bits<real>(mn);
+                if (lane == 0 && bits != min_bits(real_inf<real>())) atomicMin(&s_min[e], bits);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) my_neg += __shfl_xor_sync(0xffffffffu, my_neg, o);
+    if (lane == 0) red_neg[warp] = my_neg;
+    bad = __syncthreads_or(bad);
+    if (STAGE == 1)
+        for (int e = tid; e < n_entries; e += blockDim.x)
+            if (s_min[e] != min_bits(real_inf<real>())) atomicMin(&sc_all[e].dtmin_bits, s_min[e]);
+    if (tid == 0) {
+        long long neg = 0;
+        for (int w = 0; w < nwarps; w++) neg += red_neg[w];
+        if (neg) atomicAdd((unsigned long long *)&sc_all[n_entries].neg_count, (unsigned long long)neg);
+        if (bad) atomicOr(&sc_all[n_entries].flags, FLAG_NONFINITE_STATE);
+    }
+}
+
+// Epilogue of one batched step: per scenario t += dt (dt = 0 once it reached
+// t_end), and reset of its CFL minimum.
+template <typename real>
+__global__ void batch_post_kernel(int n_entries, DevScalars *sc_all, double cfl, double dt_fixed, double dt_max,
+                                  double t_end)
+{
+    for (int e = threadIdx.x; e < n_entries; e += blockDim.x) {
+        DevScalars *sc = sc_all + e;
+        double dt = step_dt<real>(sc, cfl, dt_fixed, dt_max, t_end);
+        sc->dt = dt;
+        if (!isfinite(dt)) sc_all[n_entries].flags |= FLAG_NONFINITE_DT;
+        if (dt > 0.0) {
+            sc->t = sc->t + dt;
+            sc->steps += 1;
+        }
+        sc->dtmin_bits = min_bits(real_inf<real>());
+    }
+}
+
 template <typename real>
 KArgs<real> make_args(const DevPtrs &d, const StepParams &p, const void *w_in, void *w_out)
 {
@@ -595,7 +711,9 @@ KArgs<real> make_args(const DevPtrs &d, const StepParams &p, const void *w_in, v
     a.nbr = d.nbr;
     a.nbrl = d.nbrl;
     a.halo_ptr = d.halo_ptr;
+    a.halo_n1 = d.halo_n1;
     a.halo_ids = d.halo_ids;
+    a.ring1_nbr = d.ring1_nbr;
     a.w = static_cast<const real *>(w_in);
     a.R0 = static_cast<real *>(d.R0);
     a.wout = static_cast<real *>(w_out);
@@ -639,6 +757,53 @@ int launch_stage(const DevPtrs &d, const StepParams &p, int stage, const void *w
     if (stage == 1) stage_kernel<real, 1><<<c.grid, d.block, c.smem, s>>>(a);
     else stage_kernel<real, 2><<<c.grid, d.block, c.smem, s>>>(a);
     return (int)cudaGetLastError();
+}
+
+template <typename real>
+int batch_config(int block, int max_halo, int &grid, size_t &smem)
+{
+    smem = stage_smem_bytes<real>(block, max_halo);
+    int best = 1 << 30;
+    for (int stage = 1; stage <= 2; stage++) {
+        auto kern = stage == 1 ? batch_stage_kernel<real, 1> : batch_stage_kernel<real, 2>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return (int)e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
+        if (e != cudaSuccess) return (int)e;
+        best = per_sm < best ? per_sm : best;
+    }
+    if (best < 1) return (int)cudaErrorInvalidConfiguration;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    grid = sms * best;
+    return 0;
+}
+
+template <typename real>
+int launch_batch_step(const void *table, int n_mesh, int n_items, int n_entries, DevScalars *sc_all, int block,
+                      int grid, size_t smem, const StepParams &p, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const BatchMesh<real> *t = static_cast<const BatchMesh<real> *>(table);
+    batch_stage_kernel<real, 1><<<grid, block, smem, s>>>(t, n_mesh, n_items, n_entries, sc_all);
+    batch_stage_kernel<real, 2><<<grid, block, smem, s>>>(t, n_mesh, n_items, n_entries, sc_all);
+    batch_post_kernel<real><<<1, 256, 0, s>>>(n_entries, sc_all, p.cfl, p.dt_fixed, p.dt_max, p.t_end);
+    return (int)cudaGetLastError();
+}
+
+template <typename real>
+void fill_batch_mesh(void *dst, const DevPtrs &d, const StepParams &p, const void *w_in, void *w_out,
+                     int n_scen, int first_item, int first_entry)
+{
+    BatchMesh<real> *bm = static_cast<BatchMesh<real> *>(dst);
+    bm->a = make_args<real>(d, p, w_in, w_out);
+    bm->stride = 3 * d.nc;
+    bm->n_scen = n_scen;
+    bm->first_item = first_item;
+    bm->first_entry = first_entry;
+    bm->pad = 0;
 }
 
 }  // namespace vg

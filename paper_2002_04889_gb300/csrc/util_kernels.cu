@@ -89,13 +89,16 @@ __global__ void import_state_kernel(int64_t nc, const int32_t *old_of_new, const
     if (bad) atomicOr(&sc->flags, FLAG_BAD_INPUT);
 }
 
+// Internal order, stored form -> original order, H.  In the eta form a cell is
+// dry when eta <= z in the kernels' own (rounded) bed, and then H is exactly 0.
 template <typename real, typename dst_t>
-__global__ void export_state_kernel(int64_t nc, const int32_t *old_of_new, const real *w, const double *z,
-                                    dst_t *H, dst_t *Hu, dst_t *Hv)
+__global__ void export_state_kernel(int64_t nc, const int32_t *old_of_new, const real *w, const real *zr,
+                                    const double *z, dst_t *H, dst_t *Hu, dst_t *Hv)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nc; k += (int64_t)gridDim.x * blockDim.x) {
         int64_t o = old_of_new[k];
-        double h = EtaForm<real>::value ? (double)w[k] - (double)z[k] : (double)w[k];
+        double h = (double)w[k];
+        if (EtaForm<real>::value) h = (w[k] - zr[k] <= real(0)) ? 0.0 : fmax(0.0, h - z[k]);
         H[o] = (dst_t)h;
         Hu[o] = (dst_t)w[nc + k];
         Hv[o] = (dst_t)w[2 * nc + k];
@@ -112,7 +115,8 @@ __global__ void diag_partial_kernel(int64_t nc, const real *w, const double *z, 
     __shared__ double s_mass[256], s_min[256], s_dry[256];
     double mass = 0.0, mn = CUDART_INF, dry = 0.0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nc; k += (int64_t)gridDim.x * blockDim.x) {
-        double h = EtaForm<real>::value ? (double)w[k] - (double)z[k] : (double)w[k];
+        double h = (double)w[k];
+        if (EtaForm<real>::value) h = h - z[k];
         mass += (double)geo[GEO_AREA * nc + k] * h;
         mn = fmin(mn, h);
         dry += h <= hthr ? 1.0 : 0.0;
@@ -196,15 +200,15 @@ int launch_export_state(const DevPtrs &d, const int32_t *old_of_new, const void 
     if (precision == 64) {
         const double *z = d.z64;
         if (dst_is_double)
-            export_state_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)w, z, (double *)H, (double *)Hu, (double *)Hv);
+            export_state_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)w, (const double *)d.z, z, (double *)H, (double *)Hu, (double *)Hv);
         else
-            export_state_kernel<double, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)w, z, (float *)H, (float *)Hu, (float *)Hv);
+            export_state_kernel<double, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const double *)w, (const double *)d.z, z, (float *)H, (float *)Hu, (float *)Hv);
     } else {
         const double *z = d.z64;
         if (dst_is_double)
-            export_state_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)w, z, (double *)H, (double *)Hu, (double *)Hv);
+            export_state_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)w, (const float *)d.z, z, (double *)H, (double *)Hu, (double *)Hv);
         else
-            export_state_kernel<float, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)w, z, (float *)H, (float *)Hu, (float *)Hv);
+            export_state_kernel<float, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)w, (const float *)d.z, z, (float *)H, (float *)Hu, (float *)Hv);
     }
     return (int)cudaGetLastError();
 }

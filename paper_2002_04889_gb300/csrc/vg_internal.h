@@ -32,15 +32,18 @@ struct HostMesh {
     int64_t n_flipped = 0;
     int32_t block = 256;                 // cells per block
     int32_t nblocks = 0;
-    int32_t max_halo = 0;
+    int32_t max_halo = 0;                // max ring-1 + ring-2 cells of a block
     std::vector<int32_t> new_of_old, old_of_new;
     std::vector<int32_t> vtx;            // [nc][3] local-order vertices (original cell order)
     std::vector<double> geo;             // [GEO_ROWS][nc]  (internal order)
     std::vector<double> z;               // [nc]            (internal order)
     std::vector<int32_t> nbr;            // [3][nc] internal neighbour ids, -1 wall
     std::vector<uint16_t> nbrl;          // [3][nc] (local << 2 | face) or NBR_WALL
-    std::vector<int32_t> halo_ptr;       // [nblocks + 1]
-    std::vector<int32_t> halo_ids;       // internal ids of each block's halo cells
+    std::vector<int32_t> halo_ptr;       // [nblocks + 1] into halo_ids / ring1_nbr
+    std::vector<int32_t> halo_n1;        // [nblocks] ring-1 cells of each block
+    std::vector<int32_t> halo_ids;       // per block: ring-1 then ring-2 cells (internal ids)
+    std::vector<uint16_t> ring1_nbr;     // [3 * halo_ids.size()] local neighbour index of
+                                         // each ring-1 cell (NBR_WALL for a wall)
     std::vector<double> xy;              // [nv][2] copy for point location
 };
 
@@ -89,7 +92,9 @@ struct DevPtrs {
     const int32_t *nbr;     // [3][nc]
     const uint16_t *nbrl;   // [3][nc]
     const int32_t *halo_ptr;
+    const int32_t *halo_n1;
     const int32_t *halo_ids;
+    const uint16_t *ring1_nbr;
     void *R0;               // [3][nc] stage-1 residual (scratch)
     DevScalars *sc;
     const int32_t *gauge_cells;   // internal ids
@@ -103,12 +108,31 @@ struct LaunchCfg {
     int grid;        // persistent CTAs
     size_t smem;     // dynamic shared memory per CTA
 };
+size_t stage_smem_f32(int block, int max_halo);
+size_t stage_smem_f64(int block, int max_halo);
 int stage_config_f32(const DevPtrs &d, int stage, LaunchCfg &cfg);
 int stage_config_f64(const DevPtrs &d, int stage, LaunchCfg &cfg);
 int launch_stage1_f32(const DevPtrs &d, const StepParams &p, const void *w_in, const LaunchCfg &c, void *stream);
 int launch_stage2_f32(const DevPtrs &d, const StepParams &p, const void *w_in, void *w_out, const LaunchCfg &c, void *stream);
 int launch_stage1_f64(const DevPtrs &d, const StepParams &p, const void *w_in, const LaunchCfg &c, void *stream);
 int launch_stage2_f64(const DevPtrs &d, const StepParams &p, const void *w_in, void *w_out, const LaunchCfg &c, void *stream);
+
+// Batched ensembles (step_f32.cu / step_f64.cu): the device table entry of one
+// mesh, the launch configuration, and one batched step (stage 1, stage 2,
+// epilogue) over all scenarios.  sc_all has n_entries scenario scalars plus one
+// batch-wide record (negative-depth count, flags).
+size_t batch_mesh_bytes_f32();
+size_t batch_mesh_bytes_f64();
+void fill_batch_mesh_f32(void *dst, const DevPtrs &d, const StepParams &p, const void *w_in, void *w_out, int n_scen,
+                         int first_item, int first_entry);
+void fill_batch_mesh_f64(void *dst, const DevPtrs &d, const StepParams &p, const void *w_in, void *w_out, int n_scen,
+                         int first_item, int first_entry);
+int batch_config_f32(int block, int max_halo, int &grid, size_t &smem);
+int batch_config_f64(int block, int max_halo, int &grid, size_t &smem);
+int launch_batch_step_f32(const void *table, int n_mesh, int n_items, int n_entries, DevScalars *sc_all, int block,
+                          int grid, size_t smem, const StepParams &p, void *stream);
+int launch_batch_step_f64(const void *table, int n_mesh, int n_items, int n_entries, DevScalars *sc_all, int block,
+                          int grid, size_t smem, const StepParams &p, void *stream);
 
 // Utility kernels (util_kernels.cu).
 int launch_post_step(const DevPtrs &d, const StepParams &p, const void *w, int precision, void *stream);
@@ -120,4 +144,13 @@ int launch_export_state(const DevPtrs &d, const int32_t *old_of_new, const void 
 int launch_diagnostics(const DevPtrs &d, const void *w, int precision, double hthr, double *part,
                        double *out, void *stream);
 
+}  // namespace vg
+
+struct vg_ctx;
+namespace vg {
+DevPtrs ctx_dev_ptrs(vg_ctx *c);
+StepParams ctx_step_params(vg_ctx *c);
+const HostMesh &ctx_host_mesh(vg_ctx *c);
+const int32_t *ctx_old_of_new(vg_ctx *c);
+int ctx_staging(vg_ctx *c, double **staging);
 }  // namespace vg

@@ -80,6 +80,18 @@ _SIGNATURES = {
     "vg_profile": ([_V, C.c_int], C.c_int),
     "vg_get_profile": ([_V, C.c_int32, C.POINTER(C.c_char_p), _I64, _D, _I32], C.c_int),
     "vg_device_bytes": ([_V, _I64], C.c_int),
+    "vg_batch_create": ([C.POINTER(_V), C.c_int, C.c_int, _V], C.c_int),
+    "vg_batch_destroy": ([_V], None),
+    "vg_batch_last_error": ([_V], C.c_char_p),
+    "vg_batch_set_params": ([_V, C.POINTER(vg_params)], C.c_int),
+    "vg_batch_add_mesh": ([_V, C.c_int64, _D, C.c_int64, _I32, _D, C.c_int, C.c_int32,
+                           C.POINTER(C.c_int32)], C.c_int),
+    "vg_batch_set_state": ([_V, C.c_int32, C.c_int32, _D, _D, _D, C.c_double], C.c_int),
+    "vg_batch_get_state": ([_V, C.c_int32, C.c_int32, _D, _D, _D, _D, _I64], C.c_int),
+    "vg_batch_step": ([_V, C.c_int64], C.c_int),
+    "vg_batch_run": ([_V, C.c_double, C.c_int64, _I64], C.c_int),
+    "vg_batch_autotune": ([_V, C.c_int32, C.POINTER(C.c_int32), _D], C.c_int),
+    "vg_batch_info": ([_V, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _I64, _I64], C.c_int),
 }
 
 
@@ -374,3 +386,97 @@ class Solver:
 
     def device_bytes(self) -> int:
         return vg_device_bytes(self.ctx)
+
+
+# ---------------------------------------------------------------- batched ensembles
+
+
+def _bcheck(b, rc: int) -> None:
+    if rc != VG_OK:
+        lib = load()
+        msg = lib.vg_batch_last_error(b).decode() if b else ""
+        raise VolnaError(rc, msg or lib.vg_strerror(rc).decode())
+
+
+class Batch:
+    """Many scenarios on several meshes advanced together (vg_batch_*)."""
+
+    def __init__(self, precision: int = 32, device: int = 0, stream=None):
+        h = _V()
+        rc = load().vg_batch_create(C.byref(h), int(precision), int(device),
+                                    _V(_stream_handle(stream)) if stream is not None else None)
+        if rc != VG_OK:
+            raise VolnaError(rc, f"vg_batch_create failed: {vg_strerror(rc)}")
+        self.h = h
+        self.precision = precision
+        self.nc = []
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            load().vg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_params(self, **kw) -> None:
+        p = vg_default_params()
+        for k, v in kw.items():
+            setattr(p, k, v)
+        _bcheck(self.h, load().vg_batch_set_params(self.h, C.byref(p)))
+
+    def add_mesh(self, mesh, n_scenarios: int, renumber="morton") -> int:
+        xy = _f64(mesh.xy).reshape(-1, 2)
+        tri = np.ascontiguousarray(mesh.tri, dtype=np.int32).reshape(-1, 3)
+        depth = _f64(mesh.depth)
+        mid = C.c_int32()
+        r = RENUMBER[renumber] if isinstance(renumber, str) else int(renumber)
+        _bcheck(self.h, load().vg_batch_add_mesh(self.h, xy.shape[0], _dp(xy), tri.shape[0],
+                                                 tri.ctypes.data_as(_I32), _dp(depth), r,
+                                                 int(n_scenarios), C.byref(mid)))
+        self.nc.append(tri.shape[0])
+        return mid.value
+
+    def set_state(self, mesh_id: int, scen: int, H, Hu, Hv, t: float = 0.0) -> None:
+        H, Hu, Hv = _f64(H), _f64(Hu), _f64(Hv)
+        _bcheck(self.h, load().vg_batch_set_state(self.h, mesh_id, scen, _dp(H), _dp(Hu), _dp(Hv),
+                                                  float(t)))
+
+    def get_state(self, mesh_id: int, scen: int):
+        n = self.nc[mesh_id]
+        H, Hu, Hv = np.empty(n), np.empty(n), np.empty(n)
+        t = C.c_double()
+        steps = C.c_int64()
+        _bcheck(self.h, load().vg_batch_get_state(self.h, mesh_id, scen, _dp(H), _dp(Hu), _dp(Hv),
+                                                  C.byref(t), C.byref(steps)))
+        return H, Hu, Hv, t.value, steps.value
+
+    def step(self, n: int) -> None:
+        _bcheck(self.h, load().vg_batch_step(self.h, int(n)))
+
+    def run(self, t_end: float, max_steps: int = 10 ** 9) -> int:
+        taken = C.c_int64()
+        _bcheck(self.h, load().vg_batch_run(self.h, float(t_end), int(max_steps), C.byref(taken)))
+        return taken.value
+
+    def autotune(self, n_steps: int = 4):
+        blk = C.c_int32()
+        ms = C.c_double()
+        _bcheck(self.h, load().vg_batch_autotune(self.h, int(n_steps), C.byref(blk), C.byref(ms)))
+        return blk.value, ms.value
+
+    def info(self) -> dict:
+        nm, ns = C.c_int32(), C.c_int32()
+        cells, launches = C.c_int64(), C.c_int64()
+        _bcheck(self.h, load().vg_batch_info(self.h, C.byref(nm), C.byref(ns), C.byref(cells),
+                                             C.byref(launches)))
+        return dict(meshes=nm.value, scenarios=ns.value, cells=cells.value, launches=launches.value)

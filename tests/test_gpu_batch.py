@@ -1,0 +1,121 @@
+"""Batched ensembles (vg_batch_*) against one context per scenario and the oracle.
+
+The batch runs the same per-block arithmetic as a single context, so each
+scenario's result must equal its own single-context run bit for bit (same
+precision, same block size); FP64 scenarios also match the oracle within the
+FP64 parity tolerance.
+"""
+import numpy as np
+import pytest
+
+from paper_2002_04889_gb300 import inputs as I
+from paper_2002_04889_gb300 import volna
+from gpu_helpers import FIELDS, oracle_run, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _meshes():
+    # three coast basins of uneven size (about 2.9k, 6.5k and 12k triangles)
+    return [I.coast_mesh_with_cells(n, seed=k) for k, n in enumerate((3000, 6500, 12000))]
+
+
+def _scenarios(mesh, k, n):
+    out = []
+    for amp, ang in I.ensemble_sources(k, n):
+        s = I.coast_initial_state(mesh, amplitude=amp, angle_deg=ang)
+        out.append(s)
+    return out
+
+
+def _single(mesh, s, precision, n_steps=None, t_end=None):
+    with volna.Solver(precision) as sv:
+        sv.set_params(h_threshold=1e-3, cfl=0.9)
+        sv.upload_mesh(mesh)
+        sv.set_state(s.H, s.Hu, s.Hv, 0.0)
+        if t_end is not None:
+            sv.advance_to(t_end)
+        else:
+            sv.step(n_steps)
+        return sv.get_state()
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_batch_equals_single_contexts(precision):
+    meshes = _meshes()
+    nscen = 3
+    scen = [_scenarios(m, k, nscen) for k, m in enumerate(meshes)]
+    with volna.Batch(precision) as b:
+        b.set_params(h_threshold=1e-3, cfl=0.9)
+        ids = [b.add_mesh(m, nscen) for m in meshes]
+        for mid, ss in zip(ids, scen):
+            for j, s in enumerate(ss):
+                b.set_state(mid, j, s.H, s.Hu, s.Hv, 0.0)
+        info = b.info()
+        assert info["scenarios"] == 9 and info["cells"] == nscen * sum(m.nc for m in meshes)
+        b.step(25)
+        for mid, m, ss in zip(ids, meshes, scen):
+            for j, s in enumerate(ss):
+                H, Hu, Hv, t, steps = b.get_state(mid, j)
+                ref = _single(m, s, precision, n_steps=25)
+                assert steps == 25
+                assert t == ref[3]
+                for a, r in zip((H, Hu, Hv), ref[:3]):
+                    np.testing.assert_array_equal(a, r)
+    if precision == 64:
+        m, s = meshes[0], scen[0][1]
+        r = oracle_run(m, s, 25, h_threshold=1e-3, cfl=0.9)
+        ref = _single(m, s, 64, n_steps=25)
+        for f, g in zip(FIELDS, ref[:3]):
+            assert rel_l2(g, r[f]) <= 1e-10
+
+
+def test_batch_run_to_common_end_time():
+    """Each scenario keeps its own dt and stops exactly at t_end."""
+    meshes = _meshes()[:2]
+    scen = [_scenarios(m, k, 2) for k, m in enumerate(meshes)]
+    t_end = 30.0
+    with volna.Batch(64) as b:
+        b.set_params(h_threshold=1e-3, cfl=0.9)
+        ids = [b.add_mesh(m, 2) for m in meshes]
+        for mid, ss in zip(ids, scen):
+            for j, s in enumerate(ss):
+                b.set_state(mid, j, s.H, s.Hu, s.Hv, 0.0)
+        taken = b.run(t_end, max_steps=100000)
+        assert taken > 0
+        steps = []
+        for mid, m, ss in zip(ids, meshes, scen):
+            for j, s in enumerate(ss):
+                H, Hu, Hv, t, n = b.get_state(mid, j)
+                assert t == pytest.approx(t_end, abs=1e-12)
+                steps.append(n)
+                ref = _single(m, s, 64, t_end=t_end)
+                for a, r in zip((H, Hu, Hv), ref[:3]):
+                    assert rel_l2(a, r) <= 1e-12
+        assert len(set(steps)) > 1          # uneven meshes take different numbers of steps
+
+
+def test_batch_autotune_keeps_results():
+    meshes = _meshes()[:2]
+    scen = [_scenarios(m, k, 2) for k, m in enumerate(meshes)]
+    with volna.Batch(32) as b:
+        b.set_params(h_threshold=1e-3, cfl=0.9)
+        ids = [b.add_mesh(m, 2) for m in meshes]
+        for mid, ss in zip(ids, scen):
+            for j, s in enumerate(ss):
+                b.set_state(mid, j, s.H, s.Hu, s.Hv, 0.0)
+        before = [b.get_state(mid, j) for mid in ids for j in range(2)]
+        block, ms = b.autotune(3)
+        assert block in (64, 128, 256) and ms > 0
+        after = [b.get_state(mid, j) for mid in ids for j in range(2)]
+        for x, y in zip(before, after):               # the tuner restores the state
+            for a, c in zip(x[:3], y[:3]):
+                np.testing.assert_array_equal(a, c)
+            assert x[3] == y[3] == 0.0
+        b.step(10)
+        for mid, m, ss in zip(ids, meshes, scen):
+            for j, s in enumerate(ss):
+                H, Hu, Hv, t, _ = b.get_state(mid, j)
+                ref = _single(m, s, 32, n_steps=10)
+                for a, r in zip((H, Hu, Hv), ref[:3]):
+                    assert rel_l2(a, r) <= 1e-5
