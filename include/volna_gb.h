@@ -197,6 +197,40 @@ int vg_get_profile(vg_ctx *ctx, int32_t n, const char **names, int64_t *launches
 /* Bytes of device memory the context holds. */
 int vg_device_bytes(vg_ctx *ctx, int64_t *bytes);
 
+/*
+ * One time step that allocates no device memory.  The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc when they step
+ * -- a caller whose memory pool is fully reserved, a real-time loop that must
+ * not touch the allocator, or a framework that forbids device allocations
+ * after its set-up phase.
+ *
+ * The step's scratch (the stage-1 residual and the step scalars) lives in one
+ * file-scope device array of fixed size inside the library, so a mesh may have
+ * at most VG_NOALLOC_MAX_CELLS cells (VG_EINVAL otherwise).  Every GPU that
+ * loads the library holds that array (about 6 MiB) until the process exits.
+ *
+ *   ctx     a context with a mesh (vg_mesh_upload, vg_set_params); its state,
+ *           time, gauges and diagnostics are neither read nor changed
+ *   w_in    device array [3][nc] of the context's precision: the state at time t
+ *           in the library's internal cell order (vg_get_permutation gives
+ *           new_of_old) -- rows H, Hu, Hv for FP64 contexts; for FP32 contexts
+ *           the first row holds eta = H + z instead of H
+ *   w_out   device array of the same shape receiving the state after one step;
+ *           must not alias w_in
+ *   t       time of w_in (for the t_end clamp)
+ *   dt_out  host pointer receiving the step's dt (may be NULL)
+ *
+ * Work runs on the context's stream; the call waits for it.  All calls share
+ * the scratch array and leave the last call's contents in it; each call clears
+ * the scalars it needs before its kernels run, but calls that overlap on the
+ * GPU (other streams or host threads) race on the array.  The first call on a
+ * device looks up the array's device address with that device current and
+ * caches it, so make that first call before any stream capture.  Returns
+ * VG_ENONFINITE or VG_ENEGDEPTH (with params.strict_positivity) like vg_step.
+ */
+#define VG_NOALLOC_MAX_CELLS 262144
+int vg_step_noalloc(vg_ctx *ctx, const void *w_in, void *w_out, double t, double *dt_out);
+
 
 /* ------------------------------------------------------------------------
  * Batched ensembles (uncertainty quantification): many scenarios -- initial

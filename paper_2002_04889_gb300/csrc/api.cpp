@@ -860,4 +860,49 @@ int vg_device_bytes(vg_ctx *c, int64_t *bytes)
     return VG_OK;
 }
 
+// One step whose scratch is the library's fixed device array (noalloc.cu):
+// the ordinary stage kernels run with R0 and the step scalars pointed there.
+int vg_step_noalloc(vg_ctx *c, const void *w_in, void *w_out, double t, double *dt_out)
+{
+    if (!c) return VG_EINVAL;
+    if (!w_in || !w_out || w_in == w_out) return fail(c, VG_EINVAL, "w_in and w_out must be distinct device arrays");
+    if (!std::isfinite(t)) return fail(c, VG_EINVAL, "t must be finite");
+    if (!c->has_mesh) return fail(c, VG_ESTATE, "no mesh");
+    if (c->hm.nc > VG_NOALLOC_MAX_CELLS)
+        return fail(c, VG_EINVAL, "vg_step_noalloc handles at most " + std::to_string(VG_NOALLOC_MAX_CELLS) +
+                                      " cells; this mesh has " + std::to_string(c->hm.nc));
+    DeviceGuard guard(c->device);
+    void *scratch = nullptr;
+    size_t bytes = 0;
+    int e = noalloc_scratch(c->device, &scratch, &bytes);
+    if (e) return cuda_fail(c, (cudaError_t)e, "cudaGetSymbolAddress of the no-allocation scratch");
+    DevScalars *sc = static_cast<DevScalars *>(scratch);
+    DevPtrs d = dev_ptrs(c);
+    d.sc = sc;
+    d.R0 = static_cast<unsigned char *>(scratch) + 256;
+    d.n_gauges = 0;
+    d.gauge_cells = nullptr;
+    d.ring_t = nullptr;
+    d.ring_eta = nullptr;
+    StepParams p = step_params(c);
+    void *s = (void *)c->stream;
+    if ((e = noalloc_launch_init(sc, t, c->precision, s))) return cuda_fail(c, (cudaError_t)e, "scratch init launch");
+    e = c->precision == 64 ? launch_stage1_f64(d, p, w_in, c->cfg1, s) : launch_stage1_f32(d, p, w_in, c->cfg1, s);
+    if (e) return cuda_fail(c, (cudaError_t)e, "stage 1 launch");
+    e = c->precision == 64 ? launch_stage2_f64(d, p, w_in, w_out, c->cfg2, s)
+                           : launch_stage2_f32(d, p, w_in, w_out, c->cfg2, s);
+    if (e) return cuda_fail(c, (cudaError_t)e, "stage 2 launch");
+    if ((e = launch_post_step(d, p, w_out, c->precision, s))) return cuda_fail(c, (cudaError_t)e, "post-step launch");
+    c->launches += 4;
+    DevScalars r;
+    VG_CUDA(c, cudaMemcpyAsync(&r, sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    VG_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (dt_out) *dt_out = r.dt;
+    if (r.flags & FLAG_NONFINITE_STATE) return fail(c, VG_ENONFINITE, "a non-finite value appeared in the state");
+    if (r.flags & FLAG_NONFINITE_DT) return fail(c, VG_ENONFINITE, "the time step is not finite");
+    if (c->prm.strict_positivity && r.neg_count > 0)
+        return fail(c, VG_ENEGDEPTH, "a stage produced a negative depth (" + std::to_string(r.neg_count) + " cells)");
+    return VG_OK;
+}
+
 }  // extern "C"

@@ -141,6 +141,11 @@ int launch_import_state(const DevPtrs &d, const int32_t *old_of_new, const void 
                         const void *Hv, int src_is_double, void *w, int precision, void *stream);
 int launch_export_state(const DevPtrs &d, const int32_t *old_of_new, const void *w, int precision,
                         void *H, void *Hu, void *Hv, int dst_is_double, void *stream);
+// No-allocation step scratch (noalloc.cu): the device address and size of the
+// file-scope scratch array on `device`, and the kernel that clears its scalars.
+int noalloc_scratch(int device, void **addr, size_t *bytes);
+int noalloc_launch_init(void *scalars, double t, int precision, void *stream);
+
 int launch_diagnostics(const DevPtrs &d, const void *w, int precision, double hthr, double *part,
                        double *out, void *stream);
 

@@ -80,6 +80,7 @@ _SIGNATURES = {
     "vg_profile": ([_V, C.c_int], C.c_int),
     "vg_get_profile": ([_V, C.c_int32, C.POINTER(C.c_char_p), _I64, _D, _I32], C.c_int),
     "vg_device_bytes": ([_V, _I64], C.c_int),
+    "vg_step_noalloc": ([_V, _V, _V, C.c_double, _D], C.c_int),
     "vg_batch_create": ([C.POINTER(_V), C.c_int, C.c_int, _V], C.c_int),
     "vg_batch_destroy": ([_V], None),
     "vg_batch_last_error": ([_V], C.c_char_p),
@@ -93,6 +94,8 @@ _SIGNATURES = {
     "vg_batch_autotune": ([_V, C.c_int32, C.POINTER(C.c_int32), _D], C.c_int),
     "vg_batch_info": ([_V, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _I64, _I64], C.c_int),
 }
+
+VG_NOALLOC_MAX_CELLS = 262144
 
 
 def library_path() -> str:
@@ -272,6 +275,14 @@ def vg_device_bytes(ctx) -> int:
     b = C.c_int64()
     _check(ctx, load().vg_device_bytes(ctx, C.byref(b)))
     return b.value
+
+
+def vg_step_noalloc(ctx, w_in_ptr: int, w_out_ptr: int, t: float) -> float:
+    """One step on caller-owned device states ([3][nc], internal cell order) that
+    allocates no device memory; returns the step's dt."""
+    dt = C.c_double()
+    _check(ctx, load().vg_step_noalloc(ctx, _V(w_in_ptr), _V(w_out_ptr), float(t), C.byref(dt)))
+    return dt.value
 
 
 # ---------------------------------------------------------------- convenience wrapper
