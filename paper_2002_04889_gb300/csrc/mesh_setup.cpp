@@ -142,7 +142,10 @@ int prepare_mesh(int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
                  const double *depth_v, int renumber, int block, HostMesh &m, std::string &err)
 {
     if (nv < 3 || nc < 1 || !xy || !tri || !depth_v) { err = "empty mesh or NULL array"; return VG_EINVAL; }
-    if (nc > (int64_t)INT32_MAX / 3 || nv > (int64_t)INT32_MAX) { err = "mesh too large for int32 ids"; return VG_EINVAL; }
+    if (nc > (int64_t)INT32_MAX / GEO_ROWS || nv > (int64_t)INT32_MAX) {
+        err = "mesh too large: at most " + std::to_string((int64_t)INT32_MAX / GEO_ROWS) + " cells";
+        return VG_EINVAL;
+    }
     if (renumber < 0 || renumber > 2) { err = "renumber must be 0, 1 or 2"; return VG_EINVAL; }
     m = HostMesh();
     m.nc = nc;

@@ -197,11 +197,11 @@ template <> struct EtaForm<float> { static constexpr bool value = true; };
 // (negative depth emptied; at or below the threshold, momentum zeroed).
 // Returns true if a negative depth was met.
 template <typename real, int STAGE>
-__device__ __forceinline__ bool stage_state(const KArgs<real> &a, int64_t gid, real dt, real zc, real &W,
+__device__ __forceinline__ bool stage_state(const KArgs<real> &a, int gid, real dt, real zc, real &W,
                                             real &Hu, real &Hv)
 {
     constexpr bool ETA = EtaForm<real>::value;
-    const int64_t nc = a.nc;
+    const int nc = (int)a.nc;
     W = a.w[gid];
     Hu = a.w[nc + gid];
     Hv = a.w[2 * nc + gid];
@@ -320,7 +320,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
 
     const int B = a.block;
     const int L = B + a.max_halo;
-    const int64_t nc = a.nc;
+    const int nc = (int)a.nc;    // per-cell arrays hold < 2^31 entries (checked at upload)
     real *sH = reinterpret_cast<real *>(smem_raw);
     real *sHu = sH + L;
     real *sHv = sHu + L;
@@ -342,8 +342,8 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     const real g = a.g, half_g = a.half_g, hthr = a.hthr;
     const real *geo = a.geo;
 
-    const int64_t c0 = (int64_t)b * B;
-    const int ncell = (int)min((int64_t)B, nc - c0);
+    const int c0 = b * B;
+    const int ncell = min(B, nc - c0);
     const int h0 = a.halo_ptr[b];
     const int nh = a.halo_ptr[b + 1] - h0;
     const int n1 = a.halo_n1[b];
@@ -351,14 +351,14 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     // A: block + ring-1 + ring-2 states into shared memory
     for (int l = tid; l < B + nh; l += blockDim.x) {
         if (l < B && l >= ncell) continue;
-        int64_t gid = l < B ? c0 + l : (int64_t)a.halo_ids[h0 + (l - B)];
+        int gid = l < B ? c0 + l : a.halo_ids[h0 + (l - B)];
         real W, Hu, Hv;
         real zc = a.z[gid];
         bool neg = stage_state<real, STAGE>(a, gid, dt, zc, W, Hu, Hv);
         if (neg && l < B) my_neg++;
         sH[l] = W; sHu[l] = Hu; sHv[l] = Hv;
         sz[l] = zc;
-        sGid[l] = (int32_t)gid;
+        sGid[l] = gid;
     }
     if (tid == 0) qcount = 0;
     __syncthreads();
@@ -367,7 +367,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     // Barth-Jespersen limiter); every neighbour is in shared memory
     for (int l = tid; l < B + n1; l += blockDim.x) {
         if (l < B && l >= ncell) continue;
-        int64_t gid = sGid[l];
+        int gid = sGid[l];
         const real HuK = sHu[l], HvK = sHv[l], zK = sz[l];
         const real HK = ETA ? sH[l] - zK : sH[l];
         real qK[3] = {ETA ? sH[l] : HK + zK, HuK, HvK};
@@ -457,15 +457,19 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     }
     __syncthreads();
 
-    // C: owned faces, one flux each (Sec. 2.2)
+    // C: owned faces, one flux each (Sec. 2.2).  The thread of block cell tid
+    // keeps that cell's face codes and ownership bits for phase D.
+    uint16_t my_code[3] = {NBR_WALL, NBR_WALL, NBR_WALL};
+    int my_owned = 0;
     if (tid < ncell) {
-        int64_t gid = c0 + tid;
+        const int gid = c0 + tid;
         int items[3], n = 0;
 #pragma unroll
         for (int f = 0; f < 3; f++) {
             uint16_t code = a.nbrl[f * nc + gid];
+            my_code[f] = code;
             bool owned = code == NBR_WALL || (code >> 2) >= B || (int)(code >> 2) > tid;
-            if (owned) items[n++] = (tid << 2) | f;
+            if (owned) { items[n++] = (tid << 2) | f; my_owned |= 1 << f; }
         }
         if (n) {
             int pos = atomicAdd(&qcount, n);
@@ -477,7 +481,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     for (int q = tid; q < nq; q += blockDim.x) {
         int item = queue[q];
         int l = item >> 2, f = item & 3;
-        int64_t gid = c0 + l;
+        int gid = c0 + l;
         uint16_t code = a.nbrl[f * nc + gid];
         bool wall = code == NBR_WALL;
         real HfR = real(0), HufR = real(0), HvfR = real(0), zR = real(0);
@@ -506,12 +510,12 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     // D: residual R_K = -(1/|K|) sum_f l_f [Phi_f + (0, P_{K,f} n_f)], faces in local order
     if (tid < ncell) {
         const int l = tid;
-        const int64_t gid = c0 + l;
+        const int gid = c0 + l;
         real aH = real(0), aHu = real(0), aHv = real(0), am = real(0);
 #pragma unroll
         for (int f = 0; f < 3; f++) {
-            uint16_t code = a.nbrl[f * nc + gid];
-            bool owned = code == NBR_WALL || (code >> 2) >= B || (int)(code >> 2) > l;
+            const uint16_t code = my_code[f];
+            const bool owned = (my_owned >> f) & 1;
             real P0, P1, P2, P, sa;
             if (owned) {
                 int s = f * B + l;
