@@ -12,10 +12,32 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "volna_oracle.c")
+AD_SRC = os.path.join(HERE, "volna_oracle_ad.cpp")
+AD_HDR = os.path.join(HERE, "ad_tape.hpp")
 
 
 def library_path() -> str:
     return os.path.join(HERE, "_build", "libvolna_oracle.so")
+
+
+def ad_library_path() -> str:
+    return os.path.join(HERE, "_build", "libvolna_oracle_ad.so")
+
+
+def build_ad(verbose: bool = False) -> str:
+    """The oracle compiled with the taping scalar (its discrete adjoint); no OpenMP."""
+    out = ad_library_path()
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    newest = max(os.path.getmtime(f) for f in (SRC, AD_SRC, AD_HDR))
+    if os.path.exists(out) and os.path.getmtime(out) >= newest:
+        return out
+    cmd = ["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c++17",
+           "-o", out + ".tmp", AD_SRC, "-lm"]
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    subprocess.run(cmd, check=True)
+    os.replace(out + ".tmp", out)
+    return out
 
 
 def build(verbose: bool = False) -> str:
@@ -34,3 +56,4 @@ def build(verbose: bool = False) -> str:
 
 if __name__ == "__main__":
     print(build(verbose=True))
+    print(build_ad(verbose=True))

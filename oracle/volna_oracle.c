@@ -36,6 +36,14 @@
 #define VO_EINVAL (-1)
 #define VO_ENOMEM (-2)
 
+/* Scalar type of everything that depends on the water state or the bed.  It is
+   double here; the oracle's discrete adjoint compiles this same file with a
+   taping scalar type (oracle/volna_oracle_ad.cpp).  vo_val() is the value. */
+#ifndef VO_REAL_DEFINED
+typedef double vo_real;
+#define vo_val(x) (x)
+#endif
+
 typedef struct vo_params {
     double g;            /* gravity, m s^-2 (the paper does not state it: 9.81) */
     double cfl;          /* Courant number of the time-step rule            */
@@ -53,13 +61,14 @@ typedef struct vo_mesh {
     int32_t *vtx;        /* [nc][3] vertex ids in local order              */
     int32_t *nbr;        /* [nc][3] neighbour across face f, -1 = wall      */
     int32_t *nbr_face;   /* [nc][3] the same face seen from the neighbour   */
-    double *z, *area, *cx, *cy;                 /* [nc]                     */
+    vo_real *z;                                 /* [nc] bed                 */
+    double *area, *cx, *cy;                     /* [nc]                     */
     double *nx, *ny, *len, *fx, *fy;            /* [nc][3] per face         */
     double *dx, *dy, *wx, *wy;                  /* [nc][3] LSQ stencil      */
     /* work arrays of the residual */
-    double *Hf, *Huf, *Hvf;                     /* [nc][3] face values      */
-    double *slot;                               /* [nc][3][6] edge results  */
-    double *R0, *R1, *W1, *amax;                /* [3][nc], [3][nc], [3][nc], [nc] */
+    vo_real *Hf, *Huf, *Hvf;                    /* [nc][3] face values      */
+    vo_real *slot;                              /* [nc][3][6] edge results  */
+    vo_real *R0, *R1, *W1, *amax;               /* [3][nc], [3][nc], [3][nc], [nc] */
 } vo_mesh;
 
 void vo_set_threads(int n)
@@ -117,7 +126,7 @@ void vo_mesh_free(vo_mesh *m)
  * direction).
  */
 int vo_mesh_build(int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
-                  const double *depth_v, vo_mesh **out)
+                  const vo_real *depth_v, vo_mesh **out)
 {
     *out = NULL;
     if (nv < 3 || nc < 1 || !xy || !tri || !depth_v) return VO_EINVAL;
@@ -127,10 +136,11 @@ int vo_mesh_build(int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
     m->nc = nc;
     size_t n3 = (size_t)nc * 3;
 #define VO_ALLOC(p, n, T) do { (p) = (T *)malloc(sizeof(T) * (size_t)(n)); if (!(p)) { vo_mesh_free(m); return VO_ENOMEM; } } while (0)
+#define VO_ALLOC_R(p, n, T) VO_ALLOC(p, n, T)
     VO_ALLOC(m->vtx, n3, int32_t);
     VO_ALLOC(m->nbr, n3, int32_t);
     VO_ALLOC(m->nbr_face, n3, int32_t);
-    VO_ALLOC(m->z, nc, double);
+    VO_ALLOC_R(m->z, nc, vo_real);
     VO_ALLOC(m->area, nc, double);
     VO_ALLOC(m->cx, nc, double);
     VO_ALLOC(m->cy, nc, double);
@@ -143,14 +153,14 @@ int vo_mesh_build(int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
     VO_ALLOC(m->dy, n3, double);
     VO_ALLOC(m->wx, n3, double);
     VO_ALLOC(m->wy, n3, double);
-    VO_ALLOC(m->Hf, n3, double);
-    VO_ALLOC(m->Huf, n3, double);
-    VO_ALLOC(m->Hvf, n3, double);
-    VO_ALLOC(m->slot, n3 * 6, double);
-    VO_ALLOC(m->R0, n3, double);
-    VO_ALLOC(m->R1, n3, double);
-    VO_ALLOC(m->W1, n3, double);
-    VO_ALLOC(m->amax, nc, double);
+    VO_ALLOC_R(m->Hf, n3, vo_real);
+    VO_ALLOC_R(m->Huf, n3, vo_real);
+    VO_ALLOC_R(m->Hvf, n3, vo_real);
+    VO_ALLOC_R(m->slot, n3 * 6, vo_real);
+    VO_ALLOC_R(m->R0, n3, vo_real);
+    VO_ALLOC_R(m->R1, n3, vo_real);
+    VO_ALLOC_R(m->W1, n3, vo_real);
+    VO_ALLOC_R(m->amax, nc, vo_real);
 
     /* orientation and local order */
     for (int64_t c = 0; c < nc; c++) {
@@ -284,10 +294,10 @@ int vo_mesh_build(int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
  * *amax receives max(|s_L|, |s_R|).
  */
 /* The two HLL wave speeds (s_L, s_R) of the normal-frame states; see below. */
-void vo_hll_speeds(double g, double HL, double unL, double HR, double unR, double s[2])
+void vo_hll_speeds(double g, vo_real HL, vo_real unL, vo_real HR, vo_real unR, vo_real s[2])
 {
-    double cL = sqrt(g * HL);
-    double cR = sqrt(g * HR);
+    vo_real cL = sqrt(g * HL);
+    vo_real cR = sqrt(g * HR);
     if (HL == 0.0) {
         s[0] = unR - 2.0 * cR;
         s[1] = unR + cR;
@@ -295,33 +305,33 @@ void vo_hll_speeds(double g, double HL, double unL, double HR, double unR, doubl
         s[0] = unL - cL;
         s[1] = unL + 2.0 * cL;
     } else {
-        double us = 0.5 * (unL + unR) + (cL - cR);
-        double cs = 0.5 * (cL + cR) - 0.25 * (unR - unL);
+        vo_real us = 0.5 * (unL + unR) + (cL - cR);
+        vo_real cs = 0.5 * (cL + cR) - 0.25 * (unR - unL);
         s[0] = fmin(unL - cL, us - cs);
         s[1] = fmax(us + cs, unR + cR);
     }
 }
 
-void vo_hll_normal(double g, double HL, double unL, double utL,
-                   double HR, double unR, double utR, double F[3], double *amax)
+void vo_hll_normal(double g, vo_real HL, vo_real unL, vo_real utL,
+                   vo_real HR, vo_real unR, vo_real utR, vo_real F[3], vo_real *amax)
 {
     if (HL == 0.0 && HR == 0.0) {
         F[0] = 0.0; F[1] = 0.0; F[2] = 0.0;
         *amax = 0.0;
         return;
     }
-    double s[2];
+    vo_real s[2];
     vo_hll_speeds(g, HL, unL, HR, unR, s);
-    double sL = s[0], sR = s[1];
-    double qL = HL * unL, qR = HR * unR;
-    double FL[3] = {qL, qL * unL + 0.5 * g * HL * HL, qL * utL};
-    double FR[3] = {qR, qR * unR + 0.5 * g * HR * HR, qR * utR};
-    double wL[3] = {HL, qL, HL * utL};
-    double wR[3] = {HR, qR, HR * utR};
+    vo_real sL = s[0], sR = s[1];
+    vo_real qL = HL * unL, qR = HR * unR;
+    vo_real FL[3] = {qL, qL * unL + 0.5 * g * HL * HL, qL * utL};
+    vo_real FR[3] = {qR, qR * unR + 0.5 * g * HR * HR, qR * utR};
+    vo_real wL[3] = {HL, qL, HL * utL};
+    vo_real wR[3] = {HR, qR, HR * utR};
     if (sL >= 0.0) {
         for (int k = 0; k < 3; k++) F[k] = FL[k];
     } else if (sR >= 0.0) {
-        double den = sR - sL;
+        vo_real den = sR - sL;
         for (int k = 0; k < 3; k++)
             F[k] = ((sR * FL[k] - sL * FR[k]) + (sL * sR) * (wR[k] - wL[k])) / den;
     } else {
@@ -342,16 +352,16 @@ void vo_hll_normal(double g, double HL, double unL, double utL,
  * pressure corrections P_s = g (H_{s,f}^2 - H*_s^2) / 2 and the wave speed.
  */
 void vo_face_flux(double g, double hthr,
-                  double HfL, double HufL, double HvfL, double zL,
-                  double HfR, double HufR, double HvfR, double zR,
+                  vo_real HfL, vo_real HufL, vo_real HvfL, vo_real zL,
+                  vo_real HfR, vo_real HufR, vo_real HvfR, vo_real zR,
                   double nx, double ny, int wall,
-                  double Phi[3], double *PL, double *PR, double *amax)
+                  vo_real Phi[3], vo_real *PL, vo_real *PR, vo_real *amax)
 {
-    double uL = 0.0, vL = 0.0;
+    vo_real uL = 0.0, vL = 0.0;
     if (HfL > hthr) { uL = HufL / HfL; vL = HvfL / HfL; }
-    double unL = uL * nx + vL * ny;
-    double utL = -uL * ny + vL * nx;
-    double HsL, HsR, unR, utR;
+    vo_real unL = uL * nx + vL * ny;
+    vo_real utL = -uL * ny + vL * nx;
+    vo_real HsL, HsR, unR, utR;
     if (wall) {
         HsL = fmax(0.0, (HfL + zL) - zL);
         HsR = HsL;
@@ -359,15 +369,15 @@ void vo_face_flux(double g, double hthr,
         utR = utL;
         HfR = HfL;
     } else {
-        double uR = 0.0, vR = 0.0;
+        vo_real uR = 0.0, vR = 0.0;
         if (HfR > hthr) { uR = HufR / HfR; vR = HvfR / HfR; }
         unR = uR * nx + vR * ny;
         utR = -uR * ny + vR * nx;
-        double zs = fmax(zL, zR);
+        vo_real zs = fmax(zL, zR);
         HsL = fmax(0.0, (HfL + zL) - zs);
         HsR = fmax(0.0, (HfR + zR) - zs);
     }
-    double F[3];
+    vo_real F[3];
     vo_hll_normal(g, HsL, unL, utL, HsR, unR, utR, F, amax);
     Phi[0] = F[0];
     Phi[1] = F[1] * nx - F[2] * ny;
@@ -396,14 +406,14 @@ void vo_face_flux(double g, double hthr,
  *             D_f < 0, 1 if D_f = 0, with D_f = grad q . (x_f - x_K) and q_max,
  *             q_min over the cell and its stencil values.
  */
-void vo_reconstruct_cell(const vo_mesh *m, const vo_params *p, const double *H,
-                         const double *Hu, const double *Hv, int64_t K,
-                         double Hf[3], double Huf[3], double Hvf[3])
+void vo_reconstruct_cell(const vo_mesh *m, const vo_params *p, const vo_real *H,
+                         const vo_real *Hu, const vo_real *Hv, int64_t K,
+                         vo_real Hf[3], vo_real Huf[3], vo_real Hvf[3])
 {
     double hthr = p->h_threshold;
-    double zK = m->z[K];
-    double qK[3] = {H[K] + zK, Hu[K], Hv[K]};
-    double qn[3][3];
+    vo_real zK = m->z[K];
+    vo_real qK[3] = {H[K] + zK, Hu[K], Hv[K]};
+    vo_real qn[3][3];
     int recon = (p->order == 2) && (H[K] > hthr);
     for (int f = 0; f < 3; f++) {
         int64_t i = 3 * K + f;
@@ -414,33 +424,33 @@ void vo_reconstruct_cell(const vo_mesh *m, const vo_params *p, const double *H,
             qn[f][2] = Hv[j];
             if (!(H[j] > hthr)) recon = 0;
         } else {
-            double mn = Hu[K] * m->nx[i] + Hv[K] * m->ny[i];
+            vo_real mn = Hu[K] * m->nx[i] + Hv[K] * m->ny[i];
             qn[f][0] = qK[0];
             qn[f][1] = Hu[K] - 2.0 * mn * m->nx[i];
             qn[f][2] = Hv[K] - 2.0 * mn * m->ny[i];
         }
     }
     if (recon) {
-        double face[3][3];
+        vo_real face[3][3];
         for (int v = 0; v < 3; v++) {
             const double *wx = m->wx + 3 * K, *wy = m->wy + 3 * K;
-            double gx = (wx[0] * (qn[0][v] - qK[v]) + wx[1] * (qn[1][v] - qK[v])) + wx[2] * (qn[2][v] - qK[v]);
-            double gy = (wy[0] * (qn[0][v] - qK[v]) + wy[1] * (qn[1][v] - qK[v])) + wy[2] * (qn[2][v] - qK[v]);
-            double qmax = qK[v], qmin = qK[v];
+            vo_real gx = (wx[0] * (qn[0][v] - qK[v]) + wx[1] * (qn[1][v] - qK[v])) + wx[2] * (qn[2][v] - qK[v]);
+            vo_real gy = (wy[0] * (qn[0][v] - qK[v]) + wy[1] * (qn[1][v] - qK[v])) + wy[2] * (qn[2][v] - qK[v]);
+            vo_real qmax = qK[v], qmin = qK[v];
             for (int f = 0; f < 3; f++) {
                 qmax = fmax(qmax, qn[f][v]);
                 qmin = fmin(qmin, qn[f][v]);
             }
-            double alpha = 1.0;
+            vo_real alpha = 1.0;
             for (int f = 0; f < 3; f++) {
-                double D = gx * m->fx[3 * K + f] + gy * m->fy[3 * K + f];
-                double phi = 1.0;
+                vo_real D = gx * m->fx[3 * K + f] + gy * m->fy[3 * K + f];
+                vo_real phi = 1.0;
                 if (D > 0.0) phi = fmin(1.0, (qmax - qK[v]) / D);
                 else if (D < 0.0) phi = fmin(1.0, (qmin - qK[v]) / D);
                 alpha = fmin(alpha, phi);
             }
             for (int f = 0; f < 3; f++) {
-                double D = gx * m->fx[3 * K + f] + gy * m->fy[3 * K + f];
+                vo_real D = gx * m->fx[3 * K + f] + gy * m->fy[3 * K + f];
                 face[f][v] = qK[v] + alpha * D;
             }
         }
@@ -482,8 +492,8 @@ static int owns(const vo_mesh *m, int64_t K, int f)
  * of K (the owner's edge flux, negated for the other cell) and P_{K,f} the
  * pressure correction on K's side.  amax[K] = max_f l_f a_f (NULL: skipped).
  */
-void vo_residual(vo_mesh *m, const vo_params *p, const double *H, const double *Hu,
-                 const double *Hv, double *RH, double *RHu, double *RHv, double *amax)
+void vo_residual(vo_mesh *m, const vo_params *p, const vo_real *H, const vo_real *Hu,
+                 const vo_real *Hv, vo_real *RH, vo_real *RHu, vo_real *RHv, vo_real *amax)
 {
     int64_t nc = m->nc;
     double g = p->g, hthr = p->h_threshold;
@@ -497,7 +507,7 @@ void vo_residual(vo_mesh *m, const vo_params *p, const double *H, const double *
             if (!owns(m, K, f)) continue;
             int64_t i = 3 * K + f;
             int32_t j = m->nbr[i];
-            double *s = m->slot + 6 * i;
+            vo_real *s = m->slot + 6 * i;
             if (j >= 0) {
                 int64_t k = 3 * (int64_t)j + m->nbr_face[i];
                 vo_face_flux(g, hthr, m->Hf[i], m->Huf[i], m->Hvf[i], m->z[K],
@@ -512,15 +522,15 @@ void vo_residual(vo_mesh *m, const vo_params *p, const double *H, const double *
 
 #pragma omp parallel for schedule(static)
     for (int64_t K = 0; K < nc; K++) {
-        double aH = 0.0, aHu = 0.0, aHv = 0.0, am = 0.0;
+        vo_real aH = 0.0, aHu = 0.0, aHv = 0.0, am = 0.0;
         for (int f = 0; f < 3; f++) {
             int64_t i = 3 * K + f;
-            double P0, P1, P2, P, a;
+            vo_real P0, P1, P2, P, a;
             if (owns(m, K, f)) {
-                const double *s = m->slot + 6 * i;
+                const vo_real *s = m->slot + 6 * i;
                 P0 = s[0]; P1 = s[1]; P2 = s[2]; P = s[3]; a = s[5];
             } else {
-                const double *s = m->slot + 6 * (3 * (int64_t)m->nbr[i] + m->nbr_face[i]);
+                const vo_real *s = m->slot + 6 * (3 * (int64_t)m->nbr[i] + m->nbr_face[i]);
                 P0 = -s[0]; P1 = -s[1]; P2 = -s[2]; P = s[4]; a = s[5];
             }
             double l = m->len[i];
@@ -543,7 +553,7 @@ void vo_residual(vo_mesh *m, const vo_params *p, const double *H, const double *
  * the time left before t_end (if > 0).  dt_fixed > 0 replaces the CFL rule.
  * With no moving wave anywhere the step is dt_max (0 when unset).
  */
-double vo_time_step(const vo_mesh *m, const vo_params *p, const double *amax, double t)
+double vo_time_step(const vo_mesh *m, const vo_params *p, const vo_real *amax, double t)
 {
     double dt;
     if (p->dt_fixed > 0.0) {
@@ -551,7 +561,7 @@ double vo_time_step(const vo_mesh *m, const vo_params *p, const double *amax, do
     } else {
         double mn = INFINITY;
         for (int64_t K = 0; K < m->nc; K++)
-            if (amax[K] > 0.0) mn = fmin(mn, m->area[K] / (3.0 * amax[K]));
+            if (vo_val(amax[K]) > 0.0) mn = fmin(mn, m->area[K] / (3.0 * vo_val(amax[K])));
         dt = isinf(mn) ? (p->dt_max > 0.0 ? p->dt_max : 0.0) : p->cfl * mn;
     }
     if (p->dt_max > 0.0) dt = fmin(dt, p->dt_max);
@@ -562,7 +572,7 @@ double vo_time_step(const vo_mesh *m, const vo_params *p, const double *amax, do
 
 /* After each stage: a negative depth is counted and the cell emptied; at or
    below H_threshold the momentum is zeroed. */
-static int64_t dry_fix(int64_t nc, double hthr, double *H, double *Hu, double *Hv)
+static int64_t dry_fix(int64_t nc, double hthr, vo_real *H, vo_real *Hu, vo_real *Hv)
 {
     int64_t neg = 0;
 #pragma omp parallel for schedule(static) reduction(+ : neg)
@@ -583,12 +593,12 @@ static int64_t dry_fix(int64_t nc, double hthr, double *H, double *Hu, double *H
  * the same dt in both stages, each stage followed by the dry fix.
  * *t advances by dt; *dt_out and *neg_count (added to) report the step.
  */
-void vo_step(vo_mesh *m, const vo_params *p, double *H, double *Hu, double *Hv,
+void vo_step(vo_mesh *m, const vo_params *p, vo_real *H, vo_real *Hu, vo_real *Hv,
              double *t, double *dt_out, int64_t *neg_count)
 {
     int64_t nc = m->nc;
-    double *R0 = m->R0, *R1 = m->R1, *W1 = m->W1;
-    double *H1 = W1, *Hu1 = W1 + nc, *Hv1 = W1 + 2 * nc;
+    vo_real *R0 = m->R0, *R1 = m->R1, *W1 = m->W1;
+    vo_real *H1 = W1, *Hu1 = W1 + nc, *Hv1 = W1 + 2 * nc;
     vo_residual(m, p, H, Hu, Hv, R0, R0 + nc, R0 + 2 * nc, m->amax);
     double dt = vo_time_step(m, p, m->amax, *t);
 #pragma omp parallel for schedule(static)
@@ -614,9 +624,9 @@ void vo_step(vo_mesh *m, const vo_params *p, double *H, double *Hu, double *Hv,
 /* n steps; dts (may be NULL) receives each step's dt.  Gauges (may be NULL):
    eta at the n_gauges cells gauge_cells[] after every step into
    gauge_eta[step][g].  Returns the number of steps taken. */
-int64_t vo_run(vo_mesh *m, const vo_params *p, double *H, double *Hu, double *Hv,
+int64_t vo_run(vo_mesh *m, const vo_params *p, vo_real *H, vo_real *Hu, vo_real *Hv,
                double *t, int64_t n_steps, double *dts, int64_t *neg_count,
-               int32_t n_gauges, const int32_t *gauge_cells, double *gauge_eta)
+               int32_t n_gauges, const int32_t *gauge_cells, vo_real *gauge_eta)
 {
     for (int64_t s = 0; s < n_steps; s++) {
         double dt;

@@ -1,0 +1,81 @@
+"""Pins of the oracle's discrete adjoint (tape AD of the oracle's arithmetic)
+against finite differences of the oracle's forward run (FP64).
+
+J is piecewise smooth: the min/max of the wave speeds (Sec. 2.2) and of the
+Barth-Jespersen limiter (Sec. 2.4) switch, and near-equal neighbour states put
+such kinks close together, so the step is small (1e-8).  The adjoint must match
+the central difference; if a kink still lies inside the step (MUSCL only), it
+must lie between the two one-sided differences.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2002_04889_gb300 import inputs as I
+
+
+def _setup(n=12, n_steps=15):
+    m = I.thacker_mesh(n=n, half_width=1.2)
+    s = I.thacker_initial_state(m)
+    om = O.OracleMesh.from_mesh(m)
+    gauges = np.array([[0.0, 0.0], [0.3, 0.1], [-0.2, 0.25], [0.1, -0.4]])
+    cells = om.locate(gauges)
+    dx = 2.4 / n
+    dt = 0.1 * dx
+    rng = np.random.default_rng(5)
+    w = rng.normal(size=(n_steps + 1, len(cells)))
+    # momentum only where the water is deep (velocities stay moderate), and in both
+    # components: an identically zero field sits on the limiter's D = 0 branch, where
+    # the directional derivative exists but is not linear in the direction
+    deep = s.H > 2e-2
+    p = m.cell_points()
+    st = (s.H, s.Hu + 1e-3 * np.sin(3 * p[:, 0]) * deep, s.Hv + 1e-3 * np.cos(2 * p[:, 1]) * deep)
+    return m, st, cells, dt, n_steps, w
+
+
+def _J(m, state, depth, cells, dt, n_steps, w, order=2):
+    om = O.OracleMesh(m.xy, m.tri, depth)
+    r = om.run(O.params(dt_fixed=dt, order=order), (state[0], state[1], state[2], 0.0), n_steps,
+               gauge_cells=cells)
+    z = om.get("z")
+    eta0 = state[0][cells] + z[cells]
+    return float(np.sum(w[0] * eta0) + np.sum(w[1:] * r["gauges"]))
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_oracle_adjoint_matches_forward_and_finite_differences(order):
+    m, st, cells, dt, n_steps, w = _setup()
+    ad = O.ad_gauge_gradient(m, st, dt, n_steps, cells, w, h_threshold=1e-5, order=order)
+    J0 = _J(m, st, m.depth, cells, dt, n_steps, w, order)
+    assert ad["J"] == pytest.approx(J0, rel=1e-13, abs=1e-15)      # the taped run is the oracle's run
+    rng = np.random.default_rng(7)
+    wet = st[0] > 1e-3
+    eps = 1e-8             # kinks (Zhou speeds, limiter) are dense: a small step stays on one piece
+    n_central = 0
+    for kind in ("H", "Hu", "Hv", "depth"):
+        for _ in range(4):
+            if kind == "depth":
+                d = rng.normal(size=m.nv)
+                grad_dot = float(np.dot(ad["ddepth"], d))
+            else:
+                d = rng.normal(size=m.nc) * wet
+                grad_dot = float(np.dot(ad["d" + kind + "0"], d))
+
+            def shifted(e):
+                if kind == "depth":
+                    return _J(m, st, m.depth + e * d, cells, dt, n_steps, w, order)
+                k = ("H", "Hu", "Hv").index(kind)
+                stt = [a.copy() for a in st]
+                stt[k] = stt[k] + e * d
+                return _J(m, stt, m.depth, cells, dt, n_steps, w, order)
+            jp, jm = shifted(eps), shifted(-eps)
+            fd = (jp - jm) / (2 * eps)
+            tol = 2e-6 * max(1.0, abs(fd))
+            if abs(grad_dot - fd) <= tol:
+                n_central += 1
+                continue
+            assert order == 2, (kind, grad_dot, fd)
+            fwd, bwd = (jp - J0) / eps, (J0 - jm) / eps
+            lo, hi = min(fwd, bwd) - tol, max(fwd, bwd) + tol
+            assert lo <= grad_dot <= hi, (kind, grad_dot, fwd, bwd)
+    assert n_central >= 12
