@@ -233,6 +233,41 @@ int vg_step_noalloc(vg_ctx *ctx, const void *w_in, void *w_out, double t, double
 
 
 /* ------------------------------------------------------------------------
+ * Discrete adjoint (FP64 contexts).  With a fixed time step dt, the run of
+ * n_steps SSP-RK(2,2) steps (Sec. 2.3) from the current state is a smooth map
+ * almost everywhere (branches -- wet/dry switches, limiter and wave-speed
+ * choices, HLL regions -- frozen where the run takes them), and the gauge
+ * records eta_g(t_n) = H + z of the gauge cells (Sec. 3 gauges) are outputs of
+ * it.  vg_adj_backward returns the gradient of any scalar J(eta) given
+ * dJ/deta, with respect to the initial state and the bathymetry.
+ * ------------------------------------------------------------------------ */
+
+/* Replace the per-vertex bathymetry depth (as in vg_mesh_upload) of the
+   uploaded mesh; the cell beds are recomputed.  The state is unchanged. */
+int vg_set_depth(vg_ctx *ctx, const double *depth_v);
+
+/*
+ * Forward run for the adjoint: n_steps steps with the fixed time step dt from
+ * the current state, recording the gauges at the start and after every step
+ * (vg_get_gauges then returns n_steps + 1 records).  The state at every
+ * checkpoint_every-th step is kept on the device (0: ceil(sqrt(n_steps)), the
+ * sqrt(N) checkpointing that bounds memory by about 2 sqrt(N) states while
+ * vg_adj_backward recomputes each segment once).  The context's state
+ * advances to step n_steps.
+ */
+int vg_adj_forward(vg_ctx *ctx, int64_t n_steps, double dt, int64_t checkpoint_every);
+
+/*
+ * Reverse sweep of the last vg_adj_forward run.  dJ_deta[n_steps + 1][G] is the
+ * derivative of J with respect to each gauge record.  Outputs (host FP64,
+ * original cell / vertex order; any may be NULL): dJ/dH0, dJ/dHu0, dJ/dHv0 [nc]
+ * for the initial state, dJ/dz [nc] for the cell beds, dJ/ddepth [nv] for the
+ * vertex depths (z = -mean of its three vertex depths).
+ */
+int vg_adj_backward(vg_ctx *ctx, const double *dJ_deta, double *dJ_dH0, double *dJ_dHu0, double *dJ_dHv0,
+                    double *dJ_dz, double *dJ_ddepth);
+
+/* ------------------------------------------------------------------------
  * Batched ensembles (uncertainty quantification): many scenarios -- initial
  * states of the same scheme -- on several meshes of uneven size, advanced
  * together.  Each scenario has its own time and its own CFL time step; one

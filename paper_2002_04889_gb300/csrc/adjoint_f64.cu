@@ -1,0 +1,584 @@
+// Hand-written discrete adjoint of the FP64 step (reverse mode), built with
+// --fmad=false like the FP64 forward kernels.
+//
+// The residual R = L(w; z) of Sec. 2 is reversed in four kernels, each thread
+// owning what it writes (no atomics, fixed summation order):
+//   adj_face_values   forward face values FV[3 vars][3 faces][nc] at w
+//   adj_flux_vjp      per owned face: Phi-bar, P-bar from R-bar of both cells,
+//                     reverse of the interface (hydrostatic depths, HLL with its
+//                     branch and speed choices, velocities) -> FV-bar and z-bar
+//                     into the (cell, face) slots of both sides
+//   adj_recon_vjp     per cell: reverse of the limited least-squares
+//                     reconstruction -> the cell's own w-bar, z-bar, and what it
+//                     sends to each face neighbour ((cell, face) slots)
+//   adj_gather        per cell: own part + the slots its neighbours sent to it
+// Branches are frozen where the forward run took them; min/max ties resolve to
+// the first argument (the convention of the oracle's taping adjoint).
+// Around them, elementwise kernels reverse the SSP-RK(2,2) stage updates, the
+// dry fixes and the gauge functional.
+#include <cuda_runtime.h>
+
+#include "step_kernels.cuh"
+
+namespace vg {
+
+namespace {
+
+struct AdjMesh {
+    int nc, order;
+    const double *geo;       // [GEO_ROWS][nc]
+    const double *z;         // [nc]
+    const int32_t *nbr;      // [3][nc]
+    const uint16_t *nbrl;    // [3][nc]: low 2 bits = neighbour's face (not a wall)
+    double g, half_g, hthr;
+};
+
+__device__ __forceinline__ double G(const AdjMesh &m, int row, int k) { return m.geo[row * m.nc + k]; }
+
+// Forward reconstruction of cell K (the same evaluation order as the forward
+// kernels), keeping what the reverse needs.
+struct ReconFwd {
+    double qK[3], qn[3][3];
+    bool wall[3];
+    bool recon;
+    double D[3][3];          // [v][f]
+    double alpha[3];
+    int fa[3];               // face whose phi is the active limiter (-1: alpha = 1)
+    int imax[3], imin[3];    // stencil index of q_max / q_min (-1 = the cell)
+    double r[3];             // q_max - q_K or q_min - q_K of the active face
+};
+
+__device__ void recon_forward(const AdjMesh &m, const double *w, int K, ReconFwd &R, double Hf[3],
+                              double Huf[3], double Hvf[3])
+{
+    const int nc = m.nc;
+    const double *H = w, *Hu = w + nc, *Hv = w + 2 * (size_t)nc;
+    double zK = m.z[K];
+    double HK = H[K], HuK = Hu[K], HvK = Hv[K];
+    R.qK[0] = HK + zK;
+    R.qK[1] = HuK;
+    R.qK[2] = HvK;
+    bool recon = (m.order == 2) && (HK > m.hthr);
+    for (int f = 0; f < 3; f++) {
+        int j = m.nbr[f * nc + K];
+        R.wall[f] = j < 0;
+        if (j >= 0) {
+            R.qn[f][0] = H[j] + m.z[j];
+            R.qn[f][1] = Hu[j];
+            R.qn[f][2] = Hv[j];
+            if (!(H[j] > m.hthr)) recon = false;
+        } else {
+            double nx = G(m, GEO_NX + f, K), ny = G(m, GEO_NY + f, K);
+            double mn = HuK * nx + HvK * ny;
+            R.qn[f][0] = R.qK[0];
+            R.qn[f][1] = HuK - 2.0 * mn * nx;
+            R.qn[f][2] = HvK - 2.0 * mn * ny;
+        }
+    }
+    if (recon) {
+        double face[3][3];
+        for (int v = 0; v < 3; v++) {
+            double d0 = R.qn[0][v] - R.qK[v], d1 = R.qn[1][v] - R.qK[v], d2 = R.qn[2][v] - R.qK[v];
+            double gx = (G(m, GEO_WX, K) * d0 + G(m, GEO_WX + 1, K) * d1) + G(m, GEO_WX + 2, K) * d2;
+            double gy = (G(m, GEO_WY, K) * d0 + G(m, GEO_WY + 1, K) * d1) + G(m, GEO_WY + 2, K) * d2;
+            double qmax = R.qK[v], qmin = R.qK[v];
+            int imax = -1, imin = -1;
+            for (int f = 0; f < 3; f++) {
+                if (R.qn[f][v] > qmax) { qmax = R.qn[f][v]; imax = f; }
+                if (R.qn[f][v] < qmin) { qmin = R.qn[f][v]; imin = f; }
+            }
+            double alpha = 1.0;
+            int fa = -1;
+            double ra = 0.0;
+            for (int f = 0; f < 3; f++) {
+                double D = gx * G(m, GEO_FX + f, K) + gy * G(m, GEO_FY + f, K);
+                R.D[v][f] = D;
+                double phi = 1.0, rr = 0.0;
+                bool lim = false;
+                if (D > 0.0) { rr = qmax - R.qK[v]; double t = rr / D; if (t < 1.0) { phi = t; lim = true; } }
+                else if (D < 0.0) { rr = qmin - R.qK[v]; double t = rr / D; if (t < 1.0) { phi = t; lim = true; } }
+                if (phi < alpha) { alpha = phi; fa = lim ? f : -1; ra = rr; }
+            }
+            R.alpha[v] = alpha;
+            R.fa[v] = fa;
+            R.r[v] = ra;
+            R.imax[v] = imax;
+            R.imin[v] = imin;
+            for (int f = 0; f < 3; f++) face[f][v] = R.qK[v] + alpha * R.D[v][f];
+        }
+        for (int f = 0; f < 3; f++) {
+            Hf[f] = face[f][0] - zK;
+            if (!(Hf[f] > m.hthr)) recon = false;
+            Huf[f] = face[f][1];
+            Hvf[f] = face[f][2];
+        }
+    }
+    R.recon = recon;
+    if (!recon) {
+        for (int f = 0; f < 3; f++) { Hf[f] = HK; Huf[f] = HuK; Hvf[f] = HvK; }
+    }
+}
+
+__global__ void adj_face_values_kernel(AdjMesh m, const double *w, double *FV)
+{
+    const int nc = m.nc;
+    for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < nc; K += gridDim.x * blockDim.x) {
+        ReconFwd R;
+        double Hf[3], Huf[3], Hvf[3];
+        recon_forward(m, w, K, R, Hf, Huf, Hvf);
+        for (int f = 0; f < 3; f++) {
+            FV[(0 * 3 + f) * (size_t)nc + K] = Hf[f];
+            FV[(1 * 3 + f) * (size_t)nc + K] = Huf[f];
+            FV[(2 * 3 + f) * (size_t)nc + K] = Hvf[f];
+        }
+    }
+}
+
+// Reverse of the face flux seen from L (forward: face_flux / hll_normal).
+// Inputs: the two face states, beds, normal, wall flag, and the adjoints of
+// Phi[3], P_L, P_R.  Outputs: adjoints of (H_f, Hu_f, Hv_f, z) on each side.
+__device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL, double zL, double HfR,
+                         double HufR, double HvfR, double zR, double nx, double ny, bool wall,
+                         const double Pb[3], double PLb, double PRb, double bL[4], double bR[4])
+{
+    const double g = m.g, hg = m.half_g, hthr = m.hthr;
+    for (int k = 0; k < 4; k++) { bL[k] = 0.0; bR[k] = 0.0; }
+    // ---- forward
+    double uL = 0.0, vL = 0.0;
+    bool velL = HfL > hthr;
+    if (velL) { uL = HufL / HfL; vL = HvfL / HfL; }
+    double unL = uL * nx + vL * ny;
+    double utL = -uL * ny + vL * nx;
+    double HsL, HsR, unR, utR, uR = 0.0, vR = 0.0, zs = 0.0;
+    bool velR = false, zR_max = false, actL, actR = false;
+    double xL, xR = 0.0;
+    if (wall) {
+        xL = (HfL + zL) - zL;
+        actL = xL > 0.0;
+        HsL = actL ? xL : 0.0;
+        HsR = HsL;
+        unR = -unL;
+        utR = utL;
+    } else {
+        velR = HfR > hthr;
+        if (velR) { uR = HufR / HfR; vR = HvfR / HfR; }
+        unR = uR * nx + vR * ny;
+        utR = -uR * ny + vR * nx;
+        zR_max = zR > zL;
+        zs = zR_max ? zR : zL;
+        xL = (HfL + zL) - zs;
+        xR = (HfR + zR) - zs;
+        actL = xL > 0.0;
+        actR = xR > 0.0;
+        HsL = actL ? xL : 0.0;
+        HsR = actR ? xR : 0.0;
+    }
+    // ---- reverse of the rotation and pressure terms
+    double Fb0 = Pb[0];
+    double Fb1 = Pb[1] * nx + Pb[2] * ny;
+    double Fb2 = -Pb[1] * ny + Pb[2] * nx;
+    double HfLb = PLb * hg * 2.0 * HfL, HsLb = -PLb * hg * 2.0 * HsL;
+    double HfRb = 0.0, HsRb = 0.0;
+    if (!wall) { HfRb = PRb * hg * 2.0 * HfR; HsRb = -PRb * hg * 2.0 * HsR; }
+    double unLb = 0.0, utLb = 0.0, unRb = 0.0, utRb = 0.0;
+    // ---- reverse of HLL
+    if (!(HsL == 0.0 && HsR == 0.0)) {
+        double cL = sqrt(g * HsL), cR = sqrt(g * HsR);
+        double sL, sR, us = 0.0, cs = 0.0;
+        int case_ = 0;    // 0 both wet, 1 L dry, 2 R dry
+        bool sL_first = true, sR_first = true;
+        if (HsL == 0.0) {
+            case_ = 1;
+            sL = unR - 2.0 * cR;
+            sR = unR + cR;
+        } else if (HsR == 0.0) {
+            case_ = 2;
+            sL = unL - cL;
+            sR = unL + 2.0 * cL;
+        } else {
+            us = 0.5 * (unL + unR) + (cL - cR);
+            cs = 0.5 * (cL + cR) - 0.25 * (unR - unL);
+            double a1 = unL - cL, a2 = us - cs;
+            sL_first = !(a2 < a1);
+            sL = sL_first ? a1 : a2;
+            double b1 = us + cs, b2 = unR + cR;
+            sR_first = !(b2 > b1);
+            sR = sR_first ? b1 : b2;
+        }
+        double qL = HsL * unL, qR = HsR * unR;
+        double FL[3] = {qL, qL * unL + hg * HsL * HsL, qL * utL};
+        double FR[3] = {qR, qR * unR + hg * HsR * HsR, qR * utR};
+        double wL[3] = {HsL, qL, HsL * utL};
+        double wR[3] = {HsR, qR, HsR * utR};
+        double Fb[3] = {Fb0, Fb1, Fb2};
+        double FLb[3] = {0, 0, 0}, FRb[3] = {0, 0, 0}, wLb[3] = {0, 0, 0}, wRb[3] = {0, 0, 0};
+        double sLb = 0.0, sRb = 0.0;
+        if (sL >= 0.0) {
+            for (int k = 0; k < 3; k++) FLb[k] = Fb[k];
+        } else if (sR >= 0.0) {
+            double den = sR - sL, sLR = sL * sR;
+            double denb = 0.0, sLRb = 0.0;
+            for (int k = 0; k < 3; k++) {
+                double N = (sR * FL[k] - sL * FR[k]) + sLR * (wR[k] - wL[k]);
+                double F = N / den;
+                double Nb = Fb[k] / den;
+                denb -= Fb[k] * F / den;
+                FLb[k] += Nb * sR;
+                FRb[k] -= Nb * sL;
+                sRb += Nb * FL[k];
+                sLb -= Nb * FR[k];
+                sLRb += Nb * (wR[k] - wL[k]);
+                wRb[k] += Nb * sLR;
+                wLb[k] -= Nb * sLR;
+            }
+            sLb += sLRb * sR;
+            sRb += sLRb * sL;
+            sRb += denb;
+            sLb -= denb;
+        } else {
+            for (int k = 0; k < 3; k++) FRb[k] = Fb[k];
+        }
+        // physical fluxes and conserved variables -> (Hs, q, un, ut)
+        double qLb = FLb[0] + FLb[1] * unL + FLb[2] * utL + wLb[1];
+        unLb += FLb[1] * qL;
+        HsLb += FLb[1] * 2.0 * hg * HsL + wLb[0] + wLb[2] * utL;
+        utLb += FLb[2] * qL + wLb[2] * HsL;
+        HsLb += qLb * unL;
+        unLb += qLb * HsL;
+        double qRb = FRb[0] + FRb[1] * unR + FRb[2] * utR + wRb[1];
+        unRb += FRb[1] * qR;
+        HsRb += FRb[1] * 2.0 * hg * HsR + wRb[0] + wRb[2] * utR;
+        utRb += FRb[2] * qR + wRb[2] * HsR;
+        HsRb += qRb * unR;
+        unRb += qRb * HsR;
+        // speeds
+        double cLb = 0.0, cRb = 0.0;
+        if (case_ == 1) {
+            unRb += sLb + sRb;
+            cRb += -2.0 * sLb + sRb;
+        } else if (case_ == 2) {
+            unLb += sLb + sRb;
+            cLb += -sLb + 2.0 * sRb;
+        } else {
+            double usb = 0.0, csb = 0.0;
+            if (sL_first) { unLb += sLb; cLb -= sLb; } else { usb += sLb; csb -= sLb; }
+            if (sR_first) { usb += sRb; csb += sRb; } else { unRb += sRb; cRb += sRb; }
+            unLb += 0.5 * usb;
+            unRb += 0.5 * usb;
+            cLb += usb;
+            cRb -= usb;
+            cLb += 0.5 * csb;
+            cRb += 0.5 * csb;
+            unRb -= 0.25 * csb;
+            unLb += 0.25 * csb;
+        }
+        if (cL > 0.0) HsLb += cLb * (0.5 / cL) * g;
+        if (cR > 0.0) HsRb += cRb * (0.5 / cR) * g;
+    }
+    // ---- reverse of the interface depths and velocities
+    if (wall) {
+        unLb -= unRb;
+        utLb += utRb;
+        HsLb += HsRb;
+        if (actL) { HfLb += HsLb; bL[3] += HsLb; bL[3] -= HsLb; }
+    } else {
+        double zsb = 0.0;
+        if (actL) { HfLb += HsLb; bL[3] += HsLb; zsb -= HsLb; }
+        if (actR) { HfRb += HsRb; bR[3] += HsRb; zsb -= HsRb; }
+        if (zR_max) bR[3] += zsb; else bL[3] += zsb;
+        double uRb = unRb * nx - utRb * ny, vRb = unRb * ny + utRb * nx;
+        if (velR) {
+            bR[1] += uRb / HfR;
+            bR[2] += vRb / HfR;
+            HfRb -= (uRb * uR + vRb * vR) / HfR;
+        }
+    }
+    double uLb = unLb * nx - utLb * ny, vLb = unLb * ny + utLb * nx;
+    if (velL) {
+        bL[1] += uLb / HfL;
+        bL[2] += vLb / HfL;
+        HfLb -= (uLb * uL + vLb * vL) / HfL;
+    }
+    bL[0] += HfLb;
+    bR[0] += HfRb;
+}
+
+// Per owned face: R-bar of both cells -> Phi-bar, P-bar -> face-state adjoints.
+// FVb[(v*3+f)*nc + K] and zfb[f*nc + K] are the (cell, face) slots; each is
+// written exactly once per residual.
+__global__ void adj_flux_vjp_kernel(AdjMesh m, const double *FV, const double *Rb, double *FVb, double *zfb)
+{
+    const int nc = m.nc;
+    for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < nc; K += gridDim.x * blockDim.x) {
+        for (int f = 0; f < 3; f++) {
+            int j = m.nbr[f * nc + K];
+            if (j >= 0 && j < K) continue;      // the lower-numbered cell owns the face
+            bool wall = j < 0;
+            int fj = wall ? 0 : (m.nbrl[f * nc + K] & 3);
+            double nx = G(m, GEO_NX + f, K), ny = G(m, GEO_NY + f, K), l = G(m, GEO_LEN + f, K);
+            double aL = G(m, GEO_AREA, K);
+            double cLf = -l / aL;
+            double Pb[3], PLb, PRb = 0.0;
+            double RLH = Rb[K], RLU = Rb[nc + K], RLV = Rb[2 * (size_t)nc + K];
+            Pb[0] = cLf * RLH;
+            Pb[1] = cLf * RLU;
+            Pb[2] = cLf * RLV;
+            PLb = cLf * (RLU * nx + RLV * ny);
+            double HfR = 0.0, HufR = 0.0, HvfR = 0.0, zR = 0.0;
+            if (!wall) {
+                double cRf = l / G(m, GEO_AREA, j);
+                double RRH = Rb[j], RRU = Rb[nc + j], RRV = Rb[2 * (size_t)nc + j];
+                Pb[0] += cRf * RRH;
+                Pb[1] += cRf * RRU;
+                Pb[2] += cRf * RRV;
+                PRb = cRf * (RRU * nx + RRV * ny);
+                HfR = FV[(0 * 3 + fj) * (size_t)nc + j];
+                HufR = FV[(1 * 3 + fj) * (size_t)nc + j];
+                HvfR = FV[(2 * 3 + fj) * (size_t)nc + j];
+                zR = m.z[j];
+            }
+            double bL[4], bR[4];
+            flux_vjp(m, FV[(0 * 3 + f) * (size_t)nc + K], FV[(1 * 3 + f) * (size_t)nc + K],
+                     FV[(2 * 3 + f) * (size_t)nc + K], m.z[K], HfR, HufR, HvfR, zR, nx, ny, wall, Pb, PLb, PRb, bL, bR);
+            for (int v = 0; v < 3; v++) FVb[(v * 3 + f) * (size_t)nc + K] = bL[v];
+            zfb[f * (size_t)nc + K] = bL[3];
+            if (!wall) {
+                for (int v = 0; v < 3; v++) FVb[(v * 3 + fj) * (size_t)nc + j] = bR[v];
+                zfb[fj * (size_t)nc + j] = bR[3];
+            }
+        }
+    }
+}
+
+// Per cell: reverse of the reconstruction.  own[4][nc] = (H, Hu, Hv, z)-bar of
+// the cell itself (including the flux slots' z-bar); send[(f*4+k)*nc + K] = the
+// (H, Hu, Hv, z)-bar that cell K passes to its face-f neighbour.
+__global__ void adj_recon_vjp_kernel(AdjMesh m, const double *w, const double *FVb, const double *zfb, double *own,
+                                     double *send)
+{
+    const int nc = m.nc;
+    for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < nc; K += gridDim.x * blockDim.x) {
+        ReconFwd R;
+        double Hf[3], Huf[3], Hvf[3];
+        recon_forward(m, w, K, R, Hf, Huf, Hvf);
+        double fb[3][3];   // [v][f]
+        for (int v = 0; v < 3; v++)
+            for (int f = 0; f < 3; f++) fb[v][f] = FVb[(v * 3 + f) * (size_t)nc + K];
+        double Hb = 0.0, Hub = 0.0, Hvb = 0.0, zb = 0.0;
+        for (int f = 0; f < 3; f++) zb += zfb[f * (size_t)nc + K];
+        double qnb[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};   // [f][v]
+        if (!R.recon) {
+            for (int f = 0; f < 3; f++) { Hb += fb[0][f]; Hub += fb[1][f]; Hvb += fb[2][f]; }
+        } else {
+            double qKb[3] = {0, 0, 0};
+            for (int f = 0; f < 3; f++) zb -= fb[0][f];      // H_f = eta_f - z_K
+            for (int v = 0; v < 3; v++) {
+                double ab = 0.0, Db[3];
+                for (int f = 0; f < 3; f++) {
+                    qKb[v] += fb[v][f];
+                    ab += fb[v][f] * R.D[v][f];
+                    Db[f] = fb[v][f] * R.alpha[v];
+                }
+                int fa = R.fa[v];
+                if (fa >= 0) {
+                    double D = R.D[v][fa];
+                    double rb = ab / D;
+                    Db[fa] -= ab * R.r[v] / (D * D);
+                    int idx = D > 0.0 ? R.imax[v] : R.imin[v];
+                    if (idx < 0) qKb[v] += rb; else qnb[idx][v] += rb;
+                    qKb[v] -= rb;
+                }
+                double gxb = 0.0, gyb = 0.0;
+                for (int f = 0; f < 3; f++) {
+                    gxb += Db[f] * G(m, GEO_FX + f, K);
+                    gyb += Db[f] * G(m, GEO_FY + f, K);
+                }
+                for (int f = 0; f < 3; f++) {
+                    double db = gxb * G(m, GEO_WX + f, K) + gyb * G(m, GEO_WY + f, K);
+                    qnb[f][v] += db;
+                    qKb[v] -= db;
+                }
+            }
+            for (int f = 0; f < 3; f++) {
+                if (!R.wall[f]) continue;
+                double nx = G(m, GEO_NX + f, K), ny = G(m, GEO_NY + f, K);
+                qKb[0] += qnb[f][0];
+                double mnb = -2.0 * nx * qnb[f][1] - 2.0 * ny * qnb[f][2];
+                Hub += qnb[f][1] + mnb * nx;
+                Hvb += qnb[f][2] + mnb * ny;
+                qnb[f][0] = qnb[f][1] = qnb[f][2] = 0.0;
+            }
+            Hb += qKb[0];
+            zb += qKb[0];
+            Hub += qKb[1];
+            Hvb += qKb[2];
+        }
+        own[K] = Hb;
+        own[nc + K] = Hub;
+        own[2 * (size_t)nc + K] = Hvb;
+        own[3 * (size_t)nc + K] = zb;
+        for (int f = 0; f < 3; f++) {
+            send[(f * 4 + 0) * (size_t)nc + K] = qnb[f][0];     // eta-bar -> H-bar and z-bar
+            send[(f * 4 + 1) * (size_t)nc + K] = qnb[f][1];
+            send[(f * 4 + 2) * (size_t)nc + K] = qnb[f][2];
+            send[(f * 4 + 3) * (size_t)nc + K] = qnb[f][0];
+        }
+    }
+}
+
+// wb[3][nc] += own + sum over faces of what the face neighbour sent; zb[nc] likewise.
+__global__ void adj_gather_kernel(AdjMesh m, const double *own, const double *send, double *wb, double *zb)
+{
+    const int nc = m.nc;
+    for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < nc; K += gridDim.x * blockDim.x) {
+        double a[4] = {own[K], own[nc + K], own[2 * (size_t)nc + K], own[3 * (size_t)nc + K]};
+        for (int f = 0; f < 3; f++) {
+            int j = m.nbr[f * nc + K];
+            if (j < 0) continue;
+            int fj = m.nbrl[f * nc + K] & 3;
+            for (int k = 0; k < 4; k++) a[k] += send[(fj * 4 + k) * (size_t)nc + j];
+        }
+        wb[K] += a[0];
+        wb[nc + K] += a[1];
+        wb[2 * (size_t)nc + K] += a[2];
+        zb[K] += a[3];
+    }
+}
+
+// Dry fix after a stage (forward: H < 0 empties the cell; H <= H_threshold zeroes
+// the momentum): its adjoint masks the incoming adjoint.
+__device__ __forceinline__ void dry_fix_mask(double Hpre, double hthr, double &Hb, double &Hub, double &Hvb)
+{
+    if (Hpre < 0.0) { Hb = 0.0; Hub = 0.0; Hvb = 0.0; }
+    else if (Hpre <= hthr) { Hub = 0.0; Hvb = 0.0; }
+}
+
+// w1 = fix(w + dt R0), keeping the pre-fix depth for the mask.
+__global__ void adj_stage1_kernel(int nc, double dt, double hthr, const double *w, const double *R0, double *w1,
+                                  double *H1pre)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nc; k += gridDim.x * blockDim.x) {
+        double H = w[k] + dt * R0[k];
+        double Hu = w[nc + k] + dt * R0[nc + k];
+        double Hv = w[2 * (size_t)nc + k] + dt * R0[2 * (size_t)nc + k];
+        H1pre[k] = H;
+        if (H < 0.0) { H = 0.0; Hu = 0.0; Hv = 0.0; }
+        else if (H <= hthr) { Hu = 0.0; Hv = 0.0; }
+        w1[k] = H;
+        w1[nc + k] = Hu;
+        w1[2 * (size_t)nc + k] = Hv;
+    }
+}
+
+// Reverse of stage 2: w^{n+1} = fix(w/2 + (w1 + dt R1)/2).  From wb (adjoint of
+// w^{n+1}) form wb_n = 1/2 wbpre, wb_1 = 1/2 wbpre, Rb = dt/2 wbpre.
+__global__ void adj_stage2_rev_kernel(int nc, double dt, double hthr, const double *w, const double *w1,
+                                      const double *R1, const double *wb, double *wbn, double *wb1, double *Rb)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nc; k += gridDim.x * blockDim.x) {
+        double Hpre = 0.5 * w[k] + 0.5 * (w1[k] + dt * R1[k]);
+        double b0 = wb[k], b1 = wb[nc + k], b2 = wb[2 * (size_t)nc + k];
+        dry_fix_mask(Hpre, hthr, b0, b1, b2);
+        double b[3] = {b0, b1, b2};
+        for (int c = 0; c < 3; c++) {
+            wbn[c * (size_t)nc + k] = 0.5 * b[c];
+            wb1[c * (size_t)nc + k] = 0.5 * b[c];
+            Rb[c * (size_t)nc + k] = 0.5 * dt * b[c];
+        }
+    }
+}
+
+// Reverse of stage 1: w1 = fix(w + dt R0).  wbn += wb1pre, Rb = dt wb1pre.
+__global__ void adj_stage1_rev_kernel(int nc, double dt, double hthr, const double *H1pre, const double *wb1,
+                                      double *wbn, double *Rb)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nc; k += gridDim.x * blockDim.x) {
+        double b0 = wb1[k], b1 = wb1[nc + k], b2 = wb1[2 * (size_t)nc + k];
+        dry_fix_mask(H1pre[k], hthr, b0, b1, b2);
+        double b[3] = {b0, b1, b2};
+        for (int c = 0; c < 3; c++) {
+            wbn[c * (size_t)nc + k] += b[c];
+            Rb[c * (size_t)nc + k] = dt * b[c];
+        }
+    }
+}
+
+// Gauge functional J = sum weights * (H + z) at the gauge cells: its adjoint.
+__global__ void adj_gauge_kernel(int n_gauges, const int32_t *cells, const double *weights, int nc, double *wb,
+                                 double *zb)
+{
+    // serial over gauges: two gauges may share a cell
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int g = 0; g < n_gauges; g++) {
+            int c = cells[g];
+            wb[c] += weights[g];
+            zb[c] += weights[g];
+        }
+    (void)nc;
+}
+
+int grid_of(int n) { return (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096; }
+
+AdjMesh adj_mesh(const DevPtrs &d, const StepParams &p)
+{
+    AdjMesh m;
+    m.nc = (int)d.nc;
+    m.order = p.order;
+    m.geo = static_cast<const double *>(d.geo);
+    m.z = static_cast<const double *>(d.z);
+    m.nbr = d.nbr;
+    m.nbrl = d.nbrl;
+    m.g = p.g;
+    m.half_g = 0.5 * p.g;
+    m.hthr = p.hthr;
+    return m;
+}
+
+}  // namespace
+
+// Adds the VJP of the residual at w: (wb, zb) += (dR/dw, dR/dz)^T Rb.
+// Scratch: FV, FVb [9][nc], zfb [3][nc], own [4][nc], send [12][nc].
+int adjoint_residual_vjp(const DevPtrs &d, const StepParams &p, const double *w, const double *Rb, double *wb,
+                         double *zb, double *FV, double *FVb, double *zfb, double *own, double *send, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    AdjMesh m = adj_mesh(d, p);
+    int grid = grid_of(m.nc);
+    adj_face_values_kernel<<<grid, 256, 0, s>>>(m, w, FV);
+    adj_flux_vjp_kernel<<<grid, 256, 0, s>>>(m, FV, Rb, FVb, zfb);
+    adj_recon_vjp_kernel<<<grid, 256, 0, s>>>(m, w, FVb, zfb, own, send);
+    adj_gather_kernel<<<grid, 256, 0, s>>>(m, own, send, wb, zb);
+    return (int)cudaGetLastError();
+}
+
+int adjoint_stage1(int nc, double dt, double hthr, const double *w, const double *R0, double *w1, double *H1pre,
+                   void *stream)
+{
+    adj_stage1_kernel<<<grid_of(nc), 256, 0, static_cast<cudaStream_t>(stream)>>>(nc, dt, hthr, w, R0, w1, H1pre);
+    return (int)cudaGetLastError();
+}
+
+int adjoint_stage2_rev(int nc, double dt, double hthr, const double *w, const double *w1, const double *R1,
+                       const double *wb, double *wbn, double *wb1, double *Rb, void *stream)
+{
+    adj_stage2_rev_kernel<<<grid_of(nc), 256, 0, static_cast<cudaStream_t>(stream)>>>(nc, dt, hthr, w, w1, R1, wb,
+                                                                                       wbn, wb1, Rb);
+    return (int)cudaGetLastError();
+}
+
+int adjoint_stage1_rev(int nc, double dt, double hthr, const double *H1pre, const double *wb1, double *wbn,
+                       double *Rb, void *stream)
+{
+    adj_stage1_rev_kernel<<<grid_of(nc), 256, 0, static_cast<cudaStream_t>(stream)>>>(nc, dt, hthr, H1pre, wb1, wbn,
+                                                                                       Rb);
+    return (int)cudaGetLastError();
+}
+
+int adjoint_gauge(int n_gauges, const int32_t *cells, const double *weights, int nc, double *wb, double *zb,
+                  void *stream)
+{
+    adj_gauge_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(n_gauges, cells, weights, nc, wb, zb);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace vg

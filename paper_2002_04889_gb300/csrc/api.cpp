@@ -57,6 +57,10 @@ struct vg_ctx {
     bool graph_dirty = true;
     int64_t launches = 0;
 
+    // discrete adjoint: checkpoints of the last vg_adj_forward run
+    std::vector<void *> ckpt;
+    int64_t adj_n = 0, adj_every = 0;
+    double adj_dt = 0.0;
     bool profile = false;
     double prof_ms[kKernels] = {0, 0, 0};
     int64_t prof_n[kKernels] = {0, 0, 0};
@@ -110,8 +114,16 @@ void dfree(T *&p)
     p = nullptr;
 }
 
+void free_adjoint(vg_ctx *c)
+{
+    for (void *p : c->ckpt) cudaFree(p);
+    c->ckpt.clear();
+    c->adj_n = 0;
+}
+
 void free_mesh(vg_ctx *c)
 {
+    free_adjoint(c);
     if (c->graph2) { cudaGraphExecDestroy(c->graph2); c->graph2 = nullptr; }
     if (c->z64 == c->z) c->z64 = nullptr;
     dfree(c->geo); dfree(c->z); dfree(c->z64); dfree(c->w[0]); dfree(c->w[1]); dfree(c->R0);
@@ -851,6 +863,192 @@ int vg_get_profile(vg_ctx *c, int32_t n, const char **names, int64_t *launches, 
     }
     if (n_out) *n_out = kKernels;
     return VG_OK;
+}
+
+int vg_set_depth(vg_ctx *c, const double *depth_v)
+{
+    if (!c || !depth_v) return VG_EINVAL;
+    if (!c->has_mesh) return fail(c, VG_ESTATE, "no mesh");
+    DeviceGuard guard(c->device);
+    HostMesh &m = c->hm;
+    std::vector<double> zo(m.nc);
+    for (int64_t o = 0; o < m.nc; o++) {
+        const int32_t *v = &m.vtx[3 * o];
+        zo[o] = -((depth_v[v[0]] + depth_v[v[1]]) + depth_v[v[2]]) / 3.0;
+        if (!std::isfinite(zo[o])) return fail(c, VG_EINVAL, "non-finite depth");
+    }
+    for (int64_t k = 0; k < m.nc; k++) m.z[k] = zo[m.old_of_new[k]];
+    cudaStreamSynchronize(c->stream);
+    int rc = upload_real(c, c->z, m.z.data(), m.z.size());
+    if (rc) return rc;
+    if (c->precision != 64) VG_CUDA(c, cudaMemcpy(c->z64, m.z.data(), 8 * m.nc, cudaMemcpyHostToDevice));
+    c->graph_dirty = true;
+    return VG_OK;
+}
+
+int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_every)
+{
+    if (!c || n_steps < 1 || !(dt > 0) || checkpoint_every < 0) return VG_EINVAL;
+    if (c->precision != 64) return fail(c, VG_EINVAL, "the adjoint runs in FP64 contexts");
+    if (!c->has_mesh || !c->has_state) return fail(c, VG_ESTATE, "mesh and state must be set");
+    if (c->n_gauges < 1) return fail(c, VG_ESTATE, "the adjoint differentiates gauge records: set gauges first");
+    DeviceGuard guard(c->device);
+    free_adjoint(c);
+    int64_t C = checkpoint_every ? checkpoint_every : (int64_t)std::ceil(std::sqrt((double)n_steps));
+    int64_t nck = (n_steps + C - 1) / C;
+    size_t bytes = 8 * 3 * (size_t)c->hm.nc;
+    for (int64_t k = 0; k < nck; k++) {
+        void *p = nullptr;
+        int rc = dmalloc(c, &p, bytes);
+        if (rc) { free_adjoint(c); return rc; }
+        c->ckpt.push_back(p);
+    }
+    vg_params saved = c->prm;
+    c->prm.dt_fixed = dt;
+    c->prm.t_end = 0.0;
+    c->prm.gauge_every = 1;
+    c->graph_dirty = true;
+    // restart the gauge record at the current state
+    DevScalars s;
+    int rc = read_scalars(c, s);
+    if (!rc) rc = drain_gauges(c, s);
+    c->rec_t.clear();
+    c->rec_eta.clear();
+    if (!rc) rc = record_now(c);
+    for (int64_t n = 0; n < n_steps && !rc; n++) {
+        if (n % C == 0) {
+            cudaError_t e = cudaMemcpyAsync(c->ckpt[n / C], c->w[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream);
+            if (e != cudaSuccess) { rc = cuda_fail(c, e, "checkpoint copy"); break; }
+        }
+        if ((rc = enqueue_step(c, c->cur))) break;
+        c->cur = 1 - c->cur;
+        c->launches += kKernels;
+        if ((n + 1) % 1024 == 0) {
+            if ((rc = read_scalars(c, s))) break;
+            if ((rc = drain_gauges(c, s))) break;
+        }
+    }
+    if (!rc) rc = read_scalars(c, s);
+    if (!rc) rc = drain_gauges(c, s);
+    if (!rc) rc = check_flags(c, s, 0);
+    c->prm = saved;
+    c->graph_dirty = true;
+    if (rc) { free_adjoint(c); return rc; }
+    c->adj_n = n_steps;
+    c->adj_every = C;
+    c->adj_dt = dt;
+    return VG_OK;
+}
+
+int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ_dHu0, double *dJ_dHv0,
+                    double *dJ_dz, double *dJ_ddepth)
+{
+    if (!c || !dJ_deta) return VG_EINVAL;
+    if (c->adj_n < 1) return fail(c, VG_ESTATE, "call vg_adj_forward first");
+    DeviceGuard guard(c->device);
+    const int64_t N = c->adj_n, C = c->adj_every;
+    const int nc = (int)c->hm.nc, G = c->n_gauges;
+    const size_t w3 = 3 * (size_t)nc;
+    // scratch (freed at the end)
+    std::vector<void *> bufs;
+    auto alloc = [&](size_t n_doubles, double **p) {
+        void *q = nullptr;
+        int rc = dmalloc(c, &q, 8 * n_doubles);
+        if (!rc) { bufs.push_back(q); *p = static_cast<double *>(q); }
+        return rc;
+    };
+    double *W, *wb, *wbn, *wb1, *zb, *Rb, *R0, *R1, *w1, *H1pre, *FV, *FVb, *zfb, *own, *send, *seg;
+    int rc = 0;
+    if ((rc = alloc((size_t)(N + 1) * G, &W)) || (rc = alloc(w3, &wb)) || (rc = alloc(w3, &wbn)) ||
+        (rc = alloc(w3, &wb1)) || (rc = alloc(nc, &zb)) || (rc = alloc(w3, &Rb)) || (rc = alloc(w3, &R0)) ||
+        (rc = alloc(w3, &R1)) || (rc = alloc(w3, &w1)) || (rc = alloc(nc, &H1pre)) || (rc = alloc(9 * (size_t)nc, &FV)) ||
+        (rc = alloc(9 * (size_t)nc, &FVb)) || (rc = alloc(3 * (size_t)nc, &zfb)) || (rc = alloc(4 * (size_t)nc, &own)) ||
+        (rc = alloc(12 * (size_t)nc, &send)) || (rc = alloc(w3 * (size_t)C, &seg))) {
+        for (void *q : bufs) cudaFree(q);
+        return rc;
+    }
+    DevScalars *asc = nullptr;
+    if ((rc = dmalloc(c, (void **)&asc, sizeof(DevScalars)))) {
+        for (void *q : bufs) cudaFree(q);
+        return rc;
+    }
+    bufs.push_back(asc);
+    DevScalars s0;
+    reset_scalars_host(c, s0, 0.0);
+    StepParams p = step_params(c);
+    p.dt_fixed = c->adj_dt;
+    p.t_end = 0.0;
+    p.dt_max = 0.0;
+    const double dt = c->adj_dt, hthr = p.hthr;
+    void *st = (void *)c->stream;
+    DevPtrs d = dev_ptrs(c);
+    d.sc = asc;
+    d.n_gauges = 0;
+    auto fwd_residual = [&](const double *w, double *R) -> int {
+        DevPtrs dd = d;
+        dd.R0 = R;
+        int e = launch_stage1_f64(dd, p, w, c->cfg1, st);
+        return e ? cuda_fail(c, (cudaError_t)e, "adjoint residual launch") : VG_OK;
+    };
+#define ADJ_CHECK(call) do { int e_ = (call); if (e_) { rc = cuda_fail(c, (cudaError_t)e_, #call); goto done; } } while (0)
+    {
+        VG_CUDA(c, cudaMemcpyAsync(asc, &s0, sizeof(s0), cudaMemcpyHostToDevice, c->stream));
+        VG_CUDA(c, cudaMemcpyAsync(W, dJ_deta, 8 * (size_t)(N + 1) * G, cudaMemcpyHostToDevice, c->stream));
+        VG_CUDA(c, cudaMemsetAsync(wb, 0, 8 * w3, c->stream));
+        VG_CUDA(c, cudaMemsetAsync(zb, 0, 8 * (size_t)nc, c->stream));
+        ADJ_CHECK(adjoint_gauge(G, c->gauge_cells, W + (size_t)N * G, nc, wb, zb, st));
+        int64_t nseg = (N + C - 1) / C;
+        for (int64_t sg = nseg - 1; sg >= 0; sg--) {
+            int64_t a = sg * C, b = std::min(a + C, N);
+            // recompute the states of this segment from its checkpoint
+            VG_CUDA(c, cudaMemcpyAsync(seg, c->ckpt[sg], 8 * w3, cudaMemcpyDeviceToDevice, c->stream));
+            for (int64_t n = a; n + 1 < b; n++) {
+                double *win = seg + (size_t)(n - a) * w3, *wout = win + w3;
+                DevPtrs dd = d;
+                dd.R0 = R0;
+                ADJ_CHECK(launch_stage1_f64(dd, p, win, c->cfg1, st));
+                ADJ_CHECK(launch_stage2_f64(dd, p, win, wout, c->cfg2, st));
+            }
+            for (int64_t n = b - 1; n >= a; n--) {
+                const double *w = seg + (size_t)(n - a) * w3;
+                if ((rc = fwd_residual(w, R0))) goto done;
+                ADJ_CHECK(adjoint_stage1(nc, dt, hthr, w, R0, w1, H1pre, st));
+                if ((rc = fwd_residual(w1, R1))) goto done;
+                ADJ_CHECK(adjoint_stage2_rev(nc, dt, hthr, w, w1, R1, wb, wbn, wb1, Rb, st));
+                ADJ_CHECK(adjoint_residual_vjp(d, p, w1, Rb, wb1, zb, FV, FVb, zfb, own, send, st));
+                ADJ_CHECK(adjoint_stage1_rev(nc, dt, hthr, H1pre, wb1, wbn, Rb, st));
+                ADJ_CHECK(adjoint_residual_vjp(d, p, w, Rb, wbn, zb, FV, FVb, zfb, own, send, st));
+                ADJ_CHECK(adjoint_gauge(G, c->gauge_cells, W + (size_t)n * G, nc, wbn, zb, st));
+                std::swap(wb, wbn);
+                c->launches += 14;
+            }
+        }
+        // internal -> original order on the host
+        std::vector<double> h(4 * (size_t)nc);
+        VG_CUDA(c, cudaMemcpyAsync(h.data(), wb, 8 * w3, cudaMemcpyDeviceToHost, c->stream));
+        VG_CUDA(c, cudaMemcpyAsync(h.data() + w3, zb, 8 * (size_t)nc, cudaMemcpyDeviceToHost, c->stream));
+        VG_CUDA(c, cudaStreamSynchronize(c->stream));
+        const std::vector<int32_t> &oon = c->hm.old_of_new;
+        std::vector<double> zo(nc);
+        for (int k = 0; k < nc; k++) {
+            int o = oon[k];
+            if (dJ_dH0) dJ_dH0[o] = h[k];
+            if (dJ_dHu0) dJ_dHu0[o] = h[nc + k];
+            if (dJ_dHv0) dJ_dHv0[o] = h[2 * (size_t)nc + k];
+            zo[o] = h[w3 + k];
+        }
+        if (dJ_dz) std::copy(zo.begin(), zo.end(), dJ_dz);
+        if (dJ_ddepth) {
+            std::fill(dJ_ddepth, dJ_ddepth + c->hm.nv, 0.0);
+            for (int o = 0; o < nc; o++)
+                for (int k = 0; k < 3; k++) dJ_ddepth[c->hm.vtx[3 * (size_t)o + k]] -= zo[o] / 3.0;
+        }
+    }
+done:
+#undef ADJ_CHECK
+    cudaStreamSynchronize(c->stream);
+    for (void *q : bufs) cudaFree(q);
+    return rc;
 }
 
 int vg_device_bytes(vg_ctx *c, int64_t *bytes)

@@ -134,6 +134,18 @@ int launch_batch_step_f32(const void *table, int n_mesh, int n_items, int n_entr
 int launch_batch_step_f64(const void *table, int n_mesh, int n_items, int n_entries, DevScalars *sc_all, int block,
                           int grid, size_t smem, const StepParams &p, void *stream);
 
+// Discrete adjoint (adjoint_f64.cu, FP64 contexts).
+int adjoint_residual_vjp(const DevPtrs &d, const StepParams &p, const double *w, const double *Rb, double *wb,
+                         double *zb, double *FV, double *FVb, double *zfb, double *own, double *send, void *stream);
+int adjoint_stage1(int nc, double dt, double hthr, const double *w, const double *R0, double *w1, double *H1pre,
+                   void *stream);
+int adjoint_stage2_rev(int nc, double dt, double hthr, const double *w, const double *w1, const double *R1,
+                       const double *wb, double *wbn, double *wb1, double *Rb, void *stream);
+int adjoint_stage1_rev(int nc, double dt, double hthr, const double *H1pre, const double *wb1, double *wbn,
+                       double *Rb, void *stream);
+int adjoint_gauge(int n_gauges, const int32_t *cells, const double *weights, int nc, double *wb, double *zb,
+                  void *stream);
+
 // Utility kernels (util_kernels.cu).
 int launch_post_step(const DevPtrs &d, const StepParams &p, const void *w, int precision, void *stream);
 int launch_record_gauges(const DevPtrs &d, const void *w, int precision, void *stream);

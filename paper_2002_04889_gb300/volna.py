@@ -81,6 +81,9 @@ _SIGNATURES = {
     "vg_get_profile": ([_V, C.c_int32, C.POINTER(C.c_char_p), _I64, _D, _I32], C.c_int),
     "vg_device_bytes": ([_V, _I64], C.c_int),
     "vg_step_noalloc": ([_V, _V, _V, C.c_double, _D], C.c_int),
+    "vg_set_depth": ([_V, _D], C.c_int),
+    "vg_adj_forward": ([_V, C.c_int64, C.c_double, C.c_int64], C.c_int),
+    "vg_adj_backward": ([_V, _D, _D, _D, _D, _D, _D], C.c_int),
     "vg_batch_create": ([C.POINTER(_V), C.c_int, C.c_int, _V], C.c_int),
     "vg_batch_destroy": ([_V], None),
     "vg_batch_last_error": ([_V], C.c_char_p),
@@ -285,6 +288,24 @@ def vg_step_noalloc(ctx, w_in_ptr: int, w_out_ptr: int, t: float) -> float:
     return dt.value
 
 
+def vg_set_depth(ctx, depth_v) -> None:
+    d = _f64(depth_v)
+    _check(ctx, load().vg_set_depth(ctx, _dp(d)))
+
+
+def vg_adj_forward(ctx, n_steps: int, dt: float, checkpoint_every: int = 0) -> None:
+    _check(ctx, load().vg_adj_forward(ctx, int(n_steps), float(dt), int(checkpoint_every)))
+
+
+def vg_adj_backward(ctx, dJ_deta, nc: int, nv: int) -> dict:
+    w = _f64(dJ_deta)
+    out = {k: np.empty(nc) for k in ("H0", "Hu0", "Hv0", "z")}
+    out["depth"] = np.empty(nv)
+    _check(ctx, load().vg_adj_backward(ctx, _dp(w), _dp(out["H0"]), _dp(out["Hu0"]), _dp(out["Hv0"]),
+                                       _dp(out["z"]), _dp(out["depth"])))
+    return out
+
+
 # ---------------------------------------------------------------- convenience wrapper
 
 
@@ -397,6 +418,17 @@ class Solver:
 
     def device_bytes(self) -> int:
         return vg_device_bytes(self.ctx)
+
+    def set_depth(self, depth_v) -> None:
+        vg_set_depth(self.ctx, depth_v)
+
+    def adj_forward(self, n_steps: int, dt: float, checkpoint_every: int = 0):
+        """Fixed-dt run keeping checkpoints; returns the gauge records (t, eta)."""
+        vg_adj_forward(self.ctx, n_steps, dt, checkpoint_every)
+        return self.gauges()
+
+    def adj_backward(self, dJ_deta, nv: int) -> dict:
+        return vg_adj_backward(self.ctx, dJ_deta, self.nc, nv)
 
 
 # ---------------------------------------------------------------- batched ensembles

@@ -1,0 +1,165 @@
+"""The hand-written CUDA adjoint (vg_adj_forward / vg_adj_backward) against
+(1) the oracle's discrete adjoint -- tape AD of the oracle's own arithmetic, an
+independent program -- and (2) central finite differences of the GPU forward
+run, all in FP64 with a fixed time step.
+
+Time step (reading of the adjoint set-up): the CFL step of the initial state
+(CFL 0.9) times a 0.8 safety factor, shared by the target run, the finite
+differences and the adjoint so that gauge times coincide.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2002_04889_gb300 import inputs as I
+from paper_2002_04889_gb300 import volna
+
+pytestmark = pytest.mark.gpu
+
+LATTICE = np.array([[x, y] for x in np.linspace(-0.6, 0.6, 4) for y in np.linspace(-0.6, 0.6, 4)])
+
+
+def _case(n, half_width=1.0):
+    m = I.thacker_mesh(n=n, half_width=half_width)
+    s = I.thacker_initial_state(m)
+    p = m.cell_points()
+    deep = s.H > 2e-2
+    Hu = s.Hu + 1e-3 * np.sin(3 * p[:, 0]) * deep
+    Hv = s.Hv + 1e-3 * np.cos(2 * p[:, 1]) * deep
+    om = O.OracleMesh.from_mesh(m)
+    _, am = om.residual(O.params(), s.H, Hu, Hv)
+    dt = 0.8 * om.time_step(O.params(cfl=0.9), am, 0.0)
+    return m, (s.H, Hu, Hv), dt, om.locate(LATTICE)
+
+
+def _gpu_adjoint(m, st, dt, n_steps, W, every=0):
+    with volna.Solver(64) as sv:
+        sv.set_params(h_threshold=1e-5)
+        sv.upload_mesh(m)
+        sv.set_gauges(LATTICE)
+        sv.set_state(*st, 0.0)
+        _, eta = sv.adj_forward(n_steps, dt, every)
+        g = sv.adj_backward(W, m.nv)
+    return eta, g
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_adjoint_matches_oracle_tape_adjoint():
+    """2,048-triangle basin, 20 steps, random weights on 16 gauges."""
+    m, st, dt, cells = _case(32)
+    n_steps = 20
+    W = np.random.default_rng(3).normal(size=(n_steps + 1, len(cells)))
+    eta, g = _gpu_adjoint(m, st, dt, n_steps, W)
+    ad = O.ad_gauge_gradient(m, st, dt, n_steps, cells, W, h_threshold=1e-5)
+    np.testing.assert_allclose(eta, ad["eta"], rtol=0, atol=1e-13)
+    for k_gpu, k_or in (("H0", "dH0"), ("Hu0", "dHu0"), ("Hv0", "dHv0"), ("depth", "ddepth")):
+        err = _rel(g[k_gpu], ad[k_or])
+        assert err <= 1e-10, (k_gpu, err)
+
+
+@pytest.mark.parametrize("every", [1, 3])
+def test_checkpoint_interval_does_not_change_the_gradient(every):
+    m, st, dt, cells = _case(24)
+    n_steps = 11
+    W = np.random.default_rng(4).normal(size=(n_steps + 1, len(cells)))
+    _, g0 = _gpu_adjoint(m, st, dt, n_steps, W, every=0)
+    _, g1 = _gpu_adjoint(m, st, dt, n_steps, W, every=every)
+    for k in ("H0", "Hu0", "Hv0", "depth"):
+        np.testing.assert_array_equal(g0[k], g1[k])
+
+
+def test_adjoint_vs_central_differences():
+    """Misfit J = 1/2 sum (eta - eta_target)^2 over 16 gauges and 150 steps on a
+    20,000-triangle basin; the target run has a seeded 0.01 m Gaussian uplift and
+    a seeded +-1 % bathymetry perturbation.  8 seeded directions in the uplift
+    (wet cells) and in the vertex depths; FD step 1e-8 (kinks are dense)."""
+    m, st, dt, cells = _case(100)
+    n_steps = 150
+    rng = np.random.default_rng(12)
+    p = m.cell_points()
+    bump = 0.01 * np.exp(-((p[:, 0] - 0.2) ** 2 + (p[:, 1] + 0.1) ** 2) / 0.05)
+    wet = st[0] > 2e-2
+    depth_t = m.depth * (1.0 + 0.01 * (2 * rng.random(m.nv) - 1))
+
+    def run(H0, depth):
+        with volna.Solver(64) as sv:
+            sv.set_params(h_threshold=1e-5)
+            sv.upload_mesh(m)
+            sv.set_depth(depth)
+            sv.set_gauges(LATTICE)
+            sv.set_state(H0, st[1], st[2], 0.0)
+            _, eta = sv.adj_forward(n_steps, dt)
+            return sv, eta
+
+    sv_t, eta_t = run(st[0] + bump * wet, depth_t)
+    sv_t.close()
+
+    def J(H0, depth):
+        sv, eta = run(H0, depth)
+        sv.close()
+        return 0.5 * float(np.sum((eta - eta_t) ** 2))
+
+    sv, eta = run(st[0], m.depth)
+    g = sv.adj_backward(eta - eta_t, m.nv)
+    sv.close()
+    eps = 1e-8
+    n_ok = 0
+    for k in range(8):
+        if k % 2 == 0:
+            d = rng.normal(size=m.nc) * wet
+            gd = float(np.dot(g["H0"], d))
+            jp, jm = J(st[0] + eps * d, m.depth), J(st[0] - eps * d, m.depth)
+        else:
+            d = rng.normal(size=m.nv) * m.depth * 1e-2
+            gd = float(np.dot(g["depth"], d))
+            jp, jm = J(st[0], m.depth + eps * d), J(st[0], m.depth - eps * d)
+        fd = (jp - jm) / (2 * eps)
+        if abs(gd - fd) <= 1e-5 * max(abs(fd), 1e-12):
+            n_ok += 1
+    assert n_ok >= 7, n_ok
+
+
+def test_autograd_uplift_and_bathymetry():
+    """torch.autograd: H0 = max(0, eta_base + uplift - z(depth)); gradients of a
+    gauge misfit with respect to the uplift field and the vertex depths agree
+    with central differences of the whole pipeline."""
+    torch = pytest.importorskip("torch")
+    from paper_2002_04889_gb300.adjoint import cell_bed, gauge_records
+    m, st, dt, cells = _case(40)
+    n_steps = 40
+    tri = torch.tensor(m.tri.astype(np.int64))
+    z0 = -m.vertex_mean(m.depth)
+    eta_base = torch.tensor(st[0] + z0)          # free surface of the base state
+    wet = torch.tensor((st[0] > 2e-2).astype(np.float64))
+    rng = np.random.default_rng(21)
+    target = torch.tensor(rng.normal(size=(n_steps + 1, len(cells))) * 1e-3)
+    sv = volna.Solver(64)
+    sv.set_params(h_threshold=1e-5)
+    sv.upload_mesh(m)
+    sv.set_gauges(LATTICE)
+
+    def loss_of(uplift, depth):
+        H0 = torch.clamp(eta_base + uplift * wet - cell_bed(tri, depth), min=0.0)
+        eta = gauge_records(sv, H0, torch.tensor(st[1]), torch.tensor(st[2]), depth, n_steps, dt)
+        return 0.5 * torch.sum((eta - target) ** 2)
+
+    up = torch.zeros(m.nc, dtype=torch.float64, requires_grad=True)
+    dep = torch.tensor(m.depth, requires_grad=True)
+    L = loss_of(up, dep)
+    L.backward()
+    eps = 1e-8
+    for grad, which in ((up.grad, 0), (dep.grad, 1)):
+        d = torch.tensor(rng.normal(size=grad.numel()))
+        with torch.no_grad():
+            if which == 0:
+                lp, lm = loss_of(eps * d, dep), loss_of(-eps * d, dep)
+            else:
+                lp, lm = loss_of(up, dep + eps * d * 1e-2), loss_of(up, dep - eps * d * 1e-2)
+                d = d * 1e-2
+        fd = float(lp - lm) / (2 * eps)
+        gd = float(torch.dot(grad, d))
+        assert gd == pytest.approx(fd, rel=1e-5, abs=1e-14), (which, gd, fd)
+    sv.close()
