@@ -186,6 +186,118 @@ def cpu_baseline(budget_s: float = 15.0, n: int = 1414):
                       f"generator (n={n}, dx=0.04 m), {el:.1f} s"}
 
 
+def batched_leg(torch, stream, steps: int, n_scen: int = 32):
+    """Config 4: 8 coast basins of 50k..2M triangles x n_scen scenarios (uplift
+    amplitude U[1,5] m, orientation U[0,180) deg), FP32, all advanced together
+    (one persistent launch per stage, graph replay, autotuned block size),
+    against a loop of single-scenario solves (one context per mesh, each scenario
+    set and stepped in turn) over the same steps on the same GPU."""
+    import numpy as np
+    from paper_2002_04889_gb300 import inputs as I
+    from paper_2002_04889_gb300 import volna
+    t0 = time.perf_counter()
+    meshes = [I.coast_mesh_with_cells(n, seed=k) for k, n in enumerate(I.ensemble_meshes())]
+    srcs = [I.ensemble_sources(k, n_scen) for k in range(len(meshes))]
+    b = volna.Batch(32, device=torch.cuda.current_device(), stream=stream)
+    b.set_params(h_threshold=1e-3, cfl=0.9)
+    ids = [b.add_mesh(m, n_scen) for m in meshes]
+    states = []
+    for mid, m, src in zip(ids, meshes, srcs):
+        st_m = []
+        for j, (amp, ang) in enumerate(src):
+            s0 = I.coast_initial_state(m, amplitude=amp, angle_deg=ang)
+            b.set_state(mid, j, s0.H, s0.Hu, s0.Hv, 0.0)
+            st_m.append(s0)
+        states.append(st_m)
+    setup = time.perf_counter() - t0
+    block, _ = b.autotune(3)
+    for mid in ids:                       # the tuner restored the state; restart all at t = 0
+        for j in range(n_scen):
+            s0 = states[mid][j]
+            b.set_state(mid, j, s0.H, s0.Hu, s0.Hv, 0.0)
+    cells = b.info()["cells"]
+    b.step(2)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    b.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = ev0.elapsed_time(ev1)
+    batch_states = [b.get_state(mid, 0)[:3] for mid in ids]
+    b.close()
+    # loop of single-scenario solves: same meshes, same scenarios, same steps
+    solvers = []
+    for m in meshes:
+        sv = volna.Solver(32, device=torch.cuda.current_device(), stream=stream)
+        sv.set_params(h_threshold=1e-3, cfl=0.9, block_cells=block)
+        sv.upload_mesh(m)
+        solvers.append(sv)
+    torch.cuda.synchronize()
+    t_loop = 0.0
+    same = True
+    for mid, sv in enumerate(solvers):
+        for j in range(n_scen):
+            s0 = states[mid][j]
+            sv.set_state(s0.H, s0.Hu, s0.Hv, 0.0)
+            sv.step(2)
+            sv.set_state(s0.H, s0.Hu, s0.Hv, 0.0)
+            ev0.record(stream)
+            sv.step(steps + 2)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            t_loop += ev0.elapsed_time(ev1) * steps / (steps + 2)
+            if j == 0:
+                H, Hu, Hv, _ = sv.get_state()
+                ref = batch_states[mid]
+                same = same and all(np.array_equal(x, y) for x, y in zip((H, Hu, Hv), ref))
+    for sv in solvers:
+        sv.close()
+    return {"workload": f"coast basins {I.ensemble_meshes()} triangles x {n_scen} scenarios, FP32",
+            "cells": cells, "steps": steps, "block_cells_autotuned": block,
+            "value": cells * steps / (ms_batch * 1e-3), "unit": UNIT,
+            "loop_of_singles": cells * steps / (t_loop * 1e-3),
+            "speedup_vs_loop": t_loop / ms_batch, "bitwise_equal_to_singles": bool(same),
+            "setup_s": round(setup, 1)}
+
+
+def adjoint_leg(torch, stream, steps: int, n: int = 707):
+    """Config 5 mesh (Thacker basin, n x n squares, 2 n^2 triangles), FP64: the cost of
+    the gradient of a 16-gauge misfit (forward with sqrt(N) checkpoints + reverse
+    sweep) against the plain forward run of the same steps."""
+    import numpy as np
+    from paper_2002_04889_gb300 import inputs as I
+    from paper_2002_04889_gb300 import volna
+    m = I.thacker_mesh(n=n, half_width=1.0)
+    s = I.thacker_initial_state(m)
+    lat = np.array([[x, y] for x in np.linspace(-0.6, 0.6, 4) for y in np.linspace(-0.6, 0.6, 4)])
+    dt = 0.8 * 0.9 * 0.1 * (2.0 / n)
+    sv = volna.Solver(64, device=torch.cuda.current_device(), stream=stream)
+    sv.set_params(h_threshold=1e-5, dt_fixed=dt)
+    sv.upload_mesh(m)
+    sv.set_gauges(lat)
+    sv.set_state(s.H, s.Hu, s.Hv)
+    sv.step(3)
+    sv.set_state(s.H, s.Hu, s.Hv)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sv.step(steps)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    sv.set_params(h_threshold=1e-5)
+    sv.set_state(s.H, s.Hu, s.Hv)
+    t0 = time.perf_counter()
+    _, eta = sv.adj_forward(steps, dt)
+    t1 = time.perf_counter()
+    sv.adj_backward(np.full_like(eta, 1e-3), m.nv)
+    t2 = time.perf_counter()
+    sv.close()
+    return {"workload": f"Thacker basin {m.nc} triangles, FP64, {steps} steps, 16 gauges",
+            "forward_s": round(t_fwd, 4), "adj_forward_s": round(t1 - t0, 4),
+            "adj_backward_s": round(t2 - t1, 4), "cost_vs_forward": round((t2 - t0) / t_fwd, 3),
+            "forward_value": m.nc * steps / t_fwd, "unit": UNIT}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -231,6 +343,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--batched-steps", type=int, default=20, help="0 skips the batched-ensemble leg")
+    ap.add_argument("--adjoint-steps", type=int, default=100, help="0 skips the adjoint-cost leg")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -256,8 +370,9 @@ def main():
     sv.upload_mesh(mesh, renumber="morton")
     sv.set_state(st0.H, st0.Hu, st0.Hv, 0.0)
     nc = mesh.nc
+    dev_gb = sv.device_bytes() / 1e9
     log(f"[bench] rank {rank}: {nc} cells ready in {time.perf_counter() - t_setup:.1f} s, "
-        f"{sv.device_bytes() / 1e9:.2f} GB on device")
+        f"{dev_gb:.2f} GB on device")
 
     sv.step(args.warmup)
 
@@ -335,6 +450,18 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_budget)
+    sv.close()
+    batched = adjoint = None
+    if rank == 0 and args.batched_steps > 0:
+        try:
+            batched = batched_leg(torch, stream, args.batched_steps)
+        except Exception as e:             # reported, not fatal: the headline is the forward step
+            batched = {"error": str(e)[:300]}
+    if rank == 0 and args.adjoint_steps > 0:
+        try:
+            adjoint = adjoint_leg(torch, stream, args.adjoint_steps)
+        except Exception as e:
+            adjoint = {"error": str(e)[:300]}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -343,13 +470,13 @@ def main():
                 "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "cells": nc, "renumber": "morton",
                            "block_cells": 256, "cfl": 0.9, "h_threshold": 1e-5,
-                           "l2": "inputs larger than L2 (%.1f GB resident)" % (sv.device_bytes() / 1e9),
+                           "l2": "inputs larger than L2 (%.1f GB resident)" % dev_gb,
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(),
-                "neg_count": d1["neg_count"], "t_sim": d1["t"]}
+                "neg_count": d1["neg_count"], "t_sim": d1["t"],
+                "batched": batched, "adjoint": adjoint}
         print(json.dumps(line), flush=True)
-    sv.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0

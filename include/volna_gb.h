@@ -68,6 +68,10 @@ typedef struct vg_params {
                               (32..256, multiple of 32; 0 = library default 256;
                               halved automatically while the block and its
                               two-ring halo exceed shared memory)                 */
+    int32_t block_threads; /* threads per thread block of the step kernels: a
+                              multiple of 32 from block_cells to 2 x block_cells
+                              and at most 512 (the extra threads share the halo
+                              and face work); 0 = block_cells                     */
 } vg_params;
 
 /* Run diagnostics (vg_get_diagnostics). */

@@ -470,16 +470,17 @@ __global__ void adj_stage1_kernel(int nc, double dt, double hthr, const double *
     }
 }
 
-// Reverse of stage 2: w^{n+1} = fix(w/2 + (w1 + dt R1)/2).  From wb (adjoint of
-// w^{n+1}) form wb_n = 1/2 wbpre, wb_1 = 1/2 wbpre, Rb = dt/2 wbpre.
-__global__ void adj_stage2_rev_kernel(int nc, double dt, double hthr, const double *w, const double *w1,
-                                      const double *R1, const double *wb, double *wbn, double *wb1, double *Rb)
+// Reverse of stage 2: w^{n+1} = fix(w/2 + (w1 + dt R1)/2), with the dry-fix
+// branch recorded by the forward stage-2 kernel (0 none, 1 momentum cut, 2
+// emptied).  From wb (adjoint of w^{n+1}): wb_n = wb_1 = 1/2 wbpre, Rb = dt/2 wbpre.
+__global__ void adj_stage2_rev_kernel(int nc, double dt, const uint8_t *mask2, const double *wb, double *wbn,
+                                      double *wb1, double *Rb)
 {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nc; k += gridDim.x * blockDim.x) {
-        double Hpre = 0.5 * w[k] + 0.5 * (w1[k] + dt * R1[k]);
-        double b0 = wb[k], b1 = wb[nc + k], b2 = wb[2 * (size_t)nc + k];
-        dry_fix_mask(Hpre, hthr, b0, b1, b2);
-        double b[3] = {b0, b1, b2};
+        uint8_t br = mask2[k];
+        double b[3] = {wb[k], wb[nc + k], wb[2 * (size_t)nc + k]};
+        if (br == 2) { b[0] = 0.0; b[1] = 0.0; b[2] = 0.0; }
+        else if (br == 1) { b[1] = 0.0; b[2] = 0.0; }
         for (int c = 0; c < 3; c++) {
             wbn[c * (size_t)nc + k] = 0.5 * b[c];
             wb1[c * (size_t)nc + k] = 0.5 * b[c];
@@ -558,11 +559,11 @@ int adjoint_stage1(int nc, double dt, double hthr, const double *w, const double
     return (int)cudaGetLastError();
 }
 
-int adjoint_stage2_rev(int nc, double dt, double hthr, const double *w, const double *w1, const double *R1,
-                       const double *wb, double *wbn, double *wb1, double *Rb, void *stream)
+int adjoint_stage2_rev(int nc, double dt, const uint8_t *mask2, const double *wb, double *wbn, double *wb1,
+                       double *Rb, void *stream)
 {
-    adj_stage2_rev_kernel<<<grid_of(nc), 256, 0, static_cast<cudaStream_t>(stream)>>>(nc, dt, hthr, w, w1, R1, wb,
-                                                                                       wbn, wb1, Rb);
+    adj_stage2_rev_kernel<<<grid_of(nc), 256, 0, static_cast<cudaStream_t>(stream)>>>(nc, dt, mask2, wb, wbn, wb1,
+                                                                                       Rb);
     return (int)cudaGetLastError();
 }
 

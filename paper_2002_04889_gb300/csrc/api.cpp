@@ -146,6 +146,10 @@ DevPtrs dev_ptrs(const vg_ctx *c)
     DevPtrs d{};
     d.nc = c->hm.nc;
     d.block = c->hm.block;
+    {
+        int t = c->prm.block_threads;
+        d.threads = (t >= c->hm.block && t <= 2 * c->hm.block && t <= 512) ? t : c->hm.block;
+    }
     d.nblocks = c->hm.nblocks;
     d.max_halo = c->hm.max_halo;
     d.n_gauges = c->n_gauges;
@@ -417,6 +421,12 @@ int validate_params(const vg_params *p, std::string &why)
         why = "block_cells must be 0 or a multiple of 32 in [32, 256]";
         return VG_EINVAL;
     }
+    int bc = p->block_cells ? p->block_cells : 256;
+    if (p->block_threads != 0 && (p->block_threads % 32 || p->block_threads < bc || p->block_threads > 2 * bc ||
+                                  p->block_threads > 512)) {
+        why = "block_threads must be 0 or a multiple of 32 from block_cells to min(2 block_cells, 512)";
+        return VG_EINVAL;
+    }
     return VG_OK;
 }
 
@@ -482,6 +492,7 @@ int vg_default_params(vg_params *p)
     p->gauge_every = 1;
     p->strict_positivity = 0;
     p->block_cells = 0;
+    p->block_threads = 0;
     return VG_OK;
 }
 
@@ -579,8 +590,14 @@ int vg_set_params(vg_ctx *c, const vg_params *p)
     DeviceGuard guard(c->device);
     int old_block = c->prm.block_cells ? c->prm.block_cells : 256;
     int new_block = p->block_cells ? p->block_cells : 256;
+    bool threads_changed = p->block_threads != c->prm.block_threads;
     c->prm = *p;
     c->graph_dirty = true;
+    if (c->has_mesh && threads_changed && new_block == old_block) {
+        cudaStreamSynchronize(c->stream);
+        int rc = configure_launch(c);
+        if (rc) return rc;
+    }
     if (c->has_mesh && new_block != old_block) {
         cudaStreamSynchronize(c->stream);
         int rc = partition_blocks(c->hm, new_block, c->err);
@@ -957,16 +974,20 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
         if (!rc) { bufs.push_back(q); *p = static_cast<double *>(q); }
         return rc;
     };
-    double *W, *wb, *wbn, *wb1, *zb, *Rb, *R0, *R1, *w1, *H1pre, *FV, *FVb, *zfb, *own, *send, *seg;
+    // seg: the segment's states, R0seg: their stage-1 residuals, m2seg: stage-2
+    // dry-fix branches (all recorded by one forward recompute of the segment)
+    double *W, *wb, *wbn, *wb1, *zb, *Rb, *w1, *H1pre, *FV, *FVb, *zfb, *own, *send, *seg, *R0seg, *wlast, *m2raw;
     int rc = 0;
     if ((rc = alloc((size_t)(N + 1) * G, &W)) || (rc = alloc(w3, &wb)) || (rc = alloc(w3, &wbn)) ||
-        (rc = alloc(w3, &wb1)) || (rc = alloc(nc, &zb)) || (rc = alloc(w3, &Rb)) || (rc = alloc(w3, &R0)) ||
-        (rc = alloc(w3, &R1)) || (rc = alloc(w3, &w1)) || (rc = alloc(nc, &H1pre)) || (rc = alloc(9 * (size_t)nc, &FV)) ||
+        (rc = alloc(w3, &wb1)) || (rc = alloc(nc, &zb)) || (rc = alloc(w3, &Rb)) || (rc = alloc(w3, &wlast)) ||
+        (rc = alloc(w3, &w1)) || (rc = alloc(nc, &H1pre)) || (rc = alloc(9 * (size_t)nc, &FV)) ||
         (rc = alloc(9 * (size_t)nc, &FVb)) || (rc = alloc(3 * (size_t)nc, &zfb)) || (rc = alloc(4 * (size_t)nc, &own)) ||
-        (rc = alloc(12 * (size_t)nc, &send)) || (rc = alloc(w3 * (size_t)C, &seg))) {
+        (rc = alloc(12 * (size_t)nc, &send)) || (rc = alloc(w3 * (size_t)C, &seg)) ||
+        (rc = alloc(w3 * (size_t)C, &R0seg)) || (rc = alloc(((size_t)nc * C + 7) / 8, &m2raw))) {
         for (void *q : bufs) cudaFree(q);
         return rc;
     }
+    uint8_t *m2seg = reinterpret_cast<uint8_t *>(m2raw);
     DevScalars *asc = nullptr;
     if ((rc = dmalloc(c, (void **)&asc, sizeof(DevScalars)))) {
         for (void *q : bufs) cudaFree(q);
@@ -984,12 +1005,6 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
     DevPtrs d = dev_ptrs(c);
     d.sc = asc;
     d.n_gauges = 0;
-    auto fwd_residual = [&](const double *w, double *R) -> int {
-        DevPtrs dd = d;
-        dd.R0 = R;
-        int e = launch_stage1_f64(dd, p, w, c->cfg1, st);
-        return e ? cuda_fail(c, (cudaError_t)e, "adjoint residual launch") : VG_OK;
-    };
 #define ADJ_CHECK(call) do { int e_ = (call); if (e_) { rc = cuda_fail(c, (cudaError_t)e_, #call); goto done; } } while (0)
     {
         VG_CUDA(c, cudaMemcpyAsync(asc, &s0, sizeof(s0), cudaMemcpyHostToDevice, c->stream));
@@ -1000,27 +1015,29 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
         int64_t nseg = (N + C - 1) / C;
         for (int64_t sg = nseg - 1; sg >= 0; sg--) {
             int64_t a = sg * C, b = std::min(a + C, N);
-            // recompute the states of this segment from its checkpoint
+            // recompute the segment from its checkpoint, recording each step's
+            // state, stage-1 residual and stage-2 dry-fix branches
             VG_CUDA(c, cudaMemcpyAsync(seg, c->ckpt[sg], 8 * w3, cudaMemcpyDeviceToDevice, c->stream));
-            for (int64_t n = a; n + 1 < b; n++) {
-                double *win = seg + (size_t)(n - a) * w3, *wout = win + w3;
+            for (int64_t n = a; n < b; n++) {
+                double *win = seg + (size_t)(n - a) * w3;
+                double *wout = n + 1 < b ? win + w3 : wlast;
                 DevPtrs dd = d;
-                dd.R0 = R0;
+                dd.R0 = R0seg + (size_t)(n - a) * w3;
+                dd.mask2 = m2seg + (size_t)(n - a) * nc;
                 ADJ_CHECK(launch_stage1_f64(dd, p, win, c->cfg1, st));
                 ADJ_CHECK(launch_stage2_f64(dd, p, win, wout, c->cfg2, st));
             }
             for (int64_t n = b - 1; n >= a; n--) {
                 const double *w = seg + (size_t)(n - a) * w3;
-                if ((rc = fwd_residual(w, R0))) goto done;
+                const double *R0 = R0seg + (size_t)(n - a) * w3;
                 ADJ_CHECK(adjoint_stage1(nc, dt, hthr, w, R0, w1, H1pre, st));
-                if ((rc = fwd_residual(w1, R1))) goto done;
-                ADJ_CHECK(adjoint_stage2_rev(nc, dt, hthr, w, w1, R1, wb, wbn, wb1, Rb, st));
+                ADJ_CHECK(adjoint_stage2_rev(nc, dt, m2seg + (size_t)(n - a) * nc, wb, wbn, wb1, Rb, st));
                 ADJ_CHECK(adjoint_residual_vjp(d, p, w1, Rb, wb1, zb, FV, FVb, zfb, own, send, st));
                 ADJ_CHECK(adjoint_stage1_rev(nc, dt, hthr, H1pre, wb1, wbn, Rb, st));
                 ADJ_CHECK(adjoint_residual_vjp(d, p, w, Rb, wbn, zb, FV, FVb, zfb, own, send, st));
                 ADJ_CHECK(adjoint_gauge(G, c->gauge_cells, W + (size_t)n * G, nc, wbn, zb, st));
                 std::swap(wb, wbn);
-                c->launches += 14;
+                c->launches += 13;
             }
         }
         // internal -> original order on the host

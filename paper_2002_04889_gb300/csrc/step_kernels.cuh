@@ -59,6 +59,7 @@ struct KArgs {
     const real *w;          // w^n [3][nc]
     real *R0;               // [3][nc]
     real *wout;             // w^{n+1} [3][nc] (stage 2)
+    uint8_t *mask2;         // optional: stage-2 dry-fix branch (0 none, 1 momentum cut, 2 emptied)
     DevScalars *sc;
     real g, half_g, hthr;
     double cfl, dt_fixed, dt_max, t_end;
@@ -544,13 +545,17 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             real Hu = real(0.5) * Hu0 + real(0.5) * (sHu[l] + dt * RHu);
             real Hv = real(0.5) * Hv0 + real(0.5) * (sHv[l] + dt * RHv);
             real H = ETA ? W - sz[l] : W;
+            uint8_t branch = 0;
             if (H < real(0)) {
                 my_neg++;
                 W = ETA ? sz[l] : real(0);
                 Hu = real(0); Hv = real(0);
+                branch = 2;
             } else if (H <= hthr) {
                 Hu = real(0); Hv = real(0);
+                branch = 1;
             }
+            if (a.mask2) a.mask2[gid] = branch;
             if (!isfinite(W) || !isfinite(Hu) || !isfinite(Hv)) bad = true;
             a.wout[gid] = W;
             a.wout[nc + gid] = Hu;
@@ -560,8 +565,8 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     __syncthreads();
 }
 
-template <typename real, int STAGE>
-__global__ void __launch_bounds__(256) stage_kernel(const KArgs<real> a)
+template <typename real, int STAGE, int MAXT>
+__global__ void __launch_bounds__(MAXT) stage_kernel(const KArgs<real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int qcount;
@@ -721,6 +726,7 @@ KArgs<real> make_args(const DevPtrs &d, const StepParams &p, const void *w_in, v
     a.w = static_cast<const real *>(w_in);
     a.R0 = static_cast<real *>(d.R0);
     a.wout = static_cast<real *>(w_out);
+    a.mask2 = d.mask2;
     a.sc = d.sc;
     a.g = (real)p.g;
     a.half_g = (real)(0.5 * p.g);
@@ -732,15 +738,24 @@ KArgs<real> make_args(const DevPtrs &d, const StepParams &p, const void *w_in, v
     return a;
 }
 
+// Kernel instance for a launch: the register budget follows the thread count
+// (launch bounds 256 or 512).
+template <typename real>
+void *stage_kernel_ptr(int stage, int threads)
+{
+    if (threads <= 256) return stage == 1 ? (void *)stage_kernel<real, 1, 256> : (void *)stage_kernel<real, 2, 256>;
+    return stage == 1 ? (void *)stage_kernel<real, 1, 512> : (void *)stage_kernel<real, 2, 512>;
+}
+
 template <typename real>
 int stage_config(const DevPtrs &d, int stage, LaunchCfg &cfg)
 {
     cfg.smem = stage_smem_bytes<real>(d.block, d.max_halo);
-    auto kern = stage == 1 ? stage_kernel<real, 1> : stage_kernel<real, 2>;
+    const void *kern = stage_kernel_ptr<real>(stage, d.threads);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, d.block, cfg.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, d.threads, cfg.smem);
     if (e != cudaSuccess) return (int)e;
     if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
     int dev = 0, sms = 0;
@@ -758,8 +773,13 @@ int launch_stage(const DevPtrs &d, const StepParams &p, int stage, const void *w
 {
     KArgs<real> a = make_args<real>(d, p, w_in, w_out);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (stage == 1) stage_kernel<real, 1><<<c.grid, d.block, c.smem, s>>>(a);
-    else stage_kernel<real, 2><<<c.grid, d.block, c.smem, s>>>(a);
+    if (d.threads <= 256) {
+        if (stage == 1) stage_kernel<real, 1, 256><<<c.grid, d.threads, c.smem, s>>>(a);
+        else stage_kernel<real, 2, 256><<<c.grid, d.threads, c.smem, s>>>(a);
+    } else {
+        if (stage == 1) stage_kernel<real, 1, 512><<<c.grid, d.threads, c.smem, s>>>(a);
+        else stage_kernel<real, 2, 512><<<c.grid, d.threads, c.smem, s>>>(a);
+    }
     return (int)cudaGetLastError();
 }
 

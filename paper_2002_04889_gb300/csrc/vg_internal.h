@@ -86,6 +86,7 @@ struct StepParams {
 struct DevPtrs {
     int64_t nc;
     int32_t block, nblocks, max_halo, n_gauges, ring_cap;
+    int32_t threads;        // threads per CTA of the stage kernels (>= block)
     const void *geo;        // [GEO_ROWS][nc]
     const void *z;          // [nc]
     const double *z64;      // [nc] FP64 bed (state import/export and diagnostics)
@@ -96,6 +97,7 @@ struct DevPtrs {
     const int32_t *halo_ids;
     const uint16_t *ring1_nbr;
     void *R0;               // [3][nc] stage-1 residual (scratch)
+    uint8_t *mask2;         // optional [nc]: stage-2 dry-fix branch per cell (adjoint)
     DevScalars *sc;
     const int32_t *gauge_cells;   // internal ids
     double *ring_t;               // [ring_cap]
@@ -139,8 +141,8 @@ int adjoint_residual_vjp(const DevPtrs &d, const StepParams &p, const double *w,
                          double *zb, double *FV, double *FVb, double *zfb, double *own, double *send, void *stream);
 int adjoint_stage1(int nc, double dt, double hthr, const double *w, const double *R0, double *w1, double *H1pre,
                    void *stream);
-int adjoint_stage2_rev(int nc, double dt, double hthr, const double *w, const double *w1, const double *R1,
-                       const double *wb, double *wbn, double *wb1, double *Rb, void *stream);
+int adjoint_stage2_rev(int nc, double dt, const uint8_t *mask2, const double *wb, double *wbn, double *wb1,
+                       double *Rb, void *stream);
 int adjoint_stage1_rev(int nc, double dt, double hthr, const double *H1pre, const double *wb1, double *wbn,
                        double *Rb, void *stream);
 int adjoint_gauge(int n_gauges, const int32_t *cells, const double *weights, int nc, double *wb, double *zb,
