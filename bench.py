@@ -344,7 +344,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--batched-steps", type=int, default=20, help="0 skips the batched-ensemble leg")
-    ap.add_argument("--adjoint-steps", type=int, default=100, help="0 skips the adjoint-cost leg")
+    ap.add_argument("--adjoint-steps", type=int, default=2000, help="0 skips the adjoint-cost leg")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

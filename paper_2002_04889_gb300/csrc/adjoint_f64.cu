@@ -119,10 +119,24 @@ __device__ void recon_forward(const AdjMesh &m, const double *w, int K, ReconFwd
     }
 }
 
-__global__ void adj_face_values_kernel(AdjMesh m, const double *w, double *FV)
+// Face values are needed only where a face's flux adjoint can be nonzero, i.e.
+// where the cell or a face neighbour has a nonzero residual adjoint; elsewhere
+// the flux VJP skips the face (the VJP of zero is zero).
+__device__ __forceinline__ bool rb_nonzero(const double *Rb, int nc, int k)
+{
+    return Rb[k] != 0.0 || Rb[nc + k] != 0.0 || Rb[2 * (size_t)nc + k] != 0.0;
+}
+
+__global__ void adj_face_values_kernel(AdjMesh m, const double *w, const double *Rb, double *FV)
 {
     const int nc = m.nc;
     for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < nc; K += gridDim.x * blockDim.x) {
+        bool need = rb_nonzero(Rb, nc, K);
+        for (int f = 0; f < 3 && !need; f++) {
+            int j = m.nbr[f * nc + K];
+            if (j >= 0) need = rb_nonzero(Rb, nc, j);
+        }
+        if (!need) continue;
         ReconFwd R;
         double Hf[3], Huf[3], Hvf[3];
         recon_forward(m, w, K, R, Hf, Huf, Hvf);
@@ -216,13 +230,13 @@ __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL,
         if (sL >= 0.0) {
             for (int k = 0; k < 3; k++) FLb[k] = Fb[k];
         } else if (sR >= 0.0) {
-            double den = sR - sL, sLR = sL * sR;
+            double den = sR - sL, sLR = sL * sR, iden = 1.0 / den;
             double denb = 0.0, sLRb = 0.0;
             for (int k = 0; k < 3; k++) {
                 double N = (sR * FL[k] - sL * FR[k]) + sLR * (wR[k] - wL[k]);
-                double F = N / den;
-                double Nb = Fb[k] / den;
-                denb -= Fb[k] * F / den;
+                double F = N * iden;
+                double Nb = Fb[k] * iden;
+                denb -= Fb[k] * F * iden;
                 FLb[k] += Nb * sR;
                 FRb[k] -= Nb * sL;
                 sRb += Nb * FL[k];
@@ -288,16 +302,18 @@ __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL,
         if (zR_max) bR[3] += zsb; else bL[3] += zsb;
         double uRb = unRb * nx - utRb * ny, vRb = unRb * ny + utRb * nx;
         if (velR) {
-            bR[1] += uRb / HfR;
-            bR[2] += vRb / HfR;
-            HfRb -= (uRb * uR + vRb * vR) / HfR;
+            double inv = 1.0 / HfR;
+            bR[1] += uRb * inv;
+            bR[2] += vRb * inv;
+            HfRb -= (uRb * uR + vRb * vR) * inv;
         }
     }
     double uLb = unLb * nx - utLb * ny, vLb = unLb * ny + utLb * nx;
     if (velL) {
-        bL[1] += uLb / HfL;
-        bL[2] += vLb / HfL;
-        HfLb -= (uLb * uL + vLb * vL) / HfL;
+        double inv = 1.0 / HfL;
+        bL[1] += uLb * inv;
+        bL[2] += vLb * inv;
+        HfLb -= (uLb * uL + vLb * vL) * inv;
     }
     bL[0] += HfLb;
     bR[0] += HfRb;
@@ -315,6 +331,15 @@ __global__ void adj_flux_vjp_kernel(AdjMesh m, const double *FV, const double *R
             if (j >= 0 && j < K) continue;      // the lower-numbered cell owns the face
             bool wall = j < 0;
             int fj = wall ? 0 : (m.nbrl[f * nc + K] & 3);
+            if (!rb_nonzero(Rb, nc, K) && (wall || !rb_nonzero(Rb, nc, j))) {
+                for (int v = 0; v < 3; v++) FVb[(v * 3 + f) * (size_t)nc + K] = 0.0;
+                zfb[f * (size_t)nc + K] = 0.0;
+                if (!wall) {
+                    for (int v = 0; v < 3; v++) FVb[(v * 3 + fj) * (size_t)nc + j] = 0.0;
+                    zfb[fj * (size_t)nc + j] = 0.0;
+                }
+                continue;
+            }
             double nx = G(m, GEO_NX + f, K), ny = G(m, GEO_NY + f, K), l = G(m, GEO_LEN + f, K);
             double aL = G(m, GEO_AREA, K);
             double cLf = -l / aL;
@@ -358,14 +383,27 @@ __global__ void adj_recon_vjp_kernel(AdjMesh m, const double *w, const double *F
 {
     const int nc = m.nc;
     for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < nc; K += gridDim.x * blockDim.x) {
+        double fb[3][3];   // [v][f]
+        bool any = false;
+        for (int v = 0; v < 3; v++)
+            for (int f = 0; f < 3; f++) {
+                fb[v][f] = FVb[(v * 3 + f) * (size_t)nc + K];
+                any = any || fb[v][f] != 0.0;
+            }
+        double zsum = 0.0;
+        for (int f = 0; f < 3; f++) zsum += zfb[f * (size_t)nc + K];
+        if (!any) {                      // nothing flows back through the reconstruction
+            own[K] = 0.0;
+            own[nc + K] = 0.0;
+            own[2 * (size_t)nc + K] = 0.0;
+            own[3 * (size_t)nc + K] = zsum;
+            for (int q = 0; q < 12; q++) send[q * (size_t)nc + K] = 0.0;
+            continue;
+        }
         ReconFwd R;
         double Hf[3], Huf[3], Hvf[3];
         recon_forward(m, w, K, R, Hf, Huf, Hvf);
-        double fb[3][3];   // [v][f]
-        for (int v = 0; v < 3; v++)
-            for (int f = 0; f < 3; f++) fb[v][f] = FVb[(v * 3 + f) * (size_t)nc + K];
-        double Hb = 0.0, Hub = 0.0, Hvb = 0.0, zb = 0.0;
-        for (int f = 0; f < 3; f++) zb += zfb[f * (size_t)nc + K];
+        double Hb = 0.0, Hub = 0.0, Hvb = 0.0, zb = zsum;
         double qnb[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};   // [f][v]
         if (!R.recon) {
             for (int f = 0; f < 3; f++) { Hb += fb[0][f]; Hub += fb[1][f]; Hvb += fb[2][f]; }
@@ -381,9 +419,10 @@ __global__ void adj_recon_vjp_kernel(AdjMesh m, const double *w, const double *F
                 }
                 int fa = R.fa[v];
                 if (fa >= 0) {
+                    double iD = 1.0 / R.D[v][fa];
+                    double rb = ab * iD;
+                    Db[fa] -= rb * R.r[v] * iD;
                     double D = R.D[v][fa];
-                    double rb = ab / D;
-                    Db[fa] -= ab * R.r[v] / (D * D);
                     int idx = D > 0.0 ? R.imax[v] : R.imin[v];
                     if (idx < 0) qKb[v] += rb; else qnb[idx][v] += rb;
                     qKb[v] -= rb;
@@ -545,7 +584,7 @@ int adjoint_residual_vjp(const DevPtrs &d, const StepParams &p, const double *w,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     AdjMesh m = adj_mesh(d, p);
     int grid = grid_of(m.nc);
-    adj_face_values_kernel<<<grid, 256, 0, s>>>(m, w, FV);
+    adj_face_values_kernel<<<grid, 256, 0, s>>>(m, w, Rb, FV);
     adj_flux_vjp_kernel<<<grid, 256, 0, s>>>(m, FV, Rb, FVb, zfb);
     adj_recon_vjp_kernel<<<grid, 256, 0, s>>>(m, w, FVb, zfb, own, send);
     adj_gather_kernel<<<grid, 256, 0, s>>>(m, own, send, wb, zb);
