@@ -579,12 +579,13 @@ AdjMesh adj_mesh(const DevPtrs &d, const StepParams &p)
 // Adds the VJP of the residual at w: (wb, zb) += (dR/dw, dR/dz)^T Rb.
 // Scratch: FV, FVb [9][nc], zfb [3][nc], own [4][nc], send [12][nc].
 int adjoint_residual_vjp(const DevPtrs &d, const StepParams &p, const double *w, const double *Rb, double *wb,
-                         double *zb, double *FV, double *FVb, double *zfb, double *own, double *send, void *stream)
+                         double *zb, double *FV, bool fv_given, double *FVb, double *zfb, double *own, double *send,
+                         void *stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     AdjMesh m = adj_mesh(d, p);
     int grid = grid_of(m.nc);
-    adj_face_values_kernel<<<grid, 256, 0, s>>>(m, w, Rb, FV);
+    if (!fv_given) adj_face_values_kernel<<<grid, 256, 0, s>>>(m, w, Rb, FV);
     adj_flux_vjp_kernel<<<grid, 256, 0, s>>>(m, FV, Rb, FVb, zfb);
     adj_recon_vjp_kernel<<<grid, 256, 0, s>>>(m, w, FVb, zfb, own, send);
     adj_gather_kernel<<<grid, 256, 0, s>>>(m, own, send, wb, zb);

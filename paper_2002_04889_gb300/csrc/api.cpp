@@ -976,11 +976,12 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
     };
     // seg: the segment's states, R0seg: their stage-1 residuals, m2seg: stage-2
     // dry-fix branches (all recorded by one forward recompute of the segment)
-    double *W, *wb, *wbn, *wb1, *zb, *Rb, *w1, *H1pre, *FV, *FVb, *zfb, *own, *send, *seg, *R0seg, *wlast, *m2raw;
+    double *W, *wb, *wbn, *wb1, *zb, *Rb, *w1, *H1pre, *FVb, *zfb, *own, *send, *seg, *R0seg, *wlast, *m2raw;
+    double *FVseg;   // face values of both stages of every step of the segment [C][2][9][nc]
     int rc = 0;
     if ((rc = alloc((size_t)(N + 1) * G, &W)) || (rc = alloc(w3, &wb)) || (rc = alloc(w3, &wbn)) ||
         (rc = alloc(w3, &wb1)) || (rc = alloc(nc, &zb)) || (rc = alloc(w3, &Rb)) || (rc = alloc(w3, &wlast)) ||
-        (rc = alloc(w3, &w1)) || (rc = alloc(nc, &H1pre)) || (rc = alloc(9 * (size_t)nc, &FV)) ||
+        (rc = alloc(w3, &w1)) || (rc = alloc(nc, &H1pre)) || (rc = alloc(18 * (size_t)nc * C, &FVseg)) ||
         (rc = alloc(9 * (size_t)nc, &FVb)) || (rc = alloc(3 * (size_t)nc, &zfb)) || (rc = alloc(4 * (size_t)nc, &own)) ||
         (rc = alloc(12 * (size_t)nc, &send)) || (rc = alloc(w3 * (size_t)C, &seg)) ||
         (rc = alloc(w3 * (size_t)C, &R0seg)) || (rc = alloc(((size_t)nc * C + 7) / 8, &m2raw))) {
@@ -1024,7 +1025,9 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
                 DevPtrs dd = d;
                 dd.R0 = R0seg + (size_t)(n - a) * w3;
                 dd.mask2 = m2seg + (size_t)(n - a) * nc;
+                dd.fv_out = FVseg + (size_t)(n - a) * 18 * nc;
                 ADJ_CHECK(launch_stage1_f64(dd, p, win, c->cfg1, st));
+                dd.fv_out = FVseg + ((size_t)(n - a) * 18 + 9) * nc;
                 ADJ_CHECK(launch_stage2_f64(dd, p, win, wout, c->cfg2, st));
             }
             for (int64_t n = b - 1; n >= a; n--) {
@@ -1032,12 +1035,13 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
                 const double *R0 = R0seg + (size_t)(n - a) * w3;
                 ADJ_CHECK(adjoint_stage1(nc, dt, hthr, w, R0, w1, H1pre, st));
                 ADJ_CHECK(adjoint_stage2_rev(nc, dt, m2seg + (size_t)(n - a) * nc, wb, wbn, wb1, Rb, st));
-                ADJ_CHECK(adjoint_residual_vjp(d, p, w1, Rb, wb1, zb, FV, FVb, zfb, own, send, st));
+                double *FV0 = FVseg + (size_t)(n - a) * 18 * nc, *FV1 = FV0 + 9 * (size_t)nc;
+                ADJ_CHECK(adjoint_residual_vjp(d, p, w1, Rb, wb1, zb, FV1, true, FVb, zfb, own, send, st));
                 ADJ_CHECK(adjoint_stage1_rev(nc, dt, hthr, H1pre, wb1, wbn, Rb, st));
-                ADJ_CHECK(adjoint_residual_vjp(d, p, w, Rb, wbn, zb, FV, FVb, zfb, own, send, st));
+                ADJ_CHECK(adjoint_residual_vjp(d, p, w, Rb, wbn, zb, FV0, true, FVb, zfb, own, send, st));
                 ADJ_CHECK(adjoint_gauge(G, c->gauge_cells, W + (size_t)n * G, nc, wbn, zb, st));
                 std::swap(wb, wbn);
-                c->launches += 13;
+                c->launches += 11;
             }
         }
         // internal -> original order on the host

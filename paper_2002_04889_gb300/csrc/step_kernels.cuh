@@ -60,6 +60,7 @@ struct KArgs {
     real *R0;               // [3][nc]
     real *wout;             // w^{n+1} [3][nc] (stage 2)
     uint8_t *mask2;         // optional: stage-2 dry-fix branch (0 none, 1 momentum cut, 2 emptied)
+    real *fv_out;           // optional [3 vars][3 faces][nc]: face values of the block cells
     DevScalars *sc;
     real g, half_g, hthr;
     double cfl, dt_fixed, dt_max, t_end;
@@ -455,6 +456,14 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             fHu[f * L + l] = Huf[f];
             fHv[f * L + l] = Hvf[f];
         }
+        if (a.fv_out && l < B) {
+#pragma unroll
+            for (int f = 0; f < 3; f++) {
+                a.fv_out[(0 * 3 + f) * (size_t)nc + gid] = Hf[f];
+                a.fv_out[(1 * 3 + f) * (size_t)nc + gid] = Huf[f];
+                a.fv_out[(2 * 3 + f) * (size_t)nc + gid] = Hvf[f];
+            }
+        }
     }
     __syncthreads();
 
@@ -727,6 +736,7 @@ KArgs<real> make_args(const DevPtrs &d, const StepParams &p, const void *w_in, v
     a.R0 = static_cast<real *>(d.R0);
     a.wout = static_cast<real *>(w_out);
     a.mask2 = d.mask2;
+    a.fv_out = static_cast<real *>(d.fv_out);
     a.sc = d.sc;
     a.g = (real)p.g;
     a.half_g = (real)(0.5 * p.g);

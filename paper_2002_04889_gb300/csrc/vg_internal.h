@@ -98,6 +98,7 @@ struct DevPtrs {
     const uint16_t *ring1_nbr;
     void *R0;               // [3][nc] stage-1 residual (scratch)
     uint8_t *mask2;         // optional [nc]: stage-2 dry-fix branch per cell (adjoint)
+    void *fv_out;           // optional [9][nc]: face values written by the stage kernels (adjoint)
     DevScalars *sc;
     const int32_t *gauge_cells;   // internal ids
     double *ring_t;               // [ring_cap]
@@ -137,8 +138,11 @@ int launch_batch_step_f64(const void *table, int n_mesh, int n_items, int n_entr
                           int grid, size_t smem, const StepParams &p, void *stream);
 
 // Discrete adjoint (adjoint_f64.cu, FP64 contexts).
+// FV: the face values at w, precomputed by the forward stage kernel (fv_out)
+// or, if fv_given is false, computed here into FV.
 int adjoint_residual_vjp(const DevPtrs &d, const StepParams &p, const double *w, const double *Rb, double *wb,
-                         double *zb, double *FV, double *FVb, double *zfb, double *own, double *send, void *stream);
+                         double *zb, double *FV, bool fv_given, double *FVb, double *zfb, double *own, double *send,
+                         void *stream);
 int adjoint_stage1(int nc, double dt, double hthr, const double *w, const double *R0, double *w1, double *H1pre,
                    void *stream);
 int adjoint_stage2_rev(int nc, double dt, const uint8_t *mask2, const double *wb, double *wbn, double *wb1,

@@ -133,9 +133,11 @@ def test_adjoint_vs_central_differences():
 
 
 def test_autograd_uplift_and_bathymetry():
-    """torch.autograd: H0 = max(0, eta_base + uplift - z(depth)); gradients of a
-    gauge misfit with respect to the uplift field and the vertex depths agree
-    with central differences of the whole pipeline."""
+    """torch.autograd: in the wet cells H0 = eta_base + uplift - z(depth), elsewhere
+    the base depth (a dry cell sits exactly on the kink of max(0, .), where no
+    derivative exists); gradients of a gauge misfit with respect to the uplift
+    field and the vertex depths agree with central differences of the whole
+    pipeline."""
     torch = pytest.importorskip("torch")
     from paper_2002_04889_gb300.adjoint import cell_bed, gauge_records
     m, st, dt, cells = _case(24)
@@ -151,8 +153,10 @@ def test_autograd_uplift_and_bathymetry():
     sv.upload_mesh(m)
     sv.set_gauges(LATTICE)
 
+    H_base = torch.tensor(st[0])
+
     def loss_of(uplift, depth):
-        H0 = torch.clamp(eta_base + uplift * wet - cell_bed(tri, depth), min=0.0)
+        H0 = wet * (eta_base + uplift - cell_bed(tri, depth)) + (1.0 - wet) * H_base
         eta = gauge_records(sv, H0, torch.tensor(st[1]), torch.tensor(st[2]), depth, n_steps, dt)
         return 0.5 * torch.sum((eta - target) ** 2)
 
