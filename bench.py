@@ -70,6 +70,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest value of x over all ranks (x itself without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(cells_per_rank: int, steps: int, ms_max: float, world: int) -> float:
+    """Whole-job cell-updates/s of independent replicas: every rank advances its own
+    cells_per_rank cells by `steps` steps; the job takes the slowest rank's time."""
+    return cells_per_rank * steps * world / (ms_max * 1e-3)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -397,11 +414,8 @@ def main():
     sv.profile(False)
     d1 = sv.diagnostics()
     launches = int(d1["launches"] - d0["launches"]) - 2   # minus the diagnostics' own 2
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = nc * args.steps * ws / (ms * 1e-3)
+    ms = max_over_ranks(ms, "cuda")
+    value = replica_throughput(nc, args.steps, ms, ws)
 
     # ---- roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
@@ -438,12 +452,8 @@ def main():
             Hu, oHu = oHu, Hu
             Hv, oHv = oHv, Hv
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([el], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": nc * args.e2e_steps * ws / el, "unit": UNIT,
+        el = max_over_ranks(time.perf_counter() - t0, "cuda")
+        e2e = {"value": replica_throughput(nc, args.e2e_steps, el * 1e3, ws), "unit": UNIT,
                "h2d_bytes_per_step": 3 * 8 * nc, "d2h_bytes_per_step": 3 * 8 * nc,
                "steps": args.e2e_steps}
 

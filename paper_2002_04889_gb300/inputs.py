@@ -190,6 +190,17 @@ def thacker_initial_state(mesh: Mesh, g: float = 9.81) -> State:
     return State(H, zero.copy(), zero.copy(), 0.0)
 
 
+def thacker_free_surface(x, y, t: float, h0: float = 0.1, alpha: float = 1.0, r0: float = 0.8,
+                         g: float = 9.81):
+    """Free-surface elevation of Thacker's periodic paraboloid at time t (Sec. 3;
+    the printed h(r, t) minus the bed), before clipping by the bed."""
+    omega = math.sqrt(8.0 * g * h0) / alpha
+    A = (alpha * alpha - r0 * r0) / (alpha * alpha + r0 * r0)
+    c = 1.0 - A * math.cos(omega * t)
+    r2 = np.asarray(x) ** 2 + np.asarray(y) ** 2
+    return h0 * (math.sqrt(1.0 - A * A) / c - 1.0 - (r2 / (alpha * alpha)) * ((1.0 - A * A) / (c * c) - 1.0))
+
+
 def lake_at_rest_state(mesh: Mesh, eta: float) -> State:
     """Still water at level eta over the mesh's bed (dry where the bed is above eta)."""
     z = -mesh.vertex_mean(mesh.depth)
