@@ -225,7 +225,7 @@ int upload_mesh_arrays(vg_ctx *c)
     const HostMesh &m = c->hm;
     size_t rs = real_size(c);
     int rc;
-    if ((rc = dmalloc(c, &c->geo, rs * GEO_ROWS * m.nc))) return rc;
+    if ((rc = dmalloc(c, &c->geo, c->precision == 64 ? 8 * GEO_ROWS * m.nc : 4 * 20 * m.nc))) return rc;
     if ((rc = dmalloc(c, &c->z, rs * m.nc))) return rc;
     if ((rc = dmalloc(c, &c->w[0], rs * 3 * m.nc))) return rc;
     if ((rc = dmalloc(c, &c->w[1], rs * 3 * m.nc))) return rc;
@@ -233,7 +233,28 @@ int upload_mesh_arrays(vg_ctx *c)
     if ((rc = dmalloc(c, (void **)&c->nbr, 4 * 3 * m.nc))) return rc;
     if ((rc = dmalloc(c, (void **)&c->old_of_new, 4 * m.nc))) return rc;
     if ((rc = dmalloc(c, (void **)&c->ring_t, 8 * kRingCap))) return rc;
-    if ((rc = upload_real(c, c->geo, m.geo.data(), m.geo.size()))) return rc;
+    if (c->precision == 64) {
+        if ((rc = upload_real(c, c->geo, m.geo.data(), m.geo.size()))) return rc;
+    } else {
+        // FP32 record per cell (20 floats): M_fj = w_j . (x_f - x_K) formed in FP64,
+        // then the normals, face lengths and area.
+        const int64_t n = m.nc;
+        std::vector<float> r(20 * (size_t)n, 0.0f);
+        for (int64_t k = 0; k < n; k++) {
+            auto G = [&](int row) { return m.geo[(size_t)row * n + k]; };
+            float *o = &r[20 * (size_t)k];
+            for (int f = 0; f < 3; f++)
+                for (int j = 0; j < 3; j++)
+                    o[3 * f + j] = (float)(G(GEO_WX + j) * G(GEO_FX + f) + G(GEO_WY + j) * G(GEO_FY + f));
+            for (int f = 0; f < 3; f++) {
+                o[10 + 2 * f] = (float)G(GEO_NX + f);
+                o[11 + 2 * f] = (float)G(GEO_NY + f);
+                o[16 + f] = (float)G(GEO_LEN + f);
+            }
+            o[19] = (float)G(GEO_AREA);
+        }
+        VG_CUDA(c, cudaMemcpy(c->geo, r.data(), 4 * r.size(), cudaMemcpyHostToDevice));
+    }
     if ((rc = upload_real(c, c->z, m.z.data(), m.z.size()))) return rc;
     if (c->precision == 64) {
         c->z64 = static_cast<double *>(c->z);

@@ -194,19 +194,36 @@ __device__ __forceinline__ void face_flux(real g, real half_g, real hthr,
 template <typename real> struct EtaForm { static constexpr bool value = false; };
 template <> struct EtaForm<float> { static constexpr bool value = true; };
 
+// FP32 cell geometry record, 20 floats (five 16-byte words) per cell:
+//   M00 M01 M02 M10 | M11 M12 M20 M21 | M22 -- nx0 ny0 | nx1 ny1 nx2 ny2 | l0 l1 l2 area
+// with M_fj = w_j . (x_f - x_K): the limited increments of the reconstruction are
+// D_f = sum_j M_fj (q_j - q_K), the same quantity as grad q . (x_f - x_K) with the
+// least-squares gradient grad q = sum_j w_j (q_j - q_K).  (FP64 keeps the rows
+// GEO_* and evaluates gradient then dot product, in the literal order.)
+constexpr int G32 = 20;
+__device__ __forceinline__ const float4 *g32(const float *geo, int k)
+{
+    return reinterpret_cast<const float4 *>(geo + (size_t)k * G32);
+}
+__device__ __forceinline__ float2 g32_normal(const float *geo, int k, int f)
+{
+    return *reinterpret_cast<const float2 *>(geo + (size_t)k * G32 + 10 + 2 * f);
+}
+
 // Stored state of cell gid as seen by the stage (H or eta first, then Hu, Hv):
 // stage 1 reads w^n; stage 2 forms w1 = w^n + dt R0 and applies the dry fix
 // (negative depth emptied; at or below the threshold, momentum zeroed).
 // Returns true if a negative depth was met.
 template <typename real, int STAGE>
 __device__ __forceinline__ bool stage_state(const KArgs<real> &a, int gid, real dt, real zc, real &W,
-                                            real &Hu, real &Hv)
+                                            real &Hu, real &Hv, real *wn = nullptr)
 {
     constexpr bool ETA = EtaForm<real>::value;
     const int nc = (int)a.nc;
     W = a.w[gid];
     Hu = a.w[nc + gid];
     Hv = a.w[2 * nc + gid];
+    if (wn) { wn[0] = W; wn[1] = Hu; wn[2] = Hv; }
     if (STAGE == 1) return false;
     W = W + dt * a.R0[gid];
     Hu = Hu + dt * a.R0[nc + gid];
@@ -307,13 +324,23 @@ template <typename real>
 __host__ __device__ inline size_t stage_smem_bytes(int block, int max_halo)
 {
     size_t L = (size_t)block + max_halo;
-    return sizeof(real) * (13 * L + 18 * (size_t)block) + sizeof(int32_t) * L +
-           sizeof(uint16_t) * 3 * (size_t)block + 16;
+    return sizeof(real) * (13 * L + 3 * (size_t)block) + sizeof(int32_t) * L +
+           sizeof(uint16_t) * 6 * (size_t)block + 16;
+}
+
+// Stage state of one local cell l (global id gid) into shared memory.
+template <typename real, int STAGE>
+__device__ __forceinline__ bool stage_cell(const KArgs<real> &a, int gid, real dt, real &W, real &Hu, real &Hv,
+                                           real &zc, real *wn = nullptr)
+{
+    zc = a.z[gid];
+    return stage_state<real, STAGE>(a, gid, dt, zc, W, Hu, Hv, wn);
 }
 
 // One block of cells for one scenario: phases A-D (see the top of this file).
 // my_min collects the thread's stage-1 CFL bound, my_neg its negative-depth
-// events, bad a non-finite result.  Every thread of the CTA must call it.
+// events, bad a non-finite result.  Every thread of the CTA must call it, and
+// qcount must be zero on entry (it is zero again on return).
 template <typename real, int STAGE>
 __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b, const real dt,
                                               unsigned char *smem_raw, int &qcount, real &my_min,
@@ -327,17 +354,15 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     real *sHu = sH + L;
     real *sHv = sHu + L;
     real *sz = sHv + L;
-    real *fH = sz + L;            // [3][L]
+    // [3][L] face values of block + ring-1 cells after phase B; after phase C the
+    // slot (f, l) of a block cell holds that cell's own term l_f [Phi_f + P_{K,f} n_f]
+    real *fH = sz + L;
     real *fHu = fH + 3 * L;
     real *fHv = fHu + 3 * L;
-    real *oP0 = fHv + 3 * L;      // [3][B]
-    real *oP1 = oP0 + 3 * B;
-    real *oP2 = oP1 + 3 * B;
-    real *oPL = oP2 + 3 * B;
-    real *oPR = oPL + 3 * B;
-    real *oA = oPR + 3 * B;
+    real *oA = fHv + 3 * L;       // [3][B] l_f a_f of block cells (stage 1)
     int32_t *sGid = reinterpret_cast<int32_t *>(oA + 3 * B);   // [L] global id of each local cell
-    uint16_t *queue = reinterpret_cast<uint16_t *>(sGid + L);
+    uint16_t *sCode = reinterpret_cast<uint16_t *>(sGid + L);  // [3][B] face codes of block cells
+    uint16_t *queue = sCode + 3 * B;                            // [3B] owned faces
 
     constexpr bool ETA = EtaForm<real>::value;
     const int tid = threadIdx.x;
@@ -350,19 +375,59 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     const int nh = a.halo_ptr[b + 1] - h0;
     const int n1 = a.halo_n1[b];
 
-    // A: block + ring-1 + ring-2 states into shared memory
-    for (int l = tid; l < B + nh; l += blockDim.x) {
-        if (l < B && l >= ncell) continue;
-        int gid = l < B ? c0 + l : a.halo_ids[h0 + (l - B)];
-        real W, Hu, Hv;
-        real zc = a.z[gid];
-        bool neg = stage_state<real, STAGE>(a, gid, dt, zc, W, Hu, Hv);
-        if (neg && l < B) my_neg++;
-        sH[l] = W; sHu[l] = Hu; sHv[l] = Hv;
-        sz[l] = zc;
-        sGid[l] = gid;
+    // A: block + ring-1 + ring-2 states into shared memory.  Thread tid < B
+    // takes block cell tid (and keeps w^n of it for stage 2's final update) and
+    // queues the faces that cell owns: a wall, a face to the halo, or a face to
+    // a block cell of higher local index.
+    real wn[3] = {real(0), real(0), real(0)};
+    {
+        int gh = -1;
+        if (tid < nh) gh = a.halo_ids[h0 + tid];
+        int owned = 0;
+        if (tid < ncell) {
+            const int gid = c0 + tid;
+            uint16_t code[3];
+#pragma unroll
+            for (int f = 0; f < 3; f++) {
+                code[f] = a.nbrl[f * nc + gid];
+                sCode[f * B + tid] = code[f];
+                if (code[f] == NBR_WALL || (code[f] >> 2) >= B || (int)(code[f] >> 2) > tid) owned |= 1 << f;
+            }
+            real W, Hu, Hv, zc;
+            bool neg = stage_cell<real, STAGE>(a, gid, dt, W, Hu, Hv, zc, wn);
+            if (neg) my_neg++;
+            sH[tid] = W; sHu[tid] = Hu; sHv[tid] = Hv; sz[tid] = zc;
+            sGid[tid] = gid;
+        }
+        if (gh >= 0) {
+            real W, Hu, Hv, zc;
+            stage_cell<real, STAGE>(a, gh, dt, W, Hu, Hv, zc);
+            const int l = B + tid;
+            sH[l] = W; sHu[l] = Hu; sHv[l] = Hv; sz[l] = zc;
+            sGid[l] = gh;
+        }
+        for (int h = tid + blockDim.x; h < nh; h += blockDim.x) {
+            const int gid = a.halo_ids[h0 + h];
+            real W, Hu, Hv, zc;
+            stage_cell<real, STAGE>(a, gid, dt, W, Hu, Hv, zc);
+            const int l = B + h;
+            sH[l] = W; sHu[l] = Hu; sHv[l] = Hv; sz[l] = zc;
+            sGid[l] = gid;
+        }
+        // warp-aggregated queue append: n = popcount(owned) in 0..3
+        const int n = __popc(owned);
+        const unsigned lane = tid & 31;
+        const unsigned lt = (1u << lane) - 1u;
+        const unsigned b1 = __ballot_sync(0xffffffffu, n & 1), b2 = __ballot_sync(0xffffffffu, n & 2);
+        const int total = __popc(b1) + 2 * __popc(b2);
+        int base = 0;
+        if (lane == 0 && total) base = atomicAdd(&qcount, total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        int pos = base + __popc(b1 & lt) + 2 * __popc(b2 & lt);
+#pragma unroll
+        for (int f = 0; f < 3; f++)
+            if ((owned >> f) & 1) queue[pos++] = (uint16_t)((tid << 2) | f);
     }
-    if (tid == 0) qcount = 0;
     __syncthreads();
 
     // B: face values of block + ring-1 cells (Sec. 2.4, Eq. recon with the
@@ -380,7 +445,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             real Wj = real(0), Huj = real(0), Hvj = real(0), zj = real(0);
             int nl;
             if (l < B) {
-                uint16_t code = a.nbrl[f * nc + gid];
+                uint16_t code = sCode[f * B + l];
                 wall = code == NBR_WALL;
                 nl = code >> 2;
             } else {
@@ -396,7 +461,13 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
                 qn[f][2] = Hvj;
                 if (!(Hj > hthr)) recon = false;
             } else {
-                real nxf = geo[(GEO_NX + f) * nc + gid], nyf = geo[(GEO_NY + f) * nc + gid];
+                real nxf, nyf;
+                if constexpr (ETA) {
+                    float2 nf = g32_normal(geo, gid, f);
+                    nxf = nf.x; nyf = nf.y;
+                } else {
+                    nxf = geo[(GEO_NX + f) * nc + gid]; nyf = geo[(GEO_NY + f) * nc + gid];
+                }
                 real mn = HuK * nxf + HvK * nyf;
                 qn[f][0] = qK[0];
                 qn[f][1] = HuK - real(2) * mn * nxf;
@@ -405,19 +476,36 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         }
         real Hf[3], Huf[3], Hvf[3];
         if (recon) {
-            real fx[3], fy[3], wx[3], wy[3];
-            for (int f = 0; f < 3; f++) {
-                fx[f] = geo[(GEO_FX + f) * nc + gid];
-                fy[f] = geo[(GEO_FY + f) * nc + gid];
-                wx[f] = geo[(GEO_WX + f) * nc + gid];
-                wy[f] = geo[(GEO_WY + f) * nc + gid];
-            }
             real face[3][3];
+            real Mf[3][3];          // FP32: M_fj of the record
+            real fx[3], fy[3], wx[3], wy[3];
+            if constexpr (ETA) {
+                const float4 *r = g32(geo, gid);
+                float4 a0 = r[0], a1 = r[1], a2 = r[2];
+                Mf[0][0] = a0.x; Mf[0][1] = a0.y; Mf[0][2] = a0.z;
+                Mf[1][0] = a0.w; Mf[1][1] = a1.x; Mf[1][2] = a1.y;
+                Mf[2][0] = a1.z; Mf[2][1] = a1.w; Mf[2][2] = a2.x;
+            } else {
+                for (int f = 0; f < 3; f++) {
+                    fx[f] = geo[(GEO_FX + f) * nc + gid];
+                    fy[f] = geo[(GEO_FY + f) * nc + gid];
+                    wx[f] = geo[(GEO_WX + f) * nc + gid];
+                    wy[f] = geo[(GEO_WY + f) * nc + gid];
+                }
+            }
 #pragma unroll
             for (int v = 0; v < 3; v++) {
                 real d0 = qn[0][v] - qK[v], d1 = qn[1][v] - qK[v], d2 = qn[2][v] - qK[v];
-                real gx = (wx[0] * d0 + wx[1] * d1) + wx[2] * d2;
-                real gy = (wy[0] * d0 + wy[1] * d1) + wy[2] * d2;
+                real D[3];
+                if constexpr (ETA) {
+#pragma unroll
+                    for (int f = 0; f < 3; f++) D[f] = Mf[f][0] * d0 + Mf[f][1] * d1 + Mf[f][2] * d2;
+                } else {
+                    real gx = (wx[0] * d0 + wx[1] * d1) + wx[2] * d2;
+                    real gy = (wy[0] * d0 + wy[1] * d1) + wy[2] * d2;
+#pragma unroll
+                    for (int f = 0; f < 3; f++) D[f] = gx * fx[f] + gy * fy[f];
+                }
                 real qmax = qK[v], qmin = qK[v];
 #pragma unroll
                 for (int f = 0; f < 3; f++) {
@@ -425,10 +513,8 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
                     qmin = vmin(qmin, qn[f][v]);
                 }
                 real alpha = real(1);
-                real D[3];
 #pragma unroll
                 for (int f = 0; f < 3; f++) {
-                    D[f] = gx * fx[f] + gy * fy[f];
                     real phi = real(1);
                     if (D[f] > real(0)) phi = vmin(real(1), (qmax - qK[v]) / D[f]);
                     else if (D[f] < real(0)) phi = vmin(real(1), (qmin - qK[v]) / D[f]);
@@ -467,81 +553,67 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     }
     __syncthreads();
 
-    // C: owned faces, one flux each (Sec. 2.2).  The thread of block cell tid
-    // keeps that cell's face codes and ownership bits for phase D.
-    uint16_t my_code[3] = {NBR_WALL, NBR_WALL, NBR_WALL};
-    int my_owned = 0;
-    if (tid < ncell) {
-        const int gid = c0 + tid;
-        int items[3], n = 0;
-#pragma unroll
-        for (int f = 0; f < 3; f++) {
-            uint16_t code = a.nbrl[f * nc + gid];
-            my_code[f] = code;
-            bool owned = code == NBR_WALL || (code >> 2) >= B || (int)(code >> 2) > tid;
-            if (owned) { items[n++] = (tid << 2) | f; my_owned |= 1 << f; }
-        }
-        if (n) {
-            int pos = atomicAdd(&qcount, n);
-            for (int k = 0; k < n; k++) queue[pos + k] = (uint16_t)items[k];
-        }
-    }
-    __syncthreads();
+    // C: owned faces, one flux each (Sec. 2.2).  The two face values a face
+    // reads are used by no other face, so its thread overwrites them with the
+    // two sides' terms l [Phi + P_s n_s] (the other side's flux and normal are
+    // the exact negations, the face length the same).
     const int nq = qcount;
     for (int q = tid; q < nq; q += blockDim.x) {
-        int item = queue[q];
-        int l = item >> 2, f = item & 3;
-        int gid = c0 + l;
-        uint16_t code = a.nbrl[f * nc + gid];
-        bool wall = code == NBR_WALL;
+        const int item = queue[q];
+        const int l = item >> 2, f = item & 3;
+        const int gid = c0 + l;
+        const uint16_t code = sCode[f * B + l];
+        const bool wall = code == NBR_WALL;
+        const int nl = code >> 2, nf = code & 3;
+        const int sL = f * L + l, sR = nf * L + nl;
         real HfR = real(0), HufR = real(0), HvfR = real(0), zR = real(0);
-        if (!wall) {
-            int nl = code >> 2, nf = code & 3;
-            HfR = fH[nf * L + nl]; HufR = fHu[nf * L + nl]; HvfR = fHv[nf * L + nl];
-            zR = sz[nl];
-        }
-        real Phi[3], PL, PR, am;
+        if (!wall) { HfR = fH[sR]; HufR = fHu[sR]; HvfR = fHv[sR]; zR = sz[nl]; }
+        real Phi[3], PL, PR, am, nx, ny, len;
         if constexpr (ETA) {
-            float eR = wall ? 0.f : sH[code >> 2];
-            face_flux_dev(g, half_g, hthr, fH[f * L + l], fHu[f * L + l], fHv[f * L + l], sz[l], sH[l],
-                          HfR, HufR, HvfR, zR, eR, geo[(GEO_NX + f) * nc + gid],
-                          geo[(GEO_NY + f) * nc + gid], wall, Phi, PL, PR, am);
+            float eR = wall ? 0.f : sH[nl];
+            float2 nv = g32_normal(geo, gid, f);
+            nx = nv.x; ny = nv.y;
+            len = geo[(size_t)gid * G32 + 16 + f];
+            face_flux_dev(g, half_g, hthr, fH[sL], fHu[sL], fHv[sL], sz[l], sH[l],
+                          HfR, HufR, HvfR, zR, eR, nx, ny, wall, Phi, PL, PR, am);
         } else {
-            face_flux<real>(g, half_g, hthr, fH[f * L + l], fHu[f * L + l], fHv[f * L + l], sz[l],
-                            HfR, HufR, HvfR, zR, geo[(GEO_NX + f) * nc + gid],
-                            geo[(GEO_NY + f) * nc + gid], wall, Phi, PL, PR, am);
+            nx = geo[(GEO_NX + f) * nc + gid];
+            ny = geo[(GEO_NY + f) * nc + gid];
+            len = geo[(GEO_LEN + f) * nc + gid];
+            face_flux<real>(g, half_g, hthr, fH[sL], fHu[sL], fHv[sL], sz[l],
+                            HfR, HufR, HvfR, zR, nx, ny, wall, Phi, PL, PR, am);
         }
-        int s = f * B + l;
-        oP0[s] = Phi[0]; oP1[s] = Phi[1]; oP2[s] = Phi[2];
-        oPL[s] = PL; oPR[s] = PR; oA[s] = am;
+        const real t0 = len * Phi[0];
+        fH[sL] = t0;
+        fHu[sL] = len * (Phi[1] + PL * nx);
+        fHv[sL] = len * (Phi[2] + PL * ny);
+        if (!wall) {
+            fH[sR] = -t0;
+            fHu[sR] = -(len * (Phi[1] + PR * nx));
+            fHv[sR] = -(len * (Phi[2] + PR * ny));
+        }
+        if (STAGE == 1) {
+            const real la = len * am;
+            oA[f * B + l] = la;
+            if (!wall && nl < B) oA[nf * B + nl] = la;
+        }
     }
     __syncthreads();
 
     // D: residual R_K = -(1/|K|) sum_f l_f [Phi_f + (0, P_{K,f} n_f)], faces in local order
+    if (tid == 0) qcount = 0;     // every thread read it before the barrier above
     if (tid < ncell) {
         const int l = tid;
         const int gid = c0 + l;
         real aH = real(0), aHu = real(0), aHv = real(0), am = real(0);
+        const real area = ETA ? geo[(size_t)gid * G32 + 19] : geo[GEO_AREA * nc + gid];
 #pragma unroll
         for (int f = 0; f < 3; f++) {
-            const uint16_t code = my_code[f];
-            const bool owned = (my_owned >> f) & 1;
-            real P0, P1, P2, P, sa;
-            if (owned) {
-                int s = f * B + l;
-                P0 = oP0[s]; P1 = oP1[s]; P2 = oP2[s]; P = oPL[s]; sa = oA[s];
-            } else {
-                int s = (code & 3) * B + (code >> 2);
-                P0 = -oP0[s]; P1 = -oP1[s]; P2 = -oP2[s]; P = oPR[s]; sa = oA[s];
-            }
-            real len = geo[(GEO_LEN + f) * nc + gid];
-            real nx = geo[(GEO_NX + f) * nc + gid], ny = geo[(GEO_NY + f) * nc + gid];
-            aH = aH + len * P0;
-            aHu = aHu + len * (P1 + P * nx);
-            aHv = aHv + len * (P2 + P * ny);
-            if (STAGE == 1) am = vmax(am, len * sa);
+            aH = aH + fH[f * L + l];
+            aHu = aHu + fHu[f * L + l];
+            aHv = aHv + fHv[f * L + l];
+            if (STAGE == 1) am = vmax(am, oA[f * B + l]);
         }
-        real area = geo[GEO_AREA * nc + gid];
         real RH = -aH / area, RHu = -aHu / area, RHv = -aHv / area;
         if (STAGE == 1) {
             a.R0[gid] = RH;
@@ -549,10 +621,9 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             a.R0[2 * nc + gid] = RHv;
             if (am > real(0)) my_min = vmin(my_min, area / (real(3) * am));
         } else {
-            real H0 = a.w[gid], Hu0 = a.w[nc + gid], Hv0 = a.w[2 * nc + gid];
-            real W = real(0.5) * H0 + real(0.5) * (sH[l] + dt * RH);
-            real Hu = real(0.5) * Hu0 + real(0.5) * (sHu[l] + dt * RHu);
-            real Hv = real(0.5) * Hv0 + real(0.5) * (sHv[l] + dt * RHv);
+            real W = real(0.5) * wn[0] + real(0.5) * (sH[l] + dt * RH);
+            real Hu = real(0.5) * wn[1] + real(0.5) * (sHu[l] + dt * RHu);
+            real Hv = real(0.5) * wn[2] + real(0.5) * (sHv[l] + dt * RHv);
             real H = ETA ? W - sz[l] : W;
             uint8_t branch = 0;
             if (H < real(0)) {
@@ -574,8 +645,14 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     __syncthreads();
 }
 
+// Resident CTAs per SM asked of the register allocator: the FP32 256-thread
+// kernels are latency-bound, and 6 CTAs (40 registers, a few spilled) beat 5
+// (48) and 4 (63, no bound) on the 10M-triangle basin; FP64 is left unbounded.
+template <typename real, int MAXT> struct StageMinCtas { static constexpr int value = 1; };
+template <> struct StageMinCtas<float, 256> { static constexpr int value = 6; };
+
 template <typename real, int STAGE, int MAXT>
-__global__ void __launch_bounds__(MAXT) stage_kernel(const KArgs<real> a)
+__global__ void __launch_bounds__(MAXT, StageMinCtas<real, MAXT>::value) stage_kernel(const KArgs<real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int qcount;
@@ -589,6 +666,8 @@ __global__ void __launch_bounds__(MAXT) stage_kernel(const KArgs<real> a)
     real my_min = real_inf<real>();
     long long my_neg = 0;
     bool bad = false;
+    if (tid == 0) qcount = 0;
+    __syncthreads();
 
     for (int b = blockIdx.x; b < a.nblocks; b += gridDim.x)
         process_block<real, STAGE>(a, b, dt, smem_raw, qcount, my_min, my_neg, bad);
@@ -659,6 +738,7 @@ __global__ void __launch_bounds__(256) batch_stage_kernel(const BatchMesh<real> 
         s_min[e] = min_bits(real_inf<real>());
         s_dt[e] = STAGE == 2 ? (real)step_dt<real>(sc_all + e, p0.cfl, p0.dt_fixed, p0.dt_max, p0.t_end) : real(0);
     }
+    if (tid == 0) qcount = 0;
     __syncthreads();
     long long my_neg = 0;
     bool bad = false;
