@@ -71,7 +71,8 @@ typedef struct vg_params {
     int32_t block_threads; /* threads per thread block of the step kernels: a
                               multiple of 32 from block_cells to 2 x block_cells
                               and at most 512 (the extra threads share the halo
-                              and face work); 0 = block_cells                     */
+                              and face work); 0 = block_cells for FP32 and
+                              min(2 x block_cells, 512) for FP64                  */
 } vg_params;
 
 /* Run diagnostics (vg_get_diagnostics). */

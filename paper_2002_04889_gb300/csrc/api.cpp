@@ -147,11 +147,15 @@ DevPtrs dev_ptrs(const vg_ctx *c)
     d.nc = c->hm.nc;
     d.block = c->hm.block;
     {
+        // default: one thread per block cell (FP32); FP64, bound by its arithmetic
+        // rate, gains from two threads per cell for the halo and face work
         int t = c->prm.block_threads;
+        if (t == 0 && c->precision == 64) t = std::min(2 * c->hm.block, 512);
         d.threads = (t >= c->hm.block && t <= 2 * c->hm.block && t <= 512) ? t : c->hm.block;
     }
     d.nblocks = c->hm.nblocks;
     d.max_halo = c->hm.max_halo;
+    d.max_ring1 = c->hm.max_ring1;
     d.n_gauges = c->n_gauges;
     d.ring_cap = kRingCap;
     d.geo = c->geo;
@@ -267,9 +271,10 @@ int upload_mesh_arrays(vg_ctx *c)
     return upload_partition(c);
 }
 
-size_t stage_smem(const vg_ctx *c, int block, int max_halo)
+size_t stage_smem(const vg_ctx *c, int block, int max_halo, int max_ring1)
 {
-    return c->precision == 64 ? stage_smem_f64(block, max_halo) : stage_smem_f32(block, max_halo);
+    return c->precision == 64 ? stage_smem_f64(block, max_halo, max_ring1)
+                              : stage_smem_f32(block, max_halo, max_ring1);
 }
 
 // Halve the block size until the stage kernels' shared memory (block + two-ring
@@ -279,7 +284,7 @@ int fit_blocks(vg_ctx *c)
 {
     int limit = 0;
     VG_CUDA(c, cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-    while (stage_smem(c, c->hm.block, c->hm.max_halo) > (size_t)limit) {
+    while (stage_smem(c, c->hm.block, c->hm.max_halo, c->hm.max_ring1) > (size_t)limit) {
         if (c->hm.block <= 32)
             return fail(c, VG_EINVAL, "mesh blocks need more shared memory than the device has; renumber the mesh");
         int rc = partition_blocks(c->hm, c->hm.block / 2, c->err);

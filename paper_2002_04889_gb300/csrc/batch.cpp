@@ -106,7 +106,7 @@ int rebuild(vg_batch *b)
     size_t eb = b->precision == 64 ? batch_mesh_bytes_f64() : batch_mesh_bytes_f32();
     size_t nm = b->meshes.size();
     std::vector<unsigned char> host(eb * nm);
-    int block = 0, max_halo = 0;
+    int block = 0, max_halo = 0, max_ring1 = 0;
     for (int parity = 0; parity < 2; parity++) {
         int item = 0;
         for (size_t m = 0; m < nm; m++) {
@@ -125,14 +125,15 @@ int rebuild(vg_batch *b)
             if (block && block != d.block) return bfail(b, VG_EINVAL, "meshes of a batch must share one block size");
             block = d.block;
             max_halo = std::max(max_halo, (int)d.max_halo);
+            max_ring1 = std::max(max_ring1, (int)d.max_ring1);
         }
         b->n_items = item;
         if (b->table[parity]) cudaFree(b->table[parity]);
         VB_CUDA(b, cudaMalloc(&b->table[parity], eb * nm));
         VB_CUDA(b, cudaMemcpy(b->table[parity], host.data(), eb * nm, cudaMemcpyHostToDevice));
     }
-    int e = b->precision == 64 ? batch_config_f64(block, max_halo, b->grid, b->smem)
-                               : batch_config_f32(block, max_halo, b->grid, b->smem);
+    int e = b->precision == 64 ? batch_config_f64(block, max_halo, max_ring1, b->grid, b->smem)
+                               : batch_config_f32(block, max_halo, max_ring1, b->grid, b->smem);
     if (e) return bcuda(b, (cudaError_t)e, "batched launch configuration");
     if (b->grid > b->n_items) b->grid = b->n_items;
     b->dirty = false;

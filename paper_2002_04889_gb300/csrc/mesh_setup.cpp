@@ -354,15 +354,17 @@ int partition_blocks(HostMesh &m, int block, std::string &err)
     }
     m.halo_ptr.assign(nb + 1, 0);
     m.halo_n1.assign(nb, 0);
-    int32_t mh = 0;
+    int32_t mh = 0, m1 = 0;
     for (int32_t b = 0; b < nb; b++) {
         int32_t n = (int32_t)(r1[b].size() + r2[b].size());
         m.halo_ptr[b + 1] = m.halo_ptr[b] + n;
         m.halo_n1[b] = (int32_t)r1[b].size();
         mh = std::max(mh, n);
+        m1 = std::max(m1, m.halo_n1[b]);
     }
     if (block + mh >= (1 << 14) - 1) { err = "a block's halo is too large"; return VG_EINVAL; }
     m.max_halo = mh;
+    m.max_ring1 = m1;
     m.halo_ids.resize(m.halo_ptr[nb]);
     m.ring1_nbr.assign(3 * (size_t)m.halo_ptr[nb], NBR_WALL);
     std::vector<uint16_t> nbrl(3 * nc, NBR_WALL);

@@ -2,7 +2,7 @@
 #include "step_kernels.cuh"
 
 namespace vg {
-size_t stage_smem_f32(int block, int max_halo) { return stage_smem_bytes<float>(block, max_halo); }
+size_t stage_smem_f32(int block, int max_halo, int max_ring1) { return stage_smem_bytes<float>(block, max_halo, max_ring1); }
 int stage_config_f32(const DevPtrs &d, int stage, LaunchCfg &cfg) { return stage_config<float>(d, stage, cfg); }
 int launch_stage1_f32(const DevPtrs &d, const StepParams &p, const void *w_in, const LaunchCfg &c, void *stream)
 {
@@ -18,7 +18,10 @@ void fill_batch_mesh_f32(void *dst, const DevPtrs &d, const StepParams &p, const
 {
     fill_batch_mesh<float>(dst, d, p, w_in, w_out, n_scen, first_item, first_entry);
 }
-int batch_config_f32(int block, int max_halo, int &grid, size_t &smem) { return batch_config<float>(block, max_halo, grid, smem); }
+int batch_config_f32(int block, int max_halo, int max_ring1, int &grid, size_t &smem)
+{
+    return batch_config<float>(block, max_halo, max_ring1, grid, smem);
+}
 int launch_batch_step_f32(const void *table, int n_mesh, int n_items, int n_entries, DevScalars *sc_all, int block,
                           int grid, size_t smem, const StepParams &p, void *stream)
 {

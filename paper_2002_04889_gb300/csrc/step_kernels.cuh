@@ -47,7 +47,7 @@ namespace vg {
 template <typename real>
 struct KArgs {
     int64_t nc;
-    int block, nblocks, max_halo, order;
+    int block, nblocks, max_halo, max_ring1, order;
     const real *geo;        // [GEO_ROWS][nc]
     const real *z;          // [nc]
     const int32_t *nbr;     // [3][nc]
@@ -255,7 +255,7 @@ __device__ __forceinline__ void face_flux_dev(float g, float half_g, float hthr,
 {
     float HfL = efL - zL;
     float uL = 0.f, vL = 0.f;
-    if (HfL > hthr) { uL = HufL / HfL; vL = HvfL / HfL; }
+    if (HfL > hthr) { const float r = 1.f / HfL; uL = HufL * r; vL = HvfL * r; }
     float unL = uL * nx + vL * ny;
     float utL = -uL * ny + vL * nx;
     float HsL, HsR, unR, utR, ds, HfR;
@@ -269,7 +269,7 @@ __device__ __forceinline__ void face_flux_dev(float g, float half_g, float hthr,
     } else {
         HfR = efR - zR;
         float uR = 0.f, vR = 0.f;
-        if (HfR > hthr) { uR = HufR / HfR; vR = HvfR / HfR; }
+        if (HfR > hthr) { const float r = 1.f / HfR; uR = HufR * r; vR = HvfR * r; }
         unR = uR * nx + vR * ny;
         utR = -uR * ny + vR * nx;
         float zs = fmaxf(zL, zR);
@@ -320,15 +320,7 @@ __device__ __forceinline__ void face_flux_dev(float g, float half_g, float hthr,
     QR = half_g * ((efR - eR) * (HfR + HR) + HsR * ds);
 }
 
-template <typename real>
-__host__ __device__ inline size_t stage_smem_bytes(int block, int max_halo)
-{
-    size_t L = (size_t)block + max_halo;
-    return sizeof(real) * (13 * L + 3 * (size_t)block) + sizeof(int32_t) * L +
-           sizeof(uint16_t) * 6 * (size_t)block + 16;
-}
-
-// Stage state of one local cell l (global id gid) into shared memory.
+// Stored state of cell gid as seen by the stage, and its bed.
 template <typename real, int STAGE>
 __device__ __forceinline__ bool stage_cell(const KArgs<real> &a, int gid, real dt, real &W, real &Hu, real &Hv,
                                            real &zc, real *wn = nullptr)
@@ -337,32 +329,61 @@ __device__ __forceinline__ bool stage_cell(const KArgs<real> &a, int gid, real d
     return stage_state<real, STAGE>(a, gid, dt, zc, W, Hu, Hv, wn);
 }
 
+// Four reals in shared memory, moved as one 16-byte (FP32) or two 16-byte
+// (FP64) accesses.
+__device__ __forceinline__ void ld4(const float *p, float &x, float &y, float &z, float &w)
+{
+    float4 v = *reinterpret_cast<const float4 *>(p);
+    x = v.x; y = v.y; z = v.z; w = v.w;
+}
+__device__ __forceinline__ void st4(float *p, float x, float y, float z, float w)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(x, y, z, w);
+}
+__device__ __forceinline__ void ld4(const double *p, double &x, double &y, double &z, double &w)
+{
+    double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    x = a.x; y = a.y; z = b.x; w = b.y;
+}
+__device__ __forceinline__ void st4(double *p, double x, double y, double z, double w)
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(x, y);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(z, w);
+}
+
+// Shared memory of one CTA: cell states [L] x 4, face slots [3][L1] x 4 (L1 =
+// block + ring 1), global ids [L1], face codes and owned-face queue [3B] each.
+template <typename real>
+__host__ __device__ inline size_t stage_smem_bytes(int block, int max_halo, int max_ring1)
+{
+    size_t L = (size_t)block + max_halo, L1 = (size_t)block + max_ring1;
+    return sizeof(real) * 4 * (L + 3 * L1) + sizeof(int32_t) * L1 + sizeof(uint16_t) * 6 * (size_t)block + 16;
+}
+
 // One block of cells for one scenario: phases A-D (see the top of this file).
 // my_min collects the thread's stage-1 CFL bound, my_neg its negative-depth
 // events, bad a non-finite result.  Every thread of the CTA must call it, and
 // qcount must be zero on entry (it is zero again on return).
+//
+// Shared layout: sW[l] = (W, Hu, Hv, z) of local cell l (W = eta for FP32, H
+// for FP64); sF[f][l] = face values (W_f, Hu_f, Hv_f, x) of face f of cell l
+// after phase B, and after phase C the cell's own term
+// (l_f Phi_0, l_f (Phi_1 + P n_x), l_f (Phi_2 + P n_y), x); x is l_f a_f in
+// stage 1 and, for block cells in stage 2, component f of w^n.
 template <typename real, int STAGE>
 __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b, const real dt,
                                               unsigned char *smem_raw, int &qcount, real &my_min,
                                               long long &my_neg, bool &bad)
 {
-
     const int B = a.block;
     const int L = B + a.max_halo;
+    const int L1 = B + a.max_ring1;
     const int nc = (int)a.nc;    // per-cell arrays hold < 2^31 entries (checked at upload)
-    real *sH = reinterpret_cast<real *>(smem_raw);
-    real *sHu = sH + L;
-    real *sHv = sHu + L;
-    real *sz = sHv + L;
-    // [3][L] face values of block + ring-1 cells after phase B; after phase C the
-    // slot (f, l) of a block cell holds that cell's own term l_f [Phi_f + P_{K,f} n_f]
-    real *fH = sz + L;
-    real *fHu = fH + 3 * L;
-    real *fHv = fHu + 3 * L;
-    real *oA = fHv + 3 * L;       // [3][B] l_f a_f of block cells (stage 1)
-    int32_t *sGid = reinterpret_cast<int32_t *>(oA + 3 * B);   // [L] global id of each local cell
-    uint16_t *sCode = reinterpret_cast<uint16_t *>(sGid + L);  // [3][B] face codes of block cells
-    uint16_t *queue = sCode + 3 * B;                            // [3B] owned faces
+    real *sW = reinterpret_cast<real *>(smem_raw);          // [L][4]
+    real *sF = sW + 4 * L;                                   // [3][L1][4]
+    int32_t *sGid = reinterpret_cast<int32_t *>(sF + 12 * L1);   // [L1]
+    uint16_t *sCode = reinterpret_cast<uint16_t *>(sGid + L1);   // [3][B]
+    uint16_t *queue = sCode + 3 * B;                              // [3B]
 
     constexpr bool ETA = EtaForm<real>::value;
     const int tid = threadIdx.x;
@@ -376,43 +397,38 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     const int n1 = a.halo_n1[b];
 
     // A: block + ring-1 + ring-2 states into shared memory.  Thread tid < B
-    // takes block cell tid (and keeps w^n of it for stage 2's final update) and
-    // queues the faces that cell owns: a wall, a face to the halo, or a face to
+    // takes block cell tid and queues the faces that cell owns: a wall, a face to the halo, or a face to
     // a block cell of higher local index.
-    real wn[3] = {real(0), real(0), real(0)};
     {
         int gh = -1;
         if (tid < nh) gh = a.halo_ids[h0 + tid];
         int owned = 0;
         if (tid < ncell) {
             const int gid = c0 + tid;
-            uint16_t code[3];
 #pragma unroll
             for (int f = 0; f < 3; f++) {
-                code[f] = a.nbrl[f * nc + gid];
-                sCode[f * B + tid] = code[f];
-                if (code[f] == NBR_WALL || (code[f] >> 2) >= B || (int)(code[f] >> 2) > tid) owned |= 1 << f;
+                const uint16_t code = a.nbrl[f * nc + gid];
+                sCode[f * B + tid] = code;
+                if (code == NBR_WALL || (code >> 2) >= B || (int)(code >> 2) > tid) owned |= 1 << f;
             }
             real W, Hu, Hv, zc;
-            bool neg = stage_cell<real, STAGE>(a, gid, dt, W, Hu, Hv, zc, wn);
+            bool neg = stage_cell<real, STAGE>(a, gid, dt, W, Hu, Hv, zc);
             if (neg) my_neg++;
-            sH[tid] = W; sHu[tid] = Hu; sHv[tid] = Hv; sz[tid] = zc;
+            st4(sW + 4 * tid, W, Hu, Hv, zc);
             sGid[tid] = gid;
         }
         if (gh >= 0) {
             real W, Hu, Hv, zc;
             stage_cell<real, STAGE>(a, gh, dt, W, Hu, Hv, zc);
-            const int l = B + tid;
-            sH[l] = W; sHu[l] = Hu; sHv[l] = Hv; sz[l] = zc;
-            sGid[l] = gh;
+            st4(sW + 4 * (B + tid), W, Hu, Hv, zc);
+            if (tid < n1) sGid[B + tid] = gh;
         }
         for (int h = tid + blockDim.x; h < nh; h += blockDim.x) {
             const int gid = a.halo_ids[h0 + h];
             real W, Hu, Hv, zc;
             stage_cell<real, STAGE>(a, gid, dt, W, Hu, Hv, zc);
-            const int l = B + h;
-            sH[l] = W; sHu[l] = Hu; sHv[l] = Hv; sz[l] = zc;
-            sGid[l] = gid;
+            st4(sW + 4 * (B + h), W, Hu, Hv, zc);
+            if (h < n1) sGid[B + h] = gid;
         }
         // warp-aggregated queue append: n = popcount(owned) in 0..3
         const int n = __popc(owned);
@@ -434,15 +450,16 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     // Barth-Jespersen limiter); every neighbour is in shared memory
     for (int l = tid; l < B + n1; l += blockDim.x) {
         if (l < B && l >= ncell) continue;
-        int gid = sGid[l];
-        const real HuK = sHu[l], HvK = sHv[l], zK = sz[l];
-        const real HK = ETA ? sH[l] - zK : sH[l];
-        real qK[3] = {ETA ? sH[l] : HK + zK, HuK, HvK};
+        const int gid = sGid[l];
+        real WK, HuK, HvK, zK;
+        ld4(sW + 4 * l, WK, HuK, HvK, zK);
+        const real HK = ETA ? WK - zK : WK;
+        real qK[3] = {ETA ? WK : HK + zK, HuK, HvK};
         real qn[3][3];
         bool recon = (a.order == 2) && (HK > hthr);
+#pragma unroll
         for (int f = 0; f < 3; f++) {
             bool wall;
-            real Wj = real(0), Huj = real(0), Hvj = real(0), zj = real(0);
             int nl;
             if (l < B) {
                 uint16_t code = sCode[f * B + l];
@@ -453,8 +470,9 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
                 wall = code == NBR_WALL;
                 nl = code;
             }
-            if (!wall) { Wj = sH[nl]; Huj = sHu[nl]; Hvj = sHv[nl]; zj = sz[nl]; }
             if (!wall) {
+                real Wj, Huj, Hvj, zj;
+                ld4(sW + 4 * nl, Wj, Huj, Hvj, zj);
                 const real Hj = ETA ? Wj - zj : Wj;
                 qn[f][0] = ETA ? Wj : Hj + zj;
                 qn[f][1] = Huj;
@@ -486,6 +504,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
                 Mf[1][0] = a0.w; Mf[1][1] = a1.x; Mf[1][2] = a1.y;
                 Mf[2][0] = a1.z; Mf[2][1] = a1.w; Mf[2][2] = a2.x;
             } else {
+#pragma unroll
                 for (int f = 0; f < 3; f++) {
                     fx[f] = geo[(GEO_FX + f) * nc + gid];
                     fy[f] = geo[(GEO_FY + f) * nc + gid];
@@ -534,14 +553,12 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         }
         if (!recon) {
 #pragma unroll
-            for (int f = 0; f < 3; f++) { Hf[f] = ETA ? sH[l] : HK; Huf[f] = HuK; Hvf[f] = HvK; }
+            for (int f = 0; f < 3; f++) { Hf[f] = ETA ? WK : HK; Huf[f] = HuK; Hvf[f] = HvK; }
         }
+        real wn[3] = {real(0), real(0), real(0)};     // stage 2: w^n of a block cell (L1/L2 hit)
+        if (STAGE == 2 && l < B) { wn[0] = a.w[gid]; wn[1] = a.w[nc + gid]; wn[2] = a.w[2 * nc + gid]; }
 #pragma unroll
-        for (int f = 0; f < 3; f++) {
-            fH[f * L + l] = Hf[f];
-            fHu[f * L + l] = Huf[f];
-            fHv[f * L + l] = Hvf[f];
-        }
+        for (int f = 0; f < 3; f++) st4(sF + 4 * (f * L1 + l), Hf[f], Huf[f], Hvf[f], wn[f]);
         if (a.fv_out && l < B) {
 #pragma unroll
             for (int f = 0; f < 3; f++) {
@@ -565,38 +582,36 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         const uint16_t code = sCode[f * B + l];
         const bool wall = code == NBR_WALL;
         const int nl = code >> 2, nf = code & 3;
-        const int sL = f * L + l, sR = nf * L + nl;
-        real HfR = real(0), HufR = real(0), HvfR = real(0), zR = real(0);
-        if (!wall) { HfR = fH[sR]; HufR = fHu[sR]; HvfR = fHv[sR]; zR = sz[nl]; }
+        real *pL = sF + 4 * (f * L1 + l);
+        real *pR = sF + 4 * (nf * L1 + nl);
+        real WfL, HufL, HvfL, xL, WL, HuK, HvK, zL;
+        ld4(pL, WfL, HufL, HvfL, xL);
+        ld4(sW + 4 * l, WL, HuK, HvK, zL);
+        real WfR = real(0), HufR = real(0), HvfR = real(0), xR = real(0), WR = real(0), zR = real(0);
+        if (!wall) {
+            real Huj, Hvj;
+            ld4(pR, WfR, HufR, HvfR, xR);
+            ld4(sW + 4 * nl, WR, Huj, Hvj, zR);
+        }
         real Phi[3], PL, PR, am, nx, ny, len;
         if constexpr (ETA) {
-            float eR = wall ? 0.f : sH[nl];
             float2 nv = g32_normal(geo, gid, f);
             nx = nv.x; ny = nv.y;
             len = geo[(size_t)gid * G32 + 16 + f];
-            face_flux_dev(g, half_g, hthr, fH[sL], fHu[sL], fHv[sL], sz[l], sH[l],
-                          HfR, HufR, HvfR, zR, eR, nx, ny, wall, Phi, PL, PR, am);
+            face_flux_dev(g, half_g, hthr, WfL, HufL, HvfL, zL, WL,
+                          WfR, HufR, HvfR, zR, WR, nx, ny, wall, Phi, PL, PR, am);
         } else {
             nx = geo[(GEO_NX + f) * nc + gid];
             ny = geo[(GEO_NY + f) * nc + gid];
             len = geo[(GEO_LEN + f) * nc + gid];
-            face_flux<real>(g, half_g, hthr, fH[sL], fHu[sL], fHv[sL], sz[l],
-                            HfR, HufR, HvfR, zR, nx, ny, wall, Phi, PL, PR, am);
+            face_flux<real>(g, half_g, hthr, WfL, HufL, HvfL, zL,
+                            WfR, HufR, HvfR, zR, nx, ny, wall, Phi, PL, PR, am);
         }
         const real t0 = len * Phi[0];
-        fH[sL] = t0;
-        fHu[sL] = len * (Phi[1] + PL * nx);
-        fHv[sL] = len * (Phi[2] + PL * ny);
-        if (!wall) {
-            fH[sR] = -t0;
-            fHu[sR] = -(len * (Phi[1] + PR * nx));
-            fHv[sR] = -(len * (Phi[2] + PR * ny));
-        }
-        if (STAGE == 1) {
-            const real la = len * am;
-            oA[f * B + l] = la;
-            if (!wall && nl < B) oA[nf * B + nl] = la;
-        }
+        const real la = len * am;
+        st4(pL, t0, len * (Phi[1] + PL * nx), len * (Phi[2] + PL * ny), STAGE == 1 ? la : xL);
+        if (!wall)
+            st4(pR, -t0, -(len * (Phi[1] + PR * nx)), -(len * (Phi[2] + PR * ny)), STAGE == 1 ? la : xR);
     }
     __syncthreads();
 
@@ -606,13 +621,16 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         const int l = tid;
         const int gid = c0 + l;
         real aH = real(0), aHu = real(0), aHv = real(0), am = real(0);
+        real x[3];
         const real area = ETA ? geo[(size_t)gid * G32 + 19] : geo[GEO_AREA * nc + gid];
 #pragma unroll
         for (int f = 0; f < 3; f++) {
-            aH = aH + fH[f * L + l];
-            aHu = aHu + fHu[f * L + l];
-            aHv = aHv + fHv[f * L + l];
-            if (STAGE == 1) am = vmax(am, oA[f * B + l]);
+            real t0, t1, t2;
+            ld4(sF + 4 * (f * L1 + l), t0, t1, t2, x[f]);
+            aH = aH + t0;
+            aHu = aHu + t1;
+            aHv = aHv + t2;
+            if (STAGE == 1) am = vmax(am, x[f]);
         }
         real RH = -aH / area, RHu = -aHu / area, RHv = -aHv / area;
         if (STAGE == 1) {
@@ -621,14 +639,16 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             a.R0[2 * nc + gid] = RHv;
             if (am > real(0)) my_min = vmin(my_min, area / (real(3) * am));
         } else {
-            real W = real(0.5) * wn[0] + real(0.5) * (sH[l] + dt * RH);
-            real Hu = real(0.5) * wn[1] + real(0.5) * (sHu[l] + dt * RHu);
-            real Hv = real(0.5) * wn[2] + real(0.5) * (sHv[l] + dt * RHv);
-            real H = ETA ? W - sz[l] : W;
+            real W1, Hu1, Hv1, z1;
+            ld4(sW + 4 * l, W1, Hu1, Hv1, z1);
+            real W = real(0.5) * x[0] + real(0.5) * (W1 + dt * RH);
+            real Hu = real(0.5) * x[1] + real(0.5) * (Hu1 + dt * RHu);
+            real Hv = real(0.5) * x[2] + real(0.5) * (Hv1 + dt * RHv);
+            real H = ETA ? W - z1 : W;
             uint8_t branch = 0;
             if (H < real(0)) {
                 my_neg++;
-                W = ETA ? sz[l] : real(0);
+                W = ETA ? z1 : real(0);
                 Hu = real(0); Hv = real(0);
                 branch = 2;
             } else if (H <= hthr) {
@@ -645,11 +665,14 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     __syncthreads();
 }
 
-// Resident CTAs per SM asked of the register allocator: the FP32 256-thread
-// kernels are latency-bound, and 6 CTAs (40 registers, a few spilled) beat 5
-// (48) and 4 (63, no bound) on the 10M-triangle basin; FP64 is left unbounded.
+// Resident CTAs per SM asked of the register allocator.  The FP32 kernels are
+// latency-bound: 40 registers a thread (a few spilled) and ~48 resident warps
+// beat fewer warps with more registers (6 CTAs of 256 threads: 40 registers;
+// 5: 48; unbounded: 63, 4 CTAs).  FP64 is left unbounded.
 template <typename real, int MAXT> struct StageMinCtas { static constexpr int value = 1; };
 template <> struct StageMinCtas<float, 256> { static constexpr int value = 6; };
+template <> struct StageMinCtas<float, 384> { static constexpr int value = 4; };
+template <> struct StageMinCtas<float, 512> { static constexpr int value = 3; };
 
 template <typename real, int STAGE, int MAXT>
 __global__ void __launch_bounds__(MAXT, StageMinCtas<real, MAXT>::value) stage_kernel(const KArgs<real> a)
@@ -803,6 +826,7 @@ KArgs<real> make_args(const DevPtrs &d, const StepParams &p, const void *w_in, v
     a.block = d.block;
     a.nblocks = d.nblocks;
     a.max_halo = d.max_halo;
+    a.max_ring1 = d.max_ring1;
     a.order = p.order;
     a.geo = static_cast<const real *>(d.geo);
     a.z = static_cast<const real *>(d.z);
@@ -834,13 +858,14 @@ template <typename real>
 void *stage_kernel_ptr(int stage, int threads)
 {
     if (threads <= 256) return stage == 1 ? (void *)stage_kernel<real, 1, 256> : (void *)stage_kernel<real, 2, 256>;
+    if (threads <= 384) return stage == 1 ? (void *)stage_kernel<real, 1, 384> : (void *)stage_kernel<real, 2, 384>;
     return stage == 1 ? (void *)stage_kernel<real, 1, 512> : (void *)stage_kernel<real, 2, 512>;
 }
 
 template <typename real>
 int stage_config(const DevPtrs &d, int stage, LaunchCfg &cfg)
 {
-    cfg.smem = stage_smem_bytes<real>(d.block, d.max_halo);
+    cfg.smem = stage_smem_bytes<real>(d.block, d.max_halo, d.max_ring1);
     const void *kern = stage_kernel_ptr<real>(stage, d.threads);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
     if (e != cudaSuccess) return (int)e;
@@ -866,6 +891,9 @@ int launch_stage(const DevPtrs &d, const StepParams &p, int stage, const void *w
     if (d.threads <= 256) {
         if (stage == 1) stage_kernel<real, 1, 256><<<c.grid, d.threads, c.smem, s>>>(a);
         else stage_kernel<real, 2, 256><<<c.grid, d.threads, c.smem, s>>>(a);
+    } else if (d.threads <= 384) {
+        if (stage == 1) stage_kernel<real, 1, 384><<<c.grid, d.threads, c.smem, s>>>(a);
+        else stage_kernel<real, 2, 384><<<c.grid, d.threads, c.smem, s>>>(a);
     } else {
         if (stage == 1) stage_kernel<real, 1, 512><<<c.grid, d.threads, c.smem, s>>>(a);
         else stage_kernel<real, 2, 512><<<c.grid, d.threads, c.smem, s>>>(a);
@@ -874,9 +902,9 @@ int launch_stage(const DevPtrs &d, const StepParams &p, int stage, const void *w
 }
 
 template <typename real>
-int batch_config(int block, int max_halo, int &grid, size_t &smem)
+int batch_config(int block, int max_halo, int max_ring1, int &grid, size_t &smem)
 {
-    smem = stage_smem_bytes<real>(block, max_halo);
+    smem = stage_smem_bytes<real>(block, max_halo, max_ring1);
     int best = 1 << 30;
     for (int stage = 1; stage <= 2; stage++) {
         auto kern = stage == 1 ? batch_stage_kernel<real, 1> : batch_stage_kernel<real, 2>;

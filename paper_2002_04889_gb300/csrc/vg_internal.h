@@ -34,6 +34,7 @@ struct HostMesh {
     int32_t block = 256;                 // cells per block
     int32_t nblocks = 0;
     int32_t max_halo = 0;                // max ring-1 + ring-2 cells of a block
+    int32_t max_ring1 = 0;               // max ring-1 cells of a block
     std::vector<int32_t> new_of_old, old_of_new;
     std::vector<int32_t> vtx;            // [nc][3] local-order vertices (original cell order)
     std::vector<double> geo;             // [GEO_ROWS][nc]  (internal order)
@@ -86,7 +87,7 @@ struct StepParams {
 // Device pointers of one context (element type = the context's real).
 struct DevPtrs {
     int64_t nc;
-    int32_t block, nblocks, max_halo, n_gauges, ring_cap;
+    int32_t block, nblocks, max_halo, max_ring1, n_gauges, ring_cap;
     int32_t threads;        // threads per CTA of the stage kernels (>= block)
     const void *geo;        // FP64: [GEO_ROWS][nc]; FP32: [nc][20] record
     const void *z;          // [nc]
@@ -112,8 +113,8 @@ struct LaunchCfg {
     int grid;        // persistent CTAs
     size_t smem;     // dynamic shared memory per CTA
 };
-size_t stage_smem_f32(int block, int max_halo);
-size_t stage_smem_f64(int block, int max_halo);
+size_t stage_smem_f32(int block, int max_halo, int max_ring1);
+size_t stage_smem_f64(int block, int max_halo, int max_ring1);
 int stage_config_f32(const DevPtrs &d, int stage, LaunchCfg &cfg);
 int stage_config_f64(const DevPtrs &d, int stage, LaunchCfg &cfg);
 int launch_stage1_f32(const DevPtrs &d, const StepParams &p, const void *w_in, const LaunchCfg &c, void *stream);
@@ -131,8 +132,8 @@ void fill_batch_mesh_f32(void *dst, const DevPtrs &d, const StepParams &p, const
                          int first_item, int first_entry);
 void fill_batch_mesh_f64(void *dst, const DevPtrs &d, const StepParams &p, const void *w_in, void *w_out, int n_scen,
                          int first_item, int first_entry);
-int batch_config_f32(int block, int max_halo, int &grid, size_t &smem);
-int batch_config_f64(int block, int max_halo, int &grid, size_t &smem);
+int batch_config_f32(int block, int max_halo, int max_ring1, int &grid, size_t &smem);
+int batch_config_f64(int block, int max_halo, int max_ring1, int &grid, size_t &smem);
 int launch_batch_step_f32(const void *table, int n_mesh, int n_items, int n_entries, DevScalars *sc_all, int block,
                           int grid, size_t smem, const StepParams &p, void *stream);
 int launch_batch_step_f64(const void *table, int n_mesh, int n_items, int n_entries, DevScalars *sc_all, int block,
