@@ -190,6 +190,14 @@ __device__ __forceinline__ void face_flux(real g, real half_g, real hthr,
     PR = half_g * (HfR * HfR - HsR * HsR);
 }
 
+// Approximate reciprocal (PTX rcp.approx.ftz.f32, max error 1 ulp); rcp(0) = +inf.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Deviation form for FP32, literal form for FP64.
 template <typename real> struct EtaForm { static constexpr bool value = false; };
 template <> struct EtaForm<float> { static constexpr bool value = true; };
@@ -255,7 +263,7 @@ __device__ __forceinline__ void face_flux_dev(float g, float half_g, float hthr,
 {
     float HfL = efL - zL;
     float uL = 0.f, vL = 0.f;
-    if (HfL > hthr) { const float r = 1.f / HfL; uL = HufL * r; vL = HvfL * r; }
+    if (HfL > hthr) { const float r = rcp_approx(HfL); uL = HufL * r; vL = HvfL * r; }
     float unL = uL * nx + vL * ny;
     float utL = -uL * ny + vL * nx;
     float HsL, HsR, unR, utR, ds, HfR;
@@ -269,7 +277,7 @@ __device__ __forceinline__ void face_flux_dev(float g, float half_g, float hthr,
     } else {
         HfR = efR - zR;
         float uR = 0.f, vR = 0.f;
-        if (HfR > hthr) { const float r = 1.f / HfR; uR = HufR * r; vR = HvfR * r; }
+        if (HfR > hthr) { const float r = rcp_approx(HfR); uR = HufR * r; vR = HvfR * r; }
         unR = uR * nx + vR * ny;
         utR = -uR * ny + vR * nx;
         float zs = fmaxf(zL, zR);
@@ -302,7 +310,7 @@ __device__ __forceinline__ void face_flux_dev(float g, float half_g, float hthr,
         if (sL >= 0.f) {
             F[0] = FL0; F[1] = FL1; F[2] = FL2;
         } else if (sR >= 0.f) {
-            float rden = 1.f / (sR - sL);
+            float rden = rcp_approx(sR - sL);
             float sLR = sL * sR;
             F[0] = ((sR * FL0 - sL * FR0) - sLR * ds) * rden;
             F[1] = ((sR * FL1 - sL * FR1) + sLR * (qR - qL)) * rden;
@@ -363,7 +371,14 @@ __host__ __device__ inline size_t stage_smem_bytes(int block, int max_halo, int 
 // One block of cells for one scenario: phases A-D (see the top of this file).
 // my_min collects the thread's stage-1 CFL bound, my_neg its negative-depth
 // events, bad a non-finite result.  Every thread of the CTA must call it, and
-// qcount must be zero on entry (it is zero again on return).
+// qcount must be zero on entry (it is zero again after phase D).
+//
+// There is no barrier after phase D: a thread's phase D reads only its own
+// cell's state slot and face slots, the next block's phase A writes state
+// slots of its own cells only, and face slots are next written in phase B,
+// behind the barrier that ends phase A.  Consecutive blocks therefore use the
+// two queue counters alternately (the reset of one in phase D may come after
+// other warps have started the next block).
 //
 // Shared layout: sW[l] = (W, Hu, Hv, z) of local cell l (W = eta for FP32, H
 // for FP64); sF[f][l] = face values (W_f, Hu_f, Hv_f, x) of face f of cell l
@@ -532,12 +547,21 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
                     qmin = vmin(qmin, qn[f][v]);
                 }
                 real alpha = real(1);
+                if constexpr (ETA) {
+                    // phi_f = |r_f| / |D_f| with r_f = qmax - q_K or q_K - qmin by the
+                    // sign of D_f; D_f = 0 gives +inf or NaN, which fminf ignores
+                    const float up = qmax - qK[v], dn = qK[v] - qmin;
 #pragma unroll
-                for (int f = 0; f < 3; f++) {
-                    real phi = real(1);
-                    if (D[f] > real(0)) phi = vmin(real(1), (qmax - qK[v]) / D[f]);
-                    else if (D[f] < real(0)) phi = vmin(real(1), (qmin - qK[v]) / D[f]);
-                    alpha = vmin(alpha, phi);
+                    for (int f = 0; f < 3; f++)
+                        alpha = fminf(alpha, (D[f] > 0.f ? up : dn) * rcp_approx(fabsf(D[f])));
+                } else {
+#pragma unroll
+                    for (int f = 0; f < 3; f++) {
+                        real phi = real(1);
+                        if (D[f] > real(0)) phi = vmin(real(1), (qmax - qK[v]) / D[f]);
+                        else if (D[f] < real(0)) phi = vmin(real(1), (qmin - qK[v]) / D[f]);
+                        alpha = vmin(alpha, phi);
+                    }
                 }
 #pragma unroll
                 for (int f = 0; f < 3; f++) face[f][v] = qK[v] + alpha * D[f];
@@ -662,7 +686,6 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             a.wout[2 * nc + gid] = Hv;
         }
     }
-    __syncthreads();
 }
 
 // Resident CTAs per SM asked of the register allocator.  The FP32 kernels are
@@ -678,7 +701,7 @@ template <typename real, int STAGE, int MAXT>
 __global__ void __launch_bounds__(MAXT, StageMinCtas<real, MAXT>::value) stage_kernel(const KArgs<real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int qcount;
+    __shared__ int qcount[2];
     __shared__ real red_min[32];
     __shared__ long long red_neg[32];
     const int tid = threadIdx.x;
@@ -689,11 +712,12 @@ __global__ void __launch_bounds__(MAXT, StageMinCtas<real, MAXT>::value) stage_k
     real my_min = real_inf<real>();
     long long my_neg = 0;
     bool bad = false;
-    if (tid == 0) qcount = 0;
+    if (tid < 2) qcount[tid] = 0;
     __syncthreads();
 
-    for (int b = blockIdx.x; b < a.nblocks; b += gridDim.x)
-        process_block<real, STAGE>(a, b, dt, smem_raw, qcount, my_min, my_neg, bad);
+    int parity = 0;
+    for (int b = blockIdx.x; b < a.nblocks; b += gridDim.x, parity ^= 1)
+        process_block<real, STAGE>(a, b, dt, smem_raw, qcount[parity], my_min, my_neg, bad);
 
     // CTA-level reductions, then one atomic per CTA
     const int lane = tid & 31, warp = tid >> 5, nwarps = (blockDim.x + 31) >> 5;
@@ -751,7 +775,7 @@ __global__ void __launch_bounds__(256) batch_stage_kernel(const BatchMesh<real> 
                                                           int n_items, int n_entries, DevScalars *sc_all)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int qcount;
+    __shared__ int qcount[2];
     __shared__ unsigned long long s_min[kBatchMaxEntries];
     __shared__ real s_dt[kBatchMaxEntries];
     __shared__ long long red_neg[32];
@@ -761,9 +785,10 @@ __global__ void __launch_bounds__(256) batch_stage_kernel(const BatchMesh<real> 
         s_min[e] = min_bits(real_inf<real>());
         s_dt[e] = STAGE == 2 ? (real)step_dt<real>(sc_all + e, p0.cfl, p0.dt_fixed, p0.dt_max, p0.t_end) : real(0);
     }
-    if (tid == 0) qcount = 0;
+    if (tid < 2) qcount[tid] = 0;
     __syncthreads();
     long long my_neg = 0;
+    int parity = 0;
     bool bad = false;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         int m = 0;
@@ -778,7 +803,8 @@ __global__ void __launch_bounds__(256) batch_stage_kernel(const BatchMesh<real> 
             a.sc += s;
             const int e = bm.first_entry + s;
             real mn = real_inf<real>();
-            process_block<real, STAGE>(a, b, s_dt[e], smem_raw, qcount, mn, my_neg, bad);
+            process_block<real, STAGE>(a, b, s_dt[e], smem_raw, qcount[parity], mn, my_neg, bad);
+            parity ^= 1;
             if (STAGE == 1) {
                 unsigned long long bits = warp_min_bits<real>(mn);
                 if (lane == 0 && bits != min_bits(real_inf<real>())) atomicMin(&s_min[e], bits);
