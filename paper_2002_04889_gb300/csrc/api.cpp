@@ -229,7 +229,7 @@ int upload_mesh_arrays(vg_ctx *c)
     const HostMesh &m = c->hm;
     size_t rs = real_size(c);
     int rc;
-    if ((rc = dmalloc(c, &c->geo, c->precision == 64 ? 8 * GEO_ROWS * m.nc : 4 * 20 * m.nc))) return rc;
+    if ((rc = dmalloc(c, &c->geo, c->precision == 64 ? 8 * GEO_ROWS * m.nc : 4 * 16 * m.nc))) return rc;
     if ((rc = dmalloc(c, &c->z, rs * m.nc))) return rc;
     if ((rc = dmalloc(c, &c->w[0], rs * 3 * m.nc))) return rc;
     if ((rc = dmalloc(c, &c->w[1], rs * 3 * m.nc))) return rc;
@@ -240,22 +240,23 @@ int upload_mesh_arrays(vg_ctx *c)
     if (c->precision == 64) {
         if ((rc = upload_real(c, c->geo, m.geo.data(), m.geo.size()))) return rc;
     } else {
-        // FP32 record per cell (20 floats): M_fj = w_j . (x_f - x_K) formed in FP64,
-        // then the normals, face lengths and area.
+        // FP32 record per cell (16 floats): rows 0 and 1 of M_fj = w_j . (x_f - x_K)
+        // formed in FP64, the area, face lengths and normals:
+        //   M00 M01 M02 M10 | M11 M12 area l0 | nx0 ny0 nx1 ny1 | nx2 ny2 l1 l2
         const int64_t n = m.nc;
-        std::vector<float> r(20 * (size_t)n, 0.0f);
+        std::vector<float> r(16 * (size_t)n, 0.0f);
         for (int64_t k = 0; k < n; k++) {
             auto G = [&](int row) { return m.geo[(size_t)row * n + k]; };
-            float *o = &r[20 * (size_t)k];
-            for (int f = 0; f < 3; f++)
+            float *o = &r[16 * (size_t)k];
+            for (int f = 0; f < 2; f++)
                 for (int j = 0; j < 3; j++)
                     o[3 * f + j] = (float)(G(GEO_WX + j) * G(GEO_FX + f) + G(GEO_WY + j) * G(GEO_FY + f));
+            o[6] = (float)G(GEO_AREA);
             for (int f = 0; f < 3; f++) {
-                o[10 + 2 * f] = (float)G(GEO_NX + f);
-                o[11 + 2 * f] = (float)G(GEO_NY + f);
-                o[16 + f] = (float)G(GEO_LEN + f);
+                o[8 + 2 * f] = (float)G(GEO_NX + f);
+                o[9 + 2 * f] = (float)G(GEO_NY + f);
+                o[f == 0 ? 7 : 13 + f] = (float)G(GEO_LEN + f);
             }
-            o[19] = (float)G(GEO_AREA);
         }
         VG_CUDA(c, cudaMemcpy(c->geo, r.data(), 4 * r.size(), cudaMemcpyHostToDevice));
     }

@@ -202,20 +202,27 @@ __device__ __forceinline__ float rcp_approx(float x)
 template <typename real> struct EtaForm { static constexpr bool value = false; };
 template <> struct EtaForm<float> { static constexpr bool value = true; };
 
-// FP32 cell geometry record, 20 floats (five 16-byte words) per cell:
-//   M00 M01 M02 M10 | M11 M12 M20 M21 | M22 -- nx0 ny0 | nx1 ny1 nx2 ny2 | l0 l1 l2 area
-// with M_fj = w_j . (x_f - x_K): the limited increments of the reconstruction are
+// FP32 cell geometry record, 16 floats (four 16-byte words, 64 bytes) per cell:
+//   M00 M01 M02 M10 | M11 M12 area l0 | nx0 ny0 nx1 ny1 | nx2 ny2 l1 l2
+// with M_fj = w_j . (x_f - x_K): the increments of the reconstruction are
 // D_f = sum_j M_fj (q_j - q_K), the same quantity as grad q . (x_f - x_K) with the
-// least-squares gradient grad q = sum_j w_j (q_j - q_K).  (FP64 keeps the rows
-// GEO_* and evaluates gradient then dot product, in the literal order.)
-constexpr int G32 = 20;
+// least-squares gradient grad q = sum_j w_j (q_j - q_K).  The face midpoints
+// average to the centroid x_K, so D_2 = -(D_0 + D_1) and row 2 is not stored.
+// (FP64 keeps the rows GEO_* and evaluates gradient then dot product, in the
+// literal order.)
+constexpr int G32 = 16;
+constexpr int G32_AREA = 6;
 __device__ __forceinline__ const float4 *g32(const float *geo, int k)
 {
     return reinterpret_cast<const float4 *>(geo + (size_t)k * G32);
 }
 __device__ __forceinline__ float2 g32_normal(const float *geo, int k, int f)
 {
-    return *reinterpret_cast<const float2 *>(geo + (size_t)k * G32 + 10 + 2 * f);
+    return *reinterpret_cast<const float2 *>(geo + (size_t)k * G32 + 8 + 2 * f);
+}
+__device__ __forceinline__ float g32_len(const float *geo, int k, int f)
+{
+    return geo[(size_t)k * G32 + (f == 0 ? 7 : 13 + f)];
 }
 
 // Stored state of cell gid as seen by the stage (H or eta first, then Hu, Hv):
@@ -307,17 +314,13 @@ __device__ __forceinline__ void face_flux_dev(float g, float half_g, float hthr,
         float qL = HsL * unL, qR = HsR * unR;
         float FL0 = qL, FL1 = qL * unL + half_g * HsL * ds, FL2 = qL * utL;
         float FR0 = qR, FR1 = qR * unR - half_g * HsR * ds, FR2 = qR * utR;
-        if (sL >= 0.f) {
-            F[0] = FL0; F[1] = FL1; F[2] = FL2;
-        } else if (sR >= 0.f) {
-            float rden = rcp_approx(sR - sL);
-            float sLR = sL * sR;
-            F[0] = ((sR * FL0 - sL * FR0) - sLR * ds) * rden;
-            F[1] = ((sR * FL1 - sL * FR1) + sLR * (qR - qL)) * rden;
-            F[2] = ((sR * FL2 - sL * FR2) + sLR * (HsR * utR - HsL * utL)) * rden;
-        } else {
-            F[0] = FR0; F[1] = FR1; F[2] = FR2;
-        }
+        // HLL with the speeds clamped to a <= 0 <= b, which also gives F_L when
+        // sL >= 0 and F_R when sR <= 0 (b - a > 0 unless both sides are dry)
+        const float a = fminf(sL, 0.f), b = fmaxf(sR, 0.f);
+        const float rden = rcp_approx(b - a), ab = a * b;
+        F[0] = ((b * FL0 - a * FR0) - ab * ds) * rden;
+        F[1] = ((b * FL1 - a * FR1) + ab * (qR - qL)) * rden;
+        F[2] = ((b * FL2 - a * FR2) + ab * (HsR * utR - HsL * utL)) * rden;
         amax = fmaxf(fabsf(sL), fabsf(sR));
     }
     Phi[0] = F[0];
@@ -510,14 +513,13 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         real Hf[3], Huf[3], Hvf[3];
         if (recon) {
             real face[3][3];
-            real Mf[3][3];          // FP32: M_fj of the record
+            real Mf[2][3];          // FP32: rows 0 and 1 of M
             real fx[3], fy[3], wx[3], wy[3];
             if constexpr (ETA) {
                 const float4 *r = g32(geo, gid);
-                float4 a0 = r[0], a1 = r[1], a2 = r[2];
+                float4 a0 = r[0], a1 = r[1];
                 Mf[0][0] = a0.x; Mf[0][1] = a0.y; Mf[0][2] = a0.z;
                 Mf[1][0] = a0.w; Mf[1][1] = a1.x; Mf[1][2] = a1.y;
-                Mf[2][0] = a1.z; Mf[2][1] = a1.w; Mf[2][2] = a2.x;
             } else {
 #pragma unroll
                 for (int f = 0; f < 3; f++) {
@@ -532,8 +534,9 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
                 real d0 = qn[0][v] - qK[v], d1 = qn[1][v] - qK[v], d2 = qn[2][v] - qK[v];
                 real D[3];
                 if constexpr (ETA) {
-#pragma unroll
-                    for (int f = 0; f < 3; f++) D[f] = Mf[f][0] * d0 + Mf[f][1] * d1 + Mf[f][2] * d2;
+                    D[0] = Mf[0][0] * d0 + Mf[0][1] * d1 + Mf[0][2] * d2;
+                    D[1] = Mf[1][0] * d0 + Mf[1][1] * d1 + Mf[1][2] * d2;
+                    D[2] = -(D[0] + D[1]);
                 } else {
                     real gx = (wx[0] * d0 + wx[1] * d1) + wx[2] * d2;
                     real gy = (wy[0] * d0 + wy[1] * d1) + wy[2] * d2;
@@ -621,7 +624,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         if constexpr (ETA) {
             float2 nv = g32_normal(geo, gid, f);
             nx = nv.x; ny = nv.y;
-            len = geo[(size_t)gid * G32 + 16 + f];
+            len = g32_len(geo, gid, f);
             face_flux_dev(g, half_g, hthr, WfL, HufL, HvfL, zL, WL,
                           WfR, HufR, HvfR, zR, WR, nx, ny, wall, Phi, PL, PR, am);
         } else {
@@ -646,7 +649,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         const int gid = c0 + l;
         real aH = real(0), aHu = real(0), aHv = real(0), am = real(0);
         real x[3];
-        const real area = ETA ? geo[(size_t)gid * G32 + 19] : geo[GEO_AREA * nc + gid];
+        const real area = ETA ? geo[(size_t)gid * G32 + G32_AREA] : geo[GEO_AREA * nc + gid];
 #pragma unroll
         for (int f = 0; f < 3; f++) {
             real t0, t1, t2;
@@ -888,12 +891,25 @@ void *stage_kernel_ptr(int stage, int threads)
     return stage == 1 ? (void *)stage_kernel<real, 1, 512> : (void *)stage_kernel<real, 2, 512>;
 }
 
+// The dynamic shared memory limit is an attribute of the kernel function, shared
+// by every context in the process: it is only ever raised, so that a context
+// configured later with a smaller block never lowers it below what another
+// context's launches need.
+inline cudaError_t raise_smem_limit(const void *kern, size_t smem)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 template <typename real>
 int stage_config(const DevPtrs &d, int stage, LaunchCfg &cfg)
 {
     cfg.smem = stage_smem_bytes<real>(d.block, d.max_halo, d.max_ring1);
     const void *kern = stage_kernel_ptr<real>(stage, d.threads);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+    cudaError_t e = raise_smem_limit(kern, cfg.smem);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, d.threads, cfg.smem);
@@ -934,7 +950,7 @@ int batch_config(int block, int max_halo, int max_ring1, int &grid, size_t &smem
     int best = 1 << 30;
     for (int stage = 1; stage <= 2; stage++) {
         auto kern = stage == 1 ? batch_stage_kernel<real, 1> : batch_stage_kernel<real, 2>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = raise_smem_limit((const void *)kern, smem);
         if (e != cudaSuccess) return (int)e;
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);

@@ -117,7 +117,7 @@ __global__ void diag_partial_kernel(int64_t nc, const real *w, const double *z, 
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nc; k += (int64_t)gridDim.x * blockDim.x) {
         double h = (double)w[k];
         if (EtaForm<real>::value) h = h - z[k];
-        double area = EtaForm<real>::value ? (double)geo[(size_t)k * G32 + 19] : (double)geo[GEO_AREA * nc + k];
+        double area = EtaForm<real>::value ? (double)geo[(size_t)k * G32 + G32_AREA] : (double)geo[GEO_AREA * nc + k];
         mass += area * h;
         mn = fmin(mn, h);
         dry += h <= hthr ? 1.0 : 0.0;

@@ -10,7 +10,7 @@
 namespace vg {
 
 // Per-cell geometry rows, [GEO_ROWS][nc], in the order below (host, and the
-// FP64 device copy; the FP32 device copy is a 20-float record per cell, formed
+// FP64 device copy; the FP32 device copy is a 16-float record per cell, formed
 // from these rows at upload, layout beside the stage kernels).  Face f of a cell joins its local vertices f and f+1; the local order
 // is counter-clockwise from the vertex with the smallest input id.
 enum GeoRow : int {
@@ -89,7 +89,7 @@ struct DevPtrs {
     int64_t nc;
     int32_t block, nblocks, max_halo, max_ring1, n_gauges, ring_cap;
     int32_t threads;        // threads per CTA of the stage kernels (>= block)
-    const void *geo;        // FP64: [GEO_ROWS][nc]; FP32: [nc][20] record
+    const void *geo;        // FP64: [GEO_ROWS][nc]; FP32: [nc][16] record
     const void *z;          // [nc]
     const double *z64;      // [nc] FP64 bed (state import/export and diagnostics)
     const int32_t *nbr;     // [3][nc]

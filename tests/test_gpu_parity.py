@@ -72,6 +72,28 @@ def test_ragged_tiles_fp64(n, block):
         assert rel_l2(g[f], r[f]) <= TOL64, f
 
 
+@pytest.mark.parametrize("precision", [32, 64])
+def test_contexts_with_different_blocks_coexist(thacker, precision):
+    """Two contexts in one process, the second configured with a smaller block
+    (less shared memory per CTA): the first still steps, with the same result
+    as a context on its own."""
+    m, s = thacker
+    big = volna.Solver(precision)
+    big.set_params(h_threshold=1e-5, block_cells=256)
+    big.upload_mesh(m)
+    small = volna.Solver(precision)
+    small.set_params(h_threshold=1e-5, block_cells=32)
+    small.upload_mesh(m)
+    for sv in (big, small):
+        sv.set_state(s.H, s.Hu, s.Hv)
+        sv.step(3)
+    a, b = big.get_state(), small.get_state()
+    big.close()
+    small.close()
+    for i in range(3):
+        np.testing.assert_allclose(a[i], b[i], rtol=0, atol=1e-5 if precision == 32 else 1e-13)
+
+
 def test_coast_basin_fp64_fp32():
     """Synthetic ocean-to-coast basin (N-wave uplift, inundation, H_threshold 1e-3 m)."""
     m = I.coast_mesh(n_theta=40, n_xi=120)
