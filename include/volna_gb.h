@@ -287,7 +287,7 @@ int vg_batch_create(vg_batch **out, int precision, int device, void *cuda_stream
 void vg_batch_destroy(vg_batch *b);
 const char *vg_batch_last_error(vg_batch *b);
 
-/* Parameters shared by all scenarios (vg_params; gauges are not recorded). */
+/* Parameters shared by all scenarios (vg_params, gauge_every included). */
 int vg_batch_set_params(vg_batch *b, const vg_params *p);
 
 /* Add a mesh (arguments as vg_mesh_upload) carrying n_scenarios scenarios;
@@ -316,6 +316,24 @@ int vg_batch_run(vg_batch *b, double t_end, int64_t max_steps, int64_t *steps_ta
    128, 256 cells per thread block) from the current state, restores the state,
    and keeps the fastest; *best_block and *best_ms_per_step report it. */
 int vg_batch_autotune(vg_batch *b, int32_t n_steps, int32_t *best_block, double *best_ms_per_step);
+
+/* Virtual gauges of one mesh, shared by all its scenarios (as vg_set_gauges:
+   xy [n][2] in the mesh's coordinates, each located in its containing cell,
+   ties to the lowest original cell id; a point outside the mesh: VG_EINVAL;
+   n = 0 removes them).  Every scenario of the mesh then records eta = H + z of
+   the gauge cells at its current time now, at vg_batch_set_state, and after
+   every gauge_every of its own steps (a scenario that has reached t_end no
+   longer records), the same records as a context of its own.  Records are
+   kept in device rings and moved to host memory by the library whenever it
+   reads the scenarios' scalars (every vg_batch_step and vg_batch_run call
+   does, often enough that no record is lost). */
+int vg_batch_set_gauges(vg_batch *b, int32_t mesh_id, int32_t n, const double *xy);
+
+/* Records of one scenario: t [cap] and eta [cap][G] (G = the mesh's gauge
+   count), copied up to cap records; *n_rec receives the number held (may
+   exceed cap).  Any of t, eta, n_rec may be NULL. */
+int vg_batch_get_gauges(vg_batch *b, int32_t mesh_id, int32_t scenario, double *t, double *eta, int64_t cap,
+                        int64_t *n_rec);
 
 /* Meshes, scenarios, total cells over all scenarios, kernels launched. */
 int vg_batch_info(vg_batch *b, int32_t *n_meshes, int32_t *n_scenarios, int64_t *cells, int64_t *launches);

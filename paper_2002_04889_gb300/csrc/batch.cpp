@@ -5,7 +5,11 @@
 // device scalar record per scenario (time, dt, CFL minimum) and a device table
 // of the meshes.  One batched step is three launches -- stage 1 and stage 2 over
 // every (mesh, block) work item for all scenarios, and a per-scenario epilogue
-// -- and the step loop is replayed from a CUDA graph two steps at a time.
+// -- and the step loop is replayed from a CUDA graph two steps at a time.  A
+// mesh may carry gauges (the same points for all its scenarios); each scenario
+// then records eta there into a circular device ring after each of its steps
+// (a fourth launch per step), and the host drains the rings whenever it reads
+// the scenario scalars, at least every kBatchRingCap - 1 records.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,6 +24,10 @@
 
 using namespace vg;
 
+namespace {
+constexpr int kBatchRingCap = 64;     // records per scenario between two drains
+}
+
 struct vg_batch {
     int precision = 32;
     int device = 0;
@@ -33,6 +41,13 @@ struct vg_batch {
         int first_entry = 0;
         void *w[2] = {nullptr, nullptr};
         void *R0 = nullptr;
+        int n_gauges = 0;
+        int32_t *gauge_cells = nullptr;    // device [G] internal cell ids
+        double *ring_t = nullptr;          // device [n_scen][kBatchRingCap]
+        double *ring_eta = nullptr;        // device [n_scen][kBatchRingCap][G]
+        std::vector<int32_t> gauge_orig;   // containing cells, original ids
+        std::vector<int64_t> drained;      // per scenario: records already on the host
+        std::vector<std::vector<double>> rec_t, rec_eta;   // per scenario
     };
     std::vector<Mesh> meshes;
     std::vector<char> has_state;           // per scenario
@@ -46,6 +61,7 @@ struct vg_batch {
     bool dirty = true;
     cudaGraphExec_t graph2 = nullptr;
     int64_t launches = 0;
+    bool gauges = false;                   // some mesh has gauges
 };
 
 namespace {
@@ -114,7 +130,11 @@ int rebuild(vg_batch *b)
             DevPtrs d = ctx_dev_ptrs(M.ctx);
             d.R0 = M.R0;
             d.sc = b->sc_all + M.first_entry;
-            d.n_gauges = 0;
+            d.n_gauges = M.n_gauges;
+            d.gauge_cells = M.gauge_cells;
+            d.ring_t = M.ring_t;
+            d.ring_eta = M.ring_eta;
+            d.ring_cap = kBatchRingCap;
             StepParams p = ctx_step_params(M.ctx);
             p.gauge_every = 1;
             if (b->precision == 64)
@@ -136,6 +156,8 @@ int rebuild(vg_batch *b)
                                : batch_config_f32(block, max_halo, max_ring1, b->grid, b->smem);
     if (e) return bcuda(b, (cudaError_t)e, "batched launch configuration");
     if (b->grid > b->n_items) b->grid = b->n_items;
+    b->gauges = false;
+    for (auto &M : b->meshes) b->gauges = b->gauges || M.n_gauges > 0;
     b->dirty = false;
     return VG_OK;
 }
@@ -150,7 +172,7 @@ StepParams batch_params(const vg_batch *b)
     p.dt_max = b->prm.dt_max;
     p.t_end = b->prm.t_end;
     p.order = b->prm.order;
-    p.gauge_every = 1;
+    p.gauge_every = b->prm.gauge_every > 0 ? b->prm.gauge_every : 1;
     return p;
 }
 
@@ -160,11 +182,11 @@ int enqueue_batch_step(vg_batch *b, int parity)
     StepParams p = batch_params(b);
     int e = b->precision == 64
                 ? launch_batch_step_f64(b->table[parity], (int)b->meshes.size(), b->n_items, b->n_entries, b->sc_all,
-                                        block, b->grid, b->smem, p, (void *)b->stream)
+                                        block, b->grid, b->smem, p, b->gauges, (void *)b->stream)
                 : launch_batch_step_f32(b->table[parity], (int)b->meshes.size(), b->n_items, b->n_entries, b->sc_all,
-                                        block, b->grid, b->smem, p, (void *)b->stream);
+                                        block, b->grid, b->smem, p, b->gauges, (void *)b->stream);
     if (e) return bcuda(b, (cudaError_t)e, "batched step launch");
-    b->launches += 3;
+    b->launches += b->gauges ? 4 : 3;
     return VG_OK;
 }
 
@@ -213,7 +235,7 @@ int run_steps(vg_batch *b, int64_t n)
     }
     while (n >= 2) {
         VB_CUDA(b, cudaGraphLaunch(b->graph2, b->stream));
-        b->launches += 6;
+        b->launches += b->gauges ? 8 : 6;
         n -= 2;
     }
     if (n == 1) {
@@ -223,13 +245,86 @@ int run_steps(vg_batch *b, int64_t n)
     return VG_OK;
 }
 
+int drain(vg_batch *b, const std::vector<DevScalars> &s);
+
+// Read every scenario's scalars, then drain the gauge rings.
 int read_all(vg_batch *b, std::vector<DevScalars> &s)
 {
     s.resize(b->n_entries + 1);
     VB_CUDA(b, cudaMemcpyAsync(s.data(), b->sc_all, sizeof(DevScalars) * (b->n_entries + 1), cudaMemcpyDeviceToHost,
                                b->stream));
     VB_CUDA(b, cudaStreamSynchronize(b->stream));
+    return drain(b, s);
+}
+
+// Copy the gauge records written since the last drain to the host (per mesh one
+// copy of each ring, then the new records of every scenario in order).
+int drain(vg_batch *b, const std::vector<DevScalars> &s)
+{
+    std::vector<double> rt, re;
+    for (auto &M : b->meshes) {
+        if (M.n_gauges == 0) continue;
+        bool any = false;
+        for (int k = 0; k < M.n_scen; k++) {
+            int64_t n = s[M.first_entry + k].n_rec - M.drained[k];
+            if (n > kBatchRingCap) return bfail(b, VG_ESTATE, "gauge ring overflow");
+            any = any || n > 0;
+        }
+        if (!any) continue;
+        const size_t G = (size_t)M.n_gauges, cap = kBatchRingCap;
+        rt.resize((size_t)M.n_scen * cap);
+        re.resize((size_t)M.n_scen * cap * G);
+        VB_CUDA(b, cudaMemcpyAsync(rt.data(), M.ring_t, 8 * rt.size(), cudaMemcpyDeviceToHost, b->stream));
+        VB_CUDA(b, cudaMemcpyAsync(re.data(), M.ring_eta, 8 * re.size(), cudaMemcpyDeviceToHost, b->stream));
+        VB_CUDA(b, cudaStreamSynchronize(b->stream));
+        for (int k = 0; k < M.n_scen; k++) {
+            const int64_t n_rec = s[M.first_entry + k].n_rec;
+            for (int64_t r = M.drained[k]; r < n_rec; r++) {
+                const size_t slot = (size_t)k * cap + (size_t)(r % kBatchRingCap);
+                M.rec_t[k].push_back(rt[slot]);
+                M.rec_eta[k].insert(M.rec_eta[k].end(), re.begin() + slot * G, re.begin() + (slot + 1) * G);
+            }
+            M.drained[k] = n_rec;
+        }
+    }
     return VG_OK;
+}
+
+// Record the gauges of scenario k of mesh M from its current state (at set_state
+// and set_gauges), as record index 0 of a cleared ring.
+int record_now(vg_batch *b, vg_batch::Mesh &M, int k)
+{
+    if (M.n_gauges == 0) return VG_OK;
+    const int e = M.first_entry + k;
+    static const long long zero = 0;
+    VB_CUDA(b, cudaMemcpyAsync(&b->sc_all[e].n_rec, &zero, sizeof(zero), cudaMemcpyHostToDevice, b->stream));
+    M.drained[k] = 0;
+    M.rec_t[k].clear();
+    M.rec_eta[k].clear();
+    if (!b->has_state[e]) return VG_OK;
+    DevPtrs d = ctx_dev_ptrs(M.ctx);
+    d.sc = b->sc_all + e;
+    d.n_gauges = M.n_gauges;
+    d.gauge_cells = M.gauge_cells;
+    d.ring_cap = kBatchRingCap;
+    d.ring_t = M.ring_t + (size_t)k * kBatchRingCap;
+    d.ring_eta = M.ring_eta + (size_t)k * kBatchRingCap * M.n_gauges;
+    const int64_t nc = ctx_host_mesh(M.ctx).nc;
+    const void *w = static_cast<unsigned char *>(M.w[b->cur]) + rsize(b) * 3 * (size_t)nc * k;
+    int err = launch_record_gauges(d, w, b->precision, (void *)b->stream);
+    if (err) return bcuda(b, (cudaError_t)err, "gauge record launch");
+    b->launches++;
+    return VG_OK;
+}
+
+void free_gauges(vg_batch::Mesh &M)
+{
+    if (M.gauge_cells) cudaFree(M.gauge_cells);
+    if (M.ring_t) cudaFree(M.ring_t);
+    if (M.ring_eta) cudaFree(M.ring_eta);
+    M.gauge_cells = nullptr;
+    M.ring_t = M.ring_eta = nullptr;
+    M.n_gauges = 0;
 }
 
 int check(vg_batch *b, const std::vector<DevScalars> &s)
@@ -249,6 +344,7 @@ void free_batch(vg_batch *b)
         if (M.w[0]) cudaFree(M.w[0]);
         if (M.w[1]) cudaFree(M.w[1]);
         if (M.R0) cudaFree(M.R0);
+        free_gauges(M);
         vg_destroy(M.ctx);
     }
     b->meshes.clear();
@@ -342,6 +438,9 @@ int vg_batch_add_mesh(vg_batch *b, int64_t nv, const double *xy, int64_t nc, con
     }
     M.n_scen = n_scenarios;
     M.first_entry = b->n_entries;
+    M.drained.assign(n_scenarios, 0);
+    M.rec_t.assign(n_scenarios, {});
+    M.rec_eta.assign(n_scenarios, {});
     // grow the scalar array: [n_entries] scenarios + one batch-wide record
     DevScalars *sc = nullptr;
     int n_new = b->n_entries + n_scenarios;
@@ -400,7 +499,7 @@ int vg_batch_set_state(vg_batch *b, int32_t mesh, int32_t scen, const double *H,
         return bfail(b, VG_EINVAL, "state has a negative or non-finite depth, or non-finite momentum");
     }
     b->has_state[e] = 1;
-    return VG_OK;
+    return record_now(b, M, scen);
 }
 
 int vg_batch_get_state(vg_batch *b, int32_t mesh, int32_t scen, double *H, double *Hu, double *Hv, double *t,
@@ -437,10 +536,18 @@ int vg_batch_step(vg_batch *b, int64_t n_steps)
     DeviceGuard guard(b->device);
     int rc = ready(b);
     if (rc) return rc;
-    if ((rc = run_steps(b, n_steps))) return rc;
+    // with gauges, drain before a ring can fill (at most one record per step)
+    const int64_t every = b->prm.gauge_every > 0 ? b->prm.gauge_every : 1;
+    const int64_t chunk_max = b->gauges ? (int64_t)(kBatchRingCap - 1) * every : std::max<int64_t>(n_steps, 1);
     std::vector<DevScalars> s;
-    if ((rc = read_all(b, s))) return rc;
-    return check(b, s);
+    do {
+        const int64_t chunk = std::min(n_steps, chunk_max);
+        if ((rc = run_steps(b, chunk))) return rc;
+        n_steps -= chunk;
+        if ((rc = read_all(b, s))) return rc;
+        if ((rc = check(b, s))) return rc;
+    } while (n_steps > 0);
+    return VG_OK;
 }
 
 int vg_batch_run(vg_batch *b, double t_end, int64_t max_steps, int64_t *steps_taken)
@@ -481,6 +588,10 @@ int vg_batch_autotune(vg_batch *b, int32_t n_steps, int32_t *best_block, double 
     DeviceGuard guard(b->device);
     int rc = ready(b);
     if (rc) return rc;
+    {
+        std::vector<DevScalars> s;      // drain, so that the trial steps overwrite no unread record
+        if ((rc = read_all(b, s))) return rc;
+    }
     // Save every scenario's state and scalars; each candidate block size runs
     // n_steps timed steps from the same state, which is restored afterwards.
     std::vector<void *> saved(b->meshes.size(), nullptr);
@@ -531,6 +642,65 @@ int vg_batch_autotune(vg_batch *b, int32_t n_steps, int32_t *best_block, double 
     if ((rc = vg_batch_set_params(b, &p))) return rc;
     if (best_block) *best_block = best;
     if (best_ms) *best_ms = best_t / n_steps;
+    return VG_OK;
+}
+
+int vg_batch_set_gauges(vg_batch *b, int32_t mesh_id, int32_t n, const double *xy)
+{
+    if (!b || n < 0 || (n > 0 && !xy)) return VG_EINVAL;
+    if (mesh_id < 0 || mesh_id >= (int)b->meshes.size()) return bfail(b, VG_EINVAL, "no such mesh");
+    DeviceGuard guard(b->device);
+    vg_batch::Mesh &M = b->meshes[mesh_id];
+    const HostMesh &hm = ctx_host_mesh(M.ctx);
+    std::vector<int32_t> cells(n);
+    locate_points(hm, n, xy, cells.data());
+    for (int32_t k = 0; k < n; k++)
+        if (cells[k] < 0) return bfail(b, VG_EINVAL, "gauge " + std::to_string(k) + " lies outside the mesh");
+    VB_CUDA(b, cudaStreamSynchronize(b->stream));
+    free_gauges(M);
+    M.gauge_orig = cells;
+    b->dirty = true;
+    if (b->graph2) { cudaGraphExecDestroy(b->graph2); b->graph2 = nullptr; }
+    for (int k = 0; k < M.n_scen; k++) {
+        M.drained[k] = 0;
+        M.rec_t[k].clear();
+        M.rec_eta[k].clear();
+    }
+    if (n == 0) return VG_OK;
+    std::vector<int32_t> internal(n);
+    for (int32_t k = 0; k < n; k++) internal[k] = hm.new_of_old[cells[k]];
+    const size_t cap = kBatchRingCap;
+    if (cudaMalloc((void **)&M.gauge_cells, 4 * (size_t)n) != cudaSuccess ||
+        cudaMalloc((void **)&M.ring_t, 8 * (size_t)M.n_scen * cap) != cudaSuccess ||
+        cudaMalloc((void **)&M.ring_eta, 8 * (size_t)M.n_scen * cap * n) != cudaSuccess) {
+        cudaGetLastError();
+        free_gauges(M);
+        return bfail(b, VG_ENOMEM, "gauge ring allocation failed");
+    }
+    M.n_gauges = n;
+    VB_CUDA(b, cudaMemcpy(M.gauge_cells, internal.data(), 4 * (size_t)n, cudaMemcpyHostToDevice));
+    for (int k = 0; k < M.n_scen; k++) {
+        int rc = record_now(b, M, k);
+        if (rc) return rc;
+    }
+    return VG_OK;
+}
+
+int vg_batch_get_gauges(vg_batch *b, int32_t mesh_id, int32_t scenario, double *t, double *eta, int64_t cap,
+                        int64_t *n_rec)
+{
+    if (!b || cap < 0) return VG_EINVAL;
+    int e, rc;
+    if ((rc = entry_of(b, mesh_id, scenario, e))) return rc;
+    DeviceGuard guard(b->device);
+    std::vector<DevScalars> s;
+    if ((rc = read_all(b, s))) return rc;
+    const vg_batch::Mesh &M = b->meshes[mesh_id];
+    const int64_t n = (int64_t)M.rec_t[scenario].size();
+    if (n_rec) *n_rec = n;
+    const int64_t k = std::min(n, cap);
+    if (t && k) std::memcpy(t, M.rec_t[scenario].data(), 8 * k);
+    if (eta && k) std::memcpy(eta, M.rec_eta[scenario].data(), 8 * k * M.n_gauges);
     return VG_OK;
 }
 

@@ -23,8 +23,8 @@ int batch_config_f32(int block, int max_halo, int max_ring1, int &grid, size_t &
     return batch_config<float>(block, max_halo, max_ring1, grid, smem);
 }
 int launch_batch_step_f32(const void *table, int n_mesh, int n_items, int n_entries, DevScalars *sc_all, int block,
-                          int grid, size_t smem, const StepParams &p, void *stream)
+                          int grid, size_t smem, const StepParams &p, bool gauges, void *stream)
 {
-    return launch_batch_step<float>(table, n_mesh, n_items, n_entries, sc_all, block, grid, smem, p, stream);
+    return launch_batch_step<float>(table, n_mesh, n_items, n_entries, sc_all, block, grid, smem, p, gauges, stream);
 }
 }  // namespace vg

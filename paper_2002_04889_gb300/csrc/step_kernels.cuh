@@ -761,7 +761,11 @@ struct BatchMesh {
     int n_scen;            // scenarios of this mesh
     int first_item;        // first work item (block) of this mesh in the launch
     int first_entry;       // index of its first scenario among all scenarios
-    int pad;
+    int n_gauges;          // gauges of this mesh (0: none)
+    const int32_t *gauge_cells;  // [n_gauges] internal cell ids
+    double *ring_t;        // [n_scen][ring_cap] record times
+    double *ring_eta;      // [n_scen][ring_cap][n_gauges] eta at the gauges
+    int ring_cap, pad;
 };
 
 // Order-preserving integer image of a non-negative value, as 32 bits (FP32) or
@@ -774,7 +778,7 @@ __device__ __forceinline__ unsigned long long warp_min_bits(real v)
 }
 
 template <typename real, int STAGE>
-__global__ void __launch_bounds__(256) batch_stage_kernel(const BatchMesh<real> *meshes, int n_mesh,
+__global__ void __launch_bounds__(256, (StageMinCtas<real, 256>::value)) batch_stage_kernel(const BatchMesh<real> *meshes, int n_mesh,
                                                           int n_items, int n_entries, DevScalars *sc_all)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -825,6 +829,40 @@ __global__ void __launch_bounds__(256) batch_stage_kernel(const BatchMesh<real> 
         for (int w = 0; w < nwarps; w++) neg += red_neg[w];
         if (neg) atomicAdd((unsigned long long *)&sc_all[n_entries].neg_count, (unsigned long long)neg);
         if (bad) atomicOr(&sc_all[n_entries].flags, FLAG_NONFINITE_STATE);
+    }
+}
+
+// Gauge records of one batched step (after the epilogue): a scenario that
+// advanced records eta at its mesh's gauges every gauge_every of its steps, in
+// the circular ring at index n_rec mod ring_cap (the host drains often enough
+// that no unread record is overwritten).  One CTA per mesh.
+template <typename real>
+__global__ void batch_gauge_kernel(const BatchMesh<real> *meshes, DevScalars *sc_all, int gauge_every)
+{
+    __shared__ int slot[kBatchMaxEntries];
+    const BatchMesh<real> &bm = meshes[blockIdx.x];
+    const int G = bm.n_gauges;
+    if (G == 0) return;
+    for (int s = threadIdx.x; s < bm.n_scen; s += blockDim.x) {
+        const DevScalars *sc = sc_all + bm.first_entry + s;
+        slot[s] = (sc->dt > 0.0 && sc->steps % gauge_every == 0) ? (int)(sc->n_rec % bm.ring_cap) : -1;
+    }
+    __syncthreads();
+    const real *z = bm.a.z;
+    for (int k = threadIdx.x; k < bm.n_scen * G; k += blockDim.x) {
+        const int s = k / G, g = k - s * G;
+        if (slot[s] < 0) continue;
+        const real *w = bm.a.wout + s * bm.stride;
+        const int32_t c = bm.gauge_cells[g];
+        bm.ring_eta[((size_t)s * bm.ring_cap + slot[s]) * G + g] =
+            EtaForm<real>::value ? (double)w[c] : (double)(w[c] + z[c]);
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < bm.n_scen; s += blockDim.x) {
+        if (slot[s] < 0) continue;
+        DevScalars *sc = sc_all + bm.first_entry + s;
+        bm.ring_t[(size_t)s * bm.ring_cap + slot[s]] = sc->t;
+        sc->n_rec += 1;
     }
 }
 
@@ -967,13 +1005,14 @@ int batch_config(int block, int max_halo, int max_ring1, int &grid, size_t &smem
 
 template <typename real>
 int launch_batch_step(const void *table, int n_mesh, int n_items, int n_entries, DevScalars *sc_all, int block,
-                      int grid, size_t smem, const StepParams &p, void *stream)
+                      int grid, size_t smem, const StepParams &p, bool gauges, void *stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const BatchMesh<real> *t = static_cast<const BatchMesh<real> *>(table);
     batch_stage_kernel<real, 1><<<grid, block, smem, s>>>(t, n_mesh, n_items, n_entries, sc_all);
     batch_stage_kernel<real, 2><<<grid, block, smem, s>>>(t, n_mesh, n_items, n_entries, sc_all);
     batch_post_kernel<real><<<1, 256, 0, s>>>(n_entries, sc_all, p.cfl, p.dt_fixed, p.dt_max, p.t_end);
+    if (gauges) batch_gauge_kernel<real><<<n_mesh, 256, 0, s>>>(t, sc_all, p.gauge_every);
     return (int)cudaGetLastError();
 }
 
@@ -987,6 +1026,11 @@ void fill_batch_mesh(void *dst, const DevPtrs &d, const StepParams &p, const voi
     bm->n_scen = n_scen;
     bm->first_item = first_item;
     bm->first_entry = first_entry;
+    bm->n_gauges = d.n_gauges;
+    bm->gauge_cells = d.gauge_cells;
+    bm->ring_t = d.ring_t;
+    bm->ring_eta = d.ring_eta;
+    bm->ring_cap = d.ring_cap;
     bm->pad = 0;
 }
 

@@ -135,9 +135,9 @@ void fill_batch_mesh_f64(void *dst, const DevPtrs &d, const StepParams &p, const
 int batch_config_f32(int block, int max_halo, int max_ring1, int &grid, size_t &smem);
 int batch_config_f64(int block, int max_halo, int max_ring1, int &grid, size_t &smem);
 int launch_batch_step_f32(const void *table, int n_mesh, int n_items, int n_entries, DevScalars *sc_all, int block,
-                          int grid, size_t smem, const StepParams &p, void *stream);
+                          int grid, size_t smem, const StepParams &p, bool gauges, void *stream);
 int launch_batch_step_f64(const void *table, int n_mesh, int n_items, int n_entries, DevScalars *sc_all, int block,
-                          int grid, size_t smem, const StepParams &p, void *stream);
+                          int grid, size_t smem, const StepParams &p, bool gauges, void *stream);
 
 // Discrete adjoint (adjoint_f64.cu, FP64 contexts).
 // FV: the face values at w, precomputed by the forward stage kernel (fv_out)

@@ -97,6 +97,8 @@ _SIGNATURES = {
     "vg_batch_run": ([_V, C.c_double, C.c_int64, _I64], C.c_int),
     "vg_batch_autotune": ([_V, C.c_int32, C.POINTER(C.c_int32), _D], C.c_int),
     "vg_batch_info": ([_V, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _I64, _I64], C.c_int),
+    "vg_batch_set_gauges": ([_V, C.c_int32, C.c_int32, _D], C.c_int),
+    "vg_batch_get_gauges": ([_V, C.c_int32, C.c_int32, _D, _D, C.c_int64, _I64], C.c_int),
 }
 
 VG_NOALLOC_MAX_CELLS = 262144
@@ -454,6 +456,7 @@ class Batch:
         self.h = h
         self.precision = precision
         self.nc = []
+        self.n_gauges = {}
 
     def close(self) -> None:
         if getattr(self, "h", None):
@@ -517,6 +520,23 @@ class Batch:
         ms = C.c_double()
         _bcheck(self.h, load().vg_batch_autotune(self.h, int(n_steps), C.byref(blk), C.byref(ms)))
         return blk.value, ms.value
+
+    def set_gauges(self, mesh_id: int, xy) -> None:
+        xy = _f64(xy).reshape(-1, 2)
+        _bcheck(self.h, load().vg_batch_set_gauges(self.h, int(mesh_id), xy.shape[0],
+                                                   _dp(xy) if xy.shape[0] else None))
+        self.n_gauges[mesh_id] = xy.shape[0]
+
+    def gauges(self, mesh_id: int, scen: int):
+        """Gauge records (t [n], eta [n, G]) of one scenario."""
+        n = C.c_int64()
+        _bcheck(self.h, load().vg_batch_get_gauges(self.h, int(mesh_id), int(scen), None, None, 0, C.byref(n)))
+        G = self.n_gauges.get(mesh_id, 0)
+        t, eta = np.empty(n.value), np.empty((n.value, G))
+        if n.value:
+            _bcheck(self.h, load().vg_batch_get_gauges(self.h, int(mesh_id), int(scen), _dp(t), _dp(eta),
+                                                       n.value, C.byref(n)))
+        return t, eta
 
     def info(self) -> dict:
         nm, ns = C.c_int32(), C.c_int32()

@@ -119,3 +119,43 @@ def test_batch_autotune_keeps_results():
                 ref = _single(m, s, 32, n_steps=10)
                 for a, r in zip((H, Hu, Hv), ref[:3]):
                     assert rel_l2(a, r) <= 1e-5
+
+
+@pytest.mark.parametrize("precision,every", [(32, 1), (64, 3)])
+def test_batch_gauges_equal_single_contexts(precision, every):
+    """Gauge records of every scenario (t and eta, at set_state and after every
+    `every` steps, 150 steps: more records than one device ring holds) equal
+    those of a context of its own, bit for bit; a scenario that reached t_end
+    records nothing more."""
+    meshes = _meshes()[:2]
+    scen = [_scenarios(m, k, 2) for k, m in enumerate(meshes)]
+    pts = [I.coast_gauges(5) for _ in meshes]
+    with volna.Batch(precision) as b:
+        b.set_params(h_threshold=1e-3, cfl=0.9, gauge_every=every)
+        ids = [b.add_mesh(m, 2) for m in meshes]
+        b.set_gauges(ids[0], pts[0])
+        for mid, ss in zip(ids, scen):
+            for j, s in enumerate(ss):
+                b.set_state(mid, j, s.H, s.Hu, s.Hv, 0.0)
+        b.set_gauges(ids[1], pts[1])            # after the state: records from now on
+        b.step(150)
+        for mid, m, ss, p in zip(ids, meshes, scen, pts):
+            for j, s in enumerate(ss):
+                t, eta = b.gauges(mid, j)
+                with volna.Solver(precision) as sv:
+                    sv.set_params(h_threshold=1e-3, cfl=0.9, gauge_every=every)
+                    sv.upload_mesh(m)
+                    sv.set_gauges(p)
+                    sv.set_state(s.H, s.Hu, s.Hv, 0.0)
+                    sv.step(150)
+                    t_ref, eta_ref = sv.gauges()
+                assert len(t) == 1 + 150 // every
+                np.testing.assert_array_equal(t, t_ref)
+                np.testing.assert_array_equal(eta, eta_ref)
+        # with t_end set, a scenario that reached it takes no step and records nothing
+        t_now = b.get_state(ids[0], 0)[3]
+        b.set_params(h_threshold=1e-3, cfl=0.9, gauge_every=every, t_end=t_now + 2.0)
+        b.step(300)
+        t, _ = b.gauges(ids[0], 0)
+        assert t[-1] <= t_now + 2.0 + 1e-9
+        assert np.all(np.diff(t) > 0)
