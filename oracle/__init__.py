@@ -56,6 +56,10 @@ def _load():
     lib.vo_run.argtypes = [C.c_void_p, C.POINTER(Params), _D, _D, _D, _D, C.c_int64, _D, _I64,
                            C.c_int32, _I32, _D]
     lib.vo_run.restype = C.c_int64
+    lib.vo_run_bed.argtypes = [C.c_void_p, C.POINTER(Params), _D, _D, _D, _D, C.c_int64, _D, _I64,
+                               C.c_int32, _I32, _D, _D, _D, _D, C.c_double]
+    lib.vo_run_bed.restype = C.c_int64
+    lib.vo_bed_at.argtypes = [C.c_void_p, _D, _D, _D, C.c_double, C.c_double]
     lib.vo_locate.argtypes = [C.c_void_p, _D, C.c_int32, _D, _I32]
     lib.vo_mesh_get.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
     lib.vo_mesh_get.restype = C.c_int
@@ -185,25 +189,37 @@ class OracleMesh:
         _load().vo_locate(self._h, _dp(self.xy), pts.shape[0], _dp(pts), out.ctypes.data_as(_I32))
         return out
 
-    def run(self, prm, state, n_steps, gauge_cells=None):
+    def run(self, prm, state, n_steps, gauge_cells=None, bed_motion=None):
         """n SSP-RK(2,2) steps (Sec. 2.3) from state (H, Hu, Hv, t), on copies.
+        bed_motion = (depth0_v, uplift_v, onset_v, rise): the moving bed of
+        vo_bed_at (time-dependent depth, Sec. 2.1); the mesh keeps the bed of
+        the final time afterwards.
         Returns dict(H, Hu, Hv, t, dts, neg_count, gauges[n_steps, G])."""
         H, Hu, Hv = _f64(state[0]).copy(), _f64(state[1]).copy(), _f64(state[2]).copy()
         t = C.c_double(float(state[3]) if len(state) > 3 else 0.0)
         dts = np.zeros(max(int(n_steps), 1))
         neg = C.c_int64(0)
+        gc = ge = None
         if gauge_cells is not None and len(gauge_cells):
             gc = np.ascontiguousarray(gauge_cells, dtype=np.int32)
             ge = np.zeros((max(int(n_steps), 1), gc.shape[0]))
+        g_args = (gc.shape[0], gc.ctypes.data_as(_I32), _dp(ge)) if gc is not None else (0, None, None)
+        if bed_motion is None:
             _load().vo_run(self._h, C.byref(prm), _dp(H), _dp(Hu), _dp(Hv), C.byref(t),
-                           int(n_steps), _dp(dts), C.byref(neg), gc.shape[0],
-                           gc.ctypes.data_as(_I32), _dp(ge))
+                           int(n_steps), _dp(dts), C.byref(neg), *g_args)
         else:
-            ge = None
-            _load().vo_run(self._h, C.byref(prm), _dp(H), _dp(Hu), _dp(Hv), C.byref(t),
-                           int(n_steps), _dp(dts), C.byref(neg), 0, None, None)
+            d0, up, on = (_f64(a) for a in bed_motion[:3])
+            _load().vo_run_bed(self._h, C.byref(prm), _dp(H), _dp(Hu), _dp(Hv), C.byref(t),
+                               int(n_steps), _dp(dts), C.byref(neg), *g_args,
+                               _dp(d0), _dp(up), _dp(on), float(bed_motion[3]))
         return dict(H=H, Hu=Hu, Hv=Hv, t=t.value, dts=dts[:n_steps], neg_count=neg.value,
                     gauges=None if ge is None else ge[:n_steps])
+
+    def bed_at(self, depth0, uplift, onset, rise, t):
+        """Sets the cell beds to the moving bed at time t (vo_bed_at) and returns them."""
+        _load().vo_bed_at(self._h, _dp(_f64(depth0)), _dp(_f64(uplift)), _dp(_f64(onset)),
+                          float(rise), float(t))
+        return self.get("z")
 
     def mass(self, H):
         """Discrete mass sum_K |K| H_K."""

@@ -23,6 +23,8 @@
  *   wall                ghost state with mirrored normal velocity        (Sec. 2.5)
  *   residual            edge fluxes gathered per cell in a fixed local order (Sec. 2.2)
  *   time step           CFL condition (reading of Sec. 2.3), SSP-RK(2,2) (Sec. 2.3)
+ *   moving bed          time-dependent bathymetry h(x, y, t) of Sec. 2.1, read as a
+ *                       kinematic rupture applied after each step        (vo_bed_at)
  */
 #include <math.h>
 #include <stdint.h>
@@ -631,6 +633,59 @@ int64_t vo_run(vo_mesh *m, const vo_params *p, vo_real *H, vo_real *Hu, vo_real 
     for (int64_t s = 0; s < n_steps; s++) {
         double dt;
         vo_step(m, p, H, Hu, Hv, t, &dt, neg_count);
+        if (dts) dts[s] = dt;
+        for (int32_t g = 0; g < n_gauges && gauge_eta; g++) {
+            int32_t c = gauge_cells[g];
+            gauge_eta[s * (int64_t)n_gauges + g] = H[c] + m->z[c];
+        }
+    }
+    return n_steps;
+}
+
+/*
+ * Moving bed.  Sec. 2.1 writes the depth as time dependent, h(x, y, t), with
+ * H = h + eta conserved by the mass equation.  Reading (the paper gives no
+ * source model): a kinematic rupture in which vertex v rises by uplift_v,
+ * linearly over `rise` seconds from its onset time,
+ *     depth_v(t) = depth0_v - uplift_v R((t - onset_v) / rise),
+ *     R(s) = min(1, max(0, s))           (rise = 0: R = 1 once t >= onset_v),
+ * and the cell bed is z_K(t) = -(mean of its vertices' depths) as at set-up.
+ * The bed moves between steps: after the step that ends at t^{n+1} the beds
+ * are set to z(t^{n+1}) with H unchanged, so the free surface eta = H + z
+ * follows the bed and no mass is created.
+ */
+static double ramp(double t, double onset, double rise)
+{
+    if (rise > 0.0) return fmin(1.0, fmax(0.0, (t - onset) / rise));
+    return t >= onset ? 1.0 : 0.0;
+}
+
+void vo_bed_at(vo_mesh *m, const double *depth0, const double *uplift, const double *onset, double rise,
+               double t)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t K = 0; K < m->nc; K++) {
+        double d[3];
+        for (int k = 0; k < 3; k++) {
+            int32_t v = m->vtx[3 * K + k];
+            d[k] = depth0[v] - uplift[v] * ramp(t, onset[v], rise);
+        }
+        m->z[K] = -((d[0] + d[1]) + d[2]) / 3.0;
+    }
+}
+
+/* vo_run with a moving bed: the beds are first set to z(t) at the start time,
+   then after every step to z at the step's end time (before the gauges). */
+int64_t vo_run_bed(vo_mesh *m, const vo_params *p, vo_real *H, vo_real *Hu, vo_real *Hv,
+                   double *t, int64_t n_steps, double *dts, int64_t *neg_count,
+                   int32_t n_gauges, const int32_t *gauge_cells, vo_real *gauge_eta,
+                   const double *depth0, const double *uplift, const double *onset, double rise)
+{
+    vo_bed_at(m, depth0, uplift, onset, rise, *t);
+    for (int64_t s = 0; s < n_steps; s++) {
+        double dt;
+        vo_step(m, p, H, Hu, Hv, t, &dt, neg_count);
+        vo_bed_at(m, depth0, uplift, onset, rise, *t);
         if (dts) dts[s] = dt;
         for (int32_t g = 0; g < n_gauges && gauge_eta; g++) {
             int32_t c = gauge_cells[g];

@@ -245,6 +245,15 @@ def dam_break_state(mesh: Mesh, h_left: float) -> State:
     return State(H, zero.copy(), zero.copy(), 0.0)
 
 
+def radial_rupture(xy: np.ndarray, amplitude: float, x0: float, y0: float, width: float,
+                   v_rupture: float, start: float = 0.0):
+    """A moving-bed source at the vertices: Gaussian uplift amplitude exp(-r^2 /
+    width^2) around (x0, y0) whose onset spreads outward from the centre at
+    v_rupture (onset = start + r / v_rupture).  Returns (uplift_v, onset_v)."""
+    r = np.hypot(xy[:, 0] - x0, xy[:, 1] - y0)
+    return amplitude * np.exp(-(r / width) ** 2), start + r / v_rupture
+
+
 # ----------------------------------------------------------------------------
 # Synthetic ocean-to-coast basin (stand-in for the paper's Sec. 5 real case)
 # ----------------------------------------------------------------------------
@@ -337,6 +346,18 @@ def nwave_uplift(p: np.ndarray, amplitude: float = 3.0, center=(300_000.0 * math
     q = (-math.sin(a) * dx + math.cos(a) * dy) / semi_axes[1]
     rho2 = s * s + q * q
     return amplitude * 2.0 * math.sqrt(math.e) * s * np.exp(-2.0 * rho2)
+
+
+def coast_rupture(mesh: Mesh, amplitude: float = 3.0, angle_deg: float = 30.0,
+                  v_rupture: float = 2_000.0):
+    """Kinematic version of the N-wave source at the mesh vertices: the same
+    uplift, released along the long axis from its far end at v_rupture (onset =
+    along-axis distance from the end / v_rupture).  Returns (uplift_v, onset_v)."""
+    up = nwave_uplift(mesh.xy, amplitude=amplitude, angle_deg=angle_deg)
+    a = math.radians(angle_deg)
+    c = (300_000.0 * math.cos(0.5), 300_000.0 * math.sin(0.5))
+    s = math.cos(a) * (mesh.xy[:, 0] - c[0]) + math.sin(a) * (mesh.xy[:, 1] - c[1])
+    return up, np.maximum(0.0, s + 75_000.0) / v_rupture
 
 
 def coast_initial_state(mesh: Mesh, amplitude: float = 3.0, angle_deg: float = 30.0) -> State:
