@@ -272,6 +272,23 @@ int vg_adj_forward(vg_ctx *ctx, int64_t n_steps, double dt, int64_t checkpoint_e
 int vg_adj_backward(vg_ctx *ctx, const double *dJ_deta, double *dJ_dH0, double *dJ_dHu0, double *dJ_dHv0,
                     double *dJ_dz, double *dJ_ddepth);
 
+/* Moving bed: the time-dependent depth h(x, y, t) of Sec. 2.1 (the governing
+ * equations conserve the total depth H = h + eta while the bed moves), read as
+ * a kinematic rupture: vertex v rises by uplift_v [nv] (metres, positive up),
+ * linearly over `rise` seconds from its onset time onset_v [nv]:
+ *     depth_v(t) = depth0_v - uplift_v * min(1, max(0, (t - onset_v) / rise))
+ * (rise = 0: a step at onset), with depth0 the depths of vg_mesh_upload /
+ * vg_set_depth.  The cell beds z_K = -(mean of their vertices' depths) are set
+ * at the end of every step to the bed of the step's end time, keeping H (the
+ * free surface follows the bed; no mass is created), before the gauges record;
+ * vg_set_state (and this call, for the current state) sets the bed of the
+ * state's time.  uplift_v = NULL removes the motion and restores the static
+ * bed (keeping H).  Host arrays, caller-owned, copied; non-finite values or a
+ * negative rise: VG_EINVAL.  One extra launch per step while set.  Not applied
+ * by vg_step_noalloc; the adjoint calls fail with VG_ESTATE while it is set,
+ * and so does vg_set_depth. */
+int vg_set_bed_motion(vg_ctx *ctx, const double *uplift_v, const double *onset_v, double rise);
+
 /* ------------------------------------------------------------------------
  * Batched ensembles (uncertainty quantification): many scenarios -- initial
  * states of the same scheme -- on several meshes of uneven size, advanced

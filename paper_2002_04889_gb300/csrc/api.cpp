@@ -20,8 +20,8 @@ namespace {
 
 constexpr int kRingCap = 2048;       // gauge records held on the device between drains
 constexpr int kDiagBlocks = 1024;
-constexpr int kKernels = 3;
-const char *kKernelNames[kKernels] = {"stage1", "stage2", "post_step"};
+constexpr int kKernels = 4;
+const char *kKernelNames[kKernels] = {"stage1", "stage2", "post_step", "bed_update"};
 
 }  // namespace
 
@@ -52,6 +52,14 @@ struct vg_ctx {
     std::vector<int32_t> gauge_orig;
     std::vector<double> rec_t, rec_eta;
 
+    // vertex depths of the static bed (mesh upload / vg_set_depth) and the
+    // moving bed (vg_set_bed_motion): device copies while it is on
+    std::vector<double> depth_v;
+    bool bed_on = false;
+    int32_t *bed_vtx = nullptr;
+    double *bed_depth0 = nullptr, *bed_uplift = nullptr, *bed_onset = nullptr;
+    double bed_rise = 0.0;
+
     LaunchCfg cfg1{}, cfg2{};
     cudaGraphExec_t graph2 = nullptr;
     bool graph_dirty = true;
@@ -62,8 +70,8 @@ struct vg_ctx {
     int64_t adj_n = 0, adj_every = 0;
     double adj_dt = 0.0;
     bool profile = false;
-    double prof_ms[kKernels] = {0, 0, 0};
-    int64_t prof_n[kKernels] = {0, 0, 0};
+    double prof_ms[kKernels] = {0, 0, 0, 0};
+    int64_t prof_n[kKernels] = {0, 0, 0, 0};
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_kernel;
     size_t ev_used = 0;
@@ -130,6 +138,9 @@ void free_mesh(vg_ctx *c)
     dfree(c->nbr); dfree(c->halo_ptr); dfree(c->halo_n1); dfree(c->halo_ids); dfree(c->ring1_nbr);
     dfree(c->old_of_new); dfree(c->nbrl);
     dfree(c->gauge_cells); dfree(c->ring_t); dfree(c->ring_eta); dfree(c->staging);
+    dfree(c->bed_vtx); dfree(c->bed_depth0); dfree(c->bed_uplift); dfree(c->bed_onset);
+    c->bed_on = false;
+    c->depth_v.clear();
     c->dev_bytes = 0;
     c->has_mesh = c->has_state = false;
     c->n_gauges = 0;
@@ -161,6 +172,11 @@ DevPtrs dev_ptrs(const vg_ctx *c)
     d.geo = c->geo;
     d.z = c->z;
     d.z64 = c->z64;
+    d.bed_vtx = c->bed_vtx;
+    d.bed_depth0 = c->bed_depth0;
+    d.bed_uplift = c->bed_uplift;
+    d.bed_onset = c->bed_onset;
+    d.bed_rise = c->bed_rise;
     d.nbr = c->nbr;
     d.nbrl = c->nbrl;
     d.halo_ptr = c->halo_ptr;
@@ -357,6 +373,9 @@ int ev_collect(vg_ctx *c)
     return VG_OK;
 }
 
+// Kernels one step launches.
+int step_kernels(const vg_ctx *c) { return c->bed_on ? 4 : 3; }
+
 // Queue one step reading w[src] and writing w[1 - src].
 int enqueue_step(vg_ctx *c, int src)
 {
@@ -374,6 +393,13 @@ int enqueue_step(vg_ctx *c, int src)
     e = c->precision == 64 ? launch_stage2_f64(d, p, win, wout, c->cfg2, s) : launch_stage2_f32(d, p, win, wout, c->cfg2, s);
     if (e) return cuda_fail(c, (cudaError_t)e, "stage 2 launch");
     if ((rc = ev_end(c))) return rc;
+    if (c->bed_on) {
+        // the bed of the step's end time, with H kept, before the gauges record
+        if ((rc = ev_begin(c, 3))) return rc;
+        e = launch_bed_update(d, p, wout, c->precision, true, 0.0, s);
+        if (e) return cuda_fail(c, (cudaError_t)e, "bed update launch");
+        if ((rc = ev_end(c))) return rc;
+    }
     if ((rc = ev_begin(c, 2))) return rc;
     e = launch_post_step(d, p, wout, c->precision, s);
     if (e) return cuda_fail(c, (cudaError_t)e, "post-step launch");
@@ -587,6 +613,7 @@ int vg_mesh_upload(vg_ctx *c, int64_t nv, const double *xy, int64_t nc, const in
     if ((rc = fit_blocks(c))) return rc;
     if ((rc = upload_mesh_arrays(c))) { free_mesh(c); return rc; }
     if ((rc = configure_launch(c))) { free_mesh(c); return rc; }
+    c->depth_v.assign(depth_v, depth_v + nv);
     c->has_mesh = true;
     c->has_state = false;
     c->cur = 0;
@@ -649,6 +676,12 @@ static int set_state_impl(vg_ctx *c, const void *H, const void *Hu, const void *
     reset_scalars_host(c, s, t);
     VG_CUDA(c, cudaMemcpyAsync(c->sc, &s, sizeof(s), cudaMemcpyHostToDevice, c->stream));
     c->cur = 0;
+    if (c->bed_on) {
+        // the moving bed at the state's time, before the state is stored over it
+        int e = launch_bed_update(dev_ptrs(c), step_params(c), nullptr, c->precision, false, t, (void *)c->stream);
+        if (e) return cuda_fail(c, (cudaError_t)e, "bed update launch");
+        c->launches++;
+    }
     int e = launch_import_state(dev_ptrs(c), c->old_of_new, H, Hu, Hv, is_double, c->w[0], c->precision,
                                 (void *)c->stream);
     if (e) return cuda_fail(c, (cudaError_t)e, "state import launch");
@@ -784,7 +817,7 @@ int vg_step(vg_ctx *c, int64_t n_steps)
             while (left > 0) {
                 if ((rc = enqueue_step(c, c->cur))) return rc;
                 c->cur = 1 - c->cur;
-                c->launches += kKernels;
+                c->launches += step_kernels(c);
                 left--;
             }
         } else {
@@ -792,18 +825,18 @@ int vg_step(vg_ctx *c, int64_t n_steps)
             if (c->cur == 1 && left > 0) {
                 if ((rc = enqueue_step(c, 1))) return rc;
                 c->cur = 0;
-                c->launches += kKernels;
+                c->launches += step_kernels(c);
                 left--;
             }
             while (left >= 2) {
                 VG_CUDA(c, cudaGraphLaunch(c->graph2, c->stream));
-                c->launches += 2 * kKernels;
+                c->launches += 2 * step_kernels(c);
                 left -= 2;
             }
             if (left == 1) {
                 if ((rc = enqueue_step(c, 0))) return rc;
                 c->cur = 1;
-                c->launches += kKernels;
+                c->launches += step_kernels(c);
             }
         }
         if ((rc = read_scalars(c, s))) return rc;
@@ -913,6 +946,8 @@ int vg_set_depth(vg_ctx *c, const double *depth_v)
 {
     if (!c || !depth_v) return VG_EINVAL;
     if (!c->has_mesh) return fail(c, VG_ESTATE, "no mesh");
+    if (c->bed_on)
+        return fail(c, VG_ESTATE, "a moving bed is set; remove it (vg_set_bed_motion with uplift NULL) first");
     DeviceGuard guard(c->device);
     HostMesh &m = c->hm;
     std::vector<double> zo(m.nc);
@@ -926,6 +961,59 @@ int vg_set_depth(vg_ctx *c, const double *depth_v)
     int rc = upload_real(c, c->z, m.z.data(), m.z.size());
     if (rc) return rc;
     if (c->precision != 64) VG_CUDA(c, cudaMemcpy(c->z64, m.z.data(), 8 * m.nc, cudaMemcpyHostToDevice));
+    c->depth_v.assign(depth_v, depth_v + m.nv);
+    c->graph_dirty = true;
+    return VG_OK;
+}
+
+int vg_set_bed_motion(vg_ctx *c, const double *uplift_v, const double *onset_v, double rise)
+{
+    if (!c) return VG_EINVAL;
+    if (!c->has_mesh) return fail(c, VG_ESTATE, "no mesh");
+    if (uplift_v && (!onset_v || !(rise >= 0.0) || !std::isfinite(rise)))
+        return fail(c, VG_EINVAL, "onset times and a finite rise time >= 0 are required");
+    DeviceGuard guard(c->device);
+    const HostMesh &m = c->hm;
+    const int64_t nv = m.nv, nc = m.nc;
+    if (uplift_v)
+        for (int64_t v = 0; v < nv; v++)
+            if (!std::isfinite(uplift_v[v]) || !std::isfinite(onset_v[v]))
+                return fail(c, VG_EINVAL, "non-finite uplift or onset at vertex " + std::to_string(v));
+    VG_CUDA(c, cudaStreamSynchronize(c->stream));
+    DevScalars sc;
+    int rc = read_scalars(c, sc);
+    if (rc) return rc;
+    if (!c->bed_vtx) {
+        std::vector<int32_t> bv(3 * (size_t)nc);
+        for (int64_t k = 0; k < nc; k++)
+            for (int j = 0; j < 3; j++) bv[j * (size_t)nc + k] = m.vtx[3 * (size_t)m.old_of_new[k] + j];
+        if ((rc = dmalloc(c, (void **)&c->bed_vtx, 4 * bv.size()))) return rc;
+        if ((rc = dmalloc(c, (void **)&c->bed_depth0, 8 * nv))) return rc;
+        if ((rc = dmalloc(c, (void **)&c->bed_uplift, 8 * nv))) return rc;
+        if ((rc = dmalloc(c, (void **)&c->bed_onset, 8 * nv))) return rc;
+        VG_CUDA(c, cudaMemcpy(c->bed_vtx, bv.data(), 4 * bv.size(), cudaMemcpyHostToDevice));
+    }
+    VG_CUDA(c, cudaMemcpy(c->bed_depth0, c->depth_v.data(), 8 * nv, cudaMemcpyHostToDevice));
+    if (uplift_v) {
+        VG_CUDA(c, cudaMemcpy(c->bed_uplift, uplift_v, 8 * nv, cudaMemcpyHostToDevice));
+        VG_CUDA(c, cudaMemcpy(c->bed_onset, onset_v, 8 * nv, cudaMemcpyHostToDevice));
+        c->bed_rise = rise;
+    } else {
+        // back to the static bed: zero uplift evaluated once, then the motion is off
+        VG_CUDA(c, cudaMemset(c->bed_uplift, 0, 8 * nv));
+        VG_CUDA(c, cudaMemset(c->bed_onset, 0, 8 * nv));
+        c->bed_rise = 0.0;
+    }
+    // the bed at the current time, keeping the state's total depth
+    int e = launch_bed_update(dev_ptrs(c), step_params(c), c->has_state ? c->w[c->cur] : nullptr, c->precision,
+                              false, sc.t, (void *)c->stream);
+    if (e) return cuda_fail(c, (cudaError_t)e, "bed update launch");
+    c->launches++;
+    VG_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->bed_on = uplift_v != nullptr;
+    if (!c->bed_on) {
+        dfree(c->bed_vtx); dfree(c->bed_depth0); dfree(c->bed_uplift); dfree(c->bed_onset);
+    }
     c->graph_dirty = true;
     return VG_OK;
 }
@@ -936,6 +1024,7 @@ int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_eve
     if (c->precision != 64) return fail(c, VG_EINVAL, "the adjoint runs in FP64 contexts");
     if (!c->has_mesh || !c->has_state) return fail(c, VG_ESTATE, "mesh and state must be set");
     if (c->n_gauges < 1) return fail(c, VG_ESTATE, "the adjoint differentiates gauge records: set gauges first");
+    if (c->bed_on) return fail(c, VG_ESTATE, "the adjoint does not differentiate a moving bed");
     DeviceGuard guard(c->device);
     free_adjoint(c);
     int64_t C = checkpoint_every ? checkpoint_every : (int64_t)std::ceil(std::sqrt((double)n_steps));
@@ -966,7 +1055,7 @@ int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_eve
         }
         if ((rc = enqueue_step(c, c->cur))) break;
         c->cur = 1 - c->cur;
-        c->launches += kKernels;
+        c->launches += step_kernels(c);
         if ((n + 1) % 1024 == 0) {
             if ((rc = read_scalars(c, s))) break;
             if ((rc = drain_gauges(c, s))) break;

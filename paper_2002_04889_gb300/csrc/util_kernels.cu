@@ -70,6 +70,46 @@ __global__ void record_gauges_kernel(DevPtrs d, const real *w)
     }
 }
 
+// Moving bed (time-dependent depth of Sec. 2.1, read as a kinematic rupture):
+// depth_v(t) = depth0_v - uplift_v R((t - onset_v) / rise), R(s) = min(1, max(0, s))
+// (rise = 0: a step at onset), cell bed z_K = -(mean of its vertices' depths),
+// applied with H unchanged.  The products and sums are rounded one by one
+// (__dmul_rn / __dadd_rn are never contracted), as written.
+__device__ __forceinline__ double bed_ramp(double t, double onset, double rise)
+{
+    if (rise > 0.0) return fmin(1.0, fmax(0.0, __dsub_rn(t, onset) / rise));
+    return t >= onset ? 1.0 : 0.0;
+}
+
+template <typename real>
+__global__ void bed_update_kernel(DevPtrs d, StepParams p, real *w, int at_step_end, double t_set)
+{
+    const double t = at_step_end ? d.sc->t + step_dt<real>(d.sc, p.cfl, p.dt_fixed, p.dt_max, p.t_end) : t_set;
+    real *z = static_cast<real *>(const_cast<void *>(d.z));
+    double *z64 = const_cast<double *>(d.z64);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.nc; k += (int64_t)gridDim.x * blockDim.x) {
+        double dv[3];
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const int32_t v = d.bed_vtx[j * d.nc + k];
+            dv[j] = __dsub_rn(d.bed_depth0[v], __dmul_rn(d.bed_uplift[v], bed_ramp(t, d.bed_onset[v], d.bed_rise)));
+        }
+        const double zn = -(__dadd_rn(__dadd_rn(dv[0], dv[1]), dv[2]) / 3.0);
+        if (EtaForm<real>::value) {
+            // eta form: keep H = eta - z; a dry cell (eta == z) stays exactly dry
+            const real zo = z[k], zr = (real)zn;
+            if (w && zr != zo) {
+                const real e = w[k];
+                w[k] = e - zo <= real(0) ? zr : (e - zo) + zr;
+            }
+            z[k] = zr;
+            z64[k] = zn;
+        } else {
+            z[k] = (real)zn;
+        }
+    }
+}
+
 // State in (original order, H) -> internal order, stored form (H, or eta = H + z
 // formed with the FP64 bed before rounding to FP32, so still water at a common
 // level gets exactly the same eta everywhere).
@@ -161,6 +201,18 @@ int launch_post_step(const DevPtrs &d, const StepParams &p, const void *w, int p
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (precision == 64) post_step_kernel<double><<<1, 128, 0, s>>>(d, p, static_cast<const double *>(w));
     else post_step_kernel<float><<<1, 128, 0, s>>>(d, p, static_cast<const float *>(w));
+    return (int)cudaGetLastError();
+}
+
+int launch_bed_update(const DevPtrs &d, const StepParams &p, void *w, int precision, bool at_step_end,
+                      double t_set, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int blocks = grid_for(d.nc);
+    if (precision == 64)
+        bed_update_kernel<double><<<blocks, 256, 0, s>>>(d, p, static_cast<double *>(w), at_step_end, t_set);
+    else
+        bed_update_kernel<float><<<blocks, 256, 0, s>>>(d, p, static_cast<float *>(w), at_step_end, t_set);
     return (int)cudaGetLastError();
 }
 

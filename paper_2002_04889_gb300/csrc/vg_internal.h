@@ -105,6 +105,11 @@ struct DevPtrs {
     const int32_t *gauge_cells;   // internal ids
     double *ring_t;               // [ring_cap]
     double *ring_eta;             // [ring_cap][n_gauges]
+    // moving bed (vg_set_bed_motion): local-order vertices [3][nc] of each cell
+    // (internal order) and per-vertex initial depth, uplift and onset time
+    const int32_t *bed_vtx;
+    const double *bed_depth0, *bed_uplift, *bed_onset;
+    double bed_rise;
 };
 
 // Launch wrappers (defined in step_f32.cu / step_f64.cu).  w_in, w_out are
@@ -157,6 +162,11 @@ int adjoint_gauge(int n_gauges, const int32_t *cells, const double *weights, int
 // Utility kernels (util_kernels.cu).
 int launch_post_step(const DevPtrs &d, const StepParams &p, const void *w, int precision, void *stream);
 int launch_record_gauges(const DevPtrs &d, const void *w, int precision, void *stream);
+// Moving bed: sets z (and z64) to the bed at time t -- the end time of the step
+// being taken (sc->t + its dt) when at_step_end, else t_set -- keeping the total
+// depth H of the state w (NULL: no state to keep).
+int launch_bed_update(const DevPtrs &d, const StepParams &p, void *w, int precision, bool at_step_end,
+                      double t_set, void *stream);
 int launch_import_state(const DevPtrs &d, const int32_t *old_of_new, const void *H, const void *Hu,
                         const void *Hv, int src_is_double, void *w, int precision, void *stream);
 int launch_export_state(const DevPtrs &d, const int32_t *old_of_new, const void *w, int precision,

@@ -83,6 +83,7 @@ _SIGNATURES = {
     "vg_device_bytes": ([_V, _I64], C.c_int),
     "vg_step_noalloc": ([_V, _V, _V, C.c_double, _D], C.c_int),
     "vg_set_depth": ([_V, _D], C.c_int),
+    "vg_set_bed_motion": ([_V, _D, _D, C.c_double], C.c_int),
     "vg_adj_forward": ([_V, C.c_int64, C.c_double, C.c_int64], C.c_int),
     "vg_adj_backward": ([_V, _D, _D, _D, _D, _D, _D], C.c_int),
     "vg_batch_create": ([C.POINTER(_V), C.c_int, C.c_int, _V], C.c_int),
@@ -424,6 +425,14 @@ class Solver:
 
     def set_depth(self, depth_v) -> None:
         vg_set_depth(self.ctx, depth_v)
+
+    def set_bed_motion(self, uplift_v, onset_v=None, rise: float = 0.0) -> None:
+        """Moving bed (vg_set_bed_motion); uplift_v None removes it."""
+        if uplift_v is None:
+            _check(self.ctx, load().vg_set_bed_motion(self.ctx, None, None, 0.0))
+            return
+        up, on = _f64(uplift_v), _f64(onset_v)
+        _check(self.ctx, load().vg_set_bed_motion(self.ctx, _dp(up), _dp(on), float(rise)))
 
     def adj_forward(self, n_steps: int, dt: float, checkpoint_every: int = 0):
         """Fixed-dt run keeping checkpoints; returns the gauge records (t, eta)."""
