@@ -21,6 +21,8 @@
  *                       the wet/dry treatment named in Sec. 2.1)
  *   numerical flux      HLL with the wave speeds of Sec. 2.2, dry-bed speeds
  *   wall                ghost state with mirrored normal velocity        (Sec. 2.5)
+ *   open boundary       transmissive ghost (the cell's own state); reading, see
+ *                       vo_set_open
  *   residual            edge fluxes gathered per cell in a fixed local order (Sec. 2.2)
  *   time step           CFL condition (reading of Sec. 2.3), SSP-RK(2,2) (Sec. 2.3)
  *   moving bed          time-dependent bathymetry h(x, y, t) of Sec. 2.1, read as a
@@ -61,7 +63,7 @@ typedef struct vo_mesh {
     int64_t nv, nc;
     int64_t n_flipped;   /* clockwise input triangles that were reoriented */
     int32_t *vtx;        /* [nc][3] vertex ids in local order              */
-    int32_t *nbr;        /* [nc][3] neighbour across face f, -1 = wall      */
+    int32_t *nbr;        /* [nc][3] neighbour across face f, -1 wall, -2 open */
     int32_t *nbr_face;   /* [nc][3] the same face seen from the neighbour   */
     vo_real *z;                                 /* [nc] bed                 */
     double *area, *cx, *cy;                     /* [nc]                     */
@@ -350,8 +352,10 @@ void vo_hll_normal(double g, vo_real HL, vo_real unL, vo_real utL,
  * the face velocity is m_f / H_f where H_f > H_threshold, else 0, and the HLL
  * states carry H* times that velocity.  A wall face (wall != 0) uses the ghost
  * state of Sec. 2.5: same depth and bed, normal velocity reversed, tangential
- * velocity kept.  Outputs: Phi (mass, x- and y-momentum flux along n), the two
- * pressure corrections P_s = g (H_{s,f}^2 - H*_s^2) / 2 and the wave speed.
+ * velocity kept.  An open face (wall == 2) uses the transmissive ghost of
+ * vo_set_open: the left face state itself, velocity unchanged.  Outputs: Phi
+ * (mass, x- and y-momentum flux along n), the two pressure corrections
+ * P_s = g (H_{s,f}^2 - H*_s^2) / 2 and the wave speed.
  */
 void vo_face_flux(double g, double hthr,
                   vo_real HfL, vo_real HufL, vo_real HvfL, vo_real zL,
@@ -367,7 +371,7 @@ void vo_face_flux(double g, double hthr,
     if (wall) {
         HsL = fmax(0.0, (HfL + zL) - zL);
         HsR = HsL;
-        unR = -unL;
+        unR = wall == 2 ? unL : -unL;
         utR = utL;
         HfR = HfL;
     } else {
@@ -395,7 +399,8 @@ void vo_face_flux(double g, double hthr,
 /*
  * Face values of cell K.  The reconstructed variables are eta = H + z, Hu, Hv.
  * Each face neighbour contributes its cell value; a wall contributes the ghost
- * of Sec. 2.5 (same eta, momentum mirrored: m - 2 (m.n) n).
+ * of Sec. 2.5 (same eta, momentum mirrored: m - 2 (m.n) n), an open face the
+ * cell's own values (zero gradient across it).
  *
  * The cell reconstructs (Eq. recon: w(x_f) = w_K + alpha_K grad(w)_K . (x_f - x_K))
  * only when it and every face neighbour are wetter than H_threshold and every
@@ -425,6 +430,10 @@ void vo_reconstruct_cell(const vo_mesh *m, const vo_params *p, const vo_real *H,
             qn[f][1] = Hu[j];
             qn[f][2] = Hv[j];
             if (!(H[j] > hthr)) recon = 0;
+        } else if (j == -2) {
+            qn[f][0] = qK[0];
+            qn[f][1] = qK[1];
+            qn[f][2] = qK[2];
         } else {
             vo_real mn = Hu[K] * m->nx[i] + Hv[K] * m->ny[i];
             qn[f][0] = qK[0];
@@ -517,7 +526,7 @@ void vo_residual(vo_mesh *m, const vo_params *p, const vo_real *H, const vo_real
                              m->nx[i], m->ny[i], 0, s, s + 3, s + 4, s + 5);
             } else {
                 vo_face_flux(g, hthr, m->Hf[i], m->Huf[i], m->Hvf[i], m->z[K],
-                             0.0, 0.0, 0.0, 0.0, m->nx[i], m->ny[i], 1, s, s + 3, s + 4, s + 5);
+                             0.0, 0.0, 0.0, 0.0, m->nx[i], m->ny[i], j == -2 ? 2 : 1, s, s + 3, s + 4, s + 5);
             }
         }
     }
@@ -693,6 +702,42 @@ int64_t vo_run_bed(vo_mesh *m, const vo_params *p, vo_real *H, vo_real *Hu, vo_r
         }
     }
     return n_steps;
+}
+
+/*
+ * Open (transmissive) boundary.  The paper's code has walls (Sec. 2.5) and defers
+ * other boundary conditions to Dutykh et al. 2011.  Reading: a boundary face
+ * marked open takes as ghost the cell's own state, unchanged (zero-gradient
+ * extrapolation): the reconstruction sees no difference across it, and the
+ * face flux is the HLL flux between the face state and itself, i.e. the
+ * physical flux of the face state, so waves leave with little reflection.
+ * The ghost's position in the least-squares stencil stays the mirrored one.
+ * Marks the n boundary edges edges[k] = (a, b) (vertex ids, either order) open
+ * and every other boundary face a wall.  VO_EINVAL if an edge is not a
+ * boundary face of the mesh (nothing is changed then).
+ */
+int vo_set_open(vo_mesh *m, int64_t n, const int32_t *edges)
+{
+    int32_t *mark = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1) * 2);
+    if (!mark) return VO_ENOMEM;
+    for (int64_t k = 0; k < n; k++) {
+        int32_t a = edges[2 * k], b = edges[2 * k + 1];
+        int64_t found = -1;
+        for (int64_t i = 0; i < 3 * m->nc && found < 0; i++) {
+            if (m->nbr[i] >= 0) continue;
+            int64_t K = i / 3;
+            int f = (int)(i % 3);
+            int32_t p = m->vtx[3 * K + f], q = m->vtx[3 * K + (f + 1) % 3];
+            if ((p == a && q == b) || (p == b && q == a)) found = i;
+        }
+        if (found < 0) { free(mark); return VO_EINVAL; }
+        mark[k] = (int32_t)found;
+    }
+    for (int64_t i = 0; i < 3 * m->nc; i++)
+        if (m->nbr[i] < 0) m->nbr[i] = -1;
+    for (int64_t k = 0; k < n; k++) m->nbr[mark[k]] = -2;
+    free(mark);
+    return VO_OK;
 }
 
 /* The cell containing each point (boundary included; among several, the lowest

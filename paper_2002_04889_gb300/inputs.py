@@ -245,6 +245,20 @@ def dam_break_state(mesh: Mesh, h_left: float) -> State:
     return State(H, zero.copy(), zero.copy(), 0.0)
 
 
+def boundary_edges(mesh: Mesh, where=None) -> np.ndarray:
+    """Boundary edges (in one triangle only) as vertex pairs [n, 2], optionally
+    only those whose midpoint m satisfies where(m) (m: [n, 2] array -> bool)."""
+    t = mesh.tri.astype(np.int64)
+    e = np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]])
+    key = np.sort(e, axis=1)
+    uniq, inv, cnt = np.unique(key, axis=0, return_inverse=True, return_counts=True)
+    b = uniq[cnt == 1]
+    if where is not None and len(b):
+        mid = 0.5 * (mesh.xy[b[:, 0]] + mesh.xy[b[:, 1]])
+        b = b[np.asarray(where(mid), dtype=bool)]
+    return b.astype(np.int32)
+
+
 def radial_rupture(xy: np.ndarray, amplitude: float, x0: float, y0: float, width: float,
                    v_rupture: float, start: float = 0.0):
     """A moving-bed source at the vertices: Gaussian uplift amplitude exp(-r^2 /
