@@ -272,6 +272,18 @@ int vg_adj_forward(vg_ctx *ctx, int64_t n_steps, double dt, int64_t checkpoint_e
 int vg_adj_backward(vg_ctx *ctx, const double *dJ_deta, double *dJ_dH0, double *dJ_dHu0, double *dJ_dHv0,
                     double *dJ_dz, double *dJ_ddepth);
 
+/* Open (transmissive) boundary.  The paper's solver has walls (Sec. 2.5: a
+ * ghost with mirrored normal velocity) and leaves other boundary conditions to
+ * Dutykh et al. 2011.  Marks the n boundary edges edges[k] = (a, b) (original
+ * vertex ids, either order; [n][2] int32, host, copied) open and every other
+ * boundary face a wall: an open face takes as ghost the cell's own state, so
+ * the reconstruction sees no jump across it and its flux is the physical flux
+ * of the face state (zero-gradient outflow; waves leave with little
+ * reflection).  n = 0 makes every boundary face a wall again.  An edge that is
+ * not a boundary edge: VG_EINVAL, nothing changed.  The adjoint calls fail
+ * with VG_ESTATE while a face is open. */
+int vg_set_open_boundary(vg_ctx *ctx, int64_t n, const int32_t *edges);
+
 /* Moving bed: the time-dependent depth h(x, y, t) of Sec. 2.1 (the governing
  * equations conserve the total depth H = h + eta while the bed moves), read as
  * a kinematic rupture: vertex v rises by uplift_v [nv] (metres, positive up),
@@ -345,6 +357,10 @@ int vg_batch_autotune(vg_batch *b, int32_t n_steps, int32_t *best_block, double 
    reads the scenarios' scalars (every vg_batch_step and vg_batch_run call
    does, often enough that no record is lost). */
 int vg_batch_set_gauges(vg_batch *b, int32_t mesh_id, int32_t n, const double *xy);
+
+/* Open boundary edges of one mesh, shared by all its scenarios (as
+   vg_set_open_boundary). */
+int vg_batch_set_open_boundary(vg_batch *b, int32_t mesh_id, int64_t n, const int32_t *edges);
 
 /* Records of one scenario: t [cap] and eta [cap][G] (G = the mesh's gauge
    count), copied up to cap records; *n_rec receives the number held (may

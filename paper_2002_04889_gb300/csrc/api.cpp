@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/volna_gb.h"
@@ -56,6 +57,7 @@ struct vg_ctx {
     // moving bed (vg_set_bed_motion): device copies while it is on
     std::vector<double> depth_v;
     bool bed_on = false;
+    int64_t n_open = 0;                 // open boundary faces (vg_set_open_boundary)
     int32_t *bed_vtx = nullptr;
     double *bed_depth0 = nullptr, *bed_uplift = nullptr, *bed_onset = nullptr;
     double bed_rise = 0.0;
@@ -140,6 +142,7 @@ void free_mesh(vg_ctx *c)
     dfree(c->gauge_cells); dfree(c->ring_t); dfree(c->ring_eta); dfree(c->staging);
     dfree(c->bed_vtx); dfree(c->bed_depth0); dfree(c->bed_uplift); dfree(c->bed_onset);
     c->bed_on = false;
+    c->n_open = 0;
     c->depth_v.clear();
     c->dev_bytes = 0;
     c->has_mesh = c->has_state = false;
@@ -966,6 +969,45 @@ int vg_set_depth(vg_ctx *c, const double *depth_v)
     return VG_OK;
 }
 
+int vg_set_open_boundary(vg_ctx *c, int64_t n, const int32_t *edges)
+{
+    if (!c || n < 0 || (n > 0 && !edges)) return VG_EINVAL;
+    if (!c->has_mesh) return fail(c, VG_ESTATE, "no mesh");
+    DeviceGuard guard(c->device);
+    HostMesh &m = c->hm;
+    const int64_t nc = m.nc;
+    // boundary faces by their (sorted) original vertex pair
+    std::unordered_map<uint64_t, int64_t> face_of;
+    for (int64_t k = 0; k < nc; k++) {
+        const int32_t *v = &m.vtx[3 * (size_t)m.old_of_new[k]];
+        for (int f = 0; f < 3; f++) {
+            if (m.nbr[f * nc + k] >= 0) continue;
+            uint32_t a = (uint32_t)v[f], b = (uint32_t)v[(f + 1) % 3];
+            if (a > b) std::swap(a, b);
+            face_of[((uint64_t)a << 32) | b] = f * nc + k;
+        }
+    }
+    std::vector<int64_t> open(n);
+    for (int64_t e = 0; e < n; e++) {
+        uint32_t a = (uint32_t)edges[2 * e], b = (uint32_t)edges[2 * e + 1];
+        if (a > b) std::swap(a, b);
+        auto it = face_of.find(((uint64_t)a << 32) | b);
+        if (it == face_of.end())
+            return fail(c, VG_EINVAL, "edge " + std::to_string(e) + " is not a boundary edge of the mesh");
+        open[e] = it->second;
+    }
+    for (auto &kv : face_of) m.nbr[kv.second] = -1;
+    for (int64_t i : open) m.nbr[i] = -2;
+    VG_CUDA(c, cudaStreamSynchronize(c->stream));
+    int rc = partition_blocks(m, m.block, c->err);
+    if (rc) return rc;
+    if ((rc = upload_partition(c))) return rc;
+    VG_CUDA(c, cudaMemcpy(c->nbr, m.nbr.data(), 4 * 3 * (size_t)nc, cudaMemcpyHostToDevice));
+    c->n_open = n > 0 ? (int64_t)open.size() : 0;
+    c->graph_dirty = true;
+    return VG_OK;
+}
+
 int vg_set_bed_motion(vg_ctx *c, const double *uplift_v, const double *onset_v, double rise)
 {
     if (!c) return VG_EINVAL;
@@ -1025,6 +1067,7 @@ int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_eve
     if (!c->has_mesh || !c->has_state) return fail(c, VG_ESTATE, "mesh and state must be set");
     if (c->n_gauges < 1) return fail(c, VG_ESTATE, "the adjoint differentiates gauge records: set gauges first");
     if (c->bed_on) return fail(c, VG_ESTATE, "the adjoint does not differentiate a moving bed");
+    if (c->n_open) return fail(c, VG_ESTATE, "the adjoint handles walls only, not open boundaries");
     DeviceGuard guard(c->device);
     free_adjoint(c);
     int64_t C = checkpoint_every ? checkpoint_every : (int64_t)std::ceil(std::sqrt((double)n_steps));

@@ -686,6 +686,19 @@ int vg_batch_set_gauges(vg_batch *b, int32_t mesh_id, int32_t n, const double *x
     return VG_OK;
 }
 
+int vg_batch_set_open_boundary(vg_batch *b, int32_t mesh_id, int64_t n, const int32_t *edges)
+{
+    if (!b) return VG_EINVAL;
+    if (mesh_id < 0 || mesh_id >= (int)b->meshes.size()) return bfail(b, VG_EINVAL, "no such mesh");
+    DeviceGuard guard(b->device);
+    vg_ctx *ctx = b->meshes[mesh_id].ctx;
+    int rc = vg_set_open_boundary(ctx, n, edges);
+    if (rc) return bfail(b, rc, vg_last_error(ctx));
+    b->dirty = true;
+    if (b->graph2) { cudaGraphExecDestroy(b->graph2); b->graph2 = nullptr; }
+    return VG_OK;
+}
+
 int vg_batch_get_gauges(vg_batch *b, int32_t mesh_id, int32_t scenario, double *t, double *eta, int64_t cap,
                         int64_t *n_rec)
 {

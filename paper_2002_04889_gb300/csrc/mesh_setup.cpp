@@ -327,7 +327,7 @@ int partition_blocks(HostMesh &m, int block, std::string &err)
     int64_t nc = m.nc;
     // recover the neighbour face of each (cell, face): low 2 bits of nbrl
     std::vector<uint8_t> nface(3 * nc);
-    for (int64_t i = 0; i < 3 * nc; i++) nface[i] = m.nbrl[i] == NBR_WALL ? 3 : (uint8_t)(m.nbrl[i] & 3u);
+    for (int64_t i = 0; i < 3 * nc; i++) nface[i] = m.nbr[i] < 0 ? 3 : (uint8_t)(m.nbrl[i] & 3u);
     int32_t nb = (int32_t)((nc + block - 1) / block);
     m.block = block;
     m.nblocks = nb;
@@ -385,13 +385,18 @@ int partition_blocks(HostMesh &m, int block, std::string &err)
         for (int f = 0; f < 3; f++)
             for (int64_t c = c0; c < c1; c++) {
                 int32_t j = m.nbr[f * nc + c];
-                if (j < 0) continue;
+                if (j < 0) {
+                    if (j == -2) nbrl[f * nc + c] = NBR_OPEN;
+                    continue;
+                }
                 nbrl[f * nc + c] = (uint16_t)((local_of(j) << 2) | nface[f * nc + c]);
             }
         for (int32_t k = 0; k < n1; k++)
             for (int f = 0; f < 3; f++) {
                 int32_t j = m.nbr[f * nc + h[k]];
-                if (j >= 0) m.ring1_nbr[3 * ((size_t)m.halo_ptr[b] + k) + f] = (uint16_t)local_of(j);
+                uint16_t &code = m.ring1_nbr[3 * ((size_t)m.halo_ptr[b] + k) + f];
+                if (j >= 0) code = (uint16_t)local_of(j);
+                else if (j == -2) code = NBR_OPEN;
             }
     }
     m.nbrl.swap(nbrl);

@@ -153,12 +153,13 @@ __device__ __forceinline__ void hll_normal(real g, real half_g, real HL, real un
 // Flux through a face seen from its left cell: face velocities, hydrostatic
 // interface depths z* = max(z_L, z_R), H*_s = max(0, H_{s,f} + z_s - z*), HLL,
 // rotation back to (x, y), pressure corrections g (H_{s,f}^2 - H*_s^2) / 2.
-// A wall uses the ghost of Sec. 2.5 (u_n reversed, u_t kept, same depth).
+// bnd: 0 interior; 1 wall, the ghost of Sec. 2.5 (u_n reversed, u_t kept, same
+// depth); 2 open, the transmissive ghost (the face state itself).
 template <typename real>
 __device__ __forceinline__ void face_flux(real g, real half_g, real hthr,
                                           real HfL, real HufL, real HvfL, real zL,
                                           real HfR, real HufR, real HvfR, real zR,
-                                          real nx, real ny, bool wall,
+                                          real nx, real ny, int bnd,
                                           real Phi[3], real &PL, real &PR, real &amax)
 {
     real uL = real(0), vL = real(0);
@@ -166,10 +167,10 @@ __device__ __forceinline__ void face_flux(real g, real half_g, real hthr,
     real unL = uL * nx + vL * ny;
     real utL = -uL * ny + vL * nx;
     real HsL, HsR, unR, utR;
-    if (wall) {
+    if (bnd) {
         HsL = vmax(real(0), (HfL + zL) - zL);
         HsR = HsL;
-        unR = -unL;
+        unR = bnd == 2 ? unL : -unL;
         utR = utL;
         HfR = HfL;
     } else {
@@ -265,7 +266,7 @@ __device__ __forceinline__ bool stage_state(const KArgs<real> &a, int gid, real 
 __device__ __forceinline__ void face_flux_dev(float g, float half_g, float hthr,
                                               float efL, float HufL, float HvfL, float zL, float eL,
                                               float efR, float HufR, float HvfR, float zR, float eR,
-                                              float nx, float ny, bool wall,
+                                              float nx, float ny, int bnd,
                                               float Phi[3], float &QL, float &QR, float &amax)
 {
     float HfL = efL - zL;
@@ -274,10 +275,10 @@ __device__ __forceinline__ void face_flux_dev(float g, float half_g, float hthr,
     float unL = uL * nx + vL * ny;
     float utL = -uL * ny + vL * nx;
     float HsL, HsR, unR, utR, ds, HfR;
-    if (wall) {
+    if (bnd) {
         HsL = fmaxf(0.f, HfL);
         HsR = HsL;
-        unR = -unL;
+        unR = bnd == 2 ? unL : -unL;
         utR = utL;
         ds = 0.f;
         HfR = HfL; efR = efL; eR = eL; zR = zL;
@@ -427,7 +428,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             for (int f = 0; f < 3; f++) {
                 const uint16_t code = a.nbrl[f * nc + gid];
                 sCode[f * B + tid] = code;
-                if (code == NBR_WALL || (code >> 2) >= B || (int)(code >> 2) > tid) owned |= 1 << f;
+                if (code >= NBR_OPEN || (code >> 2) >= B || (int)(code >> 2) > tid) owned |= 1 << f;
             }
             real W, Hu, Hv, zc;
             bool neg = stage_cell<real, STAGE>(a, gid, dt, W, Hu, Hv, zc);
@@ -477,18 +478,16 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         bool recon = (a.order == 2) && (HK > hthr);
 #pragma unroll
         for (int f = 0; f < 3; f++) {
-            bool wall;
+            uint16_t code;
             int nl;
             if (l < B) {
-                uint16_t code = sCode[f * B + l];
-                wall = code == NBR_WALL;
+                code = sCode[f * B + l];
                 nl = code >> 2;
             } else {
-                uint16_t code = a.ring1_nbr[3 * (h0 + (l - B)) + f];
-                wall = code == NBR_WALL;
+                code = a.ring1_nbr[3 * (h0 + (l - B)) + f];
                 nl = code;
             }
-            if (!wall) {
+            if (code < NBR_OPEN) {
                 real Wj, Huj, Hvj, zj;
                 ld4(sW + 4 * nl, Wj, Huj, Hvj, zj);
                 const real Hj = ETA ? Wj - zj : Wj;
@@ -496,6 +495,11 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
                 qn[f][1] = Huj;
                 qn[f][2] = Hvj;
                 if (!(Hj > hthr)) recon = false;
+            } else if (code == NBR_OPEN) {
+                // transmissive ghost: the cell's own values
+                qn[f][0] = qK[0];
+                qn[f][1] = HuK;
+                qn[f][2] = HvK;
             } else {
                 real nxf, nyf;
                 if constexpr (ETA) {
@@ -607,7 +611,8 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         const int l = item >> 2, f = item & 3;
         const int gid = c0 + l;
         const uint16_t code = sCode[f * B + l];
-        const bool wall = code == NBR_WALL;
+        const bool wall = code >= NBR_OPEN;           // wall or open: no neighbour
+        const int bnd = wall ? (code == NBR_OPEN ? 2 : 1) : 0;
         const int nl = code >> 2, nf = code & 3;
         real *pL = sF + 4 * (f * L1 + l);
         real *pR = sF + 4 * (nf * L1 + nl);
@@ -626,13 +631,13 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             nx = nv.x; ny = nv.y;
             len = g32_len(geo, gid, f);
             face_flux_dev(g, half_g, hthr, WfL, HufL, HvfL, zL, WL,
-                          WfR, HufR, HvfR, zR, WR, nx, ny, wall, Phi, PL, PR, am);
+                          WfR, HufR, HvfR, zR, WR, nx, ny, bnd, Phi, PL, PR, am);
         } else {
             nx = geo[(GEO_NX + f) * nc + gid];
             ny = geo[(GEO_NY + f) * nc + gid];
             len = geo[(GEO_LEN + f) * nc + gid];
             face_flux<real>(g, half_g, hthr, WfL, HufL, HvfL, zL,
-                            WfR, HufR, HvfR, zR, nx, ny, wall, Phi, PL, PR, am);
+                            WfR, HufR, HvfR, zR, nx, ny, bnd, Phi, PL, PR, am);
         }
         const real t0 = len * Phi[0];
         const real la = len * am;

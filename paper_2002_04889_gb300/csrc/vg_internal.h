@@ -25,7 +25,8 @@ enum GeoRow : int {
     GEO_ROWS = 22
 };
 
-constexpr uint16_t NBR_WALL = 0xFFFF;
+constexpr uint16_t NBR_WALL = 0xFFFF;   // wall face (ghost of Sec. 2.5); nbr = -1
+constexpr uint16_t NBR_OPEN = 0xFFFE;   // open (transmissive) face; nbr = -2
 
 // Host-side prepared mesh, cells in the library's (renumbered) order.
 struct HostMesh {
@@ -39,13 +40,13 @@ struct HostMesh {
     std::vector<int32_t> vtx;            // [nc][3] local-order vertices (original cell order)
     std::vector<double> geo;             // [GEO_ROWS][nc]  (internal order)
     std::vector<double> z;               // [nc]            (internal order)
-    std::vector<int32_t> nbr;            // [3][nc] internal neighbour ids, -1 wall
-    std::vector<uint16_t> nbrl;          // [3][nc] (local << 2 | face) or NBR_WALL
+    std::vector<int32_t> nbr;            // [3][nc] internal neighbour ids, -1 wall, -2 open
+    std::vector<uint16_t> nbrl;          // [3][nc] (local << 2 | face), NBR_WALL or NBR_OPEN
     std::vector<int32_t> halo_ptr;       // [nblocks + 1] into halo_ids / ring1_nbr
     std::vector<int32_t> halo_n1;        // [nblocks] ring-1 cells of each block
     std::vector<int32_t> halo_ids;       // per block: ring-1 then ring-2 cells (internal ids)
     std::vector<uint16_t> ring1_nbr;     // [3 * halo_ids.size()] local neighbour index of
-                                         // each ring-1 cell (NBR_WALL for a wall)
+                                         // each ring-1 cell (NBR_WALL / NBR_OPEN)
     std::vector<double> xy;              // [nv][2] copy for point location
 };
 

@@ -84,6 +84,7 @@ _SIGNATURES = {
     "vg_step_noalloc": ([_V, _V, _V, C.c_double, _D], C.c_int),
     "vg_set_depth": ([_V, _D], C.c_int),
     "vg_set_bed_motion": ([_V, _D, _D, C.c_double], C.c_int),
+    "vg_set_open_boundary": ([_V, C.c_int64, _I32], C.c_int),
     "vg_adj_forward": ([_V, C.c_int64, C.c_double, C.c_int64], C.c_int),
     "vg_adj_backward": ([_V, _D, _D, _D, _D, _D, _D], C.c_int),
     "vg_batch_create": ([C.POINTER(_V), C.c_int, C.c_int, _V], C.c_int),
@@ -99,6 +100,7 @@ _SIGNATURES = {
     "vg_batch_autotune": ([_V, C.c_int32, C.POINTER(C.c_int32), _D], C.c_int),
     "vg_batch_info": ([_V, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _I64, _I64], C.c_int),
     "vg_batch_set_gauges": ([_V, C.c_int32, C.c_int32, _D], C.c_int),
+    "vg_batch_set_open_boundary": ([_V, C.c_int32, C.c_int64, _I32], C.c_int),
     "vg_batch_get_gauges": ([_V, C.c_int32, C.c_int32, _D, _D, C.c_int64, _I64], C.c_int),
 }
 
@@ -426,6 +428,11 @@ class Solver:
     def set_depth(self, depth_v) -> None:
         vg_set_depth(self.ctx, depth_v)
 
+    def set_open_boundary(self, edges) -> None:
+        """Open (transmissive) boundary edges [(a, b), ...] (vg_set_open_boundary)."""
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+        _check(self.ctx, load().vg_set_open_boundary(self.ctx, e.shape[0], e.ctypes.data_as(_I32)))
+
     def set_bed_motion(self, uplift_v, onset_v=None, rise: float = 0.0) -> None:
         """Moving bed (vg_set_bed_motion); uplift_v None removes it."""
         if uplift_v is None:
@@ -535,6 +542,11 @@ class Batch:
         _bcheck(self.h, load().vg_batch_set_gauges(self.h, int(mesh_id), xy.shape[0],
                                                    _dp(xy) if xy.shape[0] else None))
         self.n_gauges[mesh_id] = xy.shape[0]
+
+    def set_open_boundary(self, mesh_id: int, edges) -> None:
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+        _bcheck(self.h, load().vg_batch_set_open_boundary(self.h, int(mesh_id), e.shape[0],
+                                                          e.ctypes.data_as(_I32)))
 
     def gauges(self, mesh_id: int, scen: int):
         """Gauge records (t [n], eta [n, G]) of one scenario."""
