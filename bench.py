@@ -56,7 +56,22 @@ WORKLOADS = {
     "thacker_paraboloid_10m": dict(n=2236),
     "thacker_paraboloid_4m": dict(n=1414),
     "thacker_paraboloid_1m": dict(n=707),
+    # all-wet control: the same grid over a flat 10 m bed with a Gaussian hump of
+    # the free surface (no dry cells, so no wet/dry divergence)
+    "flat_basin_allwet_40m": dict(n=4472, kind="flat"),
+    "flat_basin_allwet_4m": dict(n=1414, kind="flat"),
 }
+
+
+def workload_inputs(name: str, n: int):
+    """Mesh and initial state of a workload's generator on an n x n grid at dx = 0.04 m."""
+    from paper_2002_04889_gb300 import inputs as I
+    if WORKLOADS[name].get("kind") == "flat":
+        half = 0.5 * n * 0.04
+        m = I.flat_basin_mesh(n, half, 10.0, shuffle_cells=True)
+        return m, I.gaussian_hump_state(m, 0.0, 1.0, 0.0, 0.0, 0.1 * half)
+    m = I.thacker_large_mesh(n=n)
+    return m, I.thacker_initial_state(m)
 
 
 def log(*a):
@@ -174,19 +189,14 @@ def profiled_traffic(workload: str, precision: int, kernel: str):
 
 
 def make_workload(name: str):
-    from paper_2002_04889_gb300 import inputs as I
-    m = I.thacker_large_mesh(n=WORKLOADS[name]["n"])
-    s = I.thacker_initial_state(m)
-    return m, s
+    return workload_inputs(name, WORKLOADS[name]["n"])
 
 
-def cpu_baseline(budget_s: float = 15.0, n: int = 1414):
+def cpu_baseline(budget_s: float = 15.0, n: int = 1414, workload: str = "thacker_paraboloid_40m"):
     """The FP64 oracle on a bounded sample of the workload: the same generator at the
     same dx on an n x n grid (2 n^2 triangles), as many steps as fit in budget_s."""
     import oracle as O
-    from paper_2002_04889_gb300 import inputs as I
-    m = I.thacker_large_mesh(n=n)
-    s = I.thacker_initial_state(m)
+    m, s = workload_inputs(workload, n)
     om = O.OracleMesh.from_mesh(m)
     prm = O.params(h_threshold=1e-5, cfl=0.9)
     st = (s.H, s.Hu, s.Hv, 0.0)
@@ -320,10 +330,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle as O
-    from paper_2002_04889_gb300 import inputs as I
     n = 707
-    m = I.thacker_large_mesh(n=n)
-    s = I.thacker_initial_state(m)
+    m, s = workload_inputs(args.workload, n)
     om = O.OracleMesh.from_mesh(m)
     prm = O.params(h_threshold=1e-5, cfl=0.9)
     st = (s.H, s.Hu, s.Hv, 0.0)
@@ -352,7 +360,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="thacker_paraboloid_40m", choices=sorted(WORKLOADS))
@@ -459,7 +467,7 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.cpu_budget)
+        cpu = cpu_baseline(args.cpu_budget, workload=args.workload)
     sv.close()
     batched = adjoint = None
     if rank == 0 and args.batched_steps > 0:
