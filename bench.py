@@ -51,6 +51,17 @@ UNIT = "cell-updates/s"
 # reads w^n and R0 and writes w^{n+1}.
 ALGO_BYTES = {32: {"stage1": 64, "stage2": 76}, 64: {"stage1": 104, "stage2": 128}}
 
+# FP64 is bound by GB300's FP64 units, not HBM.  Algorithmic FP64 operations per
+# cell per full step (add, sub, mul, div, sqrt on state-dependent values; the
+# geometry is precomputed), counted in the oracle's own arithmetic by
+# `python -m oracle.count_ops` on a 180,000-cell sample of each generator; the
+# two stages run the same residual, so each stage is taken as half.
+FP64_FLOPS_PER_CELL_STEP = {"thacker": 472.55, "flat": 632.31}
+# FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA thread-operations
+# per cycle per SM (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak) x 2
+# flops x 2.07 GHz maximum SM clock = 1.26 TFLOP/s.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
 WORKLOADS = {
     "thacker_paraboloid_40m": dict(n=4472),
     "thacker_paraboloid_10m": dict(n=2236),
@@ -441,6 +452,15 @@ def main():
                 "algo_bytes_per_launch": algo, "peak_kind": f"{peak_kind} hbm_gbs",
                 "kernel_avg_ms": kernel_ms,
                 "step_algo_gbs": round(step_bytes / (ms * 1e-3 / args.steps) / 1e9, 1)}
+    if args.precision == 64:
+        kind = WORKLOADS[args.workload].get("kind", "thacker")
+        flops = 0.5 * FP64_FLOPS_PER_CELL_STEP[kind] * nc
+        tflops = flops / (avg_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                    "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                    "kernel": dom, "algo_flops_per_launch": flops,
+                    "peak_kind": "derived: 152 SMs x 4 FP64 flop/cycle x 2.07 GHz",
+                    "kernel_avg_ms": kernel_ms, "hbm_frac": round(achieved / peak, 4)}
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None

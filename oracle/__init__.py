@@ -278,3 +278,34 @@ def ad_gauge_gradient(mesh, state, dt, n_steps, gauge_cells, weights, g=9.81, h_
     if rc != 0:
         raise ValueError(f"oracle mesh rejected (code {rc})")
     return dict(J=J.value, eta=eta, dH0=out[0], dHu0=out[1], dHv0=out[2], ddepth=out[3])
+
+
+_count = None
+
+
+def count_step_ops(mesh, state, g=9.81, h_threshold=1e-5, cfl=0.9) -> dict:
+    """Floating-point operations of one adaptive SSP-RK(2,2) step (Sec. 2.3) of
+    the oracle's arithmetic from `state`, counted by the oracle compiled with an
+    operation-counting scalar (op_count.hpp): add, sub, mul, div, sqrt, minmax
+    (min/max/abs), and the step dt."""
+    global _count
+    from .build import build_count
+    if _count is None:
+        lib = C.CDLL(build_count())
+        lib.vo_count_step.argtypes = [C.c_int64, _D, C.c_int64, _I32, _D, _D, _D, _D, C.c_double,
+                                      C.c_double, C.c_double, _I64, _D]
+        lib.vo_count_step.restype = C.c_int
+        _count = lib
+    xy = _f64(mesh.xy).reshape(-1, 2)
+    tri = np.ascontiguousarray(mesh.tri, dtype=np.int32).reshape(-1, 3)
+    out = np.zeros(6, dtype=np.int64)
+    dt = C.c_double()
+    rc = _count.vo_count_step(xy.shape[0], _dp(xy), tri.shape[0], tri.ctypes.data_as(_I32), _dp(_f64(mesh.depth)),
+                              _dp(_f64(state[0])), _dp(_f64(state[1])), _dp(_f64(state[2])), float(g),
+                              float(h_threshold), float(cfl), out.ctypes.data_as(_I64), C.byref(dt))
+    if rc != 0:
+        raise ValueError(f"vo_count_step failed ({rc})")
+    keys = ("add", "sub", "mul", "div", "sqrt", "minmax")
+    r = {k: int(v) for k, v in zip(keys, out)}
+    r["dt"] = dt.value
+    return r

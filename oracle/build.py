@@ -14,6 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "volna_oracle.c")
 AD_SRC = os.path.join(HERE, "volna_oracle_ad.cpp")
 AD_HDR = os.path.join(HERE, "ad_tape.hpp")
+COUNT_SRC = os.path.join(HERE, "volna_oracle_count.cpp")
+COUNT_HDR = os.path.join(HERE, "op_count.hpp")
 
 
 def library_path() -> str:
@@ -22,6 +24,26 @@ def library_path() -> str:
 
 def ad_library_path() -> str:
     return os.path.join(HERE, "_build", "libvolna_oracle_ad.so")
+
+
+def count_library_path() -> str:
+    return os.path.join(HERE, "_build", "libvolna_oracle_count.so")
+
+
+def build_count(verbose: bool = False) -> str:
+    """The oracle compiled with the operation-counting scalar; no OpenMP."""
+    out = count_library_path()
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    newest = max(os.path.getmtime(f) for f in (SRC, COUNT_SRC, COUNT_HDR))
+    if os.path.exists(out) and os.path.getmtime(out) >= newest:
+        return out
+    cmd = ["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c++17",
+           "-o", out + ".tmp", COUNT_SRC, "-lm"]
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    subprocess.run(cmd, check=True)
+    os.replace(out + ".tmp", out)
+    return out
 
 
 def build_ad(verbose: bool = False) -> str:
@@ -57,3 +79,4 @@ def build(verbose: bool = False) -> str:
 if __name__ == "__main__":
     print(build(verbose=True))
     print(build_ad(verbose=True))
+    print(build_count(verbose=True))
