@@ -249,18 +249,20 @@ def _load_ad():
     build_ad()
     lib = C.CDLL(path)
     lib.vo_ad_gauge_gradient.argtypes = [C.c_int64, _D, C.c_int64, _I32, _D, _D, _D, _D, C.c_double,
-                                         C.c_double, C.c_int, C.c_double, C.c_int64, C.c_int32, _I32, _D,
-                                         _D, _D, _D, _D, _D, _D]
+                                         C.c_double, C.c_int, C.c_double, C.c_double, C.c_int64, C.c_int32,
+                                         _I32, _D, _D, _D, _D, _D, _D, _D, _D]
     lib.vo_ad_gauge_gradient.restype = C.c_int
     _ad = lib
     return lib
 
 
 def ad_gauge_gradient(mesh, state, dt, n_steps, gauge_cells, weights, g=9.81, h_threshold=1e-5,
-                      order=2):
+                      order=2, cfl=0.9):
     """The oracle's discrete adjoint (tape AD of the oracle's own arithmetic) of
-    J = sum_{n,g} weights[n, g] * eta_g(t_n), n = 0..n_steps, fixed dt (Sec. 2.3 steps).
-    Returns dict(J, eta[n+1, G], dH0, dHu0, dHv0, ddepth)."""
+    J = sum_{n,g} weights[n, g] * eta_g(t_n), n = 0..n_steps (Sec. 2.3 steps), with
+    the fixed time step dt, or for dt = 0 / None the CFL step of each step,
+    differentiated through its minimum.
+    Returns dict(J, eta[n+1, G], dts[n], dH0, dHu0, dHv0, ddepth)."""
     xy = _f64(mesh.xy).reshape(-1, 2)
     tri = np.ascontiguousarray(mesh.tri, dtype=np.int32)
     depth = _f64(mesh.depth)
@@ -269,15 +271,16 @@ def ad_gauge_gradient(mesh, state, dt, n_steps, gauge_cells, weights, g=9.81, h_
     w = _f64(weights).reshape(n_steps + 1, gc.shape[0])
     nc, nv = tri.shape[0], xy.shape[0]
     eta = np.zeros((n_steps + 1, gc.shape[0]))
+    dts = np.zeros(max(int(n_steps), 1))
     J = C.c_double()
     out = [np.zeros(nc) for _ in range(3)] + [np.zeros(nv)]
     rc = _load_ad().vo_ad_gauge_gradient(nv, _dp(xy), nc, tri.ctypes.data_as(_I32), _dp(depth),
-                                         _dp(H0), _dp(Hu0), _dp(Hv0), g, h_threshold, order, dt,
-                                         int(n_steps), gc.shape[0], gc.ctypes.data_as(_I32), _dp(w),
-                                         _dp(eta), C.byref(J), *(_dp(o) for o in out))
+                                         _dp(H0), _dp(Hu0), _dp(Hv0), g, h_threshold, order, float(cfl),
+                                         float(dt or 0.0), int(n_steps), gc.shape[0], gc.ctypes.data_as(_I32),
+                                         _dp(w), _dp(eta), _dp(dts), C.byref(J), *(_dp(o) for o in out))
     if rc != 0:
         raise ValueError(f"oracle mesh rejected (code {rc})")
-    return dict(J=J.value, eta=eta, dH0=out[0], dHu0=out[1], dHv0=out[2], ddepth=out[3])
+    return dict(J=J.value, eta=eta, dts=dts[:n_steps], dH0=out[0], dHu0=out[1], dHv0=out[2], ddepth=out[3])
 
 
 _count = None

@@ -564,20 +564,26 @@ void vo_residual(vo_mesh *m, const vo_params *p, const vo_real *H, const vo_real
  * the time left before t_end (if > 0).  dt_fixed > 0 replaces the CFL rule.
  * With no moving wave anywhere the step is dt_max (0 when unset).
  */
-double vo_time_step(const vo_mesh *m, const vo_params *p, const vo_real *amax, double t)
+vo_real vo_time_step(const vo_mesh *m, const vo_params *p, const vo_real *amax, double t)
 {
-    double dt;
+    vo_real dt;
     if (p->dt_fixed > 0.0) {
         dt = p->dt_fixed;
     } else {
-        double mn = INFINITY;
+        /* the minimum runs over the cells in order, a tie keeping the earlier cell */
+        vo_real mn = INFINITY;
+        int any = 0;
         for (int64_t K = 0; K < m->nc; K++)
-            if (vo_val(amax[K]) > 0.0) mn = fmin(mn, m->area[K] / (3.0 * vo_val(amax[K])));
-        dt = isinf(mn) ? (p->dt_max > 0.0 ? p->dt_max : 0.0) : p->cfl * mn;
+            if (vo_val(amax[K]) > 0.0) {
+                mn = fmin(mn, m->area[K] / (3.0 * amax[K]));
+                any = 1;
+            }
+        if (any) dt = p->cfl * mn;
+        else dt = p->dt_max > 0.0 ? p->dt_max : 0.0;
     }
-    if (p->dt_max > 0.0) dt = fmin(dt, p->dt_max);
-    if (p->t_end > 0.0 && t + dt > p->t_end) dt = p->t_end - t;
-    if (dt < 0.0) dt = 0.0;
+    if (p->dt_max > 0.0) dt = fmin(dt, (vo_real)p->dt_max);
+    if (p->t_end > 0.0 && t + vo_val(dt) > p->t_end) dt = p->t_end - t;
+    if (vo_val(dt) < 0.0) dt = 0.0;
     return dt;
 }
 
@@ -611,7 +617,7 @@ void vo_step(vo_mesh *m, const vo_params *p, vo_real *H, vo_real *Hu, vo_real *H
     vo_real *R0 = m->R0, *R1 = m->R1, *W1 = m->W1;
     vo_real *H1 = W1, *Hu1 = W1 + nc, *Hv1 = W1 + 2 * nc;
     vo_residual(m, p, H, Hu, Hv, R0, R0 + nc, R0 + 2 * nc, m->amax);
-    double dt = vo_time_step(m, p, m->amax, *t);
+    vo_real dt = vo_time_step(m, p, m->amax, *t);
 #pragma omp parallel for schedule(static)
     for (int64_t K = 0; K < nc; K++) {
         H1[K] = H[K] + dt * R0[K];
@@ -627,8 +633,8 @@ void vo_step(vo_mesh *m, const vo_params *p, vo_real *H, vo_real *Hu, vo_real *H
         Hv[K] = 0.5 * Hv[K] + 0.5 * (Hv1[K] + dt * R1[2 * nc + K]);
     }
     neg += dry_fix(nc, p->h_threshold, H, Hu, Hv);
-    *t += dt;
-    if (dt_out) *dt_out = dt;
+    *t += vo_val(dt);
+    if (dt_out) *dt_out = vo_val(dt);
     if (neg_count) *neg_count += neg;
 }
 

@@ -29,19 +29,21 @@ extern "C" {
 
 /*
  * Linear gauge functional and its gradient through n_steps SSP-RK(2,2) steps
- * with the fixed time step dt:
+ * with the fixed time step dt, or (dt <= 0) the CFL time step of each step
+ * (Sec. 2.3 rule with the given cfl), differentiated through the minimum:
  *   J = sum_{n = 0..n_steps} sum_g weights[n][g] * eta_g(t_n),
  * eta_g = H + z of gauge cell g (after step n; n = 0 is the initial state).
  * Inputs: the mesh (as vo_mesh_build), per-vertex depth, the initial state,
- * g / H_threshold / order.  Outputs: eta_out[n_steps + 1][G] (may be NULL),
- * *J, and dJ/dH0, dJ/dHu0, dJ/dHv0 [nc] and dJ/ddepth_v [nv].
+ * g / H_threshold / order / cfl.  Outputs: eta_out[n_steps + 1][G] and
+ * dts_out[n_steps] (may be NULL), *J, and dJ/dH0, dJ/dHu0, dJ/dHv0 [nc] and
+ * dJ/ddepth_v [nv].
  * Returns 0, or a negative code for a rejected mesh.
  */
 int vo_ad_gauge_gradient(int64_t nv, const double *xy, int64_t nc, const int32_t *tri, const double *depth_v,
                          const double *H0, const double *Hu0, const double *Hv0, double g, double hthr, int order,
-                         double dt, int64_t n_steps, int32_t n_gauges, const int32_t *gauge_cells,
-                         const double *weights, double *eta_out, double *J_out, double *gH0, double *gHu0,
-                         double *gHv0, double *gdepth)
+                         double cfl, double dt, int64_t n_steps, int32_t n_gauges, const int32_t *gauge_cells,
+                         const double *weights, double *eta_out, double *dts_out, double *J_out, double *gH0,
+                         double *gHu0, double *gHv0, double *gdepth)
 {
     VoTape &tape = vo_tape();
     tape.clear();
@@ -58,12 +60,17 @@ int vo_ad_gauge_gradient(int64_t nv, const double *xy, int64_t nc, const int32_t
     p.g = g;
     p.h_threshold = hthr;
     p.order = order;
-    p.dt_fixed = dt;
+    p.cfl = cfl;
+    p.dt_fixed = dt > 0.0 ? dt : 0.0;
     adouble J = 0.0;
     double t = 0.0;
     int64_t neg = 0;
     for (int64_t n = 0; n <= n_steps; n++) {
-        if (n > 0) vo_ad_impl::vo_step(m, &p, H.data(), Hu.data(), Hv.data(), &t, nullptr, &neg);
+        if (n > 0) {
+            double dtn = 0.0;
+            vo_ad_impl::vo_step(m, &p, H.data(), Hu.data(), Hv.data(), &t, &dtn, &neg);
+            if (dts_out) dts_out[n - 1] = dtn;
+        }
         for (int32_t k = 0; k < n_gauges; k++) {
             int32_t c = gauge_cells[k];
             adouble eta = H[c] + m->z[c];

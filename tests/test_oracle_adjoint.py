@@ -79,3 +79,50 @@ def test_oracle_adjoint_matches_forward_and_finite_differences(order):
             lo, hi = min(fwd, bwd) - tol, max(fwd, bwd) + tol
             assert lo <= grad_dot <= hi, (kind, grad_dot, fwd, bwd)
     assert n_central >= 12
+
+
+def _J_cfl(m, state, depth, cells, n_steps, w, cfl=0.9):
+    om = O.OracleMesh(m.xy, m.tri, depth)
+    r = om.run(O.params(cfl=cfl), (state[0], state[1], state[2], 0.0), n_steps, gauge_cells=cells)
+    z = om.get("z")
+    eta0 = state[0][cells] + z[cells]
+    return float(np.sum(w[0] * eta0) + np.sum(w[1:] * r["gauges"])), r["dts"]
+
+
+def test_oracle_adjoint_through_the_cfl_time_step():
+    """With the adaptive CFL step (Sec. 2.3 rule) every step's dt depends on the
+    state through the minimum over cells; the taped adjoint differentiates
+    through it and matches central differences of the adaptive forward run."""
+    m, st, cells, _, n_steps, w = _setup()
+    ad = O.ad_gauge_gradient(m, st, None, n_steps, cells, w, h_threshold=1e-5, cfl=0.9)
+    J0, dts = _J_cfl(m, st, m.depth, cells, n_steps, w)
+    assert ad["J"] == pytest.approx(J0, rel=1e-13, abs=1e-15)
+    np.testing.assert_array_equal(ad["dts"], dts)
+    assert np.ptp(dts) > 0                         # the step does change from step to step
+    rng = np.random.default_rng(11)
+    wet = st[0] > 1e-3
+    eps = 1e-8
+    n_ok = 0
+    for kind in ("H", "Hu", "depth"):
+        for _ in range(4):
+            if kind == "depth":
+                d = rng.normal(size=m.nv)
+                gd = float(np.dot(ad["ddepth"], d))
+                f = lambda e: _J_cfl(m, st, m.depth + e * d, cells, n_steps, w)[0]
+            else:
+                d = rng.normal(size=m.nc) * wet
+                gd = float(np.dot(ad["d" + kind + "0"], d))
+                k = ("H", "Hu").index(kind)
+
+                def f(e, k=k, d=d):
+                    stt = [a.copy() for a in st]
+                    stt[k] = stt[k] + e * d
+                    return _J_cfl(m, stt, m.depth, cells, n_steps, w)[0]
+            jp, jm = f(eps), f(-eps)
+            fd = (jp - jm) / (2 * eps)
+            if abs(gd - fd) <= 2e-6 * max(1.0, abs(fd)):
+                n_ok += 1
+            else:
+                fwd, bwd = (jp - J0) / eps, (J0 - jm) / eps
+                assert min(fwd, bwd) - 2e-6 <= gd <= max(fwd, bwd) + 2e-6, (kind, gd, fwd, bwd)
+    assert n_ok >= 9
