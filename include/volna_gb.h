@@ -238,9 +238,9 @@ int vg_step_noalloc(vg_ctx *ctx, const void *w_in, void *w_out, double t, double
 
 
 /* ------------------------------------------------------------------------
- * Discrete adjoint (FP64 contexts).  With a fixed time step dt, the run of
- * n_steps SSP-RK(2,2) steps (Sec. 2.3) from the current state is a smooth map
- * almost everywhere (branches -- wet/dry switches, limiter and wave-speed
+ * Discrete adjoint (FP64 contexts).  The run of n_steps SSP-RK(2,2) steps
+ * (Sec. 2.3) from the current state, with a fixed or the CFL time step, is a
+ * smooth map almost everywhere (branches -- wet/dry switches, limiter and wave-speed
  * choices, HLL regions -- frozen where the run takes them), and the gauge
  * records eta_g(t_n) = H + z of the gauge cells (Sec. 3 gauges) are outputs of
  * it.  vg_adj_backward returns the gradient of any scalar J(eta) given
@@ -252,13 +252,19 @@ int vg_step_noalloc(vg_ctx *ctx, const void *w_in, void *w_out, double t, double
 int vg_set_depth(vg_ctx *ctx, const double *depth_v);
 
 /*
- * Forward run for the adjoint: n_steps steps with the fixed time step dt from
- * the current state, recording the gauges at the start and after every step
- * (vg_get_gauges then returns n_steps + 1 records).  The state at every
- * checkpoint_every-th step is kept on the device (0: ceil(sqrt(n_steps)), the
- * sqrt(N) checkpointing that bounds memory by about 2 sqrt(N) states while
- * vg_adj_backward recomputes each segment once).  The context's state
- * advances to step n_steps.
+ * Forward run for the adjoint: n_steps steps from the current state with the
+ * fixed time step dt > 0, or, for dt = 0, the CFL time step of every step (the
+ * rule of Sec. 2.3 with the context's cfl and dt_max; t_end is ignored),
+ * recording the gauges at the start and after every step (vg_get_gauges then
+ * returns n_steps + 1 records).  With dt = 0 the backward pass differentiates
+ * through each step's time step as well: dt depends on the state through the
+ * cell of smallest bound |K| / (3 max_f l_f a_f) (a tie goes to the lowest
+ * original cell id) and its face of largest l_f a_f (a tie to the first local
+ * face); a step clamped by dt_max does not depend on the state.  The state at
+ * every checkpoint_every-th step is kept on the device (0: ceil(sqrt(n_steps)),
+ * the sqrt(N) checkpointing that bounds memory by about 2 sqrt(N) states while
+ * vg_adj_backward recomputes each segment once).  The context's state advances
+ * to step n_steps.  dt < 0 or non-finite: VG_EINVAL.
  */
 int vg_adj_forward(vg_ctx *ctx, int64_t n_steps, double dt, int64_t checkpoint_every);
 

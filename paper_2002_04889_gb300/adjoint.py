@@ -1,8 +1,10 @@
 """torch.autograd bridge of the discrete adjoint (vg_adj_forward / vg_adj_backward).
 
 ``gauge_records(solver, H0, Hu0, Hv0, depth_v, n_steps, dt)`` runs the FP64 solver
-with a fixed time step and returns the gauge records eta[n_steps + 1, G] as a
-differentiable function of the initial state and the per-vertex bathymetry.
+with the fixed time step dt, or with the CFL time step of every step for dt = 0
+(differentiated through as well), and returns the gauge records
+eta[n_steps + 1, G] as a differentiable function of the initial state and the
+per-vertex bathymetry.
 Its backward is the hand-written CUDA adjoint with sqrt(N) checkpointing; the
 tensors only cross the C ABI (argument marshalling).
 """

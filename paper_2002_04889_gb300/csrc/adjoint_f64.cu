@@ -150,10 +150,13 @@ __global__ void adj_face_values_kernel(AdjMesh m, const double *w, const double 
 
 // Reverse of the face flux seen from L (forward: face_flux / hll_normal).
 // Inputs: the two face states, beds, normal, wall flag, and the adjoints of
-// Phi[3], P_L, P_R.  Outputs: adjoints of (H_f, Hu_f, Hv_f, z) on each side.
+// Phi[3], P_L, P_R and of the wave speed a = max(|s_L|, |s_R|) (amb: nonzero
+// only for the face that sets the CFL time step).  Outputs: adjoints of
+// (H_f, Hu_f, Hv_f, z) on each side.
 __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL, double zL, double HfR,
                          double HufR, double HvfR, double zR, double nx, double ny, bool wall,
-                         const double Pb[3], double PLb, double PRb, double bL[4], double bR[4])
+                         const double Pb[3], double PLb, double PRb, double bL[4], double bR[4],
+                         double amb = 0.0)
 {
     const double g = m.g, hg = m.half_g, hthr = m.hthr;
     for (int k = 0; k < 4; k++) { bL[k] = 0.0; bR[k] = 0.0; }
@@ -265,6 +268,11 @@ __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL,
         utRb += FRb[2] * qR + wRb[2] * HsR;
         HsRb += qRb * unR;
         unRb += qRb * HsR;
+        // the wave speed a = max(|s_L|, |s_R|) (a tie takes |s_L|; |s| at s = 0 takes +s)
+        if (amb != 0.0) {
+            if (fabs(sR) > fabs(sL)) sRb += sR < 0.0 ? -amb : amb;
+            else sLb += sL < 0.0 ? -amb : amb;
+        }
         // speeds
         double cLb = 0.0, cRb = 0.0;
         if (case_ == 1) {
@@ -557,6 +565,185 @@ __global__ void adj_gauge_kernel(int n_gauges, const int32_t *cells, const doubl
     (void)nc;
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint through the CFL time step (Sec. 2.3 rule, vg_adj_forward with dt = 0):
+// dt = cfl |K*| / (3 l_f* a_f*) for the cell K* of smallest bound and its face
+// f* of largest l_f a_f, so dt-bar reaches the state only through the wave
+// speed of that one face: a-bar = -dt-bar dt / a.  dt-bar itself is
+// sum (w1-bar . R0) + sum (w-bar^{n+1}_pre . R1 / 2), the two stages' use of dt.
+// ---------------------------------------------------------------------------
+
+// Forward wave speed of one face, the forward kernels' arithmetic.
+__device__ double face_speed(const AdjMesh &m, double HfL, double HufL, double HvfL, double zL, double HfR,
+                             double HufR, double HvfR, double zR, double nx, double ny, bool wall)
+{
+    const double g = m.g, hthr = m.hthr;
+    double uL = 0.0, vL = 0.0;
+    if (HfL > hthr) { uL = HufL / HfL; vL = HvfL / HfL; }
+    double unL = uL * nx + vL * ny;
+    double HsL, HsR, unR;
+    if (wall) {
+        HsL = fmax(0.0, (HfL + zL) - zL);
+        HsR = HsL;
+        unR = -unL;
+    } else {
+        double uR = 0.0, vR = 0.0;
+        if (HfR > hthr) { uR = HufR / HfR; vR = HvfR / HfR; }
+        unR = uR * nx + vR * ny;
+        double zs = fmax(zL, zR);
+        HsL = fmax(0.0, (HfL + zL) - zs);
+        HsR = fmax(0.0, (HfR + zR) - zs);
+    }
+    if (HsL == 0.0 && HsR == 0.0) return 0.0;
+    double cL = sqrt(g * HsL), cR = sqrt(g * HsR), sL, sR;
+    if (HsL == 0.0) {
+        sL = unR - 2.0 * cR;
+        sR = unR + cR;
+    } else if (HsR == 0.0) {
+        sL = unL - cL;
+        sR = unL + 2.0 * cL;
+    } else {
+        double us = 0.5 * (unL + unR) + (cL - cR);
+        double cs = 0.5 * (cL + cR) - 0.25 * (unR - unL);
+        sL = fmin(unL - cL, us - cs);
+        sR = fmax(us + cs, unR + cR);
+    }
+    return fmax(fabs(sL), fabs(sR));
+}
+
+// The face states of face f of cell K (and its neighbour across it) from FV.
+struct FaceIn {
+    double HfL, HufL, HvfL, zL, HfR, HufR, HvfR, zR, nx, ny, l;
+    int j, fj;
+    bool wall;
+};
+__device__ FaceIn face_in(const AdjMesh &m, const double *FV, int K, int f)
+{
+    const int nc = m.nc;
+    FaceIn r;
+    r.j = m.nbr[f * nc + K];
+    r.wall = r.j < 0;
+    r.fj = r.wall ? 0 : (m.nbrl[f * nc + K] & 3);
+    r.HfL = FV[(0 * 3 + f) * (size_t)nc + K];
+    r.HufL = FV[(1 * 3 + f) * (size_t)nc + K];
+    r.HvfL = FV[(2 * 3 + f) * (size_t)nc + K];
+    r.zL = m.z[K];
+    r.HfR = r.HufR = r.HvfR = r.zR = 0.0;
+    if (!r.wall) {
+        r.HfR = FV[(0 * 3 + r.fj) * (size_t)nc + r.j];
+        r.HufR = FV[(1 * 3 + r.fj) * (size_t)nc + r.j];
+        r.HvfR = FV[(2 * 3 + r.fj) * (size_t)nc + r.j];
+        r.zR = m.z[r.j];
+    }
+    r.nx = G(m, GEO_NX + f, K);
+    r.ny = G(m, GEO_NY + f, K);
+    r.l = G(m, GEO_LEN + f, K);
+    return r;
+}
+
+// max_f l_f a_f of cell K (forward order, a tie keeping the earlier face) and its face.
+__device__ double cell_speed(const AdjMesh &m, const double *FV, int K, int &fmax_out)
+{
+    double am = 0.0;
+    fmax_out = -1;
+    for (int f = 0; f < 3; f++) {
+        FaceIn q = face_in(m, FV, K, f);
+        double la = q.l * face_speed(m, q.HfL, q.HufL, q.HvfL, q.zL, q.HfR, q.HufR, q.HvfR, q.zR, q.nx, q.ny, q.wall);
+        if (la > am) { am = la; fmax_out = f; }
+    }
+    return am;
+}
+
+__device__ __forceinline__ bool cfl_less(double b1, int o1, double b2, int o2)
+{
+    return b1 < b2 || (b1 == b2 && o1 < o2);
+}
+
+// Per CTA: the cell of smallest bound |K| / (3 max_f l_f a_f) (ties: lowest
+// original id) -> part_b, part_o, part_k [gridDim].
+__global__ void adj_cfl_part_kernel(AdjMesh m, const double *FV, const int32_t *orig, double *part_b, int *part_o,
+                                    int *part_k)
+{
+    __shared__ double sb[256];
+    __shared__ int so[256], sk[256];
+    const int nc = m.nc, tid = threadIdx.x;
+    double bb = INFINITY;
+    int bo = 0x7fffffff, bk = -1;
+    for (int K = blockIdx.x * blockDim.x + tid; K < nc; K += gridDim.x * blockDim.x) {
+        int f;
+        double am = cell_speed(m, FV, K, f);
+        if (!(am > 0.0)) continue;
+        double b = G(m, GEO_AREA, K) / (3.0 * am);
+        if (cfl_less(b, orig[K], bb, bo)) { bb = b; bo = orig[K]; bk = K; }
+    }
+    sb[tid] = bb; so[tid] = bo; sk[tid] = bk;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (tid < s && cfl_less(sb[tid + s], so[tid + s], sb[tid], so[tid])) {
+            sb[tid] = sb[tid + s]; so[tid] = so[tid + s]; sk[tid] = sk[tid + s];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) { part_b[blockIdx.x] = sb[0]; part_o[blockIdx.x] = so[0]; part_k[blockIdx.x] = sk[0]; }
+}
+
+// dt-bar's face: one thread reduces the parts, finds the face f* of the chosen
+// cell and adds the wave-speed adjoint's contribution to both sides' face slots.
+__global__ void adj_cfl_face_kernel(AdjMesh m, const double *FV, int nparts, const double *part_b,
+                                    const int *part_o, const int *part_k, const double *dtbar, double cfl,
+                                    double dt_max, double *FVb, double *zfb)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double bb = INFINITY;
+    int bo = 0x7fffffff, K = -1;
+    for (int q = 0; q < nparts; q++)
+        if (part_k[q] >= 0 && cfl_less(part_b[q], part_o[q], bb, bo)) { bb = part_b[q]; bo = part_o[q]; K = part_k[q]; }
+    if (K < 0) return;                                   // nothing moves: dt = dt_max or 0
+    const double dtc = cfl * bb;
+    if (dt_max > 0.0 && dt_max < dtc) return;            // clamped by dt_max: no dependence
+    int f;
+    cell_speed(m, FV, K, f);
+    const FaceIn q = face_in(m, FV, K, f);
+    const double a = face_speed(m, q.HfL, q.HufL, q.HvfL, q.zL, q.HfR, q.HufR, q.HvfR, q.zR, q.nx, q.ny, q.wall);
+    const double ab = -(*dtbar) * dtc / a;
+    const double P0[3] = {0.0, 0.0, 0.0};
+    double bL[4], bR[4];
+    flux_vjp(m, q.HfL, q.HufL, q.HvfL, q.zL, q.HfR, q.HufR, q.HvfR, q.zR, q.nx, q.ny, q.wall, P0, 0.0, 0.0, bL, bR, ab);
+    const int nc = m.nc;
+    for (int v = 0; v < 3; v++) FVb[(v * 3 + f) * (size_t)nc + K] += bL[v];
+    zfb[f * (size_t)nc + K] += bL[3];
+    if (!q.wall) {
+        for (int v = 0; v < 3; v++) FVb[(v * 3 + q.fj) * (size_t)nc + q.j] += bR[v];
+        zfb[q.fj * (size_t)nc + q.j] += bR[3];
+    }
+}
+
+// Deterministic dot product: per-CTA partial sums, then one thread adds them in
+// order, times scale, into *acc (reset: replaces it).
+__global__ void adj_dot_part_kernel(int64_t n, const double *a, const double *b, double *part)
+{
+    __shared__ double sh[256];
+    const int tid = threadIdx.x;
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + tid; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += a[i] * b[i];
+    sh[tid] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (tid < k) sh[tid] += sh[tid + k];
+        __syncthreads();
+    }
+    if (tid == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void adj_dot_final_kernel(int nparts, const double *part, double scale, double *acc, int reset)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int q = 0; q < nparts; q++) s += part[q];
+    *acc = reset ? s * scale : *acc + s * scale;
+}
+
 int grid_of(int n) { return (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096; }
 
 AdjMesh adj_mesh(const DevPtrs &d, const StepParams &p)
@@ -580,13 +767,18 @@ AdjMesh adj_mesh(const DevPtrs &d, const StepParams &p)
 // Scratch: FV, FVb [9][nc], zfb [3][nc], own [4][nc], send [12][nc].
 int adjoint_residual_vjp(const DevPtrs &d, const StepParams &p, const double *w, const double *Rb, double *wb,
                          double *zb, double *FV, bool fv_given, double *FVb, double *zfb, double *own, double *send,
-                         void *stream)
+                         void *stream, const AdjCfl *cfl)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     AdjMesh m = adj_mesh(d, p);
     int grid = grid_of(m.nc);
     if (!fv_given) adj_face_values_kernel<<<grid, 256, 0, s>>>(m, w, Rb, FV);
     adj_flux_vjp_kernel<<<grid, 256, 0, s>>>(m, FV, Rb, FVb, zfb);
+    if (cfl) {
+        adj_cfl_part_kernel<<<kAdjCflParts, 256, 0, s>>>(m, FV, cfl->orig, cfl->part_b, cfl->part_o, cfl->part_k);
+        adj_cfl_face_kernel<<<1, 32, 0, s>>>(m, FV, kAdjCflParts, cfl->part_b, cfl->part_o, cfl->part_k, cfl->dtbar,
+                                             cfl->cfl, cfl->dt_max, FVb, zfb);
+    }
     adj_recon_vjp_kernel<<<grid, 256, 0, s>>>(m, w, FVb, zfb, own, send);
     adj_gather_kernel<<<grid, 256, 0, s>>>(m, own, send, wb, zb);
     return (int)cudaGetLastError();
@@ -612,6 +804,15 @@ int adjoint_stage1_rev(int nc, double dt, double hthr, const double *H1pre, cons
 {
     adj_stage1_rev_kernel<<<grid_of(nc), 256, 0, static_cast<cudaStream_t>(stream)>>>(nc, dt, hthr, H1pre, wb1, wbn,
                                                                                        Rb);
+    return (int)cudaGetLastError();
+}
+
+int adjoint_dot(int64_t n, const double *a, const double *b, double scale, double *acc, bool reset, double *part,
+                void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    adj_dot_part_kernel<<<kAdjCflParts, 256, 0, s>>>(n, a, b, part);
+    adj_dot_final_kernel<<<1, 32, 0, s>>>(kAdjCflParts, part, scale, acc, reset ? 1 : 0);
     return (int)cudaGetLastError();
 }
 

@@ -70,7 +70,9 @@ struct vg_ctx {
     // discrete adjoint: checkpoints of the last vg_adj_forward run
     std::vector<void *> ckpt;
     int64_t adj_n = 0, adj_every = 0;
-    double adj_dt = 0.0;
+    double adj_dt = 0.0;                // > 0 fixed step; 0: the CFL steps below
+    double adj_cfl = 0.0, adj_dt_max = 0.0;
+    std::vector<double> adj_dts;        // each step's dt (the CFL steps of the forward run)
     bool profile = false;
     double prof_ms[kKernels] = {0, 0, 0, 0};
     int64_t prof_n[kKernels] = {0, 0, 0, 0};
@@ -1062,7 +1064,7 @@ int vg_set_bed_motion(vg_ctx *c, const double *uplift_v, const double *onset_v, 
 
 int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_every)
 {
-    if (!c || n_steps < 1 || !(dt > 0) || checkpoint_every < 0) return VG_EINVAL;
+    if (!c || n_steps < 1 || !(dt >= 0) || !std::isfinite(dt) || checkpoint_every < 0) return VG_EINVAL;
     if (c->precision != 64) return fail(c, VG_EINVAL, "the adjoint runs in FP64 contexts");
     if (!c->has_mesh || !c->has_state) return fail(c, VG_ESTATE, "mesh and state must be set");
     if (c->n_gauges < 1) return fail(c, VG_ESTATE, "the adjoint differentiates gauge records: set gauges first");
@@ -1079,8 +1081,10 @@ int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_eve
         if (rc) { free_adjoint(c); return rc; }
         c->ckpt.push_back(p);
     }
+    double *dts_dev = nullptr;
+    if (dmalloc(c, (void **)&dts_dev, 8 * (size_t)n_steps)) { free_adjoint(c); return VG_ENOMEM; }
     vg_params saved = c->prm;
-    c->prm.dt_fixed = dt;
+    c->prm.dt_fixed = dt;               // 0: the CFL rule of every step
     c->prm.t_end = 0.0;
     c->prm.gauge_every = 1;
     c->graph_dirty = true;
@@ -1097,6 +1101,10 @@ int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_eve
             if (e != cudaSuccess) { rc = cuda_fail(c, e, "checkpoint copy"); break; }
         }
         if ((rc = enqueue_step(c, c->cur))) break;
+        {
+            cudaError_t e = cudaMemcpyAsync(dts_dev + n, &c->sc->dt, 8, cudaMemcpyDeviceToDevice, c->stream);
+            if (e != cudaSuccess) { rc = cuda_fail(c, e, "time-step record"); break; }
+        }
         c->cur = 1 - c->cur;
         c->launches += step_kernels(c);
         if ((n + 1) % 1024 == 0) {
@@ -1107,12 +1115,20 @@ int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_eve
     if (!rc) rc = read_scalars(c, s);
     if (!rc) rc = drain_gauges(c, s);
     if (!rc) rc = check_flags(c, s, 0);
+    c->adj_dts.assign(n_steps, dt);
+    if (!rc) {
+        cudaError_t e = cudaMemcpy(c->adj_dts.data(), dts_dev, 8 * (size_t)n_steps, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_fail(c, e, "time-step read-back");
+    }
+    dfree(dts_dev);
     c->prm = saved;
     c->graph_dirty = true;
     if (rc) { free_adjoint(c); return rc; }
     c->adj_n = n_steps;
     c->adj_every = C;
     c->adj_dt = dt;
+    c->adj_cfl = saved.cfl;
+    c->adj_dt_max = saved.dt_max;
     return VG_OK;
 }
 
@@ -1137,15 +1153,31 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
     // dry-fix branches (all recorded by one forward recompute of the segment)
     double *W, *wb, *wbn, *wb1, *zb, *Rb, *w1, *H1pre, *FVb, *zfb, *own, *send, *seg, *R0seg, *wlast, *m2raw;
     double *FVseg;   // face values of both stages of every step of the segment [C][2][9][nc]
+    const bool adaptive = !(c->adj_dt > 0.0);
+    double *R1seg = nullptr, *cflscr = nullptr;   // adaptive steps: stage-2 residuals; dt-bar and reduction scratch
     int rc = 0;
     if ((rc = alloc((size_t)(N + 1) * G, &W)) || (rc = alloc(w3, &wb)) || (rc = alloc(w3, &wbn)) ||
         (rc = alloc(w3, &wb1)) || (rc = alloc(nc, &zb)) || (rc = alloc(w3, &Rb)) || (rc = alloc(w3, &wlast)) ||
         (rc = alloc(w3, &w1)) || (rc = alloc(nc, &H1pre)) || (rc = alloc(18 * (size_t)nc * C, &FVseg)) ||
         (rc = alloc(9 * (size_t)nc, &FVb)) || (rc = alloc(3 * (size_t)nc, &zfb)) || (rc = alloc(4 * (size_t)nc, &own)) ||
         (rc = alloc(12 * (size_t)nc, &send)) || (rc = alloc(w3 * (size_t)C, &seg)) ||
-        (rc = alloc(w3 * (size_t)C, &R0seg)) || (rc = alloc(((size_t)nc * C + 7) / 8, &m2raw))) {
+        (rc = alloc(w3 * (size_t)C, &R0seg)) || (rc = alloc(((size_t)nc * C + 7) / 8, &m2raw)) ||
+        (adaptive && ((rc = alloc(w3 * (size_t)C, &R1seg)) || (rc = alloc(8 + 3 * (size_t)kAdjCflParts, &cflscr))))) {
         for (void *q : bufs) cudaFree(q);
         return rc;
+    }
+    AdjCfl cfl{};
+    double *dtbar = nullptr, *dotpart = nullptr;
+    if (adaptive) {
+        dtbar = cflscr;
+        dotpart = cflscr + 8;
+        cfl.orig = c->old_of_new;
+        cfl.dtbar = dtbar;
+        cfl.cfl = c->adj_cfl;
+        cfl.dt_max = c->adj_dt_max;
+        cfl.part_b = cflscr + 8 + kAdjCflParts;
+        cfl.part_o = reinterpret_cast<int *>(cfl.part_b + kAdjCflParts);
+        cfl.part_k = cfl.part_o + kAdjCflParts;
     }
     uint8_t *m2seg = reinterpret_cast<uint8_t *>(m2raw);
     DevScalars *asc = nullptr;
@@ -1160,7 +1192,7 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
     p.dt_fixed = c->adj_dt;
     p.t_end = 0.0;
     p.dt_max = 0.0;
-    const double dt = c->adj_dt, hthr = p.hthr;
+    const double hthr = p.hthr;
     void *st = (void *)c->stream;
     DevPtrs d = dev_ptrs(c);
     d.sc = asc;
@@ -1185,22 +1217,33 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
                 dd.R0 = R0seg + (size_t)(n - a) * w3;
                 dd.mask2 = m2seg + (size_t)(n - a) * nc;
                 dd.fv_out = FVseg + (size_t)(n - a) * 18 * nc;
-                ADJ_CHECK(launch_stage1_f64(dd, p, win, c->cfg1, st));
+                StepParams pn = p;
+                pn.dt_fixed = c->adj_dts[n];        // the step the forward run took
+                ADJ_CHECK(launch_stage1_f64(dd, pn, win, c->cfg1, st));
                 dd.fv_out = FVseg + ((size_t)(n - a) * 18 + 9) * nc;
-                ADJ_CHECK(launch_stage2_f64(dd, p, win, wout, c->cfg2, st));
+                if (adaptive) dd.r1_out = R1seg + (size_t)(n - a) * w3;
+                ADJ_CHECK(launch_stage2_f64(dd, pn, win, wout, c->cfg2, st));
             }
             for (int64_t n = b - 1; n >= a; n--) {
+                const double dtn = c->adj_dts[n];
                 const double *w = seg + (size_t)(n - a) * w3;
                 const double *R0 = R0seg + (size_t)(n - a) * w3;
-                ADJ_CHECK(adjoint_stage1(nc, dt, hthr, w, R0, w1, H1pre, st));
-                ADJ_CHECK(adjoint_stage2_rev(nc, dt, m2seg + (size_t)(n - a) * nc, wb, wbn, wb1, Rb, st));
+                ADJ_CHECK(adjoint_stage1(nc, dtn, hthr, w, R0, w1, H1pre, st));
+                ADJ_CHECK(adjoint_stage2_rev(nc, dtn, m2seg + (size_t)(n - a) * nc, wb, wbn, wb1, Rb, st));
+                // dt-bar, stage 2: sum w-bar_pre . R1 / 2 = sum Rb . R1 / dt
+                if (adaptive)
+                    ADJ_CHECK(adjoint_dot((int64_t)w3, Rb, R1seg + (size_t)(n - a) * w3, 1.0 / dtn, dtbar, true,
+                                          dotpart, st));
                 double *FV0 = FVseg + (size_t)(n - a) * 18 * nc, *FV1 = FV0 + 9 * (size_t)nc;
                 ADJ_CHECK(adjoint_residual_vjp(d, p, w1, Rb, wb1, zb, FV1, true, FVb, zfb, own, send, st));
-                ADJ_CHECK(adjoint_stage1_rev(nc, dt, hthr, H1pre, wb1, wbn, Rb, st));
-                ADJ_CHECK(adjoint_residual_vjp(d, p, w, Rb, wbn, zb, FV0, true, FVb, zfb, own, send, st));
+                ADJ_CHECK(adjoint_stage1_rev(nc, dtn, hthr, H1pre, wb1, wbn, Rb, st));
+                // dt-bar, stage 1: sum w1-bar_pre . R0 = sum Rb . R0 / dt
+                if (adaptive) ADJ_CHECK(adjoint_dot((int64_t)w3, Rb, R0, 1.0 / dtn, dtbar, false, dotpart, st));
+                ADJ_CHECK(adjoint_residual_vjp(d, p, w, Rb, wbn, zb, FV0, true, FVb, zfb, own, send, st,
+                                               adaptive ? &cfl : nullptr));
                 ADJ_CHECK(adjoint_gauge(G, c->gauge_cells, W + (size_t)n * G, nc, wbn, zb, st));
                 std::swap(wb, wbn);
-                c->launches += 11;
+                c->launches += adaptive ? 17 : 11;
             }
         }
         // internal -> original order on the host

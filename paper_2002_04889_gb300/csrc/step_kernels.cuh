@@ -61,6 +61,7 @@ struct KArgs {
     real *wout;             // w^{n+1} [3][nc] (stage 2)
     uint8_t *mask2;         // optional: stage-2 dry-fix branch (0 none, 1 momentum cut, 2 emptied)
     real *fv_out;           // optional [3 vars][3 faces][nc]: face values of the block cells
+    real *r1_out;           // optional [3][nc]: the stage-2 residual L(w1) (stage 2)
     DevScalars *sc;
     real g, half_g, hthr;
     double cfl, dt_fixed, dt_max, t_end;
@@ -671,6 +672,11 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             a.R0[2 * nc + gid] = RHv;
             if (am > real(0)) my_min = vmin(my_min, area / (real(3) * am));
         } else {
+            if (a.r1_out) {
+                a.r1_out[gid] = RH;
+                a.r1_out[nc + gid] = RHu;
+                a.r1_out[2 * nc + gid] = RHv;
+            }
             real W1, Hu1, Hv1, z1;
             ld4(sW + 4 * l, W1, Hu1, Hv1, z1);
             real W = real(0.5) * x[0] + real(0.5) * (W1 + dt * RH);
@@ -913,6 +919,7 @@ KArgs<real> make_args(const DevPtrs &d, const StepParams &p, const void *w_in, v
     a.wout = static_cast<real *>(w_out);
     a.mask2 = d.mask2;
     a.fv_out = static_cast<real *>(d.fv_out);
+    a.r1_out = static_cast<real *>(d.r1_out);
     a.sc = d.sc;
     a.g = (real)p.g;
     a.half_g = (real)(0.5 * p.g);

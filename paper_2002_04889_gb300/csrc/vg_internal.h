@@ -102,6 +102,7 @@ struct DevPtrs {
     void *R0;               // [3][nc] stage-1 residual (scratch)
     uint8_t *mask2;         // optional [nc]: stage-2 dry-fix branch per cell (adjoint)
     void *fv_out;           // optional [9][nc]: face values written by the stage kernels (adjoint)
+    void *r1_out;           // optional [3][nc]: stage-2 residual written by the stage-2 kernel (adjoint)
     DevScalars *sc;
     const int32_t *gauge_cells;   // internal ids
     double *ring_t;               // [ring_cap]
@@ -146,11 +147,27 @@ int launch_batch_step_f64(const void *table, int n_mesh, int n_items, int n_entr
                           int grid, size_t smem, const StepParams &p, bool gauges, void *stream);
 
 // Discrete adjoint (adjoint_f64.cu, FP64 contexts).
+// The CFL time step's dependence on the state (adaptive steps): orig = original
+// cell ids [nc] (argmin ties), *dtbar = the step's dt adjoint, cfl / dt_max as in
+// the forward run, part_* scratch of kAdjCflParts entries.
+constexpr int kAdjCflParts = 1024;
+struct AdjCfl {
+    const int32_t *orig;
+    const double *dtbar;
+    double cfl, dt_max;
+    double *part_b;
+    int *part_o, *part_k;
+};
 // FV: the face values at w, precomputed by the forward stage kernel (fv_out)
-// or, if fv_given is false, computed here into FV.
+// or, if fv_given is false, computed here into FV.  cfl (may be NULL): also
+// the adjoint of the stage-1 CFL time step through the wave speed of the face
+// that set it.
 int adjoint_residual_vjp(const DevPtrs &d, const StepParams &p, const double *w, const double *Rb, double *wb,
                          double *zb, double *FV, bool fv_given, double *FVb, double *zfb, double *own, double *send,
-                         void *stream);
+                         void *stream, const AdjCfl *cfl = nullptr);
+// *acc (= or +=) scale * sum_i a[i] b[i], deterministic; part: kAdjCflParts doubles.
+int adjoint_dot(int64_t n, const double *a, const double *b, double scale, double *acc, bool reset, double *part,
+                void *stream);
 int adjoint_stage1(int nc, double dt, double hthr, const double *w, const double *R0, double *w1, double *H1pre,
                    void *stream);
 int adjoint_stage2_rev(int nc, double dt, const uint8_t *mask2, const double *wb, double *wbn, double *wb1,

@@ -441,8 +441,9 @@ class Solver:
         up, on = _f64(uplift_v), _f64(onset_v)
         _check(self.ctx, load().vg_set_bed_motion(self.ctx, _dp(up), _dp(on), float(rise)))
 
-    def adj_forward(self, n_steps: int, dt: float, checkpoint_every: int = 0):
-        """Fixed-dt run keeping checkpoints; returns the gauge records (t, eta)."""
+    def adj_forward(self, n_steps: int, dt: float = 0.0, checkpoint_every: int = 0):
+        """Run keeping checkpoints, with the fixed step dt or (dt = 0) the CFL
+        step of every step; returns the gauge records (t, eta)."""
         vg_adj_forward(self.ctx, n_steps, dt, checkpoint_every)
         return self.gauges()
 
