@@ -252,17 +252,22 @@ def _load_ad():
                                          C.c_double, C.c_int, C.c_double, C.c_double, C.c_int64, C.c_int32,
                                          _I32, _D, _D, _D, _D, _D, _D, _D, _D]
     lib.vo_ad_gauge_gradient.restype = C.c_int
+    lib.vo_ad_gauge_gradient_bed.argtypes = [C.c_int64, _D, C.c_int64, _I32, _D, _D, _D, _D, C.c_double,
+                                             C.c_double, C.c_int, C.c_double, C.c_double, C.c_int64, C.c_int32,
+                                             _I32, _D, _D, _D, C.c_double, _D, _D, _D, _D, _D, _D, _D, _D, _D]
+    lib.vo_ad_gauge_gradient_bed.restype = C.c_int
     _ad = lib
     return lib
 
 
 def ad_gauge_gradient(mesh, state, dt, n_steps, gauge_cells, weights, g=9.81, h_threshold=1e-5,
-                      order=2, cfl=0.9):
+                      order=2, cfl=0.9, bed_motion=None):
     """The oracle's discrete adjoint (tape AD of the oracle's own arithmetic) of
     J = sum_{n,g} weights[n, g] * eta_g(t_n), n = 0..n_steps (Sec. 2.3 steps), with
     the fixed time step dt, or for dt = 0 / None the CFL step of each step,
-    differentiated through its minimum.
-    Returns dict(J, eta[n+1, G], dts[n], dH0, dHu0, dHv0, ddepth)."""
+    differentiated through its minimum.  bed_motion = (uplift_v, onset_v, rise):
+    the moving bed of vo_bed_at over the mesh's depths, also differentiated.
+    Returns dict(J, eta[n+1, G], dts[n], dH0, dHu0, dHv0, ddepth[, duplift, donset])."""
     xy = _f64(mesh.xy).reshape(-1, 2)
     tri = np.ascontiguousarray(mesh.tri, dtype=np.int32)
     depth = _f64(mesh.depth)
@@ -274,13 +279,26 @@ def ad_gauge_gradient(mesh, state, dt, n_steps, gauge_cells, weights, g=9.81, h_
     dts = np.zeros(max(int(n_steps), 1))
     J = C.c_double()
     out = [np.zeros(nc) for _ in range(3)] + [np.zeros(nv)]
-    rc = _load_ad().vo_ad_gauge_gradient(nv, _dp(xy), nc, tri.ctypes.data_as(_I32), _dp(depth),
-                                         _dp(H0), _dp(Hu0), _dp(Hv0), g, h_threshold, order, float(cfl),
-                                         float(dt or 0.0), int(n_steps), gc.shape[0], gc.ctypes.data_as(_I32),
-                                         _dp(w), _dp(eta), _dp(dts), C.byref(J), *(_dp(o) for o in out))
+    if bed_motion is None:
+        rc = _load_ad().vo_ad_gauge_gradient(nv, _dp(xy), nc, tri.ctypes.data_as(_I32), _dp(depth),
+                                             _dp(H0), _dp(Hu0), _dp(Hv0), g, h_threshold, order, float(cfl),
+                                             float(dt or 0.0), int(n_steps), gc.shape[0], gc.ctypes.data_as(_I32),
+                                             _dp(w), _dp(eta), _dp(dts), C.byref(J), *(_dp(o) for o in out))
+    else:
+        up, on = _f64(bed_motion[0]), _f64(bed_motion[1])
+        out += [np.zeros(nv), np.zeros(nv)]
+        rc = _load_ad().vo_ad_gauge_gradient_bed(nv, _dp(xy), nc, tri.ctypes.data_as(_I32), _dp(depth),
+                                                 _dp(H0), _dp(Hu0), _dp(Hv0), g, h_threshold, order, float(cfl),
+                                                 float(dt or 0.0), int(n_steps), gc.shape[0],
+                                                 gc.ctypes.data_as(_I32), _dp(w), _dp(up), _dp(on),
+                                                 float(bed_motion[2]), _dp(eta), _dp(dts), C.byref(J),
+                                                 *(_dp(o) for o in out))
     if rc != 0:
         raise ValueError(f"oracle mesh rejected (code {rc})")
-    return dict(J=J.value, eta=eta, dts=dts[:n_steps], dH0=out[0], dHu0=out[1], dHv0=out[2], ddepth=out[3])
+    r = dict(J=J.value, eta=eta, dts=dts[:n_steps], dH0=out[0], dHu0=out[1], dHv0=out[2], ddepth=out[3])
+    if bed_motion is not None:
+        r["duplift"], r["donset"] = out[4], out[5]
+    return r
 
 
 _count = None

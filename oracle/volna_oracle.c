@@ -607,17 +607,18 @@ static int64_t dry_fix(int64_t nc, double hthr, vo_real *H, vo_real *Hu, vo_real
 /*
  * One SSP-RK(2,2) step (Sec. 2.3), in place on (H, Hu, Hv):
  *   w1 = w + dt L(w);  w <- 1/2 w + 1/2 (w1 + dt L(w1)),
- * the same dt in both stages, each stage followed by the dry fix.
- * *t advances by dt; *dt_out and *neg_count (added to) report the step.
+ * the same dt in both stages, each stage followed by the dry fix.  t is the
+ * time at the start; returns dt (the state-dependent scalar); *neg_count is
+ * added to.
  */
-void vo_step(vo_mesh *m, const vo_params *p, vo_real *H, vo_real *Hu, vo_real *Hv,
-             double *t, double *dt_out, int64_t *neg_count)
+vo_real vo_step_dt(vo_mesh *m, const vo_params *p, vo_real *H, vo_real *Hu, vo_real *Hv, double t,
+                   int64_t *neg_count)
 {
     int64_t nc = m->nc;
     vo_real *R0 = m->R0, *R1 = m->R1, *W1 = m->W1;
     vo_real *H1 = W1, *Hu1 = W1 + nc, *Hv1 = W1 + 2 * nc;
     vo_residual(m, p, H, Hu, Hv, R0, R0 + nc, R0 + 2 * nc, m->amax);
-    vo_real dt = vo_time_step(m, p, m->amax, *t);
+    vo_real dt = vo_time_step(m, p, m->amax, t);
 #pragma omp parallel for schedule(static)
     for (int64_t K = 0; K < nc; K++) {
         H1[K] = H[K] + dt * R0[K];
@@ -633,9 +634,17 @@ void vo_step(vo_mesh *m, const vo_params *p, vo_real *H, vo_real *Hu, vo_real *H
         Hv[K] = 0.5 * Hv[K] + 0.5 * (Hv1[K] + dt * R1[2 * nc + K]);
     }
     neg += dry_fix(nc, p->h_threshold, H, Hu, Hv);
+    if (neg_count) *neg_count += neg;
+    return dt;
+}
+
+/* vo_step_dt with the time advanced in place: *t += dt, *dt_out = dt. */
+void vo_step(vo_mesh *m, const vo_params *p, vo_real *H, vo_real *Hu, vo_real *Hv,
+             double *t, double *dt_out, int64_t *neg_count)
+{
+    vo_real dt = vo_step_dt(m, p, H, Hu, Hv, *t, neg_count);
     *t += vo_val(dt);
     if (dt_out) *dt_out = vo_val(dt);
-    if (neg_count) *neg_count += neg;
 }
 
 /* n steps; dts (may be NULL) receives each step's dt.  Gauges (may be NULL):
@@ -669,18 +678,21 @@ int64_t vo_run(vo_mesh *m, const vo_params *p, vo_real *H, vo_real *Hu, vo_real 
  * are set to z(t^{n+1}) with H unchanged, so the free surface eta = H + z
  * follows the bed and no mass is created.
  */
-static double ramp(double t, double onset, double rise)
+static vo_real ramp(vo_real t, vo_real onset, double rise)
 {
-    if (rise > 0.0) return fmin(1.0, fmax(0.0, (t - onset) / rise));
-    return t >= onset ? 1.0 : 0.0;
+    if (rise > 0.0) return fmin((vo_real)1.0, fmax((vo_real)0.0, (t - onset) / rise));
+    return vo_val(t) >= vo_val(onset) ? 1.0 : 0.0;
 }
 
-void vo_bed_at(vo_mesh *m, const double *depth0, const double *uplift, const double *onset, double rise,
-               double t)
+/* The source arrays and the time have the state-dependent scalar type, so
+   that the taped build differentiates the run with respect to them (with
+   adaptive steps the time itself depends on the state). */
+void vo_bed_at(vo_mesh *m, const vo_real *depth0, const vo_real *uplift, const vo_real *onset, double rise,
+               vo_real t)
 {
 #pragma omp parallel for schedule(static)
     for (int64_t K = 0; K < m->nc; K++) {
-        double d[3];
+        vo_real d[3];
         for (int k = 0; k < 3; k++) {
             int32_t v = m->vtx[3 * K + k];
             d[k] = depth0[v] - uplift[v] * ramp(t, onset[v], rise);
@@ -694,7 +706,7 @@ void vo_bed_at(vo_mesh *m, const double *depth0, const double *uplift, const dou
 int64_t vo_run_bed(vo_mesh *m, const vo_params *p, vo_real *H, vo_real *Hu, vo_real *Hv,
                    double *t, int64_t n_steps, double *dts, int64_t *neg_count,
                    int32_t n_gauges, const int32_t *gauge_cells, vo_real *gauge_eta,
-                   const double *depth0, const double *uplift, const double *onset, double rise)
+                   const vo_real *depth0, const vo_real *uplift, const vo_real *onset, double rise)
 {
     vo_bed_at(m, depth0, uplift, onset, rise, *t);
     for (int64_t s = 0; s < n_steps; s++) {

@@ -93,4 +93,71 @@ int vo_ad_gauge_gradient(int64_t nv, const double *xy, int64_t nc, const int32_t
     return 0;
 }
 
+/*
+ * The same functional with a moving bed (vo_bed_at: depth_v(t) = depth_v -
+ * uplift_v R((t - onset_v) / rise), applied at the start and after every step)
+ * and its gradient, adding dJ/duplift_v and dJ/donset_v [nv] to the outputs of
+ * vo_ad_gauge_gradient.
+ */
+int vo_ad_gauge_gradient_bed(int64_t nv, const double *xy, int64_t nc, const int32_t *tri, const double *depth_v,
+                             const double *H0, const double *Hu0, const double *Hv0, double g, double hthr,
+                             int order, double cfl, double dt, int64_t n_steps, int32_t n_gauges,
+                             const int32_t *gauge_cells, const double *weights, const double *uplift_v,
+                             const double *onset_v, double rise, double *eta_out, double *dts_out, double *J_out,
+                             double *gH0, double *gHu0, double *gHv0, double *gdepth, double *guplift,
+                             double *gonset)
+{
+    VoTape &tape = vo_tape();
+    tape.clear();
+    std::vector<adouble> depth(nv), H(nc), Hu(nc), Hv(nc), up(nv), on(nv);
+    for (int64_t v = 0; v < nv; v++) depth[v] = adouble::variable(depth_v[v]);
+    for (int64_t k = 0; k < nc; k++) H[k] = adouble::variable(H0[k]);
+    for (int64_t k = 0; k < nc; k++) Hu[k] = adouble::variable(Hu0[k]);
+    for (int64_t k = 0; k < nc; k++) Hv[k] = adouble::variable(Hv0[k]);
+    for (int64_t v = 0; v < nv; v++) up[v] = adouble::variable(uplift_v[v]);
+    for (int64_t v = 0; v < nv; v++) on[v] = adouble::variable(onset_v[v]);
+    vo_mesh *m = nullptr;
+    int rc = vo_ad_impl::vo_mesh_build(nv, xy, nc, tri, depth.data(), &m);
+    if (rc) return rc;
+    vo_params p;
+    vo_ad_impl::vo_default_params(&p);
+    p.g = g;
+    p.h_threshold = hthr;
+    p.order = order;
+    p.cfl = cfl;
+    p.dt_fixed = dt > 0.0 ? dt : 0.0;
+    adouble J = 0.0;
+    adouble t = 0.0;       // with adaptive steps the time, and so the bed, depend on the state
+    int64_t neg = 0;
+    vo_ad_impl::vo_bed_at(m, depth.data(), up.data(), on.data(), rise, t);
+    for (int64_t n = 0; n <= n_steps; n++) {
+        if (n > 0) {
+            adouble dtn = vo_ad_impl::vo_step_dt(m, &p, H.data(), Hu.data(), Hv.data(), t.v, &neg);
+            t = t + dtn;
+            vo_ad_impl::vo_bed_at(m, depth.data(), up.data(), on.data(), rise, t);
+            if (dts_out) dts_out[n - 1] = dtn.v;
+        }
+        for (int32_t k = 0; k < n_gauges; k++) {
+            int32_t c = gauge_cells[k];
+            adouble eta = H[c] + m->z[c];
+            if (eta_out) eta_out[n * n_gauges + k] = eta.v;
+            J = J + weights[n * n_gauges + k] * eta;
+        }
+    }
+    *J_out = J.v;
+    std::vector<double> adj(tape.size(), 0.0);
+    if (J.i >= 0) adj[J.i] = 1.0;
+    tape.reverse(adj);
+    for (int64_t v = 0; v < nv; v++) gdepth[v] = adj[v];
+    for (int64_t k = 0; k < nc; k++) gH0[k] = adj[nv + k];
+    for (int64_t k = 0; k < nc; k++) gHu0[k] = adj[nv + nc + k];
+    for (int64_t k = 0; k < nc; k++) gHv0[k] = adj[nv + 2 * nc + k];
+    for (int64_t v = 0; v < nv; v++) guplift[v] = adj[nv + 3 * nc + v];
+    for (int64_t v = 0; v < nv; v++) gonset[v] = adj[2 * nv + 3 * nc + v];
+    vo_ad_impl::vo_mesh_free(m);
+    tape.clear();
+    tape.a0.shrink_to_fit(); tape.a1.shrink_to_fit(); tape.d0.shrink_to_fit(); tape.d1.shrink_to_fit();
+    return 0;
+}
+
 }  // extern "C"

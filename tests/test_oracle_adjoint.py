@@ -126,3 +126,52 @@ def test_oracle_adjoint_through_the_cfl_time_step():
                 fwd, bwd = (jp - J0) / eps, (J0 - jm) / eps
                 assert min(fwd, bwd) - 2e-6 <= gd <= max(fwd, bwd) + 2e-6, (kind, gd, fwd, bwd)
     assert n_ok >= 9
+
+
+def _J_bed(m, state, cells, n_steps, w, motion, depth=None):
+    om = O.OracleMesh(m.xy, m.tri, m.depth if depth is None else depth)
+    up, on, rise = motion
+    d0 = m.depth if depth is None else depth
+    z0 = om.bed_at(d0, up, on, rise, 0.0)
+    eta0 = state[0][cells] + z0[cells]
+    r = om.run(O.params(cfl=0.9), (state[0], state[1], state[2], 0.0), n_steps, gauge_cells=cells,
+               bed_motion=(d0, up, on, rise))
+    return float(np.sum(w[0] * eta0) + np.sum(w[1:] * r["gauges"]))
+
+
+def test_oracle_adjoint_with_a_moving_bed():
+    """Moving bed (a Gaussian uplift spreading from a point, rising over 0.05 s)
+    under adaptive steps: the taped gradients with respect to the uplift and the
+    onset times (the rupture history) match central differences."""
+    m, st, cells, _, n_steps, w = _setup()
+    up, on = I.radial_rupture(m.xy, 0.01, 0.1, -0.05, 0.4, 2.0, 0.0)
+    motion = (up, on, 0.05)
+    ad = O.ad_gauge_gradient(m, st, None, n_steps, cells, w, h_threshold=1e-5, cfl=0.9, bed_motion=motion)
+    J0 = _J_bed(m, st, cells, n_steps, w, motion)
+    assert ad["J"] == pytest.approx(J0, rel=1e-13, abs=1e-15)
+    rng = np.random.default_rng(13)
+    eps = 1e-8
+    n_ok = 0
+    for kind in ("uplift", "onset", "depth"):
+        for _ in range(4):
+            d = rng.normal(size=m.nv)
+            if kind == "uplift":
+                d = d * (up > 1e-4)
+                gd = float(np.dot(ad["duplift"], d))
+                f = lambda e, d=d: _J_bed(m, st, cells, n_steps, w, (up + e * d, on, 0.05))
+            elif kind == "onset":
+                d = d * 0.01
+                gd = float(np.dot(ad["donset"], d))
+                f = lambda e, d=d: _J_bed(m, st, cells, n_steps, w, (up, on + e * d, 0.05))
+            else:
+                gd = float(np.dot(ad["ddepth"], d))
+                f = lambda e, d=d: _J_bed(m, st, cells, n_steps, w, motion, depth=m.depth + e * d)
+            jp, jm = f(eps), f(-eps)
+            fd = (jp - jm) / (2 * eps)
+            if abs(gd - fd) <= 2e-6 * max(1.0, abs(fd)):
+                n_ok += 1
+            else:
+                fwd, bwd = (jp - J0) / eps, (J0 - jm) / eps
+                assert min(fwd, bwd) - 2e-6 <= gd <= max(fwd, bwd) + 2e-6, (kind, gd, fwd, bwd)
+    assert n_ok >= 9
+    assert np.max(np.abs(ad["donset"])) > 0 and np.max(np.abs(ad["duplift"])) > 0
