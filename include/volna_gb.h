@@ -278,6 +278,16 @@ int vg_adj_forward(vg_ctx *ctx, int64_t n_steps, double dt, int64_t checkpoint_e
 int vg_adj_backward(vg_ctx *ctx, const double *dJ_deta, double *dJ_dH0, double *dJ_dHu0, double *dJ_dHv0,
                     double *dJ_dz, double *dJ_ddepth);
 
+/* After vg_adj_backward of a run with a moving bed (vg_set_bed_motion set
+   during vg_adj_forward): dJ/duplift_v and dJ/donset_v [nv] (host, either may
+   be NULL) -- the gradient with respect to the rupture history.  The bed of
+   step n is the vertex-mean bed at its start time t_n; onset times act where a
+   vertex is inside its rise (0 < (t_n - onset_v) / rise < 1), and with the CFL
+   time step the dependence of every later t_n on each step's dt is included.
+   No such run: VG_ESTATE.  The paper has no counterpart (its source model is
+   not given). */
+int vg_adj_bed_gradient(vg_ctx *ctx, double *dJ_duplift, double *dJ_donset);
+
 /* Open (transmissive) boundary.  The paper's solver has walls (Sec. 2.5: a
  * ghost with mirrored normal velocity) and leaves other boundary conditions to
  * Dutykh et al. 2011.  Marks the n boundary edges edges[k] = (a, b) (original
@@ -303,8 +313,10 @@ int vg_set_open_boundary(vg_ctx *ctx, int64_t n, const int32_t *edges);
  * state's time.  uplift_v = NULL removes the motion and restores the static
  * bed (keeping H).  Host arrays, caller-owned, copied; non-finite values or a
  * negative rise: VG_EINVAL.  One extra launch per step while set.  Not applied
- * by vg_step_noalloc; the adjoint calls fail with VG_ESTATE while it is set,
- * and so does vg_set_depth. */
+ * by vg_step_noalloc; vg_set_depth fails with VG_ESTATE while it is set.  The
+ * adjoint (vg_adj_forward / vg_adj_backward) differentiates through it, and
+ * vg_adj_bed_gradient returns the gradients with respect to uplift_v and
+ * onset_v. */
 int vg_set_bed_motion(vg_ctx *ctx, const double *uplift_v, const double *onset_v, double rise);
 
 /* ------------------------------------------------------------------------

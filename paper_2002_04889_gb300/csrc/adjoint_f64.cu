@@ -744,6 +744,58 @@ __global__ void adj_dot_final_kernel(int nparts, const double *part, double scal
     *acc = reset ? s * scale : *acc + s * scale;
 }
 
+// ---------------------------------------------------------------------------
+// Moving bed: the bed of step n is z_K(t_n) = -(1/3) sum_{v in K} (depth0_v -
+// uplift_v R((t_n - onset_v) / rise)).  With zs the adjoint of that step's bed
+// (its residuals and gauge record), per vertex s_v = sum_{K around v} zs_K in a
+// fixed order and
+//   uplift-bar_v += s_v R / 3,   onset-bar_v += -s_v uplift_v R' / 3,
+//   t-bar_n = sum_v s_v uplift_v R' / 3      (R' = dR/dt = 1 / rise inside the ramp),
+// the last summed per CTA into part (adaptive steps carry it to every earlier dt).
+// ---------------------------------------------------------------------------
+__global__ void adj_bed_vertex_kernel(int nv, const int32_t *vptr, const int32_t *vcell, const double *zs,
+                                      const double *uplift, const double *onset, double rise, double t, double *gU,
+                                      double *gOn, double *part)
+{
+    __shared__ double sh[256];
+    const int tid = threadIdx.x;
+    double tb = 0.0;
+    for (int v = blockIdx.x * blockDim.x + tid; v < nv; v += gridDim.x * blockDim.x) {
+        double sv = 0.0;
+        for (int k = vptr[v]; k < vptr[v + 1]; k++) sv += zs[vcell[k]];
+        double R, Rp = 0.0;
+        if (rise > 0.0) {
+            const double x = __dsub_rn(t, onset[v]) / rise;
+            R = fmin(1.0, fmax(0.0, x));
+            if (x > 0.0 && x < 1.0) Rp = 1.0 / rise;
+        } else {
+            R = t >= onset[v] ? 1.0 : 0.0;
+        }
+        gU[v] += sv * R / 3.0;
+        const double q = sv * uplift[v] * Rp / 3.0;
+        gOn[v] -= q;
+        tb += q;
+    }
+    sh[tid] = tb;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (tid < k) sh[tid] += sh[tid + k];
+        __syncthreads();
+    }
+    if (tid == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void adj_axpy_kernel(int64_t n, const double *x, double *y)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += x[i];
+}
+
+__global__ void adj_scalar_add_kernel(double *y, const double *x)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *y += *x;
+}
+
 int grid_of(int n) { return (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096; }
 
 AdjMesh adj_mesh(const DevPtrs &d, const StepParams &p)
@@ -813,6 +865,23 @@ int adjoint_dot(int64_t n, const double *a, const double *b, double scale, doubl
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     adj_dot_part_kernel<<<kAdjCflParts, 256, 0, s>>>(n, a, b, part);
     adj_dot_final_kernel<<<1, 32, 0, s>>>(kAdjCflParts, part, scale, acc, reset ? 1 : 0);
+    return (int)cudaGetLastError();
+}
+
+int adjoint_bed_flush(int nc, int nv, const int32_t *vptr, const int32_t *vcell, double *zs, const double *uplift,
+                      const double *onset, double rise, double t, double *gU, double *gOn, double *zb_total,
+                      double *tsum, double *part, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    adj_bed_vertex_kernel<<<kAdjCflParts, 256, 0, s>>>(nv, vptr, vcell, zs, uplift, onset, rise, t, gU, gOn, part);
+    adj_dot_final_kernel<<<1, 32, 0, s>>>(kAdjCflParts, part, 1.0, tsum, 0);
+    adj_axpy_kernel<<<grid_of(nc), 256, 0, s>>>(nc, zs, zb_total);
+    return (int)cudaGetLastError();
+}
+
+int adjoint_scalar_add(double *y, const double *x, void *stream)
+{
+    adj_scalar_add_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(y, x);
     return (int)cudaGetLastError();
 }
 

@@ -73,6 +73,9 @@ struct vg_ctx {
     double adj_dt = 0.0;                // > 0 fixed step; 0: the CFL steps below
     double adj_cfl = 0.0, adj_dt_max = 0.0;
     std::vector<double> adj_dts;        // each step's dt (the CFL steps of the forward run)
+    double adj_t0 = 0.0;                // time of the forward run's first state
+    bool adj_bed = false;               // the forward run had a moving bed
+    std::vector<double> adj_gU, adj_gOn;   // its uplift / onset gradients (last backward pass)
     bool profile = false;
     double prof_ms[kKernels] = {0, 0, 0, 0};
     int64_t prof_n[kKernels] = {0, 0, 0, 0};
@@ -1068,7 +1071,6 @@ int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_eve
     if (c->precision != 64) return fail(c, VG_EINVAL, "the adjoint runs in FP64 contexts");
     if (!c->has_mesh || !c->has_state) return fail(c, VG_ESTATE, "mesh and state must be set");
     if (c->n_gauges < 1) return fail(c, VG_ESTATE, "the adjoint differentiates gauge records: set gauges first");
-    if (c->bed_on) return fail(c, VG_ESTATE, "the adjoint does not differentiate a moving bed");
     if (c->n_open) return fail(c, VG_ESTATE, "the adjoint handles walls only, not open boundaries");
     DeviceGuard guard(c->device);
     free_adjoint(c);
@@ -1091,6 +1093,7 @@ int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_eve
     // restart the gauge record at the current state
     DevScalars s;
     int rc = read_scalars(c, s);
+    const double t0 = s.t;
     if (!rc) rc = drain_gauges(c, s);
     c->rec_t.clear();
     c->rec_eta.clear();
@@ -1129,6 +1132,10 @@ int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_eve
     c->adj_dt = dt;
     c->adj_cfl = saved.cfl;
     c->adj_dt_max = saved.dt_max;
+    c->adj_t0 = t0;
+    c->adj_bed = c->bed_on;
+    c->adj_gU.clear();
+    c->adj_gOn.clear();
     return VG_OK;
 }
 
@@ -1137,6 +1144,7 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
 {
     if (!c || !dJ_deta) return VG_EINVAL;
     if (c->adj_n < 1) return fail(c, VG_ESTATE, "call vg_adj_forward first");
+    if (c->adj_bed && !c->bed_on) return fail(c, VG_ESTATE, "the moving bed of the forward run was removed");
     DeviceGuard guard(c->device);
     const int64_t N = c->adj_n, C = c->adj_every;
     const int nc = (int)c->hm.nc, G = c->n_gauges;
@@ -1166,6 +1174,44 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
         for (void *q : bufs) cudaFree(q);
         return rc;
     }
+    // moving bed: each step's own bed adjoint, the uplift / onset gradients, the
+    // adjoint of time, and the cells around each vertex (fixed order)
+    const bool bed = c->adj_bed;
+    const int nv = (int)c->hm.nv;
+    double *zstep = nullptr, *gU = nullptr, *gOn = nullptr, *bedscr = nullptr;
+    int32_t *vptr = nullptr, *vcell = nullptr;
+    std::vector<double> tn;
+    if (bed) {
+        if ((rc = alloc(nc, &zstep)) || (rc = alloc(nv, &gU)) || (rc = alloc(nv, &gOn)) ||
+            (rc = alloc(8 + (size_t)kAdjCflParts, &bedscr))) {
+            for (void *q : bufs) cudaFree(q);
+            return rc;
+        }
+        std::vector<int32_t> hp(nv + 1, 0), hc(3 * (size_t)nc);
+        for (int k = 0; k < nc; k++)
+            for (int j = 0; j < 3; j++) hp[c->hm.vtx[3 * (size_t)c->hm.old_of_new[k] + j] + 1]++;
+        for (int v = 0; v < nv; v++) hp[v + 1] += hp[v];
+        std::vector<int32_t> fill(hp.begin(), hp.end() - 1);
+        for (int k = 0; k < nc; k++)          // internal ids in increasing order per vertex
+            for (int j = 0; j < 3; j++) hc[fill[c->hm.vtx[3 * (size_t)c->hm.old_of_new[k] + j]]++] = k;
+        double *vp = nullptr, *vc = nullptr;
+        if ((rc = alloc(((size_t)nv + 2) / 2, &vp)) || (rc = alloc((3 * (size_t)nc + 1) / 2, &vc))) {
+            for (void *q : bufs) cudaFree(q);
+            return rc;
+        }
+        vptr = reinterpret_cast<int32_t *>(vp);
+        vcell = reinterpret_cast<int32_t *>(vc);
+        VG_CUDA(c, cudaMemcpy(vptr, hp.data(), 4 * hp.size(), cudaMemcpyHostToDevice));
+        VG_CUDA(c, cudaMemcpy(vcell, hc.data(), 4 * hc.size(), cudaMemcpyHostToDevice));
+        VG_CUDA(c, cudaMemsetAsync(gU, 0, 8 * (size_t)nv, c->stream));
+        VG_CUDA(c, cudaMemsetAsync(gOn, 0, 8 * (size_t)nv, c->stream));
+        VG_CUDA(c, cudaMemsetAsync(bedscr, 0, 8, c->stream));
+        tn.resize(N + 1);
+        tn[0] = c->adj_t0;
+        for (int64_t n = 0; n < N; n++) tn[n + 1] = tn[n] + c->adj_dts[n];   // as the forward's epilogue
+    }
+    double *tsum = bed ? bedscr : nullptr, *bedpart = bed ? bedscr + 8 : nullptr;
+    double *zacc;                          // where the bed adjoint goes: per step (moving bed) or total
     AdjCfl cfl{};
     double *dtbar = nullptr, *dotpart = nullptr;
     if (adaptive) {
@@ -1203,7 +1249,12 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
         VG_CUDA(c, cudaMemcpyAsync(W, dJ_deta, 8 * (size_t)(N + 1) * G, cudaMemcpyHostToDevice, c->stream));
         VG_CUDA(c, cudaMemsetAsync(wb, 0, 8 * w3, c->stream));
         VG_CUDA(c, cudaMemsetAsync(zb, 0, 8 * (size_t)nc, c->stream));
-        ADJ_CHECK(adjoint_gauge(G, c->gauge_cells, W + (size_t)N * G, nc, wb, zb, st));
+        zacc = bed ? zstep : zb;
+        if (bed) VG_CUDA(c, cudaMemsetAsync(zstep, 0, 8 * (size_t)nc, c->stream));
+        ADJ_CHECK(adjoint_gauge(G, c->gauge_cells, W + (size_t)N * G, nc, wb, zacc, st));
+        if (bed)
+            ADJ_CHECK(adjoint_bed_flush(nc, nv, vptr, vcell, zstep, c->bed_uplift, c->bed_onset, c->bed_rise, tn[N],
+                                        gU, gOn, zb, tsum, bedpart, st));
         int64_t nseg = (N + C - 1) / C;
         for (int64_t sg = nseg - 1; sg >= 0; sg--) {
             int64_t a = sg * C, b = std::min(a + C, N);
@@ -1219,6 +1270,7 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
                 dd.fv_out = FVseg + (size_t)(n - a) * 18 * nc;
                 StepParams pn = p;
                 pn.dt_fixed = c->adj_dts[n];        // the step the forward run took
+                if (bed) ADJ_CHECK(launch_bed_update(d, p, nullptr, 64, false, tn[n], st));   // bed of step n
                 ADJ_CHECK(launch_stage1_f64(dd, pn, win, c->cfg1, st));
                 dd.fv_out = FVseg + ((size_t)(n - a) * 18 + 9) * nc;
                 if (adaptive) dd.r1_out = R1seg + (size_t)(n - a) * w3;
@@ -1228,6 +1280,10 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
                 const double dtn = c->adj_dts[n];
                 const double *w = seg + (size_t)(n - a) * w3;
                 const double *R0 = R0seg + (size_t)(n - a) * w3;
+                if (bed) {
+                    ADJ_CHECK(launch_bed_update(d, p, nullptr, 64, false, tn[n], st));     // bed of step n
+                    VG_CUDA(c, cudaMemsetAsync(zstep, 0, 8 * (size_t)nc, c->stream));
+                }
                 ADJ_CHECK(adjoint_stage1(nc, dtn, hthr, w, R0, w1, H1pre, st));
                 ADJ_CHECK(adjoint_stage2_rev(nc, dtn, m2seg + (size_t)(n - a) * nc, wb, wbn, wb1, Rb, st));
                 // dt-bar, stage 2: sum w-bar_pre . R1 / 2 = sum Rb . R1 / dt
@@ -1235,16 +1291,29 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
                     ADJ_CHECK(adjoint_dot((int64_t)w3, Rb, R1seg + (size_t)(n - a) * w3, 1.0 / dtn, dtbar, true,
                                           dotpart, st));
                 double *FV0 = FVseg + (size_t)(n - a) * 18 * nc, *FV1 = FV0 + 9 * (size_t)nc;
-                ADJ_CHECK(adjoint_residual_vjp(d, p, w1, Rb, wb1, zb, FV1, true, FVb, zfb, own, send, st));
+                ADJ_CHECK(adjoint_residual_vjp(d, p, w1, Rb, wb1, zacc, FV1, true, FVb, zfb, own, send, st));
                 ADJ_CHECK(adjoint_stage1_rev(nc, dtn, hthr, H1pre, wb1, wbn, Rb, st));
                 // dt-bar, stage 1: sum w1-bar_pre . R0 = sum Rb . R0 / dt
                 if (adaptive) ADJ_CHECK(adjoint_dot((int64_t)w3, Rb, R0, 1.0 / dtn, dtbar, false, dotpart, st));
-                ADJ_CHECK(adjoint_residual_vjp(d, p, w, Rb, wbn, zb, FV0, true, FVb, zfb, own, send, st,
+                // a moving bed: every later bed depends on this dt through the time
+                if (adaptive && bed) ADJ_CHECK(adjoint_scalar_add(dtbar, tsum, st));
+                ADJ_CHECK(adjoint_residual_vjp(d, p, w, Rb, wbn, zacc, FV0, true, FVb, zfb, own, send, st,
                                                adaptive ? &cfl : nullptr));
-                ADJ_CHECK(adjoint_gauge(G, c->gauge_cells, W + (size_t)n * G, nc, wbn, zb, st));
+                ADJ_CHECK(adjoint_gauge(G, c->gauge_cells, W + (size_t)n * G, nc, wbn, zacc, st));
+                if (bed)
+                    ADJ_CHECK(adjoint_bed_flush(nc, nv, vptr, vcell, zstep, c->bed_uplift, c->bed_onset, c->bed_rise,
+                                                tn[n], gU, gOn, zb, tsum, bedpart, st));
                 std::swap(wb, wbn);
-                c->launches += adaptive ? 17 : 11;
+                c->launches += (adaptive ? 17 : 11) + (bed ? 6 : 0);
             }
+        }
+        if (bed) {
+            // the context keeps the bed of the run's last time; the gradients stay on the host
+            ADJ_CHECK(launch_bed_update(d, p, nullptr, 64, false, tn[N], st));
+            c->adj_gU.resize(nv);
+            c->adj_gOn.resize(nv);
+            VG_CUDA(c, cudaMemcpyAsync(c->adj_gU.data(), gU, 8 * (size_t)nv, cudaMemcpyDeviceToHost, c->stream));
+            VG_CUDA(c, cudaMemcpyAsync(c->adj_gOn.data(), gOn, 8 * (size_t)nv, cudaMemcpyDeviceToHost, c->stream));
         }
         // internal -> original order on the host
         std::vector<double> h(4 * (size_t)nc);
@@ -1272,6 +1341,15 @@ done:
     cudaStreamSynchronize(c->stream);
     for (void *q : bufs) cudaFree(q);
     return rc;
+}
+
+int vg_adj_bed_gradient(vg_ctx *c, double *dJ_duplift, double *dJ_donset)
+{
+    if (!c) return VG_EINVAL;
+    if (c->adj_gU.empty()) return fail(c, VG_ESTATE, "no vg_adj_backward of a run with a moving bed");
+    if (dJ_duplift) std::copy(c->adj_gU.begin(), c->adj_gU.end(), dJ_duplift);
+    if (dJ_donset) std::copy(c->adj_gOn.begin(), c->adj_gOn.end(), dJ_donset);
+    return VG_OK;
 }
 
 int vg_device_bytes(vg_ctx *c, int64_t *bytes)

@@ -168,6 +168,14 @@ int adjoint_residual_vjp(const DevPtrs &d, const StepParams &p, const double *w,
 // *acc (= or +=) scale * sum_i a[i] b[i], deterministic; part: kAdjCflParts doubles.
 int adjoint_dot(int64_t n, const double *a, const double *b, double scale, double *acc, bool reset, double *part,
                 void *stream);
+// Moving bed: one step's bed adjoint zs [nc] at time t -> uplift / onset
+// gradients gU, gOn [nv] (+=), zb_total (+= zs), *tsum (+= the adjoint of t);
+// vptr [nv+1], vcell: the cells around each vertex.
+int adjoint_bed_flush(int nc, int nv, const int32_t *vptr, const int32_t *vcell, double *zs, const double *uplift,
+                      const double *onset, double rise, double t, double *gU, double *gOn, double *zb_total,
+                      double *tsum, double *part, void *stream);
+// *y += *x on the device.
+int adjoint_scalar_add(double *y, const double *x, void *stream);
 int adjoint_stage1(int nc, double dt, double hthr, const double *w, const double *R0, double *w1, double *H1pre,
                    void *stream);
 int adjoint_stage2_rev(int nc, double dt, const uint8_t *mask2, const double *wb, double *wbn, double *wb1,

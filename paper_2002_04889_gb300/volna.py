@@ -84,6 +84,7 @@ _SIGNATURES = {
     "vg_step_noalloc": ([_V, _V, _V, C.c_double, _D], C.c_int),
     "vg_set_depth": ([_V, _D], C.c_int),
     "vg_set_bed_motion": ([_V, _D, _D, C.c_double], C.c_int),
+    "vg_adj_bed_gradient": ([_V, _D, _D], C.c_int),
     "vg_set_open_boundary": ([_V, C.c_int64, _I32], C.c_int),
     "vg_adj_forward": ([_V, C.c_int64, C.c_double, C.c_int64], C.c_int),
     "vg_adj_backward": ([_V, _D, _D, _D, _D, _D, _D], C.c_int),
@@ -449,6 +450,12 @@ class Solver:
 
     def adj_backward(self, dJ_deta, nv: int) -> dict:
         return vg_adj_backward(self.ctx, dJ_deta, self.nc, nv)
+
+    def adj_bed_gradient(self, nv: int):
+        """(dJ/duplift_v, dJ/donset_v) after adj_backward of a run with a moving bed."""
+        gu, go = np.empty(nv), np.empty(nv)
+        _check(self.ctx, load().vg_adj_bed_gradient(self.ctx, _dp(gu), _dp(go)))
+        return gu, go
 
 
 # ---------------------------------------------------------------- batched ensembles

@@ -113,9 +113,6 @@ def test_remove_motion_and_guards():
             sv.set_depth(m.depth)
         assert e.value.code == volna.VG_ESTATE
         with pytest.raises(volna.VolnaError) as e:
-            sv.adj_forward(5, 1e-3)
-        assert e.value.code == volna.VG_ESTATE
-        with pytest.raises(volna.VolnaError) as e:
             sv.set_bed_motion(up, on, -1.0)
         assert e.value.code == volna.VG_EINVAL
         M0 = sv.diagnostics()["mass"]
