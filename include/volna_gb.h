@@ -296,8 +296,8 @@ int vg_adj_bed_gradient(vg_ctx *ctx, double *dJ_duplift, double *dJ_donset);
  * the reconstruction sees no jump across it and its flux is the physical flux
  * of the face state (zero-gradient outflow; waves leave with little
  * reflection).  n = 0 makes every boundary face a wall again.  An edge that is
- * not a boundary edge: VG_EINVAL, nothing changed.  The adjoint calls fail
- * with VG_ESTATE while a face is open. */
+ * not a boundary edge: VG_EINVAL, nothing changed.  The adjoint
+ * differentiates through open faces as well. */
 int vg_set_open_boundary(vg_ctx *ctx, int64_t n, const int32_t *edges);
 
 /* Moving bed: the time-dependent depth h(x, y, t) of Sec. 2.1 (the governing

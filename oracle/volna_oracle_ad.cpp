@@ -25,7 +25,24 @@ namespace vo_ad_impl {
 using vo_ad_impl::vo_mesh;
 using vo_ad_impl::vo_params;
 
+// Open boundary edges applied to every mesh the entry points below build
+// (vo_set_open); empty: all boundary faces are walls.
+static std::vector<int32_t> g_open_edges;
+
+static int apply_open(vo_mesh *m)
+{
+    if (g_open_edges.empty()) return 0;
+    return vo_ad_impl::vo_set_open(m, (int64_t)(g_open_edges.size() / 2), g_open_edges.data());
+}
+
 extern "C" {
+
+/* The open boundary edges [n][2] (vertex ids) of the following calls; n = 0: walls. */
+int vo_ad_set_open(int64_t n, const int32_t *edges)
+{
+    g_open_edges.assign(edges, edges + 2 * (n > 0 ? n : 0));
+    return 0;
+}
 
 /*
  * Linear gauge functional and its gradient through n_steps SSP-RK(2,2) steps
@@ -55,6 +72,7 @@ int vo_ad_gauge_gradient(int64_t nv, const double *xy, int64_t nc, const int32_t
     vo_mesh *m = nullptr;
     int rc = vo_ad_impl::vo_mesh_build(nv, xy, nc, tri, depth.data(), &m);
     if (rc) return rc;
+    if ((rc = apply_open(m))) { vo_ad_impl::vo_mesh_free(m); return rc; }
     vo_params p;
     vo_ad_impl::vo_default_params(&p);
     p.g = g;
@@ -119,6 +137,7 @@ int vo_ad_gauge_gradient_bed(int64_t nv, const double *xy, int64_t nc, const int
     vo_mesh *m = nullptr;
     int rc = vo_ad_impl::vo_mesh_build(nv, xy, nc, tri, depth.data(), &m);
     if (rc) return rc;
+    if ((rc = apply_open(m))) { vo_ad_impl::vo_mesh_free(m); return rc; }
     vo_params p;
     vo_ad_impl::vo_default_params(&p);
     p.g = g;

@@ -39,7 +39,8 @@ __device__ __forceinline__ double G(const AdjMesh &m, int row, int k) { return m
 // kernels), keeping what the reverse needs.
 struct ReconFwd {
     double qK[3], qn[3][3];
-    bool wall[3];
+    bool wall[3];            // boundary face (wall or open)
+    bool open[3];            // open face: the ghost is the cell itself
     bool recon;
     double D[3][3];          // [v][f]
     double alpha[3];
@@ -62,11 +63,16 @@ __device__ void recon_forward(const AdjMesh &m, const double *w, int K, ReconFwd
     for (int f = 0; f < 3; f++) {
         int j = m.nbr[f * nc + K];
         R.wall[f] = j < 0;
+        R.open[f] = j == -2;
         if (j >= 0) {
             R.qn[f][0] = H[j] + m.z[j];
             R.qn[f][1] = Hu[j];
             R.qn[f][2] = Hv[j];
             if (!(H[j] > m.hthr)) recon = false;
+        } else if (j == -2) {
+            R.qn[f][0] = R.qK[0];
+            R.qn[f][1] = HuK;
+            R.qn[f][2] = HvK;
         } else {
             double nx = G(m, GEO_NX + f, K), ny = G(m, GEO_NY + f, K);
             double mn = HuK * nx + HvK * ny;
@@ -156,7 +162,7 @@ __global__ void adj_face_values_kernel(AdjMesh m, const double *w, const double 
 __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL, double zL, double HfR,
                          double HufR, double HvfR, double zR, double nx, double ny, bool wall,
                          const double Pb[3], double PLb, double PRb, double bL[4], double bR[4],
-                         double amb = 0.0)
+                         double amb = 0.0, bool open = false)
 {
     const double g = m.g, hg = m.half_g, hthr = m.hthr;
     for (int k = 0; k < 4; k++) { bL[k] = 0.0; bR[k] = 0.0; }
@@ -174,7 +180,7 @@ __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL,
         actL = xL > 0.0;
         HsL = actL ? xL : 0.0;
         HsR = HsL;
-        unR = -unL;
+        unR = open ? unL : -unL;
         utR = utL;
     } else {
         velR = HfR > hthr;
@@ -299,7 +305,7 @@ __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL,
     }
     // ---- reverse of the interface depths and velocities
     if (wall) {
-        unLb -= unRb;
+        unLb += open ? unRb : -unRb;
         utLb += utRb;
         HsLb += HsRb;
         if (actL) { HfLb += HsLb; bL[3] += HsLb; bL[3] -= HsLb; }
@@ -372,7 +378,8 @@ __global__ void adj_flux_vjp_kernel(AdjMesh m, const double *FV, const double *R
             }
             double bL[4], bR[4];
             flux_vjp(m, FV[(0 * 3 + f) * (size_t)nc + K], FV[(1 * 3 + f) * (size_t)nc + K],
-                     FV[(2 * 3 + f) * (size_t)nc + K], m.z[K], HfR, HufR, HvfR, zR, nx, ny, wall, Pb, PLb, PRb, bL, bR);
+                     FV[(2 * 3 + f) * (size_t)nc + K], m.z[K], HfR, HufR, HvfR, zR, nx, ny, wall, Pb, PLb, PRb, bL, bR,
+                     0.0, j == -2);
             for (int v = 0; v < 3; v++) FVb[(v * 3 + f) * (size_t)nc + K] = bL[v];
             zfb[f * (size_t)nc + K] = bL[3];
             if (!wall) {
@@ -448,6 +455,13 @@ __global__ void adj_recon_vjp_kernel(AdjMesh m, const double *w, const double *F
             }
             for (int f = 0; f < 3; f++) {
                 if (!R.wall[f]) continue;
+                if (R.open[f]) {                 // ghost = the cell's own values
+                    qKb[0] += qnb[f][0];
+                    Hub += qnb[f][1];
+                    Hvb += qnb[f][2];
+                    qnb[f][0] = qnb[f][1] = qnb[f][2] = 0.0;
+                    continue;
+                }
                 double nx = G(m, GEO_NX + f, K), ny = G(m, GEO_NY + f, K);
                 qKb[0] += qnb[f][0];
                 double mnb = -2.0 * nx * qnb[f][1] - 2.0 * ny * qnb[f][2];
@@ -575,7 +589,7 @@ __global__ void adj_gauge_kernel(int n_gauges, const int32_t *cells, const doubl
 
 // Forward wave speed of one face, the forward kernels' arithmetic.
 __device__ double face_speed(const AdjMesh &m, double HfL, double HufL, double HvfL, double zL, double HfR,
-                             double HufR, double HvfR, double zR, double nx, double ny, bool wall)
+                             double HufR, double HvfR, double zR, double nx, double ny, bool wall, bool open)
 {
     const double g = m.g, hthr = m.hthr;
     double uL = 0.0, vL = 0.0;
@@ -585,7 +599,7 @@ __device__ double face_speed(const AdjMesh &m, double HfL, double HufL, double H
     if (wall) {
         HsL = fmax(0.0, (HfL + zL) - zL);
         HsR = HsL;
-        unR = -unL;
+        unR = open ? unL : -unL;
     } else {
         double uR = 0.0, vR = 0.0;
         if (HfR > hthr) { uR = HufR / HfR; vR = HvfR / HfR; }
@@ -615,7 +629,7 @@ __device__ double face_speed(const AdjMesh &m, double HfL, double HufL, double H
 struct FaceIn {
     double HfL, HufL, HvfL, zL, HfR, HufR, HvfR, zR, nx, ny, l;
     int j, fj;
-    bool wall;
+    bool wall, open;
 };
 __device__ FaceIn face_in(const AdjMesh &m, const double *FV, int K, int f)
 {
@@ -623,6 +637,7 @@ __device__ FaceIn face_in(const AdjMesh &m, const double *FV, int K, int f)
     FaceIn r;
     r.j = m.nbr[f * nc + K];
     r.wall = r.j < 0;
+    r.open = r.j == -2;
     r.fj = r.wall ? 0 : (m.nbrl[f * nc + K] & 3);
     r.HfL = FV[(0 * 3 + f) * (size_t)nc + K];
     r.HufL = FV[(1 * 3 + f) * (size_t)nc + K];
@@ -648,7 +663,8 @@ __device__ double cell_speed(const AdjMesh &m, const double *FV, int K, int &fma
     fmax_out = -1;
     for (int f = 0; f < 3; f++) {
         FaceIn q = face_in(m, FV, K, f);
-        double la = q.l * face_speed(m, q.HfL, q.HufL, q.HvfL, q.zL, q.HfR, q.HufR, q.HvfR, q.zR, q.nx, q.ny, q.wall);
+        double la = q.l * face_speed(m, q.HfL, q.HufL, q.HvfL, q.zL, q.HfR, q.HufR, q.HvfR, q.zR, q.nx, q.ny, q.wall,
+                                     q.open);
         if (la > am) { am = la; fmax_out = f; }
     }
     return am;
@@ -704,11 +720,13 @@ __global__ void adj_cfl_face_kernel(AdjMesh m, const double *FV, int nparts, con
     int f;
     cell_speed(m, FV, K, f);
     const FaceIn q = face_in(m, FV, K, f);
-    const double a = face_speed(m, q.HfL, q.HufL, q.HvfL, q.zL, q.HfR, q.HufR, q.HvfR, q.zR, q.nx, q.ny, q.wall);
+    const double a = face_speed(m, q.HfL, q.HufL, q.HvfL, q.zL, q.HfR, q.HufR, q.HvfR, q.zR, q.nx, q.ny, q.wall,
+                                q.open);
     const double ab = -(*dtbar) * dtc / a;
     const double P0[3] = {0.0, 0.0, 0.0};
     double bL[4], bR[4];
-    flux_vjp(m, q.HfL, q.HufL, q.HvfL, q.zL, q.HfR, q.HufR, q.HvfR, q.zR, q.nx, q.ny, q.wall, P0, 0.0, 0.0, bL, bR, ab);
+    flux_vjp(m, q.HfL, q.HufL, q.HvfL, q.zL, q.HfR, q.HufR, q.HvfR, q.zR, q.nx, q.ny, q.wall, P0, 0.0, 0.0, bL, bR, ab,
+             q.open);
     const int nc = m.nc;
     for (int v = 0; v < 3; v++) FVb[(v * 3 + f) * (size_t)nc + K] += bL[v];
     zfb[f * (size_t)nc + K] += bL[3];

@@ -1071,7 +1071,6 @@ int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_eve
     if (c->precision != 64) return fail(c, VG_EINVAL, "the adjoint runs in FP64 contexts");
     if (!c->has_mesh || !c->has_state) return fail(c, VG_ESTATE, "mesh and state must be set");
     if (c->n_gauges < 1) return fail(c, VG_ESTATE, "the adjoint differentiates gauge records: set gauges first");
-    if (c->n_open) return fail(c, VG_ESTATE, "the adjoint handles walls only, not open boundaries");
     DeviceGuard guard(c->device);
     free_adjoint(c);
     int64_t C = checkpoint_every ? checkpoint_every : (int64_t)std::ceil(std::sqrt((double)n_steps));

@@ -83,7 +83,7 @@ def test_batch_with_open_boundary_equals_single():
                 np.testing.assert_array_equal(a, ref[f])
 
 
-def test_reset_to_walls_and_guards():
+def test_reset_to_walls_and_invalid_edge():
     m, ends, s = _strip_wave()
     walls = _gpu(m, s, 50, 64, None, h_threshold=1e-6)
     with volna.Solver(64) as sv:
@@ -93,11 +93,6 @@ def test_reset_to_walls_and_guards():
         with pytest.raises(volna.VolnaError) as e:
             sv.set_open_boundary([[0, 1 + m.nv // 2]])
         assert e.value.code == volna.VG_EINVAL
-        sv.set_gauges([[0.0, 0.0]])
-        sv.set_state(*s, 0.0)
-        with pytest.raises(volna.VolnaError) as e:
-            sv.adj_forward(3, 1e-3)
-        assert e.value.code == volna.VG_ESTATE
         sv.set_open_boundary([])               # every boundary face a wall again
         sv.set_state(*s, 0.0)
         sv.step(50)
