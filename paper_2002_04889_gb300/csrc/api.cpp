@@ -40,6 +40,7 @@ struct vg_ctx {
     void *geo = nullptr, *z = nullptr, *w[2] = {nullptr, nullptr}, *R0 = nullptr;
     double *z64 = nullptr;
     int32_t *nbr = nullptr, *halo_ptr = nullptr, *halo_n1 = nullptr, *halo_ids = nullptr, *old_of_new = nullptr;
+    int32_t *new_of_old = nullptr;
     uint16_t *nbrl = nullptr, *ring1_nbr = nullptr;
     DevScalars *sc = nullptr;
     int32_t *gauge_cells = nullptr;
@@ -143,7 +144,7 @@ void free_mesh(vg_ctx *c)
     if (c->z64 == c->z) c->z64 = nullptr;
     dfree(c->geo); dfree(c->z); dfree(c->z64); dfree(c->w[0]); dfree(c->w[1]); dfree(c->R0);
     dfree(c->nbr); dfree(c->halo_ptr); dfree(c->halo_n1); dfree(c->halo_ids); dfree(c->ring1_nbr);
-    dfree(c->old_of_new); dfree(c->nbrl);
+    dfree(c->old_of_new); dfree(c->new_of_old); dfree(c->nbrl);
     dfree(c->gauge_cells); dfree(c->ring_t); dfree(c->ring_eta); dfree(c->staging);
     dfree(c->bed_vtx); dfree(c->bed_depth0); dfree(c->bed_uplift); dfree(c->bed_onset);
     c->bed_on = false;
@@ -260,6 +261,7 @@ int upload_mesh_arrays(vg_ctx *c)
     if ((rc = dmalloc(c, &c->R0, rs * 3 * m.nc))) return rc;
     if ((rc = dmalloc(c, (void **)&c->nbr, 4 * 3 * m.nc))) return rc;
     if ((rc = dmalloc(c, (void **)&c->old_of_new, 4 * m.nc))) return rc;
+    if ((rc = dmalloc(c, (void **)&c->new_of_old, 4 * m.nc))) return rc;
     if ((rc = dmalloc(c, (void **)&c->ring_t, 8 * kRingCap))) return rc;
     if (c->precision == 64) {
         if ((rc = upload_real(c, c->geo, m.geo.data(), m.geo.size()))) return rc;
@@ -293,6 +295,7 @@ int upload_mesh_arrays(vg_ctx *c)
     }
     VG_CUDA(c, cudaMemcpy(c->nbr, m.nbr.data(), 4 * 3 * m.nc, cudaMemcpyHostToDevice));
     VG_CUDA(c, cudaMemcpy(c->old_of_new, m.old_of_new.data(), 4 * m.nc, cudaMemcpyHostToDevice));
+    VG_CUDA(c, cudaMemcpy(c->new_of_old, m.new_of_old.data(), 4 * m.nc, cudaMemcpyHostToDevice));
     return upload_partition(c);
 }
 
@@ -678,6 +681,20 @@ int vg_get_params(vg_ctx *c, vg_params *p)
     return VG_OK;
 }
 
+// The device address of a host buffer the kernels may read or write in place
+// (pinned, mapped host memory), or NULL (pageable memory: copy through staging).
+static const void *mapped_view(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// is_double = 2: FP64 arrays in host order read in place by one thread per
+// original cell (mapped pinned host memory).
 static int set_state_impl(vg_ctx *c, const void *H, const void *Hu, const void *Hv, int is_double, double t)
 {
     DevScalars s;
@@ -690,8 +707,12 @@ static int set_state_impl(vg_ctx *c, const void *H, const void *Hu, const void *
         if (e) return cuda_fail(c, (cudaError_t)e, "bed update launch");
         c->launches++;
     }
-    int e = launch_import_state(dev_ptrs(c), c->old_of_new, H, Hu, Hv, is_double, c->w[0], c->precision,
-                                (void *)c->stream);
+    int e = is_double == 2
+                ? launch_import_state_orig(dev_ptrs(c), c->new_of_old, static_cast<const double *>(H),
+                                           static_cast<const double *>(Hu), static_cast<const double *>(Hv), c->w[0],
+                                           c->precision, (void *)c->stream)
+                : launch_import_state(dev_ptrs(c), c->old_of_new, H, Hu, Hv, is_double, c->w[0], c->precision,
+                                      (void *)c->stream);
     if (e) return cuda_fail(c, (cudaError_t)e, "state import launch");
     c->launches++;
     DevScalars r;
@@ -716,6 +737,9 @@ int vg_set_state(vg_ctx *c, const double *H, const double *Hu, const double *Hv,
     DeviceGuard guard(c->device);
     int64_t nc = c->hm.nc;
     int rc;
+    // pinned host buffers: the import kernel reads them in place over the CPU-GPU link
+    const void *mH = mapped_view(H), *mHu = mapped_view(Hu), *mHv = mapped_view(Hv);
+    if (mH && mHu && mHv) return set_state_impl(c, mH, mHu, mHv, 2, t);
     if (!c->staging && (rc = dmalloc(c, &c->staging, 8 * 3 * nc))) return rc;
     double *st = static_cast<double *>(c->staging);
     VG_CUDA(c, cudaMemcpyAsync(st, H, 8 * nc, cudaMemcpyHostToDevice, c->stream));
@@ -740,6 +764,20 @@ int vg_get_state(vg_ctx *c, double *H, double *Hu, double *Hv, double *t)
     DeviceGuard guard(c->device);
     int64_t nc = c->hm.nc;
     int rc;
+    // pinned host buffers: the export kernel writes them in place over the CPU-GPU link
+    void *mH = const_cast<void *>(mapped_view(H)), *mHu = const_cast<void *>(mapped_view(Hu));
+    void *mHv = const_cast<void *>(mapped_view(Hv));
+    if (mH && mHu && mHv) {
+        int e = launch_export_state_orig(dev_ptrs(c), c->new_of_old, c->w[c->cur], c->precision,
+                                         static_cast<double *>(mH), static_cast<double *>(mHu),
+                                         static_cast<double *>(mHv), (void *)c->stream);
+        if (e) return cuda_fail(c, (cudaError_t)e, "state export launch");
+        c->launches++;
+        DevScalars s;
+        if ((rc = read_scalars(c, s))) return rc;     // synchronises the stream
+        if (t) *t = s.t;
+        return VG_OK;
+    }
     if (!c->staging && (rc = dmalloc(c, &c->staging, 8 * 3 * nc))) return rc;
     double *st = static_cast<double *>(c->staging);
     int e = launch_export_state(dev_ptrs(c), c->old_of_new, c->w[c->cur], c->precision, st, st + nc, st + 2 * nc, 1,

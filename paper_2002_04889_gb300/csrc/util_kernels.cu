@@ -145,6 +145,40 @@ __global__ void export_state_kernel(int64_t nc, const int32_t *old_of_new, const
     }
 }
 
+// The same two conversions with one thread per ORIGINAL cell o (k =
+// new_of_old[o]): the host-order arrays are read or written contiguously, so
+// they can be pinned host memory that the kernel reads or writes in place over
+// the CPU-GPU link (the internal-order side is scattered in HBM instead).
+template <typename real, typename src_t>
+__global__ void import_state_orig_kernel(int64_t nc, const int32_t *new_of_old, const src_t *H, const src_t *Hu,
+                                         const src_t *Hv, const double *z, real *w, DevScalars *sc)
+{
+    bool bad = false;
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < nc; o += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = new_of_old[o];
+        src_t h = H[o], hu = Hu[o], hv = Hv[o];
+        if (!(h >= src_t(0)) || !isfinite(h) || !isfinite(hu) || !isfinite(hv)) bad = true;
+        w[k] = EtaForm<real>::value ? (real)((double)h + (double)z[k]) : (real)h;
+        w[nc + k] = (real)hu;
+        w[2 * nc + k] = (real)hv;
+    }
+    if (bad) atomicOr(&sc->flags, FLAG_BAD_INPUT);
+}
+
+template <typename real, typename dst_t>
+__global__ void export_state_orig_kernel(int64_t nc, const int32_t *new_of_old, const real *w, const real *zr,
+                                         const double *z, dst_t *H, dst_t *Hu, dst_t *Hv)
+{
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < nc; o += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = new_of_old[o];
+        double h = (double)w[k];
+        if (EtaForm<real>::value) h = (w[k] - zr[k] <= real(0)) ? 0.0 : fmax(0.0, h - z[k]);
+        H[o] = (dst_t)h;
+        Hu[o] = (dst_t)w[nc + k];
+        Hv[o] = (dst_t)w[2 * nc + k];
+    }
+}
+
 constexpr int DIAG_BLOCKS = 1024;
 
 // Fixed grid, fixed reduction tree: the sums do not depend on timing.
@@ -242,6 +276,30 @@ int launch_import_state(const DevPtrs &d, const int32_t *old_of_new, const void 
         else
             import_state_kernel<float, float><<<grid, 256, 0, s>>>(d.nc, old_of_new, (const float *)H, (const float *)Hu, (const float *)Hv, z, (float *)w, d.sc);
     }
+    return (int)cudaGetLastError();
+}
+
+int launch_import_state_orig(const DevPtrs &d, const int32_t *new_of_old, const double *H, const double *Hu,
+                             const double *Hv, void *w, int precision, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int grid = grid_for(d.nc);
+    if (precision == 64)
+        import_state_orig_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, H, Hu, Hv, d.z64, (double *)w, d.sc);
+    else
+        import_state_orig_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, H, Hu, Hv, d.z64, (float *)w, d.sc);
+    return (int)cudaGetLastError();
+}
+
+int launch_export_state_orig(const DevPtrs &d, const int32_t *new_of_old, const void *w, int precision, double *H,
+                             double *Hu, double *Hv, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int grid = grid_for(d.nc);
+    if (precision == 64)
+        export_state_orig_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const double *)w, (const double *)d.z, d.z64, H, Hu, Hv);
+    else
+        export_state_orig_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const float *)w, (const float *)d.z, d.z64, H, Hu, Hv);
     return (int)cudaGetLastError();
 }
 

@@ -278,3 +278,27 @@ def test_full_size_40m_sampled(precision):
         scale = max(float(np.abs(s.H[cells]).max()), 1e-3)
         for f, gv in (("H", H), ("Hu", Hu), ("Hv", Hv)):
             assert abs(gv[k] - r[f][centre]) <= tol * scale, (k, f, gv[k], r[f][centre])
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_pinned_host_buffers_are_used_in_place(thacker, precision):
+    """vg_set_state / vg_get_state with pinned (page-locked, mapped) host buffers
+    read and write them in place from the kernels (one thread per original
+    cell); the result equals the staged copy of pageable buffers bit for bit."""
+    torch = pytest.importorskip("torch")
+    m, s = thacker
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory().numpy()
+    with volna.Solver(precision) as a, volna.Solver(precision) as b:
+        for sv in (a, b):
+            sv.set_params(h_threshold=1e-5)
+            sv.upload_mesh(m)
+        a.set_state(pin(s.H), pin(s.Hu), pin(s.Hv), 0.0)
+        b.set_state(s.H, s.Hu, s.Hv, 0.0)
+        a.step(7)
+        b.step(7)
+        outs = [torch.empty(m.nc, dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+        _, _, _, ta = volna.vg_get_state(a.ctx, m.nc, out=tuple(outs))
+        ref = b.get_state()
+        for x, y in zip(outs, ref[:3]):
+            np.testing.assert_array_equal(x, y)
+        assert ta == ref[3]
