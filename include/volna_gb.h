@@ -65,7 +65,8 @@ typedef struct vg_params {
                               produced a negative depth (otherwise it is emptied
                               and counted): 0                                      */
     int32_t block_cells;   /* cells per thread block of the step kernels
-                              (32..256, multiple of 32; 0 = library default 256;
+                              (32..512, multiple of 32, at most 256 in a batch;
+                              0 = library default 256;
                               halved automatically while the block and its
                               two-ring halo exceed shared memory)                 */
     int32_t block_threads; /* threads per thread block of the step kernels: a

@@ -481,8 +481,8 @@ int validate_params(const vg_params *p, std::string &why)
     if (!(p->dt_fixed >= 0) || !(p->dt_max >= 0) || !(p->t_end >= 0)) { why = "dt_fixed, dt_max, t_end must be >= 0"; return VG_EINVAL; }
     if (p->order != 1 && p->order != 2) { why = "order must be 1 or 2"; return VG_EINVAL; }
     if (p->gauge_every < 1) { why = "gauge_every must be >= 1"; return VG_EINVAL; }
-    if (p->block_cells != 0 && (p->block_cells < 32 || p->block_cells > 256 || p->block_cells % 32)) {
-        why = "block_cells must be 0 or a multiple of 32 in [32, 256]";
+    if (p->block_cells != 0 && (p->block_cells < 32 || p->block_cells > 512 || p->block_cells % 32)) {
+        why = "block_cells must be 0 or a multiple of 32 in [32, 512]";
         return VG_EINVAL;
     }
     int bc = p->block_cells ? p->block_cells : 256;

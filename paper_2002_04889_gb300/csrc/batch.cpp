@@ -143,6 +143,7 @@ int rebuild(vg_batch *b)
                 fill_batch_mesh_f32(host.data() + m * eb, d, p, M.w[parity], M.w[1 - parity], M.n_scen, item, M.first_entry);
             item += d.nblocks;
             if (block && block != d.block) return bfail(b, VG_EINVAL, "meshes of a batch must share one block size");
+            if (d.block > 256) return bfail(b, VG_EINVAL, "batched ensembles use blocks of at most 256 cells");
             block = d.block;
             max_halo = std::max(max_halo, (int)d.max_halo);
             max_ring1 = std::max(max_ring1, (int)d.max_ring1);

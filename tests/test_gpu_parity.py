@@ -60,7 +60,7 @@ def test_fp32_parity_thacker_100_steps(thacker, thacker_ref):
     assert g["t"] == pytest.approx(thacker_ref["t"], rel=1e-4)
 
 
-@pytest.mark.parametrize("n,block", [(7, 32), (23, 64), (37, 128), (50, 256), (61, 96)])
+@pytest.mark.parametrize("n,block", [(7, 32), (23, 64), (37, 128), (50, 256), (61, 96), (70, 512)])
 def test_ragged_tiles_fp64(n, block):
     """Meshes spanning several blocks with a ragged last block, several block sizes."""
     m = I.thacker_mesh(n=n, shuffle_cells=True)
