@@ -269,6 +269,17 @@ int vg_set_depth(vg_ctx *ctx, const double *depth_v);
  */
 int vg_adj_forward(vg_ctx *ctx, int64_t n_steps, double dt, int64_t checkpoint_every);
 
+/* The same forward run for binomial checkpointing: only the first state is
+ * kept, and vg_adj_backward reverses the steps with `slots` (1..4096) state
+ * buffers on the device, recomputing forward steps along Griewank's binomial
+ * schedule (the split of each range minimises the recomputed steps: found by
+ * dynamic programming for up to 2048 steps, by halving beyond).  Device memory
+ * is slots + 3 states plus one step's recordings, instead of the sqrt(N)
+ * segment of recordings -- for meshes whose sqrt(N) segment does not fit --
+ * at the price of recomputation (for N steps and s slots about N log N / log s
+ * forward steps).  The gradients equal those of vg_adj_forward bit for bit. */
+int vg_adj_forward_binomial(vg_ctx *ctx, int64_t n_steps, double dt, int32_t slots);
+
 /*
  * Reverse sweep of the last vg_adj_forward run.  dJ_deta[n_steps + 1][G] is the
  * derivative of J with respect to each gauge record.  Outputs (host FP64,

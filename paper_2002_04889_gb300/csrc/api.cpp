@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <string>
 #include <unordered_map>
@@ -77,6 +78,7 @@ struct vg_ctx {
     double adj_t0 = 0.0;                // time of the forward run's first state
     bool adj_bed = false;               // the forward run had a moving bed
     std::vector<double> adj_gU, adj_gOn;   // its uplift / onset gradients (last backward pass)
+    int32_t adj_slots = 0;              // > 0: binomial checkpointing with this many state slots
     bool profile = false;
     double prof_ms[kKernels] = {0, 0, 0, 0};
     int64_t prof_n[kKernels] = {0, 0, 0, 0};
@@ -1173,6 +1175,16 @@ int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_eve
     c->adj_bed = c->bed_on;
     c->adj_gU.clear();
     c->adj_gOn.clear();
+    c->adj_slots = 0;
+    return VG_OK;
+}
+
+int vg_adj_forward_binomial(vg_ctx *c, int64_t n_steps, double dt, int32_t slots)
+{
+    if (!c || n_steps < 1 || slots < 1 || slots > 4096) return VG_EINVAL;
+    int rc = vg_adj_forward(c, n_steps, dt, n_steps);     // keeps the first state only
+    if (rc) return rc;
+    c->adj_slots = slots;
     return VG_OK;
 }
 
@@ -1186,6 +1198,8 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
     const int64_t N = c->adj_n, C = c->adj_every;
     const int nc = (int)c->hm.nc, G = c->n_gauges;
     const size_t w3 = 3 * (size_t)nc;
+    const bool binomial = c->adj_slots > 0;
+    const int64_t RC = binomial ? 1 : C;    // steps whose recordings are held at once
     // scratch (freed at the end)
     std::vector<void *> bufs;
     auto alloc = [&](size_t n_doubles, double **p) {
@@ -1203,11 +1217,12 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
     int rc = 0;
     if ((rc = alloc((size_t)(N + 1) * G, &W)) || (rc = alloc(w3, &wb)) || (rc = alloc(w3, &wbn)) ||
         (rc = alloc(w3, &wb1)) || (rc = alloc(nc, &zb)) || (rc = alloc(w3, &Rb)) || (rc = alloc(w3, &wlast)) ||
-        (rc = alloc(w3, &w1)) || (rc = alloc(nc, &H1pre)) || (rc = alloc(18 * (size_t)nc * C, &FVseg)) ||
+        (rc = alloc(w3, &w1)) || (rc = alloc(nc, &H1pre)) || (rc = alloc(18 * (size_t)nc * RC, &FVseg)) ||
         (rc = alloc(9 * (size_t)nc, &FVb)) || (rc = alloc(3 * (size_t)nc, &zfb)) || (rc = alloc(4 * (size_t)nc, &own)) ||
-        (rc = alloc(12 * (size_t)nc, &send)) || (rc = alloc(w3 * (size_t)C, &seg)) ||
-        (rc = alloc(w3 * (size_t)C, &R0seg)) || (rc = alloc(((size_t)nc * C + 7) / 8, &m2raw)) ||
-        (adaptive && ((rc = alloc(w3 * (size_t)C, &R1seg)) || (rc = alloc(8 + 3 * (size_t)kAdjCflParts, &cflscr))))) {
+        (rc = alloc(12 * (size_t)nc, &send)) ||
+        (rc = alloc(w3 * (size_t)(binomial ? 2 + c->adj_slots : C), &seg)) ||
+        (rc = alloc(w3 * (size_t)RC, &R0seg)) || (rc = alloc(((size_t)nc * RC + 7) / 8, &m2raw)) ||
+        (adaptive && ((rc = alloc(w3 * (size_t)RC, &R1seg)) || (rc = alloc(8 + 3 * (size_t)kAdjCflParts, &cflscr))))) {
         for (void *q : bufs) cudaFree(q);
         return rc;
     }
@@ -1292,57 +1307,141 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
         if (bed)
             ADJ_CHECK(adjoint_bed_flush(nc, nv, vptr, vcell, zstep, c->bed_uplift, c->bed_onset, c->bed_rise, tn[N],
                                         gU, gOn, zb, tsum, bedpart, st));
-        int64_t nseg = (N + C - 1) / C;
-        for (int64_t sg = nseg - 1; sg >= 0; sg--) {
-            int64_t a = sg * C, b = std::min(a + C, N);
-            // recompute the segment from its checkpoint, recording each step's
-            // state, stage-1 residual and stage-2 dry-fix branches
-            VG_CUDA(c, cudaMemcpyAsync(seg, c->ckpt[sg], 8 * w3, cudaMemcpyDeviceToDevice, c->stream));
-            for (int64_t n = a; n < b; n++) {
-                double *win = seg + (size_t)(n - a) * w3;
-                double *wout = n + 1 < b ? win + w3 : wlast;
-                DevPtrs dd = d;
-                dd.R0 = R0seg + (size_t)(n - a) * w3;
-                dd.mask2 = m2seg + (size_t)(n - a) * nc;
-                dd.fv_out = FVseg + (size_t)(n - a) * 18 * nc;
-                StepParams pn = p;
-                pn.dt_fixed = c->adj_dts[n];        // the step the forward run took
-                if (bed) ADJ_CHECK(launch_bed_update(d, p, nullptr, 64, false, tn[n], st));   // bed of step n
-                ADJ_CHECK(launch_stage1_f64(dd, pn, win, c->cfg1, st));
-                dd.fv_out = FVseg + ((size_t)(n - a) * 18 + 9) * nc;
-                if (adaptive) dd.r1_out = R1seg + (size_t)(n - a) * w3;
-                ADJ_CHECK(launch_stage2_f64(dd, pn, win, wout, c->cfg2, st));
+        // one forward step n from win to wout, recording into recording slot r what
+        // its reversal needs (stage-1 residual, face values of both stages, the
+        // stage-2 dry-fix branches, with CFL steps the stage-2 residual)
+        auto record_step = [&](int64_t n, const double *win, double *wout, int64_t r) -> int {
+            DevPtrs dd = d;
+            dd.R0 = R0seg + (size_t)r * w3;
+            dd.mask2 = m2seg + (size_t)r * nc;
+            dd.fv_out = FVseg + (size_t)r * 18 * nc;
+            StepParams pn = p;
+            pn.dt_fixed = c->adj_dts[n];        // the step the forward run took
+            int e;
+            if (bed && (e = launch_bed_update(d, p, nullptr, 64, false, tn[n], st))) return e;   // bed of step n
+            if ((e = launch_stage1_f64(dd, pn, win, c->cfg1, st))) return e;
+            dd.fv_out = FVseg + ((size_t)r * 18 + 9) * nc;
+            if (adaptive) dd.r1_out = R1seg + (size_t)r * w3;
+            return launch_stage2_f64(dd, pn, win, wout, c->cfg2, st);
+        };
+        // one forward step without recordings (binomial schedule)
+        auto advance_step = [&](int64_t n, const double *win, double *wout) -> int {
+            DevPtrs dd = d;
+            dd.R0 = R0seg;
+            StepParams pn = p;
+            pn.dt_fixed = c->adj_dts[n];
+            int e;
+            if (bed && (e = launch_bed_update(d, p, nullptr, 64, false, tn[n], st))) return e;
+            if ((e = launch_stage1_f64(dd, pn, win, c->cfg1, st))) return e;
+            return launch_stage2_f64(dd, pn, win, wout, c->cfg2, st);
+        };
+        // the reversal of step n from its state w and its recordings in slot r:
+        // wb (adjoint of w^{n+1}) -> wb (adjoint of w^n)
+        auto reverse_step = [&](int64_t n, const double *w, int64_t r) -> int {
+            const double dtn = c->adj_dts[n];
+            const double *R0 = R0seg + (size_t)r * w3;
+            int e;
+            if (bed) {
+                if ((e = launch_bed_update(d, p, nullptr, 64, false, tn[n], st))) return e;     // bed of step n
+                if ((e = (int)cudaMemsetAsync(zstep, 0, 8 * (size_t)nc, c->stream))) return e;
             }
-            for (int64_t n = b - 1; n >= a; n--) {
-                const double dtn = c->adj_dts[n];
-                const double *w = seg + (size_t)(n - a) * w3;
-                const double *R0 = R0seg + (size_t)(n - a) * w3;
-                if (bed) {
-                    ADJ_CHECK(launch_bed_update(d, p, nullptr, 64, false, tn[n], st));     // bed of step n
-                    VG_CUDA(c, cudaMemsetAsync(zstep, 0, 8 * (size_t)nc, c->stream));
+            if ((e = adjoint_stage1(nc, dtn, hthr, w, R0, w1, H1pre, st))) return e;
+            if ((e = adjoint_stage2_rev(nc, dtn, m2seg + (size_t)r * nc, wb, wbn, wb1, Rb, st))) return e;
+            // dt-bar, stage 2: sum w-bar_pre . R1 / 2 = sum Rb . R1 / dt
+            if (adaptive && (e = adjoint_dot((int64_t)w3, Rb, R1seg + (size_t)r * w3, 1.0 / dtn, dtbar, true,
+                                             dotpart, st)))
+                return e;
+            double *FV0 = FVseg + (size_t)r * 18 * nc, *FV1 = FV0 + 9 * (size_t)nc;
+            if ((e = adjoint_residual_vjp(d, p, w1, Rb, wb1, zacc, FV1, true, FVb, zfb, own, send, st))) return e;
+            if ((e = adjoint_stage1_rev(nc, dtn, hthr, H1pre, wb1, wbn, Rb, st))) return e;
+            // dt-bar, stage 1: sum w1-bar_pre . R0 = sum Rb . R0 / dt
+            if (adaptive && (e = adjoint_dot((int64_t)w3, Rb, R0, 1.0 / dtn, dtbar, false, dotpart, st))) return e;
+            // a moving bed: every later bed depends on this dt through the time
+            if (adaptive && bed && (e = adjoint_scalar_add(dtbar, tsum, st))) return e;
+            if ((e = adjoint_residual_vjp(d, p, w, Rb, wbn, zacc, FV0, true, FVb, zfb, own, send, st,
+                                          adaptive ? &cfl : nullptr)))
+                return e;
+            if ((e = adjoint_gauge(G, c->gauge_cells, W + (size_t)n * G, nc, wbn, zacc, st))) return e;
+            if (bed && (e = adjoint_bed_flush(nc, nv, vptr, vcell, zstep, c->bed_uplift, c->bed_onset, c->bed_rise,
+                                              tn[n], gU, gOn, zb, tsum, bedpart, st)))
+                return e;
+            std::swap(wb, wbn);
+            c->launches += (adaptive ? 17 : 11) + (bed ? 6 : 0);
+            return 0;
+        };
+        if (!binomial) {
+            // sqrt(N) segments: recompute each segment once from its checkpoint,
+            // recording every step, then reverse it
+            int64_t nseg = (N + C - 1) / C;
+            for (int64_t sg = nseg - 1; sg >= 0; sg--) {
+                int64_t a = sg * C, b = std::min(a + C, N);
+                VG_CUDA(c, cudaMemcpyAsync(seg, c->ckpt[sg], 8 * w3, cudaMemcpyDeviceToDevice, c->stream));
+                for (int64_t n = a; n < b; n++) {
+                    double *win = seg + (size_t)(n - a) * w3;
+                    double *wout = n + 1 < b ? win + w3 : wlast;
+                    ADJ_CHECK(record_step(n, win, wout, n - a));
                 }
-                ADJ_CHECK(adjoint_stage1(nc, dtn, hthr, w, R0, w1, H1pre, st));
-                ADJ_CHECK(adjoint_stage2_rev(nc, dtn, m2seg + (size_t)(n - a) * nc, wb, wbn, wb1, Rb, st));
-                // dt-bar, stage 2: sum w-bar_pre . R1 / 2 = sum Rb . R1 / dt
-                if (adaptive)
-                    ADJ_CHECK(adjoint_dot((int64_t)w3, Rb, R1seg + (size_t)(n - a) * w3, 1.0 / dtn, dtbar, true,
-                                          dotpart, st));
-                double *FV0 = FVseg + (size_t)(n - a) * 18 * nc, *FV1 = FV0 + 9 * (size_t)nc;
-                ADJ_CHECK(adjoint_residual_vjp(d, p, w1, Rb, wb1, zacc, FV1, true, FVb, zfb, own, send, st));
-                ADJ_CHECK(adjoint_stage1_rev(nc, dtn, hthr, H1pre, wb1, wbn, Rb, st));
-                // dt-bar, stage 1: sum w1-bar_pre . R0 = sum Rb . R0 / dt
-                if (adaptive) ADJ_CHECK(adjoint_dot((int64_t)w3, Rb, R0, 1.0 / dtn, dtbar, false, dotpart, st));
-                // a moving bed: every later bed depends on this dt through the time
-                if (adaptive && bed) ADJ_CHECK(adjoint_scalar_add(dtbar, tsum, st));
-                ADJ_CHECK(adjoint_residual_vjp(d, p, w, Rb, wbn, zacc, FV0, true, FVb, zfb, own, send, st,
-                                               adaptive ? &cfl : nullptr));
-                ADJ_CHECK(adjoint_gauge(G, c->gauge_cells, W + (size_t)n * G, nc, wbn, zacc, st));
-                if (bed)
-                    ADJ_CHECK(adjoint_bed_flush(nc, nv, vptr, vcell, zstep, c->bed_uplift, c->bed_onset, c->bed_rise,
-                                                tn[n], gU, gOn, zb, tsum, bedpart, st));
-                std::swap(wb, wbn);
-                c->launches += (adaptive ? 17 : 11) + (bed ? 6 : 0);
+                for (int64_t n = b - 1; n >= a; n--) ADJ_CHECK(reverse_step(n, seg + (size_t)(n - a) * w3, n - a));
             }
+        } else {
+            // binomial checkpointing: reverse [l, r) from the state at l with
+            // `nfree` free state slots, splitting where the fewest forward steps
+            // are recomputed (Griewank's binomial schedule, by dynamic programming
+            // for up to 2048 steps, by halving beyond)
+            const int S = c->adj_slots;
+            double *tmp[2] = {seg, seg + w3};
+            std::vector<double *> pool;
+            for (int k = 0; k < S; k++) pool.push_back(seg + (size_t)(2 + k) * w3);
+            const int64_t TD = std::min<int64_t>(N, 2048);
+            std::vector<int64_t> F((size_t)(TD + 1) * (S + 1), 0), M((size_t)(TD + 1) * (S + 1), 1);
+            auto at = [&](int64_t t, int sl) -> size_t { return (size_t)t * (S + 1) + sl; };
+            for (int64_t t = 2; t <= TD; t++) {
+                F[at(t, 0)] = t * (t - 1) / 2;
+                for (int sl = 1; sl <= S; sl++) {
+                    int64_t best = INT64_MAX, bm = 1;
+                    for (int64_t m = 1; m < t; m++) {
+                        int64_t cost = m + F[at(t - m, sl - 1)] + F[at(m, sl)];
+                        if (cost < best) { best = cost; bm = m; }
+                    }
+                    F[at(t, sl)] = best;
+                    M[at(t, sl)] = bm;
+                }
+            }
+            auto split = [&](int64_t t, int sl) -> int64_t { return t <= TD ? M[at(t, sl)] : t / 2; };
+            int err = 0;
+            std::function<int(int64_t, int64_t, const double *, int)> rev;
+            rev = [&](int64_t l, int64_t r, const double *wl, int nfree) -> int {
+                int e;
+                if (r - l == 1 || nfree == 0) {
+                    // no free slot: recompute from l for each step, last first
+                    for (int64_t k = r - 1; k >= l; k--) {
+                        const double *cur = wl;
+                        for (int64_t j = l; j < k; j++) {
+                            double *dst = tmp[(j - l) & 1];
+                            if ((e = advance_step(j, cur, dst))) return e;
+                            cur = dst;
+                        }
+                        if ((e = record_step(k, cur, wlast, 0))) return e;
+                        if ((e = reverse_step(k, cur, 0))) return e;
+                    }
+                    return 0;
+                }
+                const int64_t m = l + split(r - l, nfree);
+                double *slot = pool.back();
+                pool.pop_back();
+                const double *cur = wl;
+                for (int64_t j = l; j < m; j++) {
+                    double *dst = j + 1 == m ? slot : tmp[(j - l) & 1];
+                    if ((e = advance_step(j, cur, dst))) return e;
+                    cur = dst;
+                }
+                e = rev(m, r, slot, nfree - 1);
+                pool.push_back(slot);
+                if (e) return e;
+                return rev(l, m, wl, nfree);
+            };
+            err = rev(0, N, static_cast<const double *>(c->ckpt[0]), S);
+            ADJ_CHECK(err);
         }
         if (bed) {
             // the context keeps the bed of the run's last time; the gradients stay on the host

@@ -87,6 +87,7 @@ _SIGNATURES = {
     "vg_adj_bed_gradient": ([_V, _D, _D], C.c_int),
     "vg_set_open_boundary": ([_V, C.c_int64, _I32], C.c_int),
     "vg_adj_forward": ([_V, C.c_int64, C.c_double, C.c_int64], C.c_int),
+    "vg_adj_forward_binomial": ([_V, C.c_int64, C.c_double, C.c_int32], C.c_int),
     "vg_adj_backward": ([_V, _D, _D, _D, _D, _D, _D], C.c_int),
     "vg_batch_create": ([C.POINTER(_V), C.c_int, C.c_int, _V], C.c_int),
     "vg_batch_destroy": ([_V], None),
@@ -446,6 +447,11 @@ class Solver:
         """Run keeping checkpoints, with the fixed step dt or (dt = 0) the CFL
         step of every step; returns the gauge records (t, eta)."""
         vg_adj_forward(self.ctx, n_steps, dt, checkpoint_every)
+        return self.gauges()
+
+    def adj_forward_binomial(self, n_steps: int, dt: float = 0.0, slots: int = 8):
+        """adj_forward for binomial checkpointing with `slots` state buffers."""
+        _check(self.ctx, load().vg_adj_forward_binomial(self.ctx, int(n_steps), float(dt), int(slots)))
         return self.gauges()
 
     def adj_backward(self, dJ_deta, nv: int) -> dict:

@@ -310,3 +310,34 @@ def test_adjoint_with_open_boundaries_matches_oracle():
     for k_gpu, k_or in (("H0", "dH0"), ("Hu0", "dHu0"), ("Hv0", "dHv0"), ("depth", "ddepth")):
         err = _rel(g[k_gpu], ad[k_or])
         assert err <= 1e-10, (k_gpu, err)
+
+
+@pytest.mark.parametrize("slots", [1, 2, 5])
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_binomial_checkpointing_gives_the_same_gradient(slots, adaptive):
+    """vg_adj_forward_binomial keeps only the first state and reverses 23 steps
+    with a few state slots, recomputing along the binomial schedule: the gradient
+    (with a moving bed, so the per-step times matter too) equals the sqrt(N)
+    checkpointed one bit for bit."""
+    m, st, dt_fixed, cells = _case(24)
+    n_steps = 23
+    up, on = I.radial_rupture(m.xy, 0.01, 0.1, -0.05, 0.4, 2.0, 0.0)
+    W = np.random.default_rng(31).normal(size=(n_steps + 1, len(cells)))
+    dt = 0.0 if adaptive else dt_fixed
+    out = []
+    for mode in ("sqrt", "binomial"):
+        with volna.Solver(64) as sv:
+            sv.set_params(h_threshold=1e-5, cfl=0.9)
+            sv.upload_mesh(m)
+            sv.set_gauges(LATTICE)
+            sv.set_bed_motion(up, on, 0.05)
+            sv.set_state(*st, 0.0)
+            if mode == "sqrt":
+                sv.adj_forward(n_steps, dt)
+            else:
+                sv.adj_forward_binomial(n_steps, dt, slots)
+            g = sv.adj_backward(W, m.nv)
+            g["uplift"], g["onset"] = sv.adj_bed_gradient(m.nv)
+            out.append(g)
+    for k in ("H0", "Hu0", "Hv0", "depth", "uplift", "onset"):
+        np.testing.assert_array_equal(out[0][k], out[1][k])
