@@ -333,6 +333,14 @@ __device__ __forceinline__ void face_flux_dev(float g, float half_g, float hthr,
     QR = half_g * ((efR - eR) * (HfR + HR) + HsR * ds);
 }
 
+// An exactly dry cell: no water and no momentum.
+template <typename real>
+__device__ __forceinline__ bool exactly_dry(real W, real Hu, real Hv, real zc)
+{
+    const real H = EtaForm<real>::value ? W - zc : W;
+    return H == real(0) && Hu == real(0) && Hv == real(0);
+}
+
 // Stored state of cell gid as seen by the stage, and its bed.
 template <typename real, int STAGE>
 __device__ __forceinline__ bool stage_cell(const KArgs<real> &a, int gid, real dt, real &W, real &Hu, real &Hv,
@@ -364,6 +372,53 @@ __device__ __forceinline__ void st4(double *p, double x, double y, double z, dou
     reinterpret_cast<double2 *>(p)[1] = make_double2(z, w);
 }
 
+// Phase D's end for block cell l (global gid), from the sums of its three face
+// terms: R = -(aH, aHu, aHv) / |K|; stage 1 writes R0 and the CFL bound of
+// am = max_f l_f a_f; stage 2 forms w^{n+1} = w^n / 2 + (w1 + dt R) / 2 with
+// w^n = x, w1 from shared memory, and the dry fix.
+template <typename real, int STAGE>
+__device__ __forceinline__ void finish_cell(const KArgs<real> &a, int gid, const real *sWl, real aH, real aHu,
+                                            real aHv, real am, const real x[3], real area, real dt, real &my_min,
+                                            long long &my_neg, bool &bad)
+{
+    constexpr bool ETA = EtaForm<real>::value;
+    const int nc = (int)a.nc;
+    real RH = -aH / area, RHu = -aHu / area, RHv = -aHv / area;
+    if (STAGE == 1) {
+        a.R0[gid] = RH;
+        a.R0[nc + gid] = RHu;
+        a.R0[2 * nc + gid] = RHv;
+        if (am > real(0)) my_min = vmin(my_min, area / (real(3) * am));
+    } else {
+        if (a.r1_out) {
+            a.r1_out[gid] = RH;
+            a.r1_out[nc + gid] = RHu;
+            a.r1_out[2 * nc + gid] = RHv;
+        }
+        real W1, Hu1, Hv1, z1;
+        ld4(sWl, W1, Hu1, Hv1, z1);
+        real W = real(0.5) * x[0] + real(0.5) * (W1 + dt * RH);
+        real Hu = real(0.5) * x[1] + real(0.5) * (Hu1 + dt * RHu);
+        real Hv = real(0.5) * x[2] + real(0.5) * (Hv1 + dt * RHv);
+        real H = ETA ? W - z1 : W;
+        uint8_t branch = 0;
+        if (H < real(0)) {
+            my_neg++;
+            W = ETA ? z1 : real(0);
+            Hu = real(0); Hv = real(0);
+            branch = 2;
+        } else if (H <= a.hthr) {
+            Hu = real(0); Hv = real(0);
+            branch = 1;
+        }
+        if (a.mask2) a.mask2[gid] = branch;
+        if (!isfinite(W) || !isfinite(Hu) || !isfinite(Hv)) bad = true;
+        a.wout[gid] = W;
+        a.wout[nc + gid] = Hu;
+        a.wout[2 * nc + gid] = Hv;
+    }
+}
+
 // Shared memory of one CTA: cell states [L] x 4, face slots [3][L1] x 4 (L1 =
 // block + ring 1), global ids [L1], face codes and owned-face queue [3B] each.
 template <typename real>
@@ -390,7 +445,7 @@ __host__ __device__ inline size_t stage_smem_bytes(int block, int max_halo, int 
 // after phase B, and after phase C the cell's own term
 // (l_f Phi_0, l_f (Phi_1 + P n_x), l_f (Phi_2 + P n_y), x); x is l_f a_f in
 // stage 1 and, for block cells in stage 2, component f of w^n.
-template <typename real, int STAGE>
+template <typename real, int STAGE, bool DRY_SKIP = false>
 __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b, const real dt,
                                               unsigned char *smem_raw, int &qcount, real &my_min,
                                               long long &my_neg, bool &bad)
@@ -417,8 +472,12 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     const int n1 = a.halo_n1[b];
 
     // A: block + ring-1 + ring-2 states into shared memory.  Thread tid < B
-    // takes block cell tid and queues the faces that cell owns: a wall, a face to the halo, or a face to
-    // a block cell of higher local index.
+    // takes block cell tid and queues the faces that cell owns: a wall, a face
+    // to the halo, or a face to a block cell of higher local index.  It also
+    // notes whether the block and its ring 1 are exactly dry (dry land): then
+    // every face of the block has zero interface depths on both sides, hence
+    // zero flux and zero pressure terms, and phases B and C are skipped.
+    bool dry = true;
     {
         int gh = -1;
         if (tid < nh) gh = a.halo_ids[h0 + tid];
@@ -436,19 +495,26 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             if (neg) my_neg++;
             st4(sW + 4 * tid, W, Hu, Hv, zc);
             sGid[tid] = gid;
+            dry = exactly_dry(W, Hu, Hv, zc);
         }
         if (gh >= 0) {
             real W, Hu, Hv, zc;
             stage_cell<real, STAGE>(a, gh, dt, W, Hu, Hv, zc);
             st4(sW + 4 * (B + tid), W, Hu, Hv, zc);
-            if (tid < n1) sGid[B + tid] = gh;
+            if (tid < n1) {
+                sGid[B + tid] = gh;
+                dry = dry && exactly_dry(W, Hu, Hv, zc);
+            }
         }
         for (int h = tid + blockDim.x; h < nh; h += blockDim.x) {
             const int gid = a.halo_ids[h0 + h];
             real W, Hu, Hv, zc;
             stage_cell<real, STAGE>(a, gid, dt, W, Hu, Hv, zc);
             st4(sW + 4 * (B + h), W, Hu, Hv, zc);
-            if (h < n1) sGid[B + h] = gid;
+            if (h < n1) {
+                sGid[B + h] = gid;
+                dry = dry && exactly_dry(W, Hu, Hv, zc);
+            }
         }
         // warp-aggregated queue append: n = popcount(owned) in 0..3
         const int n = __popc(owned);
@@ -464,7 +530,20 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         for (int f = 0; f < 3; f++)
             if ((owned >> f) & 1) queue[pos++] = (uint16_t)((tid << 2) | f);
     }
-    __syncthreads();
+    // (runs with recordings for the adjoint take every phase)
+    if (__syncthreads_and(dry) && DRY_SKIP && !a.fv_out && !a.mask2 && !a.r1_out) {
+        // dry land: zero residual (phase D with zero face terms; w^n from memory)
+        if (tid == 0) qcount = 0;
+        if (tid < ncell) {
+            const int gid = c0 + tid;
+            real x[3] = {real(0), real(0), real(0)};
+            if (STAGE == 2) { x[0] = a.w[gid]; x[1] = a.w[nc + gid]; x[2] = a.w[2 * nc + gid]; }
+            const real area = ETA ? geo[(size_t)gid * G32 + G32_AREA] : geo[GEO_AREA * nc + gid];
+            finish_cell<real, STAGE>(a, gid, sW + 4 * tid, real(0), real(0), real(0), real(0), x, area, dt, my_min,
+                                     my_neg, bad);
+        }
+        return;
+    }
 
     // B: face values of block + ring-1 cells (Sec. 2.4, Eq. recon with the
     // Barth-Jespersen limiter); every neighbour is in shared memory
@@ -665,42 +744,15 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             aHv = aHv + t2;
             if (STAGE == 1) am = vmax(am, x[f]);
         }
-        real RH = -aH / area, RHu = -aHu / area, RHv = -aHv / area;
-        if (STAGE == 1) {
-            a.R0[gid] = RH;
-            a.R0[nc + gid] = RHu;
-            a.R0[2 * nc + gid] = RHv;
-            if (am > real(0)) my_min = vmin(my_min, area / (real(3) * am));
-        } else {
-            if (a.r1_out) {
-                a.r1_out[gid] = RH;
-                a.r1_out[nc + gid] = RHu;
-                a.r1_out[2 * nc + gid] = RHv;
-            }
-            real W1, Hu1, Hv1, z1;
-            ld4(sW + 4 * l, W1, Hu1, Hv1, z1);
-            real W = real(0.5) * x[0] + real(0.5) * (W1 + dt * RH);
-            real Hu = real(0.5) * x[1] + real(0.5) * (Hu1 + dt * RHu);
-            real Hv = real(0.5) * x[2] + real(0.5) * (Hv1 + dt * RHv);
-            real H = ETA ? W - z1 : W;
-            uint8_t branch = 0;
-            if (H < real(0)) {
-                my_neg++;
-                W = ETA ? z1 : real(0);
-                Hu = real(0); Hv = real(0);
-                branch = 2;
-            } else if (H <= hthr) {
-                Hu = real(0); Hv = real(0);
-                branch = 1;
-            }
-            if (a.mask2) a.mask2[gid] = branch;
-            if (!isfinite(W) || !isfinite(Hu) || !isfinite(Hv)) bad = true;
-            a.wout[gid] = W;
-            a.wout[nc + gid] = Hu;
-            a.wout[2 * nc + gid] = Hv;
-        }
+        finish_cell<real, STAGE>(a, gid, sW + 4 * l, aH, aHu, aHv, am, x, area, dt, my_min, my_neg, bad);
     }
 }
+
+// The dry-land shortcut is compiled where it costs no register spills: in the
+// stage-1 kernels (FP32 and FP64) and the FP64 stage-2 kernel; the FP32 stage-2
+// kernel, at its 40-register budget, would spill with the second path.
+template <typename real, int STAGE> struct DrySkip { static constexpr bool value = true; };
+template <> struct DrySkip<float, 2> { static constexpr bool value = false; };
 
 // Resident CTAs per SM asked of the register allocator.  The FP32 kernels are
 // latency-bound: 40 registers a thread (a few spilled) and ~48 resident warps
@@ -731,7 +783,8 @@ __global__ void __launch_bounds__(MAXT, StageMinCtas<real, MAXT>::value) stage_k
 
     int parity = 0;
     for (int b = blockIdx.x; b < a.nblocks; b += gridDim.x, parity ^= 1)
-        process_block<real, STAGE>(a, b, dt, smem_raw, qcount[parity], my_min, my_neg, bad);
+        process_block<real, STAGE, DrySkip<real, STAGE>::value>(a, b, dt, smem_raw, qcount[parity], my_min, my_neg,
+                                                                 bad);
 
     // CTA-level reductions, then one atomic per CTA
     const int lane = tid & 31, warp = tid >> 5, nwarps = (blockDim.x + 31) >> 5;
