@@ -445,7 +445,7 @@ __host__ __device__ inline size_t stage_smem_bytes(int block, int max_halo, int 
 // after phase B, and after phase C the cell's own term
 // (l_f Phi_0, l_f (Phi_1 + P n_x), l_f (Phi_2 + P n_y), x); x is l_f a_f in
 // stage 1 and, for block cells in stage 2, component f of w^n.
-template <typename real, int STAGE, bool DRY_SKIP = false>
+template <typename real, int STAGE, int DRY>
 __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b, const real dt,
                                               unsigned char *smem_raw, int &qcount, real &my_min,
                                               long long &my_neg, bool &bad)
@@ -476,7 +476,8 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     // to the halo, or a face to a block cell of higher local index.  It also
     // notes whether the block and its ring 1 are exactly dry (dry land): then
     // every face of the block has zero interface depths on both sides, hence
-    // zero flux and zero pressure terms, and phases B and C are skipped.
+    // zero flux and zero pressure terms, and phases B and C reduce to zero
+    // face terms.
     bool dry = true;
     {
         int gh = -1;
@@ -530,26 +531,42 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         for (int f = 0; f < 3; f++)
             if ((owned >> f) & 1) queue[pos++] = (uint16_t)((tid << 2) | f);
     }
-    // (runs with recordings for the adjoint take every phase)
-    if (__syncthreads_and(dry) && DRY_SKIP && !a.fv_out && !a.mask2 && !a.r1_out) {
-        // dry land: zero residual (phase D with zero face terms; w^n from memory)
+    // Dry land (runs with recordings for the adjoint take every phase).  Mode 1
+    // leaves the block here with a zero residual (phase D with zero face terms;
+    // w^n from memory); mode 2 has phase B write zero face terms for the block
+    // cells (and w^n for stage 2) and phase C no faces, which costs a few
+    // instructions more but no register spills where mode 1 would spill.
+    bool skip = false;
+    if constexpr (DRY == 0)
+        __syncthreads();
+    else
+        skip = __syncthreads_and(dry) && !a.fv_out && !a.mask2 && !a.r1_out;
+    if (DRY == 1 && skip) {
         if (tid == 0) qcount = 0;
         if (tid < ncell) {
             const int gid = c0 + tid;
             real x[3] = {real(0), real(0), real(0)};
             if (STAGE == 2) { x[0] = a.w[gid]; x[1] = a.w[nc + gid]; x[2] = a.w[2 * nc + gid]; }
-            const real area = ETA ? geo[(size_t)gid * G32 + G32_AREA] : geo[GEO_AREA * nc + gid];
-            finish_cell<real, STAGE>(a, gid, sW + 4 * tid, real(0), real(0), real(0), real(0), x, area, dt, my_min,
-                                     my_neg, bad);
+            // R = -0 / |K| = -0 for any area, so the area is not read
+            finish_cell<real, STAGE>(a, gid, sW + 4 * tid, real(0), real(0), real(0), real(0), x, real(1), dt,
+                                     my_min, my_neg, bad);
         }
         return;
     }
+    const bool zero_terms = DRY == 2 && skip;
 
     // B: face values of block + ring-1 cells (Sec. 2.4, Eq. recon with the
     // Barth-Jespersen limiter); every neighbour is in shared memory
-    for (int l = tid; l < B + n1; l += blockDim.x) {
+    for (int l = tid; l < (zero_terms ? ncell : B + n1); l += blockDim.x) {
         if (l < B && l >= ncell) continue;
         const int gid = sGid[l];
+        if (zero_terms) {
+            real wz[3] = {real(0), real(0), real(0)};
+            if (STAGE == 2) { wz[0] = a.w[gid]; wz[1] = a.w[nc + gid]; wz[2] = a.w[2 * nc + gid]; }
+#pragma unroll
+            for (int f = 0; f < 3; f++) st4(sF + 4 * (f * L1 + l), real(0), real(0), real(0), wz[f]);
+            continue;
+        }
         real WK, HuK, HvK, zK;
         ld4(sW + 4 * l, WK, HuK, HvK, zK);
         const real HK = ETA ? WK - zK : WK;
@@ -685,7 +702,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     // reads are used by no other face, so its thread overwrites them with the
     // two sides' terms l [Phi + P_s n_s] (the other side's flux and normal are
     // the exact negations, the face length the same).
-    const int nq = qcount;
+    const int nq = zero_terms ? 0 : qcount;
     for (int q = tid; q < nq; q += blockDim.x) {
         const int item = queue[q];
         const int l = item >> 2, f = item & 3;
@@ -748,11 +765,11 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     }
 }
 
-// The dry-land shortcut is compiled where it costs no register spills: in the
-// stage-1 kernels (FP32 and FP64) and the FP64 stage-2 kernel; the FP32 stage-2
-// kernel, at its 40-register budget, would spill with the second path.
-template <typename real, int STAGE> struct DrySkip { static constexpr bool value = true; };
-template <> struct DrySkip<float, 2> { static constexpr bool value = false; };
+// Dry-land shortcut of the single-scenario kernels: leave the block early
+// (mode 1) except in the FP32 stage-2 kernel, which at its 40-register budget
+// spills with that second exit and takes mode 2.  The batched kernels use mode 2.
+template <typename real, int STAGE> struct DryMode { static constexpr int value = 1; };
+template <> struct DryMode<float, 2> { static constexpr int value = 2; };
 
 // Resident CTAs per SM asked of the register allocator.  The FP32 kernels are
 // latency-bound: 40 registers a thread (a few spilled) and ~48 resident warps
@@ -783,7 +800,7 @@ __global__ void __launch_bounds__(MAXT, StageMinCtas<real, MAXT>::value) stage_k
 
     int parity = 0;
     for (int b = blockIdx.x; b < a.nblocks; b += gridDim.x, parity ^= 1)
-        process_block<real, STAGE, DrySkip<real, STAGE>::value>(a, b, dt, smem_raw, qcount[parity], my_min, my_neg,
+        process_block<real, STAGE, DryMode<real, STAGE>::value>(a, b, dt, smem_raw, qcount[parity], my_min, my_neg,
                                                                  bad);
 
     // CTA-level reductions, then one atomic per CTA
@@ -874,7 +891,7 @@ __global__ void __launch_bounds__(256, (StageMinCtas<real, 256>::value)) batch_s
             a.sc += s;
             const int e = bm.first_entry + s;
             real mn = real_inf<real>();
-            process_block<real, STAGE>(a, b, s_dt[e], smem_raw, qcount[parity], mn, my_neg, bad);
+            process_block<real, STAGE, 2>(a, b, s_dt[e], smem_raw, qcount[parity], mn, my_neg, bad);
             parity ^= 1;
             if (STAGE == 1) {
                 unsigned long long bits = warp_min_bits<real>(mn);
