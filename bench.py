@@ -14,8 +14,10 @@ One JSON line on rank 0:
                resident in HBM; the working set is ~5 GB, far above L2)
   e2e          the same metric through the public C ABI with host buffers:
                each step uploads the state from pinned host memory
-               (vg_set_state), advances one step and reads the state back
-               (vg_get_state)
+               (vg_set_state_f32 for the FP32 solver, vg_set_state for FP64),
+               advances one step and reads the state back (vg_get_state_f32 /
+               vg_get_state); the FP32 solver also reports the FP64 host
+               interface (f64_host)
   roofline     the dominant kernel's algorithmic bytes per launch over its
                CUDA-event duration, against the measured HBM copy bandwidth
   cpu_baseline the FP64 CPU oracle timed on this host on a bounded sample
@@ -475,27 +477,44 @@ def main():
                     "kernel_avg_ms": kernel_ms, "hbm_frac": round(achieved / peak, 4)}
 
     # ---- end to end through the C ABI with pinned host buffers
-    e2e = None
-    if args.e2e_steps > 0:
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    def end_to_end(host_dtype, steps):
+        """Seconds (max over ranks) for `steps` rounds of: state in from pinned host
+        arrays of host_dtype, one step, state out to pinned host arrays."""
+        fp32 = host_dtype == np.float32
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=host_dtype)).pin_memory().numpy()
         H, Hu, Hv, t_cur = sv.get_state()
         H, Hu, Hv = pin(H), pin(Hu), pin(Hv)
-        oH, oHu, oHv = (torch.empty(nc, dtype=torch.float64).pin_memory().numpy() for _ in range(3))
+        tdt = torch.float32 if fp32 else torch.float64
+        oH, oHu, oHv = (torch.empty(nc, dtype=tdt).pin_memory().numpy() for _ in range(3))
+        set_fn = volna.vg_set_state_f32 if fp32 else volna.vg_set_state
+        get_fn = volna.vg_get_state_f32 if fp32 else volna.vg_get_state
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            volna.vg_set_state(sv.ctx, H, Hu, Hv, t_cur)
+        for _ in range(steps):
+            set_fn(sv.ctx, H, Hu, Hv, t_cur)
             sv.step(1)
-            _, _, _, t_cur = volna.vg_get_state(sv.ctx, nc, out=(oH, oHu, oHv))
+            _, _, _, t_cur = get_fn(sv.ctx, nc, out=(oH, oHu, oHv))
             H, oH = oH, H
             Hu, oHu = oHu, Hu
             Hv, oHv = oHv, Hv
         torch.cuda.synchronize()
-        el = max_over_ranks(time.perf_counter() - t0, "cuda")
+        return max_over_ranks(time.perf_counter() - t0, "cuda")
+
+    e2e = None
+    if args.e2e_steps > 0:
+        # host arrays in the arithmetic's own precision (FP32 state <-> FP32 host
+        # arrays loses nothing); the FP64 host interface is reported beside it
+        host = np.float32 if args.precision == 32 else np.float64
+        esz = np.dtype(host).itemsize
+        el = end_to_end(host, args.e2e_steps)
         e2e = {"value": replica_throughput(nc, args.e2e_steps, el * 1e3, ws), "unit": UNIT,
-               "h2d_bytes_per_step": 3 * 8 * nc, "d2h_bytes_per_step": 3 * 8 * nc,
-               "steps": args.e2e_steps}
+               "h2d_bytes_per_step": 3 * esz * nc, "d2h_bytes_per_step": 3 * esz * nc,
+               "steps": args.e2e_steps, "host_dtype": np.dtype(host).name}
+        if args.precision == 32:
+            el64 = end_to_end(np.float64, args.e2e_steps)
+            e2e["f64_host"] = {"value": replica_throughput(nc, args.e2e_steps, el64 * 1e3, ws),
+                               "h2d_bytes_per_step": 24 * nc, "d2h_bytes_per_step": 24 * nc}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

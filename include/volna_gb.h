@@ -142,6 +142,7 @@ int vg_get_params(vg_ctx *ctx, vg_params *p);
  * arrays of nc values in the original cell order (converted to the context's
  * precision).  Depths must be finite and >= 0 (VG_EINVAL otherwise).  Clears
  * the gauge record and, if gauges are set, records eta = H + z at t.
+ * Page-locked (pinned) buffers are read in place by the import kernel.
  */
 int vg_set_state(vg_ctx *ctx, const double *H, const double *Hu, const double *Hv, double t);
 
@@ -151,6 +152,19 @@ int vg_set_state_dev(vg_ctx *ctx, const void *H, const void *Hu, const void *Hv,
 
 /* Copy the state out to host FP64 arrays in the original order; *t may be NULL. */
 int vg_get_state(vg_ctx *ctx, double *H, double *Hu, double *Hv, double *t);
+
+/*
+ * vg_set_state / vg_get_state with host FP32 arrays (nc values each, original
+ * cell order), half the bytes over the CPU-GPU link.  An FP32 context loses
+ * nothing by it: vg_get_state_f32 returns exactly the FP32 rounding of what
+ * vg_get_state returns (H is formed in FP64 from the stored eta and bed, then
+ * rounded once).  An FP64 context widens the inputs and rounds the outputs.
+ * Page-locked (pinned) buffers are read or written in place by the import /
+ * export kernels; pageable ones go through a device staging copy.  Errors as
+ * vg_set_state / vg_get_state.
+ */
+int vg_set_state_f32(vg_ctx *ctx, const float *H, const float *Hu, const float *Hv, double t);
+int vg_get_state_f32(vg_ctx *ctx, float *H, float *Hu, float *Hv, double *t);
 
 /* Copy the state out to device arrays of the context's precision. */
 int vg_get_state_dev(vg_ctx *ctx, void *H, void *Hu, void *Hv);

@@ -145,38 +145,82 @@ __global__ void export_state_kernel(int64_t nc, const int32_t *old_of_new, const
     }
 }
 
-// The same two conversions with one thread per ORIGINAL cell o (k =
-// new_of_old[o]): the host-order arrays are read or written contiguously, so
-// they can be pinned host memory that the kernel reads or writes in place over
-// the CPU-GPU link (the internal-order side is scattered in HBM instead).
+// The same two conversions with one thread per V consecutive ORIGINAL cells o
+// (k = new_of_old[o]): the host-order arrays are read or written contiguously,
+// 16 bytes per thread and array (V = 4 floats or 2 doubles), so they can be
+// pinned host memory that the kernel reads or writes in place over the CPU-GPU
+// link (the internal-order side is scattered in HBM instead).  vec = false (a
+// host array not 16-byte aligned) takes every cell one at a time.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+
+template <typename real, typename src_t>
+__device__ __forceinline__ void import_one(int64_t nc, int64_t k, src_t h, src_t hu, src_t hv, const double *z,
+                                           real *w, bool &bad)
+{
+    if (!(h >= src_t(0)) || !isfinite(h) || !isfinite(hu) || !isfinite(hv)) bad = true;
+    w[k] = EtaForm<real>::value ? (real)((double)h + (double)z[k]) : (real)h;
+    w[nc + k] = (real)hu;
+    w[2 * nc + k] = (real)hv;
+}
+
 template <typename real, typename src_t>
 __global__ void import_state_orig_kernel(int64_t nc, const int32_t *new_of_old, const src_t *H, const src_t *Hu,
-                                         const src_t *Hv, const double *z, real *w, DevScalars *sc)
+                                         const src_t *Hv, const double *z, real *w, DevScalars *sc, bool vec)
 {
+    constexpr int V = 16 / sizeof(src_t);
+    using vt = typename Vec16<src_t>::type;
     bool bad = false;
-    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < nc; o += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = new_of_old[o];
-        src_t h = H[o], hu = Hu[o], hv = Hv[o];
-        if (!(h >= src_t(0)) || !isfinite(h) || !isfinite(hu) || !isfinite(hv)) bad = true;
-        w[k] = EtaForm<real>::value ? (real)((double)h + (double)z[k]) : (real)h;
-        w[nc + k] = (real)hu;
-        w[2 * nc + k] = (real)hv;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t ng = vec ? nc / V : 0;
+    for (int64_t gi = tid; gi < ng; gi += stride) {
+        const vt h = reinterpret_cast<const vt *>(H)[gi], hu = reinterpret_cast<const vt *>(Hu)[gi],
+                 hv = reinterpret_cast<const vt *>(Hv)[gi];
+        const src_t *ph = reinterpret_cast<const src_t *>(&h), *phu = reinterpret_cast<const src_t *>(&hu),
+                    *phv = reinterpret_cast<const src_t *>(&hv);
+#pragma unroll
+        for (int j = 0; j < V; j++)
+            import_one<real, src_t>(nc, new_of_old[gi * V + j], ph[j], phu[j], phv[j], z, w, bad);
     }
+    for (int64_t o = ng * V + tid; o < nc; o += stride)
+        import_one<real, src_t>(nc, new_of_old[o], H[o], Hu[o], Hv[o], z, w, bad);
     if (bad) atomicOr(&sc->flags, FLAG_BAD_INPUT);
+}
+
+// H of internal cell k in the destination type (the eta form is dry at eta <= z
+// in the kernels' own rounded bed, and then H is exactly 0).
+template <typename real, typename dst_t>
+__device__ __forceinline__ void export_one(int64_t nc, int64_t k, const real *w, const real *zr, const double *z,
+                                           dst_t &h, dst_t &hu, dst_t &hv)
+{
+    double x = (double)w[k];
+    if (EtaForm<real>::value) x = (w[k] - zr[k] <= real(0)) ? 0.0 : fmax(0.0, x - z[k]);
+    h = (dst_t)x;
+    hu = (dst_t)w[nc + k];
+    hv = (dst_t)w[2 * nc + k];
 }
 
 template <typename real, typename dst_t>
 __global__ void export_state_orig_kernel(int64_t nc, const int32_t *new_of_old, const real *w, const real *zr,
-                                         const double *z, dst_t *H, dst_t *Hu, dst_t *Hv)
+                                         const double *z, dst_t *H, dst_t *Hu, dst_t *Hv, bool vec)
 {
-    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < nc; o += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = new_of_old[o];
-        double h = (double)w[k];
-        if (EtaForm<real>::value) h = (w[k] - zr[k] <= real(0)) ? 0.0 : fmax(0.0, h - z[k]);
-        H[o] = (dst_t)h;
-        Hu[o] = (dst_t)w[nc + k];
-        Hv[o] = (dst_t)w[2 * nc + k];
+    constexpr int V = 16 / sizeof(dst_t);
+    using vt = typename Vec16<dst_t>::type;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t ng = vec ? nc / V : 0;
+    for (int64_t gi = tid; gi < ng; gi += stride) {
+        vt h, hu, hv;
+        dst_t *ph = reinterpret_cast<dst_t *>(&h), *phu = reinterpret_cast<dst_t *>(&hu),
+              *phv = reinterpret_cast<dst_t *>(&hv);
+#pragma unroll
+        for (int j = 0; j < V; j++) export_one<real, dst_t>(nc, new_of_old[gi * V + j], w, zr, z, ph[j], phu[j], phv[j]);
+        reinterpret_cast<vt *>(H)[gi] = h;
+        reinterpret_cast<vt *>(Hu)[gi] = hu;
+        reinterpret_cast<vt *>(Hv)[gi] = hv;
     }
+    for (int64_t o = ng * V + tid; o < nc; o += stride)
+        export_one<real, dst_t>(nc, new_of_old[o], w, zr, z, H[o], Hu[o], Hv[o]);
 }
 
 constexpr int DIAG_BLOCKS = 1024;
@@ -279,27 +323,49 @@ int launch_import_state(const DevPtrs &d, const int32_t *old_of_new, const void 
     return (int)cudaGetLastError();
 }
 
-int launch_import_state_orig(const DevPtrs &d, const int32_t *new_of_old, const double *H, const double *Hu,
-                             const double *Hv, void *w, int precision, void *stream)
+static bool aligned16(const void *a, const void *b, const void *c)
+{
+    return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(c)) & 15) == 0;
+}
+
+int launch_import_state_orig(const DevPtrs &d, const int32_t *new_of_old, const void *H, const void *Hu,
+                             const void *Hv, int src_is_double, void *w, int precision, void *stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int grid = grid_for(d.nc);
-    if (precision == 64)
-        import_state_orig_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, H, Hu, Hv, d.z64, (double *)w, d.sc);
-    else
-        import_state_orig_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, H, Hu, Hv, d.z64, (float *)w, d.sc);
+    const double *z = d.z64;
+    const bool vec = aligned16(H, Hu, Hv);
+    if (precision == 64) {
+        if (src_is_double)
+            import_state_orig_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const double *)H, (const double *)Hu, (const double *)Hv, z, (double *)w, d.sc, vec);
+        else
+            import_state_orig_kernel<double, float><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const float *)H, (const float *)Hu, (const float *)Hv, z, (double *)w, d.sc, vec);
+    } else {
+        if (src_is_double)
+            import_state_orig_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const double *)H, (const double *)Hu, (const double *)Hv, z, (float *)w, d.sc, vec);
+        else
+            import_state_orig_kernel<float, float><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const float *)H, (const float *)Hu, (const float *)Hv, z, (float *)w, d.sc, vec);
+    }
     return (int)cudaGetLastError();
 }
 
-int launch_export_state_orig(const DevPtrs &d, const int32_t *new_of_old, const void *w, int precision, double *H,
-                             double *Hu, double *Hv, void *stream)
+int launch_export_state_orig(const DevPtrs &d, const int32_t *new_of_old, const void *w, int precision, void *H,
+                             void *Hu, void *Hv, int dst_is_double, void *stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int grid = grid_for(d.nc);
-    if (precision == 64)
-        export_state_orig_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const double *)w, (const double *)d.z, d.z64, H, Hu, Hv);
-    else
-        export_state_orig_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const float *)w, (const float *)d.z, d.z64, H, Hu, Hv);
+    const bool vec = aligned16(H, Hu, Hv);
+    if (precision == 64) {
+        if (dst_is_double)
+            export_state_orig_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const double *)w, (const double *)d.z, d.z64, (double *)H, (double *)Hu, (double *)Hv, vec);
+        else
+            export_state_orig_kernel<double, float><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const double *)w, (const double *)d.z, d.z64, (float *)H, (float *)Hu, (float *)Hv, vec);
+    } else {
+        if (dst_is_double)
+            export_state_orig_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const float *)w, (const float *)d.z, d.z64, (double *)H, (double *)Hu, (double *)Hv, vec);
+        else
+            export_state_orig_kernel<float, float><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const float *)w, (const float *)d.z, d.z64, (float *)H, (float *)Hu, (float *)Hv, vec);
+    }
     return (int)cudaGetLastError();
 }
 

@@ -200,10 +200,10 @@ int launch_export_state(const DevPtrs &d, const int32_t *old_of_new, const void 
 // The same from / to FP64 arrays in host order that the kernel may access in
 // place (device memory or mapped pinned host memory), one thread per original
 // cell: contiguous on the host-order side.
-int launch_import_state_orig(const DevPtrs &d, const int32_t *new_of_old, const double *H, const double *Hu,
-                             const double *Hv, void *w, int precision, void *stream);
-int launch_export_state_orig(const DevPtrs &d, const int32_t *new_of_old, const void *w, int precision, double *H,
-                             double *Hu, double *Hv, void *stream);
+int launch_import_state_orig(const DevPtrs &d, const int32_t *new_of_old, const void *H, const void *Hu,
+                             const void *Hv, int src_is_double, void *w, int precision, void *stream);
+int launch_export_state_orig(const DevPtrs &d, const int32_t *new_of_old, const void *w, int precision, void *H,
+                             void *Hu, void *Hv, int dst_is_double, void *stream);
 // No-allocation step scratch (noalloc.cu): the device address and size of the
 // file-scope scratch array on `device`, and the kernel that clears its scalars.
 int noalloc_scratch(int device, void **addr, size_t *bytes);

@@ -51,6 +51,7 @@ class vg_diag(C.Structure):
 
 
 _D = C.POINTER(C.c_double)
+_F = C.POINTER(C.c_float)
 _I32 = C.POINTER(C.c_int32)
 _I64 = C.POINTER(C.c_int64)
 _V = C.c_void_p
@@ -71,6 +72,8 @@ _SIGNATURES = {
     "vg_set_state": ([_V, _D, _D, _D, C.c_double], C.c_int),
     "vg_set_state_dev": ([_V, _V, _V, _V, C.c_double], C.c_int),
     "vg_get_state": ([_V, _D, _D, _D, _D], C.c_int),
+    "vg_set_state_f32": ([_V, _F, _F, _F, C.c_double], C.c_int),
+    "vg_get_state_f32": ([_V, _F, _F, _F, _D], C.c_int),
     "vg_get_state_dev": ([_V, _V, _V, _V], C.c_int),
     "vg_set_gauges": ([_V, C.c_int32, _D], C.c_int),
     "vg_get_gauge_cells": ([_V, _I32], C.c_int),
@@ -145,6 +148,14 @@ def _f64(a) -> np.ndarray:
 
 def _dp(a: np.ndarray):
     return a.ctypes.data_as(_D)
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _fp(a: np.ndarray):
+    return a.ctypes.data_as(_F)
 
 
 # ---------------------------------------------------------------- one-to-one entry points
@@ -224,8 +235,25 @@ def vg_set_state_dev(ctx, H_ptr: int, Hu_ptr: int, Hv_ptr: int, t=0.0) -> None:
 def vg_get_state(ctx, nc: int, out=None):
     if out is None:
         out = (np.empty(nc), np.empty(nc), np.empty(nc))
+    if any(o.dtype != np.float64 or not o.flags.c_contiguous or o.size != nc for o in out):
+        raise ValueError("out must be three contiguous float64 arrays of nc values")
     t = C.c_double()
     _check(ctx, load().vg_get_state(ctx, _dp(out[0]), _dp(out[1]), _dp(out[2]), C.byref(t)))
+    return out[0], out[1], out[2], t.value
+
+
+def vg_set_state_f32(ctx, H, Hu, Hv, t=0.0) -> None:
+    H, Hu, Hv = _f32(H), _f32(Hu), _f32(Hv)
+    _check(ctx, load().vg_set_state_f32(ctx, _fp(H), _fp(Hu), _fp(Hv), float(t)))
+
+
+def vg_get_state_f32(ctx, nc: int, out=None):
+    if out is None:
+        out = tuple(np.empty(nc, dtype=np.float32) for _ in range(3))
+    if any(o.dtype != np.float32 or not o.flags.c_contiguous or o.size != nc for o in out):
+        raise ValueError("out must be three contiguous float32 arrays of nc values")
+    t = C.c_double()
+    _check(ctx, load().vg_get_state_f32(ctx, _fp(out[0]), _fp(out[1]), _fp(out[2]), C.byref(t)))
     return out[0], out[1], out[2], t.value
 
 
@@ -384,12 +412,17 @@ class Solver:
             H, Hu, Hv = (x.to(dt).contiguous() for x in (H, Hu, Hv))
             vg_set_state_dev(self.ctx, H.data_ptr(), Hu.data_ptr(), Hv.data_ptr(), t)
             self._keep = (H, Hu, Hv)
+        elif all(getattr(x, "dtype", None) == np.float32 for x in (H, Hu, Hv)):
+            vg_set_state_f32(self.ctx, H, Hu, Hv, t)
         else:
             vg_set_state(self.ctx, H, Hu, Hv, t)
 
-    def get_state(self):
-        """(H, Hu, Hv, t) as float64 numpy arrays in the original cell order."""
-        return vg_get_state(self.ctx, self.nc)
+    def get_state(self, dtype=np.float64, out=None):
+        """(H, Hu, Hv, t) as numpy arrays (float64, or float32 through the FP32
+        host interface) in the original cell order."""
+        if np.dtype(dtype) == np.float32:
+            return vg_get_state_f32(self.ctx, self.nc, out)
+        return vg_get_state(self.ctx, self.nc, out)
 
     def get_state_dev(self, out=None):
         import torch

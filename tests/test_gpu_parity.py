@@ -302,3 +302,76 @@ def test_pinned_host_buffers_are_used_in_place(thacker, precision):
         for x, y in zip(outs, ref[:3]):
             np.testing.assert_array_equal(x, y)
         assert ta == ref[3]
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_fp32_host_interface(thacker, precision):
+    """vg_set_state_f32 / vg_get_state_f32: FP32 host arrays (pinned: read and
+    written in place; pageable: staged) store exactly the state that FP64 host
+    arrays of the same values store, and the FP32 export is the FP32 rounding of
+    the FP64 export, bit for bit."""
+    torch = pytest.importorskip("torch")
+    m, s = thacker
+    f32 = [np.ascontiguousarray(x, dtype=np.float32) for x in (s.H, s.Hu, s.Hv)]
+    pin = lambda a: torch.from_numpy(a.copy()).pin_memory().numpy()
+    with volna.Solver(precision) as a, volna.Solver(precision) as b, volna.Solver(precision) as c:
+        for sv in (a, b, c):
+            sv.set_params(h_threshold=1e-5)
+            sv.upload_mesh(m)
+        volna.vg_set_state_f32(a.ctx, *[pin(x) for x in f32], 0.0)
+        c.set_state(*f32, 0.0)                          # pageable FP32: staged
+        b.set_state(*[x.astype(np.float64) for x in f32], 0.0)
+        for sv in (a, b, c):
+            sv.step(7)
+        ref = b.get_state()
+        outs = tuple(torch.empty(m.nc, dtype=torch.float32).pin_memory().numpy() for _ in range(3))
+        got_pinned = volna.vg_get_state_f32(a.ctx, m.nc, out=outs)
+        got_paged = c.get_state(np.float32)
+        for got in (got_pinned, got_paged):
+            for x, y in zip(got[:3], ref[:3]):
+                assert x.dtype == np.float32
+                np.testing.assert_array_equal(x, y.astype(np.float32))
+            assert got[3] == ref[3]
+        # pinned views off the 16-byte grid take the one-cell-per-thread path
+        def pin_off(x):
+            buf = torch.empty(x.size + 1, dtype=torch.from_numpy(x).dtype).pin_memory().numpy()
+            buf[1:] = x
+            return buf[1:]
+        for dt in (np.float32, np.float64):
+            src = [pin_off(x.astype(dt)) for x in f32]
+            (volna.vg_set_state_f32 if dt == np.float32 else volna.vg_set_state)(a.ctx, *src, 0.0)
+            a.step(7)
+            out = tuple(pin_off(np.zeros(m.nc, dtype=dt)) for _ in range(3))
+            got = (volna.vg_get_state_f32 if dt == np.float32 else volna.vg_get_state)(a.ctx, m.nc, out=out)
+            for x, y in zip(got[:3], ref[:3]):
+                np.testing.assert_array_equal(x, y.astype(dt))
+        bad = f32[0].copy()
+        bad[3] = -1.0
+        with pytest.raises(volna.VolnaError):
+            volna.vg_set_state_f32(a.ctx, bad, f32[1], f32[2], 0.0)
+        with pytest.raises(ValueError):
+            volna.vg_get_state_f32(a.ctx, m.nc, out=tuple(np.empty(m.nc) for _ in range(3)))
+
+
+def test_fp32_host_interface_ragged_tail():
+    """A cell count that is not a multiple of 4 (5202 triangles): the last cells
+    after the 16-byte groups of the in-place import / export are still moved."""
+    torch = pytest.importorskip("torch")
+    m = I.thacker_mesh(n=51)
+    s = I.thacker_initial_state(m)
+    assert m.nc % 4 == 2
+    f32 = [np.ascontiguousarray(x, dtype=np.float32) for x in (s.H, s.Hu, s.Hv)]
+    pin = lambda a: torch.from_numpy(a.copy()).pin_memory().numpy()
+    with volna.Solver(32) as a, volna.Solver(32) as b:
+        for sv in (a, b):
+            sv.set_params(h_threshold=1e-5)
+            sv.upload_mesh(m)
+        volna.vg_set_state_f32(a.ctx, *[pin(x) for x in f32], 0.0)
+        b.set_state(*[x.astype(np.float64) for x in f32], 0.0)
+        a.step(3)
+        b.step(3)
+        ref = b.get_state()
+        out = tuple(torch.empty(m.nc, dtype=torch.float32).pin_memory().numpy() for _ in range(3))
+        got = volna.vg_get_state_f32(a.ctx, m.nc, out=out)
+        for x, y in zip(got[:3], ref[:3]):
+            np.testing.assert_array_equal(x, y.astype(np.float32))
