@@ -41,8 +41,8 @@ struct vg_ctx {
     void *geo = nullptr, *z = nullptr, *w[2] = {nullptr, nullptr}, *R0 = nullptr;
     double *z64 = nullptr;
     int32_t *nbr = nullptr, *halo_ptr = nullptr, *halo_n1 = nullptr, *halo_ids = nullptr, *old_of_new = nullptr;
-    int32_t *new_of_old = nullptr;
-    uint16_t *nbrl = nullptr, *ring1_nbr = nullptr;
+    int32_t *new_of_old = nullptr, *fq_ptr = nullptr;
+    uint16_t *nbrl = nullptr, *ring1_nbr = nullptr, *fq = nullptr;
     DevScalars *sc = nullptr;
     int32_t *gauge_cells = nullptr;
     double *ring_t = nullptr, *ring_eta = nullptr;
@@ -146,7 +146,7 @@ void free_mesh(vg_ctx *c)
     if (c->z64 == c->z) c->z64 = nullptr;
     dfree(c->geo); dfree(c->z); dfree(c->z64); dfree(c->w[0]); dfree(c->w[1]); dfree(c->R0);
     dfree(c->nbr); dfree(c->halo_ptr); dfree(c->halo_n1); dfree(c->halo_ids); dfree(c->ring1_nbr);
-    dfree(c->old_of_new); dfree(c->new_of_old); dfree(c->nbrl);
+    dfree(c->old_of_new); dfree(c->new_of_old); dfree(c->nbrl); dfree(c->fq_ptr); dfree(c->fq);
     dfree(c->gauge_cells); dfree(c->ring_t); dfree(c->ring_eta); dfree(c->staging);
     dfree(c->bed_vtx); dfree(c->bed_depth0); dfree(c->bed_uplift); dfree(c->bed_onset);
     c->bed_on = false;
@@ -194,6 +194,8 @@ DevPtrs dev_ptrs(const vg_ctx *c)
     d.halo_n1 = c->halo_n1;
     d.halo_ids = c->halo_ids;
     d.ring1_nbr = c->ring1_nbr;
+    d.fq_ptr = c->fq_ptr;
+    d.fq = c->fq;
     d.R0 = c->R0;
     d.sc = c->sc;
     d.gauge_cells = c->gauge_cells;
@@ -234,8 +236,13 @@ int upload_partition(vg_ctx *c)
 {
     const HostMesh &m = c->hm;
     dfree(c->halo_ptr); dfree(c->halo_n1); dfree(c->halo_ids); dfree(c->ring1_nbr); dfree(c->nbrl);
+    dfree(c->fq_ptr); dfree(c->fq);
     int rc;
     size_t nh = std::max<size_t>(1, m.halo_ids.size());
+    if ((rc = dmalloc(c, (void **)&c->fq_ptr, 4 * (m.nblocks + 1)))) return rc;
+    if ((rc = dmalloc(c, (void **)&c->fq, 2 * m.fq.size()))) return rc;
+    VG_CUDA(c, cudaMemcpy(c->fq_ptr, m.fq_ptr.data(), 4 * (m.nblocks + 1), cudaMemcpyHostToDevice));
+    VG_CUDA(c, cudaMemcpy(c->fq, m.fq.data(), 2 * m.fq.size(), cudaMemcpyHostToDevice));
     if ((rc = dmalloc(c, (void **)&c->nbrl, 2 * 3 * m.nc))) return rc;
     if ((rc = dmalloc(c, (void **)&c->halo_ptr, 4 * (m.nblocks + 1)))) return rc;
     if ((rc = dmalloc(c, (void **)&c->halo_n1, 4 * m.nblocks))) return rc;

@@ -400,6 +400,33 @@ int partition_blocks(HostMesh &m, int block, std::string &err)
             }
     }
     m.nbrl.swap(nbrl);
+    // Owned faces of each block, in cell-then-face order: a face on the domain
+    // boundary, a face to the halo, or a face to a block cell of higher local
+    // index (so every face of the block is computed once).  Only the face's
+    // kind matters, so switching a boundary face between wall and open keeps it.
+    m.fq_ptr.assign(nb + 1, 0);
+    auto owned = [&](int64_t c, int64_t c0, int f) {
+        const uint16_t code = m.nbrl[f * nc + c];
+        return code >= NBR_OPEN || (code >> 2) >= block || (int64_t)(code >> 2) > c - c0;
+    };
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int32_t b = 0; b < nb; b++) {
+        int64_t c0 = (int64_t)b * block, c1 = std::min<int64_t>(c0 + block, nc);
+        int32_t n = 0;
+        for (int64_t c = c0; c < c1; c++)
+            for (int f = 0; f < 3; f++) n += owned(c, c0, f);
+        m.fq_ptr[b + 1] = n;
+    }
+    for (int32_t b = 0; b < nb; b++) m.fq_ptr[b + 1] += m.fq_ptr[b];
+    m.fq.resize(std::max<int32_t>(m.fq_ptr[nb], 1));
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int32_t b = 0; b < nb; b++) {
+        int64_t c0 = (int64_t)b * block, c1 = std::min<int64_t>(c0 + block, nc);
+        int32_t k = m.fq_ptr[b];
+        for (int64_t c = c0; c < c1; c++)
+            for (int f = 0; f < 3; f++)
+                if (owned(c, c0, f)) m.fq[k++] = (uint16_t)(((c - c0) << 2) | f);
+    }
     return VG_OK;
 }
 

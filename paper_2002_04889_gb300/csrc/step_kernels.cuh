@@ -15,7 +15,8 @@
 // block plus a two-ring halo in shared memory (ring 1: face neighbours of the
 // block; ring 2: face neighbours of ring 1), with local indices precomputed on
 // the host so that no phase chases an index through global memory:
-//   A  load the state of block + ring-1 + ring-2 cells  (smem  sH, sHu, sHv, sz)
+//   A  load the state of block + ring-1 + ring-2 cells and the block's list of
+//      owned faces (built with the partition)         (smem  sH, sHu, sHv, sz)
 //   B  reconstruct face values of block + ring-1 cells  (smem  fH, fHu, fHv)
 //   C  one thread per owned face computes the interface flux once
 //      (a face is owned by the lower local index, a block cell facing the
@@ -56,6 +57,8 @@ struct KArgs {
     const int32_t *halo_n1;   // [nblocks] ring-1 count
     const int32_t *halo_ids;  // per block: ring 1 then ring 2
     const uint16_t *ring1_nbr;// [3 * ring cells] local neighbours of ring-1 cells
+    const int32_t *fq_ptr;  // [nblocks + 1] into fq
+    const uint16_t *fq;     // owned faces of each block: (local cell << 2) | face
     const real *w;          // w^n [3][nc]
     real *R0;               // [3][nc]
     real *wout;             // w^{n+1} [3][nc] (stage 2)
@@ -430,22 +433,30 @@ __host__ __device__ inline size_t stage_smem_bytes(int block, int max_halo, int 
 
 // One block of cells for one scenario: phases A-D (see the top of this file).
 // my_min collects the thread's stage-1 CFL bound, my_neg its negative-depth
-// events, bad a non-finite result.  Every thread of the CTA must call it, and
-// qcount must be zero on entry (it is zero again after phase D).
+// events, bad a non-finite result.  Every thread of the CTA must call it;
+// qcount is the CTA's shared count of queued faces.
+//
+// The queue of owned faces is copied from the list built with the partition
+// (LISTED) or formed in phase A from the face codes by a warp-aggregated
+// append; the list is faster in the stage-2 kernels and the batched kernels,
+// the append in the single-scenario stage-1 kernels.
+// Either way every face of the block is queued once, and the result does not
+// depend on the queue order (each face writes its own two slots).
 //
 // There is no barrier after phase D: a thread's phase D reads only its own
 // cell's state slot and face slots, the next block's phase A writes state
-// slots of its own cells only, and face slots are next written in phase B,
-// behind the barrier that ends phase A.  Consecutive blocks therefore use the
-// two queue counters alternately (the reset of one in phase D may come after
-// other warps have started the next block).
+// slots of its own cells, codes, the face queue and its count only, and face
+// slots are next written in phase B, behind the barrier that ends phase A.
+// Consecutive blocks use the two queue counters alternately (an append's
+// counter is reset in phase D, which may come after other warps have started
+// the next block).
 //
 // Shared layout: sW[l] = (W, Hu, Hv, z) of local cell l (W = eta for FP32, H
 // for FP64); sF[f][l] = face values (W_f, Hu_f, Hv_f, x) of face f of cell l
 // after phase B, and after phase C the cell's own term
 // (l_f Phi_0, l_f (Phi_1 + P n_x), l_f (Phi_2 + P n_y), x); x is l_f a_f in
 // stage 1 and, for block cells in stage 2, component f of w^n.
-template <typename real, int STAGE, int DRY>
+template <typename real, int STAGE, int DRY, bool LISTED>
 __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b, const real dt,
                                               unsigned char *smem_raw, int &qcount, real &my_min,
                                               long long &my_neg, bool &bad)
@@ -471,10 +482,10 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     const int nh = a.halo_ptr[b + 1] - h0;
     const int n1 = a.halo_n1[b];
 
-    // A: block + ring-1 + ring-2 states into shared memory.  Thread tid < B
-    // takes block cell tid and queues the faces that cell owns: a wall, a face
-    // to the halo, or a face to a block cell of higher local index.  It also
-    // notes whether the block and its ring 1 are exactly dry (dry land): then
+    // A: block + ring-1 + ring-2 states into shared memory, and the block's
+    // owned faces (a boundary face, a face to the halo, or a face to a block
+    // cell of higher local index: every face once) into the queue.  Thread
+    // tid < B takes block cell tid and notes whether the block and its ring 1 are exactly dry (dry land): then
     // every face of the block has zero interface depths on both sides, hence
     // zero flux and zero pressure terms, and phases B and C reduce to zero
     // face terms.
@@ -482,6 +493,11 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     {
         int gh = -1;
         if (tid < nh) gh = a.halo_ids[h0 + tid];
+        if constexpr (LISTED) {
+            const int q0 = a.fq_ptr[b], nq = a.fq_ptr[b + 1] - q0;
+            for (int q = tid; q < nq; q += blockDim.x) queue[q] = a.fq[q0 + q];
+            if (tid == 0) qcount = nq;
+        }
         int owned = 0;
         if (tid < ncell) {
             const int gid = c0 + tid;
@@ -489,7 +505,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             for (int f = 0; f < 3; f++) {
                 const uint16_t code = a.nbrl[f * nc + gid];
                 sCode[f * B + tid] = code;
-                if (code >= NBR_OPEN || (code >> 2) >= B || (int)(code >> 2) > tid) owned |= 1 << f;
+                if (!LISTED && (code >= NBR_OPEN || (code >> 2) >= B || (int)(code >> 2) > tid)) owned |= 1 << f;
             }
             real W, Hu, Hv, zc;
             bool neg = stage_cell<real, STAGE>(a, gid, dt, W, Hu, Hv, zc);
@@ -517,19 +533,21 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
                 dry = dry && exactly_dry(W, Hu, Hv, zc);
             }
         }
-        // warp-aggregated queue append: n = popcount(owned) in 0..3
-        const int n = __popc(owned);
-        const unsigned lane = tid & 31;
-        const unsigned lt = (1u << lane) - 1u;
-        const unsigned b1 = __ballot_sync(0xffffffffu, n & 1), b2 = __ballot_sync(0xffffffffu, n & 2);
-        const int total = __popc(b1) + 2 * __popc(b2);
-        int base = 0;
-        if (lane == 0 && total) base = atomicAdd(&qcount, total);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        int pos = base + __popc(b1 & lt) + 2 * __popc(b2 & lt);
+        if constexpr (!LISTED) {
+            // warp-aggregated queue append: n = popcount(owned) in 0..3
+            const int n = __popc(owned);
+            const unsigned lane = tid & 31;
+            const unsigned lt = (1u << lane) - 1u;
+            const unsigned b1 = __ballot_sync(0xffffffffu, n & 1), b2 = __ballot_sync(0xffffffffu, n & 2);
+            const int total = __popc(b1) + 2 * __popc(b2);
+            int base = 0;
+            if (lane == 0 && total) base = atomicAdd(&qcount, total);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            int pos = base + __popc(b1 & lt) + 2 * __popc(b2 & lt);
 #pragma unroll
-        for (int f = 0; f < 3; f++)
-            if ((owned >> f) & 1) queue[pos++] = (uint16_t)((tid << 2) | f);
+            for (int f = 0; f < 3; f++)
+                if ((owned >> f) & 1) queue[pos++] = (uint16_t)((tid << 2) | f);
+        }
     }
     // Dry land (runs with recordings for the adjoint take every phase).  Mode 1
     // leaves the block here with a zero residual (phase D with zero face terms;
@@ -542,7 +560,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     else
         skip = __syncthreads_and(dry) && !a.fv_out && !a.mask2 && !a.r1_out;
     if (DRY == 1 && skip) {
-        if (tid == 0) qcount = 0;
+        if (!LISTED && tid == 0) qcount = 0;
         if (tid < ncell) {
             const int gid = c0 + tid;
             real x[3] = {real(0), real(0), real(0)};
@@ -745,7 +763,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     __syncthreads();
 
     // D: residual R_K = -(1/|K|) sum_f l_f [Phi_f + (0, P_{K,f} n_f)], faces in local order
-    if (tid == 0) qcount = 0;     // every thread read it before the barrier above
+    if (!LISTED && tid == 0) qcount = 0;     // every thread read it before the barrier above
     if (tid < ncell) {
         const int l = tid;
         const int gid = c0 + l;
@@ -800,8 +818,8 @@ __global__ void __launch_bounds__(MAXT, StageMinCtas<real, MAXT>::value) stage_k
 
     int parity = 0;
     for (int b = blockIdx.x; b < a.nblocks; b += gridDim.x, parity ^= 1)
-        process_block<real, STAGE, DryMode<real, STAGE>::value>(a, b, dt, smem_raw, qcount[parity], my_min, my_neg,
-                                                                 bad);
+        process_block<real, STAGE, DryMode<real, STAGE>::value, STAGE == 2>(a, b, dt, smem_raw, qcount[parity], my_min,
+                                                                              my_neg, bad);
 
     // CTA-level reductions, then one atomic per CTA
     const int lane = tid & 31, warp = tid >> 5, nwarps = (blockDim.x + 31) >> 5;
@@ -891,7 +909,7 @@ __global__ void __launch_bounds__(256, (StageMinCtas<real, 256>::value)) batch_s
             a.sc += s;
             const int e = bm.first_entry + s;
             real mn = real_inf<real>();
-            process_block<real, STAGE, 2>(a, b, s_dt[e], smem_raw, qcount[parity], mn, my_neg, bad);
+            process_block<real, STAGE, 2, true>(a, b, s_dt[e], smem_raw, qcount[parity], mn, my_neg, bad);
             parity ^= 1;
             if (STAGE == 1) {
                 unsigned long long bits = warp_min_bits<real>(mn);
@@ -984,6 +1002,8 @@ KArgs<real> make_args(const DevPtrs &d, const StepParams &p, const void *w_in, v
     a.halo_n1 = d.halo_n1;
     a.halo_ids = d.halo_ids;
     a.ring1_nbr = d.ring1_nbr;
+    a.fq_ptr = d.fq_ptr;
+    a.fq = d.fq;
     a.w = static_cast<const real *>(w_in);
     a.R0 = static_cast<real *>(d.R0);
     a.wout = static_cast<real *>(w_out);

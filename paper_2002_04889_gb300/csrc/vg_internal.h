@@ -47,6 +47,8 @@ struct HostMesh {
     std::vector<int32_t> halo_ids;       // per block: ring-1 then ring-2 cells (internal ids)
     std::vector<uint16_t> ring1_nbr;     // [3 * halo_ids.size()] local neighbour index of
                                          // each ring-1 cell (NBR_WALL / NBR_OPEN)
+    std::vector<int32_t> fq_ptr;         // [nblocks + 1] into fq
+    std::vector<uint16_t> fq;            // per block: its owned faces, (local cell << 2) | face
     std::vector<double> xy;              // [nv][2] copy for point location
 };
 
@@ -99,6 +101,8 @@ struct DevPtrs {
     const int32_t *halo_n1;
     const int32_t *halo_ids;
     const uint16_t *ring1_nbr;
+    const int32_t *fq_ptr;  // [nblocks + 1]
+    const uint16_t *fq;     // owned faces of each block
     void *R0;               // [3][nc] stage-1 residual (scratch)
     uint8_t *mask2;         // optional [nc]: stage-2 dry-fix branch per cell (adjoint)
     void *fv_out;           // optional [9][nc]: face values written by the stage kernels (adjoint)
