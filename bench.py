@@ -179,12 +179,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def kernel_source_sha() -> str:
+def code_digest(texts) -> str:
+    """sha1 (first 12 hex) of source texts with // comments and whitespace
+    removed, so that an edit of comments alone keeps the digest."""
     h = hashlib.sha1()
-    for f in ("step_kernels.cuh", "step_f32.cu", "step_f64.cu"):
-        with open(os.path.join(ROOT, "paper_2002_04889_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    for t in texts:
+        code = re.sub(r"//[^\n]*", "", t)
+        h.update("".join(code.split()).encode())
     return h.hexdigest()[:12]
+
+
+def kernel_source_sha() -> str:
+    texts = []
+    for f in ("step_kernels.cuh", "step_f32.cu", "step_f64.cu"):
+        with open(os.path.join(ROOT, "paper_2002_04889_gb300", "csrc", f)) as fh:
+            texts.append(fh.read())
+    return code_digest(texts)
 
 
 def profiled_traffic(workload: str, precision: int, kernel: str):

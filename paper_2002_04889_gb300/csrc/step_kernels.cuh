@@ -15,14 +15,17 @@
 // block plus a two-ring halo in shared memory (ring 1: face neighbours of the
 // block; ring 2: face neighbours of ring 1), with local indices precomputed on
 // the host so that no phase chases an index through global memory:
-//   A  load the state of block + ring-1 + ring-2 cells and the block's list of
-//      owned faces (built with the partition)         (smem  sH, sHu, sHv, sz)
-//   B  reconstruct face values of block + ring-1 cells  (smem  fH, fHu, fHv)
-//   C  one thread per owned face computes the interface flux once
-//      (a face is owned by the lower local index, a block cell facing the
-//      halo, or a wall)                                  (smem  owned-face slots)
+//   A  load the state of block + ring-1 + ring-2 cells (smem sW: packed
+//      (W, Hu, Hv, z) slots) and queue the block's owned faces (a face is owned
+//      by the lower local index, a block cell facing the halo, or a wall)
+//   B  reconstruct face values of block + ring-1 cells (smem sF: three packed
+//      face slots per cell)
+//   C  one thread per owned face computes the interface flux once and writes
+//      both sides' terms into the two face slots it read
 //   D  one thread per block cell gathers its three faces in local order,
 //      forms the residual and updates the cell.
+// A block whose cells and ring 1 are exactly dry has zero fluxes: B and C are
+// skipped for it (dry land).
 // No float atomics: the gather order is fixed, and the CFL minimum uses an
 // integer atomicMin on the bits of a non-negative value (exact, order-free).
 //
@@ -790,7 +793,7 @@ template <typename real, int STAGE> struct DryMode { static constexpr int value 
 template <> struct DryMode<float, 2> { static constexpr int value = 2; };
 
 // Resident CTAs per SM asked of the register allocator.  The FP32 kernels are
-// latency-bound: 40 registers a thread (a few spilled) and ~48 resident warps
+// latency-bound: 40 registers a thread (no spills in these kernels) and ~48 resident warps
 // beat fewer warps with more registers (6 CTAs of 256 threads: 40 registers;
 // 5: 48; unbounded: 63, 4 CTAs).  FP64 is left unbounded.
 template <typename real, int MAXT> struct StageMinCtas { static constexpr int value = 1; };
