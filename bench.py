@@ -4,7 +4,7 @@
 Workload (default): the 40M-triangle Thacker-type paraboloid basin -- the
 paper's Sec. 3 benchmark generator on a 4472 x 4472 jittered grid at
 dx = 0.04 m (178.9 m domain), cells emitted in scattered order and
-Morton-renumbered by the library, FP32, CFL 0.9, H_threshold 1e-5 m.
+Hilbert-renumbered by the library, FP32, CFL 0.9, H_threshold 1e-5 m.
 A step is one full SSP-RK(2,2) step (both stages, the CFL reduction and the
 epilogue) over all cells; the metric is cell-updates per second (one cell
 advanced one full step).
@@ -236,7 +236,7 @@ def cpu_baseline(budget_s: float = 15.0, n: int = 1414, workload: str = "thacker
                       f"generator (n={n}, dx=0.04 m), {el:.1f} s"}
 
 
-def batched_leg(torch, stream, steps: int, n_scen: int = 32):
+def batched_leg(torch, stream, steps: int, n_scen: int = 32, renumber: str = "hilbert"):
     """Config 4: 8 coast basins of 50k..2M triangles x n_scen scenarios (uplift
     amplitude U[1,5] m, orientation U[0,180) deg), FP32, all advanced together
     (one persistent launch per stage, graph replay, autotuned block size),
@@ -250,7 +250,7 @@ def batched_leg(torch, stream, steps: int, n_scen: int = 32):
     srcs = [I.ensemble_sources(k, n_scen) for k in range(len(meshes))]
     b = volna.Batch(32, device=torch.cuda.current_device(), stream=stream)
     b.set_params(h_threshold=1e-3, cfl=0.9)
-    ids = [b.add_mesh(m, n_scen) for m in meshes]
+    ids = [b.add_mesh(m, n_scen, renumber=renumber) for m in meshes]
     states = []
     for mid, m, src in zip(ids, meshes, srcs):
         st_m = []
@@ -281,7 +281,7 @@ def batched_leg(torch, stream, steps: int, n_scen: int = 32):
     for m in meshes:
         sv = volna.Solver(32, device=torch.cuda.current_device(), stream=stream)
         sv.set_params(h_threshold=1e-3, cfl=0.9, block_cells=block)
-        sv.upload_mesh(m)
+        sv.upload_mesh(m, renumber=renumber)
         solvers.append(sv)
     torch.cuda.synchronize()
     t_loop = 0.0
@@ -400,6 +400,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="thacker_paraboloid_40m", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--renumber", default="hilbert", choices=["none", "morton", "rcm", "hilbert"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -427,7 +428,7 @@ def main():
     stream = torch.cuda.Stream()
     sv = volna.Solver(precision=args.precision, device=torch.cuda.current_device(), stream=stream)
     sv.set_params(h_threshold=1e-5, cfl=0.9)
-    sv.upload_mesh(mesh, renumber="morton")
+    sv.upload_mesh(mesh, renumber=args.renumber)
     sv.set_state(st0.H, st0.Hu, st0.Hv, 0.0)
     nc = mesh.nc
     dev_gb = sv.device_bytes() / 1e9
@@ -533,7 +534,7 @@ def main():
     batched = adjoint = None
     if rank == 0 and args.batched_steps > 0:
         try:
-            batched = batched_leg(torch, stream, args.batched_steps)
+            batched = batched_leg(torch, stream, args.batched_steps, renumber=args.renumber)
         except Exception as e:             # reported, not fatal: the headline is the forward step
             batched = {"error": str(e)[:300]}
     if rank == 0 and args.adjoint_steps > 0:
@@ -547,7 +548,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
-                "config": {"workload": args.workload, "cells": nc, "renumber": "morton",
+                "config": {"workload": args.workload, "cells": nc, "renumber": args.renumber,
                            "block_cells": 256, "cfl": 0.9, "h_threshold": 1e-5,
                            "l2": "inputs larger than L2 (%.1f GB resident)" % dev_gb,
                            "parallelism": f"replicas x{ws}"},

@@ -47,6 +47,7 @@ extern "C" {
 #define VG_RENUMBER_NONE 0
 #define VG_RENUMBER_MORTON 1
 #define VG_RENUMBER_RCM 2
+#define VG_RENUMBER_HILBERT 3
 
 typedef struct vg_ctx vg_ctx;
 
@@ -119,7 +120,9 @@ const char *vg_last_error(vg_ctx *ctx);
  *   tri[nc][3]  vertex ids per triangle; clockwise triangles are reoriented
  *   depth_v[nv] depth at each vertex; each cell's bed is the mean of its three
  *   renumber    VG_RENUMBER_NONE / _MORTON (Z-order of centroids) / _RCM
- *               (reverse Cuthill-McKee on the face graph)
+ *               (reverse Cuthill-McKee on the face graph) / _HILBERT
+ *               (Hilbert-curve order of centroids: compact blocks, the
+ *               smallest halos of the four)
  * Every edge must belong to one or two triangles; one-triangle edges are walls
  * (Sec. 2.5).  Returns VG_EINVAL for an out-of-range or repeated vertex id, a
  * zero-area triangle or a non-manifold edge.  Replaces any previous mesh and

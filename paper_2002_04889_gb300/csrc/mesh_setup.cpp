@@ -1,5 +1,5 @@
 // Host preparation of an uploaded mesh: orientation, local face order, face
-// adjacency, FP64 cell geometry, locality renumbering (Morton / reverse
+// adjacency, FP64 cell geometry, locality renumbering (Morton / Hilbert / reverse
 // Cuthill-McKee), and the partition of renumbered cells into thread-block
 // sized groups with their halos.
 //
@@ -70,6 +70,48 @@ void morton_order(const std::vector<double> &cx, const std::vector<double> &cy,
         uint64_t ix = (uint64_t)std::floor((cx[i] - x0) * scale);
         uint64_t iy = (uint64_t)std::floor((cy[i] - y0) * scale);
         key[i] = spread_bits21(ix) | (spread_bits21(iy) << 1);
+        old_of_new[i] = (int32_t)i;
+    }
+    radix_sort_pairs(key, old_of_new, 48);
+}
+
+// Hilbert-curve order of cell centroids on a 2^21 x 2^21 grid; ties keep the
+// original order.  The index is built from the most significant level down:
+// each level contributes the quadrant's position along the curve, (3 rx) ^ ry
+// of 0..3 times the level's cell count, then the lower bits are turned into
+// the quadrant's own frame (the lower-left and lower-right quadrants are
+// transposed, the latter also mirrored), so that consecutive indices are
+// always neighbouring grid cells.  Blocks of consecutive cells are then
+// compact, with shorter boundaries (smaller halos) than Z-order blocks.
+void hilbert_order(const std::vector<double> &cx, const std::vector<double> &cy,
+                   std::vector<int32_t> &old_of_new)
+{
+    size_t n = cx.size();
+    double x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+    for (size_t i = 0; i < n; i++) {
+        x0 = std::min(x0, cx[i]); x1 = std::max(x1, cx[i]);
+        y0 = std::min(y0, cy[i]); y1 = std::max(y1, cy[i]);
+    }
+    double span = std::max(x1 - x0, y1 - y0);
+    double scale = span > 0 ? 2097151.0 / span : 0.0;
+    std::vector<uint64_t> key(n);
+    old_of_new.resize(n);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < (int64_t)n; i++) {
+        uint64_t x = (uint64_t)std::floor((cx[i] - x0) * scale);
+        uint64_t y = (uint64_t)std::floor((cy[i] - y0) * scale);
+        uint64_t d = 0;
+        for (uint64_t s = 1ull << 20; s > 0; s >>= 1) {
+            const uint64_t rx = (x & s) ? 1 : 0, ry = (y & s) ? 1 : 0;
+            d += s * s * ((3 * rx) ^ ry);
+            if (ry == 0) {
+                if (rx == 1) { x = s - 1 - (x & (s - 1)); y = s - 1 - (y & (s - 1)); }
+                std::swap(x, y);
+            }
+            x &= s - 1;
+            y &= s - 1;
+        }
+        key[i] = d;
         old_of_new[i] = (int32_t)i;
     }
     radix_sort_pairs(key, old_of_new, 48);
@@ -146,7 +188,7 @@ int prepare_mesh(int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
         err = "mesh too large: at most " + std::to_string((int64_t)INT32_MAX / GEO_ROWS) + " cells";
         return VG_EINVAL;
     }
-    if (renumber < 0 || renumber > 2) { err = "renumber must be 0, 1 or 2"; return VG_EINVAL; }
+    if (renumber < 0 || renumber > 3) { err = "renumber must be 0, 1, 2 or 3"; return VG_EINVAL; }
     m = HostMesh();
     m.nc = nc;
     m.nv = nv;
@@ -278,6 +320,8 @@ int prepare_mesh(int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
     // 4. renumbering
     if (renumber == VG_RENUMBER_MORTON) {
         morton_order(cx, cy, m.old_of_new);
+    } else if (renumber == VG_RENUMBER_HILBERT) {
+        hilbert_order(cx, cy, m.old_of_new);
     } else if (renumber == VG_RENUMBER_RCM) {
         rcm_order(nbr_o, nc, m.old_of_new);
     } else {

@@ -27,7 +27,7 @@ VG_ENEGDEPTH = -5
 VG_ETIMEOUT = -6
 VG_ESTATE = -7
 
-RENUMBER = {"none": 0, "morton": 1, "rcm": 2}
+RENUMBER = {"none": 0, "morton": 1, "rcm": 2, "hilbert": 3}
 
 
 class VolnaError(RuntimeError):
@@ -191,7 +191,7 @@ def vg_last_error(ctx) -> str:
     return load().vg_last_error(ctx).decode()
 
 
-def vg_mesh_upload(ctx, xy, tri, depth_v, renumber=1) -> None:
+def vg_mesh_upload(ctx, xy, tri, depth_v, renumber="hilbert") -> None:
     xy = _f64(xy).reshape(-1, 2)
     tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
     depth_v = _f64(depth_v)
@@ -380,7 +380,7 @@ class Solver:
         self.close()
 
     # mesh / parameters
-    def upload_mesh(self, mesh=None, xy=None, tri=None, depth=None, renumber="morton") -> None:
+    def upload_mesh(self, mesh=None, xy=None, tri=None, depth=None, renumber="hilbert") -> None:
         if mesh is not None:
             xy, tri, depth = mesh.xy, mesh.tri, mesh.depth
         vg_mesh_upload(self.ctx, xy, tri, depth, renumber)
@@ -544,7 +544,7 @@ class Batch:
             setattr(p, k, v)
         _bcheck(self.h, load().vg_batch_set_params(self.h, C.byref(p)))
 
-    def add_mesh(self, mesh, n_scenarios: int, renumber="morton") -> int:
+    def add_mesh(self, mesh, n_scenarios: int, renumber="hilbert") -> int:
         xy = _f64(mesh.xy).reshape(-1, 2)
         tri = np.ascontiguousarray(mesh.tri, dtype=np.int32).reshape(-1, 3)
         depth = _f64(mesh.depth)

@@ -34,7 +34,7 @@ def thacker_ref(thacker):
     return oracle_run(m, s, 100, gauges=I.THACKER_GAUGES, h_threshold=1e-5, cfl=0.9)
 
 
-@pytest.mark.parametrize("renumber", ["none", "morton", "rcm"])
+@pytest.mark.parametrize("renumber", ["none", "morton", "rcm", "hilbert"])
 def test_fp64_parity_thacker_100_steps(thacker, thacker_ref, renumber):
     m, s = thacker
     g = gpu_run(m, s, 100, precision=64, renumber=renumber, gauges=I.THACKER_GAUGES,
@@ -50,7 +50,7 @@ def test_fp64_parity_thacker_100_steps(thacker, thacker_ref, renumber):
     np.testing.assert_allclose(np.diff(g["gauge_t"]), thacker_ref["dts"], rtol=1e-13)
 
 
-@pytest.mark.parametrize("renumber", ["none", "morton"])
+@pytest.mark.parametrize("renumber", ["none", "morton", "hilbert"])
 def test_fp64_equals_oracle_bit_for_bit(thacker, thacker_ref, renumber):
     """FP64 evaluates every formula in the oracle's order without contraction,
     so 100 CFL steps of the Thacker basin (dry land: blocks that skip their
@@ -68,9 +68,10 @@ def test_fp64_equals_oracle_bit_for_bit(thacker, thacker_ref, renumber):
     np.testing.assert_array_equal(g["gauge_eta"][1:], thacker_ref["gauges"])
 
 
-def test_fp32_parity_thacker_100_steps(thacker, thacker_ref):
+@pytest.mark.parametrize("renumber", ["morton", "hilbert"])
+def test_fp32_parity_thacker_100_steps(thacker, thacker_ref, renumber):
     m, s = thacker
-    g = gpu_run(m, s, 100, precision=32, renumber="morton", h_threshold=1e-5, cfl=0.9)
+    g = gpu_run(m, s, 100, precision=32, renumber=renumber, h_threshold=1e-5, cfl=0.9)
     errs = {f: rel_l2(g[f], thacker_ref[f]) for f in FIELDS}
     print("FP32 relative L2 after 100 steps:", errs)
     for f in FIELDS:
