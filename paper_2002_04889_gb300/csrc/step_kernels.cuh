@@ -426,12 +426,17 @@ __device__ __forceinline__ void finish_cell(const KArgs<real> &a, int gid, const
 }
 
 // Shared memory of one CTA: cell states [L] x 4, face slots [3][L1] x 4 (L1 =
-// block + ring 1), global ids [L1], face codes and owned-face queue [3B] each.
+// block + ring 1), with gids the global ids of block and ring-1 cells [L1],
+// face codes and owned-face queue [3B] each.  Without gids phase B reads a
+// ring-1 cell's global id again from the halo list: at 6 CTAs per SM every
+// kilobyte of shared memory is a kilobyte less of L1.  The batched kernels keep
+// the ids (their extra scenario state leaves no register for the reload).
 template <typename real>
-__host__ __device__ inline size_t stage_smem_bytes(int block, int max_halo, int max_ring1)
+__host__ __device__ inline size_t stage_smem_bytes(int block, int max_halo, int max_ring1, bool gids = false)
 {
     size_t L = (size_t)block + max_halo, L1 = (size_t)block + max_ring1;
-    return sizeof(real) * 4 * (L + 3 * L1) + sizeof(int32_t) * L1 + sizeof(uint16_t) * 6 * (size_t)block + 16;
+    return sizeof(real) * 4 * (L + 3 * L1) + (gids ? sizeof(int32_t) * L1 : 0) + sizeof(uint16_t) * 6 * (size_t)block +
+           16;
 }
 
 // One block of cells for one scenario: phases A-D (see the top of this file).
@@ -459,7 +464,7 @@ __host__ __device__ inline size_t stage_smem_bytes(int block, int max_halo, int 
 // after phase B, and after phase C the cell's own term
 // (l_f Phi_0, l_f (Phi_1 + P n_x), l_f (Phi_2 + P n_y), x); x is l_f a_f in
 // stage 1 and, for block cells in stage 2, component f of w^n.
-template <typename real, int STAGE, int DRY, bool LISTED>
+template <typename real, int STAGE, int DRY, bool LISTED, bool GIDS>
 __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b, const real dt,
                                               unsigned char *smem_raw, int &qcount, real &my_min,
                                               long long &my_neg, bool &bad)
@@ -470,8 +475,8 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     const int nc = (int)a.nc;    // per-cell arrays hold < 2^31 entries (checked at upload)
     real *sW = reinterpret_cast<real *>(smem_raw);          // [L][4]
     real *sF = sW + 4 * L;                                   // [3][L1][4]
-    int32_t *sGid = reinterpret_cast<int32_t *>(sF + 12 * L1);   // [L1]
-    uint16_t *sCode = reinterpret_cast<uint16_t *>(sGid + L1);   // [3][B]
+    int32_t *sGid = reinterpret_cast<int32_t *>(sF + 12 * L1);   // [L1] (GIDS)
+    uint16_t *sCode = reinterpret_cast<uint16_t *>(GIDS ? sGid + L1 : sGid);   // [3][B]
     uint16_t *queue = sCode + 3 * B;                              // [3B]
 
     constexpr bool ETA = EtaForm<real>::value;
@@ -514,7 +519,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             bool neg = stage_cell<real, STAGE>(a, gid, dt, W, Hu, Hv, zc);
             if (neg) my_neg++;
             st4(sW + 4 * tid, W, Hu, Hv, zc);
-            sGid[tid] = gid;
+            if constexpr (GIDS) sGid[tid] = gid;
             dry = exactly_dry(W, Hu, Hv, zc);
         }
         if (gh >= 0) {
@@ -522,7 +527,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             stage_cell<real, STAGE>(a, gh, dt, W, Hu, Hv, zc);
             st4(sW + 4 * (B + tid), W, Hu, Hv, zc);
             if (tid < n1) {
-                sGid[B + tid] = gh;
+                if constexpr (GIDS) sGid[B + tid] = gh;
                 dry = dry && exactly_dry(W, Hu, Hv, zc);
             }
         }
@@ -532,7 +537,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             stage_cell<real, STAGE>(a, gid, dt, W, Hu, Hv, zc);
             st4(sW + 4 * (B + h), W, Hu, Hv, zc);
             if (h < n1) {
-                sGid[B + h] = gid;
+                if constexpr (GIDS) sGid[B + h] = gid;
                 dry = dry && exactly_dry(W, Hu, Hv, zc);
             }
         }
@@ -580,7 +585,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     // Barth-Jespersen limiter); every neighbour is in shared memory
     for (int l = tid; l < (zero_terms ? ncell : B + n1); l += blockDim.x) {
         if (l < B && l >= ncell) continue;
-        const int gid = sGid[l];
+        const int gid = GIDS ? sGid[l] : l < B ? c0 + l : a.halo_ids[h0 + (l - B)];
         if (zero_terms) {
             real wz[3] = {real(0), real(0), real(0)};
             if (STAGE == 2) { wz[0] = a.w[gid]; wz[1] = a.w[nc + gid]; wz[2] = a.w[2 * nc + gid]; }
@@ -821,8 +826,8 @@ __global__ void __launch_bounds__(MAXT, StageMinCtas<real, MAXT>::value) stage_k
 
     int parity = 0;
     for (int b = blockIdx.x; b < a.nblocks; b += gridDim.x, parity ^= 1)
-        process_block<real, STAGE, DryMode<real, STAGE>::value, STAGE == 2>(a, b, dt, smem_raw, qcount[parity], my_min,
-                                                                              my_neg, bad);
+        process_block<real, STAGE, DryMode<real, STAGE>::value, STAGE == 2, false>(a, b, dt, smem_raw, qcount[parity],
+                                                                                     my_min, my_neg, bad);
 
     // CTA-level reductions, then one atomic per CTA
     const int lane = tid & 31, warp = tid >> 5, nwarps = (blockDim.x + 31) >> 5;
@@ -912,7 +917,7 @@ __global__ void __launch_bounds__(256, (StageMinCtas<real, 256>::value)) batch_s
             a.sc += s;
             const int e = bm.first_entry + s;
             real mn = real_inf<real>();
-            process_block<real, STAGE, 2, true>(a, b, s_dt[e], smem_raw, qcount[parity], mn, my_neg, bad);
+            process_block<real, STAGE, 2, true, true>(a, b, s_dt[e], smem_raw, qcount[parity], mn, my_neg, bad);
             parity ^= 1;
             if (STAGE == 1) {
                 unsigned long long bits = warp_min_bits<real>(mn);
@@ -1089,7 +1094,7 @@ int launch_stage(const DevPtrs &d, const StepParams &p, int stage, const void *w
 template <typename real>
 int batch_config(int block, int max_halo, int max_ring1, int &grid, size_t &smem)
 {
-    smem = stage_smem_bytes<real>(block, max_halo, max_ring1);
+    smem = stage_smem_bytes<real>(block, max_halo, max_ring1, true);
     int best = 1 << 30;
     for (int stage = 1; stage <= 2; stage++) {
         auto kern = stage == 1 ? batch_stage_kernel<real, 1> : batch_stage_kernel<real, 2>;
