@@ -30,6 +30,8 @@ struct AdjMesh {
     const double *z;         // [nc]
     const int32_t *nbr;      // [3][nc]
     const uint16_t *nbrl;    // [3][nc]: low 2 bits = neighbour's face (not a wall)
+    const int32_t *faces;    // every face once: (owning cell << 2) | face
+    int nfaces;
     double g, half_g, hthr;
 };
 
@@ -333,16 +335,17 @@ __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL,
     bR[0] += HfRb;
 }
 
-// Per owned face: R-bar of both cells -> Phi-bar, P-bar -> face-state adjoints.
-// FVb[(v*3+f)*nc + K] and zfb[f*nc + K] are the (cell, face) slots; each is
-// written exactly once per residual.
+// One thread per face (the face list: the lower-numbered cell owns an interior
+// face, the cell a boundary face): R-bar of both cells -> Phi-bar, P-bar ->
+// face-state adjoints.  FVb[(v*3+f)*nc + K] and zfb[f*nc + K] are the (cell,
+// face) slots; each is written exactly once per residual.
 __global__ void adj_flux_vjp_kernel(AdjMesh m, const double *FV, const double *Rb, double *FVb, double *zfb)
 {
     const int nc = m.nc;
-    for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < nc; K += gridDim.x * blockDim.x) {
-        for (int f = 0; f < 3; f++) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < m.nfaces; q += gridDim.x * blockDim.x) {
+        {
+            const int K = m.faces[q] >> 2, f = m.faces[q] & 3;
             int j = m.nbr[f * nc + K];
-            if (j >= 0 && j < K) continue;      // the lower-numbered cell owns the face
             bool wall = j < 0;
             int fj = wall ? 0 : (m.nbrl[f * nc + K] & 3);
             if (!rb_nonzero(Rb, nc, K) && (wall || !rb_nonzero(Rb, nc, j))) {
@@ -432,14 +435,21 @@ __global__ void adj_recon_vjp_kernel(AdjMesh m, const double *w, const double *F
                     ab += fb[v][f] * R.D[v][f];
                     Db[f] = fb[v][f] * R.alpha[v];
                 }
-                int fa = R.fa[v];
+                const int fa = R.fa[v];
                 if (fa >= 0) {
-                    double iD = 1.0 / R.D[v][fa];
+                    // (faces picked by compare and select, not by index: indexed
+                    // arrays would live in local memory)
+                    const double D = fa == 0 ? R.D[v][0] : fa == 1 ? R.D[v][1] : R.D[v][2];
+                    double iD = 1.0 / D;
                     double rb = ab * iD;
-                    Db[fa] -= rb * R.r[v] * iD;
-                    double D = R.D[v][fa];
+#pragma unroll
+                    for (int f = 0; f < 3; f++)
+                        if (f == fa) Db[f] -= rb * R.r[v] * iD;
                     int idx = D > 0.0 ? R.imax[v] : R.imin[v];
-                    if (idx < 0) qKb[v] += rb; else qnb[idx][v] += rb;
+                    if (idx < 0) qKb[v] += rb;
+#pragma unroll
+                    for (int f = 0; f < 3; f++)
+                        if (f == idx) qnb[f][v] += rb;
                     qKb[v] -= rb;
                 }
                 double gxb = 0.0, gyb = 0.0;
@@ -815,6 +825,11 @@ __global__ void adj_scalar_add_kernel(double *y, const double *x)
 }
 
 int grid_of(int n) { return (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096; }
+// The two heavy reverse kernels run 128-thread CTAs: at 110 / 146 registers a
+// thread that fits 4 / 3 CTAs per SM (16 / 12 warps) where 256-thread CTAs fit
+// 2 / 1.
+constexpr int kVjpThreads = 128;
+int grid_vjp(int n) { return (n + kVjpThreads - 1) / kVjpThreads < 8192 ? (n + kVjpThreads - 1) / kVjpThreads : 8192; }
 
 AdjMesh adj_mesh(const DevPtrs &d, const StepParams &p)
 {
@@ -825,6 +840,8 @@ AdjMesh adj_mesh(const DevPtrs &d, const StepParams &p)
     m.z = static_cast<const double *>(d.z);
     m.nbr = d.nbr;
     m.nbrl = d.nbrl;
+    m.faces = d.adj_faces;
+    m.nfaces = (int)d.n_adj_faces;
     m.g = p.g;
     m.half_g = 0.5 * p.g;
     m.hthr = p.hthr;
@@ -843,13 +860,14 @@ int adjoint_residual_vjp(const DevPtrs &d, const StepParams &p, const double *w,
     AdjMesh m = adj_mesh(d, p);
     int grid = grid_of(m.nc);
     if (!fv_given) adj_face_values_kernel<<<grid, 256, 0, s>>>(m, w, Rb, FV);
-    adj_flux_vjp_kernel<<<grid, 256, 0, s>>>(m, FV, Rb, FVb, zfb);
+    if (!m.faces) return (int)cudaErrorInvalidValue;     // the face list is built by vg_adj_backward
+    adj_flux_vjp_kernel<<<grid_vjp(m.nfaces), kVjpThreads, 0, s>>>(m, FV, Rb, FVb, zfb);
     if (cfl) {
         adj_cfl_part_kernel<<<kAdjCflParts, 256, 0, s>>>(m, FV, cfl->orig, cfl->part_b, cfl->part_o, cfl->part_k);
         adj_cfl_face_kernel<<<1, 32, 0, s>>>(m, FV, kAdjCflParts, cfl->part_b, cfl->part_o, cfl->part_k, cfl->dtbar,
                                              cfl->cfl, cfl->dt_max, FVb, zfb);
     }
-    adj_recon_vjp_kernel<<<grid, 256, 0, s>>>(m, w, FVb, zfb, own, send);
+    adj_recon_vjp_kernel<<<grid_vjp(m.nc), kVjpThreads, 0, s>>>(m, w, FVb, zfb, own, send);
     adj_gather_kernel<<<grid, 256, 0, s>>>(m, own, send, wb, zb);
     return (int)cudaGetLastError();
 }

@@ -41,7 +41,8 @@ struct vg_ctx {
     void *geo = nullptr, *z = nullptr, *w[2] = {nullptr, nullptr}, *R0 = nullptr;
     double *z64 = nullptr;
     int32_t *nbr = nullptr, *halo_ptr = nullptr, *halo_n1 = nullptr, *halo_ids = nullptr, *old_of_new = nullptr;
-    int32_t *new_of_old = nullptr, *fq_ptr = nullptr;
+    int32_t *new_of_old = nullptr, *fq_ptr = nullptr, *adj_faces = nullptr;
+    int64_t n_adj_faces = 0;          // built by the first adjoint sweep of a mesh
     uint16_t *nbrl = nullptr, *ring1_nbr = nullptr, *fq = nullptr;
     DevScalars *sc = nullptr;
     int32_t *gauge_cells = nullptr;
@@ -147,6 +148,7 @@ void free_mesh(vg_ctx *c)
     dfree(c->geo); dfree(c->z); dfree(c->z64); dfree(c->w[0]); dfree(c->w[1]); dfree(c->R0);
     dfree(c->nbr); dfree(c->halo_ptr); dfree(c->halo_n1); dfree(c->halo_ids); dfree(c->ring1_nbr);
     dfree(c->old_of_new); dfree(c->new_of_old); dfree(c->nbrl); dfree(c->fq_ptr); dfree(c->fq);
+    dfree(c->adj_faces); c->n_adj_faces = 0;
     dfree(c->gauge_cells); dfree(c->ring_t); dfree(c->ring_eta); dfree(c->staging);
     dfree(c->bed_vtx); dfree(c->bed_depth0); dfree(c->bed_uplift); dfree(c->bed_onset);
     c->bed_on = false;
@@ -196,6 +198,8 @@ DevPtrs dev_ptrs(const vg_ctx *c)
     d.ring1_nbr = c->ring1_nbr;
     d.fq_ptr = c->fq_ptr;
     d.fq = c->fq;
+    d.adj_faces = c->adj_faces;
+    d.n_adj_faces = c->n_adj_faces;
     d.R0 = c->R0;
     d.sc = c->sc;
     d.gauge_cells = c->gauge_cells;
@@ -1228,6 +1232,22 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
     if (c->adj_n < 1) return fail(c, VG_ESTATE, "call vg_adj_forward first");
     if (c->adj_bed && !c->bed_on) return fail(c, VG_ESTATE, "the moving bed of the forward run was removed");
     DeviceGuard guard(c->device);
+    if (!c->adj_faces) {
+        // every face once, owned by its lower-numbered cell (a boundary face by its
+        // cell), for the flux VJP's one thread per face
+        const HostMesh &hm = c->hm;
+        std::vector<int32_t> fl;
+        fl.reserve(2 * (size_t)hm.nc + 16);
+        for (int64_t k = 0; k < hm.nc; k++)
+            for (int f = 0; f < 3; f++) {
+                const int32_t j = hm.nbr[f * hm.nc + k];
+                if (j < 0 || j > k) fl.push_back((int32_t)((k << 2) | f));
+            }
+        int e = dmalloc(c, (void **)&c->adj_faces, 4 * std::max<size_t>(fl.size(), 1));
+        if (e) return e;
+        VG_CUDA(c, cudaMemcpy(c->adj_faces, fl.data(), 4 * fl.size(), cudaMemcpyHostToDevice));
+        c->n_adj_faces = (int64_t)fl.size();
+    }
     const int64_t N = c->adj_n, C = c->adj_every;
     const int nc = (int)c->hm.nc, G = c->n_gauges;
     const size_t w3 = 3 * (size_t)nc;

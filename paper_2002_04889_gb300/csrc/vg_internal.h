@@ -103,6 +103,8 @@ struct DevPtrs {
     const uint16_t *ring1_nbr;
     const int32_t *fq_ptr;  // [nblocks + 1]
     const uint16_t *fq;     // owned faces of each block
+    const int32_t *adj_faces;   // adjoint: every face once, (cell << 2) | face (cell = lower id or the boundary cell)
+    int64_t n_adj_faces;
     void *R0;               // [3][nc] stage-1 residual (scratch)
     uint8_t *mask2;         // optional [nc]: stage-2 dry-fix branch per cell (adjoint)
     void *fv_out;           // optional [9][nc]: face values written by the stage kernels (adjoint)
