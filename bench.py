@@ -311,7 +311,7 @@ def batched_leg(torch, stream, steps: int, n_scen: int = 32, renumber: str = "hi
             "setup_s": round(setup, 1)}
 
 
-def adjoint_leg(torch, stream, steps: int, n: int = 707):
+def adjoint_leg(torch, stream, steps: int, n: int = 707, slots: int = 16):
     """Config 5 mesh (Thacker basin, n x n squares, 2 n^2 triangles), FP64: the cost of
     the gradient of a 16-gauge misfit (forward with sqrt(N) checkpoints + reverse
     sweep) against the plain forward run of the same steps."""
@@ -341,13 +341,15 @@ def adjoint_leg(torch, stream, steps: int, n: int = 707):
     t1 = time.perf_counter()
     sv.adj_backward(np.full_like(eta, 1e-3), m.nv)
     t2 = time.perf_counter()
-    # binomial checkpointing with 16 state slots: far less memory, more recomputation
-    slots = 16
-    sv.set_state(s.H, s.Hu, s.Hv)
-    t3 = time.perf_counter()
-    _, eta = sv.adj_forward_binomial(steps, dt, slots)
-    sv.adj_backward(np.full_like(eta, 1e-3), m.nv)
-    t4 = time.perf_counter()
+    # binomial checkpointing with `slots` state slots (0: skipped): far less
+    # memory, more recomputation
+    t3 = t4 = 0.0
+    if slots > 0:
+        sv.set_state(s.H, s.Hu, s.Hv)
+        t3 = time.perf_counter()
+        _, eta = sv.adj_forward_binomial(steps, dt, slots)
+        sv.adj_backward(np.full_like(eta, 1e-3), m.nv)
+        t4 = time.perf_counter()
     sv.close()
     C = math.ceil(math.sqrt(steps))
     rec = 24 + 24 + 144 + 1                     # per step held: state, R0, face values (2 stages), mask
@@ -356,8 +358,8 @@ def adjoint_leg(torch, stream, steps: int, n: int = 707):
             "adj_backward_s": round(t2 - t1, 4), "cost_vs_forward": round((t2 - t0) / t_fwd, 3),
             "forward_value": m.nc * steps / t_fwd, "unit": UNIT,
             "scratch_bytes_per_cell_sqrtN": math.ceil(steps / C) * 24 + C * rec,
-            "binomial": {"slots": slots, "cost_vs_forward": round((t4 - t3) / t_fwd, 3),
-                         "scratch_bytes_per_cell": (slots + 3) * 24 + rec}}
+            "binomial": None if slots <= 0 else {"slots": slots, "cost_vs_forward": round((t4 - t3) / t_fwd, 3),
+                                                 "scratch_bytes_per_cell": (slots + 3) * 24 + rec}}
 
 
 def run_reference(args):
@@ -406,6 +408,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--batched-steps", type=int, default=20, help="0 skips the batched-ensemble leg")
     ap.add_argument("--adjoint-steps", type=int, default=2000, help="0 skips the adjoint-cost leg")
+    ap.add_argument("--adjoint-binomial-slots", type=int, default=16, help="0 skips the binomial run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -539,7 +542,7 @@ def main():
             batched = {"error": str(e)[:300]}
     if rank == 0 and args.adjoint_steps > 0:
         try:
-            adjoint = adjoint_leg(torch, stream, args.adjoint_steps)
+            adjoint = adjoint_leg(torch, stream, args.adjoint_steps, slots=args.adjoint_binomial_slots)
         except Exception as e:
             adjoint = {"error": str(e)[:300]}
 
