@@ -557,20 +557,32 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
                 if ((owned >> f) & 1) queue[pos++] = (uint16_t)((tid << 2) | f);
         }
     }
-    // Dry land (runs with recordings for the adjoint take every phase).  Mode 1
-    // leaves the block here with a zero residual (phase D with zero face terms;
-    // w^n from memory); mode 2 has phase B write zero face terms for the block
-    // cells (and w^n for stage 2) and phase C no faces, which costs a few
-    // instructions more but no register spills where mode 1 would spill.
+    // Dry land.  Mode 1 leaves the block here with a zero residual (phase D with
+    // zero face terms; w^n from memory) and writes the adjoint's recordings as
+    // the full phases would (a dry cell's face values are its own values); mode 2
+    // has phase B write zero face terms for the block cells (and w^n for stage
+    // 2) and phase C no faces, which costs a few instructions more but no
+    // register spills where mode 1 would spill (runs with recordings take every
+    // phase there).
     bool skip = false;
     if constexpr (DRY == 0)
         __syncthreads();
     else
-        skip = __syncthreads_and(dry) && !a.fv_out && !a.mask2 && !a.r1_out;
+        skip = __syncthreads_and(dry) && (DRY == 1 || (!a.fv_out && !a.mask2 && !a.r1_out));
     if (DRY == 1 && skip) {
         if (!LISTED && tid == 0) qcount = 0;
         if (tid < ncell) {
             const int gid = c0 + tid;
+            if (a.fv_out) {
+                real Wc, Huc, Hvc, zc;
+                ld4(sW + 4 * tid, Wc, Huc, Hvc, zc);
+#pragma unroll
+                for (int f = 0; f < 3; f++) {
+                    a.fv_out[(0 * 3 + f) * (size_t)nc + gid] = Wc;
+                    a.fv_out[(1 * 3 + f) * (size_t)nc + gid] = Huc;
+                    a.fv_out[(2 * 3 + f) * (size_t)nc + gid] = Hvc;
+                }
+            }
             real x[3] = {real(0), real(0), real(0)};
             if (STAGE == 2) { x[0] = a.w[gid]; x[1] = a.w[nc + gid]; x[2] = a.w[2 * nc + gid]; }
             // R = -0 / |K| = -0 for any area, so the area is not read
