@@ -40,6 +40,9 @@ struct vg_ctx {
     // device memory
     void *geo = nullptr, *z = nullptr, *w[2] = {nullptr, nullptr}, *R0 = nullptr;
     double *z64 = nullptr;
+    float *z_orig = nullptr;          // FP32: the bed in the original cell order (state import/export)
+    double *z64_orig = nullptr;
+    bool zorig_ok = false;            // the two copies match z (false once a moving bed was set)
     int32_t *nbr = nullptr, *halo_ptr = nullptr, *halo_n1 = nullptr, *halo_ids = nullptr, *old_of_new = nullptr;
     int32_t *new_of_old = nullptr, *fq_ptr = nullptr, *adj_faces = nullptr;
     int64_t n_adj_faces = 0;          // built by the first adjoint sweep of a mesh
@@ -146,6 +149,7 @@ void free_mesh(vg_ctx *c)
     if (c->graph2) { cudaGraphExecDestroy(c->graph2); c->graph2 = nullptr; }
     if (c->z64 == c->z) c->z64 = nullptr;
     dfree(c->geo); dfree(c->z); dfree(c->z64); dfree(c->w[0]); dfree(c->w[1]); dfree(c->R0);
+    dfree(c->z_orig); dfree(c->z64_orig); c->zorig_ok = false;
     dfree(c->nbr); dfree(c->halo_ptr); dfree(c->halo_n1); dfree(c->halo_ids); dfree(c->ring1_nbr);
     dfree(c->old_of_new); dfree(c->new_of_old); dfree(c->nbrl); dfree(c->fq_ptr); dfree(c->fq);
     dfree(c->adj_faces); c->n_adj_faces = 0;
@@ -185,6 +189,9 @@ DevPtrs dev_ptrs(const vg_ctx *c)
     d.geo = c->geo;
     d.z = c->z;
     d.z64 = c->z64;
+    const bool zo = c->zorig_ok && !c->bed_on;
+    d.z_orig = zo ? c->z_orig : nullptr;
+    d.z64_orig = zo ? c->z64_orig : nullptr;
     d.bed_vtx = c->bed_vtx;
     d.bed_depth0 = c->bed_depth0;
     d.bed_uplift = c->bed_uplift;
@@ -232,6 +239,29 @@ int upload_real(vg_ctx *c, void *dst, const double *src, size_t n)
         for (size_t i = 0; i < n; i++) tmp[i] = (float)src[i];
         VG_CUDA(c, cudaMemcpy(dst, tmp.data(), n * 4, cudaMemcpyHostToDevice));
     }
+    return VG_OK;
+}
+
+// FP32: the bed (as the kernels round it, and in FP64) in the original cell
+// order, so that the state import / export kernels, one thread per original
+// cell, read it contiguously instead of at scattered internal positions.
+int upload_bed_orig(vg_ctx *c)
+{
+    c->zorig_ok = false;
+    if (c->precision == 64) return VG_OK;
+    const HostMesh &m = c->hm;
+    int rc;
+    if (!c->z_orig && (rc = dmalloc(c, (void **)&c->z_orig, 4 * m.nc))) return rc;
+    if (!c->z64_orig && (rc = dmalloc(c, (void **)&c->z64_orig, 8 * m.nc))) return rc;
+    std::vector<double> zo(m.nc);
+    std::vector<float> zf(m.nc);
+    for (int64_t o = 0; o < m.nc; o++) {
+        zo[o] = m.z[m.new_of_old[o]];
+        zf[o] = (float)zo[o];             // the rounding of upload_real
+    }
+    VG_CUDA(c, cudaMemcpy(c->z64_orig, zo.data(), 8 * m.nc, cudaMemcpyHostToDevice));
+    VG_CUDA(c, cudaMemcpy(c->z_orig, zf.data(), 4 * m.nc, cudaMemcpyHostToDevice));
+    c->zorig_ok = true;
     return VG_OK;
 }
 
@@ -306,6 +336,7 @@ int upload_mesh_arrays(vg_ctx *c)
         if ((rc = dmalloc(c, (void **)&c->z64, 8 * m.nc))) return rc;
         VG_CUDA(c, cudaMemcpy(c->z64, m.z.data(), 8 * m.nc, cudaMemcpyHostToDevice));
     }
+    if ((rc = upload_bed_orig(c))) return rc;
     VG_CUDA(c, cudaMemcpy(c->nbr, m.nbr.data(), 4 * 3 * m.nc, cudaMemcpyHostToDevice));
     VG_CUDA(c, cudaMemcpy(c->old_of_new, m.old_of_new.data(), 4 * m.nc, cudaMemcpyHostToDevice));
     VG_CUDA(c, cudaMemcpy(c->new_of_old, m.new_of_old.data(), 4 * m.nc, cudaMemcpyHostToDevice));
@@ -1046,6 +1077,7 @@ int vg_set_depth(vg_ctx *c, const double *depth_v)
     int rc = upload_real(c, c->z, m.z.data(), m.z.size());
     if (rc) return rc;
     if (c->precision != 64) VG_CUDA(c, cudaMemcpy(c->z64, m.z.data(), 8 * m.nc, cudaMemcpyHostToDevice));
+    if ((rc = upload_bed_orig(c))) return rc;
     c->depth_v.assign(depth_v, depth_v + m.nv);
     c->graph_dirty = true;
     return VG_OK;
@@ -1135,6 +1167,7 @@ int vg_set_bed_motion(vg_ctx *c, const double *uplift_v, const double *onset_v, 
     c->launches++;
     VG_CUDA(c, cudaStreamSynchronize(c->stream));
     c->bed_on = uplift_v != nullptr;
+    if (c->bed_on) c->zorig_ok = false;     // the bed will move: import / export read z itself
     if (!c->bed_on) {
         dfree(c->bed_vtx); dfree(c->bed_depth0); dfree(c->bed_uplift); dfree(c->bed_onset);
     }

@@ -156,18 +156,20 @@ template <> struct Vec16<float> { using type = float4; };
 template <> struct Vec16<double> { using type = double2; };
 
 template <typename real, typename src_t>
-__device__ __forceinline__ void import_one(int64_t nc, int64_t k, src_t h, src_t hu, src_t hv, const double *z,
+__device__ __forceinline__ void import_one(int64_t nc, int64_t k, src_t h, src_t hu, src_t hv, double zk,
                                            real *w, bool &bad)
 {
     if (!(h >= src_t(0)) || !isfinite(h) || !isfinite(hu) || !isfinite(hv)) bad = true;
-    w[k] = EtaForm<real>::value ? (real)((double)h + (double)z[k]) : (real)h;
+    w[k] = EtaForm<real>::value ? (real)((double)h + zk) : (real)h;
     w[nc + k] = (real)hu;
     w[2 * nc + k] = (real)hv;
 }
 
+// zo: the FP64 bed in the original order (contiguous reads), or null (z[k]).
 template <typename real, typename src_t>
 __global__ void import_state_orig_kernel(int64_t nc, const int32_t *new_of_old, const src_t *H, const src_t *Hu,
-                                         const src_t *Hv, const double *z, real *w, DevScalars *sc, bool vec)
+                                         const src_t *Hv, const double *z, const double *zo, real *w,
+                                         DevScalars *sc, bool vec)
 {
     constexpr int V = 16 / sizeof(src_t);
     using vt = typename Vec16<src_t>::type;
@@ -180,30 +182,38 @@ __global__ void import_state_orig_kernel(int64_t nc, const int32_t *new_of_old, 
         const src_t *ph = reinterpret_cast<const src_t *>(&h), *phu = reinterpret_cast<const src_t *>(&hu),
                     *phv = reinterpret_cast<const src_t *>(&hv);
 #pragma unroll
-        for (int j = 0; j < V; j++)
-            import_one<real, src_t>(nc, new_of_old[gi * V + j], ph[j], phu[j], phv[j], z, w, bad);
+        for (int j = 0; j < V; j++) {
+            const int64_t o = gi * V + j, k = new_of_old[o];
+            import_one<real, src_t>(nc, k, ph[j], phu[j], phv[j],
+                                    EtaForm<real>::value ? (zo ? zo[o] : z[k]) : 0.0, w, bad);
+        }
     }
-    for (int64_t o = ng * V + tid; o < nc; o += stride)
-        import_one<real, src_t>(nc, new_of_old[o], H[o], Hu[o], Hv[o], z, w, bad);
+    for (int64_t o = ng * V + tid; o < nc; o += stride) {
+        const int64_t k = new_of_old[o];
+        import_one<real, src_t>(nc, k, H[o], Hu[o], Hv[o], EtaForm<real>::value ? (zo ? zo[o] : z[k]) : 0.0, w,
+                                bad);
+    }
     if (bad) atomicOr(&sc->flags, FLAG_BAD_INPUT);
 }
 
 // H of internal cell k in the destination type (the eta form is dry at eta <= z
 // in the kernels' own rounded bed, and then H is exactly 0).
 template <typename real, typename dst_t>
-__device__ __forceinline__ void export_one(int64_t nc, int64_t k, const real *w, const real *zr, const double *z,
-                                           dst_t &h, dst_t &hu, dst_t &hv)
+__device__ __forceinline__ void export_one(int64_t nc, int64_t k, const real *w, real zrk, double zk, dst_t &h,
+                                           dst_t &hu, dst_t &hv)
 {
     double x = (double)w[k];
-    if (EtaForm<real>::value) x = (w[k] - zr[k] <= real(0)) ? 0.0 : fmax(0.0, x - z[k]);
+    if (EtaForm<real>::value) x = (w[k] - zrk <= real(0)) ? 0.0 : fmax(0.0, x - zk);
     h = (dst_t)x;
     hu = (dst_t)w[nc + k];
     hv = (dst_t)w[2 * nc + k];
 }
 
+// zro / zo: the kernels' bed and the FP64 bed in the original order, or null.
 template <typename real, typename dst_t>
 __global__ void export_state_orig_kernel(int64_t nc, const int32_t *new_of_old, const real *w, const real *zr,
-                                         const double *z, dst_t *H, dst_t *Hu, dst_t *Hv, bool vec)
+                                         const double *z, const real *zro, const double *zo, dst_t *H, dst_t *Hu,
+                                         dst_t *Hv, bool vec)
 {
     constexpr int V = 16 / sizeof(dst_t);
     using vt = typename Vec16<dst_t>::type;
@@ -214,13 +224,24 @@ __global__ void export_state_orig_kernel(int64_t nc, const int32_t *new_of_old, 
         dst_t *ph = reinterpret_cast<dst_t *>(&h), *phu = reinterpret_cast<dst_t *>(&hu),
               *phv = reinterpret_cast<dst_t *>(&hv);
 #pragma unroll
-        for (int j = 0; j < V; j++) export_one<real, dst_t>(nc, new_of_old[gi * V + j], w, zr, z, ph[j], phu[j], phv[j]);
+        for (int j = 0; j < V; j++) {
+            const int64_t o = gi * V + j, k = new_of_old[o];
+            real zrk = real(0);
+            double zk = 0.0;
+            if (EtaForm<real>::value) { zrk = zro ? zro[o] : zr[k]; zk = zo ? zo[o] : z[k]; }
+            export_one<real, dst_t>(nc, k, w, zrk, zk, ph[j], phu[j], phv[j]);
+        }
         reinterpret_cast<vt *>(H)[gi] = h;
         reinterpret_cast<vt *>(Hu)[gi] = hu;
         reinterpret_cast<vt *>(Hv)[gi] = hv;
     }
-    for (int64_t o = ng * V + tid; o < nc; o += stride)
-        export_one<real, dst_t>(nc, new_of_old[o], w, zr, z, H[o], Hu[o], Hv[o]);
+    for (int64_t o = ng * V + tid; o < nc; o += stride) {
+        const int64_t k = new_of_old[o];
+        real zrk = real(0);
+        double zk = 0.0;
+        if (EtaForm<real>::value) { zrk = zro ? zro[o] : zr[k]; zk = zo ? zo[o] : z[k]; }
+        export_one<real, dst_t>(nc, k, w, zrk, zk, H[o], Hu[o], Hv[o]);
+    }
 }
 
 constexpr int DIAG_BLOCKS = 1024;
@@ -333,18 +354,18 @@ int launch_import_state_orig(const DevPtrs &d, const int32_t *new_of_old, const 
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int grid = grid_for(d.nc);
-    const double *z = d.z64;
+    const double *z = d.z64, *zo = d.z64_orig;
     const bool vec = aligned16(H, Hu, Hv);
     if (precision == 64) {
         if (src_is_double)
-            import_state_orig_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const double *)H, (const double *)Hu, (const double *)Hv, z, (double *)w, d.sc, vec);
+            import_state_orig_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const double *)H, (const double *)Hu, (const double *)Hv, z, zo, (double *)w, d.sc, vec);
         else
-            import_state_orig_kernel<double, float><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const float *)H, (const float *)Hu, (const float *)Hv, z, (double *)w, d.sc, vec);
+            import_state_orig_kernel<double, float><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const float *)H, (const float *)Hu, (const float *)Hv, z, zo, (double *)w, d.sc, vec);
     } else {
         if (src_is_double)
-            import_state_orig_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const double *)H, (const double *)Hu, (const double *)Hv, z, (float *)w, d.sc, vec);
+            import_state_orig_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const double *)H, (const double *)Hu, (const double *)Hv, z, zo, (float *)w, d.sc, vec);
         else
-            import_state_orig_kernel<float, float><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const float *)H, (const float *)Hu, (const float *)Hv, z, (float *)w, d.sc, vec);
+            import_state_orig_kernel<float, float><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const float *)H, (const float *)Hu, (const float *)Hv, z, zo, (float *)w, d.sc, vec);
     }
     return (int)cudaGetLastError();
 }
@@ -355,16 +376,18 @@ int launch_export_state_orig(const DevPtrs &d, const int32_t *new_of_old, const 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int grid = grid_for(d.nc);
     const bool vec = aligned16(H, Hu, Hv);
+    const double *zo = d.z64_orig;
     if (precision == 64) {
         if (dst_is_double)
-            export_state_orig_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const double *)w, (const double *)d.z, d.z64, (double *)H, (double *)Hu, (double *)Hv, vec);
+            export_state_orig_kernel<double, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const double *)w, (const double *)d.z, d.z64, nullptr, zo, (double *)H, (double *)Hu, (double *)Hv, vec);
         else
-            export_state_orig_kernel<double, float><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const double *)w, (const double *)d.z, d.z64, (float *)H, (float *)Hu, (float *)Hv, vec);
+            export_state_orig_kernel<double, float><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const double *)w, (const double *)d.z, d.z64, nullptr, zo, (float *)H, (float *)Hu, (float *)Hv, vec);
     } else {
+        const float *zro = static_cast<const float *>(d.z_orig);
         if (dst_is_double)
-            export_state_orig_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const float *)w, (const float *)d.z, d.z64, (double *)H, (double *)Hu, (double *)Hv, vec);
+            export_state_orig_kernel<float, double><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const float *)w, (const float *)d.z, d.z64, zro, zo, (double *)H, (double *)Hu, (double *)Hv, vec);
         else
-            export_state_orig_kernel<float, float><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const float *)w, (const float *)d.z, d.z64, (float *)H, (float *)Hu, (float *)Hv, vec);
+            export_state_orig_kernel<float, float><<<grid, 256, 0, s>>>(d.nc, new_of_old, (const float *)w, (const float *)d.z, d.z64, zro, zo, (float *)H, (float *)Hu, (float *)Hv, vec);
     }
     return (int)cudaGetLastError();
 }

@@ -95,6 +95,9 @@ struct DevPtrs {
     const void *geo;        // FP64: [GEO_ROWS][nc]; FP32: [nc][16] record
     const void *z;          // [nc]
     const double *z64;      // [nc] FP64 bed (state import/export and diagnostics)
+    const void *z_orig;     // FP32: [nc] the kernels' bed in the original cell order, or null
+    const double *z64_orig; // FP32: [nc] the FP64 bed in the original cell order, or null
+                            // (both current only while no moving bed has been set)
     const int32_t *nbr;     // [3][nc]
     const uint16_t *nbrl;   // [3][nc]
     const int32_t *halo_ptr;

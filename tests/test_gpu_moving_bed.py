@@ -122,3 +122,31 @@ def test_remove_motion_and_guards():
         sv.set_depth(m.depth)
         sv.step(5)
         assert np.isfinite(sv.get_state()[0]).all()
+
+
+def test_pinned_state_io_follows_the_moving_bed():
+    """FP32 with a moving bed: the in-place export of pinned host buffers (FP32 and
+    FP64) forms H from the moved bed, as the staged export does, bit for bit; a
+    state set from pinned buffers after the bed moved stores the same eta."""
+    torch = pytest.importorskip("torch")
+    m = I.thacker_mesh(n=40)
+    s = I.thacker_initial_state(m)
+    up, on = I.radial_rupture(m.xy, 0.02, 0.1, -0.05, 0.4, 2.0, 0.0)
+    with volna.Solver(32) as sv:
+        sv.set_params(h_threshold=1e-5, cfl=0.9)
+        sv.upload_mesh(m)
+        sv.set_bed_motion(up, on, 0.1)
+        sv.set_state(s.H, s.Hu, s.Hv, s.t)
+        sv.step(40)
+        ref = sv.get_state()                                # staged (pageable) export
+        for dt in (np.float32, np.float64):
+            tdt = torch.float32 if dt == np.float32 else torch.float64
+            out = tuple(torch.empty(m.nc, dtype=tdt).pin_memory().numpy() for _ in range(3))
+            got = (volna.vg_get_state_f32 if dt == np.float32 else volna.vg_get_state)(sv.ctx, m.nc, out=out)
+            for x, y in zip(got[:3], ref[:3]):
+                np.testing.assert_array_equal(x, y.astype(dt))
+        pin = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy() for x in ref[:3]]
+        sv.set_state(*pin, ref[3])                           # in-place import over the moved bed
+        again = sv.get_state()
+        for x, y in zip(again[:3], ref[:3]):
+            np.testing.assert_array_equal(x, y)
