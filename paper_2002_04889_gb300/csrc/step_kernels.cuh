@@ -493,10 +493,10 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     // A: block + ring-1 + ring-2 states into shared memory, and the block's
     // owned faces (a boundary face, a face to the halo, or a face to a block
     // cell of higher local index: every face once) into the queue.  Thread
-    // tid < B takes block cell tid and notes whether the block and its ring 1 are exactly dry (dry land): then
-    // every face of the block has zero interface depths on both sides, hence
-    // zero flux and zero pressure terms, and phases B and C reduce to zero
-    // face terms.
+    // tid < B takes block cell tid.  The threads also note whether the block
+    // and its ring 1 are exactly dry (dry land): then every face of the block
+    // has zero interface depths on both sides, hence zero flux and zero
+    // pressure terms, and phases B and C reduce to zero face terms.
     bool dry = true;
     {
         int gh = -1;
