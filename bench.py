@@ -58,7 +58,7 @@ ALGO_BYTES = {32: {"stage1": 64, "stage2": 76}, 64: {"stage1": 104, "stage2": 12
 # geometry is precomputed), counted in the oracle's own arithmetic by
 # `python -m oracle.count_ops` on a 180,000-cell sample of each generator; the
 # two stages run the same residual, so each stage is taken as half.
-FP64_FLOPS_PER_CELL_STEP = {"thacker": 472.55, "flat": 632.31}
+FP64_FLOPS_PER_CELL_STEP = {"thacker": 473.81, "flat": 634.31, "coast": 588.97}
 # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA thread-operations
 # per cycle per SM (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak) x 2
 # flops x 2.07 GHz maximum SM clock = 1.26 TFLOP/s.
@@ -73,12 +73,28 @@ WORKLOADS = {
     # the free surface (no dry cells, so no wet/dry divergence)
     "flat_basin_allwet_40m": dict(n=4472, kind="flat"),
     "flat_basin_allwet_4m": dict(n=1414, kind="flat"),
+    # ocean-to-coast basin (5.0M triangles graded 20:1, dry land, N-wave source)
+    "coast_basin_5m": dict(n=None, kind="coast", hthr=1e-3),
 }
 
 
-def workload_inputs(name: str, n: int):
-    """Mesh and initial state of a workload's generator on an n x n grid at dx = 0.04 m."""
+def workload_hthr(name: str) -> float:
+    return WORKLOADS[name].get("hthr", 1e-5)
+
+
+def _sample_desc(name: str, n: int) -> str:
+    if WORKLOADS[name].get("kind") == "coast":
+        return f"coast basin of about {2 * n * n} triangles"
+    return f"n={n}, dx=0.04 m"
+
+
+def workload_inputs(name: str, n):
+    """Mesh and initial state of a workload's generator on an n x n grid at dx = 0.04 m
+    (coast basin: about 2 n^2 triangles of the same generator; n = None: 5.0M)."""
     from paper_2002_04889_gb300 import inputs as I
+    if WORKLOADS[name].get("kind") == "coast":
+        m = I.coast_mesh() if n is None else I.coast_mesh_with_cells(2 * n * n, seed=0)
+        return m, I.coast_initial_state(m)
     if WORKLOADS[name].get("kind") == "flat":
         half = 0.5 * n * 0.04
         m = I.flat_basin_mesh(n, half, 10.0, shuffle_cells=True)
@@ -221,7 +237,7 @@ def cpu_baseline(budget_s: float = 15.0, n: int = 1414, workload: str = "thacker
     import oracle as O
     m, s = workload_inputs(workload, n)
     om = O.OracleMesh.from_mesh(m)
-    prm = O.params(h_threshold=1e-5, cfl=0.9)
+    prm = O.params(h_threshold=workload_hthr(workload), cfl=0.9)
     st = (s.H, s.Hu, s.Hv, 0.0)
     steps, t0 = 0, time.perf_counter()
     while True:
@@ -233,7 +249,7 @@ def cpu_baseline(budget_s: float = 15.0, n: int = 1414, workload: str = "thacker
             break
     return {"value": m.nc * steps / el, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
             "sample": f"FP64 oracle, {steps} steps on a {m.nc}-triangle sample of the same "
-                      f"generator (n={n}, dx=0.04 m), {el:.1f} s"}
+                      f"generator ({_sample_desc(workload, n)}), {el:.1f} s"}
 
 
 def batched_leg(torch, stream, steps: int, n_scen: int = 32, renumber: str = "hilbert"):
@@ -370,7 +386,7 @@ def run_reference(args):
     n = 707
     m, s = workload_inputs(args.workload, n)
     om = O.OracleMesh.from_mesh(m)
-    prm = O.params(h_threshold=1e-5, cfl=0.9)
+    prm = O.params(h_threshold=workload_hthr(args.workload), cfl=0.9)
     st = (s.H, s.Hu, s.Hv, 0.0)
     for _ in range(args.warmup):
         r = om.run(prm, st, 1)
@@ -382,7 +398,7 @@ def run_reference(args):
     el = time.perf_counter() - t0
     value = m.nc * args.steps / el
     sample = (f"FP64 CPU oracle, each step one SSP-RK(2,2) step on a {m.nc}-triangle sample of the "
-              f"workload's generator (n={n}, dx=0.04 m)")
+              f"workload's generator ({_sample_desc(args.workload, n)})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -430,7 +446,7 @@ def main():
     mesh, st0 = make_workload(args.workload)
     stream = torch.cuda.Stream()
     sv = volna.Solver(precision=args.precision, device=torch.cuda.current_device(), stream=stream)
-    sv.set_params(h_threshold=1e-5, cfl=0.9)
+    sv.set_params(h_threshold=workload_hthr(args.workload), cfl=0.9)
     sv.upload_mesh(mesh, renumber=args.renumber)
     sv.set_state(st0.H, st0.Hu, st0.Hv, 0.0)
     nc = mesh.nc
@@ -552,7 +568,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "cells": nc, "renumber": args.renumber,
-                           "block_cells": 256, "cfl": 0.9, "h_threshold": 1e-5,
+                           "block_cells": 256, "cfl": 0.9, "h_threshold": workload_hthr(args.workload),
                            "l2": "inputs larger than L2 (%.1f GB resident)" % dev_gb,
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
