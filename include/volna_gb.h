@@ -302,7 +302,11 @@ int vg_adj_forward_binomial(vg_ctx *ctx, int64_t n_steps, double dt, int32_t slo
  * derivative of J with respect to each gauge record.  Outputs (host FP64,
  * original cell / vertex order; any may be NULL): dJ/dH0, dJ/dHu0, dJ/dHv0 [nc]
  * for the initial state, dJ/dz [nc] for the cell beds, dJ/ddepth [nv] for the
- * vertex depths (z = -mean of its three vertex depths).
+ * vertex depths (z = -mean of its three vertex depths).  Scratch device memory
+ * is allocated for the sweep and freed at its end; the first sweep on a mesh
+ * also builds a list of its faces (4 bytes per face) that the context keeps
+ * until the mesh is replaced.  No forward run: VG_ESTATE; allocation failure:
+ * VG_ENOMEM.
  */
 int vg_adj_backward(vg_ctx *ctx, const double *dJ_deta, double *dJ_dH0, double *dJ_dHu0, double *dJ_dHv0,
                     double *dJ_dz, double *dJ_ddepth);
