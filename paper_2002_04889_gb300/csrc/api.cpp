@@ -1276,9 +1276,15 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
                 const int32_t j = hm.nbr[f * hm.nc + k];
                 if (j < 0 || j > k) fl.push_back((int32_t)((k << 2) | f));
             }
-        int e = dmalloc(c, (void **)&c->adj_faces, 4 * std::max<size_t>(fl.size(), 1));
+        int32_t *dev = nullptr;
+        int e = dmalloc(c, (void **)&dev, 4 * std::max<size_t>(fl.size(), 1));
         if (e) return e;
-        VG_CUDA(c, cudaMemcpy(c->adj_faces, fl.data(), 4 * fl.size(), cudaMemcpyHostToDevice));
+        cudaError_t ce = cudaMemcpy(dev, fl.data(), 4 * fl.size(), cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) {
+            dfree(dev);
+            return cuda_fail(c, ce, "face list upload");
+        }
+        c->adj_faces = dev;                   // kept only once complete
         c->n_adj_faces = (int64_t)fl.size();
     }
     const int64_t N = c->adj_n, C = c->adj_every;
