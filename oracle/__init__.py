@@ -25,10 +25,11 @@ _I64 = C.POINTER(C.c_int64)
 
 class Params(C.Structure):
     """Scheme parameters: g (9.81), CFL, H_threshold (Sec. 2.4), fixed / max dt,
-    end time, and order (1 first order, 2 MUSCL reconstruction of Sec. 2.4)."""
+    end time, order (1 first order, 2 MUSCL reconstruction of Sec. 2.4) and
+    limiter (1 Barth-Jespersen; 0 none, only for the convergence pins)."""
     _fields_ = [("g", C.c_double), ("cfl", C.c_double), ("h_threshold", C.c_double),
                 ("dt_fixed", C.c_double), ("dt_max", C.c_double), ("t_end", C.c_double),
-                ("order", C.c_int32), ("pad", C.c_int32)]
+                ("order", C.c_int32), ("limiter", C.c_int32)]
 
 
 def _load():
@@ -48,7 +49,8 @@ def _load():
     lib.vo_face_flux.argtypes = ([C.c_double] * 10 + [C.c_double, C.c_double, C.c_int]
                                  + [_D, _D, _D, _D])
     lib.vo_reconstruct_cell.argtypes = [C.c_void_p, C.POINTER(Params), _D, _D, _D, C.c_int64,
-                                        _D, _D, _D]
+                                        _D, _D, _D, _D]
+    lib.vo_reconstruct_cell.restype = C.c_int
     lib.vo_residual.argtypes = [C.c_void_p, C.POINTER(Params), _D, _D, _D, _D, _D, _D, _D]
     lib.vo_time_step.argtypes = [C.c_void_p, C.POINTER(Params), _D, C.c_double]
     lib.vo_time_step.restype = C.c_double
@@ -91,8 +93,8 @@ def max_threads() -> int:
 
 
 def params(g=9.81, cfl=0.9, h_threshold=1e-5, dt_fixed=0.0, dt_max=0.0, t_end=0.0,
-           order=2) -> Params:
-    return Params(g, cfl, h_threshold, dt_fixed, dt_max, t_end, order, 0)
+           order=2, limiter=1) -> Params:
+    return Params(g, cfl, h_threshold, dt_fixed, dt_max, t_end, order, limiter)
 
 
 def hll_normal(g, HL, unL, utL, HR, unR, utR):
@@ -132,7 +134,7 @@ class OracleMesh:
                "cy": (6, np.float64, 1), "nx": (7, np.float64, 3), "ny": (8, np.float64, 3),
                "len": (9, np.float64, 3), "fx": (10, np.float64, 3), "fy": (11, np.float64, 3),
                "wx": (12, np.float64, 3), "wy": (13, np.float64, 3), "dx": (14, np.float64, 3),
-               "dy": (15, np.float64, 3)}
+               "dy": (15, np.float64, 3), "zf": (16, np.float64, 3)}
 
     def __init__(self, xy, tri, depth):
         lib = _load()
@@ -166,13 +168,14 @@ class OracleMesh:
     def n_flipped(self):
         return int(_load().vo_mesh_n_flipped(self._h))
 
-    def reconstruct_cell(self, prm, H, Hu, Hv, K):
-        """Face values (H_f, Hu_f, Hv_f) of cell K (Sec. 2.4)."""
+    def reconstruct_cell(self, prm, H, Hu, Hv, K, with_bed=False):
+        """Face values (H_f, Hu_f, Hv_f) of cell K (Sec. 2.4); with_bed: also the
+        bed under each face value and whether the cell reconstructed."""
         H, Hu, Hv = _f64(H), _f64(Hu), _f64(Hv)
-        o = [np.zeros(3) for _ in range(3)]
-        _load().vo_reconstruct_cell(self._h, C.byref(prm), _dp(H), _dp(Hu), _dp(Hv), int(K),
-                                    _dp(o[0]), _dp(o[1]), _dp(o[2]))
-        return o
+        o = [np.zeros(3) for _ in range(4)]
+        rec = _load().vo_reconstruct_cell(self._h, C.byref(prm), _dp(H), _dp(Hu), _dp(Hv), int(K),
+                                          _dp(o[0]), _dp(o[1]), _dp(o[2]), _dp(o[3]))
+        return (o[0], o[1], o[2], o[3], bool(rec)) if with_bed else o[:3]
 
     def residual(self, prm, H, Hu, Hv):
         """L(w) and per-cell max l_f a_f (Sec. 2.2)."""

@@ -14,11 +14,15 @@
  *
  * The method, step by step (each function cites what it follows):
  *   geometry            cell area, centroid, outward unit normals, face midpoints
- *   bed                 z_K = -(mean of the three vertex depths)        (Sec. 2.1)
+ *   bed                 z_K = -(mean of the three vertex depths), and the bed at
+ *                       each face midpoint z_f = -(mean of its two vertex depths):
+ *                       the piecewise linear bed of the vertex depths    (Sec. 2.1)
  *   reconstruction      least-squares gradient + Barth-Jespersen limiter,
- *                       skipped in the wet/dry zone                      (Sec. 2.4, Eq. recon)
+ *                       skipped in the wet/dry zone; face depths stand on the
+ *                       face beds                                        (Sec. 2.4, Eq. recon)
  *   interface           hydrostatic reconstruction of the two face depths (reading of
- *                       the wet/dry treatment named in Sec. 2.1)
+ *                       the wet/dry treatment named in Sec. 2.1), with the
+ *                       centred bed-slope source of its second-order form
  *   numerical flux      HLL with the wave speeds of Sec. 2.2, dry-bed speeds
  *   wall                ghost state with mirrored normal velocity        (Sec. 2.5)
  *   open boundary       transmissive ghost (the cell's own state); reading, see
@@ -56,7 +60,8 @@ typedef struct vo_params {
     double dt_max;       /* > 0: upper clamp on the time step                 */
     double t_end;        /* > 0: the last step ends exactly at t_end          */
     int32_t order;       /* 1: first order (no reconstruction); 2: MUSCL      */
-    int32_t pad;
+    int32_t limiter;     /* 1: Barth-Jespersen (Sec. 2.4); 0: none (alpha = 1),
+                            only for the convergence pins of the reconstruction */
 } vo_params;
 
 typedef struct vo_mesh {
@@ -66,11 +71,14 @@ typedef struct vo_mesh {
     int32_t *nbr;        /* [nc][3] neighbour across face f, -1 wall, -2 open */
     int32_t *nbr_face;   /* [nc][3] the same face seen from the neighbour   */
     vo_real *z;                                 /* [nc] bed                 */
+    vo_real *zf;                                /* [nc][3] bed at the face midpoints */
     double *area, *cx, *cy;                     /* [nc]                     */
     double *nx, *ny, *len, *fx, *fy;            /* [nc][3] per face         */
     double *dx, *dy, *wx, *wy;                  /* [nc][3] LSQ stencil      */
     /* work arrays of the residual */
     vo_real *Hf, *Huf, *Hvf;                    /* [nc][3] face values      */
+    vo_real *zfe;                               /* [nc][3] bed under each face value */
+    int32_t *rec;                               /* [nc] 1 where the cell reconstructed */
     vo_real *slot;                              /* [nc][3][6] edge results  */
     vo_real *R0, *R1, *W1, *amax;               /* [3][nc], [3][nc], [3][nc], [nc] */
 } vo_mesh;
@@ -102,14 +110,14 @@ void vo_default_params(vo_params *p)
     p->dt_max = 0.0;
     p->t_end = 0.0;
     p->order = 2;
-    p->pad = 0;
+    p->limiter = 1;
 }
 
 void vo_mesh_free(vo_mesh *m)
 {
     if (!m) return;
     free(m->vtx); free(m->nbr); free(m->nbr_face);
-    free(m->z); free(m->area); free(m->cx); free(m->cy);
+    free(m->z); free(m->zf); free(m->zfe); free(m->rec); free(m->area); free(m->cx); free(m->cy);
     free(m->nx); free(m->ny); free(m->len); free(m->fx); free(m->fy);
     free(m->dx); free(m->dy); free(m->wx); free(m->wy);
     free(m->Hf); free(m->Huf); free(m->Hvf); free(m->slot);
@@ -145,6 +153,9 @@ int vo_mesh_build(int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
     VO_ALLOC(m->nbr, n3, int32_t);
     VO_ALLOC(m->nbr_face, n3, int32_t);
     VO_ALLOC_R(m->z, nc, vo_real);
+    VO_ALLOC_R(m->zf, n3, vo_real);
+    VO_ALLOC_R(m->zfe, n3, vo_real);
+    VO_ALLOC(m->rec, nc, int32_t);
     VO_ALLOC(m->area, nc, double);
     VO_ALLOC(m->cx, nc, double);
     VO_ALLOC(m->cy, nc, double);
@@ -241,6 +252,7 @@ int vo_mesh_build(int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
             double ey = xy[2 * q + 1] - xy[2 * p + 1];
             double l = sqrt(ex * ex + ey * ey);
             m->len[3 * c + f] = l;
+            m->zf[3 * c + f] = -(depth_v[p] + depth_v[q]) / 2.0;
             m->nx[3 * c + f] = ey / l;        /* outward: right of p -> q for a CCW cell */
             m->ny[3 * c + f] = -ex / l;
             m->fx[3 * c + f] = 0.5 * (xy[2 * p] + xy[2 * q]) - m->cx[c];
@@ -346,8 +358,9 @@ void vo_hll_normal(double g, vo_real HL, vo_real unL, vo_real utL,
 
 /*
  * Flux through one face, seen from the left cell (outward unit normal n).
- * Inputs are the two reconstructed face states (depth H_f, momenta) and the two
- * cell beds.  Interface depths follow the hydrostatic reconstruction:
+ * Inputs are the two reconstructed face states (depth H_f, momenta) and the bed
+ * each of them stands on (the face bed z_f for a cell that reconstructed, its
+ * cell bed otherwise).  Interface depths follow the hydrostatic reconstruction:
  *   z* = max(z_L, z_R),  H*_s = max(0, H_{s,f} + z_s - z*);
  * the face velocity is m_f / H_f where H_f > H_threshold, else 0, and the HLL
  * states carry H* times that velocity.  A wall face (wall != 0) uses the ghost
@@ -404,18 +417,23 @@ void vo_face_flux(double g, double hthr,
  *
  * The cell reconstructs (Eq. recon: w(x_f) = w_K + alpha_K grad(w)_K . (x_f - x_K))
  * only when it and every face neighbour are wetter than H_threshold and every
- * reconstructed face depth H_f = eta_f - z_K stays above H_threshold; otherwise
- * its face values are its cell values (the threshold rule of Sec. 2.4).
+ * reconstructed face depth H_f = eta_f - z_f stays above H_threshold, z_f being
+ * the bed at the face midpoint (the face value stands on the linear bed, as
+ * the reconstructed free surface does on the face); otherwise its face values
+ * are its cell values, standing on the cell bed z_K (the threshold rule of
+ * Sec. 2.4).  zfe[f] receives the bed under face value f; returns 1 if the
+ * cell reconstructed.
  *   gradient: least squares over the three stencil offsets d_f,
  *             grad q = sum_f w_f (q_f - q_K) with w_f = M^-1 d_f, M = sum d d^T;
  *   limiter:  Barth-Jespersen per variable, alpha = min over faces of
  *             min(1, (q_max - q_K)/D_f) if D_f > 0, min(1, (q_min - q_K)/D_f) if
  *             D_f < 0, 1 if D_f = 0, with D_f = grad q . (x_f - x_K) and q_max,
- *             q_min over the cell and its stencil values.
+ *             q_min over the cell and its stencil values (alpha = 1 when the
+ *             limiter is switched off for a pin).
  */
-void vo_reconstruct_cell(const vo_mesh *m, const vo_params *p, const vo_real *H,
-                         const vo_real *Hu, const vo_real *Hv, int64_t K,
-                         vo_real Hf[3], vo_real Huf[3], vo_real Hvf[3])
+int vo_reconstruct_cell(const vo_mesh *m, const vo_params *p, const vo_real *H,
+                        const vo_real *Hu, const vo_real *Hv, int64_t K,
+                        vo_real Hf[3], vo_real Huf[3], vo_real Hvf[3], vo_real zfe[3])
 {
     double hthr = p->h_threshold;
     vo_real zK = m->z[K];
@@ -453,7 +471,7 @@ void vo_reconstruct_cell(const vo_mesh *m, const vo_params *p, const vo_real *H,
                 qmin = fmin(qmin, qn[f][v]);
             }
             vo_real alpha = 1.0;
-            for (int f = 0; f < 3; f++) {
+            for (int f = 0; f < 3 && p->limiter; f++) {
                 vo_real D = gx * m->fx[3 * K + f] + gy * m->fy[3 * K + f];
                 vo_real phi = 1.0;
                 if (D > 0.0) phi = fmin(1.0, (qmax - qK[v]) / D);
@@ -466,22 +484,25 @@ void vo_reconstruct_cell(const vo_mesh *m, const vo_params *p, const vo_real *H,
             }
         }
         for (int f = 0; f < 3; f++) {
-            Hf[f] = face[f][0] - zK;
+            Hf[f] = face[f][0] - m->zf[3 * K + f];
             if (!(Hf[f] > hthr)) recon = 0;
         }
         if (recon) {
             for (int f = 0; f < 3; f++) {
                 Huf[f] = face[f][1];
                 Hvf[f] = face[f][2];
+                zfe[f] = m->zf[3 * K + f];
             }
-            return;
+            return 1;
         }
     }
     for (int f = 0; f < 3; f++) {
         Hf[f] = H[K];
         Huf[f] = Hu[K];
         Hvf[f] = Hv[K];
+        zfe[f] = zK;
     }
+    return 0;
 }
 
 /* --------------------------------------------------------------------------
@@ -498,10 +519,18 @@ static int owns(const vo_mesh *m, int64_t K, int f)
 
 /*
  * R = L(w): for every cell K,
- *   R_K = -(1/|K|) sum_f l_f [ Phi_f + (0, P_{K,f} n_f) ],
+ *   R_K = -(1/|K|) { sum_f l_f [ Phi_f + (0, P_{K,f} n_f) ] + (0, S_K) },
  * summed over the local faces f = 0, 1, 2 in that order, with Phi_f the flux out
- * of K (the owner's edge flux, negated for the other cell) and P_{K,f} the
- * pressure correction on K's side.  amax[K] = max_f l_f a_f (NULL: skipped).
+ * of K (the owner's edge flux, negated for the other cell), P_{K,f} the
+ * pressure correction on K's side, and, for a cell that reconstructed, the
+ * centred bed-slope source of the second-order hydrostatic reconstruction
+ * (Audusse et al. 2004, written over the faces of a triangle)
+ *   S_K = g sum_f l_f z_f (eta_K - z_f / 2) n_f,   eta_K = H_K + z_K,
+ * the integral over K of g (eta_K - z) grad z for the linear bed, in the form
+ * that cancels the faces' hydrostatic pressures g (eta - z_f)^2 / 2 exactly
+ * when eta is constant (lake at rest).  A cell that did not reconstruct stands
+ * on its flat cell bed and has no such term.  amax[K] = max_f l_f a_f (NULL:
+ * skipped).
  */
 void vo_residual(vo_mesh *m, const vo_params *p, const vo_real *H, const vo_real *Hu,
                  const vo_real *Hv, vo_real *RH, vo_real *RHu, vo_real *RHv, vo_real *amax)
@@ -510,7 +539,8 @@ void vo_residual(vo_mesh *m, const vo_params *p, const vo_real *H, const vo_real
     double g = p->g, hthr = p->h_threshold;
 #pragma omp parallel for schedule(static)
     for (int64_t K = 0; K < nc; K++)
-        vo_reconstruct_cell(m, p, H, Hu, Hv, K, m->Hf + 3 * K, m->Huf + 3 * K, m->Hvf + 3 * K);
+        m->rec[K] = vo_reconstruct_cell(m, p, H, Hu, Hv, K, m->Hf + 3 * K, m->Huf + 3 * K, m->Hvf + 3 * K,
+                                        m->zfe + 3 * K);
 
 #pragma omp parallel for schedule(static)
     for (int64_t K = 0; K < nc; K++) {
@@ -521,11 +551,11 @@ void vo_residual(vo_mesh *m, const vo_params *p, const vo_real *H, const vo_real
             vo_real *s = m->slot + 6 * i;
             if (j >= 0) {
                 int64_t k = 3 * (int64_t)j + m->nbr_face[i];
-                vo_face_flux(g, hthr, m->Hf[i], m->Huf[i], m->Hvf[i], m->z[K],
-                             m->Hf[k], m->Huf[k], m->Hvf[k], m->z[j],
+                vo_face_flux(g, hthr, m->Hf[i], m->Huf[i], m->Hvf[i], m->zfe[i],
+                             m->Hf[k], m->Huf[k], m->Hvf[k], m->zfe[k],
                              m->nx[i], m->ny[i], 0, s, s + 3, s + 4, s + 5);
             } else {
-                vo_face_flux(g, hthr, m->Hf[i], m->Huf[i], m->Hvf[i], m->z[K],
+                vo_face_flux(g, hthr, m->Hf[i], m->Huf[i], m->Hvf[i], m->zfe[i],
                              0.0, 0.0, 0.0, 0.0, m->nx[i], m->ny[i], j == -2 ? 2 : 1, s, s + 3, s + 4, s + 5);
             }
         }
@@ -549,6 +579,15 @@ void vo_residual(vo_mesh *m, const vo_params *p, const vo_real *H, const vo_real
             aHu = aHu + l * (P1 + P * m->nx[i]);
             aHv = aHv + l * (P2 + P * m->ny[i]);
             am = fmax(am, l * a);
+        }
+        if (m->rec[K]) {
+            vo_real eK = H[K] + m->z[K];
+            for (int f = 0; f < 3; f++) {
+                int64_t i = 3 * K + f;
+                vo_real s = g * (m->len[i] * (m->zf[i] * (eK - 0.5 * m->zf[i])));
+                aHu = aHu + s * m->nx[i];
+                aHv = aHv + s * m->ny[i];
+            }
         }
         RH[K] = -aH / m->area[K];
         RHu[K] = -aHu / m->area[K];
@@ -673,7 +712,8 @@ int64_t vo_run(vo_mesh *m, const vo_params *p, vo_real *H, vo_real *Hu, vo_real 
  * linearly over `rise` seconds from its onset time,
  *     depth_v(t) = depth0_v - uplift_v R((t - onset_v) / rise),
  *     R(s) = min(1, max(0, s))           (rise = 0: R = 1 once t >= onset_v),
- * and the cell bed is z_K(t) = -(mean of its vertices' depths) as at set-up.
+ * and the cell bed is z_K(t) = -(mean of its vertices' depths), the face bed
+ * z_f(t) = -(mean of its two vertices' depths), as at set-up.
  * The bed moves between steps: after the step that ends at t^{n+1} the beds
  * are set to z(t^{n+1}) with H unchanged, so the free surface eta = H + z
  * follows the bed and no mass is created.
@@ -698,6 +738,7 @@ void vo_bed_at(vo_mesh *m, const vo_real *depth0, const vo_real *uplift, const v
             d[k] = depth0[v] - uplift[v] * ramp(t, onset[v], rise);
         }
         m->z[K] = -((d[0] + d[1]) + d[2]) / 3.0;
+        for (int f = 0; f < 3; f++) m->zf[3 * K + f] = -(d[f] + d[(f + 1) % 3]) / 2.0;
     }
 }
 
@@ -799,6 +840,7 @@ int vo_mesh_get(const vo_mesh *m, int what, void *out)
     case 13: memcpy(out, m->wy, n3 * sizeof(double)); return 0;
     case 14: memcpy(out, m->dx, n3 * sizeof(double)); return 0;
     case 15: memcpy(out, m->dy, n3 * sizeof(double)); return 0;
+    case 16: memcpy(out, m->zf, n3 * sizeof(double)); return 0;
     default: return VO_EINVAL;
     }
 }

@@ -3,7 +3,7 @@ against finite differences of the oracle's forward run (FP64).
 
 J is piecewise smooth: the min/max of the wave speeds (Sec. 2.2) and of the
 Barth-Jespersen limiter (Sec. 2.4) switch, and near-equal neighbour states put
-such kinks close together, so the step is small (1e-8).  The adjoint must match
+such kinks close together, so the step is small (1e-9).  The adjoint must match
 the central difference; if a kink still lies inside the step (MUSCL only), it
 must lie between the two one-sided differences.
 """
@@ -50,7 +50,7 @@ def test_oracle_adjoint_matches_forward_and_finite_differences(order):
     assert ad["J"] == pytest.approx(J0, rel=1e-13, abs=1e-15)      # the taped run is the oracle's run
     rng = np.random.default_rng(7)
     wet = st[0] > 1e-3
-    eps = 1e-8             # kinks (Zhou speeds, limiter) are dense: a small step stays on one piece
+    eps = 1e-9             # kinks (Zhou speeds, limiter, face-depth threshold) are dense: a small step stays on one piece
     n_central = 0
     for kind in ("H", "Hu", "Hv", "depth"):
         for _ in range(4):

@@ -100,6 +100,26 @@ def _rand_states(rng, n, dry_frac=0.0):
     return H, rng.normal(0, 1.5, n), rng.normal(0, 1.5, n)
 
 
+def test_face_beds_are_the_linear_bed():
+    """Sec. 2.1 bed from per-vertex depths, read as the piecewise linear bed: for a
+    depth field linear in (x, y) each face bed z_f is that plane at the face
+    midpoint, the cell bed z_K the plane at the centroid, and the three face beds
+    of a cell average to its cell bed (the face midpoints average to the centroid)."""
+    m = I.thacker_mesh(n=12, half_width=1.0)
+    depth = 3.0 + 0.7 * m.xy[:, 0] - 1.3 * m.xy[:, 1]
+    om = O.OracleMesh(m.xy, m.tri, depth)
+    zf, z = om.get("zf"), om.get("z")
+    cx, cy, fx, fy = om.get("cx"), om.get("cy"), om.get("fx"), om.get("fy")
+    plane = lambda x, y: -(3.0 + 0.7 * x - 1.3 * y)
+    np.testing.assert_allclose(zf, plane(cx[:, None] + fx, cy[:, None] + fy), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(z, plane(cx, cy), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(zf.mean(axis=1), z, rtol=0, atol=1e-14)
+    # the two cells of an interior face see the same face bed, bit for bit
+    nbr, nf = om.get("nbr"), om.get("nbr_face")
+    K, f = np.nonzero(nbr >= 0)
+    assert np.array_equal(zf[K, f], zf[nbr[K, f], nf[K, f]])
+
+
 def test_hll_consistency():
     """Sec. 2.2: the flux of two identical states is the true flux of that state."""
     rng = np.random.default_rng(0)
@@ -141,6 +161,31 @@ def test_hll_star_flux_is_rankine_hugoniot():
         assert sL <= unL - math.sqrt(G * HL) + 1e-15
         assert sR >= unR + math.sqrt(G * HR) - 1e-15
     assert n_star > 100
+
+
+def test_hll_star_speeds_from_riemann_invariants():
+    """Sec. 2.2 (after Zhou 2002): u*_n and c* are the star state of the two-
+    rarefaction approximation, i.e. the state joined to the left state by the
+    Riemann invariant u_n + 2c and to the right state by u_n - 2c (exact for two
+    rarefactions).  Here (u*, c*) solve that 2x2 linear system independently,
+    and s_L = min(u_nL - c_L, u* - c*), s_R = max(u* + c*, u_nR + c_R) must match
+    the oracle's speeds.  The states are asymmetric (c_L != c_R, converging and
+    diverging flows), and the star values must be the ones selected in many of
+    them, so a wrong sign in (c_L - c_R) or a wrong weight of (u_nR - u_nL) fails."""
+    rng = np.random.default_rng(11)
+    n_star_L = n_star_R = 0
+    for _ in range(2000):
+        HL, HR = rng.uniform(0.05, 4.0, 2)
+        unL, unR = rng.normal(0.0, 2.0, 2)
+        cL, cR = math.sqrt(G * HL), math.sqrt(G * HR)
+        us, cs = np.linalg.solve(np.array([[1.0, 2.0], [1.0, -2.0]]), np.array([unL + 2 * cL, unR - 2 * cR]))
+        sL, sR = O.hll_speeds(G, HL, unL, HR, unR)
+        eL, eR = min(unL - cL, us - cs), max(us + cs, unR + cR)
+        scale = abs(unL) + abs(unR) + cL + cR
+        assert abs(sL - eL) <= 1e-14 * scale and abs(sR - eR) <= 1e-14 * scale, (HL, unL, HR, unR)
+        n_star_L += (us - cs) < (unL - cL) - 1e-9 * scale
+        n_star_R += (us + cs) > (unR + cR) + 1e-9 * scale
+    assert n_star_L > 400 and n_star_R > 400, (n_star_L, n_star_R)
 
 
 def test_dry_bed_speeds():
@@ -386,27 +431,83 @@ def test_lake_at_rest_over_wet_dry(which):
     z = om.get("z")
     assert (s.H == 0).any() and (s.H > 0).any()
     r = om.run(prm, (s.H, s.Hu, s.Hv, 0.0), 1000)
-    scale = max(1.0, float(s.H.max()))
-    assert np.abs(r["Hu"]).max() <= 1e-12 * scale ** 1.5 * 10
-    assert np.abs(r["Hv"]).max() <= 1e-12 * scale ** 1.5 * 10
     wet = s.H > 0
-    assert np.abs((r["H"] + z)[wet] - (s.H + z)[wet]).max() <= 1e-13 * scale
+    if which == "thacker_bowl":
+        # decimetre depths: absolute bounds
+        mom_tol, eta_tol = 1e-12, 1e-13
+    else:
+        # 4.4 km depths: the hydrostatic pressure g H^2 / 2 is 1e8, so FP64 round-off
+        # of the balance is relative to the depth H and the momentum scale H sqrt(g H)
+        Hm = float(s.H.max())
+        mom_tol, eta_tol = 1e-12 * Hm * math.sqrt(G * Hm), 1e-13 * Hm
+    assert np.abs(r["Hu"]).max() <= mom_tol
+    assert np.abs(r["Hv"]).max() <= mom_tol
+    assert np.abs((r["H"] + z)[wet] - (s.H + z)[wet]).max() <= eta_tol
     assert np.array_equal(r["H"][~wet], s.H[~wet])
 
 
-def test_time_step_rule():
-    """dt = CFL min_K |K| / (3 max_f l_f a_f): no cell exceeds it and one cell attains it."""
+def test_time_step_keeps_depths_positive_at_cfl_one():
+    """Sec. 2.3: the step is stable (here: positivity preserving) when the CFL
+    condition holds with CFL <= 1.  Random wet/dry states (dry cells, thin films
+    and fast flows) over a rough random bed, one SSP-RK(2,2) step at CFL 1 and at
+    0.5: no depth goes negative, in either stage (neg_count = 0), and mass is kept.
+    The positivity argument rests on the time-step rule's constant: the face
+    values of a triangle average to its cell value, so each face may carry a third
+    of the cell's water in one step; a rule with a larger constant would fail."""
+    rng = np.random.default_rng(21)
+    n_fail = 0
+    for trial in range(40):
+        m = I.thacker_mesh(n=8, half_width=1.0, seed=trial)
+        depth = m.depth + 0.05 * rng.standard_normal(m.nv)
+        om = O.OracleMesh(m.xy, m.tri, depth)
+        z = om.get("z")
+        H = np.maximum(0.0, rng.uniform(-0.05, 0.15, m.nc) - z - 0.05)
+        H[rng.uniform(size=m.nc) < 0.3] = 0.0
+        H[rng.uniform(size=m.nc) < 0.2] = 1e-4
+        Hu = H * rng.normal(0.0, 1.5, m.nc)
+        Hv = H * rng.normal(0.0, 1.5, m.nc)
+        for cfl in (1.0, 0.5):
+            r = om.run(O.params(cfl=cfl), (H, Hu, Hv, 0.0), 1)
+            assert r["neg_count"] == 0, (trial, cfl)
+            assert np.all(r["H"] >= 0.0)
+            assert om.mass(r["H"]) == pytest.approx(om.mass(H), rel=1e-13)
+        # the bound is sharp enough to matter: at CFL 3 positivity is lost somewhere
+        n_fail += om.run(O.params(cfl=3.0), (H, Hu, Hv, 0.0), 1)["neg_count"] > 0
+    assert n_fail > 0
+
+
+def test_time_step_clamps():
+    """dt_fixed replaces the CFL rule, dt_max caps it and t_end ends the run
+    exactly (the paper's fixed-step runs of Sec. 3 and its end time)."""
     m = I.thacker_mesh(n=20)
     om = O.OracleMesh.from_mesh(m)
     s = I.thacker_initial_state(m)
-    prm = O.params(cfl=0.9)
-    _, am = om.residual(prm, s.H, s.Hu, s.Hv)
-    dt = om.time_step(prm, am, 0.0)
-    area = om.get("area")
-    lim = 0.9 * area[am > 0] / (3.0 * am[am > 0])
-    assert dt <= lim.min() * (1 + 1e-15) and dt >= lim.min() * (1 - 1e-15)
+    _, am = om.residual(O.params(), s.H, s.Hu, s.Hv)
+    dt = om.time_step(O.params(), am, 0.0)
+    assert dt > 0.0
     assert om.time_step(O.params(t_end=1e-4), am, 0.0) == pytest.approx(1e-4)
     assert om.time_step(O.params(dt_fixed=1e-3), am, 0.0) == 1e-3
+    assert om.time_step(O.params(dt_max=0.5 * dt), am, 0.0) == 0.5 * dt
+
+
+def test_ssp_rk22_is_second_order_in_time():
+    """Sec. 2.3: SSP-RK(2,2) is second order in time.  On a fixed all-wet mesh (so
+    the spatial operator is the same for every run) a Gaussian hump is advanced to
+    T with fixed steps dt, dt/2, dt/4, dt/8 and compared with a dt/64 run of the same
+    operator: the observed temporal order must be about 2 (forward Euler, or a stage
+    combination that drops a term, gives 1).  First-order space keeps L(w) smooth."""
+    m = I.flat_basin_mesh(16, 1.0, 1.0)
+    s = I.gaussian_hump_state(m, 0.0, 0.1, 0.1, -0.05, 0.3)
+    om = O.OracleMesh.from_mesh(m)
+    T, dt0 = 0.064, 0.004
+    def run(dt):
+        r = om.run(O.params(dt_fixed=dt, order=1), (s.H, s.Hu, s.Hv, 0.0), int(round(T / dt)))
+        assert r["t"] == pytest.approx(T, rel=1e-12)
+        return np.concatenate([r["H"], r["Hu"], r["Hv"]])
+    ref = run(dt0 / 64)
+    errs = [np.linalg.norm(run(dt0 / 2 ** k) - ref) for k in range(4)]
+    orders = [math.log2(errs[k] / errs[k + 1]) for k in range(3)]
+    assert all(o > 1.9 for o in orders), (errs, orders)
 
 
 def test_renumbering_invariance_bitwise():
@@ -424,29 +525,62 @@ def test_renumbering_invariance_bitwise():
     assert r1["t"] == r2["t"]
 
 
-def test_thacker_error_decreases_under_refinement():
-    """Sec. 3: the error against the closed form falls as the mesh is refined
-    (dx = 0.16, 0.08, 0.04 on the jittered grid, to t = 0.5 s)."""
-    errs, centre = [], []
-    for n in (25, 50, 100):
-        m = I.thacker_mesh(n=n)
-        om = O.OracleMesh.from_mesh(m)
-        s = I.thacker_initial_state(m)
-        st = (s.H, s.Hu, s.Hv, 0.0)
-        prm = O.params(t_end=0.5)
-        while st[3] < 0.5 - 1e-12:
-            r = om.run(prm, st, 50)
-            st = (r["H"], r["Hu"], r["Hv"], r["t"])
-        cx, cy = om.get("cx"), om.get("cy")
-        eta = st[0] + om.get("z")
-        ea = AN.thacker_eta(cx, cy, 0.5)
-        inner = cx ** 2 + cy ** 2 < 0.5 ** 2
-        errs.append(np.abs(eta - ea)[inner].mean())
-        c0 = np.argmin(cx ** 2 + cy ** 2)
-        centre.append(abs(eta[c0] - ea[c0]))
-    assert errs[0] > errs[1] > errs[2]
-    order = math.log2(errs[1] / errs[2])
-    assert order > 0.8, (errs, order)
+def _thacker_errors(n, limiter, t_end=0.5, half_width=1.2, r_in=0.5):
+    """Thacker's basin (Sec. 3) on the jittered n x n grid of [-1.2, 1.2]^2 (the
+    shoreline never reaches the walls), run to t_end at CFL 0.9.  Returns the
+    interior (r < r_in) L1 and Linf errors of eta against the closed form at the
+    cell centroids at t_end, and the centre gauge's error max_t |eta_K(t) -
+    eta(x_K, t)| for the cell K holding the gauge (0, 0) of Sec. 3, taken at its
+    centroid x_K: the offset between x_K and the gauge point is a sampling error
+    of a piecewise constant gauge, O(h^2) with a constant that depends on where
+    x_K falls, not an error of the scheme."""
+    m = I.thacker_mesh(n=n, half_width=half_width)
+    om = O.OracleMesh.from_mesh(m)
+    s = I.thacker_initial_state(m)
+    st = (s.H, s.Hu, s.Hv, 0.0)
+    prm = O.params(t_end=t_end, limiter=limiter)
+    gc = om.locate(np.array([[0.0, 0.0]]))
+    cx, cy, area = om.get("cx"), om.get("cy"), om.get("area")
+    xg, yg = cx[gc[0]], cy[gc[0]]
+    cen = 0.0
+    while st[3] < t_end - 1e-12:
+        r = om.run(prm, st, 25, gauge_cells=gc)
+        t = st[3] + np.cumsum(r["dts"])
+        taken = r["dts"] > 0
+        ea = np.array([AN.thacker_eta(xg, yg, tt) for tt in t[taken]])
+        cen = max(cen, float(np.abs(r["gauges"][taken, 0] - ea).max()))
+        st = (r["H"], r["Hu"], r["Hv"], r["t"])
+    err = np.abs(st[0] + om.get("z") - AN.thacker_eta(cx, cy, st[3]))
+    inner = cx ** 2 + cy ** 2 < r_in ** 2
+    return float(np.sum((err * area)[inner]) / np.sum(area[inner])), float(err[inner].max()), cen
+
+
+def test_thacker_second_order_without_limiter():
+    """Sec. 3: "Volna-OP2 with the MUSCL extension is 2nd order accurate in space".
+    With the limiter off (alpha = 1), the reconstruction, the face beds with the
+    centred source, the HLL flux and SSP-RK(2,2) together converge at second order:
+    dx = 0.08, 0.04, 0.02, 0.01, interior L1 and Linf errors at t = 0.5 s and the
+    centre gauge's error.  The cell-bed reading (flat bed under every face value)
+    converges at about first order here and fails this test."""
+    e = [_thacker_errors(n, limiter=0) for n in (30, 60, 120, 240)]
+    for k in range(3):
+        assert e[0][k] > e[1][k] > e[2][k] > e[3][k], e
+    order = lambda k, i: math.log2(e[i][k] / e[i + 1][k])
+    assert min(order(0, 1), order(0, 2)) > 1.9, e      # interior L1
+    assert min(order(1, 1), order(1, 2)) > 1.85, e     # interior Linf
+    assert min(order(2, 1), order(2, 2)) > 1.75, e     # centre gauge
+
+
+def test_thacker_converges_with_the_limiter():
+    """Sec. 3 with the Barth-Jespersen limiter of Sec. 2.4 (the paper's scheme):
+    the errors fall under refinement (dx = 0.08, 0.04, 0.02), the interior L1
+    error at second order on the finer pair.  (The limiter clips at the bowl's
+    smooth extremum, which lowers the Linf and centre-gauge orders on finer
+    meshes.)"""
+    e = [_thacker_errors(n, limiter=1) for n in (30, 60, 120)]
+    for k in range(3):
+        assert e[0][k] > e[1][k] > e[2][k], e
+    assert math.log2(e[1][0] / e[2][0]) > 1.8, e
 
 
 def test_ritter_dam_break_converges():
