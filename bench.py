@@ -58,7 +58,7 @@ ALGO_BYTES = {32: {"stage1": 64, "stage2": 76}, 64: {"stage1": 104, "stage2": 12
 # geometry is precomputed), counted in the oracle's own arithmetic by
 # `python -m oracle.count_ops` on a 180,000-cell sample of each generator; the
 # two stages run the same residual, so each stage is taken as half.
-FP64_FLOPS_PER_CELL_STEP = {"thacker": 473.81, "flat": 634.31, "coast": 588.97}
+FP64_FLOPS_PER_CELL_STEP = {"thacker": 508.73, "flat": 690.68, "coast": 638.69}
 # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA thread-operations
 # per cycle per SM (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak) x 2
 # flops x 2.07 GHz maximum SM clock = 1.26 TFLOP/s.
@@ -378,6 +378,67 @@ def adjoint_leg(torch, stream, steps: int, n: int = 707, slots: int = 16):
                                                  "scratch_bytes_per_cell": (slots + 3) * 24 + rec}}
 
 
+def roofline_of(prof, nc: int, precision: int, workload: str, step_ms: float):
+    """Roofline of the dominant stage kernel from the per-kernel CUDA-event profile:
+    HBM (FP32: algorithmic bytes per launch over its duration) or, for FP64, the
+    FP64 units (algorithmic flops per launch over its duration)."""
+    peak, peak_kind = measured_peaks()
+    per_kernel = {k: (n, tot) for k, (n, tot) in prof.items() if n > 0}
+    dom = max(("stage1", "stage2"), key=lambda k: per_kernel.get(k, (0, 0.0))[1])
+    n_l, tot = per_kernel[dom]
+    avg_ms = tot / n_l
+    algo = ALGO_BYTES[precision][dom] * nc
+    achieved = algo / (avg_ms * 1e-3) / 1e9
+    traffic = profiled_traffic(workload, precision, dom)
+    kernel_ms = {k: round(tot_ / max(n_, 1), 4) for k, (n_, tot_) in per_kernel.items()}
+    step_bytes = (ALGO_BYTES[precision]["stage1"] + ALGO_BYTES[precision]["stage2"]) * nc
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom,
+                "algo_bytes_per_launch": algo, "peak_kind": f"{peak_kind} hbm_gbs",
+                "kernel_avg_ms": kernel_ms,
+                "step_algo_gbs": round(step_bytes / (step_ms * 1e-3) / 1e9, 1)}
+    if precision == 64:
+        kind = WORKLOADS[workload].get("kind", "thacker")
+        flops = 0.5 * FP64_FLOPS_PER_CELL_STEP[kind] * nc
+        tflops = flops / (avg_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                    "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                    "kernel": dom, "algo_flops_per_launch": flops,
+                    "peak_kind": "derived: 152 SMs x 4 FP64 flop/cycle x 2.07 GHz",
+                    "kernel_avg_ms": kernel_ms, "hbm_frac": round(achieved / peak, 4)}
+    return roofline
+
+
+def workload_leg(torch, stream, workload: str, precision: int, steps: int, warmup: int = 3, inputs=None,
+                 renumber: str = "hilbert"):
+    """One workload at one precision: device-timed cell-updates/s over `steps` steps
+    (CUDA events on the solver's stream) and the dominant kernel's roofline."""
+    from paper_2002_04889_gb300 import volna
+    mesh, st0 = inputs if inputs is not None else make_workload(workload)
+    sv = volna.Solver(precision=precision, device=torch.cuda.current_device(), stream=stream)
+    try:
+        sv.set_params(h_threshold=workload_hthr(workload), cfl=0.9)
+        sv.upload_mesh(mesh, renumber=renumber)
+        sv.set_state(st0.H, st0.Hu, st0.Hv, 0.0)
+        sv.step(warmup)
+        sv.profile(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        sv.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        prof = sv.get_profile()
+        d = sv.diagnostics()
+    finally:
+        sv.close()
+    return {"workload": workload, "cells": mesh.nc, "dtype": "f32" if precision == 32 else "f64",
+            "steps": steps, "value": mesh.nc * steps / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms / steps, "neg_count": d["neg_count"],
+            "roofline": roofline_of(prof, mesh.nc, precision, workload, ms / steps)}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -425,6 +486,9 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=20, help="0 skips the batched-ensemble leg")
     ap.add_argument("--adjoint-steps", type=int, default=2000, help="0 skips the adjoint-cost leg")
     ap.add_argument("--adjoint-binomial-slots", type=int, default=16, help="0 skips the binomial run")
+    ap.add_argument("--config-legs", type=int, default=1,
+                    help="0 skips the other configurations (the other precision on the same mesh, and "
+                         "the 5M coast basin in FP32 and FP64)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -481,30 +545,7 @@ def main():
     value = replica_throughput(nc, args.steps, ms, ws)
 
     # ---- roofline of the dominant kernel
-    peak, peak_kind = measured_peaks()
-    per_kernel = {k: (n, tot) for k, (n, tot) in prof.items() if n > 0}
-    dom = max(("stage1", "stage2"), key=lambda k: per_kernel.get(k, (0, 0.0))[1])
-    n_l, tot = per_kernel[dom]
-    avg_ms = tot / n_l
-    algo = ALGO_BYTES[args.precision][dom] * nc
-    achieved = algo / (avg_ms * 1e-3) / 1e9
-    traffic = profiled_traffic(args.workload, args.precision, dom)
-    kernel_ms = {k: round(tot_ / max(n_, 1), 4) for k, (n_, tot_) in per_kernel.items()}
-    step_bytes = (ALGO_BYTES[args.precision]["stage1"] + ALGO_BYTES[args.precision]["stage2"]) * nc
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom,
-                "algo_bytes_per_launch": algo, "peak_kind": f"{peak_kind} hbm_gbs",
-                "kernel_avg_ms": kernel_ms,
-                "step_algo_gbs": round(step_bytes / (ms * 1e-3 / args.steps) / 1e9, 1)}
-    if args.precision == 64:
-        kind = WORKLOADS[args.workload].get("kind", "thacker")
-        flops = 0.5 * FP64_FLOPS_PER_CELL_STEP[kind] * nc
-        tflops = flops / (avg_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                    "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
-                    "kernel": dom, "algo_flops_per_launch": flops,
-                    "peak_kind": "derived: 152 SMs x 4 FP64 flop/cycle x 2.07 GHz",
-                    "kernel_avg_ms": kernel_ms, "hbm_frac": round(achieved / peak, 4)}
+    roofline = roofline_of(prof, nc, args.precision, args.workload, ms / args.steps)
 
     # ---- end to end through the C ABI with pinned host buffers
     def end_to_end(host_dtype, steps):
@@ -551,6 +592,27 @@ def main():
         cpu = cpu_baseline(args.cpu_budget, workload=args.workload)
     sv.close()
     batched = adjoint = None
+    configs = None
+    if rank == 0 and args.config_legs > 0 and args.workload == "thacker_paraboloid_40m":
+        # the other precision on the same 40M mesh (FP64: at most 20 timed steps,
+        # ~90 ms each), then the 5M-triangle coast basin in FP32 and FP64
+        configs = {}
+        other = 64 if args.precision == 32 else 32
+        legs = [(f"thacker_paraboloid_40m_fp{other}", "thacker_paraboloid_40m", other, (mesh, st0)),
+                ("coast_basin_5m_fp32", "coast_basin_5m", 32, None),
+                ("coast_basin_5m_fp64", "coast_basin_5m", 64, None)]
+        coast = None
+        for key, wl, prec, inp in legs:
+            try:
+                if wl == "coast_basin_5m":
+                    coast = coast if coast is not None else make_workload(wl)
+                    inp = coast
+                n_steps = min(args.steps, 20) if prec == 64 else args.steps
+                configs[key] = workload_leg(torch, stream, wl, prec, n_steps, inputs=inp,
+                                            renumber=args.renumber)
+            except Exception as e:         # reported, not fatal: the headline is the forward step
+                configs[key] = {"error": str(e)[:300]}
+        del coast
     if rank == 0 and args.batched_steps > 0:
         try:
             batched = batched_leg(torch, stream, args.batched_steps, renumber=args.renumber)
@@ -574,7 +636,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(),
                 "neg_count": d1["neg_count"], "t_sim": d1["t"],
-                "batched": batched, "adjoint": adjoint}
+                "configs": configs, "batched": batched, "adjoint": adjoint}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

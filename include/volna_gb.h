@@ -118,7 +118,10 @@ const char *vg_last_error(vg_ctx *ctx);
  * Sec. 2.1).
  *   xy[nv][2]   vertex coordinates (m), row major
  *   tri[nc][3]  vertex ids per triangle; clockwise triangles are reoriented
- *   depth_v[nv] depth at each vertex; each cell's bed is the mean of its three
+ *   depth_v[nv] depth at each vertex; the bed is the piecewise linear bed of
+ *               the vertex depths: each cell's bed is the mean of its three,
+ *               and each face's bed (under the face values of a cell that
+ *               reconstructs, Sec. 2.4) the mean of its two
  *   renumber    VG_RENUMBER_NONE / _MORTON (Z-order of centroids) / _RCM
  *               (reverse Cuthill-McKee on the face graph) / _HILBERT
  *               (Hilbert-curve order of centroids: compact blocks, the
@@ -229,11 +232,16 @@ int vg_device_bytes(vg_ctx *ctx, int64_t *bytes);
  *
  * The step's scratch (the stage-1 residual and the step scalars) lives in one
  * file-scope device array of fixed size inside the library, so a mesh may have
- * at most VG_NOALLOC_MAX_CELLS cells (VG_EINVAL otherwise).  Every GPU that
- * loads the library holds that array (about 6 MiB) until the process exits.
+ * at most VG_NOALLOC_MAX_CELLS cells (VG_EINVAL otherwise).  The array (about
+ * 6 MiB) is committed on a device at set-up, when a context first uploads a
+ * mesh there: vg_mesh_upload looks up its address (with that device current)
+ * and loads the kernels this call uses, so the call itself loads and allocates
+ * nothing; the array is held until the process exits.
  *
- *   ctx     a context with a mesh (vg_mesh_upload, vg_set_params); its state,
- *           time, gauges and diagnostics are neither read nor changed
+ *   ctx     a context with a mesh (vg_mesh_upload, vg_set_params) and no moving
+ *           bed (vg_set_bed_motion set: VG_ESTATE, since this call steps the
+ *           static bed); its state, time, gauges and diagnostics are neither
+ *           read nor changed
  *   w_in    device array [3][nc] of the context's precision: the state at time t
  *           in the library's internal cell order (vg_get_permutation gives
  *           new_of_old) -- rows H, Hu, Hv for FP64 contexts; for FP32 contexts
@@ -246,9 +254,7 @@ int vg_device_bytes(vg_ctx *ctx, int64_t *bytes);
  * Work runs on the context's stream; the call waits for it.  All calls share
  * the scratch array and leave the last call's contents in it; each call clears
  * the scalars it needs before its kernels run, but calls that overlap on the
- * GPU (other streams or host threads) race on the array.  The first call on a
- * device looks up the array's device address with that device current and
- * caches it, so make that first call before any stream capture.  Returns
+ * GPU (other streams or host threads) race on the array.  Returns
  * VG_ENONFINITE or VG_ENEGDEPTH (with params.strict_positivity) like vg_step.
  */
 #define VG_NOALLOC_MAX_CELLS 262144
@@ -266,7 +272,8 @@ int vg_step_noalloc(vg_ctx *ctx, const void *w_in, void *w_out, double t, double
  * ------------------------------------------------------------------------ */
 
 /* Replace the per-vertex bathymetry depth (as in vg_mesh_upload) of the
-   uploaded mesh; the cell beds are recomputed.  The state is unchanged. */
+   uploaded mesh; the cell beds and the face beds are recomputed.  The state is
+   unchanged. */
 int vg_set_depth(vg_ctx *ctx, const double *depth_v);
 
 /*
@@ -301,8 +308,11 @@ int vg_adj_forward_binomial(vg_ctx *ctx, int64_t n_steps, double dt, int32_t slo
  * Reverse sweep of the last vg_adj_forward run.  dJ_deta[n_steps + 1][G] is the
  * derivative of J with respect to each gauge record.  Outputs (host FP64,
  * original cell / vertex order; any may be NULL): dJ/dH0, dJ/dHu0, dJ/dHv0 [nc]
- * for the initial state, dJ/dz [nc] for the cell beds, dJ/ddepth [nv] for the
- * vertex depths (z = -mean of its three vertex depths).  Scratch device memory
+ * for the initial state, dJ/dz [nc] for the cell beds z_K alone (the face beds
+ * held fixed), dJ/ddepth [nv] for the vertex depths, through both the cell beds
+ * (z_K = -mean of its three vertex depths) and the face beds under the face
+ * values of reconstructing cells (z_f = -mean of the face's two vertex
+ * depths).  Scratch device memory
  * is allocated for the sweep and freed at its end; the first sweep on a mesh
  * also builds a list of its faces (4 bytes per face) that the context keeps
  * until the mesh is replaced.  No forward run: VG_ESTATE; allocation failure:
@@ -339,14 +349,15 @@ int vg_set_open_boundary(vg_ctx *ctx, int64_t n, const int32_t *edges);
  * linearly over `rise` seconds from its onset time onset_v [nv]:
  *     depth_v(t) = depth0_v - uplift_v * min(1, max(0, (t - onset_v) / rise))
  * (rise = 0: a step at onset), with depth0 the depths of vg_mesh_upload /
- * vg_set_depth.  The cell beds z_K = -(mean of their vertices' depths) are set
- * at the end of every step to the bed of the step's end time, keeping H (the
+ * vg_set_depth.  The cell beds z_K = -(mean of their vertices' depths) and face
+ * beds z_f = -(mean of the face's two vertex depths) are set at the end of
+ * every step to the bed of the step's end time, keeping H (the
  * free surface follows the bed; no mass is created), before the gauges record;
  * vg_set_state (and this call, for the current state) sets the bed of the
  * state's time.  uplift_v = NULL removes the motion and restores the static
  * bed (keeping H).  Host arrays, caller-owned, copied; non-finite values or a
- * negative rise: VG_EINVAL.  One extra launch per step while set.  Not applied
- * by vg_step_noalloc; vg_set_depth fails with VG_ESTATE while it is set.  The
+ * negative rise: VG_EINVAL.  One extra launch per step while set.  While it
+ * is set, vg_step_noalloc and vg_set_depth fail with VG_ESTATE.  The
  * adjoint (vg_adj_forward / vg_adj_backward) differentiates through it, and
  * vg_adj_bed_gradient returns the gradients with respect to uplift_v and
  * onset_v. */

@@ -6,11 +6,14 @@
 //   adj_face_values   forward face values FV[3 vars][3 faces][nc] at w
 //   adj_flux_vjp      per owned face: Phi-bar, P-bar from R-bar of both cells,
 //                     reverse of the interface (hydrostatic depths, HLL with its
-//                     branch and speed choices, velocities) -> FV-bar and z-bar
-//                     into the (cell, face) slots of both sides
+//                     branch and speed choices, velocities) -> FV-bar and the
+//                     adjoint of the bed under each face value into the (cell,
+//                     face) slots of both sides
 //   adj_recon_vjp     per cell: reverse of the limited least-squares
-//                     reconstruction -> the cell's own w-bar, z-bar, and what it
-//                     sends to each face neighbour ((cell, face) slots)
+//                     reconstruction and, for a cell standing on its face beds,
+//                     of the centred bed-slope source -> the cell's own w-bar,
+//                     cell-bed and face-bed adjoints, and what it sends to each
+//                     face neighbour ((cell, face) slots)
 //   adj_gather        per cell: own part + the slots its neighbours sent to it
 // Branches are frozen where the forward run took them; min/max ties resolve to
 // the first argument (the convention of the oracle's taping adjoint).
@@ -28,6 +31,8 @@ struct AdjMesh {
     int nc, order;
     const double *geo;       // [GEO_ROWS][nc]
     const double *z;         // [nc]
+    const double *zf;        // [3][nc] face beds
+    const uint8_t *rec;      // [nc] the stage's reconstruction flags (forward record)
     const int32_t *nbr;      // [3][nc]
     const uint16_t *nbrl;    // [3][nc]: low 2 bits = neighbour's face (not a wall)
     const int32_t *faces;    // every face once: (owning cell << 2) | face
@@ -36,6 +41,13 @@ struct AdjMesh {
 };
 
 __device__ __forceinline__ double G(const AdjMesh &m, int row, int k) { return m.geo[row * m.nc + k]; }
+
+// The bed under face value f of cell K: its face bed where K reconstructed,
+// its cell bed otherwise.
+__device__ __forceinline__ double bed_under(const AdjMesh &m, int K, int f)
+{
+    return m.rec[K] ? m.zf[f * m.nc + K] : m.z[K];
+}
 
 // Forward reconstruction of cell K (the same evaluation order as the forward
 // kernels), keeping what the reverse needs.
@@ -115,7 +127,7 @@ __device__ void recon_forward(const AdjMesh &m, const double *w, int K, ReconFwd
             for (int f = 0; f < 3; f++) face[f][v] = R.qK[v] + alpha * R.D[v][f];
         }
         for (int f = 0; f < 3; f++) {
-            Hf[f] = face[f][0] - zK;
+            Hf[f] = face[f][0] - m.zf[f * nc + K];
             if (!(Hf[f] > m.hthr)) recon = false;
             Huf[f] = face[f][1];
             Hvf[f] = face[f][2];
@@ -377,12 +389,12 @@ __global__ void adj_flux_vjp_kernel(AdjMesh m, const double *FV, const double *R
                 HfR = FV[(0 * 3 + fj) * (size_t)nc + j];
                 HufR = FV[(1 * 3 + fj) * (size_t)nc + j];
                 HvfR = FV[(2 * 3 + fj) * (size_t)nc + j];
-                zR = m.z[j];
+                zR = bed_under(m, j, fj);
             }
             double bL[4], bR[4];
             flux_vjp(m, FV[(0 * 3 + f) * (size_t)nc + K], FV[(1 * 3 + f) * (size_t)nc + K],
-                     FV[(2 * 3 + f) * (size_t)nc + K], m.z[K], HfR, HufR, HvfR, zR, nx, ny, wall, Pb, PLb, PRb, bL, bR,
-                     0.0, j == -2);
+                     FV[(2 * 3 + f) * (size_t)nc + K], bed_under(m, K, f), HfR, HufR, HvfR, zR, nx, ny, wall, Pb, PLb,
+                     PRb, bL, bR, 0.0, j == -2);
             for (int v = 0; v < 3; v++) FVb[(v * 3 + f) * (size_t)nc + K] = bL[v];
             zfb[f * (size_t)nc + K] = bL[3];
             if (!wall) {
@@ -393,41 +405,65 @@ __global__ void adj_flux_vjp_kernel(AdjMesh m, const double *FV, const double *R
     }
 }
 
-// Per cell: reverse of the reconstruction.  own[4][nc] = (H, Hu, Hv, z)-bar of
-// the cell itself (including the flux slots' z-bar); send[(f*4+k)*nc + K] = the
-// (H, Hu, Hv, z)-bar that cell K passes to its face-f neighbour.
-__global__ void adj_recon_vjp_kernel(AdjMesh m, const double *w, const double *FVb, const double *zfb, double *own,
-                                     double *send)
+// Per cell: reverse of the reconstruction.  own[7][nc] = (H, Hu, Hv, z_K)-bar of
+// the cell itself, then the adjoints of its three face beds; send[(f*4+k)*nc + K]
+// = the (H, Hu, Hv, z)-bar that cell K passes to its face-f neighbour.  The
+// flux slots' bed adjoint (zfb) belongs to the bed under the face value: the
+// face bed where the cell reconstructed, its cell bed otherwise.  A cell that
+// reconstructed also carries the centred source g sum_f l_f z_f (eta_K - z_f/2)
+// n_f of its momentum residual R = -(1/|K|)(... + source): with
+// q_f = -(g/|K|) l_f (n_f . (R-bar_Hu, R-bar_Hv)), eta-bar_K += sum_f q_f z_f and
+// z_f-bar += q_f (eta_K - z_f).
+__global__ void adj_recon_vjp_kernel(AdjMesh m, const double *w, const double *Rb, const double *FVb,
+                                     const double *zfb, double *own, double *send)
 {
     const int nc = m.nc;
     for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < nc; K += gridDim.x * blockDim.x) {
         double fb[3][3];   // [v][f]
-        bool any = false;
+        bool any = m.rec[K] && (Rb[nc + K] != 0.0 || Rb[2 * (size_t)nc + K] != 0.0);
         for (int v = 0; v < 3; v++)
             for (int f = 0; f < 3; f++) {
                 fb[v][f] = FVb[(v * 3 + f) * (size_t)nc + K];
                 any = any || fb[v][f] != 0.0;
             }
-        double zsum = 0.0;
-        for (int f = 0; f < 3; f++) zsum += zfb[f * (size_t)nc + K];
+        double zsl[3];
+        for (int f = 0; f < 3; f++) zsl[f] = zfb[f * (size_t)nc + K];
         if (!any) {                      // nothing flows back through the reconstruction
             own[K] = 0.0;
             own[nc + K] = 0.0;
             own[2 * (size_t)nc + K] = 0.0;
-            own[3 * (size_t)nc + K] = zsum;
+            const bool rk = m.rec[K];
+            own[3 * (size_t)nc + K] = rk ? 0.0 : (zsl[0] + zsl[1]) + zsl[2];
+            for (int f = 0; f < 3; f++) own[(4 + f) * (size_t)nc + K] = rk ? zsl[f] : 0.0;
             for (int q = 0; q < 12; q++) send[q * (size_t)nc + K] = 0.0;
             continue;
         }
         ReconFwd R;
         double Hf[3], Huf[3], Hvf[3];
         recon_forward(m, w, K, R, Hf, Huf, Hvf);
-        double Hb = 0.0, Hub = 0.0, Hvb = 0.0, zb = zsum;
+        double Hb = 0.0, Hub = 0.0, Hvb = 0.0, zb = 0.0, zfbK[3] = {0.0, 0.0, 0.0};
         double qnb[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};   // [f][v]
         if (!R.recon) {
+            zb = (zsl[0] + zsl[1]) + zsl[2];
             for (int f = 0; f < 3; f++) { Hb += fb[0][f]; Hub += fb[1][f]; Hvb += fb[2][f]; }
         } else {
             double qKb[3] = {0, 0, 0};
-            for (int f = 0; f < 3; f++) zb -= fb[0][f];      // H_f = eta_f - z_K
+            for (int f = 0; f < 3; f++) zfbK[f] = zsl[f] - fb[0][f];      // H_f = eta_f - z_f
+            {
+                // the centred source
+                const double c = -m.g / G(m, GEO_AREA, K);
+                const double rbu = Rb[nc + K], rbv = Rb[2 * (size_t)nc + K];
+                const double eK = w[K] + m.z[K];
+                double eb = 0.0;
+                for (int f = 0; f < 3; f++) {
+                    const double zff = m.zf[f * nc + K];
+                    const double q = c * (G(m, GEO_LEN + f, K) * (G(m, GEO_NX + f, K) * rbu + G(m, GEO_NY + f, K) * rbv));
+                    eb += q * zff;
+                    zfbK[f] += q * (eK - zff);
+                }
+                Hb += eb;
+                zb += eb;
+            }
             for (int v = 0; v < 3; v++) {
                 double ab = 0.0, Db[3];
                 for (int f = 0; f < 3; f++) {
@@ -488,6 +524,7 @@ __global__ void adj_recon_vjp_kernel(AdjMesh m, const double *w, const double *F
         own[nc + K] = Hub;
         own[2 * (size_t)nc + K] = Hvb;
         own[3 * (size_t)nc + K] = zb;
+        for (int f = 0; f < 3; f++) own[(4 + f) * (size_t)nc + K] = zfbK[f];
         for (int f = 0; f < 3; f++) {
             send[(f * 4 + 0) * (size_t)nc + K] = qnb[f][0];     // eta-bar -> H-bar and z-bar
             send[(f * 4 + 1) * (size_t)nc + K] = qnb[f][1];
@@ -497,7 +534,8 @@ __global__ void adj_recon_vjp_kernel(AdjMesh m, const double *w, const double *F
     }
 }
 
-// wb[3][nc] += own + sum over faces of what the face neighbour sent; zb[nc] likewise.
+// wb[3][nc] += own + sum over faces of what the face neighbour sent; zb[nc] (cell
+// beds) likewise; zb rows 1..3 (face beds) += the cell's own face-bed adjoints.
 __global__ void adj_gather_kernel(AdjMesh m, const double *own, const double *send, double *wb, double *zb)
 {
     const int nc = m.nc;
@@ -513,6 +551,7 @@ __global__ void adj_gather_kernel(AdjMesh m, const double *own, const double *se
         wb[nc + K] += a[1];
         wb[2 * (size_t)nc + K] += a[2];
         zb[K] += a[3];
+        for (int f = 0; f < 3; f++) zb[(1 + f) * (size_t)nc + K] += own[(4 + f) * (size_t)nc + K];
     }
 }
 
@@ -652,13 +691,13 @@ __device__ FaceIn face_in(const AdjMesh &m, const double *FV, int K, int f)
     r.HfL = FV[(0 * 3 + f) * (size_t)nc + K];
     r.HufL = FV[(1 * 3 + f) * (size_t)nc + K];
     r.HvfL = FV[(2 * 3 + f) * (size_t)nc + K];
-    r.zL = m.z[K];
+    r.zL = bed_under(m, K, f);
     r.HfR = r.HufR = r.HvfR = r.zR = 0.0;
     if (!r.wall) {
         r.HfR = FV[(0 * 3 + r.fj) * (size_t)nc + r.j];
         r.HufR = FV[(1 * 3 + r.fj) * (size_t)nc + r.j];
         r.HvfR = FV[(2 * 3 + r.fj) * (size_t)nc + r.j];
-        r.zR = m.z[r.j];
+        r.zR = bed_under(m, r.j, r.fj);
     }
     r.nx = G(m, GEO_NX + f, K);
     r.ny = G(m, GEO_NY + f, K);
@@ -773,15 +812,17 @@ __global__ void adj_dot_final_kernel(int nparts, const double *part, double scal
 }
 
 // ---------------------------------------------------------------------------
-// Moving bed: the bed of step n is z_K(t_n) = -(1/3) sum_{v in K} (depth0_v -
-// uplift_v R((t_n - onset_v) / rise)).  With zs the adjoint of that step's bed
-// (its residuals and gauge record), per vertex s_v = sum_{K around v} zs_K in a
-// fixed order and
-//   uplift-bar_v += s_v R / 3,   onset-bar_v += -s_v uplift_v R' / 3,
-//   t-bar_n = sum_v s_v uplift_v R' / 3      (R' = dR/dt = 1 / rise inside the ramp),
+// Moving bed: the beds of step n are z_K(t_n) = -(1/3) sum_{v in K} d_v(t_n) and
+// z_f(t_n) = -(1/2) sum_{v on f} d_v(t_n), d_v(t) = depth0_v - uplift_v R((t -
+// onset_v) / rise).  With zs the adjoints of that step's beds (its residuals
+// and gauge record; row 0 cell beds, rows 1..3 face beds), per vertex
+// s_v = sum over the cells K around v of zs_K / 3 + (zs of K's two faces at v) / 2,
+// in a fixed order, and
+//   uplift-bar_v += s_v R,   onset-bar_v += -s_v uplift_v R',
+//   t-bar_n = sum_v s_v uplift_v R'      (R' = dR/dt = 1 / rise inside the ramp),
 // the last summed per CTA into part (adaptive steps carry it to every earlier dt).
 // ---------------------------------------------------------------------------
-__global__ void adj_bed_vertex_kernel(int nv, const int32_t *vptr, const int32_t *vcell, const double *zs,
+__global__ void adj_bed_vertex_kernel(int nv, int ncs, const int32_t *vptr, const int32_t *vcell, const double *zs,
                                       const double *uplift, const double *onset, double rise, double t, double *gU,
                                       double *gOn, double *part)
 {
@@ -790,7 +831,11 @@ __global__ void adj_bed_vertex_kernel(int nv, const int32_t *vptr, const int32_t
     double tb = 0.0;
     for (int v = blockIdx.x * blockDim.x + tid; v < nv; v += gridDim.x * blockDim.x) {
         double sv = 0.0;
-        for (int k = vptr[v]; k < vptr[v + 1]; k++) sv += zs[vcell[k]];
+        for (int k = vptr[v]; k < vptr[v + 1]; k++) {
+            const int K = vcell[k] >> 2, j = vcell[k] & 3;
+            // faces j (vertices j, j+1) and j+2 (vertices j+2, j) of K touch vertex j
+            sv += zs[K] / 3.0 + (zs[(size_t)(1 + j) * ncs + K] + zs[(size_t)(1 + (j + 2) % 3) * ncs + K]) / 2.0;
+        }
         double R, Rp = 0.0;
         if (rise > 0.0) {
             const double x = __dsub_rn(t, onset[v]) / rise;
@@ -799,8 +844,8 @@ __global__ void adj_bed_vertex_kernel(int nv, const int32_t *vptr, const int32_t
         } else {
             R = t >= onset[v] ? 1.0 : 0.0;
         }
-        gU[v] += sv * R / 3.0;
-        const double q = sv * uplift[v] * Rp / 3.0;
+        gU[v] += sv * R;
+        const double q = sv * uplift[v] * Rp;
         gOn[v] -= q;
         tb += q;
     }
@@ -838,6 +883,8 @@ AdjMesh adj_mesh(const DevPtrs &d, const StepParams &p)
     m.order = p.order;
     m.geo = static_cast<const double *>(d.geo);
     m.z = static_cast<const double *>(d.z);
+    m.zf = static_cast<const double *>(d.zf);
+    m.rec = nullptr;
     m.nbr = d.nbr;
     m.nbrl = d.nbrl;
     m.faces = d.adj_faces;
@@ -850,14 +897,17 @@ AdjMesh adj_mesh(const DevPtrs &d, const StepParams &p)
 
 }  // namespace
 
-// Adds the VJP of the residual at w: (wb, zb) += (dR/dw, dR/dz)^T Rb.
-// Scratch: FV, FVb [9][nc], zfb [3][nc], own [4][nc], send [12][nc].
-int adjoint_residual_vjp(const DevPtrs &d, const StepParams &p, const double *w, const double *Rb, double *wb,
-                         double *zb, double *FV, bool fv_given, double *FVb, double *zfb, double *own, double *send,
-                         void *stream, const AdjCfl *cfl)
+// Adds the VJP of the residual at w: (wb, zb) += (dR/dw, dR/dz)^T Rb, zb [4][nc]
+// = (cell beds, face beds of faces 0..2).  rec: the stage's reconstruction flags.
+// Scratch: FV, FVb [9][nc], zfb [3][nc], own [7][nc], send [12][nc].
+int adjoint_residual_vjp(const DevPtrs &d, const StepParams &p, const double *w, const uint8_t *rec, const double *Rb,
+                         double *wb, double *zb, double *FV, bool fv_given, double *FVb, double *zfb, double *own,
+                         double *send, void *stream, const AdjCfl *cfl)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     AdjMesh m = adj_mesh(d, p);
+    m.rec = rec;
+    if (!rec) return (int)cudaErrorInvalidValue;
     int grid = grid_of(m.nc);
     if (!fv_given) adj_face_values_kernel<<<grid, 256, 0, s>>>(m, w, Rb, FV);
     if (!m.faces) return (int)cudaErrorInvalidValue;     // the face list is built by vg_adj_backward
@@ -867,7 +917,7 @@ int adjoint_residual_vjp(const DevPtrs &d, const StepParams &p, const double *w,
         adj_cfl_face_kernel<<<1, 32, 0, s>>>(m, FV, kAdjCflParts, cfl->part_b, cfl->part_o, cfl->part_k, cfl->dtbar,
                                              cfl->cfl, cfl->dt_max, FVb, zfb);
     }
-    adj_recon_vjp_kernel<<<grid_vjp(m.nc), kVjpThreads, 0, s>>>(m, w, FVb, zfb, own, send);
+    adj_recon_vjp_kernel<<<grid_vjp(m.nc), kVjpThreads, 0, s>>>(m, w, Rb, FVb, zfb, own, send);
     adj_gather_kernel<<<grid, 256, 0, s>>>(m, own, send, wb, zb);
     return (int)cudaGetLastError();
 }
@@ -909,9 +959,9 @@ int adjoint_bed_flush(int nc, int nv, const int32_t *vptr, const int32_t *vcell,
                       double *tsum, double *part, void *stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    adj_bed_vertex_kernel<<<kAdjCflParts, 256, 0, s>>>(nv, vptr, vcell, zs, uplift, onset, rise, t, gU, gOn, part);
+    adj_bed_vertex_kernel<<<kAdjCflParts, 256, 0, s>>>(nv, nc, vptr, vcell, zs, uplift, onset, rise, t, gU, gOn, part);
     adj_dot_final_kernel<<<1, 32, 0, s>>>(kAdjCflParts, part, 1.0, tsum, 0);
-    adj_axpy_kernel<<<grid_of(nc), 256, 0, s>>>(nc, zs, zb_total);
+    adj_axpy_kernel<<<grid_of(4 * nc), 256, 0, s>>>(4 * (int64_t)nc, zs, zb_total);
     return (int)cudaGetLastError();
 }
 

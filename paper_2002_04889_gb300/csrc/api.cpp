@@ -39,6 +39,7 @@ struct vg_ctx {
 
     // device memory
     void *geo = nullptr, *z = nullptr, *w[2] = {nullptr, nullptr}, *R0 = nullptr;
+    void *zf = nullptr;               // face beds (layout: DevPtrs::zf)
     double *z64 = nullptr;
     float *z_orig = nullptr;          // FP32: the bed in the original cell order (state import/export)
     double *z64_orig = nullptr;
@@ -148,7 +149,7 @@ void free_mesh(vg_ctx *c)
     free_adjoint(c);
     if (c->graph2) { cudaGraphExecDestroy(c->graph2); c->graph2 = nullptr; }
     if (c->z64 == c->z) c->z64 = nullptr;
-    dfree(c->geo); dfree(c->z); dfree(c->z64); dfree(c->w[0]); dfree(c->w[1]); dfree(c->R0);
+    dfree(c->geo); dfree(c->z); dfree(c->zf); dfree(c->z64); dfree(c->w[0]); dfree(c->w[1]); dfree(c->R0);
     dfree(c->z_orig); dfree(c->z64_orig); c->zorig_ok = false;
     dfree(c->nbr); dfree(c->halo_ptr); dfree(c->halo_n1); dfree(c->halo_ids); dfree(c->ring1_nbr);
     dfree(c->old_of_new); dfree(c->new_of_old); dfree(c->nbrl); dfree(c->fq_ptr); dfree(c->fq);
@@ -188,6 +189,7 @@ DevPtrs dev_ptrs(const vg_ctx *c)
     d.ring_cap = kRingCap;
     d.geo = c->geo;
     d.z = c->z;
+    d.zf = c->zf;
     d.z64 = c->z64;
     const bool zo = c->zorig_ok && !c->bed_on;
     d.z_orig = zo ? c->z_orig : nullptr;
@@ -265,6 +267,25 @@ int upload_bed_orig(vg_ctx *c)
     return VG_OK;
 }
 
+// Face beds of the host mesh in the device layout: FP64 [3][nc] as they are;
+// FP32 [nc][2] the differences z_f - z_K of faces 0 and 1, formed in FP64.
+int upload_face_beds(vg_ctx *c)
+{
+    const HostMesh &m = c->hm;
+    const int64_t n = m.nc;
+    int rc;
+    if (!c->zf && (rc = dmalloc(c, &c->zf, c->precision == 64 ? 8 * 3 * n : 8 * n))) return rc;
+    if (c->precision == 64) {
+        VG_CUDA(c, cudaMemcpy(c->zf, m.zf.data(), 8 * 3 * n, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> d(2 * (size_t)n);
+        for (int64_t k = 0; k < n; k++)
+            for (int f = 0; f < 2; f++) d[2 * k + f] = (float)(m.zf[f * (size_t)n + k] - m.z[k]);
+        VG_CUDA(c, cudaMemcpy(c->zf, d.data(), 4 * d.size(), cudaMemcpyHostToDevice));
+    }
+    return VG_OK;
+}
+
 // Block partition arrays (re-uploaded when block_cells changes).
 int upload_partition(vg_ctx *c)
 {
@@ -330,6 +351,7 @@ int upload_mesh_arrays(vg_ctx *c)
         VG_CUDA(c, cudaMemcpy(c->geo, r.data(), 4 * r.size(), cudaMemcpyHostToDevice));
     }
     if ((rc = upload_real(c, c->z, m.z.data(), m.z.size()))) return rc;
+    if ((rc = upload_face_beds(c))) return rc;
     if (c->precision == 64) {
         c->z64 = static_cast<double *>(c->z);
     } else {
@@ -668,6 +690,13 @@ int vg_mesh_upload(vg_ctx *c, int64_t nv, const double *xy, int64_t nc, const in
     if ((rc = fit_blocks(c))) return rc;
     if ((rc = upload_mesh_arrays(c))) { free_mesh(c); return rc; }
     if ((rc = configure_launch(c))) { free_mesh(c); return rc; }
+    {
+        // the no-allocation step's scratch and kernels are resolved here, so that
+        // vg_step_noalloc itself loads and allocates nothing
+        int e = noalloc_prepare(c->device);
+        if (!e) e = util_preload();
+        if (e) { free_mesh(c); return cuda_fail(c, (cudaError_t)e, "no-allocation step set-up"); }
+    }
     c->depth_v.assign(depth_v, depth_v + nv);
     c->has_mesh = true;
     c->has_state = false;
@@ -1066,16 +1095,14 @@ int vg_set_depth(vg_ctx *c, const double *depth_v)
         return fail(c, VG_ESTATE, "a moving bed is set; remove it (vg_set_bed_motion with uplift NULL) first");
     DeviceGuard guard(c->device);
     HostMesh &m = c->hm;
-    std::vector<double> zo(m.nc);
-    for (int64_t o = 0; o < m.nc; o++) {
-        const int32_t *v = &m.vtx[3 * o];
-        zo[o] = -((depth_v[v[0]] + depth_v[v[1]]) + depth_v[v[2]]) / 3.0;
-        if (!std::isfinite(zo[o])) return fail(c, VG_EINVAL, "non-finite depth");
-    }
-    for (int64_t k = 0; k < m.nc; k++) m.z[k] = zo[m.old_of_new[k]];
+    for (int64_t v = 0; v < m.nv; v++)
+        if (!std::isfinite(depth_v[v])) return fail(c, VG_EINVAL, "non-finite depth");
+    std::string err;
+    if (bed_arrays(m, depth_v, err)) return fail(c, VG_EINVAL, err);
     cudaStreamSynchronize(c->stream);
     int rc = upload_real(c, c->z, m.z.data(), m.z.size());
     if (rc) return rc;
+    if ((rc = upload_face_beds(c))) return rc;
     if (c->precision != 64) VG_CUDA(c, cudaMemcpy(c->z64, m.z.data(), 8 * m.nc, cudaMemcpyHostToDevice));
     if ((rc = upload_bed_orig(c))) return rc;
     c->depth_v.assign(depth_v, depth_v + m.nv);
@@ -1281,6 +1308,7 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
         if (e) return e;
         cudaError_t ce = cudaMemcpy(dev, fl.data(), 4 * fl.size(), cudaMemcpyHostToDevice);
         if (ce != cudaSuccess) {
+            c->dev_bytes -= (int64_t)(4 * std::max<size_t>(fl.size(), 1));
             dfree(dev);
             return cuda_fail(c, ce, "face list upload");
         }
@@ -1303,17 +1331,19 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
     // seg: the segment's states, R0seg: their stage-1 residuals, m2seg: stage-2
     // dry-fix branches (all recorded by one forward recompute of the segment)
     double *W, *wb, *wbn, *wb1, *zb, *Rb, *w1, *H1pre, *FVb, *zfb, *own, *send, *seg, *R0seg, *wlast, *m2raw;
+    double *recraw;  // reconstruction flags of both stages of every recorded step [RC][2][nc] (bytes)
     double *FVseg;   // face values of both stages of every step of the segment [C][2][9][nc]
     const bool adaptive = !(c->adj_dt > 0.0);
     double *R1seg = nullptr, *cflscr = nullptr;   // adaptive steps: stage-2 residuals; dt-bar and reduction scratch
     int rc = 0;
     if ((rc = alloc((size_t)(N + 1) * G, &W)) || (rc = alloc(w3, &wb)) || (rc = alloc(w3, &wbn)) ||
-        (rc = alloc(w3, &wb1)) || (rc = alloc(nc, &zb)) || (rc = alloc(w3, &Rb)) || (rc = alloc(w3, &wlast)) ||
+        (rc = alloc(w3, &wb1)) || (rc = alloc(4 * (size_t)nc, &zb)) || (rc = alloc(w3, &Rb)) || (rc = alloc(w3, &wlast)) ||
         (rc = alloc(w3, &w1)) || (rc = alloc(nc, &H1pre)) || (rc = alloc(18 * (size_t)nc * RC, &FVseg)) ||
-        (rc = alloc(9 * (size_t)nc, &FVb)) || (rc = alloc(3 * (size_t)nc, &zfb)) || (rc = alloc(4 * (size_t)nc, &own)) ||
+        (rc = alloc(9 * (size_t)nc, &FVb)) || (rc = alloc(3 * (size_t)nc, &zfb)) || (rc = alloc(7 * (size_t)nc, &own)) ||
         (rc = alloc(12 * (size_t)nc, &send)) ||
         (rc = alloc(w3 * (size_t)(binomial ? 2 + c->adj_slots : C), &seg)) ||
         (rc = alloc(w3 * (size_t)RC, &R0seg)) || (rc = alloc(((size_t)nc * RC + 7) / 8, &m2raw)) ||
+        (rc = alloc((2 * (size_t)nc * RC + 7) / 8, &recraw)) ||
         (adaptive && ((rc = alloc(w3 * (size_t)RC, &R1seg)) || (rc = alloc(8 + 3 * (size_t)kAdjCflParts, &cflscr))))) {
         for (void *q : bufs) cudaFree(q);
         return rc;
@@ -1322,11 +1352,15 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
     // adjoint of time, and the cells around each vertex (fixed order)
     const bool bed = c->adj_bed;
     const int nv = (int)c->hm.nv;
+    if (bed && nc >= (1 << 29)) {
+        for (void *q : bufs) cudaFree(q);
+        return fail(c, VG_EINVAL, "moving-bed adjoint: at most 2^29 - 1 cells");
+    }
     double *zstep = nullptr, *gU = nullptr, *gOn = nullptr, *bedscr = nullptr;
     int32_t *vptr = nullptr, *vcell = nullptr;
     std::vector<double> tn;
     if (bed) {
-        if ((rc = alloc(nc, &zstep)) || (rc = alloc(nv, &gU)) || (rc = alloc(nv, &gOn)) ||
+        if ((rc = alloc(4 * (size_t)nc, &zstep)) || (rc = alloc(nv, &gU)) || (rc = alloc(nv, &gOn)) ||
             (rc = alloc(8 + (size_t)kAdjCflParts, &bedscr))) {
             for (void *q : bufs) cudaFree(q);
             return rc;
@@ -1336,8 +1370,9 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
             for (int j = 0; j < 3; j++) hp[c->hm.vtx[3 * (size_t)c->hm.old_of_new[k] + j] + 1]++;
         for (int v = 0; v < nv; v++) hp[v + 1] += hp[v];
         std::vector<int32_t> fill(hp.begin(), hp.end() - 1);
-        for (int k = 0; k < nc; k++)          // internal ids in increasing order per vertex
-            for (int j = 0; j < 3; j++) hc[fill[c->hm.vtx[3 * (size_t)c->hm.old_of_new[k] + j]]++] = k;
+        for (int k = 0; k < nc; k++)          // internal ids in increasing order per vertex, with the
+            for (int j = 0; j < 3; j++)        // vertex's local index: (cell << 2) | j
+                hc[fill[c->hm.vtx[3 * (size_t)c->hm.old_of_new[k] + j]]++] = (k << 2) | j;
         double *vp = nullptr, *vc = nullptr;
         if ((rc = alloc(((size_t)nv + 2) / 2, &vp)) || (rc = alloc((3 * (size_t)nc + 1) / 2, &vc))) {
             for (void *q : bufs) cudaFree(q);
@@ -1370,6 +1405,7 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
         cfl.part_k = cfl.part_o + kAdjCflParts;
     }
     uint8_t *m2seg = reinterpret_cast<uint8_t *>(m2raw);
+    uint8_t *recseg = reinterpret_cast<uint8_t *>(recraw);
     DevScalars *asc = nullptr;
     if ((rc = dmalloc(c, (void **)&asc, sizeof(DevScalars)))) {
         for (void *q : bufs) cudaFree(q);
@@ -1392,9 +1428,9 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
         VG_CUDA(c, cudaMemcpyAsync(asc, &s0, sizeof(s0), cudaMemcpyHostToDevice, c->stream));
         VG_CUDA(c, cudaMemcpyAsync(W, dJ_deta, 8 * (size_t)(N + 1) * G, cudaMemcpyHostToDevice, c->stream));
         VG_CUDA(c, cudaMemsetAsync(wb, 0, 8 * w3, c->stream));
-        VG_CUDA(c, cudaMemsetAsync(zb, 0, 8 * (size_t)nc, c->stream));
+        VG_CUDA(c, cudaMemsetAsync(zb, 0, 8 * 4 * (size_t)nc, c->stream));
         zacc = bed ? zstep : zb;
-        if (bed) VG_CUDA(c, cudaMemsetAsync(zstep, 0, 8 * (size_t)nc, c->stream));
+        if (bed) VG_CUDA(c, cudaMemsetAsync(zstep, 0, 8 * 4 * (size_t)nc, c->stream));
         ADJ_CHECK(adjoint_gauge(G, c->gauge_cells, W + (size_t)N * G, nc, wb, zacc, st));
         if (bed)
             ADJ_CHECK(adjoint_bed_flush(nc, nv, vptr, vcell, zstep, c->bed_uplift, c->bed_onset, c->bed_rise, tn[N],
@@ -1407,12 +1443,14 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
             dd.R0 = R0seg + (size_t)r * w3;
             dd.mask2 = m2seg + (size_t)r * nc;
             dd.fv_out = FVseg + (size_t)r * 18 * nc;
+            dd.rec_out = recseg + (size_t)r * 2 * nc;
             StepParams pn = p;
             pn.dt_fixed = c->adj_dts[n];        // the step the forward run took
             int e;
             if (bed && (e = launch_bed_update(d, p, nullptr, 64, false, tn[n], st))) return e;   // bed of step n
             if ((e = launch_stage1_f64(dd, pn, win, c->cfg1, st))) return e;
             dd.fv_out = FVseg + ((size_t)r * 18 + 9) * nc;
+            dd.rec_out = recseg + ((size_t)r * 2 + 1) * nc;
             if (adaptive) dd.r1_out = R1seg + (size_t)r * w3;
             return launch_stage2_f64(dd, pn, win, wout, c->cfg2, st);
         };
@@ -1435,7 +1473,7 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
             int e;
             if (bed) {
                 if ((e = launch_bed_update(d, p, nullptr, 64, false, tn[n], st))) return e;     // bed of step n
-                if ((e = (int)cudaMemsetAsync(zstep, 0, 8 * (size_t)nc, c->stream))) return e;
+                if ((e = (int)cudaMemsetAsync(zstep, 0, 8 * 4 * (size_t)nc, c->stream))) return e;
             }
             if ((e = adjoint_stage1(nc, dtn, hthr, w, R0, w1, H1pre, st))) return e;
             if ((e = adjoint_stage2_rev(nc, dtn, m2seg + (size_t)r * nc, wb, wbn, wb1, Rb, st))) return e;
@@ -1444,13 +1482,14 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
                                              dotpart, st)))
                 return e;
             double *FV0 = FVseg + (size_t)r * 18 * nc, *FV1 = FV0 + 9 * (size_t)nc;
-            if ((e = adjoint_residual_vjp(d, p, w1, Rb, wb1, zacc, FV1, true, FVb, zfb, own, send, st))) return e;
+            const uint8_t *rec0 = recseg + (size_t)r * 2 * nc, *rec1 = rec0 + nc;
+            if ((e = adjoint_residual_vjp(d, p, w1, rec1, Rb, wb1, zacc, FV1, true, FVb, zfb, own, send, st))) return e;
             if ((e = adjoint_stage1_rev(nc, dtn, hthr, H1pre, wb1, wbn, Rb, st))) return e;
             // dt-bar, stage 1: sum w1-bar_pre . R0 = sum Rb . R0 / dt
             if (adaptive && (e = adjoint_dot((int64_t)w3, Rb, R0, 1.0 / dtn, dtbar, false, dotpart, st))) return e;
             // a moving bed: every later bed depends on this dt through the time
             if (adaptive && bed && (e = adjoint_scalar_add(dtbar, tsum, st))) return e;
-            if ((e = adjoint_residual_vjp(d, p, w, Rb, wbn, zacc, FV0, true, FVb, zfb, own, send, st,
+            if ((e = adjoint_residual_vjp(d, p, w, rec0, Rb, wbn, zacc, FV0, true, FVb, zfb, own, send, st,
                                           adaptive ? &cfl : nullptr)))
                 return e;
             if ((e = adjoint_gauge(G, c->gauge_cells, W + (size_t)n * G, nc, wbn, zacc, st))) return e;
@@ -1544,24 +1583,29 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
             VG_CUDA(c, cudaMemcpyAsync(c->adj_gOn.data(), gOn, 8 * (size_t)nv, cudaMemcpyDeviceToHost, c->stream));
         }
         // internal -> original order on the host
-        std::vector<double> h(4 * (size_t)nc);
+        std::vector<double> h(7 * (size_t)nc);
         VG_CUDA(c, cudaMemcpyAsync(h.data(), wb, 8 * w3, cudaMemcpyDeviceToHost, c->stream));
-        VG_CUDA(c, cudaMemcpyAsync(h.data() + w3, zb, 8 * (size_t)nc, cudaMemcpyDeviceToHost, c->stream));
+        VG_CUDA(c, cudaMemcpyAsync(h.data() + w3, zb, 8 * 4 * (size_t)nc, cudaMemcpyDeviceToHost, c->stream));
         VG_CUDA(c, cudaStreamSynchronize(c->stream));
         const std::vector<int32_t> &oon = c->hm.old_of_new;
-        std::vector<double> zo(nc);
+        std::vector<double> zo(nc), zfo(3 * (size_t)nc);
         for (int k = 0; k < nc; k++) {
             int o = oon[k];
             if (dJ_dH0) dJ_dH0[o] = h[k];
             if (dJ_dHu0) dJ_dHu0[o] = h[nc + k];
             if (dJ_dHv0) dJ_dHv0[o] = h[2 * (size_t)nc + k];
             zo[o] = h[w3 + k];
+            for (int f = 0; f < 3; f++) zfo[3 * (size_t)o + f] = h[w3 + (size_t)(1 + f) * nc + k];
         }
         if (dJ_dz) std::copy(zo.begin(), zo.end(), dJ_dz);
         if (dJ_ddepth) {
+            // z_K = -(1/3) sum of its vertex depths, z_f = -(1/2) the sum over the
+            // face's two vertices (face f joins local vertices f and f + 1)
             std::fill(dJ_ddepth, dJ_ddepth + c->hm.nv, 0.0);
             for (int o = 0; o < nc; o++)
-                for (int k = 0; k < 3; k++) dJ_ddepth[c->hm.vtx[3 * (size_t)o + k]] -= zo[o] / 3.0;
+                for (int k = 0; k < 3; k++)
+                    dJ_ddepth[c->hm.vtx[3 * (size_t)o + k]] -=
+                        zo[o] / 3.0 + (zfo[3 * (size_t)o + k] + zfo[3 * (size_t)o + (k + 2) % 3]) / 2.0;
         }
     }
 done:
@@ -1595,6 +1639,8 @@ int vg_step_noalloc(vg_ctx *c, const void *w_in, void *w_out, double t, double *
     if (!w_in || !w_out || w_in == w_out) return fail(c, VG_EINVAL, "w_in and w_out must be distinct device arrays");
     if (!std::isfinite(t)) return fail(c, VG_EINVAL, "t must be finite");
     if (!c->has_mesh) return fail(c, VG_ESTATE, "no mesh");
+    if (c->bed_on)
+        return fail(c, VG_ESTATE, "a moving bed is set: vg_step_noalloc steps a static bed (remove the motion first)");
     if (c->hm.nc > VG_NOALLOC_MAX_CELLS)
         return fail(c, VG_EINVAL, "vg_step_noalloc handles at most " + std::to_string(VG_NOALLOC_MAX_CELLS) +
                                       " cells; this mesh has " + std::to_string(c->hm.nc));

@@ -180,6 +180,27 @@ void rcm_order(const std::vector<int32_t> &nbr3, int64_t nc, std::vector<int32_t
 
 }  // namespace
 
+int bed_arrays(HostMesh &m, const double *depth_v, std::string &err)
+{
+    const int64_t nc = m.nc;
+    std::vector<double> z(nc), zf(3 * (size_t)nc);
+    int64_t bad = -1;
+    for (int64_t k = 0; k < nc; k++) {
+        const int32_t *v = &m.vtx[3 * (size_t)m.old_of_new[k]];
+        z[k] = -((depth_v[v[0]] + depth_v[v[1]]) + depth_v[v[2]]) / 3.0;
+        bool ok = std::isfinite(z[k]);
+        for (int f = 0; f < 3; f++) {
+            zf[f * (size_t)nc + k] = -(depth_v[v[f]] + depth_v[v[(f + 1) % 3]]) / 2.0;
+            ok = ok && std::isfinite(zf[f * (size_t)nc + k]);
+        }
+        if (!ok && bad < 0) bad = m.old_of_new[k];
+    }
+    if (bad >= 0) { err = "triangle " + std::to_string(bad) + " has a non-finite depth"; return VG_EINVAL; }
+    m.z.swap(z);
+    m.zf.swap(zf);
+    return VG_OK;
+}
+
 int prepare_mesh(int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
                  const double *depth_v, int renumber, int block, HostMesh &m, std::string &err)
 {
@@ -333,7 +354,6 @@ int prepare_mesh(int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
 
     // 5. internal-order arrays
     m.geo.resize((size_t)GEO_ROWS * nc);
-    m.z.resize(nc);
     m.nbr.resize(3 * nc);
     std::vector<int32_t> nface(3 * nc);
 #pragma omp parallel for schedule(static)
@@ -352,7 +372,10 @@ int prepare_mesh(int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
             nface[f * nc + k] = nface_o[i];
         }
         m.geo[GEO_AREA * nc + k] = area[o];
-        m.z[k] = zc[o];
+    }
+    {
+        int rc = bed_arrays(m, depth_v, err);
+        if (rc) return rc;
     }
     // keep the neighbour faces for partition_blocks
     m.nbrl.assign(3 * nc, NBR_WALL);

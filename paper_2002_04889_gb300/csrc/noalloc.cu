@@ -12,14 +12,15 @@
 //
 // Limits and caveats (also in include/volna_gb.h):
 //  * at most VG_NOALLOC_MAX_CELLS cells (larger meshes: VG_EINVAL);
-//  * every GPU that loads the library holds the array (about 6 MiB) until the
-//    process exits;
+//  * the array (about 6 MiB) is committed on a device when a context first
+//    uploads a mesh there (vg_mesh_upload calls noalloc_prepare: it looks up the
+//    array's address and loads this file's kernels, without launching one), and
+//    is held until the process exits;
 //  * all calls share the array, which keeps the last call's contents; each call
 //    clears what must start fresh (the step scalars) before its kernels run, and
 //    calls that overlap on the GPU (other streams, other threads) race on it;
-//  * the first call on a device looks up the array's device address (with that
-//    device current) and caches it; make that first call before any stream
-//    capture.
+//  * the device address of the array is looked up once per device (with that
+//    device current) at that set-up and cached, so a step loads nothing.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -85,6 +86,18 @@ int noalloc_scratch(int device, void **addr, size_t *bytes)
     *addr = g_addr[device];
     *bytes = kScratchBytes;
     return 0;
+}
+
+// Set-up at mesh upload: the array's address on `device` (committing the array
+// under lazy module loading) and this file's kernel, loaded without a launch.
+int noalloc_prepare(int device)
+{
+    void *addr = nullptr;
+    size_t bytes = 0;
+    int e = noalloc_scratch(device, &addr, &bytes);
+    if (e) return e;
+    cudaFuncAttributes fa;
+    return (int)cudaFuncGetAttributes(&fa, (const void *)noalloc_init_kernel);
 }
 
 int noalloc_launch_init(void *scalars, double t, int precision, void *stream)

@@ -33,9 +33,11 @@
 //  * FP64 ("literal"): the state is (H, Hu, Hv) and every formula is evaluated
 //    as written, in the same order as any plain implementation of the scheme.
 //  * FP32 ("deviation"): the state is (eta, Hu, Hv) with eta = H + z, and the
-//    momentum flux through each face is carried relative to each cell's own
-//    hydrostatic pressure g H_K^2 / 2.  Because sum_f l_f n_f = 0 on a closed
-//    triangle this reference drops out of the residual exactly, so the scheme is
+//    momentum flux through each face is carried relative to the hydrostatic
+//    pressure g (eta_K - z_{K,f})^2 / 2 of the cell's own free surface over the
+//    bed z_{K,f} under its face value.  Summed over a closed triangle these
+//    references give exactly the centred bed-slope source of a cell standing on
+//    its face beds (and zero for a cell on its flat cell bed), so the scheme is
 //    unchanged; but the large terms g H^2 / 2 (1e8 in a 4000 m ocean) never
 //    appear, only products of small differences (eta_f - eta_K, z* - z_K), so
 //    still water stays still in FP32 and eta keeps full FP32 resolution.
@@ -54,6 +56,7 @@ struct KArgs {
     int block, nblocks, max_halo, max_ring1, order;
     const real *geo;        // [GEO_ROWS][nc]
     const real *z;          // [nc]
+    const real *zf;         // face beds: FP64 [3][nc]; FP32 [nc][2] z_f - z_K of faces 0, 1
     const int32_t *nbr;     // [3][nc]
     const uint16_t *nbrl;   // [3][nc]
     const int32_t *halo_ptr;  // [nblocks + 1]
@@ -68,6 +71,7 @@ struct KArgs {
     uint8_t *mask2;         // optional: stage-2 dry-fix branch (0 none, 1 momentum cut, 2 emptied)
     real *fv_out;           // optional [3 vars][3 faces][nc]: face values of the block cells
     real *r1_out;           // optional [3][nc]: the stage-2 residual L(w1) (stage 2)
+    uint8_t *rec_out;       // optional [nc]: 1 where the block cell reconstructed (FP64)
     DevScalars *sc;
     real g, half_g, hthr;
     double cfl, dt_fixed, dt_max, t_end;
@@ -158,7 +162,8 @@ __device__ __forceinline__ void hll_normal(real g, real half_g, real HL, real un
 }
 
 // Flux through a face seen from its left cell: face velocities, hydrostatic
-// interface depths z* = max(z_L, z_R), H*_s = max(0, H_{s,f} + z_s - z*), HLL,
+// interface depths z* = max(z_L, z_R), H*_s = max(0, H_{s,f} + z_s - z*) with z_s
+// the bed under side s's face value (its face bed if it reconstructed), HLL,
 // rotation back to (x, y), pressure corrections g (H_{s,f}^2 - H*_s^2) / 2.
 // bnd: 0 interior; 1 wall, the ghost of Sec. 2.5 (u_n reversed, u_t kept, same
 // depth); 2 open, the transmissive ghost (the face state itself).
@@ -261,8 +266,9 @@ __device__ __forceinline__ bool stage_state(const KArgs<real> &a, int gid, real 
     return false;
 }
 
-// Deviation-form flux (FP32).  Inputs per side: face eta_f and momenta, bed z
-// and the cell's own eta.  Same interface depths and HLL as face_flux, with
+// Deviation-form flux (FP32).  Inputs per side: face eta_f and momenta, the bed
+// z under the face value (face bed or cell bed) and the cell's own eta; H below
+// is eta - z of that side.  Same interface depths and HLL as face_flux, with
 //   d* = H*_L - H*_R          (eta_fL - eta_fR when both sides are wet)
 //   F1 - C_e for C_e = g H*_L H*_R / 2:  L: q_L u_nL + g H*_L d* / 2,
 //                                        R: q_R u_nR - g H*_R d* / 2
@@ -427,7 +433,8 @@ __device__ __forceinline__ void finish_cell(const KArgs<real> &a, int gid, const
 
 // Shared memory of one CTA: cell states [L] x 4, face slots [3][L1] x 4 (L1 =
 // block + ring 1), with gids the global ids of block and ring-1 cells [L1],
-// face codes and owned-face queue [3B] each.  Without gids phase B reads a
+// face codes and owned-face queue [3B] each, and for FP64 one byte per block and
+// ring-1 cell: whether it reconstructed (phase D adds its bed-slope source).  Without gids phase B reads a
 // ring-1 cell's global id again from the halo list: at 6 CTAs per SM every
 // kilobyte of shared memory is a kilobyte less of L1.  The batched kernels keep
 // the ids (their extra scenario state leaves no register for the reload).
@@ -436,7 +443,7 @@ __host__ __device__ inline size_t stage_smem_bytes(int block, int max_halo, int 
 {
     size_t L = (size_t)block + max_halo, L1 = (size_t)block + max_ring1;
     return sizeof(real) * 4 * (L + 3 * L1) + (gids ? sizeof(int32_t) * L1 : 0) + sizeof(uint16_t) * 6 * (size_t)block +
-           16;
+           (sizeof(real) == 8 ? L1 : 0) + 16;
 }
 
 // One block of cells for one scenario: phases A-D (see the top of this file).
@@ -460,10 +467,10 @@ __host__ __device__ inline size_t stage_smem_bytes(int block, int max_halo, int 
 // the next block).
 //
 // Shared layout: sW[l] = (W, Hu, Hv, z) of local cell l (W = eta for FP32, H
-// for FP64); sF[f][l] = face values (W_f, Hu_f, Hv_f, x) of face f of cell l
-// after phase B, and after phase C the cell's own term
-// (l_f Phi_0, l_f (Phi_1 + P n_x), l_f (Phi_2 + P n_y), x); x is l_f a_f in
-// stage 1 and, for block cells in stage 2, component f of w^n.
+// for FP64); sF[f][l] = face values (W_f, Hu_f, Hv_f, z_f) of face f of cell l
+// after phase B, z_f the bed the face value stands on, and after phase C the
+// cell's own term (l_f Phi_0, l_f (Phi_1 + P n_x), l_f (Phi_2 + P n_y), l_f a_f).
+// Stage 2's phase D reads w^n of its cell from global memory.
 template <typename real, int STAGE, int DRY, bool LISTED, bool GIDS>
 __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b, const real dt,
                                               unsigned char *smem_raw, int &qcount, real &my_min,
@@ -478,6 +485,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     int32_t *sGid = reinterpret_cast<int32_t *>(sF + 12 * L1);   // [L1] (GIDS)
     uint16_t *sCode = reinterpret_cast<uint16_t *>(GIDS ? sGid + L1 : sGid);   // [3][B]
     uint16_t *queue = sCode + 3 * B;                              // [3B]
+    uint8_t *sRec = reinterpret_cast<uint8_t *>(queue + 3 * B);   // [L1]
 
     constexpr bool ETA = EtaForm<real>::value;
     const int tid = threadIdx.x;
@@ -568,11 +576,13 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
     if constexpr (DRY == 0)
         __syncthreads();
     else
-        skip = __syncthreads_and(dry) && (DRY == 1 || (!a.fv_out && !a.mask2 && !a.r1_out));
+        skip = __syncthreads_and(dry) && (DRY == 1 || (!a.fv_out && !a.mask2 && !a.r1_out && (ETA || !a.rec_out)));
     if (DRY == 1 && skip) {
         if (!LISTED && tid == 0) qcount = 0;
         if (tid < ncell) {
             const int gid = c0 + tid;
+            if constexpr (!ETA)
+                if (a.rec_out) a.rec_out[gid] = 0;
             if (a.fv_out) {
                 real Wc, Huc, Hvc, zc;
                 ld4(sW + 4 * tid, Wc, Huc, Hvc, zc);
@@ -599,10 +609,9 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         if (l < B && l >= ncell) continue;
         const int gid = GIDS ? sGid[l] : l < B ? c0 + l : a.halo_ids[h0 + (l - B)];
         if (zero_terms) {
-            real wz[3] = {real(0), real(0), real(0)};
-            if (STAGE == 2) { wz[0] = a.w[gid]; wz[1] = a.w[nc + gid]; wz[2] = a.w[2 * nc + gid]; }
 #pragma unroll
-            for (int f = 0; f < 3; f++) st4(sF + 4 * (f * L1 + l), real(0), real(0), real(0), wz[f]);
+            for (int f = 0; f < 3; f++) st4(sF + 4 * (f * L1 + l), real(0), real(0), real(0), real(0));
+            if constexpr (!ETA) sRec[l] = 0;
             continue;
         }
         real WK, HuK, HvK, zK;
@@ -650,6 +659,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             }
         }
         real Hf[3], Huf[3], Hvf[3];
+        real zfK[3] = {zK, zK, zK};       // the bed under each face value
         if (recon) {
             real face[3][3];
             real Mf[2][3];          // FP32: rows 0 and 1 of M
@@ -708,9 +718,20 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
 #pragma unroll
                 for (int f = 0; f < 3; f++) face[f][v] = qK[v] + alpha * D[f];
             }
+            // the face values stand on the face beds z_f (the linear bed at the
+            // face midpoints); the face depths must stay above the threshold
+            if constexpr (ETA) {
+                const float2 dz = reinterpret_cast<const float2 *>(a.zf)[gid];
+                zfK[0] = zK + dz.x;
+                zfK[1] = zK + dz.y;
+                zfK[2] = zK - (dz.x + dz.y);
+            } else {
+#pragma unroll
+                for (int f = 0; f < 3; f++) zfK[f] = a.zf[f * nc + gid];
+            }
 #pragma unroll
             for (int f = 0; f < 3; f++) {
-                Hf[f] = face[f][0] - zK;
+                Hf[f] = face[f][0] - zfK[f];
                 if (!(Hf[f] > hthr)) recon = false;
                 if (ETA) Hf[f] = face[f][0];      // FP32 keeps eta_f
                 Huf[f] = face[f][1];
@@ -719,12 +740,13 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         }
         if (!recon) {
 #pragma unroll
-            for (int f = 0; f < 3; f++) { Hf[f] = ETA ? WK : HK; Huf[f] = HuK; Hvf[f] = HvK; }
+            for (int f = 0; f < 3; f++) { Hf[f] = ETA ? WK : HK; Huf[f] = HuK; Hvf[f] = HvK; zfK[f] = zK; }
         }
-        real wn[3] = {real(0), real(0), real(0)};     // stage 2: w^n of a block cell (L1/L2 hit)
-        if (STAGE == 2 && l < B) { wn[0] = a.w[gid]; wn[1] = a.w[nc + gid]; wn[2] = a.w[2 * nc + gid]; }
+        if constexpr (!ETA) sRec[l] = recon ? 1 : 0;
+        if constexpr (!ETA)              // (the adjoint, which reads it, is FP64 only)
+            if (a.rec_out && l < B) a.rec_out[gid] = recon ? 1 : 0;
 #pragma unroll
-        for (int f = 0; f < 3; f++) st4(sF + 4 * (f * L1 + l), Hf[f], Huf[f], Hvf[f], wn[f]);
+        for (int f = 0; f < 3; f++) st4(sF + 4 * (f * L1 + l), Hf[f], Huf[f], Hvf[f], zfK[f]);
         if (a.fv_out && l < B) {
 #pragma unroll
             for (int f = 0; f < 3; f++) {
@@ -751,14 +773,16 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         const int nl = code >> 2, nf = code & 3;
         real *pL = sF + 4 * (f * L1 + l);
         real *pR = sF + 4 * (nf * L1 + nl);
-        real WfL, HufL, HvfL, xL, WL, HuK, HvK, zL;
-        ld4(pL, WfL, HufL, HvfL, xL);
-        ld4(sW + 4 * l, WL, HuK, HvK, zL);
-        real WfR = real(0), HufR = real(0), HvfR = real(0), xR = real(0), WR = real(0), zR = real(0);
+        // zL, zR: the bed under each side's face value (its face bed where that
+        // cell reconstructed, its cell bed otherwise), from the slots' 4th word
+        real WfL, HufL, HvfL, zL, WL, HuK, HvK, zKL;
+        ld4(pL, WfL, HufL, HvfL, zL);
+        ld4(sW + 4 * l, WL, HuK, HvK, zKL);
+        real WfR = real(0), HufR = real(0), HvfR = real(0), WR = real(0), zR = real(0);
         if (!wall) {
-            real Huj, Hvj;
-            ld4(pR, WfR, HufR, HvfR, xR);
-            ld4(sW + 4 * nl, WR, Huj, Hvj, zR);
+            real Huj, Hvj, zKR;
+            ld4(pR, WfR, HufR, HvfR, zR);
+            ld4(sW + 4 * nl, WR, Huj, Hvj, zKR);
         }
         real Phi[3], PL, PR, am, nx, ny, len;
         if constexpr (ETA) {
@@ -776,9 +800,8 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         }
         const real t0 = len * Phi[0];
         const real la = len * am;
-        st4(pL, t0, len * (Phi[1] + PL * nx), len * (Phi[2] + PL * ny), STAGE == 1 ? la : xL);
-        if (!wall)
-            st4(pR, -t0, -(len * (Phi[1] + PR * nx)), -(len * (Phi[2] + PR * ny)), STAGE == 1 ? la : xR);
+        st4(pL, t0, len * (Phi[1] + PL * nx), len * (Phi[2] + PL * ny), la);
+        if (!wall) st4(pR, -t0, -(len * (Phi[1] + PR * nx)), -(len * (Phi[2] + PR * ny)), la);
     }
     __syncthreads();
 
@@ -799,6 +822,24 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             aHv = aHv + t2;
             if (STAGE == 1) am = vmax(am, x[f]);
         }
+        if constexpr (!ETA) {
+            // centred bed-slope source of a cell standing on its face beds:
+            // g sum_f l_f z_f (eta_K - z_f / 2) n_f, eta_K = H_K + z_K (the deviation
+            // form carries it in its per-face terms)
+            if (sRec[l]) {
+                real HKs, Hus, Hvs, zKs;
+                ld4(sW + 4 * l, HKs, Hus, Hvs, zKs);
+                const real eK = HKs + zKs;
+#pragma unroll
+                for (int f = 0; f < 3; f++) {
+                    const real zff = a.zf[f * nc + gid];
+                    const real sf = g * (geo[(GEO_LEN + f) * nc + gid] * (zff * (eK - real(0.5) * zff)));
+                    aHu = aHu + sf * geo[(GEO_NX + f) * nc + gid];
+                    aHv = aHv + sf * geo[(GEO_NY + f) * nc + gid];
+                }
+            }
+        }
+        if (STAGE == 2) { x[0] = a.w[gid]; x[1] = a.w[nc + gid]; x[2] = a.w[2 * nc + gid]; }
         finish_cell<real, STAGE>(a, gid, sW + 4 * l, aH, aHu, aHv, am, x, area, dt, my_min, my_neg, bad);
     }
 }
@@ -1016,6 +1057,7 @@ KArgs<real> make_args(const DevPtrs &d, const StepParams &p, const void *w_in, v
     a.order = p.order;
     a.geo = static_cast<const real *>(d.geo);
     a.z = static_cast<const real *>(d.z);
+    a.zf = static_cast<const real *>(d.zf);
     a.nbr = d.nbr;
     a.nbrl = d.nbrl;
     a.halo_ptr = d.halo_ptr;
@@ -1030,6 +1072,7 @@ KArgs<real> make_args(const DevPtrs &d, const StepParams &p, const void *w_in, v
     a.mask2 = d.mask2;
     a.fv_out = static_cast<real *>(d.fv_out);
     a.r1_out = static_cast<real *>(d.r1_out);
+    a.rec_out = d.rec_out;
     a.sc = d.sc;
     a.g = (real)p.g;
     a.half_g = (real)(0.5 * p.g);

@@ -72,7 +72,8 @@ __global__ void record_gauges_kernel(DevPtrs d, const real *w)
 
 // Moving bed (time-dependent depth of Sec. 2.1, read as a kinematic rupture):
 // depth_v(t) = depth0_v - uplift_v R((t - onset_v) / rise), R(s) = min(1, max(0, s))
-// (rise = 0: a step at onset), cell bed z_K = -(mean of its vertices' depths),
+// (rise = 0: a step at onset), cell bed z_K = -(mean of its vertices' depths) and face
+// beds z_f = -(mean of the face's two vertex depths),
 // applied with H unchanged.  The products and sums are rounded one by one
 // (__dmul_rn / __dadd_rn are never contracted), as written.
 __device__ __forceinline__ double bed_ramp(double t, double onset, double rise)
@@ -86,6 +87,7 @@ __global__ void bed_update_kernel(DevPtrs d, StepParams p, real *w, int at_step_
 {
     const double t = at_step_end ? d.sc->t + step_dt<real>(d.sc, p.cfl, p.dt_fixed, p.dt_max, p.t_end) : t_set;
     real *z = static_cast<real *>(const_cast<void *>(d.z));
+    void *zf = const_cast<void *>(d.zf);
     double *z64 = const_cast<double *>(d.z64);
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.nc; k += (int64_t)gridDim.x * blockDim.x) {
         double dv[3];
@@ -95,6 +97,15 @@ __global__ void bed_update_kernel(DevPtrs d, StepParams p, real *w, int at_step_
             dv[j] = __dsub_rn(d.bed_depth0[v], __dmul_rn(d.bed_uplift[v], bed_ramp(t, d.bed_onset[v], d.bed_rise)));
         }
         const double zn = -(__dadd_rn(__dadd_rn(dv[0], dv[1]), dv[2]) / 3.0);
+        // face beds: -(mean of the face's two vertex depths); FP32 keeps z_f - z_K
+        // of faces 0 and 1
+        double zfn[3];
+#pragma unroll
+        for (int f = 0; f < 3; f++) zfn[f] = -(__dadd_rn(dv[f], dv[(f + 1) % 3]) / 2.0);
+        if (EtaForm<real>::value)
+            reinterpret_cast<float2 *>(zf)[k] = make_float2((float)(zfn[0] - zn), (float)(zfn[1] - zn));
+        else
+            for (int f = 0; f < 3; f++) reinterpret_cast<double *>(zf)[f * d.nc + k] = zfn[f];
         if (EtaForm<real>::value) {
             // eta form: keep H = eta - z; a dry cell (eta == z) stays exactly dry
             const real zo = z[k], zr = (real)zn;
@@ -313,6 +324,14 @@ int launch_bed_update(const DevPtrs &d, const StepParams &p, void *w, int precis
     else
         bed_update_kernel<float><<<blocks, 256, 0, s>>>(d, p, static_cast<float *>(w), at_step_end, t_set);
     return (int)cudaGetLastError();
+}
+
+int util_preload()
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, (const void *)post_step_kernel<double>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void *)post_step_kernel<float>);
+    return (int)e;
 }
 
 int launch_record_gauges(const DevPtrs &d, const void *w, int precision, void *stream)

@@ -40,6 +40,8 @@ struct HostMesh {
     std::vector<int32_t> vtx;            // [nc][3] local-order vertices (original cell order)
     std::vector<double> geo;             // [GEO_ROWS][nc]  (internal order)
     std::vector<double> z;               // [nc]            (internal order)
+    std::vector<double> zf;              // [3][nc] bed at the face midpoints (internal order):
+                                         // -(mean of the face's two vertex depths)
     std::vector<int32_t> nbr;            // [3][nc] internal neighbour ids, -1 wall, -2 open
     std::vector<uint16_t> nbrl;          // [3][nc] (local << 2 | face), NBR_WALL or NBR_OPEN
     std::vector<int32_t> halo_ptr;       // [nblocks + 1] into halo_ids / ring1_nbr
@@ -55,6 +57,12 @@ struct HostMesh {
 // Builds everything in HostMesh.  Returns 0 or a VG_E* code with a message.
 int prepare_mesh(int64_t nv, const double *xy, int64_t nc, const int32_t *tri,
                  const double *depth_v, int renumber, int block, HostMesh &m, std::string &err);
+
+// Cell beds z [nc] and face beds zf [3][nc] (internal order) of the per-vertex
+// depths: z_K = -(mean of the three vertex depths), z_f = -(mean of the face's two
+// vertex depths), the piecewise linear bed (Sec. 2.1).  Returns 0, or VG_EINVAL
+// for a non-finite bed.
+int bed_arrays(HostMesh &m, const double *depth_v, std::string &err);
 
 // Re-partitions an already prepared mesh into blocks of `block` cells.
 int partition_blocks(HostMesh &m, int block, std::string &err);
@@ -94,6 +102,9 @@ struct DevPtrs {
     int32_t threads;        // threads per CTA of the stage kernels (>= block)
     const void *geo;        // FP64: [GEO_ROWS][nc]; FP32: [nc][16] record
     const void *z;          // [nc]
+    const void *zf;         // face beds: FP64 [3][nc]; FP32 [nc][2] = (z_f - z_K) of faces 0
+                            // and 1 (face 2: minus their sum, the face midpoints average
+                            // to the centroid)
     const double *z64;      // [nc] FP64 bed (state import/export and diagnostics)
     const void *z_orig;     // FP32: [nc] the kernels' bed in the original cell order, or null
     const double *z64_orig; // FP32: [nc] the FP64 bed in the original cell order, or null
@@ -112,6 +123,8 @@ struct DevPtrs {
     uint8_t *mask2;         // optional [nc]: stage-2 dry-fix branch per cell (adjoint)
     void *fv_out;           // optional [9][nc]: face values written by the stage kernels (adjoint)
     void *r1_out;           // optional [3][nc]: stage-2 residual written by the stage-2 kernel (adjoint)
+    uint8_t *rec_out;       // optional [nc]: 1 where a cell reconstructed (its face values stand on
+                            // the face beds), written by the stage kernels (adjoint)
     DevScalars *sc;
     const int32_t *gauge_cells;   // internal ids
     double *ring_t;               // [ring_cap]
@@ -171,15 +184,19 @@ struct AdjCfl {
 // or, if fv_given is false, computed here into FV.  cfl (may be NULL): also
 // the adjoint of the stage-1 CFL time step through the wave speed of the face
 // that set it.
-int adjoint_residual_vjp(const DevPtrs &d, const StepParams &p, const double *w, const double *Rb, double *wb,
-                         double *zb, double *FV, bool fv_given, double *FVb, double *zfb, double *own, double *send,
-                         void *stream, const AdjCfl *cfl = nullptr);
+// rec: the reconstruction flags [nc] of the stage (recorded by the forward kernel
+// with rec_out).  zb [4][nc] receives the bed adjoints: row 0 the cell beds z_K,
+// rows 1..3 the face beds z_f of faces 0..2.
+int adjoint_residual_vjp(const DevPtrs &d, const StepParams &p, const double *w, const uint8_t *rec, const double *Rb,
+                         double *wb, double *zb, double *FV, bool fv_given, double *FVb, double *zfb, double *own,
+                         double *send, void *stream, const AdjCfl *cfl = nullptr);
 // *acc (= or +=) scale * sum_i a[i] b[i], deterministic; part: kAdjCflParts doubles.
 int adjoint_dot(int64_t n, const double *a, const double *b, double scale, double *acc, bool reset, double *part,
                 void *stream);
-// Moving bed: one step's bed adjoint zs [nc] at time t -> uplift / onset
-// gradients gU, gOn [nv] (+=), zb_total (+= zs), *tsum (+= the adjoint of t);
-// vptr [nv+1], vcell: the cells around each vertex.
+// Moving bed: one step's bed adjoint zs [4][nc] (cell beds, then the face beds of
+// faces 0..2) at time t -> uplift / onset gradients gU, gOn [nv] (+=), zb_total
+// [4][nc] (+= zs), *tsum (+= the adjoint of t); vptr [nv+1], vcell: the cells
+// around each vertex as (cell << 2) | the vertex's local index in it.
 int adjoint_bed_flush(int nc, int nv, const int32_t *vptr, const int32_t *vcell, double *zs, const double *uplift,
                       const double *onset, double rise, double t, double *gU, double *gOn, double *zb_total,
                       double *tsum, double *part, void *stream);
@@ -217,6 +234,11 @@ int launch_export_state_orig(const DevPtrs &d, const int32_t *new_of_old, const 
 // file-scope scratch array on `device`, and the kernel that clears its scalars.
 int noalloc_scratch(int device, void **addr, size_t *bytes);
 int noalloc_launch_init(void *scalars, double t, int precision, void *stream);
+// Set-up at mesh upload: resolves the scratch address on `device` and loads the
+// no-allocation kernels (no launch), so that a later step loads nothing.
+int noalloc_prepare(int device);
+// Loads the epilogue kernels (util_kernels.cu) without launching them.
+int util_preload();
 
 int launch_diagnostics(const DevPtrs &d, const void *w, int precision, double hthr, double *part,
                        double *out, void *stream);

@@ -257,7 +257,7 @@ def test_advance_to_and_graph_replay_consistency(thacker):
 @pytest.mark.slow
 @pytest.mark.parametrize("precision", [32, 64])
 def test_full_size_40m_sampled(precision):
-    """The 40M-triangle workload in the benchmark's launch configuration (Morton
+    """The 40M-triangle workload in the benchmark's launch configuration (Hilbert
     renumbering, 256-cell blocks): one step on the GPU; 48 sampled cells checked
     against the oracle run on their 4-ring patches with the GPU's time step, the
     time step checked against the sampled CFL bounds, and mass conservation."""
@@ -271,7 +271,7 @@ def test_full_size_40m_sampled(precision):
     samples = np.concatenate([rng.choice(wet_pool, 32, replace=False),
                               rng.choice(shore_pool, 16, replace=False)])
     with volna.Solver(precision) as sv:
-        sv.upload_mesh(m, renumber="morton")
+        sv.upload_mesh(m, renumber="hilbert")
         sv.set_params(h_threshold=1e-5, cfl=0.9)
         sv.set_state(s.H, s.Hu, s.Hv)
         d0 = sv.diagnostics()

@@ -1,0 +1,121 @@
+"""Parity of the CUDA path with the FP64 oracle at the benchmark's launch shape
+and at the stated run lengths of the Thacker and coast-basin workloads.
+
+* Many blocks per persistent CTA: the 1M-triangle Thacker basin in Hilbert
+  order (the benchmark's renumbering) has about 3,900 blocks of 256 cells, so
+  every resident CTA walks several blocks (the alternating queue counters and
+  the barrier-free end of phase D are exercised), full field after 100 CFL steps.
+* Thacker's basin (Sec. 3) for 1000 CFL steps: FP64 and FP32 against the
+  oracle, and both against the closed form.
+* The ocean-to-coast basin (stand-in for the real case of Sec. 5) for 5000
+  CFL steps with its 16 gauges, inundation included.
+
+Tolerances as in the short parity tests: FP64 1e-10 relative L2 per field,
+FP32 1e-4 relative L2 per field against the FP64 oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import analytic as AN
+from paper_2002_04889_gb300 import inputs as I
+from gpu_helpers import FIELDS, gpu_run, oracle_run, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-4
+
+
+def thacker_state_at(mesh, t0):
+    """Thacker's closed form (Sec. 3) at time t0 sampled at the cells' vertex-mean
+    points: depth max(0, eta - z_cell), momentum depth times the closed-form
+    velocity (nonzero for t0 > 0, so the momentum fields carry signal)."""
+    p = mesh.cell_points()
+    kw = dict(h0=mesh.meta["h0"], alpha=mesh.meta["alpha"], r0=mesh.meta["r0"])
+    z = -mesh.vertex_mean(mesh.depth)
+    H = np.maximum(0.0, AN.thacker_eta(p[:, 0], p[:, 1], t0, **kw) - z)
+    u, v = AN.thacker_velocity(p[:, 0], p[:, 1], t0, **kw)
+    return I.State(H, H * u, H * v, t0)
+
+
+@pytest.fixture(scope="module")
+def thacker_1m():
+    m = I.thacker_mesh(n=707)                  # 999,698 triangles, dx = 0.00566 m
+    omega, _ = AN.thacker_constants()
+    s = thacker_state_at(m, 0.25 * 2.0 * math.pi / omega)   # a quarter period: fastest flow
+    return m, s, oracle_run(m, s, 100, h_threshold=1e-5, cfl=0.9)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_many_blocks_per_persistent_cta_1m_hilbert(thacker_1m, precision):
+    m, s, r = thacker_1m
+    assert m.nc // 256 > 4 * 912
+    g = gpu_run(m, s, 100, precision=precision, renumber="hilbert", h_threshold=1e-5, cfl=0.9)
+    tol = TOL64 if precision == 64 else TOL32
+    errs = {f: rel_l2(g[f], r[f]) for f in FIELDS}
+    print(f"1M Thacker, 100 steps, FP{precision} relative L2 vs oracle:", errs)
+    for f in FIELDS:
+        assert errs[f] <= tol, (f, errs[f])
+    assert g["t"] == pytest.approx(r["t"], rel=1e-14 if precision == 64 else 1e-5)
+    assert g["diag"]["neg_count"] == r["neg_count"] == 0
+
+
+@pytest.fixture(scope="module")
+def thacker_1000():
+    m = I.thacker_mesh(n=100)                  # the Sec. 3 basin, 20,000 triangles
+    s = I.thacker_initial_state(m)
+    return m, s, oracle_run(m, s, 1000, gauges=I.THACKER_GAUGES, h_threshold=1e-5, cfl=0.9)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_thacker_1000_steps_oracle_and_closed_form(thacker_1000, precision):
+    """1000 CFL steps (about one period of the basin's oscillation) with a moving
+    shoreline: the field against the oracle, the gauges too, and the solution's
+    own error against Thacker's closed form equal to the oracle's."""
+    m, s, r = thacker_1000
+    g = gpu_run(m, s, 1000, precision=precision, renumber="hilbert", gauges=I.THACKER_GAUGES,
+                h_threshold=1e-5, cfl=0.9)
+    tol = TOL64 if precision == 64 else TOL32
+    errs = {f: rel_l2(g[f], r[f]) for f in FIELDS}
+    print(f"Thacker 1000 steps, FP{precision} relative L2 vs oracle:", errs)
+    for f in FIELDS:
+        assert errs[f] <= tol, (f, errs[f])
+    assert g["t"] == pytest.approx(r["t"], rel=1e-13 if precision == 64 else 1e-4)
+    gauge_tol = 1e-12 if precision == 64 else 1e-5
+    np.testing.assert_allclose(g["gauge_eta"][1:], r["gauges"], rtol=0, atol=gauge_tol)
+    # error against the closed form at the final time, wet interior (r < 0.5)
+    p = m.cell_points()
+    inner = p[:, 0] ** 2 + p[:, 1] ** 2 < 0.25
+    z = -m.vertex_mean(m.depth)
+    ea = AN.thacker_eta(p[:, 0], p[:, 1], r["t"])
+    e_or = np.abs(r["H"] + z - ea)[inner].mean()
+    e_gpu = np.abs(g["H"] + z - ea)[inner].mean()
+    print(f"mean |eta - closed form| (r < 0.5) at t = {r['t']:.4f}: oracle {e_or:.3e}, FP{precision} {e_gpu:.3e}")
+    assert e_or < 5e-4
+    assert abs(e_gpu - e_or) <= (1e-12 if precision == 64 else 1e-6)
+
+
+def test_coast_basin_5000_steps_16_gauges():
+    """The ocean-to-coast basin (N-wave uplift, H_threshold 1e-3 m) on a 50k-triangle
+    mesh for 5000 CFL steps, 16 gauges on the offshore arc: FP64 and FP32 fields
+    and gauges against the oracle."""
+    m = I.coast_mesh_with_cells(50_000, seed=0)
+    s = I.coast_initial_state(m)
+    gauges = I.coast_gauges()
+    r = oracle_run(m, s, 5000, gauges=gauges, h_threshold=1e-3, cfl=0.9)
+    assert r["neg_count"] == 0
+    g64 = gpu_run(m, s, 5000, precision=64, renumber="hilbert", gauges=gauges, h_threshold=1e-3, cfl=0.9)
+    g32 = gpu_run(m, s, 5000, precision=32, renumber="hilbert", gauges=gauges, h_threshold=1e-3, cfl=0.9)
+    e64 = {f: rel_l2(g64[f], r[f]) for f in FIELDS}
+    e32 = {f: rel_l2(g32[f], r[f]) for f in FIELDS}
+    print(f"coast basin {m.nc} triangles, 5000 steps to t = {r['t']:.0f} s: FP64 {e64}, FP32 {e32}")
+    for f in FIELDS:
+        assert e64[f] <= TOL64, (f, e64[f])
+        assert e32[f] <= TOL32, (f, e32[f])
+    scale = float(np.abs(r["gauges"]).max())
+    np.testing.assert_allclose(g64["gauge_eta"][1:], r["gauges"], rtol=0, atol=1e-10 * scale)
+    g32_err = np.abs(g32["gauge_eta"][1:] - r["gauges"]).max() / scale
+    print(f"FP32 gauges: max |error| / max |eta| = {g32_err:.3e}")
+    assert g32_err <= TOL32
