@@ -207,7 +207,7 @@ def code_digest(texts) -> str:
 
 def kernel_source_sha() -> str:
     texts = []
-    for f in ("step_kernels.cuh", "step_f32.cu", "step_f64.cu"):
+    for f in ("step_kernels.cuh", "step_f32.cu", "step_f64.cu", "step_f64_fast.cu"):
         with open(os.path.join(ROOT, "paper_2002_04889_gb300", "csrc", f)) as fh:
             texts.append(fh.read())
     return code_digest(texts)
@@ -231,33 +231,52 @@ def make_workload(name: str):
     return workload_inputs(name, WORKLOADS[name]["n"])
 
 
-def cpu_baseline(budget_s: float = 15.0, n: int = 1414, workload: str = "thacker_paraboloid_40m"):
+def cpu_baseline(budget_s: float = 15.0, n: int = 1414, workload: str = "thacker_paraboloid_40m",
+                 single_budget_s: float = 5.0):
     """The FP64 oracle on a bounded sample of the workload: the same generator at the
-    same dx on an n x n grid (2 n^2 triangles), as many steps as fit in budget_s."""
+    same dx on an n x n grid (2 n^2 triangles), as many steps as fit in budget_s, on
+    all host cores (OpenMP); then the single-threaded oracle on the same sample for
+    single_budget_s (reported beside it)."""
     import oracle as O
     m, s = workload_inputs(workload, n)
     om = O.OracleMesh.from_mesh(m)
     prm = O.params(h_threshold=workload_hthr(workload), cfl=0.9)
-    st = (s.H, s.Hu, s.Hv, 0.0)
-    steps, t0 = 0, time.perf_counter()
-    while True:
-        r = om.run(prm, st, 1)
-        st = (r["H"], r["Hu"], r["Hv"], r["t"])
-        steps += 1
-        el = time.perf_counter() - t0
-        if el >= budget_s or steps >= 200:
-            break
-    return {"value": m.nc * steps / el, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+    cores = O.max_threads()
+
+    def timed(budget):
+        st = (s.H, s.Hu, s.Hv, 0.0)
+        steps, t0 = 0, time.perf_counter()
+        while True:
+            r = om.run(prm, st, 1)
+            st = (r["H"], r["Hu"], r["Hv"], r["t"])
+            steps += 1
+            el = time.perf_counter() - t0
+            if el >= budget or steps >= 200:
+                return steps, el
+
+    steps, el = timed(budget_s)
+    O.set_threads(1)
+    try:
+        steps1, el1 = timed(single_budget_s)
+    finally:
+        O.set_threads(cores)
+    return {"value": m.nc * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle, {steps} steps on a {m.nc}-triangle sample of the same "
-                      f"generator ({_sample_desc(workload, n)}), {el:.1f} s"}
+                      f"generator ({_sample_desc(workload, n)}), {el:.1f} s",
+            "single_thread": {"value": m.nc * steps1 / el1, "unit": UNIT, "cores": 1,
+                              "sample": f"the same sample, {steps1} steps, {el1:.1f} s"}}
 
 
 def batched_leg(torch, stream, steps: int, n_scen: int = 32, renumber: str = "hilbert"):
     """Config 4: 8 coast basins of 50k..2M triangles x n_scen scenarios (uplift
-    amplitude U[1,5] m, orientation U[0,180) deg), FP32, all advanced together
-    (one persistent launch per stage, graph replay, autotuned block size),
-    against a loop of single-scenario solves (one context per mesh, each scenario
-    set and stepped in turn) over the same steps on the same GPU."""
+    amplitude U[1,5] m, orientation U[0,180) deg), FP32, all advanced together to a
+    common end time t_end with per-scenario time steps (one persistent launch per
+    stage, graph replay, autotuned block size and CTAs per SM), against a loop of
+    single-scenario solves (one context per mesh, each scenario set and advanced
+    to t_end in turn) on the same GPU.  t_end is `steps` CFL steps of the fastest
+    scenario.  Throughput counts each scenario's own steps (a scenario that reached
+    t_end stops counting); every scenario's final state is compared with its
+    single-context run, bit for bit."""
     import numpy as np
     from paper_2002_04889_gb300 import inputs as I
     from paper_2002_04889_gb300 import volna
@@ -267,64 +286,70 @@ def batched_leg(torch, stream, steps: int, n_scen: int = 32, renumber: str = "hi
     b = volna.Batch(32, device=torch.cuda.current_device(), stream=stream)
     b.set_params(h_threshold=1e-3, cfl=0.9)
     ids = [b.add_mesh(m, n_scen, renumber=renumber) for m in meshes]
-    states = []
-    for mid, m, src in zip(ids, meshes, srcs):
-        st_m = []
-        for j, (amp, ang) in enumerate(src):
-            s0 = I.coast_initial_state(m, amplitude=amp, angle_deg=ang)
-            b.set_state(mid, j, s0.H, s0.Hu, s0.Hv, 0.0)
-            st_m.append(s0)
-        states.append(st_m)
+    states = [[I.coast_initial_state(m, amplitude=amp, angle_deg=ang) for amp, ang in src]
+              for m, src in zip(meshes, srcs)]
+
+    def reset():
+        for mid in ids:
+            for j in range(n_scen):
+                s0 = states[mid][j]
+                b.set_state(mid, j, s0.H, s0.Hu, s0.Hv, 0.0)
+
+    reset()
     setup = time.perf_counter() - t0
-    block, _ = b.autotune(3)
-    for mid in ids:                       # the tuner restored the state; restart all at t = 0
-        for j in range(n_scen):
-            s0 = states[mid][j]
-            b.set_state(mid, j, s0.H, s0.Hu, s0.Hv, 0.0)
+    tuned = b.autotune(3)
+    reset()                               # the tuner restored the state; restart all at t = 0
     cells = b.info()["cells"]
-    b.step(2)
+    b.step(1)                             # t_end: `steps` steps of the fastest scenario
+    dt1 = max(b.get_state(mid, j)[3] for mid in ids for j in range(n_scen))
+    t_end = steps * dt1
+    reset()
+    b.run(t_end)                          # warm-up over the same run
+    reset()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(stream)
-    b.step(steps)
+    batch_steps = b.run(t_end)
     ev1.record(stream)
     torch.cuda.synchronize()
     ms_batch = ev0.elapsed_time(ev1)
-    batch_states = [b.get_state(mid, 0)[:3] for mid in ids]
-    b.close()
-    # loop of single-scenario solves: same meshes, same scenarios, same steps
-    solvers = []
-    for m in meshes:
-        sv = volna.Solver(32, device=torch.cuda.current_device(), stream=stream)
-        sv.set_params(h_threshold=1e-3, cfl=0.9, block_cells=block)
-        sv.upload_mesh(m, renumber=renumber)
-        solvers.append(sv)
-    torch.cuda.synchronize()
+    # loop of single-scenario solves to the same t_end, each compared with its scenario
     t_loop = 0.0
+    updates = 0
     same = True
-    for mid, sv in enumerate(solvers):
+    n_cmp = 0
+    for mid, m in enumerate(meshes):
+        sv = volna.Solver(32, device=torch.cuda.current_device(), stream=stream)
+        sv.set_params(h_threshold=1e-3, cfl=0.9, block_cells=tuned[0])
+        sv.upload_mesh(m, renumber=renumber)
         for j in range(n_scen):
             s0 = states[mid][j]
             sv.set_state(s0.H, s0.Hu, s0.Hv, 0.0)
-            sv.step(2)
+            sv.step(2)                    # warm-up
             sv.set_state(s0.H, s0.Hu, s0.Hv, 0.0)
+            torch.cuda.synchronize()
             ev0.record(stream)
-            sv.step(steps + 2)
+            sv.advance_to(t_end)
             ev1.record(stream)
             torch.cuda.synchronize()
-            t_loop += ev0.elapsed_time(ev1) * steps / (steps + 2)
-            if j == 0:
-                H, Hu, Hv, _ = sv.get_state()
-                ref = batch_states[mid]
-                same = same and all(np.array_equal(x, y) for x, y in zip((H, Hu, Hv), ref))
-    for sv in solvers:
+            t_loop += ev0.elapsed_time(ev1)
+            H, Hu, Hv, t_s = sv.get_state()
+            steps_s = int(sv.diagnostics()["steps"])
+            bH, bHu, bHv, bt, bsteps = b.get_state(mid, j)
+            updates += m.nc * int(bsteps)
+            same = same and bsteps == steps_s and bt == t_s and all(
+                np.array_equal(x, y) for x, y in zip((H, Hu, Hv), (bH, bHu, bHv)))
+            n_cmp += 1
         sv.close()
-    return {"workload": f"coast basins {I.ensemble_meshes()} triangles x {n_scen} scenarios, FP32",
-            "cells": cells, "steps": steps, "block_cells_autotuned": block,
-            "value": cells * steps / (ms_batch * 1e-3), "unit": UNIT,
-            "loop_of_singles": cells * steps / (t_loop * 1e-3),
-            "speedup_vs_loop": t_loop / ms_batch, "bitwise_equal_to_singles": bool(same),
-            "setup_s": round(setup, 1)}
+    b.close()
+    return {"workload": f"coast basins {I.ensemble_meshes()} triangles x {n_scen} scenarios, FP32, to a common "
+                        f"t_end with per-scenario dt",
+            "cells": cells, "t_end": t_end, "batched_steps": batch_steps,
+            "cell_updates": updates, "autotuned": {"block_cells": tuned[0], "ctas_per_sm": tuned[2]},
+            "value": updates / (ms_batch * 1e-3), "unit": UNIT,
+            "loop_of_singles": updates / (t_loop * 1e-3),
+            "speedup_vs_loop": t_loop / ms_batch, "scenarios_compared": n_cmp,
+            "bitwise_equal_to_singles": bool(same), "setup_s": round(setup, 1)}
 
 
 def adjoint_leg(torch, stream, steps: int, n: int = 707, slots: int = 16):
@@ -347,10 +372,19 @@ def adjoint_leg(torch, stream, steps: int, n: int = 707, slots: int = 16):
     sv.set_state(s.H, s.Hu, s.Hv)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sv.step(steps)
+    sv.step(steps)                        # the literal FP64 build, which the adjoint reverses
     torch.cuda.synchronize()
     t_fwd = time.perf_counter() - t0
-    sv.set_params(h_threshold=1e-5)
+    sv.set_params(fp64_literal=0)         # the contracted build, for context
+    sv.set_state(s.H, s.Hu, s.Hv)
+    sv.step(3)
+    sv.set_state(s.H, s.Hu, s.Hv)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sv.step(steps)
+    torch.cuda.synchronize()
+    t_fwd_fast = time.perf_counter() - t0
+    sv.set_params(h_threshold=1e-5, fp64_literal=1)
     sv.set_state(s.H, s.Hu, s.Hv)
     t0 = time.perf_counter()
     _, eta = sv.adj_forward(steps, dt)
@@ -368,9 +402,11 @@ def adjoint_leg(torch, stream, steps: int, n: int = 707, slots: int = 16):
         t4 = time.perf_counter()
     sv.close()
     C = math.ceil(math.sqrt(steps))
-    rec = 24 + 24 + 144 + 1                     # per step held: state, R0, face values (2 stages), mask
+    rec = 24 + 24 + 144 + 1 + 2                 # per step held: state, R0, face values (2 stages), mask,
+                                                # reconstruction flags (2 stages)
     return {"workload": f"Thacker basin {m.nc} triangles, FP64, {steps} steps, 16 gauges",
-            "forward_s": round(t_fwd, 4), "adj_forward_s": round(t1 - t0, 4),
+            "forward_s": round(t_fwd, 4), "forward_contracted_s": round(t_fwd_fast, 4),
+            "adj_forward_s": round(t1 - t0, 4),
             "adj_backward_s": round(t2 - t1, 4), "cost_vs_forward": round((t2 - t0) / t_fwd, 3),
             "forward_value": m.nc * steps / t_fwd, "unit": UNIT,
             "scratch_bytes_per_cell_sqrtN": math.ceil(steps / C) * 24 + C * rec,
@@ -410,33 +446,50 @@ def roofline_of(prof, nc: int, precision: int, workload: str, step_ms: float):
 
 
 def workload_leg(torch, stream, workload: str, precision: int, steps: int, warmup: int = 3, inputs=None,
-                 renumber: str = "hilbert"):
+                 renumber: str = "hilbert", variants=None):
     """One workload at one precision: device-timed cell-updates/s over `steps` steps
-    (CUDA events on the solver's stream) and the dominant kernel's roofline."""
+    (CUDA events on the solver's stream) and the dominant kernel's roofline.
+    variants: {name: params} timed in turn on the same context from the same
+    initial state (FP64: the literal and the contracted build); the first is the
+    leg's own line, the others go under "variants"."""
     from paper_2002_04889_gb300 import volna
     mesh, st0 = inputs if inputs is not None else make_workload(workload)
+    variants = variants or {"default": {}}
     sv = volna.Solver(precision=precision, device=torch.cuda.current_device(), stream=stream)
+    out = None
     try:
         sv.set_params(h_threshold=workload_hthr(workload), cfl=0.9)
         sv.upload_mesh(mesh, renumber=renumber)
-        sv.set_state(st0.H, st0.Hu, st0.Hv, 0.0)
-        sv.step(warmup)
-        sv.profile(True)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        sv.step(steps)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1)
-        prof = sv.get_profile()
-        d = sv.diagnostics()
+        for name, prm in variants.items():
+            if prm:
+                sv.set_params(**prm)
+            sv.set_state(st0.H, st0.Hu, st0.Hv, 0.0)
+            sv.step(warmup)
+            sv.profile(True)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            sv.step(steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            prof = sv.get_profile()
+            sv.profile(False)
+            d = sv.diagnostics()
+            line = {"workload": workload, "cells": mesh.nc, "dtype": "f32" if precision == 32 else "f64",
+                    "steps": steps, "value": mesh.nc * steps / (ms * 1e-3), "unit": UNIT,
+                    "ms_per_step": ms / steps, "neg_count": d["neg_count"],
+                    "roofline": roofline_of(prof, mesh.nc, precision, workload, ms / steps)}
+            if out is None:
+                out = line
+                if len(variants) > 1:
+                    out["variant"] = name
+                    out["variants"] = {}
+            else:
+                out["variants"][name] = line
     finally:
         sv.close()
-    return {"workload": workload, "cells": mesh.nc, "dtype": "f32" if precision == 32 else "f64",
-            "steps": steps, "value": mesh.nc * steps / (ms * 1e-3), "unit": UNIT,
-            "ms_per_step": ms / steps, "neg_count": d["neg_count"],
-            "roofline": roofline_of(prof, mesh.nc, precision, workload, ms / steps)}
+    return out
 
 
 def run_reference(args):
@@ -480,10 +533,15 @@ def main():
     ap.add_argument("--workload", default="thacker_paraboloid_40m", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--renumber", default="hilbert", choices=["none", "morton", "rcm", "hilbert"])
+    ap.add_argument("--fp64-build", default="literal", choices=["literal", "contracted"],
+                    help="FP64 stage kernels of the main leg: literal (bit for bit the oracle's arithmetic, the "
+                         "library default) or contracted (fused multiply-adds, fewer divisions)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--batched-steps", type=int, default=20, help="0 skips the batched-ensemble leg")
+    ap.add_argument("--batched-scenarios", type=int, default=32,
+                    help="scenarios per mesh of the batched leg (32: the ensemble configuration)")
     ap.add_argument("--adjoint-steps", type=int, default=2000, help="0 skips the adjoint-cost leg")
     ap.add_argument("--adjoint-binomial-slots", type=int, default=16, help="0 skips the binomial run")
     ap.add_argument("--config-legs", type=int, default=1,
@@ -510,7 +568,8 @@ def main():
     mesh, st0 = make_workload(args.workload)
     stream = torch.cuda.Stream()
     sv = volna.Solver(precision=args.precision, device=torch.cuda.current_device(), stream=stream)
-    sv.set_params(h_threshold=workload_hthr(args.workload), cfl=0.9)
+    sv.set_params(h_threshold=workload_hthr(args.workload), cfl=0.9,
+                  fp64_literal=0 if args.fp64_build == "contracted" else 1)
     sv.upload_mesh(mesh, renumber=args.renumber)
     sv.set_state(st0.H, st0.Hu, st0.Hv, 0.0)
     nc = mesh.nc
@@ -608,14 +667,18 @@ def main():
                     coast = coast if coast is not None else make_workload(wl)
                     inp = coast
                 n_steps = min(args.steps, 20) if prec == 64 else args.steps
+                # FP64: the literal build (bit for bit the oracle's arithmetic, the
+                # default) and the contracted build (fp64_literal = 0)
+                var = {"literal": {}, "contracted": {"fp64_literal": 0}} if prec == 64 else None
                 configs[key] = workload_leg(torch, stream, wl, prec, n_steps, inputs=inp,
-                                            renumber=args.renumber)
+                                            renumber=args.renumber, variants=var)
             except Exception as e:         # reported, not fatal: the headline is the forward step
                 configs[key] = {"error": str(e)[:300]}
         del coast
     if rank == 0 and args.batched_steps > 0:
         try:
-            batched = batched_leg(torch, stream, args.batched_steps, renumber=args.renumber)
+            batched = batched_leg(torch, stream, args.batched_steps, n_scen=args.batched_scenarios,
+                                  renumber=args.renumber)
         except Exception as e:             # reported, not fatal: the headline is the forward step
             batched = {"error": str(e)[:300]}
     if rank == 0 and args.adjoint_steps > 0:
@@ -630,6 +693,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "cells": nc, "renumber": args.renumber,
+                           **({"fp64_build": args.fp64_build} if args.precision == 64 else {}),
                            "block_cells": 256, "cfl": 0.9, "h_threshold": workload_hthr(args.workload),
                            "l2": "inputs larger than L2 (%.1f GB resident)" % dev_gb,
                            "parallelism": f"replicas x{ws}"},

@@ -75,6 +75,18 @@ typedef struct vg_params {
                               and at most 512 (the extra threads share the halo
                               and face work); 0 = block_cells for FP32 and
                               min(2 x block_cells, 512) for FP64                  */
+    int32_t fp64_literal;  /* FP64 contexts and batches: 1 evaluates every formula
+                              as written, without multiply-add contraction, so
+                              the result equals a plain FP64 implementation of
+                              the scheme (the oracle's order) bit for bit; 0 lets
+                              the compiler contract multiply-adds and divides
+                              once where the literal form divides several times
+                              by the same value: about 1.7x faster, rounding
+                              differences only, but over long runs with moving
+                              shorelines those decide discontinuous switches
+                              (a thin film's velocity, hence the CFL step)
+                              differently, so trajectories drift apart.  The
+                              adjoint always runs the literal form: 1           */
 } vg_params;
 
 /* Run diagnostics (vg_get_diagnostics). */
@@ -403,10 +415,14 @@ int vg_batch_step(vg_batch *b, int64_t n_steps);
    max_steps; *steps_taken receives the batched steps run. */
 int vg_batch_run(vg_batch *b, double t_end, int64_t max_steps, int64_t *steps_taken);
 
-/* Autotuner: times n_steps batched steps for each candidate block size (64,
-   128, 256 cells per thread block) from the current state, restores the state,
-   and keeps the fastest; *best_block and *best_ms_per_step report it. */
-int vg_batch_autotune(vg_batch *b, int32_t n_steps, int32_t *best_block, double *best_ms_per_step);
+/* Autotuner: times n_steps batched steps from the current state for each
+   candidate launch shape -- block size (64, 128, 256 cells per thread block)
+   times resident CTAs per SM (as many as fit, and one and two fewer: fewer CTAs
+   leave each more L1 for the mesh data its scenarios share) -- restores the
+   state after each, and keeps the fastest; *best_block, *best_ctas_per_sm (0:
+   as many as fit) and *best_ms_per_step report it (any may be NULL). */
+int vg_batch_autotune(vg_batch *b, int32_t n_steps, int32_t *best_block, int32_t *best_ctas_per_sm,
+                      double *best_ms_per_step);
 
 /* Virtual gauges of one mesh, shared by all its scenarios (as vg_set_gauges:
    xy [n][2] in the mesh's coordinates, each located in its containing cell,

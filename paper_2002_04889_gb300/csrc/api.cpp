@@ -182,6 +182,7 @@ DevPtrs dev_ptrs(const vg_ctx *c)
         if (t == 0 && c->precision == 64) t = std::min(2 * c->hm.block, 512);
         d.threads = (t >= c->hm.block && t <= 2 * c->hm.block && t <= 512) ? t : c->hm.block;
     }
+    d.fp64_fast = c->precision == 64 && !c->prm.fp64_literal;
     d.nblocks = c->hm.nblocks;
     d.max_halo = c->hm.max_halo;
     d.max_ring1 = c->hm.max_ring1;
@@ -228,6 +229,7 @@ StepParams step_params(const vg_ctx *c)
     p.t_end = c->prm.t_end;
     p.order = c->prm.order;
     p.gauge_every = c->prm.gauge_every;
+    p.fp64_fast = c->precision == 64 && !c->prm.fp64_literal;
     return p;
 }
 
@@ -557,6 +559,7 @@ int validate_params(const vg_params *p, std::string &why)
         why = "block_threads must be 0 or a multiple of 32 from block_cells to min(2 block_cells, 512)";
         return VG_EINVAL;
     }
+    if (p->fp64_literal != 0 && p->fp64_literal != 1) { why = "fp64_literal must be 0 or 1"; return VG_EINVAL; }
     return VG_OK;
 }
 
@@ -623,6 +626,7 @@ int vg_default_params(vg_params *p)
     p->strict_positivity = 0;
     p->block_cells = 0;
     p->block_threads = 0;
+    p->fp64_literal = 1;
     return VG_OK;
 }
 
@@ -728,7 +732,7 @@ int vg_set_params(vg_ctx *c, const vg_params *p)
     DeviceGuard guard(c->device);
     int old_block = c->prm.block_cells ? c->prm.block_cells : 256;
     int new_block = p->block_cells ? p->block_cells : 256;
-    bool threads_changed = p->block_threads != c->prm.block_threads;
+    bool threads_changed = p->block_threads != c->prm.block_threads || p->fp64_literal != c->prm.fp64_literal;
     c->prm = *p;
     c->graph_dirty = true;
     if (c->has_mesh && threads_changed && new_block == old_block) {
@@ -1222,10 +1226,16 @@ int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_eve
     double *dts_dev = nullptr;
     if (dmalloc(c, (void **)&dts_dev, 8 * (size_t)n_steps)) { free_adjoint(c); return VG_ENOMEM; }
     vg_params saved = c->prm;
+    const LaunchCfg saved_cfg1 = c->cfg1, saved_cfg2 = c->cfg2;
     c->prm.dt_fixed = dt;               // 0: the CFL rule of every step
     c->prm.t_end = 0.0;
     c->prm.gauge_every = 1;
+    c->prm.fp64_literal = 1;            // the adjoint reverses the literal form
     c->graph_dirty = true;
+    {
+        int rc0 = configure_launch(c);
+        if (rc0) { c->prm = saved; c->cfg1 = saved_cfg1; c->cfg2 = saved_cfg2; free_adjoint(c); return rc0; }
+    }
     // restart the gauge record at the current state
     DevScalars s;
     int rc = read_scalars(c, s);
@@ -1261,6 +1271,8 @@ int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_eve
     }
     dfree(dts_dev);
     c->prm = saved;
+    c->cfg1 = saved_cfg1;
+    c->cfg2 = saved_cfg2;
     c->graph_dirty = true;
     if (rc) { free_adjoint(c); return rc; }
     c->adj_n = n_steps;
@@ -1423,6 +1435,17 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
     DevPtrs d = dev_ptrs(c);
     d.sc = asc;
     d.n_gauges = 0;
+    d.fp64_fast = 0;                       // the literal form, as the forward run
+    p.fp64_fast = 0;
+    LaunchCfg lc1{}, lc2{};
+    {
+        int e1 = stage_config_f64(d, 1, lc1);
+        if (!e1) e1 = stage_config_f64(d, 2, lc2);
+        if (e1) {
+            for (void *q : bufs) cudaFree(q);
+            return cuda_fail(c, (cudaError_t)e1, "adjoint launch configuration");
+        }
+    }
 #define ADJ_CHECK(call) do { int e_ = (call); if (e_) { rc = cuda_fail(c, (cudaError_t)e_, #call); goto done; } } while (0)
     {
         VG_CUDA(c, cudaMemcpyAsync(asc, &s0, sizeof(s0), cudaMemcpyHostToDevice, c->stream));
@@ -1448,11 +1471,11 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
             pn.dt_fixed = c->adj_dts[n];        // the step the forward run took
             int e;
             if (bed && (e = launch_bed_update(d, p, nullptr, 64, false, tn[n], st))) return e;   // bed of step n
-            if ((e = launch_stage1_f64(dd, pn, win, c->cfg1, st))) return e;
+            if ((e = launch_stage1_f64(dd, pn, win, lc1, st))) return e;
             dd.fv_out = FVseg + ((size_t)r * 18 + 9) * nc;
             dd.rec_out = recseg + ((size_t)r * 2 + 1) * nc;
             if (adaptive) dd.r1_out = R1seg + (size_t)r * w3;
-            return launch_stage2_f64(dd, pn, win, wout, c->cfg2, st);
+            return launch_stage2_f64(dd, pn, win, wout, lc2, st);
         };
         // one forward step without recordings (binomial schedule)
         auto advance_step = [&](int64_t n, const double *win, double *wout) -> int {
@@ -1462,8 +1485,8 @@ int vg_adj_backward(vg_ctx *c, const double *dJ_deta, double *dJ_dH0, double *dJ
             pn.dt_fixed = c->adj_dts[n];
             int e;
             if (bed && (e = launch_bed_update(d, p, nullptr, 64, false, tn[n], st))) return e;
-            if ((e = launch_stage1_f64(dd, pn, win, c->cfg1, st))) return e;
-            return launch_stage2_f64(dd, pn, win, wout, c->cfg2, st);
+            if ((e = launch_stage1_f64(dd, pn, win, lc1, st))) return e;
+            return launch_stage2_f64(dd, pn, win, wout, lc2, st);
         };
         // the reversal of step n from its state w and its recordings in slot r:
         // wb (adjoint of w^{n+1}) -> wb (adjoint of w^n)

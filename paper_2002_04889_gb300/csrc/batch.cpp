@@ -56,6 +56,8 @@ struct vg_batch {
     void *table[2] = {nullptr, nullptr};   // device BatchMesh arrays for both step parities
     int n_items = 0;
     int grid = 0;
+    int ctas_per_sm = 0;                   // autotuned limit of resident CTAs per SM (0: as many as fit)
+    int fit_per_sm = 0;                    // CTAs per SM that fit the current block size
     size_t smem = 0;
     int cur = 0;
     bool dirty = true;
@@ -153,9 +155,15 @@ int rebuild(vg_batch *b)
         VB_CUDA(b, cudaMalloc(&b->table[parity], eb * nm));
         VB_CUDA(b, cudaMemcpy(b->table[parity], host.data(), eb * nm, cudaMemcpyHostToDevice));
     }
-    int e = b->precision == 64 ? batch_config_f64(block, max_halo, max_ring1, b->grid, b->smem)
+    int e = b->precision == 64 ? batch_config_f64(block, max_halo, max_ring1, b->grid, b->smem, !b->prm.fp64_literal)
                                : batch_config_f32(block, max_halo, max_ring1, b->grid, b->smem);
     if (e) return bcuda(b, (cudaError_t)e, "batched launch configuration");
+    {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+        b->fit_per_sm = sms > 0 ? b->grid / sms : 1;
+        if (b->ctas_per_sm > 0 && b->ctas_per_sm < b->fit_per_sm) b->grid = sms * b->ctas_per_sm;
+    }
     if (b->grid > b->n_items) b->grid = b->n_items;
     b->gauges = false;
     for (auto &M : b->meshes) b->gauges = b->gauges || M.n_gauges > 0;
@@ -174,6 +182,7 @@ StepParams batch_params(const vg_batch *b)
     p.t_end = b->prm.t_end;
     p.order = b->prm.order;
     p.gauge_every = b->prm.gauge_every > 0 ? b->prm.gauge_every : 1;
+    p.fp64_fast = b->precision == 64 && !b->prm.fp64_literal;
     return p;
 }
 
@@ -583,7 +592,7 @@ int vg_batch_run(vg_batch *b, double t_end, int64_t max_steps, int64_t *steps_ta
     return rc;
 }
 
-int vg_batch_autotune(vg_batch *b, int32_t n_steps, int32_t *best_block, double *best_ms)
+int vg_batch_autotune(vg_batch *b, int32_t n_steps, int32_t *best_block, int32_t *best_ctas, double *best_ms)
 {
     if (!b || n_steps < 1) return VG_EINVAL;
     DeviceGuard guard(b->device);
@@ -606,7 +615,7 @@ int vg_batch_autotune(vg_batch *b, int32_t n_steps, int32_t *best_block, double 
     VB_CUDA(b, cudaMalloc(&sc_saved, sc_bytes));
     VB_CUDA(b, cudaMemcpyAsync(sc_saved, b->sc_all, sc_bytes, cudaMemcpyDeviceToDevice, b->stream));
     const int candidates[3] = {64, 128, 256};
-    int best = 0;
+    int best = 0, best_c = 0;
     double best_t = INFINITY;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -616,21 +625,32 @@ int vg_batch_autotune(vg_batch *b, int32_t n_steps, int32_t *best_block, double 
         vg_params p = b->prm;
         p.block_cells = candidates[k];
         if ((rc = vg_batch_set_params(b, &p))) break;
+        b->ctas_per_sm = 0;
+        b->dirty = true;
         if ((rc = ready(b))) break;
-        if ((rc = run_steps(b, 2))) break;      // warm-up
-        cudaEventRecord(e0, b->stream);
-        if ((rc = run_steps(b, n_steps))) break;
-        cudaEventRecord(e1, b->stream);
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_t) { best_t = ms; best = candidates[k]; }
-        for (size_t m = 0; m < b->meshes.size(); m++) {
-            size_t bytes = rsize(b) * 3 * ctx_host_mesh(b->meshes[m].ctx).nc * b->meshes[m].n_scen;
-            cudaMemcpyAsync(b->meshes[m].w[cur0], saved[m], bytes, cudaMemcpyDeviceToDevice, b->stream);
+        const int fit = b->fit_per_sm;
+        // as many CTAs per SM as fit, then one and two fewer
+        for (int drop = 0; drop < 3 && !rc; drop++) {
+            const int c = fit - drop;
+            if (c < 1) break;
+            b->ctas_per_sm = drop == 0 ? 0 : c;
+            b->dirty = true;
+            if ((rc = ready(b))) break;
+            if ((rc = run_steps(b, 2))) break;      // warm-up
+            cudaEventRecord(e0, b->stream);
+            if ((rc = run_steps(b, n_steps))) break;
+            cudaEventRecord(e1, b->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_t) { best_t = ms; best = candidates[k]; best_c = b->ctas_per_sm; }
+            for (size_t m = 0; m < b->meshes.size(); m++) {
+                size_t bytes = rsize(b) * 3 * ctx_host_mesh(b->meshes[m].ctx).nc * b->meshes[m].n_scen;
+                cudaMemcpyAsync(b->meshes[m].w[cur0], saved[m], bytes, cudaMemcpyDeviceToDevice, b->stream);
+            }
+            cudaMemcpyAsync(b->sc_all, sc_saved, sc_bytes, cudaMemcpyDeviceToDevice, b->stream);
+            b->cur = cur0;
         }
-        cudaMemcpyAsync(b->sc_all, sc_saved, sc_bytes, cudaMemcpyDeviceToDevice, b->stream);
-        b->cur = cur0;
     }
     cudaStreamSynchronize(b->stream);
     cudaEventDestroy(e0);
@@ -641,7 +661,10 @@ int vg_batch_autotune(vg_batch *b, int32_t n_steps, int32_t *best_block, double 
     vg_params p = b->prm;
     p.block_cells = best;
     if ((rc = vg_batch_set_params(b, &p))) return rc;
+    b->ctas_per_sm = best_c;
+    b->dirty = true;
     if (best_block) *best_block = best;
+    if (best_ctas) *best_ctas = best_c;
     if (best_ms) *best_ms = best_t / n_steps;
     return VG_OK;
 }

@@ -30,8 +30,13 @@
 // integer atomicMin on the bits of a non-negative value (exact, order-free).
 //
 // Two arithmetic forms of the same scheme:
-//  * FP64 ("literal"): the state is (H, Hu, Hv) and every formula is evaluated
-//    as written, in the same order as any plain implementation of the scheme.
+//  * FP64: the state is (H, Hu, Hv).  Two builds of the same code: the literal
+//    one (FAST = false, step_f64.cu, no multiply-add contraction) evaluates every
+//    formula as written, in the same order as any plain implementation of the
+//    scheme; the fast one (FAST = true, step_f64_fast.cu, contraction allowed)
+//    divides once where the literal form divides several times by the same value
+//    (face velocities, the HLL star flux, the residual's 1/|K|) and finds the
+//    limiter's smallest ratio by cross products with one division.
 //  * FP32 ("deviation"): the state is (eta, Hu, Hv) with eta = H + z, and the
 //    momentum flux through each face is carried relative to the hydrostatic
 //    pressure g (eta_K - z_{K,f})^2 / 2 of the cell's own free surface over the
@@ -120,7 +125,7 @@ __device__ __forceinline__ double step_dt(const DevScalars *sc, double cfl, doub
 
 // HLL flux in the face normal frame (Sec. 2.2) with the dry-bed speeds when one
 // side is dry; each side is (H*, u_n, u_t).
-template <typename real>
+template <typename real, bool FAST = false>
 __device__ __forceinline__ void hll_normal(real g, real half_g, real HL, real unL, real utL,
                                            real HR, real unR, real utR, real F[3], real &amax)
 {
@@ -152,9 +157,16 @@ __device__ __forceinline__ void hll_normal(real g, real half_g, real HL, real un
     } else if (sR >= real(0)) {
         real den = sR - sL;
         real sLR = sL * sR;
-        F[0] = ((sR * FL0 - sL * FR0) + sLR * (HR - HL)) / den;
-        F[1] = ((sR * FL1 - sL * FR1) + sLR * (qR - qL)) / den;
-        F[2] = ((sR * FL2 - sL * FR2) + sLR * (HR * utR - HL * utL)) / den;
+        if constexpr (FAST) {
+            const real rd = real(1) / den;
+            F[0] = ((sR * FL0 - sL * FR0) + sLR * (HR - HL)) * rd;
+            F[1] = ((sR * FL1 - sL * FR1) + sLR * (qR - qL)) * rd;
+            F[2] = ((sR * FL2 - sL * FR2) + sLR * (HR * utR - HL * utL)) * rd;
+        } else {
+            F[0] = ((sR * FL0 - sL * FR0) + sLR * (HR - HL)) / den;
+            F[1] = ((sR * FL1 - sL * FR1) + sLR * (qR - qL)) / den;
+            F[2] = ((sR * FL2 - sL * FR2) + sLR * (HR * utR - HL * utL)) / den;
+        }
     } else {
         F[0] = FR0; F[1] = FR1; F[2] = FR2;
     }
@@ -167,7 +179,7 @@ __device__ __forceinline__ void hll_normal(real g, real half_g, real HL, real un
 // rotation back to (x, y), pressure corrections g (H_{s,f}^2 - H*_s^2) / 2.
 // bnd: 0 interior; 1 wall, the ghost of Sec. 2.5 (u_n reversed, u_t kept, same
 // depth); 2 open, the transmissive ghost (the face state itself).
-template <typename real>
+template <typename real, bool FAST = false>
 __device__ __forceinline__ void face_flux(real g, real half_g, real hthr,
                                           real HfL, real HufL, real HvfL, real zL,
                                           real HfR, real HufR, real HvfR, real zR,
@@ -175,7 +187,14 @@ __device__ __forceinline__ void face_flux(real g, real half_g, real hthr,
                                           real Phi[3], real &PL, real &PR, real &amax)
 {
     real uL = real(0), vL = real(0);
-    if (HfL > hthr) { uL = HufL / HfL; vL = HvfL / HfL; }
+    if (HfL > hthr) {
+        if constexpr (FAST) {
+            const real r = real(1) / HfL;
+            uL = HufL * r; vL = HvfL * r;
+        } else {
+            uL = HufL / HfL; vL = HvfL / HfL;
+        }
+    }
     real unL = uL * nx + vL * ny;
     real utL = -uL * ny + vL * nx;
     real HsL, HsR, unR, utR;
@@ -187,7 +206,14 @@ __device__ __forceinline__ void face_flux(real g, real half_g, real hthr,
         HfR = HfL;
     } else {
         real uR = real(0), vR = real(0);
-        if (HfR > hthr) { uR = HufR / HfR; vR = HvfR / HfR; }
+        if (HfR > hthr) {
+            if constexpr (FAST) {
+                const real r = real(1) / HfR;
+                uR = HufR * r; vR = HvfR * r;
+            } else {
+                uR = HufR / HfR; vR = HvfR / HfR;
+            }
+        }
         unR = uR * nx + vR * ny;
         utR = -uR * ny + vR * nx;
         real zs = vmax(zL, zR);
@@ -195,7 +221,7 @@ __device__ __forceinline__ void face_flux(real g, real half_g, real hthr,
         HsR = vmax(real(0), (HfR + zR) - zs);
     }
     real F[3];
-    hll_normal<real>(g, half_g, HsL, unL, utL, HsR, unR, utR, F, amax);
+    hll_normal<real, FAST>(g, half_g, HsL, unL, utL, HsR, unR, utR, F, amax);
     Phi[0] = F[0];
     Phi[1] = F[1] * nx - F[2] * ny;
     Phi[2] = F[1] * ny + F[2] * nx;
@@ -388,14 +414,20 @@ __device__ __forceinline__ void st4(double *p, double x, double y, double z, dou
 // terms: R = -(aH, aHu, aHv) / |K|; stage 1 writes R0 and the CFL bound of
 // am = max_f l_f a_f; stage 2 forms w^{n+1} = w^n / 2 + (w1 + dt R) / 2 with
 // w^n = x, w1 from shared memory, and the dry fix.
-template <typename real, int STAGE>
+template <typename real, int STAGE, bool FAST = false>
 __device__ __forceinline__ void finish_cell(const KArgs<real> &a, int gid, const real *sWl, real aH, real aHu,
                                             real aHv, real am, const real x[3], real area, real dt, real &my_min,
                                             long long &my_neg, bool &bad)
 {
     constexpr bool ETA = EtaForm<real>::value;
     const int nc = (int)a.nc;
-    real RH = -aH / area, RHu = -aHu / area, RHv = -aHv / area;
+    real RH, RHu, RHv;
+    if constexpr (FAST) {
+        const real ia = real(1) / area;
+        RH = -aH * ia; RHu = -aHu * ia; RHv = -aHv * ia;
+    } else {
+        RH = -aH / area; RHu = -aHu / area; RHv = -aHv / area;
+    }
     if (STAGE == 1) {
         a.R0[gid] = RH;
         a.R0[nc + gid] = RHu;
@@ -471,7 +503,7 @@ __host__ __device__ inline size_t stage_smem_bytes(int block, int max_halo, int 
 // after phase B, z_f the bed the face value stands on, and after phase C the
 // cell's own term (l_f Phi_0, l_f (Phi_1 + P n_x), l_f (Phi_2 + P n_y), l_f a_f).
 // Stage 2's phase D reads w^n of its cell from global memory.
-template <typename real, int STAGE, int DRY, bool LISTED, bool GIDS>
+template <typename real, int STAGE, int DRY, bool LISTED, bool GIDS, bool FAST = false>
 __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b, const real dt,
                                               unsigned char *smem_raw, int &qcount, real &my_min,
                                               long long &my_neg, bool &bad)
@@ -596,7 +628,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             real x[3] = {real(0), real(0), real(0)};
             if (STAGE == 2) { x[0] = a.w[gid]; x[1] = a.w[nc + gid]; x[2] = a.w[2 * nc + gid]; }
             // R = -0 / |K| = -0 for any area, so the area is not read
-            finish_cell<real, STAGE>(a, gid, sW + 4 * tid, real(0), real(0), real(0), real(0), x, real(1), dt,
+            finish_cell<real, STAGE, FAST>(a, gid, sW + 4 * tid, real(0), real(0), real(0), real(0), x, real(1), dt,
                                      my_min, my_neg, bad);
         }
         return;
@@ -706,6 +738,19 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
 #pragma unroll
                     for (int f = 0; f < 3; f++)
                         alpha = fminf(alpha, (D[f] > 0.f ? up : dn) * rcp_approx(fabsf(D[f])));
+                } else if constexpr (FAST) {
+                    // the smallest ratio |r_f| / |D_f| below 1 (r_f = q_max - q_K or
+                    // q_K - q_min by the sign of D_f) found by cross products; one
+                    // division, none when no face limits
+                    const real up = qmax - qK[v], dn = qK[v] - qmin;
+                    real num = real(1), den = real(1);
+#pragma unroll
+                    for (int f = 0; f < 3; f++) {
+                        const real aD = vabs(D[f]);
+                        const real r = D[f] > real(0) ? up : dn;
+                        if (r * den < num * aD) { num = r; den = aD; }
+                    }
+                    if (num != den) alpha = num / den;
                 } else {
 #pragma unroll
                     for (int f = 0; f < 3; f++) {
@@ -795,7 +840,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             nx = geo[(GEO_NX + f) * nc + gid];
             ny = geo[(GEO_NY + f) * nc + gid];
             len = geo[(GEO_LEN + f) * nc + gid];
-            face_flux<real>(g, half_g, hthr, WfL, HufL, HvfL, zL,
+            face_flux<real, FAST>(g, half_g, hthr, WfL, HufL, HvfL, zL,
                             WfR, HufR, HvfR, zR, nx, ny, bnd, Phi, PL, PR, am);
         }
         const real t0 = len * Phi[0];
@@ -840,7 +885,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             }
         }
         if (STAGE == 2) { x[0] = a.w[gid]; x[1] = a.w[nc + gid]; x[2] = a.w[2 * nc + gid]; }
-        finish_cell<real, STAGE>(a, gid, sW + 4 * l, aH, aHu, aHv, am, x, area, dt, my_min, my_neg, bad);
+        finish_cell<real, STAGE, FAST>(a, gid, sW + 4 * l, aH, aHu, aHv, am, x, area, dt, my_min, my_neg, bad);
     }
 }
 
@@ -859,7 +904,7 @@ template <> struct StageMinCtas<float, 256> { static constexpr int value = 6; };
 template <> struct StageMinCtas<float, 384> { static constexpr int value = 4; };
 template <> struct StageMinCtas<float, 512> { static constexpr int value = 3; };
 
-template <typename real, int STAGE, int MAXT>
+template <typename real, int STAGE, int MAXT, bool FAST = false>
 __global__ void __launch_bounds__(MAXT, StageMinCtas<real, MAXT>::value) stage_kernel(const KArgs<real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -867,6 +912,19 @@ __global__ void __launch_bounds__(MAXT, StageMinCtas<real, MAXT>::value) stage_k
     __shared__ real red_min[32];
     __shared__ long long red_neg[32];
     const int tid = threadIdx.x;
+
+    // a context that has reached t_end takes steps of dt = 0 that leave its state
+    // as it is: stage 1 does nothing (the CFL minimum stays empty) and stage 2
+    // copies w^n to the output buffer, bit for bit (computing w/2 + (w + 0 R)/2
+    // would flush the smallest FP32 values to zero), as the batched kernels do
+    if (a.t_end > 0.0 && a.sc->t >= a.t_end) {
+        if (STAGE == 2) {
+            const int64_t n3 = 3 * a.nc;
+            for (int64_t i = blockIdx.x * (int64_t)blockDim.x + tid; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+                a.wout[i] = a.w[i];
+        }
+        return;
+    }
 
     real dt = real(0);
     if (STAGE == 2) dt = (real)step_dt<real>(a.sc, a.cfl, a.dt_fixed, a.dt_max, a.t_end);
@@ -879,7 +937,7 @@ __global__ void __launch_bounds__(MAXT, StageMinCtas<real, MAXT>::value) stage_k
 
     int parity = 0;
     for (int b = blockIdx.x; b < a.nblocks; b += gridDim.x, parity ^= 1)
-        process_block<real, STAGE, DryMode<real, STAGE>::value, STAGE == 2, false>(a, b, dt, smem_raw, qcount[parity],
+        process_block<real, STAGE, DryMode<real, STAGE>::value, STAGE == 2, false, FAST>(a, b, dt, smem_raw, qcount[parity],
                                                                                      my_min, my_neg, bad);
 
     // CTA-level reductions, then one atomic per CTA
@@ -937,7 +995,7 @@ __device__ __forceinline__ unsigned long long warp_min_bits(real v)
     return min_bits(v);
 }
 
-template <typename real, int STAGE>
+template <typename real, int STAGE, bool FAST = false>
 __global__ void __launch_bounds__(256, (StageMinCtas<real, 256>::value)) batch_stage_kernel(const BatchMesh<real> *meshes, int n_mesh,
                                                           int n_items, int n_entries, DevScalars *sc_all)
 {
@@ -945,12 +1003,16 @@ __global__ void __launch_bounds__(256, (StageMinCtas<real, 256>::value)) batch_s
     __shared__ int qcount[2];
     __shared__ unsigned long long s_min[kBatchMaxEntries];
     __shared__ real s_dt[kBatchMaxEntries];
+    __shared__ unsigned char s_done[kBatchMaxEntries];
     __shared__ long long red_neg[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = (blockDim.x + 31) >> 5;
     const KArgs<real> &p0 = meshes[0].a;
     for (int e = tid; e < n_entries; e += blockDim.x) {
         s_min[e] = min_bits(real_inf<real>());
         s_dt[e] = STAGE == 2 ? (real)step_dt<real>(sc_all + e, p0.cfl, p0.dt_fixed, p0.dt_max, p0.t_end) : real(0);
+        // a scenario that has reached t_end takes steps of dt = 0 that leave its
+        // state as it is (as a single context's do): skip its work, copy its state
+        s_done[e] = (p0.t_end > 0.0 && sc_all[e].t >= p0.t_end) ? 1 : 0;
     }
     if (tid < 2) qcount[tid] = 0;
     __syncthreads();
@@ -963,6 +1025,20 @@ __global__ void __launch_bounds__(256, (StageMinCtas<real, 256>::value)) batch_s
         const BatchMesh<real> &bm = meshes[m];
         const int b = item - bm.first_item;
         for (int s = 0; s < bm.n_scen; s++) {
+            if (s_done[bm.first_entry + s]) {
+                if (STAGE == 2) {
+                    // the state carries over to the other buffer of the pair
+                    const int c = b * bm.a.block + tid, nc = (int)bm.a.nc;
+                    if (tid < bm.a.block && c < nc) {
+                        const real *wi = bm.a.w + s * bm.stride;
+                        real *wo = bm.a.wout + s * bm.stride;
+                        wo[c] = wi[c];
+                        wo[nc + c] = wi[nc + c];
+                        wo[2 * nc + c] = wi[2 * nc + c];
+                    }
+                }
+                continue;
+            }
             KArgs<real> a = bm.a;
             a.w += s * bm.stride;
             a.R0 += s * bm.stride;
@@ -970,7 +1046,7 @@ __global__ void __launch_bounds__(256, (StageMinCtas<real, 256>::value)) batch_s
             a.sc += s;
             const int e = bm.first_entry + s;
             real mn = real_inf<real>();
-            process_block<real, STAGE, 2, true, true>(a, b, s_dt[e], smem_raw, qcount[parity], mn, my_neg, bad);
+            process_block<real, STAGE, 2, true, true, FAST>(a, b, s_dt[e], smem_raw, qcount[parity], mn, my_neg, bad);
             parity ^= 1;
             if (STAGE == 1) {
                 unsigned long long bits = warp_min_bits<real>(mn);
@@ -1086,12 +1162,14 @@ KArgs<real> make_args(const DevPtrs &d, const StepParams &p, const void *w_in, v
 
 // Kernel instance for a launch: the register budget follows the thread count
 // (launch bounds 256 or 512).
-template <typename real>
+template <typename real, bool FAST = false>
 void *stage_kernel_ptr(int stage, int threads)
 {
-    if (threads <= 256) return stage == 1 ? (void *)stage_kernel<real, 1, 256> : (void *)stage_kernel<real, 2, 256>;
-    if (threads <= 384) return stage == 1 ? (void *)stage_kernel<real, 1, 384> : (void *)stage_kernel<real, 2, 384>;
-    return stage == 1 ? (void *)stage_kernel<real, 1, 512> : (void *)stage_kernel<real, 2, 512>;
+    if (threads <= 256)
+        return stage == 1 ? (void *)stage_kernel<real, 1, 256, FAST> : (void *)stage_kernel<real, 2, 256, FAST>;
+    if (threads <= 384)
+        return stage == 1 ? (void *)stage_kernel<real, 1, 384, FAST> : (void *)stage_kernel<real, 2, 384, FAST>;
+    return stage == 1 ? (void *)stage_kernel<real, 1, 512, FAST> : (void *)stage_kernel<real, 2, 512, FAST>;
 }
 
 // The dynamic shared memory limit is an attribute of the kernel function, shared
@@ -1107,11 +1185,11 @@ inline cudaError_t raise_smem_limit(const void *kern, size_t smem)
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <typename real>
+template <typename real, bool FAST = false>
 int stage_config(const DevPtrs &d, int stage, LaunchCfg &cfg)
 {
     cfg.smem = stage_smem_bytes<real>(d.block, d.max_halo, d.max_ring1);
-    const void *kern = stage_kernel_ptr<real>(stage, d.threads);
+    const void *kern = stage_kernel_ptr<real, FAST>(stage, d.threads);
     cudaError_t e = raise_smem_limit(kern, cfg.smem);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0;
@@ -1127,32 +1205,32 @@ int stage_config(const DevPtrs &d, int stage, LaunchCfg &cfg)
     return 0;
 }
 
-template <typename real>
+template <typename real, bool FAST = false>
 int launch_stage(const DevPtrs &d, const StepParams &p, int stage, const void *w_in, void *w_out,
                  const LaunchCfg &c, void *stream)
 {
     KArgs<real> a = make_args<real>(d, p, w_in, w_out);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (d.threads <= 256) {
-        if (stage == 1) stage_kernel<real, 1, 256><<<c.grid, d.threads, c.smem, s>>>(a);
-        else stage_kernel<real, 2, 256><<<c.grid, d.threads, c.smem, s>>>(a);
+        if (stage == 1) stage_kernel<real, 1, 256, FAST><<<c.grid, d.threads, c.smem, s>>>(a);
+        else stage_kernel<real, 2, 256, FAST><<<c.grid, d.threads, c.smem, s>>>(a);
     } else if (d.threads <= 384) {
-        if (stage == 1) stage_kernel<real, 1, 384><<<c.grid, d.threads, c.smem, s>>>(a);
-        else stage_kernel<real, 2, 384><<<c.grid, d.threads, c.smem, s>>>(a);
+        if (stage == 1) stage_kernel<real, 1, 384, FAST><<<c.grid, d.threads, c.smem, s>>>(a);
+        else stage_kernel<real, 2, 384, FAST><<<c.grid, d.threads, c.smem, s>>>(a);
     } else {
-        if (stage == 1) stage_kernel<real, 1, 512><<<c.grid, d.threads, c.smem, s>>>(a);
-        else stage_kernel<real, 2, 512><<<c.grid, d.threads, c.smem, s>>>(a);
+        if (stage == 1) stage_kernel<real, 1, 512, FAST><<<c.grid, d.threads, c.smem, s>>>(a);
+        else stage_kernel<real, 2, 512, FAST><<<c.grid, d.threads, c.smem, s>>>(a);
     }
     return (int)cudaGetLastError();
 }
 
-template <typename real>
+template <typename real, bool FAST = false>
 int batch_config(int block, int max_halo, int max_ring1, int &grid, size_t &smem)
 {
     smem = stage_smem_bytes<real>(block, max_halo, max_ring1, true);
     int best = 1 << 30;
     for (int stage = 1; stage <= 2; stage++) {
-        auto kern = stage == 1 ? batch_stage_kernel<real, 1> : batch_stage_kernel<real, 2>;
+        auto kern = stage == 1 ? batch_stage_kernel<real, 1, FAST> : batch_stage_kernel<real, 2, FAST>;
         cudaError_t e = raise_smem_limit((const void *)kern, smem);
         if (e != cudaSuccess) return (int)e;
         int per_sm = 0;
@@ -1168,14 +1246,14 @@ int batch_config(int block, int max_halo, int max_ring1, int &grid, size_t &smem
     return 0;
 }
 
-template <typename real>
+template <typename real, bool FAST = false>
 int launch_batch_step(const void *table, int n_mesh, int n_items, int n_entries, DevScalars *sc_all, int block,
                       int grid, size_t smem, const StepParams &p, bool gauges, void *stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const BatchMesh<real> *t = static_cast<const BatchMesh<real> *>(table);
-    batch_stage_kernel<real, 1><<<grid, block, smem, s>>>(t, n_mesh, n_items, n_entries, sc_all);
-    batch_stage_kernel<real, 2><<<grid, block, smem, s>>>(t, n_mesh, n_items, n_entries, sc_all);
+    batch_stage_kernel<real, 1, FAST><<<grid, block, smem, s>>>(t, n_mesh, n_items, n_entries, sc_all);
+    batch_stage_kernel<real, 2, FAST><<<grid, block, smem, s>>>(t, n_mesh, n_items, n_entries, sc_all);
     batch_post_kernel<real><<<1, 256, 0, s>>>(n_entries, sc_all, p.cfl, p.dt_fixed, p.dt_max, p.t_end);
     if (gauges) batch_gauge_kernel<real><<<n_mesh, 256, 0, s>>>(t, sc_all, p.gauge_every);
     return (int)cudaGetLastError();

@@ -93,6 +93,7 @@ enum : unsigned int {
 struct StepParams {
     double g, cfl, hthr, dt_fixed, dt_max, t_end;
     int order, gauge_every;
+    int fp64_fast;          // FP64: the contracted build of the stage kernels (step_f64_fast.cu)
 };
 
 // Device pointers of one context (element type = the context's real).
@@ -100,6 +101,7 @@ struct DevPtrs {
     int64_t nc;
     int32_t block, nblocks, max_halo, max_ring1, n_gauges, ring_cap;
     int32_t threads;        // threads per CTA of the stage kernels (>= block)
+    int32_t fp64_fast;      // FP64: launch the contracted build (step_f64_fast.cu), not the literal one
     const void *geo;        // FP64: [GEO_ROWS][nc]; FP32: [nc][16] record
     const void *z;          // [nc]
     const void *zf;         // face beds: FP64 [3][nc]; FP32 [nc][2] = (z_f - z_K) of faces 0
@@ -151,6 +153,16 @@ int launch_stage2_f32(const DevPtrs &d, const StepParams &p, const void *w_in, v
 int launch_stage1_f64(const DevPtrs &d, const StepParams &p, const void *w_in, const LaunchCfg &c, void *stream);
 int launch_stage2_f64(const DevPtrs &d, const StepParams &p, const void *w_in, void *w_out, const LaunchCfg &c, void *stream);
 
+// The contracted FP64 build (step_f64_fast.cu); the *_f64 entry points above
+// dispatch to it when DevPtrs::fp64_fast / StepParams::fp64_fast is set.
+int stage_config_f64_fast(const DevPtrs &d, int stage, LaunchCfg &cfg);
+int launch_stage1_f64_fast(const DevPtrs &d, const StepParams &p, const void *w_in, const LaunchCfg &c, void *stream);
+int launch_stage2_f64_fast(const DevPtrs &d, const StepParams &p, const void *w_in, void *w_out, const LaunchCfg &c,
+                           void *stream);
+int batch_config_f64_fast(int block, int max_halo, int max_ring1, int &grid, size_t &smem);
+int launch_batch_step_f64_fast(const void *table, int n_mesh, int n_items, int n_entries, DevScalars *sc_all,
+                               int block, int grid, size_t smem, const StepParams &p, bool gauges, void *stream);
+
 // Batched ensembles (step_f32.cu / step_f64.cu): the device table entry of one
 // mesh, the launch configuration, and one batched step (stage 1, stage 2,
 // epilogue) over all scenarios.  sc_all has n_entries scenario scalars plus one
@@ -162,7 +174,7 @@ void fill_batch_mesh_f32(void *dst, const DevPtrs &d, const StepParams &p, const
 void fill_batch_mesh_f64(void *dst, const DevPtrs &d, const StepParams &p, const void *w_in, void *w_out, int n_scen,
                          int first_item, int first_entry);
 int batch_config_f32(int block, int max_halo, int max_ring1, int &grid, size_t &smem);
-int batch_config_f64(int block, int max_halo, int max_ring1, int &grid, size_t &smem);
+int batch_config_f64(int block, int max_halo, int max_ring1, int &grid, size_t &smem, bool fast);
 int launch_batch_step_f32(const void *table, int n_mesh, int n_items, int n_entries, DevScalars *sc_all, int block,
                           int grid, size_t smem, const StepParams &p, bool gauges, void *stream);
 int launch_batch_step_f64(const void *table, int n_mesh, int n_items, int n_entries, DevScalars *sc_all, int block,

@@ -41,7 +41,7 @@ class vg_params(C.Structure):
                 ("dt_fixed", C.c_double), ("dt_max", C.c_double), ("t_end", C.c_double),
                 ("order", C.c_int32), ("gauge_every", C.c_int32),
                 ("strict_positivity", C.c_int32), ("block_cells", C.c_int32),
-                ("block_threads", C.c_int32)]
+                ("block_threads", C.c_int32), ("fp64_literal", C.c_int32)]
 
 
 class vg_diag(C.Structure):
@@ -102,7 +102,7 @@ _SIGNATURES = {
     "vg_batch_get_state": ([_V, C.c_int32, C.c_int32, _D, _D, _D, _D, _I64], C.c_int),
     "vg_batch_step": ([_V, C.c_int64], C.c_int),
     "vg_batch_run": ([_V, C.c_double, C.c_int64, _I64], C.c_int),
-    "vg_batch_autotune": ([_V, C.c_int32, C.POINTER(C.c_int32), _D], C.c_int),
+    "vg_batch_autotune": ([_V, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _D], C.c_int),
     "vg_batch_info": ([_V, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _I64, _I64], C.c_int),
     "vg_batch_set_gauges": ([_V, C.c_int32, C.c_int32, _D], C.c_int),
     "vg_batch_set_open_boundary": ([_V, C.c_int32, C.c_int64, _I32], C.c_int),
@@ -579,10 +579,12 @@ class Batch:
         return taken.value
 
     def autotune(self, n_steps: int = 4):
-        blk = C.c_int32()
+        """(block cells, ms per step, CTAs per SM or 0 for as many as fit) of the
+        fastest launch shape (vg_batch_autotune)."""
+        blk, ctas = C.c_int32(), C.c_int32()
         ms = C.c_double()
-        _bcheck(self.h, load().vg_batch_autotune(self.h, int(n_steps), C.byref(blk), C.byref(ms)))
-        return blk.value, ms.value
+        _bcheck(self.h, load().vg_batch_autotune(self.h, int(n_steps), C.byref(blk), C.byref(ctas), C.byref(ms)))
+        return blk.value, ms.value, ctas.value
 
     def set_gauges(self, mesh_id: int, xy) -> None:
         xy = _f64(xy).reshape(-1, 2)
