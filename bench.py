@@ -545,8 +545,8 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=2000, help="0 skips the adjoint-cost leg")
     ap.add_argument("--adjoint-binomial-slots", type=int, default=16, help="0 skips the binomial run")
     ap.add_argument("--config-legs", type=int, default=1,
-                    help="0 skips the other configurations (the other precision on the same mesh, and "
-                         "the 5M coast basin in FP32 and FP64)")
+                    help="0 skips the other configurations (the other precision on the same mesh, the "
+                         "all-wet control, and the 5M coast basin in FP32 and FP64)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -654,10 +654,13 @@ def main():
     configs = None
     if rank == 0 and args.config_legs > 0 and args.workload == "thacker_paraboloid_40m":
         # the other precision on the same 40M mesh (FP64: at most 20 timed steps,
-        # ~90 ms each), then the 5M-triangle coast basin in FP32 and FP64
+        # ~90 ms each), the all-wet control (the 40M grid over a flat 10 m bed: no
+        # dry cell, every cell reconstructs), then the 5M-triangle coast basin in
+        # FP32 and FP64
         configs = {}
         other = 64 if args.precision == 32 else 32
         legs = [(f"thacker_paraboloid_40m_fp{other}", "thacker_paraboloid_40m", other, (mesh, st0)),
+                ("flat_basin_allwet_40m_fp32", "flat_basin_allwet_40m", 32, None),
                 ("coast_basin_5m_fp32", "coast_basin_5m", 32, None),
                 ("coast_basin_5m_fp64", "coast_basin_5m", 64, None)]
         coast = None
