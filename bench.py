@@ -52,6 +52,11 @@ UNIT = "cell-updates/s"
 # touched once): stage 1 reads w^n, bed, mesh and writes R0; stage 2 also
 # reads w^n and R0 and writes w^{n+1}.
 ALGO_BYTES = {32: {"stage1": 64, "stage2": 76}, 64: {"stage1": 104, "stage2": 128}}
+# The unfused RK stages (rk_unfused = 1) replace stage 2 by: update 1 (reads w^n,
+# R0 and the bed, writes w1), the residual of w1 (stage 1's bytes) and update 2
+# (reads w^n, w1, R(w1) and the bed, writes w^{n+1}).
+UNFUSED_BYTES = {32: {"rk_update1": 40, "residual_w1": 64, "rk_update2": 52},
+                 64: {"rk_update1": 80, "residual_w1": 104, "rk_update2": 104}}
 
 # FP64 is bound by GB300's FP64 units, not HBM.  Algorithmic FP64 operations per
 # cell per full step (add, sub, mul, div, sqrt on state-dependent values; the
@@ -437,12 +442,20 @@ def roofline_of(prof, nc: int, precision: int, workload: str, step_ms: float):
     achieved = algo / (avg_ms * 1e-3) / 1e9
     traffic = profiled_traffic(workload, precision, dom)
     kernel_ms = {k: round(tot_ / max(n_, 1), 4) for k, (n_, tot_) in per_kernel.items()}
-    step_bytes = (ALGO_BYTES[precision]["stage1"] + ALGO_BYTES[precision]["stage2"]) * nc
+    per_cell = dict(ALGO_BYTES[precision], **UNFUSED_BYTES[precision])
+    unfused = "rk_update1" in per_kernel
+    step_bytes = sum(per_cell[k] for k in (("stage1", "rk_update1", "residual_w1", "rk_update2") if unfused
+                                           else ("stage1", "stage2"))) * nc
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom,
                 "algo_bytes_per_launch": algo, "peak_kind": f"{peak_kind} hbm_gbs",
                 "kernel_avg_ms": kernel_ms,
                 "step_algo_gbs": round(step_bytes / (step_ms * 1e-3) / 1e9, 1)}
+    if unfused:
+        # every kernel of the unfused step against the same peak
+        roofline["per_kernel_gbs"] = {k: round(per_cell[k] * nc / (kernel_ms[k] * 1e-3) / 1e9, 1)
+                                      for k in ("stage1", "rk_update1", "residual_w1", "rk_update2")
+                                      if kernel_ms.get(k)}
     if precision == 64:
         kind = WORKLOADS[workload].get("kind", "thacker")
         flops = 0.5 * FP64_FLOPS_PER_CELL_STEP[kind] * nc
@@ -546,6 +559,9 @@ def main():
     ap.add_argument("--fp64-build", default="literal", choices=["literal", "contracted"],
                     help="FP64 stage kernels of the main leg: literal (bit for bit the oracle's arithmetic, the "
                          "library default) or contracted (fused multiply-adds, fewer divisions)")
+    ap.add_argument("--rk-unfused", type=int, default=0, choices=[0, 1],
+                    help="1 runs the main leg with the RK stage updates as kernels of their own "
+                         "(for profiling them; the default line is the fused step)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -579,7 +595,7 @@ def main():
     stream = torch.cuda.Stream()
     sv = volna.Solver(precision=args.precision, device=torch.cuda.current_device(), stream=stream)
     sv.set_params(h_threshold=workload_hthr(args.workload), cfl=0.9,
-                  fp64_literal=0 if args.fp64_build == "contracted" else 1)
+                  fp64_literal=0 if args.fp64_build == "contracted" else 1, rk_unfused=args.rk_unfused)
     sv.upload_mesh(mesh, renumber=args.renumber)
     sv.set_state(st0.H, st0.Hu, st0.Hv, 0.0)
     nc = mesh.nc
@@ -671,6 +687,7 @@ def main():
         other = 64 if args.precision == 32 else 32
         legs = [(f"thacker_paraboloid_40m_fp{other}", "thacker_paraboloid_40m", other, (mesh, st0)),
                 ("flat_basin_allwet_40m_fp32", "flat_basin_allwet_40m", 32, None),
+                ("thacker_paraboloid_40m_fp32_rk_unfused", "thacker_paraboloid_40m", 32, (mesh, st0)),
                 ("coast_basin_5m_fp32", "coast_basin_5m", 32, None),
                 ("coast_basin_5m_fp64", "coast_basin_5m", 64, None)]
         coast = None
@@ -683,6 +700,10 @@ def main():
                 # FP64: the literal build (bit for bit the oracle's arithmetic, the
                 # default) and the contracted build (fp64_literal = 0)
                 var = {"literal": {}, "contracted": {"fp64_literal": 0}} if prec == 64 else None
+                if key.endswith("_rk_unfused"):
+                    # the RK stage updates as kernels of their own (w1 and R(w1)
+                    # through HBM), against the fused headline step
+                    var = {"rk_unfused": {"rk_unfused": 1}}
                 configs[key] = workload_leg(torch, stream, wl, prec, n_steps, inputs=inp,
                                             renumber=args.renumber, variants=var)
             except Exception as e:         # reported, not fatal: the headline is the forward step
@@ -707,6 +728,7 @@ def main():
                 "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "cells": nc, "renumber": args.renumber,
                            **({"fp64_build": args.fp64_build} if args.precision == 64 else {}),
+                           **({"rk_unfused": 1} if args.rk_unfused else {}),
                            "block_cells": 256, "cfl": 0.9, "h_threshold": workload_hthr(args.workload),
                            "l2": "inputs larger than L2 (%.1f GB resident)" % dev_gb,
                            "parallelism": f"replicas x{ws}"},

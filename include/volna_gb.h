@@ -87,6 +87,15 @@ typedef struct vg_params {
                               (a thin film's velocity, hence the CFL step)
                               differently, so trajectories drift apart.  The
                               adjoint always runs the literal form: 1           */
+    int32_t rk_unfused;    /* 1: vg_step and vg_advance_to run the SSP-RK(2,2)
+                              stage updates (Sec. 2.3) as kernels of their own,
+                              with w1 and R(w1) in device memory (two more
+                              [3][N] arrays, allocated by vg_set_params or
+                              vg_mesh_upload), instead of forming w1 inside the
+                              second residual kernel and ending it with the
+                              update: the same arithmetic cell by cell, kept
+                              to measure what the fusion saves.  Batches, the
+                              adjoint and vg_step_noalloc always run fused: 0 */
 } vg_params;
 
 /* Run diagnostics (vg_get_diagnostics). */

@@ -22,8 +22,9 @@ namespace {
 
 constexpr int kRingCap = 2048;       // gauge records held on the device between drains
 constexpr int kDiagBlocks = 1024;
-constexpr int kKernels = 4;
-const char *kKernelNames[kKernels] = {"stage1", "stage2", "post_step", "bed_update"};
+constexpr int kKernels = 7;
+const char *kKernelNames[kKernels] = {"stage1", "stage2", "post_step", "bed_update",
+                                      "rk_update1", "residual_w1", "rk_update2"};
 
 }  // namespace
 
@@ -40,6 +41,7 @@ struct vg_ctx {
     // device memory
     void *geo = nullptr, *z = nullptr, *w[2] = {nullptr, nullptr}, *R0 = nullptr;
     void *zf = nullptr;               // face beds (layout: DevPtrs::zf)
+    void *rk_w1 = nullptr, *rk_R1 = nullptr;   // [3][nc] each: w1 and R(w1) of the unfused RK stages
     double *z64 = nullptr;
     float *z_orig = nullptr;          // FP32: the bed in the original cell order (state import/export)
     double *z64_orig = nullptr;
@@ -150,6 +152,7 @@ void free_mesh(vg_ctx *c)
     if (c->graph2) { cudaGraphExecDestroy(c->graph2); c->graph2 = nullptr; }
     if (c->z64 == c->z) c->z64 = nullptr;
     dfree(c->geo); dfree(c->z); dfree(c->zf); dfree(c->z64); dfree(c->w[0]); dfree(c->w[1]); dfree(c->R0);
+    dfree(c->rk_w1); dfree(c->rk_R1);
     dfree(c->z_orig); dfree(c->z64_orig); c->zorig_ok = false;
     dfree(c->nbr); dfree(c->halo_ptr); dfree(c->halo_n1); dfree(c->halo_ids); dfree(c->ring1_nbr);
     dfree(c->old_of_new); dfree(c->new_of_old); dfree(c->nbrl); dfree(c->fq_ptr); dfree(c->fq);
@@ -453,7 +456,7 @@ int ev_collect(vg_ctx *c)
 }
 
 // Kernels one step launches.
-int step_kernels(const vg_ctx *c) { return c->bed_on ? 4 : 3; }
+int step_kernels(const vg_ctx *c) { return (c->bed_on ? 4 : 3) + (c->prm.rk_unfused ? 2 : 0); }
 
 // Queue one step reading w[src] and writing w[1 - src].
 int enqueue_step(vg_ctx *c, int src)
@@ -468,10 +471,22 @@ int enqueue_step(vg_ctx *c, int src)
     e = c->precision == 64 ? launch_stage1_f64(d, p, win, c->cfg1, s) : launch_stage1_f32(d, p, win, c->cfg1, s);
     if (e) return cuda_fail(c, (cudaError_t)e, "stage 1 launch");
     if ((rc = ev_end(c))) return rc;
-    if ((rc = ev_begin(c, 1))) return rc;
-    e = c->precision == 64 ? launch_stage2_f64(d, p, win, wout, c->cfg2, s) : launch_stage2_f32(d, p, win, wout, c->cfg2, s);
-    if (e) return cuda_fail(c, (cudaError_t)e, "stage 2 launch");
-    if ((rc = ev_end(c))) return rc;
+    if (c->prm.rk_unfused) {
+        // the stage updates as kernels of their own (w1 and R(w1) through memory)
+        for (int part = 0; part < 3; part++) {
+            if ((rc = ev_begin(c, 4 + part))) return rc;
+            e = c->precision == 64 ? launch_rk_unfused_f64(d, p, part, win, wout, c->rk_w1, c->rk_R1, c->cfg1, s)
+                                   : launch_rk_unfused_f32(d, p, part, win, wout, c->rk_w1, c->rk_R1, c->cfg1, s);
+            if (e) return cuda_fail(c, (cudaError_t)e, "unfused RK stage launch");
+            if ((rc = ev_end(c))) return rc;
+        }
+    } else {
+        if ((rc = ev_begin(c, 1))) return rc;
+        e = c->precision == 64 ? launch_stage2_f64(d, p, win, wout, c->cfg2, s)
+                               : launch_stage2_f32(d, p, win, wout, c->cfg2, s);
+        if (e) return cuda_fail(c, (cudaError_t)e, "stage 2 launch");
+        if ((rc = ev_end(c))) return rc;
+    }
     if (c->bed_on) {
         // the bed of the step's end time, with H kept, before the gauges record
         if ((rc = ev_begin(c, 3))) return rc;
@@ -560,6 +575,19 @@ int validate_params(const vg_params *p, std::string &why)
         return VG_EINVAL;
     }
     if (p->fp64_literal != 0 && p->fp64_literal != 1) { why = "fp64_literal must be 0 or 1"; return VG_EINVAL; }
+    if (p->rk_unfused != 0 && p->rk_unfused != 1) { why = "rk_unfused must be 0 or 1"; return VG_EINVAL; }
+    return VG_OK;
+}
+
+// The unfused RK stages' w1 and R(w1), allocated once a context with a mesh asks
+// for them (never during a step, which a CUDA graph may be capturing).
+int ensure_rk_buffers(vg_ctx *c)
+{
+    if (!c->has_mesh || !c->prm.rk_unfused) return VG_OK;
+    const size_t bytes = 3 * (size_t)c->hm.nc * real_size(c);
+    int rc;
+    if (!c->rk_w1 && (rc = dmalloc(c, &c->rk_w1, bytes))) return rc;
+    if (!c->rk_R1 && (rc = dmalloc(c, &c->rk_R1, bytes))) return rc;
     return VG_OK;
 }
 
@@ -627,6 +655,7 @@ int vg_default_params(vg_params *p)
     p->block_cells = 0;
     p->block_threads = 0;
     p->fp64_literal = 1;
+    p->rk_unfused = 0;
     return VG_OK;
 }
 
@@ -705,6 +734,8 @@ int vg_mesh_upload(vg_ctx *c, int64_t nv, const double *xy, int64_t nc, const in
     c->has_mesh = true;
     c->has_state = false;
     c->cur = 0;
+    int rc_rk = ensure_rk_buffers(c);
+    if (rc_rk) { free_mesh(c); return rc_rk; }
     return VG_OK;
 }
 
@@ -748,7 +779,7 @@ int vg_set_params(vg_ctx *c, const vg_params *p)
         if ((rc = upload_partition(c))) return rc;
         if ((rc = configure_launch(c))) return rc;
     }
-    return VG_OK;
+    return ensure_rk_buffers(c);
 }
 
 int vg_get_params(vg_ctx *c, vg_params *p)
@@ -1231,6 +1262,7 @@ int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_eve
     c->prm.t_end = 0.0;
     c->prm.gauge_every = 1;
     c->prm.fp64_literal = 1;            // the adjoint reverses the literal form
+    c->prm.rk_unfused = 0;
     c->graph_dirty = true;
     {
         int rc0 = configure_launch(c);

@@ -12,6 +12,11 @@ int launch_stage2_f32(const DevPtrs &d, const StepParams &p, const void *w_in, v
 {
     return launch_stage<float>(d, p, 2, w_in, w_out, c, stream);
 }
+int launch_rk_unfused_f32(const DevPtrs &d, const StepParams &p, int part, const void *w_in, void *w_out, void *w1,
+                          void *R1, const LaunchCfg &c1, void *stream)
+{
+    return launch_rk_unfused<float>(d, p, part, w_in, w_out, w1, R1, c1, stream);
+}
 size_t batch_mesh_bytes_f32() { return sizeof(BatchMesh<float>); }
 void fill_batch_mesh_f32(void *dst, const DevPtrs &d, const StepParams &p, const void *w_in, void *w_out, int n_scen,
                          int first_item, int first_entry)

@@ -21,6 +21,12 @@ int launch_stage2_f64(const DevPtrs &d, const StepParams &p, const void *w_in, v
     if (d.fp64_fast) return launch_stage2_f64_fast(d, p, w_in, w_out, c, stream);
     return launch_stage<double, false>(d, p, 2, w_in, w_out, c, stream);
 }
+int launch_rk_unfused_f64(const DevPtrs &d, const StepParams &p, int part, const void *w_in, void *w_out, void *w1,
+                          void *R1, const LaunchCfg &c1, void *stream)
+{
+    if (d.fp64_fast) return launch_rk_unfused_f64_fast(d, p, part, w_in, w_out, w1, R1, c1, stream);
+    return launch_rk_unfused<double, false>(d, p, part, w_in, w_out, w1, R1, c1, stream);
+}
 size_t batch_mesh_bytes_f64() { return sizeof(BatchMesh<double>); }
 void fill_batch_mesh_f64(void *dst, const DevPtrs &d, const StepParams &p, const void *w_in, void *w_out, int n_scen,
                          int first_item, int first_entry)

@@ -15,6 +15,11 @@ int launch_stage2_f64_fast(const DevPtrs &d, const StepParams &p, const void *w_
 {
     return launch_stage<double, true>(d, p, 2, w_in, w_out, c, stream);
 }
+int launch_rk_unfused_f64_fast(const DevPtrs &d, const StepParams &p, int part, const void *w_in, void *w_out,
+                               void *w1, void *R1, const LaunchCfg &c1, void *stream)
+{
+    return launch_rk_unfused<double, true>(d, p, part, w_in, w_out, w1, R1, c1, stream);
+}
 int batch_config_f64_fast(int block, int max_halo, int max_ring1, int &grid, size_t &smem)
 {
     return batch_config<double, true>(block, max_halo, max_ring1, grid, smem);

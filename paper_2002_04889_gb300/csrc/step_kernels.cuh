@@ -80,6 +80,7 @@ struct KArgs {
     DevScalars *sc;
     real g, half_g, hthr;
     double cfl, dt_fixed, dt_max, t_end;
+    int cfl_min;            // stage 1: 1 adds the CFL bound to the step's minimum
 };
 
 __device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
@@ -264,6 +265,12 @@ __device__ __forceinline__ float g32_len(const float *geo, int k, int f)
     return geo[(size_t)k * G32 + (f == 0 ? 7 : 13 + f)];
 }
 
+// L1 prefetch (a hint: nothing waits for it and it holds no register).
+__device__ __forceinline__ void prefetch_l1(const void *ptr)
+{
+    asm volatile("prefetch.global.L1 [%0];" :: "l"(ptr));
+}
+
 // Stored state of cell gid as seen by the stage (H or eta first, then Hu, Hv):
 // stage 1 reads w^n; stage 2 forms w1 = w^n + dt R0 and applies the dry fix
 // (negative depth emptied; at or below the threshold, momentum zeroed).
@@ -410,6 +417,31 @@ __device__ __forceinline__ void st4(double *p, double x, double y, double z, dou
     reinterpret_cast<double2 *>(p)[1] = make_double2(z, w);
 }
 
+// SSP-RK(2,2) second stage (Sec. 2.3) of one cell: w^{n+1} = w^n / 2 + (w1 + dt R(w1)) / 2
+// from w^n = x, w1 = (W1, Hu1, Hv1) and R(w1) = (RH, RHu, RHv), then the dry fix.
+// Returns the fix's branch: 0 none, 1 momentum cut (depth at or below the
+// threshold), 2 negative depth emptied.
+template <typename real>
+__device__ __forceinline__ uint8_t rk2_final(const real x[3], real W1, real Hu1, real Hv1, real RH, real RHu,
+                                             real RHv, real dt, real z1, real hthr, real &W, real &Hu, real &Hv)
+{
+    constexpr bool ETA = EtaForm<real>::value;
+    W = real(0.5) * x[0] + real(0.5) * (W1 + dt * RH);
+    Hu = real(0.5) * x[1] + real(0.5) * (Hu1 + dt * RHu);
+    Hv = real(0.5) * x[2] + real(0.5) * (Hv1 + dt * RHv);
+    const real H = ETA ? W - z1 : W;
+    if (H < real(0)) {
+        W = ETA ? z1 : real(0);
+        Hu = real(0); Hv = real(0);
+        return 2;
+    }
+    if (H <= hthr) {
+        Hu = real(0); Hv = real(0);
+        return 1;
+    }
+    return 0;
+}
+
 // Phase D's end for block cell l (global gid), from the sums of its three face
 // terms: R = -(aH, aHu, aHv) / |K|; stage 1 writes R0 and the CFL bound of
 // am = max_f l_f a_f; stage 2 forms w^{n+1} = w^n / 2 + (w1 + dt R) / 2 with
@@ -441,20 +473,9 @@ __device__ __forceinline__ void finish_cell(const KArgs<real> &a, int gid, const
         }
         real W1, Hu1, Hv1, z1;
         ld4(sWl, W1, Hu1, Hv1, z1);
-        real W = real(0.5) * x[0] + real(0.5) * (W1 + dt * RH);
-        real Hu = real(0.5) * x[1] + real(0.5) * (Hu1 + dt * RHu);
-        real Hv = real(0.5) * x[2] + real(0.5) * (Hv1 + dt * RHv);
-        real H = ETA ? W - z1 : W;
-        uint8_t branch = 0;
-        if (H < real(0)) {
-            my_neg++;
-            W = ETA ? z1 : real(0);
-            Hu = real(0); Hv = real(0);
-            branch = 2;
-        } else if (H <= a.hthr) {
-            Hu = real(0); Hv = real(0);
-            branch = 1;
-        }
+        real W, Hu, Hv;
+        const uint8_t branch = rk2_final(x, W1, Hu1, Hv1, RH, RHu, RHv, dt, z1, a.hthr, W, Hu, Hv);
+        if (branch == 2) my_neg++;
         if (a.mask2) a.mask2[gid] = branch;
         if (!isfinite(W) || !isfinite(Hu) || !isfinite(Hv)) bad = true;
         a.wout[gid] = W;
@@ -557,6 +578,15 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             }
             real W, Hu, Hv, zc;
             bool neg = stage_cell<real, STAGE>(a, gid, dt, W, Hu, Hv, zc);
+            if constexpr (ETA) {
+                // a wet cell may reconstruct: phase B reads its geometry record and
+                // face beds right after the barrier below, so start bringing them
+                // into L1 (a dry cell reads neither)
+                if (W - zc > hthr) {
+                    prefetch_l1(g32(geo, gid));
+                    prefetch_l1(reinterpret_cast<const float2 *>(a.zf) + gid);
+                }
+            }
             if (neg) my_neg++;
             st4(sW + 4 * tid, W, Hu, Hv, zc);
             if constexpr (GIDS) sGid[tid] = gid;
@@ -565,6 +595,13 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         if (gh >= 0) {
             real W, Hu, Hv, zc;
             stage_cell<real, STAGE>(a, gh, dt, W, Hu, Hv, zc);
+            if constexpr (ETA) {
+                if (tid < n1 && W - zc > hthr) {     // a wet ring-1 cell: phase B reconstructs it too
+                    prefetch_l1(g32(geo, gh));
+                    prefetch_l1(reinterpret_cast<const float2 *>(a.zf) + gh);
+                    prefetch_l1(a.ring1_nbr + 3 * (h0 + tid));
+                }
+            }
             st4(sW + 4 * (B + tid), W, Hu, Hv, zc);
             if (tid < n1) {
                 if constexpr (GIDS) sGid[B + tid] = gh;
@@ -956,10 +993,83 @@ __global__ void __launch_bounds__(MAXT, StageMinCtas<real, MAXT>::value) stage_k
             neg += red_neg[w];
             if (STAGE == 1) mn = vmin(mn, red_min[w]);
         }
-        if (STAGE == 1 && mn < real_inf<real>()) atomicMin(&a.sc->dtmin_bits, min_bits(mn));
+        if (STAGE == 1 && a.cfl_min && mn < real_inf<real>()) atomicMin(&a.sc->dtmin_bits, min_bits(mn));
         if (neg) atomicAdd((unsigned long long *)&a.sc->neg_count, (unsigned long long)neg);
         if (bad) atomicOr(&a.sc->flags, FLAG_NONFINITE_STATE);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Unfused SSP-RK(2,2) (Sec. 2.3; vg_params.rk_unfused): the two stage updates as
+// kernels of their own, with w1 and R(w1) in global memory, to compare with the
+// fused stage-2 kernel, which forms w1 = w^n + dt R0 as it loads a block and ends
+// with the second update.  Update 1 writes w1 with the dry fix; the stage-1
+// kernel, without its CFL bound, writes R(w1); update 2 writes w^{n+1}.  The
+// arithmetic of each cell is the fused path's (stage_cell, rk2_final).
+// 256 threads, grid-stride over the cells; one atomic per CTA for the counts.
+template <typename real>
+__device__ __forceinline__ void cta_counts(long long my_neg, bool bad, DevScalars *sc)
+{
+    __shared__ long long red[8];
+    __shared__ int any_bad;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) any_bad = 0;
+    for (int o = 16; o > 0; o >>= 1) my_neg += __shfl_xor_sync(0xffffffffu, my_neg, o);
+    if (lane == 0) red[warp] = my_neg;
+    __syncthreads();
+    if (bad) any_bad = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long n = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) n += red[w];
+        if (n) atomicAdd((unsigned long long *)&sc->neg_count, (unsigned long long)n);
+        if (any_bad) atomicOr(&sc->flags, FLAG_NONFINITE_STATE);
+    }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) rk_update1_kernel(const KArgs<real> a, real *w1)
+{
+    if (a.t_end > 0.0 && a.sc->t >= a.t_end) return;     // finished: update 2 copies w^n
+    const real dt = (real)step_dt<real>(a.sc, a.cfl, a.dt_fixed, a.dt_max, a.t_end);
+    const int64_t nc = a.nc;
+    long long my_neg = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc; i += (int64_t)gridDim.x * blockDim.x) {
+        const int gid = (int)i;
+        real W, Hu, Hv, zc;
+        if (stage_cell<real, 2>(a, gid, dt, W, Hu, Hv, zc)) my_neg++;
+        w1[gid] = W;
+        w1[nc + gid] = Hu;
+        w1[2 * nc + gid] = Hv;
+    }
+    cta_counts<real>(my_neg, false, a.sc);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) rk_update2_kernel(const KArgs<real> a, const real *w1, const real *R1)
+{
+    const int64_t nc = a.nc;
+    if (a.t_end > 0.0 && a.sc->t >= a.t_end) {           // as the fused kernel: w^n, bit for bit
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * nc; i += (int64_t)gridDim.x * blockDim.x)
+            a.wout[i] = a.w[i];
+        return;
+    }
+    const real dt = (real)step_dt<real>(a.sc, a.cfl, a.dt_fixed, a.dt_max, a.t_end);
+    long long my_neg = 0;
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc; i += (int64_t)gridDim.x * blockDim.x) {
+        const int gid = (int)i;
+        const real x[3] = {a.w[gid], a.w[nc + gid], a.w[2 * nc + gid]};
+        real W, Hu, Hv;
+        const uint8_t branch = rk2_final(x, w1[gid], w1[nc + gid], w1[2 * nc + gid], R1[gid], R1[nc + gid],
+                                         R1[2 * nc + gid], dt, a.z[gid], a.hthr, W, Hu, Hv);
+        if (branch == 2) my_neg++;
+        if (!isfinite(W) || !isfinite(Hu) || !isfinite(Hv)) bad = true;
+        a.wout[gid] = W;
+        a.wout[nc + gid] = Hu;
+        a.wout[2 * nc + gid] = Hv;
+    }
+    cta_counts<real>(my_neg, bad, a.sc);
 }
 
 // ---------------------------------------------------------------------------
@@ -1157,6 +1267,7 @@ KArgs<real> make_args(const DevPtrs &d, const StepParams &p, const void *w_in, v
     a.dt_fixed = p.dt_fixed;
     a.dt_max = p.dt_max;
     a.t_end = p.t_end;
+    a.cfl_min = 1;
     return a;
 }
 
@@ -1203,6 +1314,49 @@ int stage_config(const DevPtrs &d, int stage, LaunchCfg &cfg)
     if (grid > d.nblocks) grid = d.nblocks;
     cfg.grid = (int)(grid < 1 ? 1 : grid);
     return 0;
+}
+
+template <typename real, bool FAST = false>
+int launch_stage_args(const KArgs<real> &a, int threads, int stage, const LaunchCfg &c, cudaStream_t s)
+{
+    const int t = threads;
+    if (t <= 256) {
+        if (stage == 1) stage_kernel<real, 1, 256, FAST><<<c.grid, t, c.smem, s>>>(a);
+        else stage_kernel<real, 2, 256, FAST><<<c.grid, t, c.smem, s>>>(a);
+    } else if (t <= 384) {
+        if (stage == 1) stage_kernel<real, 1, 384, FAST><<<c.grid, t, c.smem, s>>>(a);
+        else stage_kernel<real, 2, 384, FAST><<<c.grid, t, c.smem, s>>>(a);
+    } else {
+        if (stage == 1) stage_kernel<real, 1, 512, FAST><<<c.grid, t, c.smem, s>>>(a);
+        else stage_kernel<real, 2, 512, FAST><<<c.grid, t, c.smem, s>>>(a);
+    }
+    return (int)cudaGetLastError();
+}
+
+// The unfused step's three launches after stage 1 (part 0: update 1; 1: the
+// stage-1 kernel on w1 writing R(w1) to R1, without its CFL bound; 2: update 2).
+// w1 and R1 are [3][nc] buffers of the context.
+template <typename real, bool FAST = false>
+int launch_rk_unfused(const DevPtrs &d, const StepParams &p, int part, const void *w_in, void *w_out, void *w1,
+                      void *R1, const LaunchCfg &c1, void *stream)
+{
+    KArgs<real> a = make_args<real>(d, p, w_in, w_out);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (part == 1) {
+        a.w = static_cast<const real *>(w1);
+        a.R0 = static_cast<real *>(R1);
+        a.wout = nullptr;
+        a.cfl_min = 0;
+        return launch_stage_args<real, FAST>(a, d.threads, 1, c1, s);
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = (d.nc + 255) / 256, cap = 8LL * (sms > 0 ? sms : 1);
+    const int grid = (int)(want < 1 ? 1 : want < cap ? want : cap);
+    if (part == 0) rk_update1_kernel<real><<<grid, 256, 0, s>>>(a, static_cast<real *>(w1));
+    else rk_update2_kernel<real><<<grid, 256, 0, s>>>(a, static_cast<const real *>(w1), static_cast<const real *>(R1));
+    return (int)cudaGetLastError();
 }
 
 template <typename real, bool FAST = false>

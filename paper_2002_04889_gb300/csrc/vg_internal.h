@@ -152,6 +152,16 @@ int launch_stage1_f32(const DevPtrs &d, const StepParams &p, const void *w_in, c
 int launch_stage2_f32(const DevPtrs &d, const StepParams &p, const void *w_in, void *w_out, const LaunchCfg &c, void *stream);
 int launch_stage1_f64(const DevPtrs &d, const StepParams &p, const void *w_in, const LaunchCfg &c, void *stream);
 int launch_stage2_f64(const DevPtrs &d, const StepParams &p, const void *w_in, void *w_out, const LaunchCfg &c, void *stream);
+// Unfused RK stages (vg_params.rk_unfused), after stage 1: part 0 writes
+// w1 = w^n + dt R0 (dry fix) to w1, part 1 runs the stage-1 kernel on w1 into R1
+// without its CFL bound (c1: stage 1's launch configuration), part 2 writes
+// w^{n+1} = w^n / 2 + (w1 + dt R1) / 2 (dry fix) to w_out.
+int launch_rk_unfused_f32(const DevPtrs &d, const StepParams &p, int part, const void *w_in, void *w_out, void *w1,
+                          void *R1, const LaunchCfg &c1, void *stream);
+int launch_rk_unfused_f64(const DevPtrs &d, const StepParams &p, int part, const void *w_in, void *w_out, void *w1,
+                          void *R1, const LaunchCfg &c1, void *stream);
+int launch_rk_unfused_f64_fast(const DevPtrs &d, const StepParams &p, int part, const void *w_in, void *w_out,
+                               void *w1, void *R1, const LaunchCfg &c1, void *stream);
 
 // The contracted FP64 build (step_f64_fast.cu); the *_f64 entry points above
 // dispatch to it when DevPtrs::fp64_fast / StepParams::fp64_fast is set.

@@ -41,7 +41,8 @@ class vg_params(C.Structure):
                 ("dt_fixed", C.c_double), ("dt_max", C.c_double), ("t_end", C.c_double),
                 ("order", C.c_int32), ("gauge_every", C.c_int32),
                 ("strict_positivity", C.c_int32), ("block_cells", C.c_int32),
-                ("block_threads", C.c_int32), ("fp64_literal", C.c_int32)]
+                ("block_threads", C.c_int32), ("fp64_literal", C.c_int32),
+                ("rk_unfused", C.c_int32)]
 
 
 class vg_diag(C.Structure):

@@ -2,10 +2,10 @@
 
 Tolerances: FP64 within 1e-10 relative L2 per field, FP32 within 1e-4 relative
 L2 of the FP64 oracle per field (both after 100 steps on the Thacker basin).
-FP64 runs the contracted build by default (multiply-adds fused, fewer
-divisions): rounding differences only.  With fp64_literal = 1 the kernels are
-built without contraction and evaluate every formula in the oracle's order, and
-the result equals the oracle's bit for bit (tested).
+FP64 runs the literal build by default (fp64_literal = 1: no multiply-add
+contraction, every formula in the oracle's order), whose result equals the
+oracle's bit for bit (tested); the contracted build (fp64_literal = 0) differs
+by rounding only and is held to the 1e-10 tolerance.
 """
 import math
 
