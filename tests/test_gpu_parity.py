@@ -271,13 +271,10 @@ def test_advance_to_and_graph_replay_consistency(thacker):
         assert a.diagnostics()["t"] == pytest.approx(0.2, abs=1e-15)
 
 
-@pytest.mark.slow
-@pytest.mark.parametrize("precision", [32, 64])
-def test_full_size_40m_sampled(precision):
-    """The 40M-triangle workload in the benchmark's launch configuration (Hilbert
-    renumbering, 256-cell blocks): one step on the GPU; 48 sampled cells checked
-    against the oracle run on their 4-ring patches with the GPU's time step, the
-    time step checked against the sampled CFL bounds, and mass conservation."""
+@pytest.fixture(scope="module")
+def big40m():
+    """The 40M-triangle Thacker workload of the benchmark, its initial state, 48
+    sampled cells (32 wet, 16 in the shoreline band) and the vertex adjacency."""
     m = I.thacker_large_mesh()
     s = I.thacker_initial_state(m)
     rng = np.random.default_rng(11)
@@ -287,6 +284,55 @@ def test_full_size_40m_sampled(precision):
     shore_pool = np.nonzero((r2 > 0.75) & (r2 < 0.85))[0]
     samples = np.concatenate([rng.choice(wet_pool, 32, replace=False),
                               rng.choice(shore_pool, 16, replace=False)])
+    return m, s, samples, VertexAdjacency(m.tri, m.nv)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", [32, 64])
+def test_full_size_40m_sampled_10_steps(big40m, precision):
+    """The 40M-triangle workload in the benchmark's launch configuration (Hilbert
+    renumbering, 256-cell blocks, persistent CTAs walking many blocks) for 10
+    steps of a fixed time step (0.8 of the initial CFL step, so that both sides
+    take the same steps): each sampled cell against the oracle run on the cells
+    within 40 vertex rings of it, which hold everything 10 steps can reach (a
+    step reaches 4 face rings: two stages of a two-ring stencil)."""
+    m, s, samples, adj = big40m
+    n_steps = 10
+    with volna.Solver(precision) as sv:
+        sv.upload_mesh(m, renumber="hilbert")
+        sv.set_params(h_threshold=1e-5, cfl=0.9)
+        sv.set_state(s.H, s.Hu, s.Hv)
+        sv.step(1)
+        dt = 0.8 * sv.diagnostics()["last_dt"]
+        sv.set_params(h_threshold=1e-5, cfl=0.9, dt_fixed=dt)
+        sv.set_state(s.H, s.Hu, s.Hv)
+        sv.step(n_steps)
+        d = sv.diagnostics()
+        H, Hu, Hv, t = sv.get_state()
+    assert t == pytest.approx(n_steps * dt, rel=1e-12) and d["neg_count"] == 0
+    tol = 1e-12 if precision == 64 else 1e-4
+    worst = 0.0
+    for k in samples:
+        cells = adj.rings([k], 4 * n_steps)
+        centre = int(np.searchsorted(cells, k))
+        om = O.OracleMesh.from_mesh(patch_mesh(m, cells))
+        r = om.run(O.params(h_threshold=1e-5, dt_fixed=dt), (s.H[cells], s.Hu[cells], s.Hv[cells], 0.0), n_steps)
+        scale = max(float(np.abs(s.H[cells]).max()), 1e-3)
+        for f, gv in (("H", H), ("Hu", Hu), ("Hv", Hv)):
+            err = abs(gv[k] - r[f][centre]) / scale
+            worst = max(worst, err)
+            assert err <= tol, (k, f, gv[k], r[f][centre])
+    print(f"40M, {n_steps} fixed steps, FP{precision}: largest sampled error / local depth scale {worst:.3e}")
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", [32, 64])
+def test_full_size_40m_sampled(big40m, precision):
+    """The 40M-triangle workload in the benchmark's launch configuration (Hilbert
+    renumbering, 256-cell blocks): one step on the GPU; 48 sampled cells checked
+    against the oracle run on their 4-ring patches with the GPU's time step, the
+    time step checked against the sampled CFL bounds, and mass conservation."""
+    m, s, samples, adj = big40m
     with volna.Solver(precision) as sv:
         sv.upload_mesh(m, renumber="hilbert")
         sv.set_params(h_threshold=1e-5, cfl=0.9)
@@ -299,7 +345,6 @@ def test_full_size_40m_sampled(precision):
     assert dt > 0 and t == pytest.approx(dt)
     assert abs(d1["mass"] - d0["mass"]) / d0["mass"] < (1e-13 if precision == 64 else 1e-5)
     tol = 1e-12 if precision == 64 else 1e-4
-    adj = VertexAdjacency(m.tri, m.nv)
     for k in samples:
         cells = adj.rings([k], 4)
         pm = patch_mesh(m, cells)
