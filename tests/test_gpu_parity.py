@@ -327,6 +327,53 @@ def test_full_size_40m_sampled_10_steps(big40m, precision):
 
 @pytest.mark.slow
 @pytest.mark.parametrize("precision", [32, 64])
+def test_full_size_coast_5m_sampled_10_steps(precision):
+    """The 5M-triangle ocean-to-coast basin of the benchmark (graded 20:1, dry land,
+    N-wave uplift, H_threshold 1e-3 m) in its launch configuration for 10 fixed steps:
+    sampled cells in the uplift, on the shoreline, in the open ocean and on dry
+    land against the oracle on their 40-ring patches.  Errors are taken per field
+    against that field's largest magnitude over the whole basin (the scale of the
+    relative L2 tolerance; near the shore the momentum is round-off noise)."""
+    m = I.coast_mesh()
+    s = I.coast_initial_state(m)
+    h = m.vertex_mean(m.depth)
+    xi = np.abs(s.H - np.where(h > 0, h, 0.0))
+    rng = np.random.default_rng(5)
+    pools = [np.nonzero(xi > 0.5)[0],                            # in the uplift
+             np.nonzero((s.H > 0) & (s.H < 5.0))[0],             # shoreline water
+             np.nonzero(s.H > 1000.0)[0],                        # open ocean
+             np.nonzero((s.H == 0) & (h > -5.0))[0]]             # dry land by the shore
+    samples = np.concatenate([rng.choice(pl, 8, replace=False) for pl in pools])
+    n_steps = 10
+    with volna.Solver(precision) as sv:
+        sv.upload_mesh(m, renumber="hilbert")
+        sv.set_params(h_threshold=1e-3, cfl=0.9)
+        sv.set_state(s.H, s.Hu, s.Hv)
+        sv.step(1)
+        dt = 0.8 * sv.diagnostics()["last_dt"]
+        sv.set_params(h_threshold=1e-3, cfl=0.9, dt_fixed=dt)
+        sv.set_state(s.H, s.Hu, s.Hv)
+        sv.step(n_steps)
+        H, Hu, Hv, t = sv.get_state()
+    tol = 1e-12 if precision == 64 else 1e-4
+    scales = {f: float(np.abs(v).max()) for f, v in (("H", H), ("Hu", Hu), ("Hv", Hv))}
+    adj = VertexAdjacency(m.tri, m.nv)
+    worst = 0.0
+    for k in samples:
+        cells = adj.rings([k], 4 * n_steps)
+        centre = int(np.searchsorted(cells, k))
+        om = O.OracleMesh.from_mesh(patch_mesh(m, cells))
+        r = om.run(O.params(h_threshold=1e-3, dt_fixed=dt), (s.H[cells], s.Hu[cells], s.Hv[cells], 0.0), n_steps)
+        for f, gv in (("H", H), ("Hu", Hu), ("Hv", Hv)):
+            scale = scales[f]
+            err = abs(gv[k] - r[f][centre]) / scale
+            worst = max(worst, err)
+            assert err <= tol, (k, f, gv[k], r[f][centre], scale)
+    print(f"coast 5M, {n_steps} fixed steps, FP{precision}: largest sampled error / field scale {worst:.3e}")
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", [32, 64])
 def test_full_size_40m_sampled(big40m, precision):
     """The 40M-triangle workload in the benchmark's launch configuration (Hilbert
     renumbering, 256-cell blocks): one step on the GPU; 48 sampled cells checked
