@@ -369,8 +369,9 @@ def batched_leg(torch, stream, steps: int, n_scen: int = 32, renumber: str = "hi
 
 def adjoint_leg(torch, stream, steps: int, n: int = 707, slots: int = 16):
     """Config 5 mesh (Thacker basin, n x n squares, 2 n^2 triangles), FP64: the cost of
-    the gradient of a 16-gauge misfit (forward with sqrt(N) checkpoints + reverse
-    sweep) against the plain forward run of the same steps."""
+    the gradient of a 16-gauge misfit (forward with checkpoints every C steps, C the
+    library's memory-balanced default, + reverse sweep recomputing each segment
+    once) against the plain forward run of the same steps."""
     import numpy as np
     from paper_2002_04889_gb300 import inputs as I
     from paper_2002_04889_gb300 import volna
@@ -416,15 +417,17 @@ def adjoint_leg(torch, stream, steps: int, n: int = 707, slots: int = 16):
         sv.adj_backward(np.full_like(eta, 1e-3), m.nv)
         t4 = time.perf_counter()
     sv.close()
-    C = math.ceil(math.sqrt(steps))
-    rec = 24 + 24 + 144 + 1 + 2                 # per step held: state, R0, face values (2 stages), mask,
-                                                # reconstruction flags (2 stages)
+    # per cell and recorded step: state, R0, face values of both stages, one bit
+    # of dry-fix branch and two of reconstruction flags; per checkpoint: the state
+    rec = 24 + 24 + 144 + 3 / 8
+    C = max(1, round(math.sqrt(steps * 24 / rec)))     # the library's default segment length
     return {"workload": f"Thacker basin {m.nc} triangles, FP64, {steps} steps, 16 gauges",
             "forward_s": round(t_fwd, 4), "forward_contracted_s": round(t_fwd_fast, 4),
             "adj_forward_s": round(t1 - t0, 4),
             "adj_backward_s": round(t2 - t1, 4), "cost_vs_forward": round((t2 - t0) / t_fwd, 3),
             "forward_value": m.nc * steps / t_fwd, "unit": UNIT,
-            "scratch_bytes_per_cell_sqrtN": math.ceil(steps / C) * 24 + C * rec,
+            "segment_steps": C,
+            "scratch_bytes_per_cell": round(math.ceil(steps / C) * 24 + C * rec),
             "binomial": None if slots <= 0 else {"slots": slots, "cost_vs_forward": round((t4 - t3) / t_fwd, 3),
                                                  "scratch_bytes_per_cell": (slots + 3) * 24 + rec}}
 

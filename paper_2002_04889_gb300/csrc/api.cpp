@@ -1245,7 +1245,13 @@ int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_eve
     if (c->n_gauges < 1) return fail(c, VG_ESTATE, "the adjoint differentiates gauge records: set gauges first");
     DeviceGuard guard(c->device);
     free_adjoint(c);
-    int64_t C = checkpoint_every ? checkpoint_every : (int64_t)std::ceil(std::sqrt((double)n_steps));
+    // default segment length: the one that minimises device memory, C checkpoints'
+    // worth of recordings (per cell: face values of both stages, the segment state,
+    // R0, R1 with CFL steps, flag bits) plus n_steps / C checkpoints of 24 bytes
+    // each; every segment is recomputed once whatever C is
+    const double rec_bytes = 8.0 * (18 + 3 + 3 + (dt > 0.0 ? 0 : 3)) + 3.0 / 8.0, ckpt_bytes = 24.0;
+    int64_t C = checkpoint_every ? checkpoint_every
+                                 : std::max<int64_t>(1, std::llround(std::sqrt((double)n_steps * ckpt_bytes / rec_bytes)));
     int64_t nck = (n_steps + C - 1) / C;
     size_t bytes = 8 * 3 * (size_t)c->hm.nc;
     for (int64_t k = 0; k < nck; k++) {
