@@ -235,7 +235,9 @@ int vg_get_diagnostics(vg_ctx *ctx, vg_diag *d);
  * kernel (no graph) with CUDA events around each launch on the context
  * stream, and accumulate device time per kernel.  vg_get_profile returns, for
  * up to n kernels, their names (static strings), launch counts and total
- * milliseconds; *n_out receives the number of kernels timed.
+ * milliseconds; *n_out receives the number of kernels timed: "stage1",
+ * "stage2", "post_step", "bed_update", and with rk_unfused "rk_update1",
+ * "residual_w1", "rk_update2" (in that order; a kernel never launched has 0).
  */
 int vg_profile(vg_ctx *ctx, int enable);
 int vg_get_profile(vg_ctx *ctx, int32_t n, const char **names, int64_t *launches, double *ms,
