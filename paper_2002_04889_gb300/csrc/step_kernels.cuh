@@ -92,6 +92,36 @@ __device__ __forceinline__ double vabs(double a) { return fabs(a); }
 __device__ __forceinline__ float vsqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ double vsqrt(double a) { return sqrt(a); }
 
+// Compare and select.  GB300 runs FP64 compares and min/max on its FP64 units,
+// which issue two lane-operations per SM and cycle, while its integer units are
+// idle in the FP64 kernels; so the FP64 forms below work on the IEEE bit patterns
+// with integer instructions.  For the non-NaN values of the step they decide and
+// select exactly as the FP64 instructions do (a zero result may carry the other
+// sign, which no later operation of the step distinguishes).  The FP32 forms are
+// the plain FP32 instructions.
+//   gt_nn(x, y): x > y for y >= +0;  is_zero(x): x == 0;  is_neg(x): x < 0;
+//   is_pos(x): x > 0;  smax / smin: max / min;  max0(x): max(0, x).
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ long long okey(double x)   // order-preserving for every non-NaN x
+{
+    const long long b = dbits(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool gt_nn(float x, float y) { return x > y; }
+__device__ __forceinline__ bool gt_nn(double x, double y) { return dbits(x) > dbits(y); }
+__device__ __forceinline__ bool is_zero(float x) { return x == 0.f; }
+__device__ __forceinline__ bool is_zero(double x) { return (dbits(x) << 1) == 0; }
+__device__ __forceinline__ bool is_neg(float x) { return x < 0.f; }
+__device__ __forceinline__ bool is_neg(double x) { return dbits(x) < 0 && (dbits(x) << 1) != 0; }
+__device__ __forceinline__ bool is_pos(float x) { return x > 0.f; }
+__device__ __forceinline__ bool is_pos(double x) { return dbits(x) > 0; }
+__device__ __forceinline__ float smax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double smax(double a, double b) { return okey(a) < okey(b) ? b : a; }
+__device__ __forceinline__ float smin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double smin(double a, double b) { return okey(b) < okey(a) ? b : a; }
+__device__ __forceinline__ float max0(float x) { return fmaxf(0.f, x); }
+__device__ __forceinline__ double max0(double x) { return dbits(x) > 0 ? x : 0.0; }
+
 template <typename real> __device__ __forceinline__ real real_inf();
 template <> __device__ __forceinline__ float real_inf<float>() { return CUDART_INF_F; }
 template <> __device__ __forceinline__ double real_inf<double>() { return CUDART_INF; }
@@ -130,7 +160,7 @@ template <typename real, bool FAST = false>
 __device__ __forceinline__ void hll_normal(real g, real half_g, real HL, real unL, real utL,
                                            real HR, real unR, real utR, real F[3], real &amax)
 {
-    if (HL == real(0) && HR == real(0)) {
+    if (is_zero(HL) && is_zero(HR)) {
         F[0] = real(0); F[1] = real(0); F[2] = real(0);
         amax = real(0);
         return;
@@ -138,24 +168,24 @@ __device__ __forceinline__ void hll_normal(real g, real half_g, real HL, real un
     real cL = vsqrt(g * HL);
     real cR = vsqrt(g * HR);
     real sL, sR;
-    if (HL == real(0)) {
+    if (is_zero(HL)) {
         sL = unR - real(2) * cR;
         sR = unR + cR;
-    } else if (HR == real(0)) {
+    } else if (is_zero(HR)) {
         sL = unL - cL;
         sR = unL + real(2) * cL;
     } else {
         real us = real(0.5) * (unL + unR) + (cL - cR);
         real cs = real(0.5) * (cL + cR) - real(0.25) * (unR - unL);
-        sL = vmin(unL - cL, us - cs);
-        sR = vmax(us + cs, unR + cR);
+        sL = smin(unL - cL, us - cs);
+        sR = smax(us + cs, unR + cR);
     }
     real qL = HL * unL, qR = HR * unR;
     real FL0 = qL, FL1 = qL * unL + half_g * HL * HL, FL2 = qL * utL;
     real FR0 = qR, FR1 = qR * unR + half_g * HR * HR, FR2 = qR * utR;
-    if (sL >= real(0)) {
+    if (!is_neg(sL)) {
         F[0] = FL0; F[1] = FL1; F[2] = FL2;
-    } else if (sR >= real(0)) {
+    } else if (!is_neg(sR)) {
         real den = sR - sL;
         real sLR = sL * sR;
         if constexpr (FAST) {
@@ -171,7 +201,7 @@ __device__ __forceinline__ void hll_normal(real g, real half_g, real HL, real un
     } else {
         F[0] = FR0; F[1] = FR1; F[2] = FR2;
     }
-    amax = vmax(vabs(sL), vabs(sR));
+    amax = smax(vabs(sL), vabs(sR));
 }
 
 // Flux through a face seen from its left cell: face velocities, hydrostatic
@@ -188,7 +218,7 @@ __device__ __forceinline__ void face_flux(real g, real half_g, real hthr,
                                           real Phi[3], real &PL, real &PR, real &amax)
 {
     real uL = real(0), vL = real(0);
-    if (HfL > hthr) {
+    if (gt_nn(HfL, hthr)) {
         if constexpr (FAST) {
             const real r = real(1) / HfL;
             uL = HufL * r; vL = HvfL * r;
@@ -200,14 +230,14 @@ __device__ __forceinline__ void face_flux(real g, real half_g, real hthr,
     real utL = -uL * ny + vL * nx;
     real HsL, HsR, unR, utR;
     if (bnd) {
-        HsL = vmax(real(0), (HfL + zL) - zL);
+        HsL = max0((HfL + zL) - zL);
         HsR = HsL;
         unR = bnd == 2 ? unL : -unL;
         utR = utL;
         HfR = HfL;
     } else {
         real uR = real(0), vR = real(0);
-        if (HfR > hthr) {
+        if (gt_nn(HfR, hthr)) {
             if constexpr (FAST) {
                 const real r = real(1) / HfR;
                 uR = HufR * r; vR = HvfR * r;
@@ -217,9 +247,9 @@ __device__ __forceinline__ void face_flux(real g, real half_g, real hthr,
         }
         unR = uR * nx + vR * ny;
         utR = -uR * ny + vR * nx;
-        real zs = vmax(zL, zR);
-        HsL = vmax(real(0), (HfL + zL) - zs);
-        HsR = vmax(real(0), (HfR + zR) - zs);
+        real zs = smax(zL, zR);
+        HsL = max0((HfL + zL) - zs);
+        HsR = max0((HfR + zR) - zs);
     }
     real F[3];
     hll_normal<real, FAST>(g, half_g, HsL, unL, utL, HsR, unR, utR, F, amax);
@@ -290,12 +320,12 @@ __device__ __forceinline__ bool stage_state(const KArgs<real> &a, int gid, real 
     Hu = Hu + dt * a.R0[nc + gid];
     Hv = Hv + dt * a.R0[2 * nc + gid];
     real H = ETA ? W - zc : W;
-    if (H < real(0)) {
+    if (is_neg(H)) {
         W = ETA ? zc : real(0);
         Hu = real(0); Hv = real(0);
         return true;
     }
-    if (H <= a.hthr) { Hu = real(0); Hv = real(0); }
+    if (!gt_nn(H, a.hthr)) { Hu = real(0); Hv = real(0); }
     return false;
 }
 
@@ -383,7 +413,7 @@ template <typename real>
 __device__ __forceinline__ bool exactly_dry(real W, real Hu, real Hv, real zc)
 {
     const real H = EtaForm<real>::value ? W - zc : W;
-    return H == real(0) && Hu == real(0) && Hv == real(0);
+    return is_zero(H) && is_zero(Hu) && is_zero(Hv);
 }
 
 // Stored state of cell gid as seen by the stage, and its bed.
@@ -430,12 +460,12 @@ __device__ __forceinline__ uint8_t rk2_final(const real x[3], real W1, real Hu1,
     Hu = real(0.5) * x[1] + real(0.5) * (Hu1 + dt * RHu);
     Hv = real(0.5) * x[2] + real(0.5) * (Hv1 + dt * RHv);
     const real H = ETA ? W - z1 : W;
-    if (H < real(0)) {
+    if (is_neg(H)) {
         W = ETA ? z1 : real(0);
         Hu = real(0); Hv = real(0);
         return 2;
     }
-    if (H <= hthr) {
+    if (!gt_nn(H, hthr)) {
         Hu = real(0); Hv = real(0);
         return 1;
     }
@@ -464,7 +494,7 @@ __device__ __forceinline__ void finish_cell(const KArgs<real> &a, int gid, const
         a.R0[gid] = RH;
         a.R0[nc + gid] = RHu;
         a.R0[2 * nc + gid] = RHv;
-        if (am > real(0)) my_min = vmin(my_min, area / (real(3) * am));
+        if (is_pos(am)) my_min = smin(my_min, area / (real(3) * am));
     } else {
         if (a.r1_out) {
             a.r1_out[gid] = RH;
@@ -688,7 +718,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         const real HK = ETA ? WK - zK : WK;
         real qK[3] = {ETA ? WK : HK + zK, HuK, HvK};
         real qn[3][3];
-        bool recon = (a.order == 2) && (HK > hthr);
+        bool recon = (a.order == 2) && gt_nn(HK, hthr);
 #pragma unroll
         for (int f = 0; f < 3; f++) {
             uint16_t code;
@@ -707,7 +737,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
                 qn[f][0] = ETA ? Wj : Hj + zj;
                 qn[f][1] = Huj;
                 qn[f][2] = Hvj;
-                if (!(Hj > hthr)) recon = false;
+                if (!gt_nn(Hj, hthr)) recon = false;
             } else if (code == NBR_OPEN) {
                 // transmissive ghost: the cell's own values
                 qn[f][0] = qK[0];
@@ -764,8 +794,8 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
                 real qmax = qK[v], qmin = qK[v];
 #pragma unroll
                 for (int f = 0; f < 3; f++) {
-                    qmax = vmax(qmax, qn[f][v]);
-                    qmin = vmin(qmin, qn[f][v]);
+                    qmax = smax(qmax, qn[f][v]);
+                    qmin = smin(qmin, qn[f][v]);
                 }
                 real alpha = real(1);
                 if constexpr (ETA) {
@@ -784,17 +814,17 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
 #pragma unroll
                     for (int f = 0; f < 3; f++) {
                         const real aD = vabs(D[f]);
-                        const real r = D[f] > real(0) ? up : dn;
-                        if (r * den < num * aD) { num = r; den = aD; }
+                        const real r = is_pos(D[f]) ? up : dn;
+                        if (gt_nn(num * aD, r * den)) { num = r; den = aD; }   // both products >= 0
                     }
                     if (num != den) alpha = num / den;
                 } else {
 #pragma unroll
                     for (int f = 0; f < 3; f++) {
                         real phi = real(1);
-                        if (D[f] > real(0)) phi = vmin(real(1), (qmax - qK[v]) / D[f]);
-                        else if (D[f] < real(0)) phi = vmin(real(1), (qmin - qK[v]) / D[f]);
-                        alpha = vmin(alpha, phi);
+                        if (is_pos(D[f])) phi = smin(real(1), (qmax - qK[v]) / D[f]);
+                        else if (is_neg(D[f])) phi = smin(real(1), (qmin - qK[v]) / D[f]);
+                        alpha = smin(alpha, phi);
                     }
                 }
 #pragma unroll
@@ -814,7 +844,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
 #pragma unroll
             for (int f = 0; f < 3; f++) {
                 Hf[f] = face[f][0] - zfK[f];
-                if (!(Hf[f] > hthr)) recon = false;
+                if (!gt_nn(Hf[f], hthr)) recon = false;
                 if (ETA) Hf[f] = face[f][0];      // FP32 keeps eta_f
                 Huf[f] = face[f][1];
                 Hvf[f] = face[f][2];
@@ -902,7 +932,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             aH = aH + t0;
             aHu = aHu + t1;
             aHv = aHv + t2;
-            if (STAGE == 1) am = vmax(am, x[f]);
+            if (STAGE == 1) am = smax(am, x[f]);
         }
         if constexpr (!ETA) {
             // centred bed-slope source of a cell standing on its face beds:
