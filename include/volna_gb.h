@@ -73,8 +73,7 @@ typedef struct vg_params {
     int32_t block_threads; /* threads per thread block of the step kernels: a
                               multiple of 32 from block_cells to 2 x block_cells
                               and at most 512 (the extra threads share the halo
-                              and face work); 0 = block_cells for FP32 and
-                              min(2 x block_cells, 512) for FP64                  */
+                              and face work); 0 = block_cells                  */
     int32_t fp64_literal;  /* FP64 contexts and batches: 1 evaluates every formula
                               as written, without multiply-add contraction, so
                               the result equals a plain FP64 implementation of

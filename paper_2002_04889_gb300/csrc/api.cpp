@@ -179,10 +179,10 @@ DevPtrs dev_ptrs(const vg_ctx *c)
     d.nc = c->hm.nc;
     d.block = c->hm.block;
     {
-        // default: one thread per block cell (FP32); FP64, bound by its arithmetic
-        // rate, gains from two threads per cell for the halo and face work
-        int t = c->prm.block_threads;
-        if (t == 0 && c->precision == 64) t = std::min(2 * c->hm.block, 512);
+        // default: one thread per block cell.  (FP64 with two threads per cell, one
+        // CTA of 512 threads per SM, was 5-8 % slower than two CTAs of 256 that
+        // take turns at the barriers.)
+        const int t = c->prm.block_threads;
         d.threads = (t >= c->hm.block && t <= 2 * c->hm.block && t <= 512) ? t : c->hm.block;
     }
     d.fp64_fast = c->precision == 64 && !c->prm.fp64_literal;

@@ -970,6 +970,13 @@ template <typename real, int MAXT> struct StageMinCtas { static constexpr int va
 template <> struct StageMinCtas<float, 256> { static constexpr int value = 6; };
 template <> struct StageMinCtas<float, 384> { static constexpr int value = 4; };
 template <> struct StageMinCtas<float, 512> { static constexpr int value = 3; };
+// FP64 with one thread per cell: two CTAs per SM, so that one CTA's phases run
+// while the other waits at a barrier (118-122 registers, no spills)
+template <> struct StageMinCtas<double, 256> { static constexpr int value = 2; };
+// The batched kernels' own budget (their extra scenario state needs the FP64
+// registers of one CTA per SM).
+template <typename real> struct BatchMinCtas { static constexpr int value = 1; };
+template <> struct BatchMinCtas<float> { static constexpr int value = 6; };
 
 template <typename real, int STAGE, int MAXT, bool FAST = false>
 __global__ void __launch_bounds__(MAXT, StageMinCtas<real, MAXT>::value) stage_kernel(const KArgs<real> a)
@@ -1136,7 +1143,7 @@ __device__ __forceinline__ unsigned long long warp_min_bits(real v)
 }
 
 template <typename real, int STAGE, bool FAST = false>
-__global__ void __launch_bounds__(256, (StageMinCtas<real, 256>::value)) batch_stage_kernel(const BatchMesh<real> *meshes, int n_mesh,
+__global__ void __launch_bounds__(256, (BatchMinCtas<real>::value)) batch_stage_kernel(const BatchMesh<real> *meshes, int n_mesh,
                                                           int n_items, int n_entries, DevScalars *sc_all)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
