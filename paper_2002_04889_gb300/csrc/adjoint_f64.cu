@@ -27,6 +27,23 @@ namespace vg {
 
 namespace {
 
+// Exact IEEE comparisons of FP64 values on the integer units (for every
+// non-NaN input), beside the sign and threshold tests of step_kernels.cuh:
+// the reverse kernels record which argument of a min / max or which side of a
+// test carried the value, so a tie between +0 and -0 must decide as FP64 does.
+__device__ __forceinline__ bool lt_x(double a, double b)      // a < b
+{
+    return okey(a) < okey(b) && ((dbits(a) | dbits(b)) << 1) != 0;
+}
+__device__ __forceinline__ bool lt_pos(double x, double y)    // x < y for y > 0
+{
+    return dbits(x) < dbits(y);
+}
+__device__ __forceinline__ bool gt_abs(double a, double b)    // |a| > |b|
+{
+    return (dbits(a) & 0x7fffffffffffffffLL) > (dbits(b) & 0x7fffffffffffffffLL);
+}
+
 struct AdjMesh {
     int nc, order;
     const double *geo;       // [GEO_ROWS][nc]
@@ -104,8 +121,8 @@ __device__ void recon_forward(const AdjMesh &m, const double *w, int K, ReconFwd
             double qmax = R.qK[v], qmin = R.qK[v];
             int imax = -1, imin = -1;
             for (int f = 0; f < 3; f++) {
-                if (R.qn[f][v] > qmax) { qmax = R.qn[f][v]; imax = f; }
-                if (R.qn[f][v] < qmin) { qmin = R.qn[f][v]; imin = f; }
+                if (lt_x(qmax, R.qn[f][v])) { qmax = R.qn[f][v]; imax = f; }
+                if (lt_x(R.qn[f][v], qmin)) { qmin = R.qn[f][v]; imin = f; }
             }
             double alpha = 1.0;
             int fa = -1;
@@ -115,9 +132,9 @@ __device__ void recon_forward(const AdjMesh &m, const double *w, int K, ReconFwd
                 R.D[v][f] = D;
                 double phi = 1.0, rr = 0.0;
                 bool lim = false;
-                if (D > 0.0) { rr = qmax - R.qK[v]; double t = rr / D; if (t < 1.0) { phi = t; lim = true; } }
-                else if (D < 0.0) { rr = qmin - R.qK[v]; double t = rr / D; if (t < 1.0) { phi = t; lim = true; } }
-                if (phi < alpha) { alpha = phi; fa = lim ? f : -1; ra = rr; }
+                if (is_pos(D)) { rr = qmax - R.qK[v]; double t = rr / D; if (lt_pos(t, 1.0)) { phi = t; lim = true; } }
+                else if (is_neg(D)) { rr = qmin - R.qK[v]; double t = rr / D; if (lt_pos(t, 1.0)) { phi = t; lim = true; } }
+                if (lt_x(phi, alpha)) { alpha = phi; fa = lim ? f : -1; ra = rr; }
             }
             R.alpha[v] = alpha;
             R.fa[v] = fa;
@@ -144,7 +161,7 @@ __device__ void recon_forward(const AdjMesh &m, const double *w, int K, ReconFwd
 // the flux VJP skips the face (the VJP of zero is zero).
 __device__ __forceinline__ bool rb_nonzero(const double *Rb, int nc, int k)
 {
-    return Rb[k] != 0.0 || Rb[nc + k] != 0.0 || Rb[2 * (size_t)nc + k] != 0.0;
+    return !is_zero(Rb[k]) || !is_zero(Rb[nc + k]) || !is_zero(Rb[2 * (size_t)nc + k]);
 }
 
 __global__ void adj_face_values_kernel(AdjMesh m, const double *w, const double *Rb, double *FV)
@@ -182,7 +199,7 @@ __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL,
     for (int k = 0; k < 4; k++) { bL[k] = 0.0; bR[k] = 0.0; }
     // ---- forward
     double uL = 0.0, vL = 0.0;
-    bool velL = HfL > hthr;
+    bool velL = gt_nn(HfL, hthr);
     if (velL) { uL = HufL / HfL; vL = HvfL / HfL; }
     double unL = uL * nx + vL * ny;
     double utL = -uL * ny + vL * nx;
@@ -191,22 +208,22 @@ __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL,
     double xL, xR = 0.0;
     if (wall) {
         xL = (HfL + zL) - zL;
-        actL = xL > 0.0;
+        actL = is_pos(xL);
         HsL = actL ? xL : 0.0;
         HsR = HsL;
         unR = open ? unL : -unL;
         utR = utL;
     } else {
-        velR = HfR > hthr;
+        velR = gt_nn(HfR, hthr);
         if (velR) { uR = HufR / HfR; vR = HvfR / HfR; }
         unR = uR * nx + vR * ny;
         utR = -uR * ny + vR * nx;
-        zR_max = zR > zL;
+        zR_max = lt_x(zL, zR);
         zs = zR_max ? zR : zL;
         xL = (HfL + zL) - zs;
         xR = (HfR + zR) - zs;
-        actL = xL > 0.0;
-        actR = xR > 0.0;
+        actL = is_pos(xL);
+        actR = is_pos(xR);
         HsL = actL ? xL : 0.0;
         HsR = actR ? xR : 0.0;
     }
@@ -219,16 +236,16 @@ __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL,
     if (!wall) { HfRb = PRb * hg * 2.0 * HfR; HsRb = -PRb * hg * 2.0 * HsR; }
     double unLb = 0.0, utLb = 0.0, unRb = 0.0, utRb = 0.0;
     // ---- reverse of HLL
-    if (!(HsL == 0.0 && HsR == 0.0)) {
+    if (!(is_zero(HsL) && is_zero(HsR))) {
         double cL = sqrt(g * HsL), cR = sqrt(g * HsR);
         double sL, sR, us = 0.0, cs = 0.0;
         int case_ = 0;    // 0 both wet, 1 L dry, 2 R dry
         bool sL_first = true, sR_first = true;
-        if (HsL == 0.0) {
+        if (is_zero(HsL)) {
             case_ = 1;
             sL = unR - 2.0 * cR;
             sR = unR + cR;
-        } else if (HsR == 0.0) {
+        } else if (is_zero(HsR)) {
             case_ = 2;
             sL = unL - cL;
             sR = unL + 2.0 * cL;
@@ -236,10 +253,10 @@ __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL,
             us = 0.5 * (unL + unR) + (cL - cR);
             cs = 0.5 * (cL + cR) - 0.25 * (unR - unL);
             double a1 = unL - cL, a2 = us - cs;
-            sL_first = !(a2 < a1);
+            sL_first = !lt_x(a2, a1);
             sL = sL_first ? a1 : a2;
             double b1 = us + cs, b2 = unR + cR;
-            sR_first = !(b2 > b1);
+            sR_first = !lt_x(b1, b2);
             sR = sR_first ? b1 : b2;
         }
         double qL = HsL * unL, qR = HsR * unR;
@@ -250,9 +267,9 @@ __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL,
         double Fb[3] = {Fb0, Fb1, Fb2};
         double FLb[3] = {0, 0, 0}, FRb[3] = {0, 0, 0}, wLb[3] = {0, 0, 0}, wRb[3] = {0, 0, 0};
         double sLb = 0.0, sRb = 0.0;
-        if (sL >= 0.0) {
+        if (!is_neg(sL)) {
             for (int k = 0; k < 3; k++) FLb[k] = Fb[k];
-        } else if (sR >= 0.0) {
+        } else if (!is_neg(sR)) {
             double den = sR - sL, sLR = sL * sR, iden = 1.0 / den;
             double denb = 0.0, sLRb = 0.0;
             for (int k = 0; k < 3; k++) {
@@ -289,9 +306,9 @@ __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL,
         HsRb += qRb * unR;
         unRb += qRb * HsR;
         // the wave speed a = max(|s_L|, |s_R|) (a tie takes |s_L|; |s| at s = 0 takes +s)
-        if (amb != 0.0) {
-            if (fabs(sR) > fabs(sL)) sRb += sR < 0.0 ? -amb : amb;
-            else sLb += sL < 0.0 ? -amb : amb;
+        if (!is_zero(amb)) {
+            if (gt_abs(sR, sL)) sRb += is_neg(sR) ? -amb : amb;
+            else sLb += is_neg(sL) ? -amb : amb;
         }
         // speeds
         double cLb = 0.0, cRb = 0.0;
@@ -314,8 +331,8 @@ __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL,
             unRb -= 0.25 * csb;
             unLb += 0.25 * csb;
         }
-        if (cL > 0.0) HsLb += cLb * (0.5 / cL) * g;
-        if (cR > 0.0) HsRb += cRb * (0.5 / cR) * g;
+        if (is_pos(cL)) HsLb += cLb * (0.5 / cL) * g;
+        if (is_pos(cR)) HsRb += cRb * (0.5 / cR) * g;
     }
     // ---- reverse of the interface depths and velocities
     if (wall) {
@@ -420,11 +437,11 @@ __global__ void adj_recon_vjp_kernel(AdjMesh m, const double *w, const double *R
     const int nc = m.nc;
     for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < nc; K += gridDim.x * blockDim.x) {
         double fb[3][3];   // [v][f]
-        bool any = m.rec[K] && (Rb[nc + K] != 0.0 || Rb[2 * (size_t)nc + K] != 0.0);
+        bool any = m.rec[K] && (!is_zero(Rb[nc + K]) || !is_zero(Rb[2 * (size_t)nc + K]));
         for (int v = 0; v < 3; v++)
             for (int f = 0; f < 3; f++) {
                 fb[v][f] = FVb[(v * 3 + f) * (size_t)nc + K];
-                any = any || fb[v][f] != 0.0;
+                any = any || !is_zero(fb[v][f]);
             }
         double zsl[3];
         for (int f = 0; f < 3; f++) zsl[f] = zfb[f * (size_t)nc + K];
@@ -481,7 +498,7 @@ __global__ void adj_recon_vjp_kernel(AdjMesh m, const double *w, const double *R
 #pragma unroll
                     for (int f = 0; f < 3; f++)
                         if (f == fa) Db[f] -= rb * R.r[v] * iD;
-                    int idx = D > 0.0 ? R.imax[v] : R.imin[v];
+                    int idx = is_pos(D) ? R.imax[v] : R.imin[v];
                     if (idx < 0) qKb[v] += rb;
 #pragma unroll
                     for (int f = 0; f < 3; f++)
@@ -559,8 +576,8 @@ __global__ void adj_gather_kernel(AdjMesh m, const double *own, const double *se
 // the momentum): its adjoint masks the incoming adjoint.
 __device__ __forceinline__ void dry_fix_mask(double Hpre, double hthr, double &Hb, double &Hub, double &Hvb)
 {
-    if (Hpre < 0.0) { Hb = 0.0; Hub = 0.0; Hvb = 0.0; }
-    else if (Hpre <= hthr) { Hub = 0.0; Hvb = 0.0; }
+    if (is_neg(Hpre)) { Hb = 0.0; Hub = 0.0; Hvb = 0.0; }
+    else if (!gt_nn(Hpre, hthr)) { Hub = 0.0; Hvb = 0.0; }
 }
 
 // w1 = fix(w + dt R0), keeping the pre-fix depth for the mask.
@@ -572,8 +589,8 @@ __global__ void adj_stage1_kernel(int nc, double dt, double hthr, const double *
         double Hu = w[nc + k] + dt * R0[nc + k];
         double Hv = w[2 * (size_t)nc + k] + dt * R0[2 * (size_t)nc + k];
         H1pre[k] = H;
-        if (H < 0.0) { H = 0.0; Hu = 0.0; Hv = 0.0; }
-        else if (H <= hthr) { Hu = 0.0; Hv = 0.0; }
+        if (is_neg(H)) { H = 0.0; Hu = 0.0; Hv = 0.0; }
+        else if (!gt_nn(H, hthr)) { Hu = 0.0; Hv = 0.0; }
         w1[k] = H;
         w1[nc + k] = Hu;
         w1[2 * (size_t)nc + k] = Hv;
@@ -642,36 +659,36 @@ __device__ double face_speed(const AdjMesh &m, double HfL, double HufL, double H
 {
     const double g = m.g, hthr = m.hthr;
     double uL = 0.0, vL = 0.0;
-    if (HfL > hthr) { uL = HufL / HfL; vL = HvfL / HfL; }
+    if (gt_nn(HfL, hthr)) { uL = HufL / HfL; vL = HvfL / HfL; }
     double unL = uL * nx + vL * ny;
     double HsL, HsR, unR;
     if (wall) {
-        HsL = fmax(0.0, (HfL + zL) - zL);
+        HsL = max0((HfL + zL) - zL);
         HsR = HsL;
         unR = open ? unL : -unL;
     } else {
         double uR = 0.0, vR = 0.0;
-        if (HfR > hthr) { uR = HufR / HfR; vR = HvfR / HfR; }
+        if (gt_nn(HfR, hthr)) { uR = HufR / HfR; vR = HvfR / HfR; }
         unR = uR * nx + vR * ny;
-        double zs = fmax(zL, zR);
-        HsL = fmax(0.0, (HfL + zL) - zs);
-        HsR = fmax(0.0, (HfR + zR) - zs);
+        double zs = smax(zL, zR);
+        HsL = max0((HfL + zL) - zs);
+        HsR = max0((HfR + zR) - zs);
     }
-    if (HsL == 0.0 && HsR == 0.0) return 0.0;
+    if (is_zero(HsL) && is_zero(HsR)) return 0.0;
     double cL = sqrt(g * HsL), cR = sqrt(g * HsR), sL, sR;
-    if (HsL == 0.0) {
+    if (is_zero(HsL)) {
         sL = unR - 2.0 * cR;
         sR = unR + cR;
-    } else if (HsR == 0.0) {
+    } else if (is_zero(HsR)) {
         sL = unL - cL;
         sR = unL + 2.0 * cL;
     } else {
         double us = 0.5 * (unL + unR) + (cL - cR);
         double cs = 0.5 * (cL + cR) - 0.25 * (unR - unL);
-        sL = fmin(unL - cL, us - cs);
-        sR = fmax(us + cs, unR + cR);
+        sL = smin(unL - cL, us - cs);
+        sR = smax(us + cs, unR + cR);
     }
-    return fmax(fabs(sL), fabs(sR));
+    return smax(fabs(sL), fabs(sR));
 }
 
 // The face states of face f of cell K (and its neighbour across it) from FV.
@@ -714,7 +731,7 @@ __device__ double cell_speed(const AdjMesh &m, const double *FV, int K, int &fma
         FaceIn q = face_in(m, FV, K, f);
         double la = q.l * face_speed(m, q.HfL, q.HufL, q.HvfL, q.zL, q.HfR, q.HufR, q.HvfR, q.zR, q.nx, q.ny, q.wall,
                                      q.open);
-        if (la > am) { am = la; fmax_out = f; }
+        if (gt_nn(la, am)) { am = la; fmax_out = f; }
     }
     return am;
 }
@@ -737,7 +754,7 @@ __global__ void adj_cfl_part_kernel(AdjMesh m, const double *FV, const int32_t *
     for (int K = blockIdx.x * blockDim.x + tid; K < nc; K += gridDim.x * blockDim.x) {
         int f;
         double am = cell_speed(m, FV, K, f);
-        if (!(am > 0.0)) continue;
+        if (!is_pos(am)) continue;
         double b = G(m, GEO_AREA, K) / (3.0 * am);
         if (cfl_less(b, orig[K], bb, bo)) { bb = b; bo = orig[K]; bk = K; }
     }
