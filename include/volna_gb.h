@@ -80,7 +80,7 @@ typedef struct vg_params {
                               the scheme (the oracle's order) bit for bit; 0 lets
                               the compiler contract multiply-adds and divides
                               once where the literal form divides several times
-                              by the same value: about 1.7x faster, rounding
+                              by the same value: about 1.8x faster, rounding
                               differences only, but over long runs with moving
                               shorelines those decide discontinuous switches
                               (a thin film's velocity, hence the CFL step)
