@@ -33,7 +33,7 @@ namespace {
 // test carried the value, so a tie between +0 and -0 must decide as FP64 does.
 __device__ __forceinline__ bool lt_x(double a, double b)      // a < b
 {
-    return okey(a) < okey(b) && ((dbits(a) | dbits(b)) << 1) != 0;
+    return okey(a) < okey(b) && ((ubits(a) | ubits(b)) << 1) != 0;
 }
 __device__ __forceinline__ bool lt_pos(double x, double y)    // x < y for y > 0
 {

@@ -102,17 +102,18 @@ __device__ __forceinline__ double vsqrt(double a) { return sqrt(a); }
 //   gt_nn(x, y): x > y for y >= +0;  is_zero(x): x == 0;  is_neg(x): x < 0;
 //   is_pos(x): x > 0;  smax / smin: max / min;  max0(x): max(0, x).
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ unsigned long long ubits(double x) { return (unsigned long long)__double_as_longlong(x); }
 __device__ __forceinline__ long long okey(double x)   // order-preserving for every non-NaN x
 {
     const long long b = dbits(x);
-    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+    return b < 0 ? b ^ 0x7fffffffffffffffLL : b;
 }
 __device__ __forceinline__ bool gt_nn(float x, float y) { return x > y; }
 __device__ __forceinline__ bool gt_nn(double x, double y) { return dbits(x) > dbits(y); }
 __device__ __forceinline__ bool is_zero(float x) { return x == 0.f; }
-__device__ __forceinline__ bool is_zero(double x) { return (dbits(x) << 1) == 0; }
+__device__ __forceinline__ bool is_zero(double x) { return (ubits(x) << 1) == 0; }
 __device__ __forceinline__ bool is_neg(float x) { return x < 0.f; }
-__device__ __forceinline__ bool is_neg(double x) { return dbits(x) < 0 && (dbits(x) << 1) != 0; }
+__device__ __forceinline__ bool is_neg(double x) { return dbits(x) < 0 && (ubits(x) << 1) != 0; }
 __device__ __forceinline__ bool is_pos(float x) { return x > 0.f; }
 __device__ __forceinline__ bool is_pos(double x) { return dbits(x) > 0; }
 __device__ __forceinline__ float smax(float a, float b) { return fmaxf(a, b); }
