@@ -64,6 +64,8 @@ def _load():
     lib.vo_bed_at.argtypes = [C.c_void_p, _D, _D, _D, C.c_double, C.c_double]
     lib.vo_set_open.argtypes = [C.c_void_p, C.c_int64, _I32]
     lib.vo_set_open.restype = C.c_int
+    lib.vo_set_boundary.argtypes = [C.c_void_p, C.c_int64, _I32, _I32]
+    lib.vo_set_boundary.restype = C.c_int
     lib.vo_locate.argtypes = [C.c_void_p, _D, C.c_int32, _D, _I32]
     lib.vo_mesh_get.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
     lib.vo_mesh_get.restype = C.c_int
@@ -115,13 +117,14 @@ def hll_speeds(g, HL, unL, HR, unR):
 def face_flux(g, hthr, left, zL, right, zR, n, wall=False):
     """Flux through a face seen from the left cell (hydrostatic reconstruction +
     HLL, Sec. 2.2; wall ghost of Sec. 2.5; wall="open" for the transmissive
-    ghost of vo_set_open).  left/right = (H_f, Hu_f, Hv_f).
+    ghost of vo_set_open, wall="absorbing" for the characteristic ghost of
+    vo_set_boundary).  left/right = (H_f, Hu_f, Hv_f).
     Returns (Phi[3], P_L, P_R, a)."""
     Phi = np.zeros(3)
     PL, PR, a = C.c_double(), C.c_double(), C.c_double()
     r = right if right is not None else (0.0, 0.0, 0.0)
     _load().vo_face_flux(g, hthr, left[0], left[1], left[2], zL, r[0], r[1], r[2], zR,
-                         n[0], n[1], 2 if wall == "open" else (1 if wall else 0), _dp(Phi), C.byref(PL), C.byref(PR),
+                         n[0], n[1], {"open": 2, "absorbing": 3}.get(wall, 1 if wall else 0), _dp(Phi), C.byref(PL), C.byref(PR),
                          C.byref(a))
     return Phi, PL.value, PR.value, a.value
 
@@ -228,6 +231,18 @@ class OracleMesh:
         rc = _load().vo_set_open(self._h, e.shape[0], e.ctypes.data_as(_I32))
         if rc != 0:
             raise ValueError("an edge is not a boundary face of the mesh")
+
+    def set_boundary(self, edges, kinds):
+        """Boundary kinds per edge [(a, b), ...]: 1 wall, 2 open, 3 absorbing (the
+        characteristic ghost of a sea at rest beyond the boundary); every other
+        boundary face a wall (vo_set_boundary)."""
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+        k = np.ascontiguousarray(np.asarray(kinds, dtype=np.int32).reshape(-1))
+        if k.shape[0] != e.shape[0]:
+            raise ValueError("one kind per edge")
+        rc = _load().vo_set_boundary(self._h, e.shape[0], e.ctypes.data_as(_I32), k.ctypes.data_as(_I32))
+        if rc != 0:
+            raise ValueError("an edge is not a boundary face of the mesh, or an unknown kind")
 
     def bed_at(self, depth0, uplift, onset, rise, t):
         """Sets the cell beds to the moving bed at time t (vo_bed_at) and returns them."""

@@ -68,7 +68,7 @@ typedef struct vo_mesh {
     int64_t nv, nc;
     int64_t n_flipped;   /* clockwise input triangles that were reoriented */
     int32_t *vtx;        /* [nc][3] vertex ids in local order              */
-    int32_t *nbr;        /* [nc][3] neighbour across face f, -1 wall, -2 open */
+    int32_t *nbr;        /* [nc][3] neighbour across face f, -1 wall, -2 open, -3 absorbing */
     int32_t *nbr_face;   /* [nc][3] the same face seen from the neighbour   */
     vo_real *z;                                 /* [nc] bed                 */
     vo_real *zf;                                /* [nc][3] bed at the face midpoints */
@@ -366,7 +366,12 @@ void vo_hll_normal(double g, vo_real HL, vo_real unL, vo_real utL,
  * states carry H* times that velocity.  A wall face (wall != 0) uses the ghost
  * state of Sec. 2.5: same depth and bed, normal velocity reversed, tangential
  * velocity kept.  An open face (wall == 2) uses the transmissive ghost of
- * vo_set_open: the left face state itself, velocity unchanged.  Outputs: Phi
+ * vo_set_open: the left face state itself, velocity unchanged.  An absorbing
+ * face (wall == 3) uses the characteristic ghost of vo_set_boundary: the
+ * outgoing Riemann invariant u_n + 2c of the face state and the incoming
+ * u_n - 2c of the sea at rest beyond the boundary (eta = 0 over the face's bed,
+ * c_0 = sqrt(g max(0, -z_L))) give u_n,g = (R+ + R-)/2 and c_g = max(0, (R+ - R-)/4),
+ * depth c_g^2 / g on the same bed, tangential velocity kept.  Outputs: Phi
  * (mass, x- and y-momentum flux along n), the two pressure corrections
  * P_s = g (H_{s,f}^2 - H*_s^2) / 2 and the wave speed.
  */
@@ -381,7 +386,16 @@ void vo_face_flux(double g, double hthr,
     vo_real unL = uL * nx + vL * ny;
     vo_real utL = -uL * ny + vL * nx;
     vo_real HsL, HsR, unR, utR;
-    if (wall) {
+    if (wall == 3) {
+        HsL = fmax(0.0, (HfL + zL) - zL);
+        vo_real cL = sqrt(g * HsL), c0 = sqrt(g * fmax(0.0, 0.0 - zL));
+        vo_real Rp = unL + 2.0 * cL, Rm = 0.0 - 2.0 * c0;
+        unR = 0.5 * (Rp + Rm);
+        vo_real cg = fmax(0.0, 0.25 * (Rp - Rm));
+        HsR = cg * cg / g;
+        utR = utL;
+        HfR = HsR;
+    } else if (wall) {
         HsL = fmax(0.0, (HfL + zL) - zL);
         HsR = HsL;
         unR = wall == 2 ? unL : -unL;
@@ -412,8 +426,8 @@ void vo_face_flux(double g, double hthr,
 /*
  * Face values of cell K.  The reconstructed variables are eta = H + z, Hu, Hv.
  * Each face neighbour contributes its cell value; a wall contributes the ghost
- * of Sec. 2.5 (same eta, momentum mirrored: m - 2 (m.n) n), an open face the
- * cell's own values (zero gradient across it).
+ * of Sec. 2.5 (same eta, momentum mirrored: m - 2 (m.n) n), an open or an
+ * absorbing face the cell's own values (zero gradient across it).
  *
  * The cell reconstructs (Eq. recon: w(x_f) = w_K + alpha_K grad(w)_K . (x_f - x_K))
  * only when it and every face neighbour are wetter than H_threshold and every
@@ -448,7 +462,7 @@ int vo_reconstruct_cell(const vo_mesh *m, const vo_params *p, const vo_real *H,
             qn[f][1] = Hu[j];
             qn[f][2] = Hv[j];
             if (!(H[j] > hthr)) recon = 0;
-        } else if (j == -2) {
+        } else if (j == -2 || j == -3) {
             qn[f][0] = qK[0];
             qn[f][1] = qK[1];
             qn[f][2] = qK[2];
@@ -556,7 +570,7 @@ void vo_residual(vo_mesh *m, const vo_params *p, const vo_real *H, const vo_real
                              m->nx[i], m->ny[i], 0, s, s + 3, s + 4, s + 5);
             } else {
                 vo_face_flux(g, hthr, m->Hf[i], m->Huf[i], m->Hvf[i], m->zfe[i],
-                             0.0, 0.0, 0.0, 0.0, m->nx[i], m->ny[i], j == -2 ? 2 : 1, s, s + 3, s + 4, s + 5);
+                             0.0, 0.0, 0.0, 0.0, m->nx[i], m->ny[i], j == -2 ? 2 : j == -3 ? 3 : 1, s, s + 3, s + 4, s + 5);
             }
         }
     }
@@ -775,7 +789,23 @@ int64_t vo_run_bed(vo_mesh *m, const vo_params *p, vo_real *H, vo_real *Hu, vo_r
  * and every other boundary face a wall.  VO_EINVAL if an edge is not a
  * boundary face of the mesh (nothing is changed then).
  */
+int vo_set_boundary(vo_mesh *m, int64_t n, const int32_t *edges, const int32_t *kinds);
+
 int vo_set_open(vo_mesh *m, int64_t n, const int32_t *edges)
+{
+    return vo_set_boundary(m, n, edges, NULL);
+}
+
+/*
+ * Boundary kinds per edge: kinds[k] = 1 wall, 2 open (vo_set_open), 3 absorbing
+ * (kinds NULL: all open); every other boundary face a wall.  Absorbing reading:
+ * the paper defers such conditions to Dutykh et al. 2011; here the
+ * characteristic condition of a sea at rest (eta = 0) beyond the boundary, the
+ * ghost of vo_face_flux (wall == 3), with the open face's zero-gradient ghost
+ * in the reconstruction.  VO_EINVAL for an edge that is not a boundary face or
+ * an unknown kind (nothing is changed then).
+ */
+int vo_set_boundary(vo_mesh *m, int64_t n, const int32_t *edges, const int32_t *kinds)
 {
     int32_t *mark = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1) * 2);
     if (!mark) return VO_ENOMEM;
@@ -792,9 +822,11 @@ int vo_set_open(vo_mesh *m, int64_t n, const int32_t *edges)
         if (found < 0) { free(mark); return VO_EINVAL; }
         mark[k] = (int32_t)found;
     }
+    for (int64_t k = 0; k < n; k++)
+        if (kinds && (kinds[k] < 1 || kinds[k] > 3)) { free(mark); return VO_EINVAL; }
     for (int64_t i = 0; i < 3 * m->nc; i++)
         if (m->nbr[i] < 0) m->nbr[i] = -1;
-    for (int64_t k = 0; k < n; k++) m->nbr[mark[k]] = -2;
+    for (int64_t k = 0; k < n; k++) m->nbr[mark[k]] = kinds ? -kinds[k] : -2;
     free(mark);
     return VO_OK;
 }
