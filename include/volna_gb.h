@@ -49,6 +49,11 @@ extern "C" {
 #define VG_RENUMBER_RCM 2
 #define VG_RENUMBER_HILBERT 3
 
+/* Boundary kinds (vg_set_boundary). */
+#define VG_BOUNDARY_WALL 1
+#define VG_BOUNDARY_OPEN 2
+#define VG_BOUNDARY_ABSORBING 3
+
 typedef struct vg_ctx vg_ctx;
 
 /* Scheme and run parameters.  Defaults from vg_default_params(). */
@@ -369,6 +374,21 @@ int vg_adj_bed_gradient(vg_ctx *ctx, double *dJ_duplift, double *dJ_donset);
  * differentiates through open faces as well. */
 int vg_set_open_boundary(vg_ctx *ctx, int64_t n, const int32_t *edges);
 
+/* Boundary kinds per edge: edges as for vg_set_open_boundary, kinds[k]
+ * (int32, host, copied; NULL: all open) VG_BOUNDARY_WALL, VG_BOUNDARY_OPEN or
+ * VG_BOUNDARY_ABSORBING; every other boundary face a wall.  An absorbing face
+ * (a reading: the paper defers such conditions to Dutykh et al. 2011) takes the
+ * characteristic ghost of a sea at rest at eta = 0 beyond the boundary: the
+ * outgoing Riemann invariant u_n + 2c comes from the face state, the incoming
+ * u_n - 2c = -2 c_0 from the rest state (c_0 = sqrt(g max(0, -z)) on the face's
+ * bed), giving u_n,g = (R+ + R-)/2, c_g = max(0, (R+ - R-)/4), depth c_g^2 / g,
+ * tangential velocity kept; the reconstruction sees it as the open ghost.
+ * Waves leave with far less reflection than through open faces, and water
+ * above or below the outer level flows out or in.  An edge that is not a
+ * boundary edge or an unknown kind: VG_EINVAL, nothing changed.  The adjoint
+ * (vg_adj_forward) does not differentiate absorbing faces: VG_EINVAL there. */
+int vg_set_boundary(vg_ctx *ctx, int64_t n, const int32_t *edges, const int32_t *kinds);
+
 /* Moving bed: the time-dependent depth h(x, y, t) of Sec. 2.1 (the governing
  * equations conserve the total depth H = h + eta while the bed moves), read as
  * a kinematic rupture: vertex v rises by uplift_v [nv] (metres, positive up),
@@ -453,6 +473,10 @@ int vg_batch_set_gauges(vg_batch *b, int32_t mesh_id, int32_t n, const double *x
 /* Open boundary edges of one mesh, shared by all its scenarios (as
    vg_set_open_boundary). */
 int vg_batch_set_open_boundary(vg_batch *b, int32_t mesh_id, int64_t n, const int32_t *edges);
+
+/* Boundary kinds per edge of one mesh, shared by all its scenarios (as
+   vg_set_boundary). */
+int vg_batch_set_boundary(vg_batch *b, int32_t mesh_id, int64_t n, const int32_t *edges, const int32_t *kinds);
 
 /* Records of one scenario: t [cap] and eta [cap][G] (G = the mesh's gauge
    count), copied up to cap records; *n_rec receives the number held (may

@@ -712,11 +712,16 @@ int vg_batch_set_gauges(vg_batch *b, int32_t mesh_id, int32_t n, const double *x
 
 int vg_batch_set_open_boundary(vg_batch *b, int32_t mesh_id, int64_t n, const int32_t *edges)
 {
+    return vg_batch_set_boundary(b, mesh_id, n, edges, nullptr);
+}
+
+int vg_batch_set_boundary(vg_batch *b, int32_t mesh_id, int64_t n, const int32_t *edges, const int32_t *kinds)
+{
     if (!b) return VG_EINVAL;
     if (mesh_id < 0 || mesh_id >= (int)b->meshes.size()) return bfail(b, VG_EINVAL, "no such mesh");
     DeviceGuard guard(b->device);
     vg_ctx *ctx = b->meshes[mesh_id].ctx;
-    int rc = vg_set_open_boundary(ctx, n, edges);
+    int rc = vg_set_boundary(ctx, n, edges, kinds);
     if (rc) return bfail(b, rc, vg_last_error(ctx));
     b->dirty = true;
     if (b->graph2) { cudaGraphExecDestroy(b->graph2); b->graph2 = nullptr; }

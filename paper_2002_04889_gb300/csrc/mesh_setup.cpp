@@ -454,6 +454,7 @@ int partition_blocks(HostMesh &m, int block, std::string &err)
                 int32_t j = m.nbr[f * nc + c];
                 if (j < 0) {
                     if (j == -2) nbrl[f * nc + c] = NBR_OPEN;
+                    else if (j == -3) nbrl[f * nc + c] = NBR_ABSORB;
                     continue;
                 }
                 nbrl[f * nc + c] = (uint16_t)((local_of(j) << 2) | nface[f * nc + c]);
@@ -464,6 +465,7 @@ int partition_blocks(HostMesh &m, int block, std::string &err)
                 uint16_t &code = m.ring1_nbr[3 * ((size_t)m.halo_ptr[b] + k) + f];
                 if (j >= 0) code = (uint16_t)local_of(j);
                 else if (j == -2) code = NBR_OPEN;
+                else if (j == -3) code = NBR_ABSORB;
             }
     }
     m.nbrl.swap(nbrl);
@@ -474,7 +476,7 @@ int partition_blocks(HostMesh &m, int block, std::string &err)
     m.fq_ptr.assign(nb + 1, 0);
     auto owned = [&](int64_t c, int64_t c0, int f) {
         const uint16_t code = m.nbrl[f * nc + c];
-        return code >= NBR_OPEN || (code >> 2) >= block || (int64_t)(code >> 2) > c - c0;
+        return code >= NBR_ABSORB || (code >> 2) >= block || (int64_t)(code >> 2) > c - c0;
     };
 #pragma omp parallel for schedule(dynamic, 256)
     for (int32_t b = 0; b < nb; b++) {

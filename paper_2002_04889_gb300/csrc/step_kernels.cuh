@@ -210,7 +210,9 @@ __device__ __forceinline__ void hll_normal(real g, real half_g, real HL, real un
 // the bed under side s's face value (its face bed if it reconstructed), HLL,
 // rotation back to (x, y), pressure corrections g (H_{s,f}^2 - H*_s^2) / 2.
 // bnd: 0 interior; 1 wall, the ghost of Sec. 2.5 (u_n reversed, u_t kept, same
-// depth); 2 open, the transmissive ghost (the face state itself).
+// depth); 2 open, the transmissive ghost (the face state itself); 3 absorbing,
+// the characteristic ghost (u_n + 2c of the face state, u_n - 2c = -2 c_0 of the
+// sea at rest with c_0 = sqrt(g max(0, -z)): depth c_g^2 / g, u_t kept).
 template <typename real, bool FAST = false>
 __device__ __forceinline__ void face_flux(real g, real half_g, real hthr,
                                           real HfL, real HufL, real HvfL, real zL,
@@ -230,7 +232,18 @@ __device__ __forceinline__ void face_flux(real g, real half_g, real hthr,
     real unL = uL * nx + vL * ny;
     real utL = -uL * ny + vL * nx;
     real HsL, HsR, unR, utR;
-    if (bnd) {
+    if (bnd == 3) {
+        // absorbing: the characteristic ghost of a sea at rest (eta = 0) beyond
+        // the boundary, on the same bed (the oracle's order of operations)
+        HsL = max0((HfL + zL) - zL);
+        const real cL = vsqrt(g * HsL), c0 = vsqrt(g * max0(real(0) - zL));
+        const real Rp = unL + real(2) * cL, Rm = real(0) - real(2) * c0;
+        unR = real(0.5) * (Rp + Rm);
+        const real cg = max0(real(0.25) * (Rp - Rm));
+        HsR = cg * cg / g;
+        utR = utL;
+        HfR = HsR;
+    } else if (bnd) {
         HsL = max0((HfL + zL) - zL);
         HsR = HsL;
         unR = bnd == 2 ? unL : -unL;
@@ -352,7 +365,19 @@ __device__ __forceinline__ void face_flux_dev(float g, float half_g, float hthr,
     float unL = uL * nx + vL * ny;
     float utL = -uL * ny + vL * nx;
     float HsL, HsR, unR, utR, ds, HfR;
-    if (bnd) {
+    if (bnd == 3) {
+        // absorbing: the outgoing invariant u_n + 2c of the face state and the
+        // incoming u_n - 2c of the sea at rest (eta = 0) beyond the boundary
+        HsL = fmaxf(0.f, HfL);
+        const float cL = sqrtf(g * HsL), c0 = sqrtf(g * fmaxf(0.f, -zL));
+        const float Rp = unL + 2.f * cL, Rm = -2.f * c0;
+        const float cg = fmaxf(0.f, 0.25f * (Rp - Rm));
+        unR = 0.5f * (Rp + Rm);
+        HsR = cg * cg / g;
+        utR = utL;
+        ds = HsL - HsR;
+        HfR = HsR; efR = zL + HsR; eR = efR; zR = zL;
+    } else if (bnd) {
         HsL = fmaxf(0.f, HfL);
         HsR = HsL;
         unR = bnd == 2 ? unL : -unL;
@@ -605,7 +630,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
             for (int f = 0; f < 3; f++) {
                 const uint16_t code = a.nbrl[f * nc + gid];
                 sCode[f * B + tid] = code;
-                if (!LISTED && (code >= NBR_OPEN || (code >> 2) >= B || (int)(code >> 2) > tid)) owned |= 1 << f;
+                if (!LISTED && (code >= NBR_ABSORB || (code >> 2) >= B || (int)(code >> 2) > tid)) owned |= 1 << f;
             }
             real W, Hu, Hv, zc;
             bool neg = stage_cell<real, STAGE>(a, gid, dt, W, Hu, Hv, zc);
@@ -731,7 +756,7 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
                 code = a.ring1_nbr[3 * (h0 + (l - B)) + f];
                 nl = code;
             }
-            if (code < NBR_OPEN) {
+            if (code < NBR_ABSORB) {
                 real Wj, Huj, Hvj, zj;
                 ld4(sW + 4 * nl, Wj, Huj, Hvj, zj);
                 const real Hj = ETA ? Wj - zj : Wj;
@@ -739,8 +764,8 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
                 qn[f][1] = Huj;
                 qn[f][2] = Hvj;
                 if (!gt_nn(Hj, hthr)) recon = false;
-            } else if (code == NBR_OPEN) {
-                // transmissive ghost: the cell's own values
+            } else if (code != NBR_WALL) {
+                // open or absorbing face: the cell's own values (zero gradient)
                 qn[f][0] = qK[0];
                 qn[f][1] = HuK;
                 qn[f][2] = HvK;
@@ -881,8 +906,8 @@ __device__ __forceinline__ void process_block(const KArgs<real> &a, const int b,
         const int l = item >> 2, f = item & 3;
         const int gid = c0 + l;
         const uint16_t code = sCode[f * B + l];
-        const bool wall = code >= NBR_OPEN;           // wall or open: no neighbour
-        const int bnd = wall ? (code == NBR_OPEN ? 2 : 1) : 0;
+        const bool wall = code >= NBR_ABSORB;         // wall, open or absorbing: no neighbour
+        const int bnd = wall ? (code == NBR_WALL ? 1 : code == NBR_OPEN ? 2 : 3) : 0;
         const int nl = code >> 2, nf = code & 3;
         real *pL = sF + 4 * (f * L1 + l);
         real *pR = sF + 4 * (nf * L1 + nl);

@@ -27,6 +27,8 @@ enum GeoRow : int {
 
 constexpr uint16_t NBR_WALL = 0xFFFF;   // wall face (ghost of Sec. 2.5); nbr = -1
 constexpr uint16_t NBR_OPEN = 0xFFFE;   // open (transmissive) face; nbr = -2
+constexpr uint16_t NBR_ABSORB = 0xFFFD; // absorbing (characteristic) face; nbr = -3; every code
+                                        // >= NBR_ABSORB is a boundary face
 
 // Host-side prepared mesh, cells in the library's (renumbered) order.
 struct HostMesh {
@@ -42,7 +44,7 @@ struct HostMesh {
     std::vector<double> z;               // [nc]            (internal order)
     std::vector<double> zf;              // [3][nc] bed at the face midpoints (internal order):
                                          // -(mean of the face's two vertex depths)
-    std::vector<int32_t> nbr;            // [3][nc] internal neighbour ids, -1 wall, -2 open
+    std::vector<int32_t> nbr;            // [3][nc] internal neighbour ids, -1 wall, -2 open, -3 absorbing
     std::vector<uint16_t> nbrl;          // [3][nc] (local << 2 | face), NBR_WALL or NBR_OPEN
     std::vector<int32_t> halo_ptr;       // [nblocks + 1] into halo_ids / ring1_nbr
     std::vector<int32_t> halo_n1;        // [nblocks] ring-1 cells of each block

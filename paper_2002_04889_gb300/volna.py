@@ -28,6 +28,7 @@ VG_ETIMEOUT = -6
 VG_ESTATE = -7
 
 RENUMBER = {"none": 0, "morton": 1, "rcm": 2, "hilbert": 3}
+BOUNDARY = {"wall": 1, "open": 2, "absorbing": 3}
 
 
 class VolnaError(RuntimeError):
@@ -90,6 +91,7 @@ _SIGNATURES = {
     "vg_set_bed_motion": ([_V, _D, _D, C.c_double], C.c_int),
     "vg_adj_bed_gradient": ([_V, _D, _D], C.c_int),
     "vg_set_open_boundary": ([_V, C.c_int64, _I32], C.c_int),
+    "vg_set_boundary": ([_V, C.c_int64, _I32, _I32], C.c_int),
     "vg_adj_forward": ([_V, C.c_int64, C.c_double, C.c_int64], C.c_int),
     "vg_adj_forward_binomial": ([_V, C.c_int64, C.c_double, C.c_int32], C.c_int),
     "vg_adj_backward": ([_V, _D, _D, _D, _D, _D, _D], C.c_int),
@@ -107,6 +109,7 @@ _SIGNATURES = {
     "vg_batch_info": ([_V, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _I64, _I64], C.c_int),
     "vg_batch_set_gauges": ([_V, C.c_int32, C.c_int32, _D], C.c_int),
     "vg_batch_set_open_boundary": ([_V, C.c_int32, C.c_int64, _I32], C.c_int),
+    "vg_batch_set_boundary": ([_V, C.c_int32, C.c_int64, _I32, _I32], C.c_int),
     "vg_batch_get_gauges": ([_V, C.c_int32, C.c_int32, _D, _D, C.c_int64, _I64], C.c_int),
 }
 
@@ -330,6 +333,16 @@ def vg_set_depth(ctx, depth_v) -> None:
     _check(ctx, load().vg_set_depth(ctx, _dp(d)))
 
 
+def _boundary_arrays(edges, kinds):
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    if isinstance(kinds, str):
+        kinds = [kinds] * e.shape[0]
+    k = np.ascontiguousarray([BOUNDARY[x] if isinstance(x, str) else int(x) for x in kinds], dtype=np.int32)
+    if k.shape[0] != e.shape[0]:
+        raise ValueError("one boundary kind per edge")
+    return e, k
+
+
 def vg_adj_forward(ctx, n_steps: int, dt: float, checkpoint_every: int = 0) -> None:
     _check(ctx, load().vg_adj_forward(ctx, int(n_steps), float(dt), int(checkpoint_every)))
 
@@ -469,6 +482,12 @@ class Solver:
         e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
         _check(self.ctx, load().vg_set_open_boundary(self.ctx, e.shape[0], e.ctypes.data_as(_I32)))
 
+    def set_boundary(self, edges, kinds) -> None:
+        """Boundary kinds per edge [(a, b), ...]: "wall", "open" or "absorbing" (or
+        1, 2, 3); every other boundary face a wall (vg_set_boundary)."""
+        e, k = _boundary_arrays(edges, kinds)
+        _check(self.ctx, load().vg_set_boundary(self.ctx, e.shape[0], e.ctypes.data_as(_I32), k.ctypes.data_as(_I32)))
+
     def set_bed_motion(self, uplift_v, onset_v=None, rise: float = 0.0) -> None:
         """Moving bed (vg_set_bed_motion); uplift_v None removes it."""
         if uplift_v is None:
@@ -597,6 +616,11 @@ class Batch:
         e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
         _bcheck(self.h, load().vg_batch_set_open_boundary(self.h, int(mesh_id), e.shape[0],
                                                           e.ctypes.data_as(_I32)))
+
+    def set_boundary(self, mesh_id: int, edges, kinds) -> None:
+        e, k = _boundary_arrays(edges, kinds)
+        _bcheck(self.h, load().vg_batch_set_boundary(self.h, int(mesh_id), e.shape[0], e.ctypes.data_as(_I32),
+                                                     k.ctypes.data_as(_I32)))
 
     def gauges(self, mesh_id: int, scen: int):
         """Gauge records (t [n], eta [n, G]) of one scenario."""
