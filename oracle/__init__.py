@@ -276,21 +276,27 @@ def _load_ad():
     lib.vo_ad_gauge_gradient_bed.restype = C.c_int
     lib.vo_ad_set_open.argtypes = [C.c_int64, _I32]
     lib.vo_ad_set_open.restype = C.c_int
+    lib.vo_ad_set_boundary.argtypes = [C.c_int64, _I32, _I32]
+    lib.vo_ad_set_boundary.restype = C.c_int
     _ad = lib
     return lib
 
 
 def ad_gauge_gradient(mesh, state, dt, n_steps, gauge_cells, weights, g=9.81, h_threshold=1e-5,
-                      order=2, cfl=0.9, bed_motion=None, open_edges=None):
+                      order=2, cfl=0.9, bed_motion=None, open_edges=None, boundary_kinds=None):
     """The oracle's discrete adjoint (tape AD of the oracle's own arithmetic) of
     J = sum_{n,g} weights[n, g] * eta_g(t_n), n = 0..n_steps (Sec. 2.3 steps), with
     the fixed time step dt, or for dt = 0 / None the CFL step of each step,
     differentiated through its minimum.  bed_motion = (uplift_v, onset_v, rise):
     the moving bed of vo_bed_at over the mesh's depths, also differentiated.
-    open_edges: boundary edges [(a, b), ...] made open (vo_set_open).
+    open_edges: boundary edges [(a, b), ...] made open (vo_set_open), or of the
+    kinds boundary_kinds [n] (1 wall, 2 open, 3 absorbing: vo_set_boundary).
     Returns dict(J, eta[n+1, G], dts[n], dH0, dHu0, dHv0, ddepth[, duplift, donset])."""
     oe = np.ascontiguousarray(np.asarray(open_edges if open_edges is not None else [], dtype=np.int32).reshape(-1, 2))
-    _load_ad().vo_ad_set_open(oe.shape[0], oe.ctypes.data_as(_I32))
+    bk = None
+    if boundary_kinds is not None:
+        bk = np.ascontiguousarray(np.broadcast_to(np.asarray(boundary_kinds, dtype=np.int32), (oe.shape[0],)))
+    _load_ad().vo_ad_set_boundary(oe.shape[0], oe.ctypes.data_as(_I32), None if bk is None else bk.ctypes.data_as(_I32))
     xy = _f64(mesh.xy).reshape(-1, 2)
     tri = np.ascontiguousarray(mesh.tri, dtype=np.int32)
     depth = _f64(mesh.depth)
@@ -316,7 +322,7 @@ def ad_gauge_gradient(mesh, state, dt, n_steps, gauge_cells, weights, g=9.81, h_
                                                  gc.ctypes.data_as(_I32), _dp(w), _dp(up), _dp(on),
                                                  float(bed_motion[2]), _dp(eta), _dp(dts), C.byref(J),
                                                  *(_dp(o) for o in out))
-    _load_ad().vo_ad_set_open(0, None)
+    _load_ad().vo_ad_set_boundary(0, None, None)
     if rc != 0:
         raise ValueError(f"oracle mesh rejected (code {rc})")
     r = dict(J=J.value, eta=eta, dts=dts[:n_steps], dH0=out[0], dHu0=out[1], dHv0=out[2], ddepth=out[3])

@@ -25,23 +25,34 @@ namespace vo_ad_impl {
 using vo_ad_impl::vo_mesh;
 using vo_ad_impl::vo_params;
 
-// Open boundary edges applied to every mesh the entry points below build
-// (vo_set_open); empty: all boundary faces are walls.
-static std::vector<int32_t> g_open_edges;
+// Boundary edges and their kinds (vo_set_boundary: 1 wall, 2 open, 3
+// absorbing) applied to every mesh the entry points below build; empty: all
+// boundary faces are walls.
+static std::vector<int32_t> g_bnd_edges, g_bnd_kinds;
 
-static int apply_open(vo_mesh *m)
+static int apply_boundary(vo_mesh *m)
 {
-    if (g_open_edges.empty()) return 0;
-    return vo_ad_impl::vo_set_open(m, (int64_t)(g_open_edges.size() / 2), g_open_edges.data());
+    if (g_bnd_kinds.empty()) return 0;
+    return vo_ad_impl::vo_set_boundary(m, (int64_t)g_bnd_kinds.size(), g_bnd_edges.data(), g_bnd_kinds.data());
 }
 
 extern "C" {
 
+/* The boundary edges [n][2] (vertex ids) and kinds [n] (NULL: all open) of the
+ * following calls; n = 0: walls. */
+int vo_ad_set_boundary(int64_t n, const int32_t *edges, const int32_t *kinds)
+{
+    if (n < 0) n = 0;
+    g_bnd_edges.assign(edges, edges + 2 * n);
+    g_bnd_kinds.assign((size_t)n, 2);
+    if (kinds) g_bnd_kinds.assign(kinds, kinds + n);
+    return 0;
+}
+
 /* The open boundary edges [n][2] (vertex ids) of the following calls; n = 0: walls. */
 int vo_ad_set_open(int64_t n, const int32_t *edges)
 {
-    g_open_edges.assign(edges, edges + 2 * (n > 0 ? n : 0));
-    return 0;
+    return vo_ad_set_boundary(n, edges, nullptr);
 }
 
 /*
@@ -72,7 +83,7 @@ int vo_ad_gauge_gradient(int64_t nv, const double *xy, int64_t nc, const int32_t
     vo_mesh *m = nullptr;
     int rc = vo_ad_impl::vo_mesh_build(nv, xy, nc, tri, depth.data(), &m);
     if (rc) return rc;
-    if ((rc = apply_open(m))) { vo_ad_impl::vo_mesh_free(m); return rc; }
+    if ((rc = apply_boundary(m))) { vo_ad_impl::vo_mesh_free(m); return rc; }
     vo_params p;
     vo_ad_impl::vo_default_params(&p);
     p.g = g;
@@ -137,7 +148,7 @@ int vo_ad_gauge_gradient_bed(int64_t nv, const double *xy, int64_t nc, const int
     vo_mesh *m = nullptr;
     int rc = vo_ad_impl::vo_mesh_build(nv, xy, nc, tri, depth.data(), &m);
     if (rc) return rc;
-    if ((rc = apply_open(m))) { vo_ad_impl::vo_mesh_free(m); return rc; }
+    if ((rc = apply_boundary(m))) { vo_ad_impl::vo_mesh_free(m); return rc; }
     vo_params p;
     vo_ad_impl::vo_default_params(&p);
     p.g = g;

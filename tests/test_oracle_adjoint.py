@@ -177,10 +177,13 @@ def test_oracle_adjoint_with_a_moving_bed():
     assert np.max(np.abs(ad["donset"])) > 0 and np.max(np.abs(ad["duplift"])) > 0
 
 
-def test_oracle_adjoint_with_open_boundaries():
+@pytest.mark.parametrize("absorbing", [False, True])
+def test_oracle_adjoint_with_open_boundaries(absorbing):
     """Open (transmissive) boundary faces on two sides of a 0.1 m basin whose hump
     drifts out through them, CFL steps: the taped gradients match central
-    differences of the open-boundary run."""
+    differences of the open-boundary run.  absorbing: the x side takes the
+    characteristic ghost of a sea at rest instead (its c_0 = sqrt(g h) brings the
+    bed into the ghost), the y side stays open."""
     m0 = I.flat_basin_mesh(12, 1.2, 0.1)
     # a gentle slope and curvature: on a perfectly flat bed every face is a tie of
     # max(z_L, z_R), where the depth derivative does not exist
@@ -195,11 +198,14 @@ def test_oracle_adjoint_with_open_boundaries():
     edges = np.concatenate([I.boundary_edges(m, lambda mid: mid[:, 0] > 1.19),
                             I.boundary_edges(m, lambda mid: mid[:, 1] < -1.19)])
     assert len(edges) > 5
-    ad = O.ad_gauge_gradient(m, st, None, n_steps, cells, w, h_threshold=1e-5, cfl=0.9, open_edges=edges)
+    n_x = len(I.boundary_edges(m, lambda mid: mid[:, 0] > 1.19))
+    kinds = np.array([3 if absorbing and e < n_x else 2 for e in range(len(edges))], dtype=np.int32)
+    ad = O.ad_gauge_gradient(m, st, None, n_steps, cells, w, h_threshold=1e-5, cfl=0.9, open_edges=edges,
+                             boundary_kinds=kinds)
 
     def J(state, depth):
         om = O.OracleMesh(m.xy, m.tri, depth)
-        om.set_open(edges)
+        om.set_boundary(edges, kinds)
         r = om.run(O.params(cfl=0.9), (state[0], state[1], state[2], 0.0), n_steps, gauge_cells=cells)
         z = om.get("z")
         return float(np.sum(w[0] * (state[0][cells] + z[cells])) + np.sum(w[1:] * r["gauges"]))
@@ -208,6 +214,10 @@ def test_oracle_adjoint_with_open_boundaries():
     assert ad["J"] == pytest.approx(J0, rel=1e-13, abs=1e-15)
     closed = O.ad_gauge_gradient(m, st, None, n_steps, cells, w, h_threshold=1e-5, cfl=0.9)
     assert np.linalg.norm(closed["dH0"] - ad["dH0"]) > 1e-6 * np.linalg.norm(ad["dH0"])
+    if absorbing:
+        opened = O.ad_gauge_gradient(m, st, None, n_steps, cells, w, h_threshold=1e-5, cfl=0.9, open_edges=edges)
+        for k in ("dH0", "ddepth"):
+            assert np.linalg.norm(opened[k] - ad[k]) > 1e-6 * np.linalg.norm(ad[k]), k
     # the state is nearly uniform, so limiter and wave-speed min/max kinks are dense:
     # central differences approach the adjoint as the step shrinks (the plateau)
     rng = np.random.default_rng(17)
