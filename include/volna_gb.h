@@ -386,7 +386,8 @@ int vg_set_open_boundary(vg_ctx *ctx, int64_t n, const int32_t *edges);
  * Waves leave with far less reflection than through open faces, and water
  * above or below the outer level flows out or in.  An edge that is not a
  * boundary edge or an unknown kind: VG_EINVAL, nothing changed.  The adjoint
- * (vg_adj_forward) does not differentiate absorbing faces: VG_EINVAL there. */
+ * differentiates all three kinds, the absorbing ghost's dependence on the bed
+ * (through c_0) included. */
 int vg_set_boundary(vg_ctx *ctx, int64_t n, const int32_t *edges, const int32_t *kinds);
 
 /* Moving bed: the time-dependent depth h(x, y, t) of Sec. 2.1 (the governing

@@ -70,8 +70,8 @@ __device__ __forceinline__ double bed_under(const AdjMesh &m, int K, int f)
 // kernels), keeping what the reverse needs.
 struct ReconFwd {
     double qK[3], qn[3][3];
-    bool wall[3];            // boundary face (wall or open)
-    bool open[3];            // open face: the ghost is the cell itself
+    bool wall[3];            // boundary face (wall, open or absorbing)
+    bool open[3];            // open or absorbing face: the ghost is the cell itself
     bool recon;
     double D[3][3];          // [v][f]
     double alpha[3];
@@ -94,13 +94,13 @@ __device__ void recon_forward(const AdjMesh &m, const double *w, int K, ReconFwd
     for (int f = 0; f < 3; f++) {
         int j = m.nbr[f * nc + K];
         R.wall[f] = j < 0;
-        R.open[f] = j == -2;
+        R.open[f] = j == -2 || j == -3;
         if (j >= 0) {
             R.qn[f][0] = H[j] + m.z[j];
             R.qn[f][1] = Hu[j];
             R.qn[f][2] = Hv[j];
             if (!(H[j] > m.hthr)) recon = false;
-        } else if (j == -2) {
+        } else if (R.open[f]) {
             R.qn[f][0] = R.qK[0];
             R.qn[f][1] = HuK;
             R.qn[f][2] = HvK;
@@ -188,12 +188,15 @@ __global__ void adj_face_values_kernel(AdjMesh m, const double *w, const double 
 // Reverse of the face flux seen from L (forward: face_flux / hll_normal).
 // Inputs: the two face states, beds, normal, wall flag, and the adjoints of
 // Phi[3], P_L, P_R and of the wave speed a = max(|s_L|, |s_R|) (amb: nonzero
-// only for the face that sets the CFL time step).  Outputs: adjoints of
-// (H_f, Hu_f, Hv_f, z) on each side.
+// only for the face that sets the CFL time step); bnd, the kind of a boundary
+// face: 1 wall, 2 open, 3 absorbing.  Outputs: adjoints of (H_f, Hu_f, Hv_f, z)
+// on each side.  The absorbing ghost (characteristic ghost of a sea at rest at
+// eta = 0 beyond the face) depends on the face state through the outgoing
+// invariant u_n + 2c and on the bed under the face through c_0 = sqrt(g max(0, -z)).
 __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL, double zL, double HfR,
                          double HufR, double HvfR, double zR, double nx, double ny, bool wall,
                          const double Pb[3], double PLb, double PRb, double bL[4], double bR[4],
-                         double amb = 0.0, bool open = false)
+                         double amb = 0.0, int bnd = 1)
 {
     const double g = m.g, hg = m.half_g, hthr = m.hthr;
     for (int k = 0; k < 4; k++) { bL[k] = 0.0; bR[k] = 0.0; }
@@ -206,12 +209,29 @@ __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL,
     double HsL, HsR, unR, utR, uR = 0.0, vR = 0.0, zs = 0.0;
     bool velR = false, zR_max = false, actL, actR = false;
     double xL, xR = 0.0;
-    if (wall) {
+    double cgL = 0.0, c0 = 0.0, cg = 0.0;    // absorbing ghost: c of the face state, of the sea, of the ghost
+    bool act0 = false, actg = false;
+    if (wall && bnd == 3) {
+        xL = (HfL + zL) - zL;
+        actL = is_pos(xL);
+        HsL = actL ? xL : 0.0;
+        cgL = sqrt(g * HsL);
+        const double x0 = 0.0 - zL;
+        act0 = is_pos(x0);
+        c0 = sqrt(g * (act0 ? x0 : 0.0));
+        const double Rp = unL + 2.0 * cgL, Rm = 0.0 - 2.0 * c0;
+        unR = 0.5 * (Rp + Rm);
+        const double y = 0.25 * (Rp - Rm);
+        actg = is_pos(y);
+        cg = actg ? y : 0.0;
+        HsR = cg * cg / g;
+        utR = utL;
+    } else if (wall) {
         xL = (HfL + zL) - zL;
         actL = is_pos(xL);
         HsL = actL ? xL : 0.0;
         HsR = HsL;
-        unR = open ? unL : -unL;
+        unR = bnd == 2 ? unL : -unL;
         utR = utL;
     } else {
         velR = gt_nn(HfR, hthr);
@@ -335,8 +355,18 @@ __device__ void flux_vjp(const AdjMesh &m, double HfL, double HufL, double HvfL,
         if (is_pos(cR)) HsRb += cRb * (0.5 / cR) * g;
     }
     // ---- reverse of the interface depths and velocities
-    if (wall) {
-        unLb += open ? unRb : -unRb;
+    if (wall && bnd == 3) {
+        // HsR = c_g^2 / g, c_g = max(0, (R+ - R-)/4), u_n,R = (R+ + R-)/2,
+        // R+ = u_n,L + 2 c_L, R- = -2 c_0
+        const double yb = actg ? HsRb * (2.0 * cg / g) : 0.0;
+        const double Rpb = 0.5 * unRb + 0.25 * yb, Rmb = 0.5 * unRb - 0.25 * yb;
+        unLb += Rpb;
+        if (is_pos(cgL)) HsLb += (2.0 * Rpb) * (0.5 / cgL) * g;
+        if (is_pos(c0) && act0) bL[3] -= (-2.0 * Rmb) * (0.5 / c0) * g;
+        utLb += utRb;
+        if (actL) { HfLb += HsLb; bL[3] += HsLb; bL[3] -= HsLb; }
+    } else if (wall) {
+        unLb += bnd == 2 ? unRb : -unRb;
         utLb += utRb;
         HsLb += HsRb;
         if (actL) { HfLb += HsLb; bL[3] += HsLb; bL[3] -= HsLb; }
@@ -411,7 +441,7 @@ __global__ void adj_flux_vjp_kernel(AdjMesh m, const double *FV, const double *R
             double bL[4], bR[4];
             flux_vjp(m, FV[(0 * 3 + f) * (size_t)nc + K], FV[(1 * 3 + f) * (size_t)nc + K],
                      FV[(2 * 3 + f) * (size_t)nc + K], bed_under(m, K, f), HfR, HufR, HvfR, zR, nx, ny, wall, Pb, PLb,
-                     PRb, bL, bR, 0.0, j == -2);
+                     PRb, bL, bR, 0.0, wall ? -j : 0);
             for (int v = 0; v < 3; v++) FVb[(v * 3 + f) * (size_t)nc + K] = bL[v];
             zfb[f * (size_t)nc + K] = bL[3];
             if (!wall) {
@@ -655,17 +685,24 @@ __global__ void adj_gauge_kernel(int n_gauges, const int32_t *cells, const doubl
 
 // Forward wave speed of one face, the forward kernels' arithmetic.
 __device__ double face_speed(const AdjMesh &m, double HfL, double HufL, double HvfL, double zL, double HfR,
-                             double HufR, double HvfR, double zR, double nx, double ny, bool wall, bool open)
+                             double HufR, double HvfR, double zR, double nx, double ny, bool wall, int bnd)
 {
     const double g = m.g, hthr = m.hthr;
     double uL = 0.0, vL = 0.0;
     if (gt_nn(HfL, hthr)) { uL = HufL / HfL; vL = HvfL / HfL; }
     double unL = uL * nx + vL * ny;
     double HsL, HsR, unR;
-    if (wall) {
+    if (wall && bnd == 3) {
+        HsL = max0((HfL + zL) - zL);
+        const double cL = sqrt(g * HsL), c0 = sqrt(g * max0(0.0 - zL));
+        const double Rp = unL + 2.0 * cL, Rm = 0.0 - 2.0 * c0;
+        unR = 0.5 * (Rp + Rm);
+        const double cg = max0(0.25 * (Rp - Rm));
+        HsR = cg * cg / g;
+    } else if (wall) {
         HsL = max0((HfL + zL) - zL);
         HsR = HsL;
-        unR = open ? unL : -unL;
+        unR = bnd == 2 ? unL : -unL;
     } else {
         double uR = 0.0, vR = 0.0;
         if (gt_nn(HfR, hthr)) { uR = HufR / HfR; vR = HvfR / HfR; }
@@ -695,7 +732,8 @@ __device__ double face_speed(const AdjMesh &m, double HfL, double HufL, double H
 struct FaceIn {
     double HfL, HufL, HvfL, zL, HfR, HufR, HvfR, zR, nx, ny, l;
     int j, fj;
-    bool wall, open;
+    bool wall;
+    int bnd;                 // boundary kind: 1 wall, 2 open, 3 absorbing (0: interior)
 };
 __device__ FaceIn face_in(const AdjMesh &m, const double *FV, int K, int f)
 {
@@ -703,7 +741,7 @@ __device__ FaceIn face_in(const AdjMesh &m, const double *FV, int K, int f)
     FaceIn r;
     r.j = m.nbr[f * nc + K];
     r.wall = r.j < 0;
-    r.open = r.j == -2;
+    r.bnd = r.wall ? -r.j : 0;
     r.fj = r.wall ? 0 : (m.nbrl[f * nc + K] & 3);
     r.HfL = FV[(0 * 3 + f) * (size_t)nc + K];
     r.HufL = FV[(1 * 3 + f) * (size_t)nc + K];
@@ -730,7 +768,7 @@ __device__ double cell_speed(const AdjMesh &m, const double *FV, int K, int &fma
     for (int f = 0; f < 3; f++) {
         FaceIn q = face_in(m, FV, K, f);
         double la = q.l * face_speed(m, q.HfL, q.HufL, q.HvfL, q.zL, q.HfR, q.HufR, q.HvfR, q.zR, q.nx, q.ny, q.wall,
-                                     q.open);
+                                     q.bnd);
         if (gt_nn(la, am)) { am = la; fmax_out = f; }
     }
     return am;
@@ -787,12 +825,12 @@ __global__ void adj_cfl_face_kernel(AdjMesh m, const double *FV, int nparts, con
     cell_speed(m, FV, K, f);
     const FaceIn q = face_in(m, FV, K, f);
     const double a = face_speed(m, q.HfL, q.HufL, q.HvfL, q.zL, q.HfR, q.HufR, q.HvfR, q.zR, q.nx, q.ny, q.wall,
-                                q.open);
+                                q.bnd);
     const double ab = -(*dtbar) * dtc / a;
     const double P0[3] = {0.0, 0.0, 0.0};
     double bL[4], bR[4];
     flux_vjp(m, q.HfL, q.HufL, q.HvfL, q.zL, q.HfR, q.HufR, q.HvfR, q.zR, q.nx, q.ny, q.wall, P0, 0.0, 0.0, bL, bR, ab,
-             q.open);
+             q.bnd);
     const int nc = m.nc;
     for (int v = 0; v < 3; v++) FVb[(v * 3 + f) * (size_t)nc + K] += bL[v];
     zfb[f * (size_t)nc + K] += bL[3];

@@ -67,7 +67,6 @@ struct vg_ctx {
     std::vector<double> depth_v;
     bool bed_on = false;
     int64_t n_open = 0;                 // open or absorbing boundary faces (vg_set_boundary)
-    int64_t n_absorb = 0;               // of which absorbing
     int32_t *bed_vtx = nullptr;
     double *bed_depth0 = nullptr, *bed_uplift = nullptr, *bed_onset = nullptr;
     double bed_rise = 0.0;
@@ -162,7 +161,6 @@ void free_mesh(vg_ctx *c)
     dfree(c->bed_vtx); dfree(c->bed_depth0); dfree(c->bed_uplift); dfree(c->bed_onset);
     c->bed_on = false;
     c->n_open = 0;
-    c->n_absorb = 0;
     c->depth_v.clear();
     c->dev_bytes = 0;
     c->has_mesh = c->has_state = false;
@@ -1183,12 +1181,11 @@ int vg_set_boundary(vg_ctx *c, int64_t n, const int32_t *edges, const int32_t *k
         open[e] = it->second;
     }
     for (auto &kv : face_of) m.nbr[kv.second] = -1;
-    int64_t n_open = 0, n_absorb = 0;
+    int64_t n_open = 0;
     for (int64_t e = 0; e < n; e++) {
         const int kind = kinds ? kinds[e] : VG_BOUNDARY_OPEN;
         m.nbr[open[e]] = -kind;                     // -1 wall, -2 open, -3 absorbing
         n_open += kind != VG_BOUNDARY_WALL;
-        n_absorb += kind == VG_BOUNDARY_ABSORBING;
     }
     VG_CUDA(c, cudaStreamSynchronize(c->stream));
     int rc = partition_blocks(m, m.block, c->err);
@@ -1196,7 +1193,6 @@ int vg_set_boundary(vg_ctx *c, int64_t n, const int32_t *edges, const int32_t *k
     if ((rc = upload_partition(c))) return rc;
     VG_CUDA(c, cudaMemcpy(c->nbr, m.nbr.data(), 4 * 3 * (size_t)nc, cudaMemcpyHostToDevice));
     c->n_open = n_open;
-    c->n_absorb = n_absorb;
     c->graph_dirty = true;
     return VG_OK;
 }
@@ -1260,7 +1256,6 @@ int vg_adj_forward(vg_ctx *c, int64_t n_steps, double dt, int64_t checkpoint_eve
     if (c->precision != 64) return fail(c, VG_EINVAL, "the adjoint runs in FP64 contexts");
     if (!c->has_mesh || !c->has_state) return fail(c, VG_ESTATE, "mesh and state must be set");
     if (c->n_gauges < 1) return fail(c, VG_ESTATE, "the adjoint differentiates gauge records: set gauges first");
-    if (c->n_absorb > 0) return fail(c, VG_EINVAL, "the adjoint does not differentiate absorbing boundary faces");
     DeviceGuard guard(c->device);
     free_adjoint(c);
     // default segment length: the one that minimises device memory, C checkpoints'

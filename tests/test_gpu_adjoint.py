@@ -280,10 +280,13 @@ def test_adjoint_with_moving_bed_matches_oracle(adaptive):
     assert np.max(np.abs(go)) > 0 and np.max(np.abs(gu)) > 0
 
 
-def test_adjoint_with_open_boundaries_matches_oracle():
+@pytest.mark.parametrize("absorbing", [False, True])
+def test_adjoint_with_open_boundaries_matches_oracle(absorbing):
     """Two sides of a 0.1 m basin open, a hump drifting out through them, CFL steps
     (3,200 triangles, 25 steps): the GPU gradients equal the oracle's taped ones
-    (same open edges) to 1e-10."""
+    (same open edges) to 1e-10.  absorbing: the x side takes the characteristic
+    ghost of a sea at rest (whose c_0 brings the bed into the ghost), the y side
+    stays open."""
     m0 = I.flat_basin_mesh(40, 1.0, 0.1)
     # a gentle slope and curvature: on a perfectly flat bed every face is a tie of
     # max(z_L, z_R), where the depth derivative does not exist
@@ -296,16 +299,19 @@ def test_adjoint_with_open_boundaries_matches_oracle():
     edges = np.concatenate([I.boundary_edges(m, lambda mid: mid[:, 0] > 0.999),
                             I.boundary_edges(m, lambda mid: mid[:, 1] < -0.999)])
     assert len(edges) > 10
+    n_x = len(I.boundary_edges(m, lambda mid: mid[:, 0] > 0.999))
+    kinds = np.array([3 if absorbing and e < n_x else 2 for e in range(len(edges))], dtype=np.int32)
     W = np.random.default_rng(29).normal(size=(n_steps + 1, len(cells)))
     with volna.Solver(64) as sv:
         sv.set_params(h_threshold=1e-5, cfl=0.9)
         sv.upload_mesh(m)
-        sv.set_open_boundary(edges)
+        sv.set_boundary(edges, kinds)
         sv.set_gauges(LATTICE)
         sv.set_state(*st, 0.0)
         _, eta = sv.adj_forward(n_steps, 0.0)
         g = sv.adj_backward(W, m.nv)
-    ad = O.ad_gauge_gradient(m, st, None, n_steps, cells, W, h_threshold=1e-5, cfl=0.9, open_edges=edges)
+    ad = O.ad_gauge_gradient(m, st, None, n_steps, cells, W, h_threshold=1e-5, cfl=0.9, open_edges=edges,
+                             boundary_kinds=kinds)
     np.testing.assert_allclose(eta, ad["eta"], rtol=0, atol=1e-13)
     for k_gpu, k_or in (("H0", "dH0"), ("Hu0", "dHu0"), ("Hv0", "dHv0"), ("depth", "ddepth")):
         err = _rel(g[k_gpu], ad[k_or])
