@@ -295,7 +295,9 @@ int vg_step_noalloc(vg_ctx *ctx, const void *w_in, void *w_out, double t, double
  * choices, HLL regions -- frozen where the run takes them), and the gauge
  * records eta_g(t_n) = H + z of the gauge cells (Sec. 3 gauges) are outputs of
  * it.  vg_adj_backward returns the gradient of any scalar J(eta) given
- * dJ/deta, with respect to the initial state and the bathymetry.
+ * dJ/deta, with respect to the initial state and the bathymetry.  Every
+ * boundary kind of vg_set_boundary (wall, open, absorbing) and a moving bed
+ * (vg_set_bed_motion) are differentiated.
  * ------------------------------------------------------------------------ */
 
 /* Replace the per-vertex bathymetry depth (as in vg_mesh_upload) of the
