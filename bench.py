@@ -20,6 +20,8 @@ One JSON line on rank 0:
                interface (f64_host)
   roofline     the dominant kernel's algorithmic bytes per launch over its
                CUDA-event duration, against the measured HBM copy bandwidth
+               (MEASURED_PEAKS.json; without it the 6800 GB/s fallback,
+               named in peak_kind)
   cpu_baseline the FP64 CPU oracle timed on this host on a bounded sample
                of the same workload
 
